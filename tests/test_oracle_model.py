@@ -1,0 +1,260 @@
+"""Pins of the CPU oracle's model, discretisation and Newton loop against
+closed forms, invariants and finite differences (no GPU needed).
+
+Passages: eqs. (3)-(18) (model and discretisation), eq. (10) (wells),
+Algorithm 1 (Newton), eq. (26) (forcing term) of arXiv 1701.06254.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1701_06254_gb300 import inputs as I
+
+CDARCY = 9.869233e-16 * 1e5 / 1e-3 * 86400.0   # m3 cP / (day bar mD m)
+
+
+def incompressible_fluid(g=0.0):
+    return I.Fluid(c_f=(0.0, 0.0), c_r=0.0, c_mu=(0.0, 0.0), g=g)
+
+
+def line_case(nx, dx, k, q_inj, p_bhp, sw0, inj_at_start=True, dt=1.0, phi=0.2, fluid=None, p0=None):
+    n = nx
+    kk = np.full(n, float(k))
+    c = I.Case(f"line{nx}", nx, 1, 1, dx, 1.0, 1.0, 1000.0, kk, kk.copy(), kk.copy(),
+               np.full(n, phi), fluid or incompressible_fluid(), [], dt=dt, n_steps=1,
+               p_init=p_bhp + 10.0 if p0 is None else p0, sw_init=sw0)
+    a, b = (0, nx - 1) if inj_at_start else (nx - 1, 0)
+    c.wells = [I.Well(I.INJ, I.WRATE, q_inj, [a]), I.Well(I.PROD, I.BHP, p_bhp, [b])]
+    return c
+
+
+def test_linear_pressure_profile(oracle_lib):
+    """Homogeneous, incompressible, single-phase water (s_w = 1 - S_or, so
+    k_ro = 0) between a rate injector and a BHP producer: Darcy's law,
+    eq. (1), gives a linear pressure with drop q mu_w dx / (C_D k A) per
+    cell, exact for two-point fluxes; the well drops follow eq. (10)."""
+    q, mu_w, k, dx, A = 10.0, 0.5, 100.0, 10.0, 100.0
+    c = line_case(50, dx, k, q, 100.0, 0.8)
+    c.dy = c.dz = 10.0
+    s = oracle_lib.Sim(c, newton_tol=1e-13, lin_tol=1e-13, max_lin=200)
+    s.init_hydrostatic()
+    assert s.advance(1) == 0
+    p, sw, pb, t = s.get_state()
+    T = CDARCY * k * A / dx
+    dp_expect = q * mu_w / T
+    np.testing.assert_allclose(np.diff(p), -dp_expect, rtol=1e-10)
+    np.testing.assert_allclose(sw, 0.8, atol=1e-12)
+    wi = s.well_index()
+    # producer: rho q = WI rho (k_rw / mu_w) (p - p_b), k_rw = 1
+    np.testing.assert_allclose(p[-1] - pb[1], q * mu_w / wi[1], rtol=1e-10)
+    # injector uses the total mobility k_rw/mu_w + k_ro/mu_o = 1/mu_w here
+    np.testing.assert_allclose(pb[0] - p[0], q * mu_w / wi[0], rtol=1e-10)
+    qw, qo = s.well_rates()
+    np.testing.assert_allclose(qw, [1000.0 * q, -1000.0 * q], rtol=1e-10)
+
+
+def test_peaceman_isotropic_square(oracle_lib):
+    """Peaceman's equivalent radius for an isotropic square cell is
+    0.14 sqrt(dx^2 + dy^2) = 0.198 dx (the classical result)."""
+    c = I.small_case(3, 3, 2, seed=1)
+    k = 50.0
+    c.kx[:] = k; c.ky[:] = k; c.kz[:] = 0.1 * k
+    s = oracle_lib.Sim(c)
+    wi = s.well_index()
+    ro = 0.14 * math.sqrt(2.0) * c.dx
+    expect = 2 * math.pi * CDARCY * k * c.dz / math.log(ro / 0.1)
+    np.testing.assert_allclose(wi, expect, rtol=1e-13)
+
+
+def _closed_form_accumulation(case, p, sw):
+    """phi rho_a s_a from eqs. (4), (6), (8) (oil, water), per cell."""
+    f = case.fluid
+    phi = case.phi * (1.0 + f.c_r * (p - f.p_ref))
+    rw = f.rho_ref[0] * (1.0 + f.c_f[0] * (p - f.p_ref))
+    ro = f.rho_ref[1] * (1.0 + f.c_f[1] * (p - f.p_ref))
+    return phi * ro * (1.0 - sw), phi * rw * sw
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_mass_balance_identity(oracle_lib, seed):
+    """Face fluxes cancel pairwise (the paper's conservation remark after
+    eq. 17), so for ANY state the sum of the residuals of eq. (17) over all
+    cells equals the total accumulation change minus the well rates."""
+    c = I.small_case(5, 4, 3, seed=seed)
+    s = oracle_lib.Sim(c)
+    p0, s0, pb0 = I.random_state(c, seed + 100)
+    p1, s1, pb1 = I.random_state(c, seed + 200)
+    s.set_state(p0, s0, pb0); s.store_old()
+    s.set_state(p1, s1, pb1); s.set_dt(2.0)
+    s.assemble()
+    rp, ci, val, b, key = s.system()
+    R = -b[:2 * c.n].reshape(c.n, 2)
+    ao0, aw0 = _closed_form_accumulation(c, p0, s0)
+    ao1, aw1 = _closed_form_accumulation(c, p1, s1)
+    V = c.dx * c.dy * c.dz
+    qw, qo = s.well_rates()
+    exp_o = (V / 2.0) * (ao1 - ao0).sum() - qo.sum()
+    exp_w = (V / 2.0) * (aw1 - aw0).sum() - qw.sum()
+    scale_o = (V / 2.0) * np.abs(ao1 - ao0).sum()
+    scale_w = (V / 2.0) * np.abs(aw1 - aw0).sum()
+    assert abs(R[:, 0].sum() - exp_o) <= 1e-9 * scale_o
+    assert abs(R[:, 1].sum() - exp_w) <= 1e-9 * scale_w
+    # and the residual is not trivially balanced: individual rows are large
+    assert np.abs(R[:, 0]).max() > 1e-3 * scale_o / c.n
+
+
+def _dense_J(rp, ci, val, nb):
+    J = np.zeros((2 * nb, 2 * nb))
+    for i in range(nb):
+        for q in range(rp[i], rp[i + 1]):
+            j = ci[q]
+            J[2 * i:2 * i + 2, 2 * j:2 * j + 2] = val[4 * q:4 * q + 4].reshape(2, 2)
+    return J
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_jacobian_matches_finite_differences(oracle_lib, seed):
+    """Analytic 2x2-block Jacobian vs central differences of the residual
+    (eq. 17 with upstreaming eq. 18 and wells eq. 10) at a random state
+    away from relative-permeability and upstream kinks."""
+    c = I.small_case(3, 3, 2, seed=seed)
+    s = oracle_lib.Sim(c)
+    p0, s0, pb0 = I.random_state(c, seed + 10)
+    p1, s1, pb1 = I.random_state(c, seed + 20)
+    s.set_state(p0, s0, pb0); s.store_old()
+    s.set_dt(1.5)
+    s.set_state(p1, s1, pb1); s.assemble()
+    rp, ci, val, b, key = s.system()
+    nb = c.n + len(c.wells)
+    J = _dense_J(rp, ci, val, nb)
+    x0 = np.concatenate([np.stack([p1, s1], 1).ravel(), np.stack([pb1, np.zeros_like(pb1)], 1).ravel()])
+
+    def resid(x):
+        xc = x[:2 * c.n].reshape(c.n, 2); xw = x[2 * c.n:].reshape(-1, 2)
+        s.set_state(xc[:, 0], xc[:, 1], xw[:, 0]); s.assemble()
+        return -s.system()[3]
+
+    Jfd = np.zeros_like(J)
+    for k in range(2 * nb):
+        if k >= 2 * c.n and k % 2 == 1:
+            continue                      # padded dummy unknown of a well row
+        h = 1e-6 * max(1.0, abs(x0[k])) if k % 2 == 0 else 1e-7
+        xp = x0.copy(); xp[k] += h
+        xm = x0.copy(); xm[k] -= h
+        Jfd[:, k] = (resid(xp) - resid(xm)) / (2 * h)
+    Jfd[2 * c.n + 1::2, 2 * c.n + 1::2] = J[2 * c.n + 1::2, 2 * c.n + 1::2]
+    rowscale = np.abs(J).max(axis=1, keepdims=True)
+    err = np.abs(Jfd - J) / rowscale
+    assert err.max() < 1e-6, err.max()
+
+
+def test_hydrostatic_initial_state_is_at_rest(oracle_lib):
+    """The initial state gives every cell the datum oil potential (eq. 5)
+    with s_w = S_wc (no water mobility): without wells nothing moves."""
+    c = I.small_case(4, 4, 5, seed=9)
+    c.wells = []
+    s = oracle_lib.Sim(c, newton_tol=1e-12, lin_tol=1e-12)
+    s.init_hydrostatic()
+    p0, s0, _, _ = s.get_state()
+    assert np.all(np.diff(p0.reshape(5, 16)[:, 0]) > 0)       # pressure rises with depth
+    assert s.advance(2) == 0
+    p1, s1, _, _ = s.get_state()
+    np.testing.assert_allclose(p1, p0, rtol=1e-12)
+    np.testing.assert_allclose(s1, s0, atol=1e-14)
+
+
+def test_forcing_term_choice_two(oracle_lib):
+    """Eq. (26), second choice, with the clamp to [0.01, 0.1]; eta_0 = 0.1."""
+    f = oracle_lib.forcing
+    assert f(0, 5.0, 1.0, 2.0) == 0.1
+    assert f(3, 1.0, 0.95, 2.0) == pytest.approx(0.025, rel=1e-15)     # inside the band
+    assert f(3, 1.0, 0.99999, 10.0) == 0.01                              # clamped low
+    assert f(3, 5.0, 0.0, 2.0) == 0.1                                    # clamped high
+    assert f(3, 1.0, 2.0, 3.0) == 0.01                                   # negative -> 0.01
+
+
+# ---------------------------------------------------------------------------
+# Buckley-Leverett: 1D, incompressible, no gravity, no capillary pressure.
+# Corey n = 2, S_wc = S_or = 0.2, M = mu_o / mu_w = 4.  The Welge tangent
+# gives s_hat_f = 1/sqrt(5): S_f = 0.2 + 0.6/sqrt(5) = 0.468328, and the
+# front travels at q/(phi A) * df_w/dS_w(S_f) = q/(phi A) * 2.696723.
+# ---------------------------------------------------------------------------
+def _fw(s, muw=0.5, muo=2.0):
+    sh = np.clip((s - 0.2) / 0.6, 0, 1)
+    lw, lo = sh ** 2 / muw, (1 - sh) ** 2 / muo
+    return lw / (lw + lo)
+
+
+def _dfw(s, muw=0.5, muo=2.0):
+    sh = np.clip((s - 0.2) / 0.6, 0, 1)
+    lw, lo = sh ** 2 / muw, (1 - sh) ** 2 / muo
+    dlw, dlo = 2 * sh / muw / 0.6, -2 * (1 - sh) / muo / 0.6
+    return (dlw * (lw + lo) - lw * (dlw + dlo)) / (lw + lo) ** 2
+
+
+def test_welge_constants():
+    sf = 0.2 + 0.6 / math.sqrt(5.0)
+    assert sf == pytest.approx(0.468328, abs=1e-6)
+    assert _fw(sf) == pytest.approx(0.723607, abs=1e-6)
+    # tangent from (S_wc, 0): f_w(S_f) / (S_f - S_wc) = f_w'(S_f)
+    assert _dfw(sf) == pytest.approx(_fw(sf) / (sf - 0.2), rel=1e-12)
+    assert _dfw(sf) == pytest.approx(2.696723, abs=1e-6)
+
+
+def _bl_analytic(x, t, q, phi, A):
+    sf = 0.2 + 0.6 / math.sqrt(5.0)
+    v = x * phi * A / (q * t)
+    out = np.full_like(x, 0.2)
+    for i, vi in enumerate(v):
+        if vi < _dfw(sf):
+            lo, hi = sf, 0.8 - 1e-12
+            if vi <= _dfw(hi):
+                out[i] = hi
+                continue
+            for _ in range(80):
+                mid = 0.5 * (lo + hi)
+                if _dfw(mid) > vi:
+                    lo = mid
+                else:
+                    hi = mid
+            out[i] = 0.5 * (lo + hi)
+    return out
+
+
+def _bl_run(oracle_lib, nx, nsteps, t_end):
+    L, q, phi = 100.0, 0.02, 0.2
+    fl = incompressible_fluid()
+    c = line_case(nx, L / nx, 100.0, q, 100.0, 0.2, dt=t_end / nsteps, phi=phi, fluid=fl)
+    s = oracle_lib.Sim(c, newton_tol=1e-9, lin_tol=1e-10, max_lin=200)
+    s.init_hydrostatic()
+    assert s.advance(nsteps) == 0
+    p, sw, pb, t = s.get_state()
+    x = (np.arange(nx) + 0.5) * (L / nx)
+    return x, sw, _bl_analytic(x, t, q, phi, 1.0)
+
+
+def test_buckley_leverett_front(oracle_lib):
+    """The saturation front sits at x_f = q t / (phi A) * 2.696723; the
+    first-order implicit upwind scheme smears it ahead of x_f by a distance
+    that shrinks under refinement (3.0 m at dx = 1 m, 1.8 m at 0.5 m)."""
+    t_end = 150.0
+    xf = 0.02 * t_end / 0.2 * 2.696723                        # 40.45 m
+    mid = 0.5 * (0.2 + 0.2 + 0.6 / math.sqrt(5.0))
+    gaps = []
+    for nx in (100, 200):
+        x, sw, ex = _bl_run(oracle_lib, nx, nx * 3 // 2, t_end)
+        gaps.append(x[np.nonzero(sw < mid)[0][0]] - xf)
+        # saturation never exceeds 1 - S_or and the injected water is all in place
+        assert sw.max() <= 0.8 + 1e-9
+        np.testing.assert_allclose(((sw - 0.2) * 0.2 * (100.0 / nx)).sum(), 0.02 * t_end, rtol=1e-6)
+    assert 0.0 < gaps[1] < gaps[0] <= 3.5, gaps
+    assert gaps[1] <= 2.5, gaps
+
+
+def test_buckley_leverett_converges_under_refinement(oracle_lib):
+    errs = []
+    for nx in (50, 100, 200):
+        x, sw, ex = _bl_run(oracle_lib, nx, nx, 150.0)
+        errs.append(np.abs(sw - ex).mean())
+    assert errs[0] > errs[1] > errs[2], errs
