@@ -1,0 +1,291 @@
+"""Benchmark: cell-timesteps/s of the GPU CPR-FGMRES Newton path.
+
+A step is one time step of the 200x200x25 channelised case (1M cells,
+13 wells, dt = 10 days): Newton iterations with assembly, ABF decoupling,
+per-subdomain potential reordering, RAS/BILU(0) and PMIS-AMG setup and
+CPR-FGMRES solves to relres 1e-6, all on the device.  Inputs are resident
+in HBM when the timed region starts; the working set (2x2 BSR Jacobian,
+Krylov basis) is larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+  python bench.py --impl reference     # the CPU oracle on the same workload
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-timesteps/s at 1M cells, relres 1e-6: mixed+learned vs plain FP64; %HBM peak"
+UNIT = "cell-timesteps/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock, power and throttle reasons."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            v = [x.strip() for x in line.split(",")]
+            if len(v) >= 9:
+                try:
+                    rows.append((float(v[1]), float(v[2]), float(v[3]), v[5], v[6], v[7], v[8]))
+                except ValueError:
+                    pass
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        reasons = set()
+        for r in rows:
+            for name, flag in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[3:]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def ras_bytes(ls, precision):
+    """Algorithmic bytes of one RAS apply: each factor block and its column
+    index once (L and U together), the inverse diagonal blocks, the
+    position/row index arrays, the gather of the extended rows and the
+    restricted scatter of the owned rows."""
+    import paper_1701_06254_gb300 as R
+    vb = 16 if precision == "mixed" else 32
+    xb = 4 if precision == "mixed" else 8
+    nsub = ls.ras_count()
+    nnz = nxt = own = 0
+    for s in range(nsub):
+        o, e, z = ls.ras_sizes(s)
+        own += o; nxt += e; nnz += z
+    return nnz * (vb + 4) + nxt * (vb + 4 * 4) + nxt * 2 * xb + own * 2 * xb
+
+
+def spmv_bytes(nb, nnzb, val_b, x_b, f_b, y_b):
+    return nnzb * (val_b + 4) + (nb + 1) * 4 + 2 * nb * (x_b + f_b + y_b)
+
+
+def oracle_newton_iteration(case, opts):
+    """One Newton iteration of the CPU oracle on the first time step of the
+    case (assembly + decoupling + reordering + RAS/AMG setup + CPR-FGMRES)."""
+    import oracle
+    s = oracle.Sim(case, **opts)
+    s.init_hydrostatic()
+    s.store_old(); s.set_dt(case.dt)
+    t0 = time.perf_counter()
+    s.assemble()
+    rc, y, its, rel = s.linear_solve(case.lin_tol)
+    t1 = time.perf_counter()
+    return t1 - t0, its
+
+
+def oracle_full_step(case, opts):
+    import oracle
+    s = oracle.Sim(case, **opts)
+    s.init_hydrostatic()
+    t0 = time.perf_counter()
+    rc = s.advance(1)
+    t1 = time.perf_counter()
+    return t1 - t0, rc, s.stats()
+
+
+def run_reference(args, case, rank):
+    if rank != 0:
+        return
+    opts = dict(max_lin=args.max_lin)
+    dt, rc, st = oracle_full_step(case, opts)
+    value = case.n / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": 1, "warmup": 0, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": case.name, "cells": case.n, "dt_days": case.dt, "relres": case.lin_tol,
+                   "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"the CPU oracle's complete first time step of {case.name} "
+                                   f"({st['newton']} Newton iterations, {st['lin']} FGMRES iterations, rc={rc}); "
+                                   "--steps/--warmup are not applied: one step is the bounded sample"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="cfg2")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--max-lin", type=int, default=200)
+    ap.add_argument("--roofline", default="ras", choices=["ras", "spmv64", "spmv_prec"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_1701_06254_gb300 import inputs as I
+    case = I.CASES[args.config]()
+    if args.impl == "reference":
+        run_reference(args, case, rank)
+        return
+
+    import torch
+    import paper_1701_06254_gb300 as R
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prec = R.PREC_MIXED if args.precision == "mixed" else R.PREC_FP64
+    opts = dict(precision=prec, max_lin=args.max_lin)
+    sim = R.Sim(case, **opts)
+    sim.init_hydrostatic()
+    for _ in range(args.warmup):
+        sim.advance(1)
+    fam = {"ras": R.T_RAS, "spmv64": R.T_SPMV64, "spmv_prec": R.T_SPMV_PREC}[args.roofline]
+    sim.ls.kernel_timer(fam)
+    st0 = sim.stats()
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    l0 = R.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    e0.record()
+    for _ in range(args.steps):
+        sim.advance(1)
+    e1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = R.launch_count() - l0
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    st1 = sim.stats()
+    nk, kms = sim.ls.kernel_time()
+    value = world * case.n * args.steps / (ms / 1e3)
+    newton_per_step = (st1["newton"] - st0["newton"]) / args.steps
+    its_per_newton = (st1["linear_its"] - st0["linear_its"]) / max(1, st1["newton"] - st0["newton"])
+
+    # roofline of the chosen kernel family (algorithmic bytes / event time)
+    rp = sim.ls.export(R.X_ROWPTR, 0, np.int32)
+    nb, nnzb = len(rp) - 1, int(rp[-1])
+    if args.roofline == "ras":
+        bpl = ras_bytes(sim.ls, args.precision)
+    elif args.roofline == "spmv64":
+        bpl = spmv_bytes(nb, nnzb, 32, 4 if args.precision == "mixed" else 8, 0, 8)
+    else:
+        bpl = spmv_bytes(nb, nnzb, 16, 4, 8, 4) if args.precision == "mixed" else spmv_bytes(nb, nnzb, 32, 8, 8, 8)
+    peak, src = peaks()
+    achieved = bpl / (kms / nk * 1e-3) / 1e9 if nk else 0.0
+    roof = {"kernel": args.roofline, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": src, "traffic": None, "launches": nk,
+            "ms_per_launch": kms / nk if nk else None, "algorithmic_bytes_per_launch": bpl}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        nw = len(case.wells)
+        hp = torch.empty(case.n, dtype=torch.float64, pin_memory=True)
+        hs = torch.empty(case.n, dtype=torch.float64, pin_memory=True)
+        hb = torch.empty(max(nw, 1), dtype=torch.float64, pin_memory=True)
+        sim.get_state((hp, hs, hb))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        tt = sim.stats()["t"]
+        for _ in range(args.steps):
+            sim.set_state(hp, hs, hb, tt)
+            sim.advance(1)
+            tt = sim.get_state((hp, hs, hb))[3]
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * case.n * args.steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": (2 * case.n + nw) * 8, "d2h_bytes_per_step": (2 * case.n + nw) * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_it, its = oracle_newton_iteration(case, dict(max_lin=args.max_lin))
+        cpu = {"value": case.n / (t_it * max(newton_per_step, 1.0)), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one Newton iteration of the first time step of {case.name} by the FP64 CPU oracle "
+                         f"(assembly + setup + {its} FGMRES iterations, {t_it:.1f} s), scaled by the GPU run's "
+                         f"{newton_per_step:.2f} Newton iterations per step"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": case.name, "cells": case.n, "wells": len(case.wells), "dt_days": case.dt,
+                       "relres": case.lin_tol, "precision": args.precision, "learned_warm_start": False,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "working set larger than L2 (no flush needed)",
+                       "newton_per_step": newton_per_step, "fgmres_its_per_newton": its_per_newton},
+            "roofline": roof, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

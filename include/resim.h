@@ -1,0 +1,237 @@
+/* resim.h -- C ABI of the GB300 (sm_103a) CPR-FGMRES reservoir solver.
+ *
+ * The library implements, on one GPU, the Newton/linear-solve path of the
+ * fully implicit two-phase oil-water simulator of Liu, Shen, Chen, Wang,
+ * Yang and Chen, "A Parallel Simulator for Massive Reservoir Models
+ * Utilizing Distributed-Memory Parallel Systems" (arXiv 1701.06254):
+ *   model and discretisation      Sec. "Two-phase oil-water flow model",
+ *                                 eqs. (3)-(18), wells eqs. (10)-(12)
+ *   Newton / inexact Newton       Algorithm 1, eqs. (24)-(27)
+ *   decoupling                    eq. (29), ABF and Quasi-IMPES operators
+ *   local potential reordering    eqs. (30)-(32)
+ *   CPR-FPF preconditioner        Algorithm 2, eqs. (34)-(35)
+ *   Krylov solver                 GMRES(m) (flexible, right preconditioned)
+ *
+ * Conventions (every entry point):
+ *  - Returns a sim_status; SIM_OK = 0.  No entry point aborts the process.
+ *    sim_last_error() returns a thread-local message for the last failure.
+ *  - Units: p in bar, t in days, lengths in m, permeability in mD,
+ *    viscosity in cP, density in kg/m3, compressibility in 1/bar, well
+ *    rates in standard m3/day.
+ *  - Cells are numbered naturally, c = i + nx*(j + ny*k), k = 0 at the top;
+ *    z is depth (positive downwards).
+ *  - Inputs are copied at creation; the caller keeps ownership of every
+ *    array it passes.  Pointers documented as "host or device" are
+ *    accepted in either memory (the library asks the CUDA runtime).
+ *  - All GPU work is issued on the stream given in sim_options.cuda_stream
+ *    (NULL = the legacy default stream).  Entry points that return host
+ *    values synchronise that stream.
+ *  - A handle is not thread-safe; distinct handles may be used from
+ *    distinct threads.
+ */
+#ifndef RESIM_H
+#define RESIM_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SIM_OK = 0,
+  SIM_ERR_ARG = 1,           /* invalid argument (NULL, size, unsupported option)   */
+  SIM_ERR_CUDA = 2,          /* a CUDA runtime call failed                           */
+  SIM_ERR_OOM = 3,           /* device allocation failed                              */
+  SIM_ERR_NOT_CONVERGED = 4, /* Newton did not converge within the time-step cuts    */
+  SIM_ERR_NAN = 5,           /* a non-finite residual or update was produced          */
+  SIM_ERR_TIMEOUT = 6,       /* a bounded device loop hit its iteration cap           */
+  SIM_ERR_STATE = 7          /* call out of order (e.g. solve before assemble)        */
+} sim_status;
+
+enum { SIM_INJ = 0, SIM_PROD = 1 };                            /* well kind           */
+enum { SIM_BHP = 0, SIM_WRATE = 1, SIM_ORATE = 2, SIM_LRATE = 3 }; /* eqs. (11)-(14)   */
+enum { SIM_DEC_NONE = 0, SIM_DEC_ABF = 1, SIM_DEC_QI = 2 };    /* eq. (29) operator   */
+enum { SIM_NEWTON_STANDARD = 0, SIM_NEWTON_INEXACT = 1 };      /* Algorithm 1         */
+enum { SIM_PREC_FP64 = 0, SIM_PREC_MIXED = 1 };                /* preconditioner type */
+
+typedef struct { int nx, ny, nz; double dx, dy, dz, top_depth; } sim_grid;
+
+/* Rock: n = nx*ny*nz values each, host or device; permeability in mD. */
+typedef struct { const double *kx, *ky, *kz, *phi; } sim_rock;
+
+/* Fluid: index 0 = water, 1 = oil.  eqs. (4), (6), (7) and Corey relative
+ * permeabilities kr_w = krw_max s^nw, kr_o = kro_max (1-s)^no with
+ * s = (s_w - swc)/(1 - swc - sor) clipped to [0, 1]; g in m/s^2. */
+typedef struct {
+  double rho_ref[2], c_f[2], mu_ref[2], c_mu[2];
+  double p_ref, c_r, swc, sor, nw, no, krw_max, kro_max, g;
+} sim_fluid;
+
+/* A well (eq. 10): perforated cells (host array, n_perf entries), well
+ * index per perforation (host, or NULL for Peaceman's formula with r_w and
+ * skin), reference depth z_ref of p_b.  Supported controls: SIM_BHP for
+ * any well, SIM_WRATE for injectors. */
+typedef struct {
+  int kind, control;
+  double target, r_w, skin, z_ref;
+  int n_perf;
+  const int *perf_cell;
+  const double *wi;
+} sim_well;
+
+typedef struct {
+  int precision;       /* SIM_PREC_FP64 or SIM_PREC_MIXED (FP32 AMG + FP32 RAS)    */
+  int decoupling;      /* SIM_DEC_*                                                */
+  int reorder;         /* 1: local potential reordering in each RAS subdomain     */
+  int newton;          /* SIM_NEWTON_*                                             */
+  double newton_tol;   /* scaled max-residual tolerance                            */
+  double lin_tol;      /* relative linear residual (standard Newton)               */
+  int max_newton, restart, max_lin;
+  int tile_x, tile_y;  /* RAS subdomain = tile_x x tile_y cell columns             */
+  double amg_theta;
+  int amg_max_levels, amg_coarse_max;
+  uint64_t seed;       /* PMIS hash seed                                           */
+  int max_cuts;        /* time-step halvings allowed per step                      */
+  double dt;           /* time step, days                                          */
+  void *cuda_stream;   /* cudaStream_t or NULL                                     */
+} sim_options;
+
+/* Statistics, cumulative since creation. */
+typedef struct {
+  long long steps, newton, linear_its, cuts, linear_solves;
+  double last_relres, last_norm, t;
+  int last_its, last_newton;
+  double ms_assemble, ms_setup, ms_solve;   /* CUDA-event time, cumulative */
+} sim_stats;
+
+typedef struct sim_s *sim_t;
+typedef struct sim_ls_s *sim_ls_t;
+
+/* Fill *o with the defaults: FP64, ABF, reordering on, standard Newton,
+ * newton_tol 1e-8, lin_tol 1e-8, max_newton 20, restart 50, max_lin 100,
+ * 8x8 tiles, theta 0.25, 25 levels, coarsest <= 128 rows, 6 cuts, dt 1. */
+void sim_default_options(sim_options *o);
+
+/* Create a simulator (copies everything).  Builds transmissibilities,
+ * well indices, the 2x2 block sparsity pattern (cells, then one padded
+ * block row per well) and the RAS partition; allocates device memory.
+ * Errors: SIM_ERR_ARG for bad sizes/controls, SIM_ERR_OOM, SIM_ERR_CUDA. */
+sim_status sim_create(sim_t *out, const sim_grid *g, const sim_rock *r, const sim_fluid *f,
+                      const sim_well *wells, int n_wells, const sim_options *o);
+void sim_destroy(sim_t h);
+
+/* Equilibrium start: each cell gets the oil potential (eq. 5) of p_datum at
+ * the top depth, s_w = sw0; BHP wells start at target, rate wells 10 bar
+ * above the oil pressure of their first perforated cell; t = 0. */
+sim_status sim_init_hydrostatic(sim_t h, double p_datum, double sw0);
+
+/* State in caller buffers: p, sw (n each), pb (n_wells); host or device. */
+sim_status sim_set_state(sim_t h, const double *p, const double *sw, const double *pb, double t);
+sim_status sim_get_state(sim_t h, double *p, double *sw, double *pb, double *t);
+
+/* Store the accumulation of the current state as the old time level
+ * (eq. 15) and set the step length used by sim_assemble. */
+sim_status sim_begin_step(sim_t h, double dt);
+
+/* Residual and Jacobian at the current iterate (eq. 17 with eq. 18
+ * upstreaming and eq. 10 wells), b = -F, plus the scaled residual norm
+ * (max over cells of |R| dt / (rho_ref V phi) and over wells of |R|). */
+sim_status sim_assemble(sim_t h, double *scaled_norm);
+
+/* Solve J y = b for the assembled system: decouple (eq. 29), reorder
+ * (eqs. 30-32), build RAS and AMG, run FGMRES(restart) with CPR-FPF
+ * (Algorithm 2) to ||b - J y|| <= tol ||b|| on the decoupled system or
+ * max_lin iterations.  y stays on the device (see sim_export). */
+sim_status sim_linear_solve(sim_t h, double tol, int *iters, double *relres);
+
+/* One Newton iteration of Algorithm 1 at the current step length:
+ * assemble, test, solve, x += y.  *converged = 1 when the test passed
+ * (then nothing is solved). */
+sim_status sim_newton_step(sim_t h, int *converged, sim_stats *st);
+
+/* Advance n_steps time steps of options.dt: Newton per step, halving the
+ * step on failure (max_cuts per step).  SIM_ERR_NOT_CONVERGED / SIM_ERR_NAN
+ * when a step could not be completed (the state is the last good one). */
+sim_status sim_advance(sim_t h, int n_steps, sim_stats *st);
+
+sim_status sim_get_stats(sim_t h, sim_stats *st);
+
+/* The simulator's linear system (borrowed handle, valid until sim_destroy). */
+sim_ls_t sim_linear_system(sim_t h);
+
+/* ---- linear-system level (used by sim_*, exposed for callers that bring
+ *      their own Jacobian, and for testing each stage) ---- */
+
+/* A 2x2-block system over n = nx*ny*nz cells plus n_wells padded well rows.
+ * rowptr (n+n_wells+1), cols (nnzb): host arrays, columns sorted per row;
+ * well_cell0[w] = first perforated cell of well w (fixes its subdomain).
+ * The pattern must be structurally symmetric. */
+sim_status sim_ls_create(sim_ls_t *out, int nx, int ny, int nz, int n_wells,
+                         const int *rowptr, const int *cols, const int *well_cell0,
+                         const sim_options *o);
+void sim_ls_destroy(sim_ls_t ls);
+
+/* Values (4 per block, row-major: [dR_oil/dp, dR_oil/ds; dR_w/dp, dR_w/ds]),
+ * right-hand side (2 per block row) and reordering key (oil potential, n):
+ * host or device. */
+sim_status sim_ls_set(sim_ls_t ls, const double *vals, const double *b, const double *key);
+
+/* Decoupling, reordering, RAS factorisation and AMG hierarchy. */
+sim_status sim_ls_setup(sim_ls_t ls);
+
+/* FGMRES from y = 0 on the (decoupled) system; y: 2 per block row, host
+ * or device.  SIM_ERR_NOT_CONVERGED is NOT returned for an iteration cap:
+ * check *relres. */
+sim_status sim_ls_solve(sim_ls_t ls, double tol, double *y, int *iters, double *relres);
+
+/* Apply one operator of the set-up system to x (2 per block row; for
+ * SIM_OP_VCYCLE n pressure values), host or device:
+ * SIM_OP_SPMV y = A x, SIM_OP_RAS y = R(A)^{-1} x, SIM_OP_VCYCLE one V-cycle
+ * on A_pp, SIM_OP_CPR Algorithm 2.  A is the decoupled matrix. */
+enum { SIM_OP_SPMV = 0, SIM_OP_RAS = 1, SIM_OP_VCYCLE = 2, SIM_OP_CPR = 3 };
+sim_status sim_ls_apply(sim_ls_t ls, int op, const double *x, double *y);
+
+/* Copy internal arrays to host memory for inspection.  what / index:
+ *  SIM_X_VALS, 0      decoupled block values (4*nnzb doubles)
+ *  SIM_X_RHS, 0       decoupled right-hand side (2*nb doubles)
+ *  SIM_X_SOLUTION, 0  last solution y (2*nb doubles)
+ *  SIM_X_ROWPTR, 0    block row pointers (nb+1 ints)
+ *  SIM_X_COLS, 0      block columns (nnzb ints)
+ *  SIM_X_KEY, 0       reordering key (n doubles)
+ *  SIM_X_AMG_SIZES, l int[6]: n, nnz, nnzP, nc, pmis_rounds, coarsest_dense
+ *                     (index -1: int[1] = number of levels)
+ *  SIM_X_AMG_RP/CI/V, l   level-l CSR of A (int, int, double)
+ *  SIM_X_AMG_CF, l        C/F marks (int8: 1 = C, -1 = F)
+ *  SIM_X_AMG_PRP/PCI/PV, l  interpolation P of level l
+ *  SIM_X_RAS_SIZES, s int[3]: owned rows, extended rows, local nnzb
+ *                     (index -1: int[1] = number of subdomains)
+ *  SIM_X_RAS_EXT, s   global rows of subdomain s in local (reordered) order
+ *  SIM_X_RAS_LEVELS, s int[2*next+2]: number of L levels, number of U
+ *                     levels, then the L level and the U level of each row
+ * *needed receives the byte size; dst may be NULL to query it. */
+enum {
+  SIM_X_VALS = 0, SIM_X_RHS = 1, SIM_X_SOLUTION = 2, SIM_X_ROWPTR = 3, SIM_X_COLS = 4, SIM_X_KEY = 5,
+  SIM_X_AMG_SIZES = 10, SIM_X_AMG_RP = 11, SIM_X_AMG_CI = 12, SIM_X_AMG_V = 13,
+  SIM_X_AMG_CF = 14, SIM_X_AMG_PRP = 15, SIM_X_AMG_PCI = 16, SIM_X_AMG_PV = 17,
+  SIM_X_RAS_SIZES = 20, SIM_X_RAS_EXT = 21, SIM_X_RAS_LEVELS = 22
+};
+sim_status sim_ls_export(sim_ls_t ls, int what, int index, void *dst, size_t bytes, size_t *needed);
+
+/* Per-kernel timing (CUDA events on the library stream) for one named
+ * kernel family: 0 off, else SIM_T_* below.  sim_kernel_time returns the
+ * number of timed launches and their summed milliseconds. */
+enum { SIM_T_NONE = 0, SIM_T_SPMV64 = 1, SIM_T_SPMV_PREC = 2, SIM_T_RAS = 3, SIM_T_VCYCLE = 4,
+       SIM_T_ORTHO = 5, SIM_T_ASSEMBLE = 6 };
+sim_status sim_kernel_timer(sim_ls_t ls, int which);
+sim_status sim_kernel_time(sim_ls_t ls, long long *launches, double *ms);
+
+/* Number of this library's kernel launches issued so far (all handles). */
+long long sim_launch_count(void);
+
+const char *sim_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,342 @@
+"""Python binding of libresim.so, the sm_103a CPR-FGMRES reservoir solver.
+
+Thin ctypes marshalling over the C ABI declared in include/resim.h: every
+step of the Newton / linear-solve path runs in the library's CUDA kernels.
+Arrays may be numpy arrays (host) or CUDA tensors (device); the library
+accepts either.  Importing this package does not load the library; the
+first call does, and raises if the library cannot be built or loaded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import inputs  # noqa: F401  (synthetic workloads)
+
+_lib = None
+
+PREC_FP64, PREC_MIXED = 0, 1
+DEC_NONE, DEC_ABF, DEC_QI = 0, 1, 2
+OP_SPMV, OP_RAS, OP_VCYCLE, OP_CPR = 0, 1, 2, 3
+T_NONE, T_SPMV64, T_SPMV_PREC, T_RAS, T_VCYCLE, T_ORTHO, T_ASSEMBLE = 0, 1, 2, 3, 4, 5, 6
+X_VALS, X_RHS, X_SOLUTION, X_ROWPTR, X_COLS, X_KEY = 0, 1, 2, 3, 4, 5
+X_AMG_SIZES, X_AMG_RP, X_AMG_CI, X_AMG_V, X_AMG_CF, X_AMG_PRP, X_AMG_PCI, X_AMG_PV = 10, 11, 12, 13, 14, 15, 16, 17
+X_RAS_SIZES, X_RAS_EXT, X_RAS_LEVELS = 20, 21, 22
+STATUS = {0: "SIM_OK", 1: "SIM_ERR_ARG", 2: "SIM_ERR_CUDA", 3: "SIM_ERR_OOM", 4: "SIM_ERR_NOT_CONVERGED",
+          5: "SIM_ERR_NAN", 6: "SIM_ERR_TIMEOUT", 7: "SIM_ERR_STATE"}
+
+
+class SimError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double), ("dy", C.c_double),
+                ("dz", C.c_double), ("top_depth", C.c_double)]
+
+
+class Rock(C.Structure):
+    _fields_ = [("kx", C.c_void_p), ("ky", C.c_void_p), ("kz", C.c_void_p), ("phi", C.c_void_p)]
+
+
+class Fluid(C.Structure):
+    _fields_ = [("rho_ref", C.c_double * 2), ("c_f", C.c_double * 2), ("mu_ref", C.c_double * 2),
+                ("c_mu", C.c_double * 2), ("p_ref", C.c_double), ("c_r", C.c_double), ("swc", C.c_double),
+                ("sor", C.c_double), ("nw", C.c_double), ("no", C.c_double), ("krw_max", C.c_double),
+                ("kro_max", C.c_double), ("g", C.c_double)]
+
+
+class Well(C.Structure):
+    _fields_ = [("kind", C.c_int), ("control", C.c_int), ("target", C.c_double), ("r_w", C.c_double),
+                ("skin", C.c_double), ("z_ref", C.c_double), ("n_perf", C.c_int),
+                ("perf_cell", C.POINTER(C.c_int)), ("wi", C.POINTER(C.c_double))]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("decoupling", C.c_int), ("reorder", C.c_int), ("newton", C.c_int),
+                ("newton_tol", C.c_double), ("lin_tol", C.c_double), ("max_newton", C.c_int),
+                ("restart", C.c_int), ("max_lin", C.c_int), ("tile_x", C.c_int), ("tile_y", C.c_int),
+                ("amg_theta", C.c_double), ("amg_max_levels", C.c_int), ("amg_coarse_max", C.c_int),
+                ("seed", C.c_uint64), ("max_cuts", C.c_int), ("dt", C.c_double), ("cuda_stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("steps", C.c_longlong), ("newton", C.c_longlong), ("linear_its", C.c_longlong),
+                ("cuts", C.c_longlong), ("linear_solves", C.c_longlong), ("last_relres", C.c_double),
+                ("last_norm", C.c_double), ("t", C.c_double), ("last_its", C.c_int), ("last_newton", C.c_int),
+                ("ms_assemble", C.c_double), ("ms_setup", C.c_double), ("ms_solve", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def lib_path():
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libresim.so")
+
+
+def build(force=False):
+    from . import _build
+    return _build.build(force=force)
+
+
+def lib():
+    """Load libresim.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = build()
+        L = C.CDLL(path)
+        P, I, D = C.c_void_p, C.c_int, C.c_double
+        sig = {
+            "sim_default_options": (None, [C.POINTER(Options)]),
+            "sim_create": (I, [C.POINTER(P), C.POINTER(Grid), C.POINTER(Rock), C.POINTER(Fluid), C.POINTER(Well), I,
+                               C.POINTER(Options)]),
+            "sim_destroy": (None, [P]),
+            "sim_init_hydrostatic": (I, [P, D, D]),
+            "sim_set_state": (I, [P, P, P, P, D]),
+            "sim_get_state": (I, [P, P, P, P, C.POINTER(D)]),
+            "sim_begin_step": (I, [P, D]),
+            "sim_assemble": (I, [P, C.POINTER(D)]),
+            "sim_linear_solve": (I, [P, D, C.POINTER(I), C.POINTER(D)]),
+            "sim_newton_step": (I, [P, C.POINTER(I), C.POINTER(Stats)]),
+            "sim_advance": (I, [P, I, C.POINTER(Stats)]),
+            "sim_get_stats": (I, [P, C.POINTER(Stats)]),
+            "sim_linear_system": (P, [P]),
+            "sim_ls_create": (I, [C.POINTER(P), I, I, I, I, P, P, P, C.POINTER(Options)]),
+            "sim_ls_destroy": (None, [P]),
+            "sim_ls_set": (I, [P, P, P, P]),
+            "sim_ls_setup": (I, [P]),
+            "sim_ls_solve": (I, [P, D, P, C.POINTER(I), C.POINTER(D)]),
+            "sim_ls_apply": (I, [P, I, P, P]),
+            "sim_ls_export": (I, [P, I, I, P, C.c_size_t, C.POINTER(C.c_size_t)]),
+            "sim_kernel_timer": (I, [P, I]),
+            "sim_kernel_time": (I, [P, C.POINTER(C.c_longlong), C.POINTER(D)]),
+            "sim_launch_count": (C.c_longlong, []),
+            "sim_last_error": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise SimError(rc, lib().sim_last_error().decode(errors="replace"))
+
+
+def _ptr(a):
+    """Raw address of a numpy array or a CUDA tensor (anything with data_ptr)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def launch_count():
+    return lib().sim_launch_count()
+
+
+OPT_KEYS = ("precision", "decoupling", "reorder", "newton", "newton_tol", "lin_tol", "max_newton", "restart",
+            "max_lin", "tile_x", "tile_y", "amg_theta", "amg_max_levels", "amg_coarse_max", "seed", "max_cuts", "dt")
+
+
+def make_options(stream=None, **kw):
+    o = Options()
+    lib().sim_default_options(C.byref(o))
+    for k, v in kw.items():
+        if k not in OPT_KEYS:
+            raise KeyError(k)
+        setattr(o, k, v)
+    o.cuda_stream = stream
+    return o
+
+
+class LinearSystem:
+    """A 2x2-block Newton system with its CPR-FGMRES solver (sim_ls_*)."""
+
+    def __init__(self, nx=None, ny=None, nz=None, nw=0, rp=None, ci=None, well_cell0=None, stream=None,
+                 _handle=None, _owner=None, **opts):
+        self._L = lib()
+        if _handle is not None:
+            self.h, self._own, self._owner = _handle, False, _owner
+        else:
+            rp = np.ascontiguousarray(rp, np.int32); ci = np.ascontiguousarray(ci, np.int32)
+            wc = np.ascontiguousarray(well_cell0 if nw else [0], np.int32)
+            self.opts = make_options(stream, **opts)
+            h = C.c_void_p()
+            _check(self._L.sim_ls_create(C.byref(h), nx, ny, nz, nw, _ptr(rp), _ptr(ci), _ptr(wc), C.byref(self.opts)))
+            self.h, self._own = h, True
+            self.n, self.nw, self.nb, self.nnzb = nx * ny * nz, nw, nx * ny * nz + nw, int(rp[-1])
+
+    def __del__(self):
+        if getattr(self, "_own", False) and self.h:
+            self._L.sim_ls_destroy(self.h)
+            self.h = None
+
+    def set(self, val, b, key):
+        val = np.ascontiguousarray(val, np.float64) if isinstance(val, np.ndarray) else val
+        b = np.ascontiguousarray(b, np.float64) if isinstance(b, np.ndarray) else b
+        key = np.ascontiguousarray(key, np.float64) if isinstance(key, np.ndarray) else key
+        _check(self._L.sim_ls_set(self.h, _ptr(val), _ptr(b), _ptr(key)))
+
+    def setup(self):
+        _check(self._L.sim_ls_setup(self.h))
+
+    def solve(self, tol, y=None):
+        nb = self._nb()
+        out = np.zeros(2 * nb) if y is None else y
+        its, rel = C.c_int(), C.c_double()
+        _check(self._L.sim_ls_solve(self.h, tol, _ptr(out), C.byref(its), C.byref(rel)))
+        return out, its.value, rel.value
+
+    def apply(self, op, x):
+        x = np.ascontiguousarray(x, np.float64)
+        y = np.zeros_like(x)
+        _check(self._L.sim_ls_apply(self.h, op, _ptr(x), _ptr(y)))
+        return y
+
+    def export(self, what, index=0, dtype=np.float64):
+        need = C.c_size_t()
+        _check(self._L.sim_ls_export(self.h, what, index, None, 0, C.byref(need)))
+        out = np.zeros(need.value // np.dtype(dtype).itemsize, dtype)
+        if need.value:
+            _check(self._L.sim_ls_export(self.h, what, index, _ptr(out), need.value, C.byref(need)))
+        return out
+
+    def _nb(self):
+        return len(self.export(X_RHS)) // 2
+
+    def amg_nlev(self):
+        return int(self.export(X_AMG_SIZES, -1, np.int32)[0])
+
+    def amg_level(self, l):
+        sz = self.export(X_AMG_SIZES, l, np.int32)
+        d = dict(n=int(sz[0]), nnz=int(sz[1]), nnzP=int(sz[2]), nc=int(sz[3]), rounds=int(sz[4]),
+                 coarse_dense=int(sz[5]))
+        d["rp"] = self.export(X_AMG_RP, l, np.int32)
+        d["ci"] = self.export(X_AMG_CI, l, np.int32)
+        d["v"] = self.export(X_AMG_V, l, np.float64)
+        d["cf"] = self.export(X_AMG_CF, l, np.int8)
+        if l < self.amg_nlev() - 1:
+            d["prp"] = self.export(X_AMG_PRP, l, np.int32)
+            d["pci"] = self.export(X_AMG_PCI, l, np.int32)
+            d["pv"] = self.export(X_AMG_PV, l, np.float64)
+        return d
+
+    def ras_count(self):
+        return int(self.export(X_RAS_SIZES, -1, np.int32)[0])
+
+    def ras_ext(self, s):
+        return self.export(X_RAS_EXT, s, np.int32)
+
+    def ras_levels(self, s):
+        v = self.export(X_RAS_LEVELS, s, np.int32)
+        return int(v[0]), int(v[1]), v[2::2].copy(), v[3::2].copy()
+
+    def ras_sizes(self, s):
+        v = self.export(X_RAS_SIZES, s, np.int32)
+        return int(v[0]), int(v[1]), int(v[2])
+
+    def kernel_timer(self, which):
+        _check(self._L.sim_kernel_timer(self.h, which))
+
+    def kernel_time(self):
+        n, ms = C.c_longlong(), C.c_double()
+        _check(self._L.sim_kernel_time(self.h, C.byref(n), C.byref(ms)))
+        return n.value, ms.value
+
+
+def _case_structs(case):
+    g = Grid(case.nx, case.ny, case.nz, case.dx, case.dy, case.dz, case.top)
+    f = case.fluid
+    fl = Fluid((C.c_double * 2)(*f.rho_ref), (C.c_double * 2)(*f.c_f), (C.c_double * 2)(*f.mu_ref),
+               (C.c_double * 2)(*f.c_mu), f.p_ref, f.c_r, f.swc, f.sor, f.nw, f.no, f.krw_max, f.kro_max, f.g)
+    keep = []
+    wells = (Well * max(len(case.wells), 1))()
+    for k, w in enumerate(case.wells):
+        pc = np.ascontiguousarray(w.perf_cells, np.int32)
+        keep.append(pc)
+        wells[k] = Well(w.kind, w.control, w.target, w.r_w, w.skin, case.well_z_ref(w), len(pc),
+                        pc.ctypes.data_as(C.POINTER(C.c_int)), None)
+    return g, fl, wells, keep
+
+
+class Sim:
+    """GPU simulator for one inputs.Case (sim_* entry points)."""
+
+    def __init__(self, case, stream=None, **opts):
+        self._L = lib()
+        self.case = case
+        o = dict(newton=0 if case.newton == "standard" else 1, newton_tol=case.newton_tol, lin_tol=case.lin_tol,
+                 dt=case.dt)
+        o.update(opts)
+        self.opts = make_options(stream, **o)
+        g, fl, wells, keep = _case_structs(case)
+        self._k = [np.ascontiguousarray(a, np.float64) for a in (case.kx, case.ky, case.kz, case.phi)]
+        rock = Rock(*(_ptr(a) for a in self._k))
+        h = C.c_void_p()
+        _check(self._L.sim_create(C.byref(h), C.byref(g), C.byref(rock), C.byref(fl), wells, len(case.wells),
+                                  C.byref(self.opts)))
+        self.h = h
+        self.n, self.nw = case.n, len(case.wells)
+        self.ls = LinearSystem(_handle=self._L.sim_linear_system(h), _owner=self)
+        self.ls.n, self.ls.nw, self.ls.nb = self.n, self.nw, self.n + self.nw
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self._L.sim_destroy(self.h)
+            self.h = None
+
+    def init_hydrostatic(self, p_datum=None, sw0=None):
+        _check(self._L.sim_init_hydrostatic(self.h, self.case.p_init if p_datum is None else p_datum,
+                                            self.case.sw_init if sw0 is None else sw0))
+
+    def set_state(self, p, sw, pb, t=0.0):
+        conv = lambda a: np.ascontiguousarray(a, np.float64) if not hasattr(a, "data_ptr") else a
+        p, sw = conv(p), conv(sw)
+        pb = conv(pb if self.nw else np.zeros(1))
+        _check(self._L.sim_set_state(self.h, _ptr(p), _ptr(sw), _ptr(pb), t))
+
+    def get_state(self, out=None):
+        if out is None:
+            p, sw, pb = np.zeros(self.n), np.zeros(self.n), np.zeros(max(self.nw, 1))
+        else:
+            p, sw, pb = out
+        t = C.c_double()
+        _check(self._L.sim_get_state(self.h, _ptr(p), _ptr(sw), _ptr(pb), C.byref(t)))
+        return p, sw, pb[:self.nw] if out is None else pb, t.value
+
+    def begin_step(self, dt):
+        _check(self._L.sim_begin_step(self.h, dt))
+
+    def assemble(self):
+        nr = C.c_double()
+        _check(self._L.sim_assemble(self.h, C.byref(nr)))
+        return nr.value
+
+    def linear_solve(self, tol):
+        its, rel = C.c_int(), C.c_double()
+        _check(self._L.sim_linear_solve(self.h, tol, C.byref(its), C.byref(rel)))
+        return its.value, rel.value
+
+    def newton_step(self):
+        conv, st = C.c_int(), Stats()
+        _check(self._L.sim_newton_step(self.h, C.byref(conv), C.byref(st)))
+        return bool(conv.value), st.as_dict()
+
+    def advance(self, n_steps):
+        st = Stats()
+        _check(self._L.sim_advance(self.h, n_steps, C.byref(st)))
+        return st.as_dict()
+
+    def stats(self):
+        st = Stats()
+        _check(self._L.sim_get_stats(self.h, C.byref(st)))
+        return st.as_dict()

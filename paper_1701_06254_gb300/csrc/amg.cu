@@ -1,0 +1,542 @@
+// Algebraic multigrid on the pressure block A_pp: the M(A_pp)^{-1} stage of
+// CPR-FPF (Algorithm 2, step 3) of arXiv 1701.06254.  The paper fixes no AMG
+// component; this library uses
+//   strength   S_i = { j != i : -a_ij >= theta * max_{k != i}(-a_ik) }
+//   coarsening PMIS with weights |S^T_i| + h(i), h = splitmix64 hash in [0,1)
+//   interpolation direct (positive off-diagonals lumped into the diagonal),
+//              R = P^T, Galerkin A_c = R (A P)
+//   cycle      V(1,1), l1-Jacobi smoothing, zero initial guess
+//   coarsest   dense inverse (FP64) from an LU with partial pivoting
+// Setup runs in FP64 with explicit round-to-nearest operations in a fixed
+// order, so the C/F split, P and every coarse operator are bit-identical to
+// a plain sequential evaluation of the same formulas on the same input.
+#include "common.cuh"
+#include <algorithm>
+
+// ------------------------------------------------------------ pattern -----
+__global__ void k_tpos(int n, const int *rp, const int *ci, int *tpos, int *err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int q = rp[i]; q < rp[i + 1]; q++) {
+    int j = ci[q], lo = rp[j], hi = rp[j + 1] - 1, pos = -1;
+    while (lo <= hi) {
+      int mid = (lo + hi) >> 1, c = ci[mid];
+      if (c == i) { pos = mid; break; }
+      if (c < i) lo = mid + 1; else hi = mid - 1;
+    }
+    if (pos < 0) atomicExch(err, 1);       // pattern not structurally symmetric
+    tpos[q] = pos < 0 ? q : pos;
+  }
+}
+
+__global__ void k_strength(int n, const int *rp, const int *ci, const double *v, double theta, uint8_t *S) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  bool have = false; double mx = 0.0;
+  for (int q = rp[i]; q < rp[i + 1]; q++) {
+    if (ci[q] == i) continue;
+    double t = -v[q];
+    if (!have || t > mx) { mx = t; have = true; }
+  }
+  double thr = mul_rn(theta, mx);
+  for (int q = rp[i]; q < rp[i + 1]; q++)
+    S[q] = (uint8_t)(have && mx > 0.0 && ci[q] != i && -v[q] >= thr);
+}
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_pmis_init(int n, const int *rp, const int *ci, const uint8_t *S, const int *tpos,
+                            uint64_t seed, int level, double *w, int8_t *cf) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int cnt = 0;
+  for (int q = rp[i]; q < rp[i + 1]; q++) if (ci[q] != i && S[tpos[q]]) cnt++;   // |S^T_i|
+  uint64_t z = splitmix64(seed ^ ((uint64_t)level << 40) ^ (uint64_t)(uint32_t)i);
+  double h = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  w[i] = add_rn((double)cnt, h);
+  cf[i] = cnt == 0 ? (int8_t)-1 : (int8_t)0;
+}
+
+__global__ void k_pmis_select(int n, const int *rp, const int *ci, const uint8_t *S, const int *tpos,
+                              const double *w, const int8_t *cf, int8_t *newc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int8_t best = 0;
+  if (cf[i] == 0) {
+    best = 1;
+    double wi = w[i];
+    for (int q = rp[i]; q < rp[i + 1] && best; q++) {
+      int j = ci[q];
+      if (j == i || !(S[q] || S[tpos[q]]) || cf[j] != 0) continue;
+      double wj = w[j];
+      if (wj > wi || (wj == wi && j < i)) best = 0;
+    }
+  }
+  newc[i] = best;
+}
+
+__global__ void k_pmis_update(int n, const int *rp, const int *ci, const uint8_t *S, int8_t *cf,
+                              const int8_t *newc, int *undecided) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (cf[i] != 0) return;
+  if (newc[i]) { cf[i] = 1; return; }
+  for (int q = rp[i]; q < rp[i + 1]; q++) {
+    int j = ci[q];
+    if (S[q] && (cf[j] == 1 || newc[j])) { cf[i] = -1; return; }
+  }
+  atomicAdd(undecided, 1);
+}
+
+__global__ void k_cflag(int n, const int8_t *cf, int *flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = cf[i] == 1;
+}
+
+// ------------------------------------------------------- interpolation ----
+__global__ void k_interp_count(int n, const int *rp, const int *ci, const uint8_t *S, const int8_t *cf, int *len) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = 0;
+  if (cf[i] == 1) c = 1;
+  else for (int q = rp[i]; q < rp[i + 1]; q++) if (S[q] && cf[ci[q]] == 1) c++;
+  len[i] = c;
+}
+
+__global__ void k_interp_fill(int n, const int *rp, const int *ci, const double *v, const uint8_t *S,
+                              const int8_t *cf, const int *cidx, const int *prp, int *pci, double *pv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int o = prp[i];
+  if (cf[i] == 1) { pci[o] = cidx[i]; pv[o] = 1.0; return; }
+  if (prp[i + 1] == o) return;
+  double sneg = 0.0, spos = 0.0, snegc = 0.0, aii = 0.0;
+  for (int q = rp[i]; q < rp[i + 1]; q++) {
+    double a = v[q];
+    if (ci[q] == i) { aii = a; continue; }
+    if (a < 0.0) sneg = add_rn(sneg, a); else spos = add_rn(spos, a);
+  }
+  for (int q = rp[i]; q < rp[i + 1]; q++) if (S[q] && cf[ci[q]] == 1) snegc = add_rn(snegc, v[q]);
+  double dg = add_rn(aii, spos), alpha = div_rn(sneg, snegc);
+  for (int q = rp[i]; q < rp[i + 1]; q++)
+    if (S[q] && cf[ci[q]] == 1) { pci[o] = cidx[ci[q]]; pv[o++] = div_rn(-mul_rn(alpha, v[q]), dg); }
+}
+
+// ------------------------------------------------------------ transpose ---
+__global__ void k_col_count(int nnz, const int *ci, int *cnt) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nnz) atomicAdd(&cnt[ci[q]], 1);
+}
+__global__ void k_transpose_fill(int n, const int *rp, const int *ci, const double *v, const int *trp, int *fill,
+                                 int *tci, double *tv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int q = rp[i]; q < rp[i + 1]; q++) {
+    int j = ci[q], o = trp[j] + atomicAdd(&fill[j], 1);
+    tci[o] = i; tv[o] = v[q];
+  }
+}
+__global__ void k_sort_rows(int n, const int *rp, int *ci, double *v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int a0 = rp[i], a1 = rp[i + 1];
+  for (int a = a0 + 1; a < a1; a++) {
+    int c = ci[a]; double x = v[a]; int b = a - 1;
+    while (b >= a0 && ci[b] > c) { ci[b + 1] = ci[b]; v[b + 1] = v[b]; b--; }
+    ci[b + 1] = c; v[b + 1] = x;
+  }
+}
+
+// -------------------------------------------------------------- SpGEMM ----
+// C = A B, one warp per row of C: expand every product A_ik B_kj with its
+// sequence number (row of A ascending, then row of B ascending), sort the
+// (column, sequence) keys in shared memory, and sum each column's products
+// in sequence order starting from 0.  The symbolic pass only counts.
+__global__ void k_expand_count(int n, const int *arp, const int *aci, const int *brp, int *mx) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int s = 0;
+  for (int q = arp[i]; q < arp[i + 1]; q++) { int k = aci[q]; s += brp[k + 1] - brp[k]; }
+  atomicMax(mx, s);
+}
+
+template <bool NUMERIC>
+__global__ void k_spgemm(int n, const int *arp, const int *aci, const double *av, const int *brp, const int *bci,
+                         const double *bv, const int *crp, int *clen, int *cci, double *cv, int cap) {
+  extern __shared__ unsigned long long sm_keys[];
+  const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned long long *keys = sm_keys + (size_t)wid * cap;
+  double *vals = reinterpret_cast<double *>(sm_keys + (size_t)warps * cap) + (size_t)wid * cap;
+  const unsigned FULL = 0xffffffffu;
+  for (int row = blockIdx.x * warps + wid; row < n; row += gridDim.x * warps) {
+    int a0 = arp[row], a1 = arp[row + 1], base = 0;
+    for (int q0 = a0; q0 < a1; q0 += 32) {
+      int q = q0 + lane, len = 0, k = 0;
+      if (q < a1) { k = aci[q]; len = brp[k + 1] - brp[k]; }
+      int incl = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) { int y = __shfl_up_sync(FULL, incl, o); if (lane >= o) incl += y; }
+      int tot = __shfl_sync(FULL, incl, 31), off = base + incl - len;
+      if (q < a1) {
+        double a = NUMERIC ? av[q] : 0.0;
+        int b0 = brp[k];
+        for (int r = 0; r < len; r++) {
+          int seq = off + r;
+          keys[seq] = ((unsigned long long)(unsigned)bci[b0 + r] << 32) | (unsigned)seq;
+          if (NUMERIC) vals[seq] = mul_rn(a, bv[b0 + r]);
+        }
+      }
+      base += tot;
+    }
+    int m = 1;
+    while (m < base) m <<= 1;
+    for (int i = base + lane; i < m; i += 32) keys[i] = ~0ull;
+    __syncwarp();
+    for (int k = 2; k <= m; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = lane; i < m; i += 32) {
+          int ixj = i ^ j;
+          if (ixj > i) {
+            unsigned long long x = keys[i], y = keys[ixj];
+            bool up = (i & k) == 0;
+            if ((x > y) == up) { keys[i] = y; keys[ixj] = x; }
+          }
+        }
+        __syncwarp();
+      }
+    int running = 0, out = NUMERIC ? crp[row] : 0;
+    for (int c0 = 0; c0 < base; c0 += 32) {
+      int i = c0 + lane;
+      unsigned col = i < base ? (unsigned)(keys[i] >> 32) : 0u;
+      bool head = i < base && (i == 0 || (unsigned)(keys[i - 1] >> 32) != col);
+      unsigned mask = __ballot_sync(FULL, head);
+      if (NUMERIC && head) {
+        int pre = __popc(mask & ((1u << lane) - 1u));
+        double s = 0.0;
+        for (int t = i; t < base && (unsigned)(keys[t] >> 32) == col; t++) s = add_rn(s, vals[(unsigned)keys[t]]);
+        cci[out + running + pre] = (int)col; cv[out + running + pre] = s;
+      }
+      running += __popc(mask);
+    }
+    if (!NUMERIC && lane == 0) clen[row] = running;
+    __syncwarp();
+  }
+}
+
+static void spgemm(const csr_dev<double> &A, const csr_dev<double> &B, csr_dev<double> &C, dbuf<int> &flag,
+                   cudaStream_t s) {
+  int n = A.n;
+  rs_fill_i(flag.p, 0, 1, s);
+  k_expand_count<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, B.rp.p, flag.p);
+  RS_LAUNCHED(1);
+  int mx = d2h(flag.p, 1, s)[0];
+  int cap = 32;
+  while (cap < mx) cap <<= 1;
+  size_t per_warp = (size_t)cap * 16;
+  if (per_warp > 200 * 1024) RS_FAIL(SIM_ERR_ARG, "AMG: Galerkin row needs %d products (limit 12800)", mx);
+  int warps = (int)std::min<size_t>(8, std::max<size_t>(1, (96 * 1024) / per_warp));
+  size_t smem = per_warp * warps;
+  static bool attr = false;
+  if (!attr) {
+    RS_CUDA(cudaFuncSetAttribute(k_spgemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    RS_CUDA(cudaFuncSetAttribute(k_spgemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  unsigned grid = (unsigned)std::min<size_t>((n + warps - 1) / warps, 152 * 64);
+  C.n = n; C.m = B.m;
+  C.rp.ensure(n + 1);
+  k_spgemm<false><<<grid, warps * 32, smem, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, nullptr, C.rp.p,
+                                                 nullptr, nullptr, cap);
+  RS_LAUNCHED(1);
+  RS_CHECK_LAUNCH();
+  C.nnz = rs_scan(C.rp.p, C.rp.p, n, s);
+  RS_CUDA(cudaMemcpyAsync(C.rp.p + n, &C.nnz, sizeof(int), cudaMemcpyHostToDevice, s));
+  C.ci.ensure(C.nnz); C.v.ensure(C.nnz);
+  k_spgemm<true><<<grid, warps * 32, smem, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, C.rp.p, nullptr,
+                                                C.ci.p, C.v.p, cap);
+  RS_LAUNCHED(1);
+  RS_CHECK_LAUNCH();
+  RS_CUDA(cudaStreamSynchronize(s));   // C.nnz host value lives on this stack frame's caller
+}
+
+// ------------------------------------------------------------ smoother ----
+__global__ void k_l1(int n, const int *rp, const int *ci, const double *v, double *dinv, float *dinv32) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0, aii = 0.0;
+  for (int q = rp[i]; q < rp[i + 1]; q++) { if (ci[q] == i) aii = v[q]; else s = add_rn(s, fabs(v[q])); }
+  double d = add_rn(aii, s);
+  dinv[i] = 1.0 / d;
+  if (dinv32) dinv32[i] = (float)(1.0 / d);
+}
+
+// --------------------------------------------------------- dense coarsest -
+__global__ void k_dense_build(int n, const int *rp, const int *ci, const double *v, double *a) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int j = 0; j < n; j++) a[(size_t)i * n + j] = 0.0;
+  for (int q = rp[i]; q < rp[i + 1]; q++) a[(size_t)i * n + ci[q]] = v[q];
+}
+// LU with partial pivoting (first row of maximal |a_ik|), then the inverse
+// column by column; one block.
+__global__ void k_dense_lu_inv(int n, double *a, int *piv, double *inv) {
+  __shared__ double smx[1024]; __shared__ int sid[1024];
+  int t = threadIdx.x, nt = blockDim.x;
+  for (int k = 0; k < n; k++) {
+    double best = -1.0; int bi = n;
+    for (int i = k + t; i < n; i += nt) { double x = fabs(a[(size_t)i * n + k]); if (x > best) { best = x; bi = i; } }
+    smx[t] = best; sid[t] = bi;
+    __syncthreads();
+    for (int o = nt >> 1; o > 0; o >>= 1) {
+      if (t < o) {
+        double x = smx[t + o]; int xi = sid[t + o];
+        if (x > smx[t] || (x == smx[t] && xi < sid[t])) { smx[t] = x; sid[t] = xi; }
+      }
+      __syncthreads();
+    }
+    int p = sid[0];
+    if (t == 0) piv[k] = p;
+    if (p != k)
+      for (int j = t; j < n; j += nt) { double x = a[(size_t)k * n + j]; a[(size_t)k * n + j] = a[(size_t)p * n + j]; a[(size_t)p * n + j] = x; }
+    __syncthreads();
+    for (int i = k + 1 + t; i < n; i += nt) a[(size_t)i * n + k] = div_rn(a[(size_t)i * n + k], a[(size_t)k * n + k]);
+    __syncthreads();
+    for (int e = t; e < (n - k - 1) * (n - k - 1); e += nt) {
+      int i = k + 1 + e / (n - k - 1), j = k + 1 + e % (n - k - 1);
+      a[(size_t)i * n + j] = sub_rn(a[(size_t)i * n + j], mul_rn(a[(size_t)i * n + k], a[(size_t)k * n + j]));
+    }
+    __syncthreads();
+  }
+  // inverse: column c of A^{-1} solves A x = e_c
+  for (int c = t; c < n; c += nt) {
+    double *x = inv + (size_t)c * n;            // stored transposed: inv[c][i] = (A^{-1})_{ic}
+    for (int i = 0; i < n; i++) x[i] = (i == c) ? 1.0 : 0.0;
+    for (int k = 0; k < n; k++) if (piv[k] != k) { double y = x[k]; x[k] = x[piv[k]]; x[piv[k]] = y; }
+    for (int i = 0; i < n; i++) { double s = x[i]; for (int j = 0; j < i; j++) s -= a[(size_t)i * n + j] * x[j]; x[i] = s; }
+    for (int i = n - 1; i >= 0; i--) { double s = x[i]; for (int j = i + 1; j < n; j++) s -= a[(size_t)i * n + j] * x[j]; x[i] = s / a[(size_t)i * n + i]; }
+  }
+}
+
+// ----------------------------------------------------------- host setup ---
+static void csr_cast(const csr_dev<double> &a, csr_dev<float> &b, cudaStream_t s) {
+  b.n = a.n; b.m = a.m; b.nnz = a.nnz;
+  b.rp.ensure(a.n + 1); b.ci.ensure(a.nnz); b.v.ensure(a.nnz);
+  RS_CUDA(cudaMemcpyAsync(b.rp.p, a.rp.p, (a.n + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  if (a.nnz) RS_CUDA(cudaMemcpyAsync(b.ci.p, a.ci.p, a.nnz * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  rs_cast_d2f(a.v.p, b.v.p, a.nnz, s);
+}
+
+void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
+  h.flag.ensure(4);
+  bool mixed = o.precision == SIM_PREC_MIXED;
+  int l = 0;
+  for (;;) {
+    amg_level &L = h.lev[l];
+    int n = L.A.n;
+    L.dinv.ensure(n);
+    if (mixed) L.dinv32.ensure(n);
+    k_l1<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, L.dinv.p, mixed ? L.dinv32.p : nullptr);
+    RS_LAUNCHED(1);
+    L.f.ensure(n); L.x.ensure(n); L.r.ensure(n); L.t.ensure(n);
+    if (mixed) { L.f32.ensure(n); L.x32.ensure(n); L.r32.ensure(n); L.t32.ensure(n); }
+    L.cf.ensure(n); L.strong.ensure(L.A.nnz); L.tpos.ensure(L.A.nnz);
+    L.nc = 0; L.rounds = 0;
+    if (n <= o.coarse_max || l == o.max_levels - 1) { h.coarse_dense = 1; break; }
+    rs_fill_i(h.flag.p, 0, 4, s);
+    k_tpos<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.tpos.p, h.flag.p + 1);
+    k_strength<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, o.theta, L.strong.p);
+    h.hashw.ensure(n); h.newc.ensure(n);
+    k_pmis_init<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, o.seed, l,
+                                                 h.hashw.p, L.cf.p);
+    RS_LAUNCHED(3);
+    RS_CHECK_LAUNCH();
+    if (d2h(h.flag.p + 1, 1, s)[0]) RS_FAIL(SIM_ERR_ARG, "AMG: level %d pattern is not structurally symmetric", l);
+    for (;;) {
+      int und;
+      rs_fill_i(h.flag.p, 0, 1, s);
+      k_pmis_select<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, h.hashw.p,
+                                                     L.cf.p, h.newc.p);
+      k_pmis_update<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, h.newc.p, h.flag.p);
+      RS_LAUNCHED(2);
+      RS_CHECK_LAUNCH();
+      L.rounds++;
+      und = d2h(h.flag.p, 1, s)[0];
+      if (!und) break;
+      if (L.rounds > 1000) RS_FAIL(SIM_ERR_TIMEOUT, "AMG: PMIS did not finish in 1000 rounds");
+    }
+    static thread_local dbuf<int> scratch;   // C flags, then coarse index of each C point
+    scratch.ensure(n + 1);
+    k_cflag<<<grid_for(n, 256), 256, 0, s>>>(n, L.cf.p, scratch.p);
+    RS_LAUNCHED(1);
+    int nc = rs_scan(scratch.p, scratch.p, n, s);
+    L.nc = nc;
+    if (nc == 0) { h.coarse_dense = 0; break; }
+    // P
+    L.P.n = n; L.P.m = nc;
+    L.P.rp.ensure(n + 1);
+    k_interp_count<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, L.P.rp.p);
+    RS_LAUNCHED(1);
+    L.P.nnz = rs_scan(L.P.rp.p, L.P.rp.p, n, s);
+    RS_CUDA(cudaMemcpyAsync(L.P.rp.p + n, &L.P.nnz, sizeof(int), cudaMemcpyHostToDevice, s));
+    L.P.ci.ensure(L.P.nnz); L.P.v.ensure(L.P.nnz);
+    k_interp_fill<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, L.strong.p, L.cf.p, scratch.p,
+                                                   L.P.rp.p, L.P.ci.p, L.P.v.p);
+    RS_LAUNCHED(1);
+    // R = P^T
+    L.R.n = nc; L.R.m = n; L.R.nnz = L.P.nnz;
+    L.R.rp.ensure(nc + 1); L.R.ci.ensure(L.P.nnz); L.R.v.ensure(L.P.nnz);
+    static thread_local dbuf<int> fill;
+    fill.ensure(nc + 1);
+    rs_fill_i(L.R.rp.p, 0, nc + 1, s);
+    rs_fill_i(fill.p, 0, nc + 1, s);
+    k_col_count<<<grid_for(L.P.nnz, 256), 256, 0, s>>>(L.P.nnz, L.P.ci.p, L.R.rp.p);
+    RS_LAUNCHED(1);
+    rs_scan(L.R.rp.p, L.R.rp.p, nc, s);
+    RS_CUDA(cudaMemcpyAsync(L.R.rp.p + nc, &L.R.nnz, sizeof(int), cudaMemcpyHostToDevice, s));
+    k_transpose_fill<<<grid_for(n, 256), 256, 0, s>>>(n, L.P.rp.p, L.P.ci.p, L.P.v.p, L.R.rp.p, fill.p, L.R.ci.p,
+                                                      L.R.v.p);
+    k_sort_rows<<<grid_for(nc, 128), 128, 0, s>>>(nc, L.R.rp.p, L.R.ci.p, L.R.v.p);
+    RS_LAUNCHED(2);
+    // A_{l+1} = R (A P)
+    static thread_local csr_dev<double> AP;
+    spgemm(L.A, L.P, AP, h.flag, s);
+    spgemm(L.R, AP, h.lev[l + 1].A, h.flag, s);
+    if (mixed) { csr_cast(L.P, L.P32, s); csr_cast(L.R, L.R32, s); }
+    l++;
+  }
+  h.nlev = l + 1;
+  for (int k = 0; k < h.nlev && mixed; k++) csr_cast(h.lev[k].A, h.lev[k].A32, s);
+  amg_level &C = h.lev[l];
+  if (h.coarse_dense) {
+    int n = C.A.n;
+    if (n > 2048) RS_FAIL(SIM_ERR_ARG, "AMG: coarsest level of %d rows is too large for the dense solve", n);
+    static thread_local dbuf<double> a;
+    a.ensure((size_t)n * n); h.lu.ensure((size_t)n * n); h.piv.ensure(n);
+    k_dense_build<<<grid_for(n, 128), 128, 0, s>>>(n, C.A.rp.p, C.A.ci.p, C.A.v.p, a.p);
+    k_dense_lu_inv<<<1, 512, 0, s>>>(n, a.p, h.piv.p, h.lu.p);
+    RS_LAUNCHED(2);
+  }
+  RS_CHECK_LAUNCH();
+}
+
+// -------------------------------------------------------------- V-cycle ---
+template <class T>
+__global__ void k_vc_pre(int n, const int *rp, const int *ci, const T *v, const T *dinv, const T *f, T *x, T *r) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T s = f[i];
+  for (int q = rp[i]; q < rp[i + 1]; q++) { int j = ci[q]; s -= v[q] * (f[j] * dinv[j]); }
+  x[i] = f[i] * dinv[i];
+  r[i] = s;
+}
+template <class T>
+__global__ void k_prolong_add(int n, const int *rp, const int *ci, const T *v, const T *e, const T *x, T *t) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T s = x[i];
+  for (int q = rp[i]; q < rp[i + 1]; q++) s += v[q] * e[ci[q]];
+  t[i] = s;
+}
+template <class T>
+__global__ void k_vc_post(int n, const int *rp, const int *ci, const T *v, const T *dinv, const T *f, const T *t, T *x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T s = f[i];
+  for (int q = rp[i]; q < rp[i + 1]; q++) s -= v[q] * t[ci[q]];
+  x[i] = t[i] + dinv[i] * s;
+}
+template <class T>
+__global__ void k_jacobi(int n, const int *rp, const int *ci, const T *v, const T *dinv, const T *f, const T *x, T *y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T s = f[i];
+  for (int q = rp[i]; q < rp[i + 1]; q++) s -= v[q] * x[ci[q]];
+  y[i] = x[i] + dinv[i] * s;
+}
+template <class T>
+__global__ void k_dense_apply(int n, const double *invT, const T *f, T *x) {
+  // x_i = sum_c (A^{-1})_{ic} f_c, invT[c][i]; one warp per row
+  int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int c = lane; c < n; c += 32) s += invT[(size_t)c * n + i] * (double)f[c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) x[i] = (T)s;
+}
+
+template <class T> struct lvl_ptrs;
+template <> struct lvl_ptrs<double> {
+  static const csr_dev<double> &A(amg_level &L) { return L.A; }
+  static const csr_dev<double> &P(amg_level &L) { return L.P; }
+  static const csr_dev<double> &R(amg_level &L) { return L.R; }
+  static double *dinv(amg_level &L) { return L.dinv.p; }
+  static double *f(amg_level &L) { return L.f.p; } static double *x(amg_level &L) { return L.x.p; }
+  static double *r(amg_level &L) { return L.r.p; } static double *t(amg_level &L) { return L.t.p; }
+};
+template <> struct lvl_ptrs<float> {
+  static const csr_dev<float> &A(amg_level &L) { return L.A32; }
+  static const csr_dev<float> &P(amg_level &L) { return L.P32; }
+  static const csr_dev<float> &R(amg_level &L) { return L.R32; }
+  static float *dinv(amg_level &L) { return L.dinv32.p; }
+  static float *f(amg_level &L) { return L.f32.p; } static float *x(amg_level &L) { return L.x32.p; }
+  static float *r(amg_level &L) { return L.r32.p; } static float *t(amg_level &L) { return L.t32.p; }
+};
+
+template <class T>
+void amg_vcycle(amg_hier &h, int l, cudaStream_t s) {
+  typedef lvl_ptrs<T> LP;
+  amg_level &L = h.lev[l];
+  const auto &A = LP::A(L);
+  int n = A.n;
+  if (l == h.nlev - 1) {
+    if (h.coarse_dense) {
+      k_dense_apply<T><<<grid_for(n, 8), 256, 0, s>>>(n, h.lu.p, LP::f(L), LP::x(L));
+      RS_LAUNCHED(1);
+    } else {
+      T *x = LP::x(L), *t = LP::t(L);
+      k_vc_pre<T><<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), x, LP::r(L));
+      RS_LAUNCHED(1);
+      for (int it = 1; it < 10; it++) {
+        k_jacobi<T><<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), x, t);
+        std::swap(x, t);
+        RS_LAUNCHED(1);
+      }
+      if (x != LP::x(L)) RS_CUDA(cudaMemcpyAsync(LP::x(L), x, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    }
+    return;
+  }
+  amg_level &Cl = h.lev[l + 1];
+  const auto &P = LP::P(L);
+  const auto &R = LP::R(L);
+  k_vc_pre<T><<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), LP::x(L), LP::r(L));
+  RS_LAUNCHED(1);
+  csr_spmv<T>(R.rp.p, R.ci.p, R.v.p, LP::r(L), LP::f(Cl), R.n, s);
+  amg_vcycle<T>(h, l + 1, s);
+  k_prolong_add<T><<<grid_for(n, 256), 256, 0, s>>>(n, P.rp.p, P.ci.p, P.v.p, LP::x(Cl), LP::x(L), LP::t(L));
+  k_vc_post<T><<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), LP::t(L), LP::x(L));
+  RS_LAUNCHED(2);
+}
+template void amg_vcycle<double>(amg_hier &, int, cudaStream_t);
+template void amg_vcycle<float>(amg_hier &, int, cudaStream_t);
+
+template <class T>
+__global__ void k_csr_spmv(int n, const int *rp, const int *ci, const T *v, const T *x, T *y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T s = 0;
+  for (int q = rp[i]; q < rp[i + 1]; q++) s += v[q] * x[ci[q]];
+  y[i] = s;
+}
+template <class T>
+void csr_spmv(const int *rp, const int *ci, const T *v, const T *x, T *y, int n, cudaStream_t s) {
+  k_csr_spmv<T><<<grid_for(n, 256), 256, 0, s>>>(n, rp, ci, v, x, y);
+  RS_LAUNCHED(1);
+}
+template void csr_spmv<double>(const int *, const int *, const double *, const double *, double *, int, cudaStream_t);
+template void csr_spmv<float>(const int *, const int *, const float *, const float *, float *, int, cudaStream_t);

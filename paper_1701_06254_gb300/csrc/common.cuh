@@ -1,0 +1,209 @@
+// Internal declarations of the sm_103a CPR-FGMRES library (libresim.so).
+// Not part of the public ABI (that is include/resim.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <string>
+#include <vector>
+#include "../../include/resim.h"
+
+#define RS_CDARCY (9.869233e-16 * 1e5 / 1e-3 * 86400.0)   // k[mD] A/L dp[bar]/mu[cP] -> m3/day
+#define RS_PA2BAR 1e-5
+
+// ---------------------------------------------------------------- errors --
+void rs_set_error(const char *fmt, ...);
+struct rs_error {                       // thrown inside the library, caught at the ABI
+  sim_status code;
+  explicit rs_error(sim_status c) : code(c) {}
+};
+#define RS_CUDA(call)                                                                 \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      rs_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+      throw rs_error(e_ == cudaErrorMemoryAllocation ? SIM_ERR_OOM : SIM_ERR_CUDA);   \
+    }                                                                                 \
+  } while (0)
+#define RS_CHECK_LAUNCH() RS_CUDA(cudaGetLastError())
+#define RS_FAIL(code, ...) do { rs_set_error(__VA_ARGS__); throw rs_error(code); } while (0)
+
+extern unsigned long long rs_launches;     // kernel launches issued (all handles)
+#define RS_LAUNCHED(k) (rs_launches += (k))
+
+// ---------------------------------------------------------------- memory --
+template <class T> struct dbuf {            // owning device buffer
+  T *p = nullptr; size_t n = 0;
+  void alloc(size_t m) {
+    if (m == n && p) return;
+    free();
+    if (m) RS_CUDA(cudaMalloc((void **)&p, m * sizeof(T)));
+    n = m;
+  }
+  void ensure(size_t m) { if (m > n) alloc(m); }
+  void free() { if (p) cudaFree(p); p = nullptr; n = 0; }
+  ~dbuf() { free(); }
+  dbuf() = default;
+  dbuf(const dbuf &) = delete;
+  dbuf &operator=(const dbuf &) = delete;
+};
+template <class T> void h2d(dbuf<T> &d, const T *h, size_t m, cudaStream_t s) {
+  d.alloc(m);
+  if (m) RS_CUDA(cudaMemcpyAsync(d.p, h, m * sizeof(T), cudaMemcpyDefault, s));
+}
+template <class T> void h2d(dbuf<T> &d, const std::vector<T> &h, cudaStream_t s) { h2d(d, h.data(), h.size(), s); }
+template <class T> std::vector<T> d2h(const T *d, size_t m, cudaStream_t s) {
+  std::vector<T> h(m);
+  if (m) RS_CUDA(cudaMemcpyAsync(h.data(), d, m * sizeof(T), cudaMemcpyDefault, s));
+  RS_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+inline unsigned grid_for(size_t n, int bs) { size_t g = (n + bs - 1) / bs; return (unsigned)(g ? g : 1); }
+
+// ------------------------------------------------------- device helpers --
+// Arithmetic used where a floating-point value decides an integer (the
+// decoupled matrix, the reordering key, AMG strength / PMIS / P / RAP):
+// explicit round-to-nearest operations that the compiler may not contract
+// into fused multiply-adds, so results match a plain IEEE evaluation in the
+// order written.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+
+// ------------------------------------------------------------ utilities --
+// exclusive scan of n int32 values (in may alias out); returns the total
+int rs_scan(const int *in, int *out, int n, cudaStream_t s);
+// deterministic reductions (fixed association order for a given n)
+void rs_dot_partials(const double *x, const double *y, int n, double *partials, int nblk, cudaStream_t s);
+double rs_norm2(const double *x, int n, cudaStream_t s);   // syncs
+void rs_fill_i(int *p, int v, size_t n, cudaStream_t s);
+void rs_fill_d(double *p, double v, size_t n, cudaStream_t s);
+void rs_fill_f(float *p, float v, size_t n, cudaStream_t s);
+void rs_cast_d2f(const double *a, float *b, size_t n, cudaStream_t s);
+
+// --------------------------------------------------------------- options --
+struct rs_opts {
+  int precision, decoupling, reorder, newton;
+  double newton_tol, lin_tol;
+  int max_newton, restart, max_lin, tile_x, tile_y;
+  double theta;
+  int max_levels, coarse_max;
+  uint64_t seed;
+  int max_cuts;
+  double dt;
+};
+rs_opts rs_opts_from(const sim_options *o);
+
+// ---------------------------------------------------------------- AMG -----
+template <class T> struct csr_dev { int n = 0, m = 0, nnz = 0; dbuf<int> rp, ci; dbuf<T> v; };
+
+struct amg_level {
+  csr_dev<double> A;            // FP64 operator (setup)
+  csr_dev<double> P, R;         // interpolation / restriction (FP64)
+  csr_dev<float> A32, P32, R32; // mixed-precision copies
+  dbuf<double> dinv;            // 1 / l1 diagonal
+  dbuf<float> dinv32;
+  dbuf<int8_t> cf;
+  dbuf<uint8_t> strong;
+  dbuf<int> tpos;               // position of (j,i) in row j for each (i,j)
+  int nc = 0, rounds = 0;
+  dbuf<double> f, x, r, t;      // cycle work vectors (FP64)
+  dbuf<float> f32, x32, r32, t32;
+};
+
+struct amg_hier {
+  int nlev = 0;
+  amg_level lev[32];
+  int coarse_dense = 1;
+  dbuf<double> lu;              // dense LU of the coarsest level
+  dbuf<int> piv;
+  dbuf<int> flag;               // device counters / error words
+  dbuf<double> hashw;           // PMIS weights
+  dbuf<int8_t> newc;
+};
+
+void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s);   // level 0 A must be filled
+template <class T> void amg_vcycle(amg_hier &h, int l, cudaStream_t s);  // f -> x of level l
+
+// ---------------------------------------------------------------- RAS -----
+struct ras_data {
+  int nsub = 0, max_ext = 0, max_nnz = 0;
+  // static (host-built at creation): per subdomain, ext rows in natural
+  // order (cells ascending then wells ascending)
+  dbuf<int> sub_ptr;            // nsub+1 offsets into ext arrays
+  dbuf<int> ext;                // global row of each ext entry
+  dbuf<uint8_t> owned;          // 1 if the ext entry is owned
+  dbuf<int> ncell;              // cells among ext entries, per subdomain
+  dbuf<int> lrp_ptr;            // nsub+1 offsets into the local-pattern entries
+  dbuf<int> lrlen;              // local row length per ext entry
+  dbuf<int> lrp;                // local row start per ext entry (natural ext order)
+  dbuf<int> lci;                // ext-index column per local entry
+  dbuf<int> lsrc;               // BSR block position per local entry
+  // per setup
+  dbuf<int> perm;               // position -> ext index (per subdomain segment)
+  dbuf<int> ipos;               // ext index -> position
+  dbuf<int> frp;                // factor row start per position (segment-local offsets)
+  dbuf<int> fci;                // factor column (position) per entry
+  dbuf<int> fdiag;              // diagonal entry per position
+  dbuf<double> fval;            // FP64 factors (4 per entry)
+  dbuf<float> fval32;           // FP32 factors
+  dbuf<double> dinv;            // inverse U diagonal blocks (4 per row)
+  dbuf<float> dinv32;
+  dbuf<int> lvl;                // per position: L level, U level
+  dbuf<int> lvl_rows;           // rows grouped by L level, then by U level
+  dbuf<int> nlev;               // per subdomain: #L levels, #U levels
+  dbuf<int> lvl_ptr;            // per subdomain: offsets of the L and U level groups
+  int max_lvl_ptr = 0;
+};
+
+// ---------------------------------------------------------- linear system --
+struct sim_ls_s {
+  int nx, ny, nz, n, nw, nb, nnzb;
+  rs_opts o;
+  cudaStream_t st = nullptr;
+  std::vector<int> h_rp, h_ci, h_wc0;
+  dbuf<int> rp, ci, dpos;       // pattern, diagonal position per row
+  dbuf<double> val, b, key, dmat;
+  dbuf<float> val32;
+  dbuf<int> app_src;            // BSR positions of the A_pp entries
+  ras_data ras;
+  amg_hier amg;
+  // Krylov
+  dbuf<double> V, Z, w, r, y, hbuf, partial;
+  dbuf<float> Z32;
+  dbuf<double> x64a, x64b;      // CPR work (FP64)
+  dbuf<float> x32a, x32b, x32c; // CPR work (FP32)
+  double *hpin = nullptr;       // pinned host scalars
+  bool have_setup = false;
+  // timing
+  int timer_which = 0;
+  long long timer_launches = 0;
+  double timer_ms = 0;
+  std::vector<cudaEvent_t> ev;
+  int ev_used = 0;
+  void timer_flush();
+  ~sim_ls_s();
+};
+
+struct rs_timed {                       // brackets launches of one kernel family
+  sim_ls_s *ls; bool on;
+  rs_timed(sim_ls_s *l, int which);
+  ~rs_timed();
+};
+
+void ls_init(sim_ls_s *ls, int nx, int ny, int nz, int nw, const int *rp, const int *ci,
+             const int *well_cell0, const rs_opts &o, cudaStream_t st);
+void ls_setup(sim_ls_s *ls);
+int ls_solve(sim_ls_s *ls, double tol, int *its, double *relres);   // solution in ls->y
+void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32);
+void ls_spmv64(sim_ls_s *ls, const double *x, double *y);
+template <class T> void ls_ras_apply(sim_ls_s *ls, const T *f, T *x);
+void ras_build_static(sim_ls_s *ls);
+void ras_setup(sim_ls_s *ls);
+
+// SpMV kernels (block 2x2, values Tv, vectors Tx in / Ty out)
+template <class Tv, class Tx, class Ty>
+void bsr_spmv(const int *rp, const int *ci, const Tv *val, const Tx *x, Ty *y, const Ty *f, int nb, cudaStream_t s);
+template <class T>
+void csr_spmv(const int *rp, const int *ci, const T *v, const T *x, T *y, int n, cudaStream_t s);

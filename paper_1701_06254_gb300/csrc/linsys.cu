@@ -1,0 +1,487 @@
+// The Newton linear system and its solver (arXiv 1701.06254):
+//   decoupling D^{-1} A x = D^{-1} b, eq. (29), with the ABF or Quasi-IMPES
+//   operator (Sec. "Matrix decoupling strategy");
+//   CPR-FPF, Algorithm 2, with the restriction / prolongation of eqs. (34)-(35);
+//   restarted flexible GMRES, right preconditioned, stopping per eq. (24).
+// Storage: 2x2 blocks with cell-interleaved unknowns (p, s_w), which is the
+// field-split system of eqs. (20)-(23) under a fixed permutation; each well
+// row is padded to a 2x2 block with a dummy unknown whose equation is 1*x = 0.
+#include "common.cuh"
+#include <algorithm>
+#include <cmath>
+
+// ------------------------------------------------------------ timers -----
+rs_timed::rs_timed(sim_ls_s *l, int which) : ls(l), on(l->timer_which == which && which != 0) {
+  if (!on) return;
+  if (ls->ev_used + 2 > (int)ls->ev.size()) ls->timer_flush();
+  if (ls->ev_used + 2 > (int)ls->ev.size()) {
+    for (int k = 0; k < 64; k++) { cudaEvent_t e; RS_CUDA(cudaEventCreate(&e)); ls->ev.push_back(e); }
+  }
+  RS_CUDA(cudaEventRecord(ls->ev[ls->ev_used], ls->st));
+}
+rs_timed::~rs_timed() {
+  if (!on) return;
+  cudaEventRecord(ls->ev[ls->ev_used + 1], ls->st);
+  ls->ev_used += 2;
+  ls->timer_launches++;
+}
+void sim_ls_s::timer_flush() {
+  if (!ev_used) return;
+  cudaEventSynchronize(ev[ev_used - 1]);
+  for (int k = 0; k < ev_used; k += 2) {
+    float ms = 0; cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+    timer_ms += ms;
+  }
+  ev_used = 0;
+}
+sim_ls_s::~sim_ls_s() {
+  for (auto e : ev) cudaEventDestroy(e);
+  if (hpin) cudaFreeHost(hpin);
+}
+
+// ---------------------------------------------------------- decoupling ---
+// ABF: every cell row is multiplied by the inverse of its 2x2 diagonal
+// block, [[d, -b], [-c, a]] / (ad - bc); each entry is formed by separate
+// round-to-nearest multiplications, additions and divisions in the order
+// written (so the decoupled matrix is the IEEE evaluation of this formula).
+__global__ void k_abf(int n, int nb, const int *rp, const int *dpos, double *val, double *b, double *dmat, float *val32) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  double *D = dmat + 4 * (size_t)i;
+  if (i >= n) {
+    D[0] = 1; D[1] = 0; D[2] = 0; D[3] = 1;
+    if (val32) for (int q = rp[i]; q < rp[i + 1]; q++) for (int e = 0; e < 4; e++) val32[4 * (size_t)q + e] = (float)val[4 * (size_t)q + e];
+    return;
+  }
+  const double *M = val + 4 * (size_t)dpos[i];
+  double a = M[0], bb = M[1], c = M[2], d = M[3];
+  D[0] = a; D[1] = bb; D[2] = c; D[3] = d;
+  double det = sub_rn(mul_rn(a, d), mul_rn(bb, c));
+  double i00 = div_rn(d, det), i01 = div_rn(-bb, det), i10 = div_rn(-c, det), i11 = div_rn(a, det);
+  for (int q = rp[i]; q < rp[i + 1]; q++) {
+    double *B = val + 4 * (size_t)q;
+    double b00 = B[0], b01 = B[1], b10 = B[2], b11 = B[3];
+    double n0 = add_rn(mul_rn(i00, b00), mul_rn(i01, b10));
+    double n1 = add_rn(mul_rn(i00, b01), mul_rn(i01, b11));
+    double n2 = add_rn(mul_rn(i10, b00), mul_rn(i11, b10));
+    double n3 = add_rn(mul_rn(i10, b01), mul_rn(i11, b11));
+    B[0] = n0; B[1] = n1; B[2] = n2; B[3] = n3;
+    if (val32) { float4 f4 = make_float4((float)n0, (float)n1, (float)n2, (float)n3); reinterpret_cast<float4 *>(val32)[q] = f4; }
+  }
+  double r0 = b[2 * (size_t)i], r1 = b[2 * (size_t)i + 1];
+  b[2 * (size_t)i] = add_rn(mul_rn(i00, r0), mul_rn(i01, r1));
+  b[2 * (size_t)i + 1] = add_rn(mul_rn(i10, r0), mul_rn(i11, r1));
+}
+
+// Quasi-IMPES: pressure row -= Diag(A_ps) Diag(A_ss)^{-1} * saturation row.
+__global__ void k_qi(int n, int nb, const int *rp, const int *dpos, double *val, double *b, double *dmat, float *val32) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  double *D = dmat + 4 * (size_t)i;
+  D[0] = 1; D[1] = 0; D[2] = 0; D[3] = 1;
+  if (i < n) {
+    const double *M = val + 4 * (size_t)dpos[i];
+    double ratio = div_rn(M[1], M[3]);
+    D[1] = ratio;
+    for (int q = rp[i]; q < rp[i + 1]; q++) {
+      double *B = val + 4 * (size_t)q;
+      B[0] = sub_rn(B[0], mul_rn(ratio, B[2]));
+      B[1] = sub_rn(B[1], mul_rn(ratio, B[3]));
+    }
+    b[2 * (size_t)i] = sub_rn(b[2 * (size_t)i], mul_rn(ratio, b[2 * (size_t)i + 1]));
+  }
+  if (val32) for (int q = rp[i]; q < rp[i + 1]; q++) for (int e = 0; e < 4; e++) val32[4 * (size_t)q + e] = (float)val[4 * (size_t)q + e];
+}
+
+__global__ void k_identity_d(int nb, double *dmat) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  double *D = dmat + 4 * (size_t)i;
+  D[0] = 1; D[1] = 0; D[2] = 0; D[3] = 1;
+}
+
+// A_pp: entry [0][0] of every cell-cell block (Pi_r of eq. 34 keeps cell pressures)
+__global__ void k_extract_app(int nnz, const int *src, const double *val, double *v) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nnz) v[k] = val[4 * (size_t)src[k]];
+}
+
+// ------------------------------------------------------------- SpMV ------
+template <class T> struct vec2_t;
+template <> struct vec2_t<double> { typedef double2 type; };
+template <> struct vec2_t<float> { typedef float2 type; };
+
+// y = A x  (f == nullptr) or y = f - A x.  One warp owns 32 consecutive
+// block rows: the warp reads its contiguous range of blocks coalesced
+// (lane t takes block q0 + t + 32k), stages the 2-vectors A_q x_{c(q)} in
+// shared memory, and each lane then sums the products of its own row in
+// ascending block order.
+#define SPMV_WARPS 8
+#define SPMV_CHUNK 256
+template <class Tv, class Tx, class Tf, class Ty>
+__global__ void __launch_bounds__(SPMV_WARPS * 32)
+k_bsr_spmv(int nb, const int *__restrict__ rp, const int *__restrict__ ci, const Tv *__restrict__ val,
+           const Tx *__restrict__ x, const Tf *__restrict__ f, Ty *__restrict__ y) {
+  __shared__ Ty prod[SPMV_WARPS][SPMV_CHUNK][2];
+  int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int r0 = (blockIdx.x * SPMV_WARPS + wid) * 32;
+  if (r0 >= nb) return;
+  int r = r0 + lane, rend = min(r0 + 32, nb);
+  int q0 = rp[r0], q1 = rp[rend];
+  int myq0 = r < nb ? rp[r] : q1, myq1 = r < nb ? rp[r + 1] : q1;
+  Ty a0 = 0, a1 = 0;
+  typedef typename vec2_t<Tx>::type X2;
+  for (int c0 = q0; c0 < q1; c0 += SPMV_CHUNK) {
+    int c1 = min(c0 + SPMV_CHUNK, q1);
+    for (int q = c0 + lane; q < c1; q += 32) {
+      int c = __ldg(ci + q);
+      X2 xv = reinterpret_cast<const X2 *>(x)[c];
+      Ty b0, b1, b2, b3;
+      if (sizeof(Tv) == 8) {
+        double2 u = __ldg(reinterpret_cast<const double2 *>(val) + 2 * (size_t)q);
+        double2 w = __ldg(reinterpret_cast<const double2 *>(val) + 2 * (size_t)q + 1);
+        b0 = (Ty)u.x; b1 = (Ty)u.y; b2 = (Ty)w.x; b3 = (Ty)w.y;
+      } else {
+        float4 u = __ldg(reinterpret_cast<const float4 *>(val) + q);
+        b0 = (Ty)u.x; b1 = (Ty)u.y; b2 = (Ty)u.z; b3 = (Ty)u.w;
+      }
+      Ty x0 = (Ty)xv.x, x1 = (Ty)xv.y;
+      prod[wid][q - c0][0] = b0 * x0 + b1 * x1;
+      prod[wid][q - c0][1] = b2 * x0 + b3 * x1;
+    }
+    __syncwarp();
+    int s0 = max(myq0, c0), s1 = min(myq1, c1);
+    for (int q = s0; q < s1; q++) { a0 += prod[wid][q - c0][0]; a1 += prod[wid][q - c0][1]; }
+    __syncwarp();
+  }
+  if (r < nb) {
+    if (f) { a0 = (Ty)f[2 * (size_t)r] - a0; a1 = (Ty)f[2 * (size_t)r + 1] - a1; }
+    typedef typename vec2_t<Ty>::type Y2;
+    Y2 o; o.x = a0; o.y = a1;
+    reinterpret_cast<Y2 *>(y)[r] = o;
+  }
+}
+
+template <class Tv, class Tx, class Tf, class Ty>
+static void spmv(const sim_ls_s *ls, const Tv *val, const Tx *x, const Tf *f, Ty *y, cudaStream_t s) {
+  unsigned g = grid_for(ls->nb, SPMV_WARPS * 32);
+  k_bsr_spmv<Tv, Tx, Tf, Ty><<<g, SPMV_WARPS * 32, 0, s>>>(ls->nb, ls->rp.p, ls->ci.p, val, x, f, y);
+  RS_LAUNCHED(1);
+}
+
+void ls_spmv64(sim_ls_s *ls, const double *x, double *y) {
+  rs_timed tm(ls, SIM_T_SPMV64);
+  spmv<double, double, double, double>(ls, ls->val.p, x, (const double *)nullptr, y, ls->st);
+}
+
+// ------------------------------------------------------- CPR pieces ------
+template <class Ti, class To>
+__global__ void k_gather_p(int n, const Ti *r, To *f) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) f[i] = (To)r[2 * (size_t)i];
+}
+template <class T>
+__global__ void k_add_p(int n, const T *e, T *x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[2 * (size_t)i] += e[i];
+}
+template <class Ti, class T>
+__global__ void k_ras_in_cast(size_t m, const Ti *a, T *b) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < m) b[i] = (T)a[i];
+}
+template <class T>
+__global__ void k_add_vec(size_t m, const T *a, T *b) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < m) b[i] += a[i];
+}
+
+// CPR-FPF (Algorithm 2): z = R^{-1} v; r = v - A z; z += Pi_p M(A_pp)^{-1} Pi_r r;
+// r = v - A z; z += R^{-1} r.  FP64 preconditioner: A is the decoupled FP64
+// matrix; mixed: FP32 matrix, factors, hierarchy and vectors (FP64 coarsest).
+void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32) {
+  cudaStream_t s = ls->st;
+  int n = ls->n, nu = 2 * ls->nb;
+  amg_level &L0 = ls->amg.lev[0];
+  if (ls->o.precision == SIM_PREC_MIXED) {
+    float *z = z32, *r = ls->x32b.p, *t = ls->x32c.p;
+    k_ras_in_cast<double, float><<<grid_for(nu, 256), 256, 0, s>>>(nu, v, t);
+    RS_LAUNCHED(1);
+    ls_ras_apply<float>(ls, t, z);                                                     // 1
+    { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, double, float>(ls, ls->val32.p, z, v, r, s); }  // 2
+    k_gather_p<float, float><<<grid_for(n, 256), 256, 0, s>>>(n, r, L0.f32.p);
+    RS_LAUNCHED(1);
+    { rs_timed tm(ls, SIM_T_VCYCLE); amg_vcycle<float>(ls->amg, 0, s); }               // 3
+    k_add_p<float><<<grid_for(n, 256), 256, 0, s>>>(n, L0.x32.p, z);
+    RS_LAUNCHED(1);
+    { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, double, float>(ls, ls->val32.p, z, v, r, s); }  // 4
+    ls_ras_apply<float>(ls, r, t);                                                     // 5
+    k_add_vec<float><<<grid_for(nu, 256), 256, 0, s>>>(nu, t, z);
+    RS_LAUNCHED(1);
+  } else {
+    double *z = z64, *r = ls->x64a.p, *t = ls->x64b.p;
+    ls_ras_apply<double>(ls, v, z);
+    { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<double, double, double, double>(ls, ls->val.p, z, v, r, s); }
+    k_gather_p<double, double><<<grid_for(n, 256), 256, 0, s>>>(n, r, L0.f.p);
+    RS_LAUNCHED(1);
+    { rs_timed tm(ls, SIM_T_VCYCLE); amg_vcycle<double>(ls->amg, 0, s); }
+    k_add_p<double><<<grid_for(n, 256), 256, 0, s>>>(n, L0.x.p, z);
+    RS_LAUNCHED(1);
+    { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<double, double, double, double>(ls, ls->val.p, z, v, r, s); }
+    ls_ras_apply<double>(ls, r, t);
+    k_add_vec<double><<<grid_for(nu, 256), 256, 0, s>>>(nu, t, z);
+    RS_LAUNCHED(1);
+  }
+}
+
+// ------------------------------------------------------------ init -------
+void ls_init(sim_ls_s *ls, int nx, int ny, int nz, int nw, const int *rp, const int *ci, const int *well_cell0,
+             const rs_opts &o, cudaStream_t st) {
+  ls->nx = nx; ls->ny = ny; ls->nz = nz; ls->n = nx * ny * nz; ls->nw = nw; ls->nb = ls->n + nw;
+  ls->o = o; ls->st = st;
+  int nb = ls->nb;
+  ls->h_rp.assign(rp, rp + nb + 1);
+  ls->nnzb = rp[nb];
+  ls->h_ci.assign(ci, ci + ls->nnzb);
+  ls->h_wc0.assign(well_cell0, well_cell0 + nw);
+  std::vector<int> dpos(nb, -1), app_src, app_rp(ls->n + 1, 0), app_ci;
+  for (int i = 0; i < nb; i++) {
+    for (int q = rp[i]; q < rp[i + 1]; q++) {
+      if (q > rp[i] && ci[q] <= ci[q - 1]) RS_FAIL(SIM_ERR_ARG, "row %d: columns not strictly ascending", i);
+      if (ci[q] < 0 || ci[q] >= nb) RS_FAIL(SIM_ERR_ARG, "row %d: column out of range", i);
+      if (ci[q] == i) dpos[i] = q;
+      if (i < ls->n && ci[q] < ls->n) { app_src.push_back(q); app_ci.push_back(ci[q]); }
+    }
+    if (dpos[i] < 0) RS_FAIL(SIM_ERR_ARG, "row %d has no diagonal block", i);
+    if (i < ls->n) app_rp[i + 1] = (int)app_src.size();
+  }
+  for (int w = 0; w < nw; w++)
+    if (well_cell0[w] < 0 || well_cell0[w] >= ls->n) RS_FAIL(SIM_ERR_ARG, "well %d: bad first perforation", w);
+  h2d(ls->rp, ls->h_rp, st); h2d(ls->ci, ls->h_ci, st); h2d(ls->dpos, dpos, st);
+  ls->val.alloc(4 * (size_t)ls->nnzb); ls->b.alloc(2 * (size_t)nb); ls->key.alloc(ls->n);
+  ls->dmat.alloc(4 * (size_t)nb);
+  if (o.precision == SIM_PREC_MIXED) ls->val32.alloc(4 * (size_t)ls->nnzb);
+  h2d(ls->app_src, app_src, st);
+  csr_dev<double> &A0 = ls->amg.lev[0].A;
+  A0.n = A0.m = ls->n; A0.nnz = (int)app_src.size();
+  h2d(A0.rp, app_rp, st); h2d(A0.ci, app_ci, st); A0.v.alloc(A0.nnz);
+  ras_build_static(ls);
+  size_t nu = 2 * (size_t)nb;
+  ls->y.alloc(nu); ls->w.alloc(nu); ls->r.alloc(nu);
+  ls->x64a.alloc(nu); ls->x64b.alloc(nu);
+  if (o.precision == SIM_PREC_MIXED) { ls->x32b.alloc(nu); ls->x32c.alloc(nu); }
+  RS_CUDA(cudaHostAlloc((void **)&ls->hpin, 64 * sizeof(double), cudaHostAllocMapped));
+  RS_CUDA(cudaStreamSynchronize(st));
+}
+
+void ls_setup(sim_ls_s *ls) {
+  cudaStream_t s = ls->st;
+  float *v32 = ls->o.precision == SIM_PREC_MIXED ? ls->val32.p : nullptr;
+  unsigned g = grid_for(ls->nb, 128);
+  if (ls->o.decoupling == SIM_DEC_ABF)
+    k_abf<<<g, 128, 0, s>>>(ls->n, ls->nb, ls->rp.p, ls->dpos.p, ls->val.p, ls->b.p, ls->dmat.p, v32);
+  else if (ls->o.decoupling == SIM_DEC_QI)
+    k_qi<<<g, 128, 0, s>>>(ls->n, ls->nb, ls->rp.p, ls->dpos.p, ls->val.p, ls->b.p, ls->dmat.p, v32);
+  else {
+    k_identity_d<<<g, 128, 0, s>>>(ls->nb, ls->dmat.p);
+    if (v32) rs_cast_d2f(ls->val.p, v32, 4 * (size_t)ls->nnzb, s);
+  }
+  RS_LAUNCHED(1);
+  csr_dev<double> &A0 = ls->amg.lev[0].A;
+  k_extract_app<<<grid_for(A0.nnz, 256), 256, 0, s>>>(A0.nnz, ls->app_src.p, ls->val.p, A0.v.p);
+  RS_LAUNCHED(1);
+  RS_CHECK_LAUNCH();
+  ras_setup(ls);
+  amg_setup(ls->amg, ls->o, s);
+  ls->have_setup = true;
+}
+
+// ------------------------------------------------------------ FGMRES -----
+// Classical Gram-Schmidt, applied twice.  Each pass is one sweep over the
+// rows: a block owns a fixed row range, every thread accumulates its part of
+// each dot product, warps reduce with shuffles and the block writes one
+// partial per vector; a second kernel adds the partials in block order, so
+// the result does not depend on scheduling.
+#define ORTHO_BS 256
+#define ORTHO_MAXV 64
+static int ortho_blocks(int nu) { int b = (nu + 8191) / 8192; return b < 1 ? 1 : (b > 608 ? 608 : b); }
+
+// mode 0: dots d_k = V_k . w;  mode 1: w -= sum_k h_k V_k, then dots with the new w;
+// mode 2: w -= sum_k h_k V_k, then ||w||^2 (partial index 0).
+template <int MODE>
+__global__ void __launch_bounds__(ORTHO_BS) k_ortho(int nu, int nv, const double *__restrict__ V, double *w,
+                                                    const double *__restrict__ h, double *part) {
+  __shared__ double sred[ORTHO_MAXV][ORTHO_BS / 32];
+  __shared__ double sh[ORTHO_MAXV];
+  int nblk = gridDim.x, chunk = (nu + nblk - 1) / nblk;
+  int i0 = blockIdx.x * chunk, i1 = min(nu, i0 + chunk);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (MODE != 0) { for (int k = threadIdx.x; k < nv; k += blockDim.x) sh[k] = h[k]; __syncthreads(); }
+  if (MODE != 0) {
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      double s = 0.0;
+      for (int k = 0; k < nv; k++) s += sh[k] * V[(size_t)k * nu + i];
+      w[i] -= s;
+    }
+    __syncthreads();
+  }
+  if (MODE == 2) {
+    double s = 0.0;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += w[i] * w[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) sred[0][wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) { double t = 0; for (int k = 0; k < ORTHO_BS / 32; k++) t += sred[0][k]; part[blockIdx.x] = t; }
+    return;
+  }
+  for (int k = 0; k < (MODE == 2 ? 0 : nv); k++) {
+    double s = 0.0;
+    const double *vk = V + (size_t)k * nu;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += vk[i] * w[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) sred[k][wid] = s;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+    double t = 0; for (int q = 0; q < ORTHO_BS / 32; q++) t += sred[k][q];
+    part[(size_t)k * nblk + blockIdx.x] = t;
+  }
+}
+__global__ void k_reduce_parts(int nv, int nblk, const double *part, double *out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nv) return;
+  double t = 0;
+  for (int b = 0; b < nblk; b++) t += part[(size_t)k * nblk + b];
+  out[k] = t;
+}
+
+// Hessenberg column j: h = h1 + h2, h_{j+1,j} = ||w||; previous Givens
+// rotations, a new one, and the residual estimate |g_{j+1}|.
+// G layout: [0..m*(m+1)) H column-major (m+1 per column), cs[m], sn[m], g[m+1]
+__global__ void k_arnoldi_col(int j, int m, const double *h1, const double *h2, const double *nrm2, double *G,
+                              double *hnorm, volatile double *host) {
+  double *H = G, *cs = G + (size_t)m * (m + 1), *sn = cs + m, *g = sn + m;
+  double *col = H + (size_t)j * (m + 1);
+  for (int k = 0; k <= j; k++) col[k] = h1[k] + h2[k];
+  double hn = sqrt(*nrm2);
+  *hnorm = hn;
+  for (int k = 0; k < j; k++) {
+    double t = cs[k] * col[k] + sn[k] * col[k + 1];
+    col[k + 1] = -sn[k] * col[k] + cs[k] * col[k + 1];
+    col[k] = t;
+  }
+  double rr = sqrt(col[j] * col[j] + hn * hn);
+  cs[j] = col[j] / rr; sn[j] = hn / rr;
+  col[j] = rr; col[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  host[0] = fabs(g[j + 1]);
+  host[1] = hn;
+}
+__global__ void k_scale(int nu, const double *w, const double *hn, double *v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double s = *hn;
+  if (i < nu) v[i] = s > 0.0 ? w[i] / s : 0.0;
+}
+__global__ void k_start(int nu, const double *r, double beta, double *v0, double *G, int m) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nu) v0[i] = r[i] / beta;
+  if (i == 0) { double *g = G + (size_t)m * (m + 1) + 2 * m; for (int k = 0; k <= m; k++) g[k] = 0.0; g[0] = beta; }
+}
+__global__ void k_hsolve(int jend, int m, const double *G, double *yk) {
+  const double *H = G, *g = G + (size_t)m * (m + 1) + 2 * m;
+  for (int k = jend - 1; k >= 0; k--) {
+    double s = g[k];
+    for (int l = k + 1; l < jend; l++) s -= H[(size_t)l * (m + 1) + k] * yk[l];
+    yk[k] = s / H[(size_t)k * (m + 1) + k];
+  }
+}
+template <class Tz>
+__global__ void k_xupdate(int nu, int jend, const double *yk, const Tz *Z, double *x) {
+  __shared__ double sy[ORTHO_MAXV];
+  for (int k = threadIdx.x; k < jend; k += blockDim.x) sy[k] = yk[k];
+  __syncthreads();
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nu) return;
+  double s = 0.0;
+  for (int k = 0; k < jend; k++) s += sy[k] * (double)Z[(size_t)k * nu + i];
+  x[i] += s;
+}
+
+int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres) {
+  cudaStream_t s = ls->st;
+  int nu = 2 * ls->nb, m = std::min(ls->o.restart, ORTHO_MAXV - 1), maxit = ls->o.max_lin;
+  bool mixed = ls->o.precision == SIM_PREC_MIXED;
+  ls->V.ensure((size_t)(m + 1) * nu);
+  if (mixed) ls->Z32.ensure((size_t)m * nu); else ls->Z.ensure((size_t)m * nu);
+  int nblk = ortho_blocks(nu);
+  ls->partial.ensure((size_t)ORTHO_MAXV * nblk + 8);
+  ls->hbuf.ensure((size_t)(m + 1) * (m + 1) + 4 * (m + 1) + 4 * ORTHO_MAXV + 8);
+  double *G = ls->hbuf.p, *h1 = G + (size_t)(m + 1) * (m + 1) + 3 * (m + 1), *h2 = h1 + ORTHO_MAXV,
+         *nrm = h2 + ORTHO_MAXV, *hn = nrm + 1, *yk = hn + 1;
+  volatile double *hp = ls->hpin;
+  double *hp_dev;
+  RS_CUDA(cudaHostGetDevicePointer((void **)&hp_dev, ls->hpin, 0));
+  rs_fill_d(ls->y.p, 0.0, nu, s);
+  double bn = rs_norm2(ls->b.p, nu, s);
+  if (bn == 0.0) { *its_out = 0; *relres = 0.0; return 0; }
+  if (!std::isfinite(bn)) { *its_out = 0; *relres = NAN; return 2; }
+  RS_CUDA(cudaMemcpyAsync(ls->r.p, ls->b.p, nu * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  double beta = bn;
+  int its = 0, rc = 1;
+  for (;;) {
+    k_start<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->r.p, beta, ls->V.p, G, m);
+    RS_LAUNCHED(1);
+    int jend = 0;
+    for (int j = 0; j < m; j++) {
+      double *vj = ls->V.p + (size_t)j * nu;
+      if (mixed) {
+        float *zj = ls->Z32.p + (size_t)j * nu;
+        ls_cpr(ls, vj, nullptr, zj);
+        rs_timed tm(ls, SIM_T_SPMV64);
+        spmv<double, float, double, double>(ls, ls->val.p, zj, (const double *)nullptr, ls->w.p, s);
+      } else {
+        double *zj = ls->Z.p + (size_t)j * nu;
+        ls_cpr(ls, vj, zj, nullptr);
+        ls_spmv64(ls, zj, ls->w.p);
+      }
+      {
+        rs_timed tm(ls, SIM_T_ORTHO);
+        int nv = j + 1;
+        k_ortho<0><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, ls->V.p, ls->w.p, nullptr, ls->partial.p);
+        k_reduce_parts<<<1, 64, 0, s>>>(nv, nblk, ls->partial.p, h1);
+        k_ortho<1><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, ls->V.p, ls->w.p, h1, ls->partial.p);
+        k_reduce_parts<<<1, 64, 0, s>>>(nv, nblk, ls->partial.p, h2);
+        k_ortho<2><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, ls->V.p, ls->w.p, h2, ls->partial.p);
+        k_reduce_parts<<<1, 64, 0, s>>>(1, nblk, ls->partial.p, nrm);
+        k_arnoldi_col<<<1, 1, 0, s>>>(j, m, h1, h2, nrm, G, hn, hp_dev);
+        k_scale<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->w.p, hn, ls->V.p + (size_t)(j + 1) * nu);
+        RS_LAUNCHED(8);
+      }
+      RS_CHECK_LAUNCH();
+      RS_CUDA(cudaStreamSynchronize(s));
+      ls->timer_flush();
+      double est = hp[0], hnv = hp[1];
+      its++;
+      jend = j + 1;
+      if (!std::isfinite(est) || !std::isfinite(hnv)) { *its_out = its; *relres = NAN; return 2; }
+      if (est <= tol * bn || its >= maxit || hnv == 0.0) break;
+    }
+    k_hsolve<<<1, 1, 0, s>>>(jend, m, G, yk);
+    if (mixed) k_xupdate<float><<<grid_for(nu, 256), 256, 0, s>>>(nu, jend, yk, ls->Z32.p, ls->y.p);
+    else k_xupdate<double><<<grid_for(nu, 256), 256, 0, s>>>(nu, jend, yk, ls->Z.p, ls->y.p);
+    RS_LAUNCHED(2);
+    {
+      rs_timed tm(ls, SIM_T_SPMV64);
+      spmv<double, double, double, double>(ls, ls->val.p, ls->y.p, ls->b.p, ls->r.p, s);
+    }
+    beta = rs_norm2(ls->r.p, nu, s);
+    ls->timer_flush();
+    if (!std::isfinite(beta)) { rc = 2; break; }
+    if (beta <= tol * bn) { rc = 0; break; }
+    if (its >= maxit) { rc = 1; break; }
+  }
+  *its_out = its;
+  *relres = beta / bn;
+  return rc;
+}

@@ -1,0 +1,368 @@
+// Restricted additive Schwarz with block ILU(0) subdomain solves: the
+// R(A)^{-1} stage of CPR-FPF (Algorithm 2, steps 1 and 5) of arXiv 1701.06254,
+// with the local potential reordering of eqs. (30)-(32) applied inside each
+// subdomain.  A subdomain is a column tile of tile_x x tile_y cells over all
+// layers (a well goes with the tile of its first perforated cell); its local
+// system is the owned rows plus their graph neighbours (overlap 1).  Each
+// subdomain maps to one thread block: the potential sort, the level sets of
+// the reordered factors, the factorisation and both triangular solves run
+// level by level inside that block.
+#include "common.cuh"
+#include <algorithm>
+#include <cfloat>
+#include <climits>
+
+// ------------------------------------------------- static partition (host)
+void ras_build_static(sim_ls_s *ls) {
+  ras_data &R = ls->ras;
+  int tx = ls->o.tile_x, ty = ls->o.tile_y;
+  int ntx = (ls->nx + tx - 1) / tx, nty = (ls->ny + ty - 1) / ty;
+  int nsub = ntx * nty, nb = ls->nb, n = ls->n;
+  R.nsub = nsub;
+  std::vector<int> owner(nb);
+  for (int c = 0; c < n; c++) {
+    int i = c % ls->nx, j = (c / ls->nx) % ls->ny;
+    owner[c] = (i / tx) + ntx * (j / ty);
+  }
+  for (int w = 0; w < ls->nw; w++) owner[n + w] = owner[ls->h_wc0[w]];
+  std::vector<std::vector<int>> own(nsub);
+  for (int r = 0; r < nb; r++) own[owner[r]].push_back(r);
+  std::vector<int> sub_ptr(nsub + 1, 0), ext, owned, ncell(nsub), lrp_ptr(nsub + 1, 0), lrlen, lrp, lci, lsrc;
+  std::vector<int> mark(nb, 0), loc(nb, -1);
+  R.max_ext = 0; R.max_nnz = 0;
+  int maxcells = 0;
+  for (int s = 0; s < nsub; s++) {
+    std::vector<int> list;
+    for (int g : own[s]) {
+      if (!mark[g]) { mark[g] = 1; list.push_back(g); }
+      for (int q = ls->h_rp[g]; q < ls->h_rp[g + 1]; q++) {
+        int c = ls->h_ci[q];
+        if (!mark[c]) { mark[c] = 1; list.push_back(c); }
+      }
+    }
+    std::sort(list.begin(), list.end());      // cells ascending, then wells ascending
+    int m = (int)list.size(), base = (int)ext.size(), nc = 0;
+    for (int a = 0; a < m; a++) {
+      int g = list[a];
+      mark[g] = 0; loc[g] = a;
+      ext.push_back(g);
+      owned.push_back(owner[g] == s);
+      nc += g < n;
+    }
+    ncell[s] = nc;
+    maxcells = std::max(maxcells, nc);
+    int nnz0 = (int)lci.size();
+    for (int a = 0; a < m; a++) {
+      int g = list[a], len = 0;
+      lrp.push_back((int)lci.size());
+      for (int q = ls->h_rp[g]; q < ls->h_rp[g + 1]; q++) {
+        int lc = loc[ls->h_ci[q]];
+        if (lc < 0) continue;
+        lci.push_back(lc); lsrc.push_back(q); len++;
+      }
+      lrlen.push_back(len);
+    }
+    for (int a = 0; a < m; a++) loc[list[a]] = -1;
+    sub_ptr[s + 1] = base + m;
+    lrp_ptr[s + 1] = (int)lci.size();
+    R.max_ext = std::max(R.max_ext, m);
+    R.max_nnz = std::max(R.max_nnz, (int)lci.size() - nnz0);
+  }
+  cudaStream_t st = ls->st;
+  h2d(R.sub_ptr, sub_ptr, st); h2d(R.ext, ext, st);
+  std::vector<uint8_t> ow(owned.begin(), owned.end());
+  h2d(R.owned, ow, st); h2d(R.ncell, ncell, st);
+  h2d(R.lrp_ptr, lrp_ptr, st); h2d(R.lrlen, lrlen, st); h2d(R.lrp, lrp, st);
+  h2d(R.lci, lci, st); h2d(R.lsrc, lsrc, st);
+  size_t next_tot = ext.size(), nnz_tot = lci.size();
+  R.perm.alloc(next_tot); R.ipos.alloc(next_tot); R.frp.alloc(next_tot + nsub);
+  R.fci.alloc(nnz_tot); R.fdiag.alloc(next_tot);
+  R.lvl.alloc(2 * next_tot); R.lvl_rows.alloc(2 * next_tot); R.nlev.alloc(2 * nsub);
+  R.lvl_ptr.alloc(2 * (next_tot + nsub));
+  if (ls->o.precision == SIM_PREC_MIXED) { R.fval32.alloc(4 * nnz_tot); R.dinv32.alloc(4 * next_tot); }
+  else { R.fval.alloc(4 * nnz_tot); R.dinv.alloc(4 * next_tot); }
+  int m = 1;
+  while (m < maxcells) m <<= 1;
+  R.max_lvl_ptr = m;   // sort width (power of two >= most cells in a subdomain)
+  if ((size_t)m * 12 > 200 * 1024) RS_FAIL(SIM_ERR_ARG, "RAS: %d cells per subdomain is too many (reduce tile_x/tile_y)", maxcells);
+  if ((size_t)R.max_ext * 16 > 200 * 1024) RS_FAIL(SIM_ERR_ARG, "RAS: subdomain too large");
+}
+
+// --------------------------------------------- potential ordering (eq. 30)
+// Sort the cells of each subdomain by descending oil potential; equal keys
+// keep ascending natural order (ext indices of cells ascend with the natural
+// index).  Wells keep their place after the cells (eq. 32).
+__global__ void k_ras_order(const int *sub_ptr, const int *ext, const int *ncell, const double *key, int reorder,
+                            int *perm, int *ipos) {
+  extern __shared__ unsigned char smem[];
+  int s = blockIdx.x, base = sub_ptr[s], m = sub_ptr[s + 1] - base, nc = ncell[s];
+  int w = 1;
+  while (w < nc) w <<= 1;
+  double *k = reinterpret_cast<double *>(smem);
+  int *id = reinterpret_cast<int *>(k + w);
+  if (reorder) {
+    for (int i = threadIdx.x; i < w; i += blockDim.x) {
+      if (i < nc) {
+        double kv = key[ext[base + i]];
+        k[i] = kv > -DBL_MAX ? kv : -DBL_MAX;   // NaN / -inf sort with the padding, before it
+        id[i] = i;
+      }
+      else { k[i] = -DBL_MAX; id[i] = INT_MAX; }
+    }
+    __syncthreads();
+    for (int kk = 2; kk <= w; kk <<= 1)
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < w; i += blockDim.x) {
+          int ixj = i ^ j;
+          if (ixj > i) {
+            // "a before b": larger key first, then smaller index
+            double ka = k[i], kb = k[ixj]; int ia = id[i], ib = id[ixj];
+            bool a_first = (ka > kb) || (ka == kb && ia < ib);
+            bool up = (i & kk) == 0;
+            if (a_first != up) { k[i] = kb; k[ixj] = ka; id[i] = ib; id[ixj] = ia; }
+          }
+        }
+        __syncthreads();
+      }
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) { perm[base + i] = id[i]; ipos[base + id[i]] = i; }
+  } else {
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) { perm[base + i] = i; ipos[base + i] = i; }
+  }
+  for (int i = nc + threadIdx.x; i < m; i += blockDim.x) { perm[base + i] = i; ipos[base + i] = i; }
+}
+
+// local pattern in position order; columns sorted by position
+__global__ void k_ras_pattern(const int *sub_ptr, const int *lrp_ptr, const int *lrp, const int *lrlen,
+                              const int *lci, const int *lsrc, const int *perm, const int *ipos, int *frp, int *fci,
+                              int *fdiag, int *fsrc) {
+  __shared__ int warp_tot[32];
+  __shared__ int carry;
+  int s = blockIdx.x, base = sub_ptr[s], m = sub_ptr[s + 1] - base, pbase = lrp_ptr[s];
+  int fbase = base + s;                   // frp segment has m + 1 entries
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < m; c0 += blockDim.x) {
+    int pos = c0 + threadIdx.x, len = pos < m ? lrlen[base + perm[base + pos]] : 0;
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, x = len;
+    for (int o = 1; o < 32; o <<= 1) { int y = __shfl_up_sync(0xffffffffu, x, o); if (lane >= o) x += y; }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int nw = blockDim.x >> 5, v = lane < nw ? warp_tot[lane] : 0, z = v;
+      for (int o = 1; o < 32; o <<= 1) { int y = __shfl_up_sync(0xffffffffu, z, o); if (lane >= o) z += y; }
+      if (lane < nw) warp_tot[lane] = z - v;
+    }
+    __syncthreads();
+    int excl = carry + warp_tot[wid] + x - len;
+    if (pos < m) frp[fbase + pos] = excl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = excl + len;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) frp[fbase + m] = carry;
+  __syncthreads();
+  for (int pos = threadIdx.x; pos < m; pos += blockDim.x) {
+    int e = perm[base + pos], src0 = lrp[base + e], len = lrlen[base + e], o = pbase + frp[fbase + pos];
+    for (int a = 0; a < len; a++) {         // insertion by position
+      int c = ipos[base + lci[src0 + a]], q = lsrc[src0 + a], b = o + a - 1;
+      while (b >= o && fci[b] > c) { fci[b + 1] = fci[b]; fsrc[b + 1] = fsrc[b]; b--; }
+      fci[b + 1] = c; fsrc[b + 1] = q;
+    }
+    for (int a = 0; a < len; a++) if (fci[o + a] == pos) fdiag[base + pos] = o + a;
+  }
+}
+
+// level sets of the L and U factors; rows of a level in ascending position
+__global__ void k_ras_levels(const int *sub_ptr, const int *lrp_ptr, const int *frp, const int *fci, int *lvl,
+                             int *lvl_rows, int *nlev, int *lvl_ptr) {
+  int s = blockIdx.x, base = sub_ptr[s], m = sub_ptr[s + 1] - base, pbase = lrp_ptr[s], fbase = base + s;
+  if (threadIdx.x != 0) return;
+  int *L = lvl + 2 * base, *U = L + m;
+  int nL = 0, nU = 0;
+  for (int i = 0; i < m; i++) {
+    int lv = 0;
+    for (int q = pbase + frp[fbase + i]; q < pbase + frp[fbase + i + 1]; q++) {
+      int c = fci[q];
+      if (c < i && L[c] + 1 > lv) lv = L[c] + 1;
+    }
+    L[i] = lv; if (lv + 1 > nL) nL = lv + 1;
+  }
+  for (int i = m - 1; i >= 0; i--) {
+    int lv = 0;
+    for (int q = pbase + frp[fbase + i]; q < pbase + frp[fbase + i + 1]; q++) {
+      int c = fci[q];
+      if (c > i && U[c] + 1 > lv) lv = U[c] + 1;
+    }
+    U[i] = lv; if (lv + 1 > nU) nU = lv + 1;
+  }
+  nlev[2 * s] = nL; nlev[2 * s + 1] = nU;
+  int *pL = lvl_ptr + 2 * (base + s), *pU = pL + (m + 1);
+  int *rL = lvl_rows + 2 * base, *rU = rL + m;
+  for (int l = 0; l <= nL; l++) pL[l] = 0;
+  for (int l = 0; l <= nU; l++) pU[l] = 0;
+  for (int i = 0; i < m; i++) { pL[L[i] + 1]++; pU[U[i] + 1]++; }
+  for (int l = 0; l < nL; l++) pL[l + 1] += pL[l];
+  for (int l = 0; l < nU; l++) pU[l + 1] += pU[l];
+  // fill: rows in ascending position within a level (counts reused as cursors)
+  for (int i = 0; i < m; i++) rL[pL[L[i]]++] = i;
+  for (int i = 0; i < m; i++) rU[pU[U[i]]++] = i;
+  for (int l = nL; l > 0; l--) pL[l] = pL[l - 1];
+  pL[0] = 0;
+  for (int l = nU; l > 0; l--) pU[l] = pU[l - 1];
+  pU[0] = 0;
+}
+
+template <class T> __device__ __forceinline__ void inv2x2(const T *M, T *I) {
+  T det = M[0] * M[3] - M[1] * M[2];
+  T r = T(1) / det;
+  I[0] = M[3] * r; I[1] = -M[1] * r; I[2] = -M[2] * r; I[3] = M[0] * r;
+}
+
+// block ILU(0), level by level (IKJ form per row): for each k < i in the
+// row, L_ik = A_ik U_kk^{-1}; A_ij -= L_ik U_kj for j > k present in row i.
+template <class T>
+__global__ void k_ras_factor(const int *sub_ptr, const int *lrp_ptr, const int *frp, const int *fci, const int *fdiag,
+                             const int *fsrc, const double *val, const int *lvl_rows, const int *nlev,
+                             const int *lvl_ptr, T *fv, T *dinv) {
+  int s = blockIdx.x, base = sub_ptr[s], m = sub_ptr[s + 1] - base, pbase = lrp_ptr[s], fbase = base + s;
+  int q0 = pbase + frp[fbase], q1 = pbase + frp[fbase + m];
+  for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {   // gather values in factor order
+    const double *src = val + 4 * (size_t)fsrc[q];
+    fv[4 * (size_t)q + 0] = (T)src[0]; fv[4 * (size_t)q + 1] = (T)src[1];
+    fv[4 * (size_t)q + 2] = (T)src[2]; fv[4 * (size_t)q + 3] = (T)src[3];
+  }
+  __syncthreads();
+  const int *pL = lvl_ptr + 2 * (base + s), *rL = lvl_rows + 2 * base;
+  int nL = nlev[2 * s];
+  for (int l = 0; l < nL; l++) {
+    for (int a = pL[l] + threadIdx.x; a < pL[l + 1]; a += blockDim.x) {
+      int i = rL[a];
+      int r0 = pbase + frp[fbase + i], r1 = pbase + frp[fbase + i + 1];
+      for (int q = r0; q < r1; q++) {
+        int k = fci[q];
+        if (k >= i) break;
+        T *Aq = fv + 4 * (size_t)q;
+        const T *Dk = dinv + 4 * (size_t)(base + k);
+        T l0 = Aq[0] * Dk[0] + Aq[1] * Dk[2], l1 = Aq[0] * Dk[1] + Aq[1] * Dk[3];
+        T l2 = Aq[2] * Dk[0] + Aq[3] * Dk[2], l3 = Aq[2] * Dk[1] + Aq[3] * Dk[3];
+        Aq[0] = l0; Aq[1] = l1; Aq[2] = l2; Aq[3] = l3;
+        int k1 = pbase + frp[fbase + k + 1];
+        int qi = q + 1;
+        for (int qk = fdiag[base + k] + 1; qk < k1; qk++) {
+          int j = fci[qk];
+          while (qi < r1 && fci[qi] < j) qi++;
+          if (qi >= r1) break;
+          if (fci[qi] != j) continue;
+          const T *U = fv + 4 * (size_t)qk;
+          T *A = fv + 4 * (size_t)qi;
+          A[0] -= l0 * U[0] + l1 * U[2]; A[1] -= l0 * U[1] + l1 * U[3];
+          A[2] -= l2 * U[0] + l3 * U[2]; A[3] -= l2 * U[1] + l3 * U[3];
+        }
+      }
+      inv2x2(fv + 4 * (size_t)fdiag[base + i], dinv + 4 * (size_t)(base + i));
+    }
+    __syncthreads();
+  }
+}
+
+void ras_setup(sim_ls_s *ls) {
+  ras_data &R = ls->ras;
+  cudaStream_t s = ls->st;
+  int w = R.max_lvl_ptr;
+  size_t smem = (size_t)w * 12;
+  static bool attr = false;
+  if (!attr) {
+    RS_CUDA(cudaFuncSetAttribute(k_ras_order, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  k_ras_order<<<R.nsub, 512, smem, s>>>(R.sub_ptr.p, R.ext.p, R.ncell.p, ls->key.p, ls->o.reorder, R.perm.p, R.ipos.p);
+  static thread_local dbuf<int> fsrc;
+  fsrc.ensure(R.lci.n);
+  k_ras_pattern<<<R.nsub, 256, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.lrp.p, R.lrlen.p, R.lci.p, R.lsrc.p, R.perm.p,
+                                       R.ipos.p, R.frp.p, R.fci.p, R.fdiag.p, fsrc.p);
+  k_ras_levels<<<R.nsub, 32, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.frp.p, R.fci.p, R.lvl.p, R.lvl_rows.p, R.nlev.p,
+                                     R.lvl_ptr.p);
+  if (ls->o.precision == SIM_PREC_MIXED)
+    k_ras_factor<float><<<R.nsub, 128, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.frp.p, R.fci.p, R.fdiag.p, fsrc.p,
+                                               ls->val.p, R.lvl_rows.p, R.nlev.p, R.lvl_ptr.p, R.fval32.p, R.dinv32.p);
+  else
+    k_ras_factor<double><<<R.nsub, 128, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.frp.p, R.fci.p, R.fdiag.p, fsrc.p,
+                                                ls->val.p, R.lvl_rows.p, R.nlev.p, R.lvl_ptr.p, R.fval.p, R.dinv.p);
+  RS_LAUNCHED(4);
+  RS_CHECK_LAUNCH();
+}
+
+// x = R(A)^{-1} f: gather the local right-hand side in position order,
+// forward solve with L (unit diagonal) level by level, backward solve with U,
+// write back the owned rows only.
+template <class T>
+__global__ void k_ras_apply(const int *sub_ptr, const int *ext, const uint8_t *owned, const int *lrp_ptr,
+                            const int *frp, const int *fci, const int *fdiag, const int *perm, const int *lvl_rows,
+                            const int *nlev, const int *lvl_ptr, const T *fv, const T *dinv, const T *f, T *x) {
+  extern __shared__ unsigned char smem_raw[];
+  T *y = reinterpret_cast<T *>(smem_raw);
+  int s = blockIdx.x, base = sub_ptr[s], m = sub_ptr[s + 1] - base, pbase = lrp_ptr[s], fbase = base + s;
+  for (int pos = threadIdx.x; pos < m; pos += blockDim.x) {
+    int g = ext[base + perm[base + pos]];
+    y[2 * pos] = f[2 * (size_t)g]; y[2 * pos + 1] = f[2 * (size_t)g + 1];
+  }
+  __syncthreads();
+  const int *pL = lvl_ptr + 2 * (base + s), *pU = pL + (m + 1);
+  const int *rL = lvl_rows + 2 * base, *rU = rL + m;
+  int nL = nlev[2 * s], nU = nlev[2 * s + 1];
+  for (int l = 1; l < nL; l++) {                 // level 0 rows have no L entries
+    for (int a = pL[l] + threadIdx.x; a < pL[l + 1]; a += blockDim.x) {
+      int i = rL[a];
+      T y0 = y[2 * i], y1 = y[2 * i + 1];
+      for (int q = pbase + frp[fbase + i]; q < fdiag[base + i]; q++) {
+        const T *B = fv + 4 * (size_t)q; int c = fci[q];
+        T c0 = y[2 * c], c1 = y[2 * c + 1];
+        y0 -= B[0] * c0 + B[1] * c1; y1 -= B[2] * c0 + B[3] * c1;
+      }
+      y[2 * i] = y0; y[2 * i + 1] = y1;
+    }
+    __syncthreads();
+  }
+  for (int l = 0; l < nU; l++) {
+    for (int a = pU[l] + threadIdx.x; a < pU[l + 1]; a += blockDim.x) {
+      int i = rU[a];
+      T y0 = y[2 * i], y1 = y[2 * i + 1];
+      int r1 = pbase + frp[fbase + i + 1];
+      for (int q = fdiag[base + i] + 1; q < r1; q++) {
+        const T *B = fv + 4 * (size_t)q; int c = fci[q];
+        T c0 = y[2 * c], c1 = y[2 * c + 1];
+        y0 -= B[0] * c0 + B[1] * c1; y1 -= B[2] * c0 + B[3] * c1;
+      }
+      const T *D = dinv + 4 * (size_t)(base + i);
+      y[2 * i] = D[0] * y0 + D[1] * y1; y[2 * i + 1] = D[2] * y0 + D[3] * y1;
+    }
+    __syncthreads();
+  }
+  for (int pos = threadIdx.x; pos < m; pos += blockDim.x) {
+    int e = perm[base + pos];
+    if (owned[base + e]) {
+      int g = ext[base + e];
+      x[2 * (size_t)g] = y[2 * pos]; x[2 * (size_t)g + 1] = y[2 * pos + 1];
+    }
+  }
+}
+
+template <class T> void ls_ras_apply(sim_ls_s *ls, const T *f, T *x) {
+  ras_data &R = ls->ras;
+  size_t smem = (size_t)R.max_ext * 2 * sizeof(T);
+  static bool attr = false;
+  if (!attr) {
+    RS_CUDA(cudaFuncSetAttribute(k_ras_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    RS_CUDA(cudaFuncSetAttribute(k_ras_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  bool mixed = sizeof(T) == 4;
+  rs_timed tm(ls, SIM_T_RAS);
+  k_ras_apply<T><<<R.nsub, 256, smem, ls->st>>>(R.sub_ptr.p, R.ext.p, R.owned.p, R.lrp_ptr.p, R.frp.p, R.fci.p,
+                                                R.fdiag.p, R.perm.p, R.lvl_rows.p, R.nlev.p, R.lvl_ptr.p,
+                                                mixed ? (const T *)R.fval32.p : (const T *)R.fval.p,
+                                                mixed ? (const T *)R.dinv32.p : (const T *)R.dinv.p, f, x);
+  RS_LAUNCHED(1);
+}
+template void ls_ras_apply<double>(sim_ls_s *, const double *, double *);
+template void ls_ras_apply<float>(sim_ls_s *, const float *, float *);

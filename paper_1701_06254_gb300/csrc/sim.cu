@@ -1,0 +1,904 @@
+// The fully implicit oil-water model on the GPU and the C ABI.
+//
+// Model (arXiv 1701.06254, Sec. "Two-phase oil-water flow model"): mass
+// balance eq. (3) with porosity eq. (4), potential eq. (5) (z = depth),
+// density eq. (6), viscosity eq. (7), s_o = 1 - s_w eq. (8), Corey relative
+// permeabilities, Peaceman wells eq. (10) with BHP eq. (11) and water-rate
+// eq. (12) constraints.  Discretisation (Sec. "Numerical methods"): backward
+// Euler eq. (15), two-point fluxes with the geometric transmissibility times
+// the upstream mobility (eqs. 16-18; upstream cell of face (c, d), c < d:
+// c if Phi_c >= Phi_d, else d), residual eq. (17).  Newton: Algorithm 1,
+// forcing term eq. (26) second choice, clamped to [0.01, 0.1].
+#include "common.cuh"
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+
+struct fluid_c {
+  double rho_ref[2], c_f[2], mu_ref[2], c_mu[2];
+  double p_ref, c_r, swc, sor, nw, no, krw_max, kro_max, g;
+};
+
+struct sim_s {
+  int nx, ny, nz, n, nw, np_;
+  double dx, dy, dz, top;
+  fluid_c fl;
+  rs_opts o;
+  cudaStream_t st;
+  std::vector<int> wkind, wctrl, pptr;
+  std::vector<double> wtarget, wzref;
+  dbuf<double> kx, ky, kz, phi, tx, ty, tz;
+  dbuf<int> pcell, pwell, ppos_cw, ppos_wc, cpp, cpi, wpptr, wdiag, wkind_d, wctrl_d;
+  dbuf<double> pwi, wtarget_d, wzref_d;
+  dbuf<double> p, s, pb, acc0, props, p0, s0, pb0, red;
+  double t = 0.0, dt = 1.0;
+  sim_ls_s *ls = nullptr;
+  sim_stats stats;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ~sim_s() { delete ls; if (e0) cudaEventDestroy(e0); if (e1) cudaEventDestroy(e1); }
+};
+
+// ----------------------------------------------------------- properties --
+struct cprops { double phi, dphi, rho[2], drho[2], mu[2], dmu[2], kr[2], dkr[2], m[2], dmp[2], dms[2], pot[2], dpot[2]; };
+
+__device__ __forceinline__ double corey(double x, double e) {
+  if (e == 2.0) return x * x;
+  if (e == 1.0) return x;
+  if (e == 3.0) return x * x * x;
+  return pow(x, e);
+}
+
+__device__ __forceinline__ void cell_props(const fluid_c &f, double phir, double z, double p, double sw, cprops &P) {
+  double dp = p - f.p_ref;
+  P.phi = phir * (1.0 + f.c_r * dp);
+  P.dphi = phir * f.c_r;
+  double span = 1.0 - f.swc - f.sor;
+  double sh = (sw - f.swc) / span, dsh = 1.0 / span;
+  if (sh < 0.0) { sh = 0.0; dsh = 0.0; } else if (sh > 1.0) { sh = 1.0; dsh = 0.0; }
+  P.kr[0] = f.krw_max * corey(sh, f.nw);
+  P.dkr[0] = f.krw_max * f.nw * corey(sh, f.nw - 1.0) * dsh;
+  P.kr[1] = f.kro_max * corey(1.0 - sh, f.no);
+  P.dkr[1] = -f.kro_max * f.no * corey(1.0 - sh, f.no - 1.0) * dsh;
+  double gz5 = f.g * z * RS_PA2BAR;
+#pragma unroll
+  for (int a = 0; a < 2; a++) {
+    P.rho[a] = f.rho_ref[a] * (1.0 + f.c_f[a] * dp);
+    P.drho[a] = f.rho_ref[a] * f.c_f[a];
+    P.mu[a] = f.mu_ref[a] + f.c_mu[a] * dp;
+    P.dmu[a] = f.c_mu[a];
+    double imu = 1.0 / P.mu[a];
+    P.m[a] = P.rho[a] * P.kr[a] * imu;
+    P.dmp[a] = P.drho[a] * P.kr[a] * imu - P.rho[a] * P.kr[a] * P.dmu[a] * imu * imu;
+    P.dms[a] = P.rho[a] * P.dkr[a] * imu;
+    P.pot[a] = p - P.rho[a] * gz5;
+    P.dpot[a] = 1.0 - P.drho[a] * gz5;
+  }
+}
+
+__device__ __forceinline__ double depth(double top, double dz, int k) { return add_rn(top, mul_rn((double)k + 0.5, dz)); }
+
+// per-cell mobility / potential table for the face terms: 10 x n (SoA)
+__global__ void k_props(int n, int nxy, fluid_c f, double top, double dz, const double *phi, const double *p,
+                        const double *s, double *pr) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  cprops P;
+  cell_props(f, phi[c], depth(top, dz, c / nxy), p[c], s[c], P);
+  pr[0 * (size_t)n + c] = P.m[0]; pr[1 * (size_t)n + c] = P.m[1];
+  pr[2 * (size_t)n + c] = P.dmp[0]; pr[3 * (size_t)n + c] = P.dmp[1];
+  pr[4 * (size_t)n + c] = P.dms[0]; pr[5 * (size_t)n + c] = P.dms[1];
+  pr[6 * (size_t)n + c] = P.pot[0]; pr[7 * (size_t)n + c] = P.pot[1];
+  pr[8 * (size_t)n + c] = P.dpot[0]; pr[9 * (size_t)n + c] = P.dpot[1];
+}
+
+// geometric two-point transmissibility of the +x, +y, +z face of each cell
+__global__ void k_trans(int nx, int ny, int nz, double dx, double dy, double dz, const double *kx, const double *ky,
+                        const double *kz, double *tx, double *ty, double *tz) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x, n = nx * ny * nz;
+  if (c >= n) return;
+  int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+  tx[c] = i + 1 < nx ? RS_CDARCY * (dy * dz) / (dx / (2.0 * kx[c]) + dx / (2.0 * kx[c + 1])) : 0.0;
+  ty[c] = j + 1 < ny ? RS_CDARCY * (dx * dz) / (dy / (2.0 * ky[c]) + dy / (2.0 * ky[c + nx])) : 0.0;
+  tz[c] = k + 1 < nz ? RS_CDARCY * (dx * dy) / (dz / (2.0 * kz[c]) + dz / (2.0 * kz[c + nx * ny])) : 0.0;
+}
+
+// Peaceman well index per perforation
+__global__ void k_peaceman(int np_, double dx, double dy, double dz, const int *pcell, const int *pwell,
+                           const double *rw, const double *skin, const double *kx, const double *ky, double *wi) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= np_) return;
+  if (wi[q] >= 0.0) return;                 // given by the caller
+  int c = pcell[q], w = pwell[q];
+  double a = kx[c], b = ky[c];
+  double ro = 0.28 * sqrt(sqrt(b / a) * dx * dx + sqrt(a / b) * dy * dy) / (pow(b / a, 0.25) + pow(a / b, 0.25));
+  wi[q] = 2.0 * M_PI * RS_CDARCY * sqrt(a * b) * dz / (log(ro / rw[w]) + skin[w]);
+}
+
+// --------------------------------------------------------------- assembly --
+// One thread per cell: accumulation, the six faces (evaluated from this
+// cell's side; the neighbour evaluates the same face with the same
+// transmissibility and upstream choice, so the two fluxes are exact
+// negatives), and the cell's perforations.  Writes the whole block row.
+__global__ void __launch_bounds__(128)
+k_assemble(int nx, int ny, int nz, fluid_c f, double top, double dz, double vol_dt, const double *__restrict__ phi,
+           const double *__restrict__ p, const double *__restrict__ s, const double *__restrict__ pbh,
+           const double *__restrict__ acc0, const double *__restrict__ pr, const double *__restrict__ tx,
+           const double *__restrict__ ty, const double *__restrict__ tz, const int *__restrict__ rp,
+           const int *__restrict__ cpp, const int *__restrict__ cpi, const int *__restrict__ pwell,
+           const double *__restrict__ pwi, const int *__restrict__ ppos_cw, const int *__restrict__ wkind,
+           const double *__restrict__ wzref, double *__restrict__ val, double *__restrict__ b) {
+  int n = nx * ny * nz, c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  int nxy = nx * ny, i = c % nx, j = (c / nx) % ny, k = c / nxy;
+  double z = depth(top, dz, k);
+  cprops P;
+  double pc = p[c], sc = s[c];
+  cell_props(f, phi[c], z, pc, sc, P);
+  double so = 1.0 - sc;
+  double R0 = vol_dt * (P.phi * P.rho[1] * so - acc0[2 * (size_t)c]);
+  double R1 = vol_dt * (P.phi * P.rho[0] * sc - acc0[2 * (size_t)c + 1]);
+  double D[4];
+  D[0] = vol_dt * (P.dphi * P.rho[1] + P.phi * P.drho[1]) * so;
+  D[1] = vol_dt * (-P.phi * P.rho[1]);
+  D[2] = vol_dt * (P.dphi * P.rho[0] + P.phi * P.drho[0]) * sc;
+  D[3] = vol_dt * (P.phi * P.rho[0]);
+  // neighbours in ascending column order: -z, -y, -x, (self), +x, +y, +z
+  int nb_[6] = {k > 0 ? c - nxy : -1, j > 0 ? c - nx : -1, i > 0 ? c - 1 : -1,
+                i + 1 < nx ? c + 1 : -1, j + 1 < ny ? c + nx : -1, k + 1 < nz ? c + nxy : -1};
+  double T_[6] = {k > 0 ? tz[c - nxy] : 0.0, j > 0 ? ty[c - nx] : 0.0, i > 0 ? tx[c - 1] : 0.0, tx[c], ty[c], tz[c]};
+  int slot = rp[c], diag_slot = -1;
+  for (int t = 0; t < 6; t++) {
+    if (t == 3) diag_slot = slot++;
+    int d = nb_[t];
+    if (d < 0) continue;
+    double T = T_[t];
+    double O[4];
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+      int e = 1 - a;
+      double md = pr[(size_t)a * n + d], dmpd = pr[(size_t)(2 + a) * n + d], dmsd = pr[(size_t)(4 + a) * n + d];
+      double potd = pr[(size_t)(6 + a) * n + d], dpotd = pr[(size_t)(8 + a) * n + d];
+      double mc = pr[(size_t)a * n + c], dmpc = pr[(size_t)(2 + a) * n + c], dmsc = pr[(size_t)(4 + a) * n + c];
+      double potc = pr[(size_t)(6 + a) * n + c], dpotc = pr[(size_t)(8 + a) * n + c];
+      bool upc = (c < d) ? (potc >= potd) : !(potd >= potc);
+      double dpot = potd - potc;
+      double Tm = T * (upc ? mc : md);
+      double F = Tm * dpot;
+      double dFdpc = T * ((upc ? dmpc : 0.0) * dpot) - Tm * dpotc;
+      double dFdsc = T * ((upc ? dmsc : 0.0) * dpot);
+      double dFdpd = T * ((upc ? 0.0 : dmpd) * dpot) + Tm * dpotd;
+      double dFdsd = T * ((upc ? 0.0 : dmsd) * dpot);
+      if (e == 0) R0 -= F; else R1 -= F;
+      D[2 * e] -= dFdpc; D[2 * e + 1] -= dFdsc;
+      O[2 * e] = -dFdpd; O[2 * e + 1] = -dFdsd;
+    }
+    double *Bo = val + 4 * (size_t)slot++;
+    reinterpret_cast<double2 *>(Bo)[0] = make_double2(O[0], O[1]);
+    reinterpret_cast<double2 *>(Bo)[1] = make_double2(O[2], O[3]);
+  }
+  // perforations of this cell (eq. 10): producer per phase, outflow only;
+  // injector water only with the total mobility
+  for (int a2 = cpp[c]; a2 < cpp[c + 1]; a2++) {
+    int q = cpi[a2], w = pwell[q];
+    double wi = pwi[q];
+    double dz5 = f.g * (z - wzref[w]) * RS_PA2BAR;
+    double W[4] = {0, 0, 0, 0};
+    for (int a = 0; a < 2; a++) {
+      int e = 1 - a;
+      double dd = (pbh[w] - pc) + P.rho[a] * dz5, dd_dp = -1.0 + P.drho[a] * dz5;
+      double q_ = 0, dqdp = 0, dqds = 0, dqdb = 0;
+      if (wkind[w] == SIM_PROD) {
+        if (dd <= 0.0) {
+          q_ = wi * P.m[a] * dd; dqdp = wi * (P.dmp[a] * dd + P.m[a] * dd_dp);
+          dqds = wi * P.dms[a] * dd; dqdb = wi * P.m[a];
+        }
+      } else if (a == 0) {
+        double lt = P.kr[0] / P.mu[0] + P.kr[1] / P.mu[1];
+        double lt_p = -P.kr[0] * P.dmu[0] / (P.mu[0] * P.mu[0]) - P.kr[1] * P.dmu[1] / (P.mu[1] * P.mu[1]);
+        double lt_s = P.dkr[0] / P.mu[0] + P.dkr[1] / P.mu[1];
+        q_ = wi * P.rho[0] * lt * dd;
+        dqdp = wi * (P.drho[0] * lt * dd + P.rho[0] * lt_p * dd + P.rho[0] * lt * dd_dp);
+        dqds = wi * P.rho[0] * lt_s * dd; dqdb = wi * P.rho[0] * lt;
+      }
+      if (e == 0) R0 -= q_; else R1 -= q_;
+      D[2 * e] -= dqdp; D[2 * e + 1] -= dqds;
+      W[2 * e] = -dqdb;
+    }
+    double *Bw = val + 4 * (size_t)ppos_cw[q];
+    Bw[0] = W[0]; Bw[1] = 0.0; Bw[2] = W[2]; Bw[3] = 0.0;
+  }
+  double *Bd = val + 4 * (size_t)diag_slot;
+  reinterpret_cast<double2 *>(Bd)[0] = make_double2(D[0], D[1]);
+  reinterpret_cast<double2 *>(Bd)[1] = make_double2(D[2], D[3]);
+  reinterpret_cast<double2 *>(b)[c] = make_double2(-R0, -R1);
+}
+
+// well rows: eq. (11) scaled by the target, or eq. (12) scaled by the target
+// mass rate; one thread per well, perforations in order
+__global__ void k_wells(int n, int nw, fluid_c f, double top, double dz, int nxy, const double *phi, const double *p,
+                        const double *s, const double *pbh, const int *wpptr, const int *pcell, const double *pwi,
+                        const int *ppos_wc, const int *wdiag, const int *wkind, const int *wctrl, const double *wtarget,
+                        const double *wzref, double *val, double *b) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nw) return;
+  double R = 0.0, Jww = 0.0;
+  bool rate = wctrl[w] == SIM_WRATE;
+  double scale = rate ? 1.0 / (f.rho_ref[0] * wtarget[w]) : 0.0;
+  for (int q = wpptr[w]; q < wpptr[w + 1]; q++) {
+    int c = pcell[q];
+    double *B = val + 4 * (size_t)ppos_wc[q];
+    double b0 = 0, b1 = 0;
+    if (rate) {
+      cprops P;
+      double z = depth(top, dz, c / nxy);
+      cell_props(f, phi[c], z, p[c], s[c], P);
+      double dz5 = f.g * (z - wzref[w]) * RS_PA2BAR;
+      double dd = (pbh[w] - p[c]) + P.rho[0] * dz5, dd_dp = -1.0 + P.drho[0] * dz5;
+      double q_ = 0, dqdp = 0, dqds = 0, dqdb = 0;
+      if (wkind[w] == SIM_PROD) {
+        if (dd <= 0.0) { q_ = pwi[q] * P.m[0] * dd; dqdp = pwi[q] * (P.dmp[0] * dd + P.m[0] * dd_dp);
+                         dqds = pwi[q] * P.dms[0] * dd; dqdb = pwi[q] * P.m[0]; }
+      } else {
+        double lt = P.kr[0] / P.mu[0] + P.kr[1] / P.mu[1];
+        double lt_p = -P.kr[0] * P.dmu[0] / (P.mu[0] * P.mu[0]) - P.kr[1] * P.dmu[1] / (P.mu[1] * P.mu[1]);
+        double lt_s = P.dkr[0] / P.mu[0] + P.dkr[1] / P.mu[1];
+        double wi = pwi[q];
+        q_ = wi * P.rho[0] * lt * dd;
+        dqdp = wi * (P.drho[0] * lt * dd + P.rho[0] * lt_p * dd + P.rho[0] * lt * dd_dp);
+        dqds = wi * P.rho[0] * lt_s * dd; dqdb = wi * P.rho[0] * lt;
+      }
+      R += scale * q_; b0 = scale * dqdp; b1 = scale * dqds; Jww += scale * dqdb;
+    }
+    B[0] = b0; B[1] = b1; B[2] = 0.0; B[3] = 0.0;
+  }
+  if (rate) R -= 1.0;
+  else { R = (pbh[w] - wtarget[w]) / wtarget[w]; Jww = 1.0 / wtarget[w]; }
+  double *Bd = val + 4 * (size_t)wdiag[w];
+  Bd[0] = Jww; Bd[1] = 0.0; Bd[2] = 0.0; Bd[3] = 1.0;
+  b[2 * (size_t)(n + w)] = -R; b[2 * (size_t)(n + w) + 1] = 0.0;
+}
+
+// reordering key: oil potential, eq. (5), evaluated in a fixed IEEE order
+__global__ void k_key(int n, int nxy, fluid_c f, double top, double dz, const double *p, double *key) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  double z = depth(top, dz, c / nxy);
+  double gz5 = mul_rn(mul_rn(f.g, z), RS_PA2BAR);
+  double rho = mul_rn(f.rho_ref[1], add_rn(1.0, mul_rn(f.c_f[1], sub_rn(p[c], f.p_ref))));
+  key[c] = sub_rn(p[c], mul_rn(rho, gz5));
+}
+
+// scaled residual norm (max), one partial per block, then a max in order
+__global__ void k_norm_part(int n, int nw, double dt_vol_inv, const fluid_c f, const double *phi, const double *b,
+                            double *part) {
+  __shared__ double sh[256];
+  double mx = 0.0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n + nw; c += gridDim.x * blockDim.x) {
+    double r0, r1;
+    if (c < n) {
+      r0 = fabs(b[2 * (size_t)c]) * dt_vol_inv / (f.rho_ref[1] * phi[c]);
+      r1 = fabs(b[2 * (size_t)c + 1]) * dt_vol_inv / (f.rho_ref[0] * phi[c]);
+    } else { r0 = fabs(b[2 * (size_t)c]); r1 = 0.0; }
+    if (!(r0 <= mx)) mx = r0;
+    if (!(r1 <= mx)) mx = r1;
+  }
+  sh[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) { double x = sh[threadIdx.x + o]; if (!(x <= sh[threadIdx.x])) sh[threadIdx.x] = x; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+__global__ void k_max_part(int m, const double *part, double *out) {
+  double mx = 0.0;
+  for (int k = 0; k < m; k++) { double x = part[k]; if (!(x <= mx)) mx = x; }
+  *out = mx;
+}
+
+__global__ void k_update(int n, int nw, const double *y, double *p, double *s, double *pb) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n) {
+    p[c] += y[2 * (size_t)c];
+    double v = s[c] + y[2 * (size_t)c + 1];
+    s[c] = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+  } else if (c < n + nw) {
+    pb[c - n] += y[2 * (size_t)c];
+  }
+}
+
+__global__ void k_store_old(int n, int nxy, fluid_c f, double top, double dz, const double *phi, const double *p,
+                            const double *s, double *acc0) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  cprops P;
+  cell_props(f, phi[c], depth(top, dz, c / nxy), p[c], s[c], P);
+  acc0[2 * (size_t)c] = P.phi * P.rho[1] * (1.0 - s[c]);
+  acc0[2 * (size_t)c + 1] = P.phi * P.rho[0] * s[c];
+}
+
+__global__ void k_hydrostatic(int n, int nxy, fluid_c f, double top, double dz, double p_datum, double sw0, double *p,
+                              double *s) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  double G0 = f.g * top * RS_PA2BAR;
+  double rho0 = f.rho_ref[1] * (1.0 + f.c_f[1] * (p_datum - f.p_ref));
+  double pot = p_datum - rho0 * G0;
+  double G = f.g * depth(top, dz, c / nxy) * RS_PA2BAR;
+  double a = 1.0 - f.rho_ref[1] * f.c_f[1] * G;
+  double r = pot + f.rho_ref[1] * (1.0 - f.c_f[1] * f.p_ref) * G;
+  p[c] = r / a;
+  s[c] = sw0;
+}
+__global__ void k_init_pb(int nw, const int *wctrl, const double *wtarget, const int *wpptr, const int *pcell,
+                          const double *p, double *pb) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nw) return;
+  pb[w] = wctrl[w] == SIM_BHP ? wtarget[w] : p[pcell[wpptr[w]]] + 10.0;
+}
+
+// ------------------------------------------------------------- host side --
+static void s_props_assemble(sim_s *h) {
+  cudaStream_t s = h->st;
+  int n = h->n, nxy = h->nx * h->ny;
+  sim_ls_s *ls = h->ls;
+  rs_timed tm(ls, SIM_T_ASSEMBLE);
+  k_props<<<grid_for(n, 256), 256, 0, s>>>(n, nxy, h->fl, h->top, h->dz, h->phi.p, h->p.p, h->s.p, h->props.p);
+  k_assemble<<<grid_for(n, 128), 128, 0, s>>>(h->nx, h->ny, h->nz, h->fl, h->top, h->dz, h->dx * h->dy * h->dz / h->dt,
+                                              h->phi.p, h->p.p, h->s.p, h->pb.p, h->acc0.p, h->props.p, h->tx.p,
+                                              h->ty.p, h->tz.p, ls->rp.p, h->cpp.p, h->cpi.p, h->pwell.p, h->pwi.p,
+                                              h->ppos_cw.p, h->wkind_d.p, h->wzref_d.p, ls->val.p, ls->b.p);
+  RS_LAUNCHED(2);
+  if (h->nw) {
+    k_wells<<<grid_for(h->nw, 32), 32, 0, s>>>(n, h->nw, h->fl, h->top, h->dz, nxy, h->phi.p, h->p.p, h->s.p, h->pb.p,
+                                               h->wpptr.p, h->pcell.p, h->pwi.p, h->ppos_wc.p, h->wdiag.p, h->wkind_d.p,
+                                               h->wctrl_d.p, h->wtarget_d.p, h->wzref_d.p, ls->val.p, ls->b.p);
+    RS_LAUNCHED(1);
+  }
+  k_key<<<grid_for(n, 256), 256, 0, s>>>(n, nxy, h->fl, h->top, h->dz, h->p.p, ls->key.p);
+  RS_LAUNCHED(1);
+  RS_CHECK_LAUNCH();
+  ls->have_setup = false;
+}
+
+static double s_norm(sim_s *h) {
+  cudaStream_t s = h->st;
+  int nb = 120;
+  h->red.ensure(nb + 1);
+  double dvi = h->dt / (h->dx * h->dy * h->dz);
+  k_norm_part<<<nb, 256, 0, s>>>(h->n, h->nw, dvi, h->fl, h->phi.p, h->ls->b.p, h->red.p);
+  k_max_part<<<1, 1, 0, s>>>(nb, h->red.p, h->red.p + nb);
+  RS_LAUNCHED(2);
+  return d2h(h->red.p + nb, 1, s)[0];
+}
+
+static double s_forcing(int l, double bn, double rprev, double bprev) {
+  if (l == 0) return 0.1;
+  double eta = (bn - rprev) / bprev;
+  return eta < 0.01 ? 0.01 : (eta > 0.1 ? 0.1 : eta);
+}
+
+static float ev_ms(sim_s *h) {
+  float ms = 0;
+  RS_CUDA(cudaEventRecord(h->e1, h->st));
+  RS_CUDA(cudaEventSynchronize(h->e1));
+  RS_CUDA(cudaEventElapsedTime(&ms, h->e0, h->e1));
+  return ms;
+}
+
+// Algorithm 1 for one time step at h->dt.  0 = converged, 1 = iteration cap,
+// 2 = non-finite value.
+static int s_newton(sim_s *h, int *iters) {
+  RS_CUDA(cudaEventRecord(h->e0, h->st));
+  s_props_assemble(h);
+  double nr = s_norm(h);
+  h->stats.ms_assemble += ev_ms(h);
+  double bprev = 0, rprev = 0;
+  for (int l = 0;; l++) {
+    h->stats.last_norm = nr;
+    if (!std::isfinite(nr)) { *iters = l; return 2; }
+    if (nr <= h->o.newton_tol) { *iters = l; return 0; }
+    if (l >= h->o.max_newton) { *iters = l; return 1; }
+    RS_CUDA(cudaEventRecord(h->e0, h->st));
+    ls_setup(h->ls);
+    int nu = 2 * h->ls->nb;
+    double bn = rs_norm2(h->ls->b.p, nu, h->st);
+    h->stats.ms_setup += ev_ms(h);
+    double eta = h->o.newton == SIM_NEWTON_INEXACT ? s_forcing(l, bn, rprev, bprev) : h->o.lin_tol;
+    int its; double rel;
+    RS_CUDA(cudaEventRecord(h->e0, h->st));
+    int rc = ls_solve(h->ls, eta, &its, &rel);
+    h->stats.ms_solve += ev_ms(h);
+    h->stats.linear_its += its; h->stats.linear_solves++;
+    h->stats.last_its = its; h->stats.last_relres = rel;
+    if (rc == 2) { *iters = l; return 2; }
+    bprev = bn; rprev = rel * bn;
+    k_update<<<grid_for(h->n + h->nw, 256), 256, 0, h->st>>>(h->n, h->nw, h->ls->y.p, h->p.p, h->s.p, h->pb.p);
+    RS_LAUNCHED(1);
+    h->stats.newton++;
+    RS_CUDA(cudaEventRecord(h->e0, h->st));
+    s_props_assemble(h);
+    nr = s_norm(h);
+    h->stats.ms_assemble += ev_ms(h);
+  }
+}
+
+static void s_store_old(sim_s *h) {
+  k_store_old<<<grid_for(h->n, 256), 256, 0, h->st>>>(h->n, h->nx * h->ny, h->fl, h->top, h->dz, h->phi.p, h->p.p,
+                                                      h->s.p, h->acc0.p);
+  RS_LAUNCHED(1);
+}
+
+// ------------------------------------------------------------------ ABI ---
+#define ABI_BEGIN try {
+#define ABI_END                                                       \
+  }                                                                   \
+  catch (const rs_error &e) { return e.code; }                        \
+  catch (const std::bad_alloc &) { rs_set_error("host allocation failed"); return SIM_ERR_OOM; } \
+  catch (...) { rs_set_error("unexpected exception"); return SIM_ERR_CUDA; }                       \
+  return SIM_OK;
+
+static void copy_in(dbuf<double> &d, const double *src, size_t m, cudaStream_t s) {
+  d.alloc(m);
+  if (m) RS_CUDA(cudaMemcpyAsync(d.p, src, m * sizeof(double), cudaMemcpyDefault, s));
+}
+
+extern "C" sim_status sim_create(sim_t *out, const sim_grid *g, const sim_rock *r, const sim_fluid *f,
+                                 const sim_well *wells, int n_wells, const sim_options *o) {
+  ABI_BEGIN
+  if (!out || !g || !r || !f || !o || (n_wells > 0 && !wells) || n_wells < 0) RS_FAIL(SIM_ERR_ARG, "sim_create: NULL argument");
+  *out = nullptr;
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1 || !(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0))
+    RS_FAIL(SIM_ERR_ARG, "sim_create: bad grid");
+  if ((long long)g->nx * g->ny * g->nz > 400000000LL) RS_FAIL(SIM_ERR_ARG, "sim_create: grid too large");
+  if (!r->kx || !r->ky || !r->kz || !r->phi) RS_FAIL(SIM_ERR_ARG, "sim_create: NULL rock array");
+  sim_s *h = new sim_s();
+  std::unique_ptr<sim_s> guard(h);
+  h->nx = g->nx; h->ny = g->ny; h->nz = g->nz; h->n = g->nx * g->ny * g->nz; h->nw = n_wells;
+  h->dx = g->dx; h->dy = g->dy; h->dz = g->dz; h->top = g->top_depth;
+  memcpy(&h->fl, f, sizeof(fluid_c));
+  h->o = rs_opts_from(o);
+  h->st = (cudaStream_t)o->cuda_stream;
+  h->dt = h->o.dt;
+  memset(&h->stats, 0, sizeof(h->stats));
+  int n = h->n, nw = n_wells;
+  cudaStream_t s = h->st;
+  copy_in(h->kx, r->kx, n, s); copy_in(h->ky, r->ky, n, s); copy_in(h->kz, r->kz, n, s); copy_in(h->phi, r->phi, n, s);
+  // wells, perforations and the block pattern
+  h->pptr.assign(nw + 1, 0);
+  std::vector<int> pcell, pwell;
+  std::vector<double> pwi, rw(nw), skin(nw);
+  std::vector<std::vector<int>> cellwells(n);
+  for (int w = 0; w < nw; w++) {
+    const sim_well &W = wells[w];
+    if (W.kind != SIM_INJ && W.kind != SIM_PROD) RS_FAIL(SIM_ERR_ARG, "well %d: bad kind", w);
+    if (W.control == SIM_WRATE && W.kind != SIM_INJ) RS_FAIL(SIM_ERR_ARG, "well %d: water-rate control needs an injector", w);
+    if (W.control != SIM_BHP && W.control != SIM_WRATE) RS_FAIL(SIM_ERR_ARG, "well %d: control not supported", w);
+    if (W.n_perf < 1 || !W.perf_cell) RS_FAIL(SIM_ERR_ARG, "well %d: no perforations", w);
+    if (!(W.target > 0)) RS_FAIL(SIM_ERR_ARG, "well %d: target must be positive", w);
+    h->wkind.push_back(W.kind); h->wctrl.push_back(W.control);
+    h->wtarget.push_back(W.target); h->wzref.push_back(W.z_ref);
+    rw[w] = W.r_w; skin[w] = W.skin;
+    for (int q = 0; q < W.n_perf; q++) {
+      int c = W.perf_cell[q];
+      if (c < 0 || c >= n) RS_FAIL(SIM_ERR_ARG, "well %d: perforation outside the grid", w);
+      for (int w2 : cellwells[c]) if (w2 == w) RS_FAIL(SIM_ERR_ARG, "well %d perforates cell %d twice", w, c);
+      cellwells[c].push_back(w);
+      pcell.push_back(c); pwell.push_back(w);
+      pwi.push_back(W.wi ? W.wi[q] : -1.0);
+    }
+    h->pptr[w + 1] = (int)pcell.size();
+  }
+  h->np_ = (int)pcell.size();
+  int nb = n + nw, nx = h->nx, ny = h->ny, nz = h->nz, nxy = nx * ny;
+  std::vector<int> rp(nb + 1, 0), ci;
+  ci.reserve((size_t)7 * n + 2 * h->np_ + nw);
+  for (int c = 0; c < n; c++) {
+    int i = c % nx, j = (c / nx) % ny, k = c / nxy;
+    if (k > 0) ci.push_back(c - nxy);
+    if (j > 0) ci.push_back(c - nx);
+    if (i > 0) ci.push_back(c - 1);
+    ci.push_back(c);
+    if (i + 1 < nx) ci.push_back(c + 1);
+    if (j + 1 < ny) ci.push_back(c + nx);
+    if (k + 1 < nz) ci.push_back(c + nxy);
+    std::vector<int> ws = cellwells[c];
+    std::sort(ws.begin(), ws.end());
+    for (int w : ws) ci.push_back(n + w);
+    rp[c + 1] = (int)ci.size();
+  }
+  for (int w = 0; w < nw; w++) {
+    std::vector<int> cs(pcell.begin() + h->pptr[w], pcell.begin() + h->pptr[w + 1]);
+    std::sort(cs.begin(), cs.end());
+    for (int c : cs) ci.push_back(c);
+    ci.push_back(n + w);
+    rp[n + w + 1] = (int)ci.size();
+  }
+  auto find = [&](int row, int col) {
+    for (int q = rp[row]; q < rp[row + 1]; q++) if (ci[q] == col) return q;
+    return -1;
+  };
+  std::vector<int> ppos_cw(h->np_), ppos_wc(h->np_), wdiag(nw), cpp(n + 1, 0), cpi(h->np_), wc0(nw);
+  for (int q = 0; q < h->np_; q++) {
+    ppos_cw[q] = find(pcell[q], n + pwell[q]);
+    ppos_wc[q] = find(n + pwell[q], pcell[q]);
+    cpp[pcell[q] + 1]++;
+  }
+  for (int c = 0; c < n; c++) cpp[c + 1] += cpp[c];
+  {
+    std::vector<int> fill(n, 0);
+    for (int q = 0; q < h->np_; q++) cpi[cpp[pcell[q]] + fill[pcell[q]]++] = q;
+  }
+  for (int w = 0; w < nw; w++) { wdiag[w] = find(n + w, n + w); wc0[w] = pcell[h->pptr[w]]; }
+  h2d(h->pcell, pcell, s); h2d(h->pwell, pwell, s); h2d(h->pwi, pwi, s);
+  h2d(h->ppos_cw, ppos_cw, s); h2d(h->ppos_wc, ppos_wc, s); h2d(h->cpp, cpp, s); h2d(h->cpi, cpi, s);
+  h2d(h->wpptr, h->pptr, s); h2d(h->wdiag, wdiag, s);
+  h2d(h->wkind_d, h->wkind, s); h2d(h->wctrl_d, h->wctrl, s); h2d(h->wtarget_d, h->wtarget, s); h2d(h->wzref_d, h->wzref, s);
+  dbuf<double> rw_d, skin_d;
+  h2d(rw_d, rw, s); h2d(skin_d, skin, s);
+  h->tx.alloc(n); h->ty.alloc(n); h->tz.alloc(n);
+  k_trans<<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, h->dx, h->dy, h->dz, h->kx.p, h->ky.p, h->kz.p, h->tx.p, h->ty.p, h->tz.p);
+  RS_LAUNCHED(1);
+  if (h->np_) {
+    k_peaceman<<<grid_for(h->np_, 128), 128, 0, s>>>(h->np_, h->dx, h->dy, h->dz, h->pcell.p, h->pwell.p, rw_d.p, skin_d.p,
+                                                     h->kx.p, h->ky.p, h->pwi.p);
+    RS_LAUNCHED(1);
+  }
+  h->p.alloc(n); h->s.alloc(n); h->pb.alloc(nw ? nw : 1); h->acc0.alloc(2 * (size_t)n);
+  h->props.alloc(10 * (size_t)n); h->p0.alloc(n); h->s0.alloc(n); h->pb0.alloc(nw ? nw : 1);
+  rs_fill_d(h->p.p, h->fl.p_ref, n, s); rs_fill_d(h->s.p, h->fl.swc, n, s); rs_fill_d(h->pb.p, 0.0, nw ? nw : 1, s);
+  h->ls = new sim_ls_s();
+  ls_init(h->ls, nx, ny, nz, nw, rp.data(), ci.data(), wc0.data(), h->o, s);
+  RS_CUDA(cudaEventCreate(&h->e0)); RS_CUDA(cudaEventCreate(&h->e1));
+  s_store_old(h);
+  RS_CUDA(cudaStreamSynchronize(s));
+  *out = guard.release();
+  ABI_END
+}
+
+extern "C" void sim_destroy(sim_t h) { if (h) { cudaStreamSynchronize(h->st); delete h; } }
+
+extern "C" sim_status sim_init_hydrostatic(sim_t h, double p_datum, double sw0) {
+  ABI_BEGIN
+  if (!h) RS_FAIL(SIM_ERR_ARG, "NULL handle");
+  int nxy = h->nx * h->ny;
+  k_hydrostatic<<<grid_for(h->n, 256), 256, 0, h->st>>>(h->n, nxy, h->fl, h->top, h->dz, p_datum, sw0, h->p.p, h->s.p);
+  RS_LAUNCHED(1);
+  if (h->nw) {
+    k_init_pb<<<grid_for(h->nw, 32), 32, 0, h->st>>>(h->nw, h->wctrl_d.p, h->wtarget_d.p, h->wpptr.p, h->pcell.p, h->p.p, h->pb.p);
+    RS_LAUNCHED(1);
+  }
+  h->t = 0.0;
+  s_store_old(h);
+  RS_CHECK_LAUNCH();
+  RS_CUDA(cudaStreamSynchronize(h->st));
+  ABI_END
+}
+
+extern "C" sim_status sim_set_state(sim_t h, const double *p, const double *sw, const double *pb, double t) {
+  ABI_BEGIN
+  if (!h || !p || !sw || (h->nw && !pb)) RS_FAIL(SIM_ERR_ARG, "sim_set_state: NULL argument");
+  RS_CUDA(cudaMemcpyAsync(h->p.p, p, h->n * sizeof(double), cudaMemcpyDefault, h->st));
+  RS_CUDA(cudaMemcpyAsync(h->s.p, sw, h->n * sizeof(double), cudaMemcpyDefault, h->st));
+  if (h->nw) RS_CUDA(cudaMemcpyAsync(h->pb.p, pb, h->nw * sizeof(double), cudaMemcpyDefault, h->st));
+  h->t = t;
+  RS_CUDA(cudaStreamSynchronize(h->st));
+  ABI_END
+}
+
+extern "C" sim_status sim_get_state(sim_t h, double *p, double *sw, double *pb, double *t) {
+  ABI_BEGIN
+  if (!h) RS_FAIL(SIM_ERR_ARG, "NULL handle");
+  if (p) RS_CUDA(cudaMemcpyAsync(p, h->p.p, h->n * sizeof(double), cudaMemcpyDefault, h->st));
+  if (sw) RS_CUDA(cudaMemcpyAsync(sw, h->s.p, h->n * sizeof(double), cudaMemcpyDefault, h->st));
+  if (pb && h->nw) RS_CUDA(cudaMemcpyAsync(pb, h->pb.p, h->nw * sizeof(double), cudaMemcpyDefault, h->st));
+  if (t) *t = h->t;
+  RS_CUDA(cudaStreamSynchronize(h->st));
+  ABI_END
+}
+
+extern "C" sim_status sim_begin_step(sim_t h, double dt) {
+  ABI_BEGIN
+  if (!h || !(dt > 0)) RS_FAIL(SIM_ERR_ARG, "sim_begin_step: bad argument");
+  h->dt = dt;
+  s_store_old(h);
+  RS_CHECK_LAUNCH();
+  ABI_END
+}
+
+extern "C" sim_status sim_assemble(sim_t h, double *scaled_norm) {
+  ABI_BEGIN
+  if (!h) RS_FAIL(SIM_ERR_ARG, "NULL handle");
+  s_props_assemble(h);
+  double nr = s_norm(h);
+  if (scaled_norm) *scaled_norm = nr;
+  ABI_END
+}
+
+extern "C" sim_status sim_linear_solve(sim_t h, double tol, int *iters, double *relres) {
+  ABI_BEGIN
+  if (!h) RS_FAIL(SIM_ERR_ARG, "NULL handle");
+  ls_setup(h->ls);
+  int its; double rel;
+  int rc = ls_solve(h->ls, tol, &its, &rel);
+  if (iters) *iters = its;
+  if (relres) *relres = rel;
+  if (rc == 2) RS_FAIL(SIM_ERR_NAN, "linear solve produced a non-finite value");
+  ABI_END
+}
+
+extern "C" sim_status sim_newton_step(sim_t h, int *converged, sim_stats *st) {
+  ABI_BEGIN
+  if (!h) RS_FAIL(SIM_ERR_ARG, "NULL handle");
+  s_props_assemble(h);
+  double nr = s_norm(h);
+  h->stats.last_norm = nr;
+  if (!std::isfinite(nr)) RS_FAIL(SIM_ERR_NAN, "non-finite residual");
+  if (converged) *converged = nr <= h->o.newton_tol;
+  if (nr > h->o.newton_tol) {
+    ls_setup(h->ls);
+    int its; double rel;
+    int rc = ls_solve(h->ls, h->o.lin_tol, &its, &rel);
+    h->stats.linear_its += its; h->stats.linear_solves++; h->stats.last_its = its; h->stats.last_relres = rel;
+    if (rc == 2) RS_FAIL(SIM_ERR_NAN, "linear solve produced a non-finite value");
+    k_update<<<grid_for(h->n + h->nw, 256), 256, 0, h->st>>>(h->n, h->nw, h->ls->y.p, h->p.p, h->s.p, h->pb.p);
+    RS_LAUNCHED(1);
+    h->stats.newton++;
+  }
+  if (st) *st = h->stats;
+  ABI_END
+}
+
+extern "C" sim_status sim_advance(sim_t h, int n_steps, sim_stats *st) {
+  ABI_BEGIN
+  if (!h || n_steps < 0) RS_FAIL(SIM_ERR_ARG, "sim_advance: bad argument");
+  cudaStream_t s = h->st;
+  int n = h->n, nw = h->nw;
+  sim_status bad = SIM_OK;
+  for (int stp = 0; stp < n_steps && bad == SIM_OK; stp++) {
+    double rem = h->o.dt, hh = h->o.dt;
+    int cuts = 0;
+    while (rem > 0.0) {
+      double dt = hh < rem ? hh : rem;
+      RS_CUDA(cudaMemcpyAsync(h->p0.p, h->p.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      RS_CUDA(cudaMemcpyAsync(h->s0.p, h->s.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      if (nw) RS_CUDA(cudaMemcpyAsync(h->pb0.p, h->pb.p, nw * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      s_store_old(h);
+      h->dt = dt;
+      int its;
+      int r = s_newton(h, &its);
+      h->stats.last_newton = its;
+      if (r == 0) { h->t += dt; rem -= dt; h->stats.steps++; continue; }
+      RS_CUDA(cudaMemcpyAsync(h->p.p, h->p0.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      RS_CUDA(cudaMemcpyAsync(h->s.p, h->s0.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      if (nw) RS_CUDA(cudaMemcpyAsync(h->pb.p, h->pb0.p, nw * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      h->stats.cuts++; cuts++;
+      if (cuts > h->o.max_cuts) { bad = r == 2 ? SIM_ERR_NAN : SIM_ERR_NOT_CONVERGED; break; }
+      hh = 0.5 * hh;
+    }
+  }
+  h->stats.t = h->t;
+  if (st) *st = h->stats;
+  RS_CUDA(cudaStreamSynchronize(s));
+  if (bad != SIM_OK) RS_FAIL(bad, "time step did not converge after %d cuts", h->o.max_cuts);
+  ABI_END
+}
+
+extern "C" sim_status sim_get_stats(sim_t h, sim_stats *st) {
+  ABI_BEGIN
+  if (!h || !st) RS_FAIL(SIM_ERR_ARG, "NULL argument");
+  h->stats.t = h->t;
+  *st = h->stats;
+  ABI_END
+}
+
+extern "C" sim_ls_t sim_linear_system(sim_t h) { return h ? h->ls : nullptr; }
+
+// ---------------------------------------------------- linear-system ABI --
+extern "C" sim_status sim_ls_create(sim_ls_t *out, int nx, int ny, int nz, int n_wells, const int *rowptr,
+                                    const int *cols, const int *well_cell0, const sim_options *o) {
+  ABI_BEGIN
+  if (!out || !rowptr || !cols || !o || nx < 1 || ny < 1 || nz < 1 || n_wells < 0 || (n_wells && !well_cell0))
+    RS_FAIL(SIM_ERR_ARG, "sim_ls_create: bad argument");
+  *out = nullptr;
+  std::unique_ptr<sim_ls_s> ls(new sim_ls_s());
+  ls_init(ls.get(), nx, ny, nz, n_wells, rowptr, cols, well_cell0, rs_opts_from(o), (cudaStream_t)o->cuda_stream);
+  *out = ls.release();
+  ABI_END
+}
+
+extern "C" void sim_ls_destroy(sim_ls_t ls) { if (ls) { cudaStreamSynchronize(ls->st); delete ls; } }
+
+extern "C" sim_status sim_ls_set(sim_ls_t ls, const double *vals, const double *b, const double *key) {
+  ABI_BEGIN
+  if (!ls || !vals || !b || !key) RS_FAIL(SIM_ERR_ARG, "sim_ls_set: NULL argument");
+  RS_CUDA(cudaMemcpyAsync(ls->val.p, vals, 4 * (size_t)ls->nnzb * sizeof(double), cudaMemcpyDefault, ls->st));
+  RS_CUDA(cudaMemcpyAsync(ls->b.p, b, 2 * (size_t)ls->nb * sizeof(double), cudaMemcpyDefault, ls->st));
+  RS_CUDA(cudaMemcpyAsync(ls->key.p, key, (size_t)ls->n * sizeof(double), cudaMemcpyDefault, ls->st));
+  RS_CUDA(cudaStreamSynchronize(ls->st));
+  ls->have_setup = false;
+  ABI_END
+}
+
+extern "C" sim_status sim_ls_setup(sim_ls_t ls) {
+  ABI_BEGIN
+  if (!ls) RS_FAIL(SIM_ERR_ARG, "NULL handle");
+  ls_setup(ls);
+  RS_CUDA(cudaStreamSynchronize(ls->st));
+  ABI_END
+}
+
+extern "C" sim_status sim_ls_solve(sim_ls_t ls, double tol, double *y, int *iters, double *relres) {
+  ABI_BEGIN
+  if (!ls) RS_FAIL(SIM_ERR_ARG, "NULL handle");
+  if (!ls->have_setup) RS_FAIL(SIM_ERR_STATE, "sim_ls_solve before sim_ls_setup");
+  int its; double rel;
+  int rc = ls_solve(ls, tol, &its, &rel);
+  if (iters) *iters = its;
+  if (relres) *relres = rel;
+  if (y) RS_CUDA(cudaMemcpyAsync(y, ls->y.p, 2 * (size_t)ls->nb * sizeof(double), cudaMemcpyDefault, ls->st));
+  RS_CUDA(cudaStreamSynchronize(ls->st));
+  if (rc == 2) RS_FAIL(SIM_ERR_NAN, "non-finite value in the linear solve");
+  ABI_END
+}
+
+__global__ void k_cast_f2d(size_t m, const float *a, double *b) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < m) b[i] = a[i];
+}
+__global__ void k_cast_d2f_(size_t m, const double *a, float *b) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < m) b[i] = (float)a[i];
+}
+
+extern "C" sim_status sim_ls_apply(sim_ls_t ls, int op, const double *x, double *y) {
+  ABI_BEGIN
+  if (!ls || !x || !y) RS_FAIL(SIM_ERR_ARG, "sim_ls_apply: NULL argument");
+  if (op != SIM_OP_SPMV && !ls->have_setup) RS_FAIL(SIM_ERR_STATE, "sim_ls_apply before sim_ls_setup");
+  cudaStream_t s = ls->st;
+  size_t nu = 2 * (size_t)ls->nb, m = op == SIM_OP_VCYCLE ? (size_t)ls->n : nu;
+  dbuf<double> xin, yout;
+  xin.alloc(m); yout.alloc(m);
+  RS_CUDA(cudaMemcpyAsync(xin.p, x, m * sizeof(double), cudaMemcpyDefault, s));
+  bool mixed = ls->o.precision == SIM_PREC_MIXED;
+  if (op == SIM_OP_SPMV) ls_spmv64(ls, xin.p, yout.p);
+  else if (op == SIM_OP_RAS) {
+    if (mixed) {
+      dbuf<float> a, b2; a.alloc(nu); b2.alloc(nu);
+      k_cast_d2f_<<<grid_for(nu, 256), 256, 0, s>>>(nu, xin.p, a.p);
+      ls_ras_apply<float>(ls, a.p, b2.p);
+      k_cast_f2d<<<grid_for(nu, 256), 256, 0, s>>>(nu, b2.p, yout.p);
+      RS_LAUNCHED(2);
+      RS_CUDA(cudaStreamSynchronize(s));
+    } else ls_ras_apply<double>(ls, xin.p, yout.p);
+  } else if (op == SIM_OP_VCYCLE) {
+    amg_level &L0 = ls->amg.lev[0];
+    if (mixed) {
+      k_cast_d2f_<<<grid_for(m, 256), 256, 0, s>>>(m, xin.p, L0.f32.p);
+      amg_vcycle<float>(ls->amg, 0, s);
+      k_cast_f2d<<<grid_for(m, 256), 256, 0, s>>>(m, L0.x32.p, yout.p);
+      RS_LAUNCHED(2);
+    } else {
+      RS_CUDA(cudaMemcpyAsync(L0.f.p, xin.p, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      amg_vcycle<double>(ls->amg, 0, s);
+      RS_CUDA(cudaMemcpyAsync(yout.p, L0.x.p, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+  } else if (op == SIM_OP_CPR) {
+    if (mixed) {
+      dbuf<float> z; z.alloc(nu);
+      ls_cpr(ls, xin.p, nullptr, z.p);
+      k_cast_f2d<<<grid_for(nu, 256), 256, 0, s>>>(nu, z.p, yout.p);
+      RS_LAUNCHED(1);
+      RS_CUDA(cudaStreamSynchronize(s));
+    } else ls_cpr(ls, xin.p, yout.p, nullptr);
+  } else RS_FAIL(SIM_ERR_ARG, "sim_ls_apply: unknown operator %d", op);
+  RS_CHECK_LAUNCH();
+  RS_CUDA(cudaMemcpyAsync(y, yout.p, m * sizeof(double), cudaMemcpyDefault, s));
+  RS_CUDA(cudaStreamSynchronize(s));
+  ABI_END
+}
+
+template <class T>
+static void put(void *dst, size_t bytes, size_t *needed, const T *src_dev, size_t count, cudaStream_t s) {
+  size_t need = count * sizeof(T);
+  if (needed) *needed = need;
+  if (!dst) return;
+  if (bytes < need) RS_FAIL(SIM_ERR_ARG, "sim_ls_export: buffer of %zu bytes, %zu needed", bytes, need);
+  if (count) RS_CUDA(cudaMemcpyAsync(dst, src_dev, need, cudaMemcpyDefault, s));
+  RS_CUDA(cudaStreamSynchronize(s));
+}
+static void put_host(void *dst, size_t bytes, size_t *needed, const void *src, size_t need) {
+  if (needed) *needed = need;
+  if (!dst) return;
+  if (bytes < need) RS_FAIL(SIM_ERR_ARG, "sim_ls_export: buffer of %zu bytes, %zu needed", bytes, need);
+  memcpy(dst, src, need);
+}
+
+extern "C" sim_status sim_ls_export(sim_ls_t ls, int what, int index, void *dst, size_t bytes, size_t *needed) {
+  ABI_BEGIN
+  if (!ls) RS_FAIL(SIM_ERR_ARG, "NULL handle");
+  cudaStream_t s = ls->st;
+  RS_CUDA(cudaStreamSynchronize(s));
+  amg_hier &H = ls->amg;
+  auto lev = [&](int l) -> amg_level & {
+    if (l < 0 || l >= H.nlev) RS_FAIL(SIM_ERR_ARG, "sim_ls_export: no AMG level %d", l);
+    return H.lev[l];
+  };
+  switch (what) {
+    case SIM_X_VALS: put(dst, bytes, needed, ls->val.p, 4 * (size_t)ls->nnzb, s); break;
+    case SIM_X_RHS: put(dst, bytes, needed, ls->b.p, 2 * (size_t)ls->nb, s); break;
+    case SIM_X_SOLUTION: put(dst, bytes, needed, ls->y.p, 2 * (size_t)ls->nb, s); break;
+    case SIM_X_ROWPTR: put_host(dst, bytes, needed, ls->h_rp.data(), ls->h_rp.size() * sizeof(int)); break;
+    case SIM_X_COLS: put_host(dst, bytes, needed, ls->h_ci.data(), ls->h_ci.size() * sizeof(int)); break;
+    case SIM_X_KEY: put(dst, bytes, needed, ls->key.p, (size_t)ls->n, s); break;
+    case SIM_X_AMG_SIZES: {
+      if (index < 0) { int v = H.nlev; put_host(dst, bytes, needed, &v, sizeof(int)); break; }
+      amg_level &L = lev(index);
+      bool last = index == H.nlev - 1;
+      int v[6] = {L.A.n, L.A.nnz, last ? 0 : L.P.nnz, last ? 0 : L.nc, L.rounds, H.coarse_dense};
+      put_host(dst, bytes, needed, v, sizeof(v));
+      break;
+    }
+    case SIM_X_AMG_RP: { amg_level &L = lev(index); put(dst, bytes, needed, L.A.rp.p, L.A.n + 1, s); break; }
+    case SIM_X_AMG_CI: { amg_level &L = lev(index); put(dst, bytes, needed, L.A.ci.p, L.A.nnz, s); break; }
+    case SIM_X_AMG_V: { amg_level &L = lev(index); put(dst, bytes, needed, L.A.v.p, L.A.nnz, s); break; }
+    case SIM_X_AMG_CF: { amg_level &L = lev(index); put(dst, bytes, needed, L.cf.p, L.A.n, s); break; }
+    case SIM_X_AMG_PRP: case SIM_X_AMG_PCI: case SIM_X_AMG_PV: {
+      amg_level &L = lev(index);
+      if (index == H.nlev - 1) RS_FAIL(SIM_ERR_ARG, "sim_ls_export: the coarsest level has no P");
+      if (what == SIM_X_AMG_PRP) put(dst, bytes, needed, L.P.rp.p, L.P.n + 1, s);
+      else if (what == SIM_X_AMG_PCI) put(dst, bytes, needed, L.P.ci.p, L.P.nnz, s);
+      else put(dst, bytes, needed, L.P.v.p, L.P.nnz, s);
+      break;
+    }
+    case SIM_X_RAS_SIZES: {
+      if (index < 0) { int v = ls->ras.nsub; put_host(dst, bytes, needed, &v, sizeof(int)); break; }
+      if (index >= ls->ras.nsub) RS_FAIL(SIM_ERR_ARG, "sim_ls_export: no subdomain %d", index);
+      std::vector<int> sp = d2h(ls->ras.sub_ptr.p + index, 2, s), lp = d2h(ls->ras.lrp_ptr.p + index, 2, s);
+      int m = sp[1] - sp[0];
+      std::vector<uint8_t> ow = d2h(ls->ras.owned.p + sp[0], m, s);
+      int nown = 0; for (auto o : ow) nown += o;
+      int v[3] = {nown, m, lp[1] - lp[0]};
+      put_host(dst, bytes, needed, v, sizeof(v));
+      break;
+    }
+    case SIM_X_RAS_EXT: case SIM_X_RAS_LEVELS: {
+      if (index < 0 || index >= ls->ras.nsub) RS_FAIL(SIM_ERR_ARG, "sim_ls_export: no subdomain %d", index);
+      if (!ls->have_setup) RS_FAIL(SIM_ERR_STATE, "sim_ls_export: no setup yet");
+      std::vector<int> sp = d2h(ls->ras.sub_ptr.p + index, 2, s);
+      int base = sp[0], m = sp[1] - sp[0];
+      if (what == SIM_X_RAS_EXT) {
+        std::vector<int> perm = d2h(ls->ras.perm.p + base, m, s), ext = d2h(ls->ras.ext.p + base, m, s), out(m);
+        for (int a = 0; a < m; a++) out[a] = ext[perm[a]];
+        put_host(dst, bytes, needed, out.data(), m * sizeof(int));
+      } else {
+        std::vector<int> nl = d2h(ls->ras.nlev.p + 2 * index, 2, s), lv = d2h(ls->ras.lvl.p + 2 * base, 2 * m, s);
+        std::vector<int> out(2 + 2 * m);
+        out[0] = nl[0]; out[1] = nl[1];
+        for (int a = 0; a < m; a++) { out[2 + 2 * a] = lv[a]; out[3 + 2 * a] = lv[m + a]; }
+        put_host(dst, bytes, needed, out.data(), out.size() * sizeof(int));
+      }
+      break;
+    }
+    default: RS_FAIL(SIM_ERR_ARG, "sim_ls_export: unknown item %d", what);
+  }
+  ABI_END
+}
+
+extern "C" sim_status sim_kernel_timer(sim_ls_t ls, int which) {
+  ABI_BEGIN
+  if (!ls) RS_FAIL(SIM_ERR_ARG, "NULL handle");
+  ls->timer_flush();
+  ls->timer_which = which; ls->timer_launches = 0; ls->timer_ms = 0;
+  ABI_END
+}
+extern "C" sim_status sim_kernel_time(sim_ls_t ls, long long *launches, double *ms) {
+  ABI_BEGIN
+  if (!ls) RS_FAIL(SIM_ERR_ARG, "NULL handle");
+  ls->timer_flush();
+  if (launches) *launches = ls->timer_launches;
+  if (ms) *ms = ls->timer_ms;
+  ABI_END
+}

@@ -1,0 +1,295 @@
+"""GPU (sm_103a) path vs the CPU oracle, through the C ABI.
+
+Integer work (sparsity patterns, reordering permutations, C/F splits, AMG
+patterns, level sets) must match bit for bit when both sides get the same
+FP64 input; the ABF-decoupled matrix and the FP64 AMG setup also match bit
+for bit (both evaluate the same formulas with round-to-nearest operations in
+the same order).  Floating-point results are compared with the tolerances
+stated in each test: 1e-12 relative for assembly (different summation
+order), 1e-10 for FP64 operator applications, and per-cell |dp|/p <= 1e-6,
+|ds| <= 1e-6 with Newton counts within +-1 for whole runs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1701_06254_gb300 as R
+from paper_1701_06254_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _states(case, seed):
+    p0, s0, pb0 = I.random_state(case, seed)
+    p1, s1, pb1 = I.random_state(case, seed + 1)
+    return (p0, s0, pb0), (p1, s1, pb1)
+
+
+def _pair(case, seed, dt=1.5, **opts):
+    """Oracle and GPU simulators on the same random (old, new) states, assembled."""
+    (p0, s0, pb0), (p1, s1, pb1) = _states(case, seed)
+    o = oracle.Sim(case, **opts)
+    o.set_state(p0, s0, pb0); o.store_old(); o.set_dt(dt)
+    o.set_state(p1, s1, pb1); o.assemble()
+    g = R.Sim(case, **opts)
+    g.set_state(p0, s0, pb0); g.begin_step(dt)
+    g.set_state(p1, s1, pb1)
+    nrm = g.assemble()
+    return o, g, nrm
+
+
+def _rowscale(val, rp, nb):
+    a = np.abs(val.reshape(-1, 4)).max(axis=1)
+    return np.maximum.reduceat(a, rp[:-1])
+
+
+CASES = [
+    lambda: I.small_case(6, 5, 3, seed=21),
+    lambda: I.small_case(11, 7, 4, seed=22),            # ragged 8x8 tiles
+    lambda: I.small_case(13, 1, 1, seed=23),            # 1D
+    lambda: I.small_case(3, 3, 9, seed=24, gravity=True),
+]
+
+
+@pytest.mark.parametrize("mk", CASES)
+def test_assembly_matches_oracle(mk):
+    c = mk()
+    o, g, nrm = _pair(c, 100)
+    rp, ci, val, b, key = o.system()
+    grp = g.ls.export(R.X_ROWPTR, 0, np.int32)
+    gci = g.ls.export(R.X_COLS, 0, np.int32)
+    np.testing.assert_array_equal(grp, rp)
+    np.testing.assert_array_equal(gci, ci)
+    gval = g.ls.export(R.X_VALS)
+    gb = g.ls.export(R.X_RHS)
+    nb = len(rp) - 1
+    sc = np.repeat(_rowscale(val, rp, nb), np.diff(rp))
+    err = np.abs(gval - val).reshape(-1, 4).max(axis=1) / sc
+    assert err.max() < 1e-12, err.max()
+    bs = np.abs(b).reshape(-1, 2).max(axis=1).max()
+    assert np.abs(gb - b).max() <= 1e-12 * bs
+    np.testing.assert_array_equal(g.ls.export(R.X_KEY), key)          # eq. (5), same IEEE order
+    np.testing.assert_allclose(nrm, o.residual_norm(), rtol=1e-12)
+
+
+def _shared_system(case, seed, **opts):
+    """The oracle's assembled Jacobian handed to both linear solvers."""
+    o, _, _ = _pair(case, seed, **opts)
+    rp, ci, val, b, key = o.system()
+    wc0 = [w.perf_cells[0] for w in case.wells]
+    gl = R.LinearSystem(case.nx, case.ny, case.nz, len(case.wells), rp, ci, wc0, **opts)
+    gl.set(val, b, key)
+    return o, gl, (rp, ci, val, b, key)
+
+
+SYS = [
+    (lambda: I.small_case(6, 5, 3, seed=31), dict(tile_x=2, tile_y=2, amg_coarse_max=8)),
+    (lambda: I.small_case(11, 7, 4, seed=32), dict(tile_x=3, tile_y=4, amg_coarse_max=16)),
+    (lambda: I.case0(), dict()),
+    (lambda: I.case0(), dict(amg_coarse_max=40, tile_x=5, tile_y=3)),
+]
+
+
+@pytest.mark.parametrize("mk,opts", SYS)
+def test_setup_integer_work_is_bit_exact(mk, opts):
+    c = mk()
+    o, gl, (rp, ci, val, b, key) = _shared_system(c, 200, **opts)
+    o.ls.setup()
+    gl.setup()
+    _, _, dval, db, _ = o.ls.get()
+    # ABF decoupling: same bits
+    np.testing.assert_array_equal(gl.export(R.X_VALS), dval)
+    np.testing.assert_array_equal(gl.export(R.X_RHS), db)
+    # local potential reordering per subdomain (eqs. 30-32)
+    assert gl.ras_count() == o.ls.nsub
+    for s in range(o.ls.nsub):
+        np.testing.assert_array_equal(gl.ras_ext(s), o.ls.sub(s)["ext"])
+    # AMG hierarchy: every level, bit for bit
+    oa = o.ls.amg()
+    assert gl.amg_nlev() == oa.nlev
+    for l in range(oa.nlev):
+        Lo, Lg = oa.level(l), gl.amg_level(l)
+        np.testing.assert_array_equal(Lg["rp"], Lo["rp"])
+        np.testing.assert_array_equal(Lg["ci"], Lo["ci"])
+        np.testing.assert_array_equal(Lg["v"], Lo["v"])
+        if l < oa.nlev - 1:
+            np.testing.assert_array_equal(Lg["cf"], Lo["cf"])
+            assert Lg["rounds"] == Lo["rounds"]
+            np.testing.assert_array_equal(Lg["prp"], Lo["prp"])
+            np.testing.assert_array_equal(Lg["pci"], Lo["pci"])
+            np.testing.assert_array_equal(Lg["pv"], Lo["pv"])
+
+
+def _levels_brute(rp, ci):
+    m = len(rp) - 1
+    L = np.zeros(m, int); U = np.zeros(m, int)
+    for i in range(m):
+        cols = ci[rp[i]:rp[i + 1]]
+        lo = [L[c] for c in cols if c < i]
+        L[i] = 1 + max(lo) if lo else 0
+    for i in range(m - 1, -1, -1):
+        cols = ci[rp[i]:rp[i + 1]]
+        hi = [U[c] for c in cols if c > i]
+        U[i] = 1 + max(hi) if hi else 0
+    return L, U
+
+
+def test_ilu_level_sets_match_topological_levels():
+    c = I.small_case(9, 6, 5, seed=41)
+    o, gl, _ = _shared_system(c, 300, tile_x=4, tile_y=3)
+    o.ls.setup(); gl.setup()
+    for s in range(o.ls.nsub):
+        d = o.ls.sub(s)
+        L, U = _levels_brute(d["rp"], d["ci"])
+        nL, nU, gL, gU = gl.ras_levels(s)
+        np.testing.assert_array_equal(gL, L)
+        np.testing.assert_array_equal(gU, U)
+        assert nL == L.max() + 1 and nU == U.max() + 1
+
+
+@pytest.mark.parametrize("mk,opts", SYS[:3])
+def test_operators_match_oracle_fp64(mk, opts):
+    c = mk()
+    o, gl, _ = _shared_system(c, 400, **opts)
+    o.ls.setup(); gl.setup()
+    rng = np.random.default_rng(5)
+    nb = c.n + len(c.wells)
+    x = rng.standard_normal(2 * nb)
+    for op, fo in ((R.OP_SPMV, o.ls.mv), (R.OP_RAS, o.ls.ras), (R.OP_CPR, o.ls.cpr)):
+        yg, yo = gl.apply(op, x), fo(x)
+        assert np.abs(yg - yo).max() <= 1e-10 * np.abs(yo).max(), op
+    xp = rng.standard_normal(c.n)
+    yg, yo = gl.apply(R.OP_VCYCLE, xp), o.ls.amg().apply(xp)
+    assert np.abs(yg - yo).max() <= 1e-10 * np.abs(yo).max()
+
+
+@pytest.mark.parametrize("mk,opts", SYS)
+def test_fgmres_matches_oracle(mk, opts):
+    c = mk()
+    o, gl, _ = _shared_system(c, 500, **opts)
+    o.ls.setup(); gl.setup()
+    rco, yo, itso, relo = o.ls.solve(1e-10)
+    yg, itsg, relg = gl.solve(1e-10)
+    assert rco == 0 and relg <= 1e-10
+    assert abs(itsg - itso) <= 1
+    assert np.abs(yg - yo).max() <= 1e-7 * np.abs(yo).max()
+
+
+def test_mixed_precision_operators_track_fp64():
+    """FP32 RAS / AMG / CPR stay within single-precision distance of the
+    FP64 oracle; the integer setup work is unchanged (done in FP64)."""
+    c = I.case0()
+    o, gl, _ = _shared_system(c, 600, precision=R.PREC_MIXED)
+    o.ls.setup(); gl.setup()
+    oa = o.ls.amg()
+    for l in range(oa.nlev - 1):
+        np.testing.assert_array_equal(gl.amg_level(l)["cf"], oa.level(l)["cf"])
+    x = np.random.default_rng(6).standard_normal(2 * (c.n + 2))
+    for op, fo in ((R.OP_RAS, o.ls.ras), (R.OP_CPR, o.ls.cpr)):
+        yg, yo = gl.apply(op, x), fo(x)
+        assert np.abs(yg - yo).max() <= 1e-3 * np.abs(yo).max(), op
+    yg, itsg, relg = gl.solve(1e-8)
+    assert relg <= 1e-8
+
+
+def _run_compare(case, nsteps, **opts):
+    o = oracle.Sim(case, **opts)
+    o.init_hydrostatic()
+    g = R.Sim(case, **opts)
+    g.init_hydrostatic()
+    po, so, pbo, _ = o.get_state()
+    pg, sg, pbg, _ = g.get_state()
+    np.testing.assert_allclose(pg, po, rtol=1e-13)
+    np.testing.assert_array_equal(sg, so)
+    for k in range(nsteps):
+        n0o, n0g = o.stats()["newton"], g.stats()["newton"]
+        assert o.advance(1) == 0
+        g.advance(1)
+        po, so, pbo, to = o.get_state()
+        pg, sg, pbg, tg = g.get_state()
+        assert tg == to
+        assert np.max(np.abs(pg - po) / np.abs(po)) <= 1e-6, k
+        assert np.max(np.abs(sg - so)) <= 1e-6, k
+        assert abs((g.stats()["newton"] - n0g) - (o.stats()["newton"] - n0o)) <= 1, k
+    return o, g
+
+
+def test_whole_run_cfg0_fp64():
+    """The plain method on the 20x20x5 case: 10 steps of 1 day, standard
+    Newton to 1e-8, CPR-FGMRES to 1e-8."""
+    _run_compare(I.case0(), 10)
+
+
+def test_whole_run_cfg0_mixed_precision():
+    """Same run with the FP32 preconditioner: the converged Newton states do
+    not depend on the preconditioner precision, so the same tolerances hold."""
+    _run_compare(I.case0(), 10, precision=R.PREC_MIXED)
+
+
+def test_whole_run_inexact_newton():
+    c = I.small_case(10, 8, 4, seed=51, dt=5.0)
+    c.newton, c.newton_tol = "inexact", 1e-7
+    _run_compare(c, 4, newton=1, newton_tol=1e-7)
+
+
+@pytest.mark.parametrize("mk", [
+    lambda: I.Case("one", 1, 1, 1, 10.0, 10.0, 10.0, 1000.0, np.array([50.0]), np.array([50.0]),
+                   np.array([5.0]), np.array([0.2]), I.Fluid(), [], dt=1.0, n_steps=1),
+    lambda: I.small_case(2, 1, 1, seed=61),
+    lambda: I.small_case(17, 9, 2, seed=62),
+])
+def test_edge_grids_run(mk):
+    """Degenerate and ragged grids: a single cell without wells, two cells,
+    tiles that do not divide the grid."""
+    c = mk()
+    _run_compare(c, 2)
+
+
+def test_zero_rhs_and_errors():
+    c = I.small_case(4, 4, 2, seed=71)
+    o, gl, (rp, ci, val, b, key) = _shared_system(c, 700)
+    gl.set(val, np.zeros_like(b), key)
+    gl.setup()
+    y, its, rel = gl.solve(1e-8)
+    assert its == 0 and rel == 0.0 and not y.any()
+    with pytest.raises(R.SimError):
+        gl.apply(99, np.zeros(2 * (c.n + 2)))
+    bad = b.copy(); bad[3] = np.nan
+    gl.set(val, bad, key)
+    gl.setup()
+    with pytest.raises(R.SimError) as e:
+        gl.solve(1e-8)
+    assert e.value.code == 5          # SIM_ERR_NAN
+
+
+def test_full_size_cfg2_parity():
+    """The 1M-cell case in the benchmark's configuration (mixed precision):
+    assembly over all cells, bit-exact ABF, reordering and level-0 C/F split,
+    and the GPU solution's true residual checked with the oracle's SpMV."""
+    c = I.case2()
+    opts = dict(precision=R.PREC_MIXED)
+    o = oracle.Sim(c, **opts)
+    o.init_hydrostatic(); o.store_old(); o.set_dt(c.dt); o.assemble()
+    g = R.Sim(c, **opts)
+    g.init_hydrostatic(); g.begin_step(c.dt)
+    nrm = g.assemble()
+    rp, ci, val, b, key = o.system()
+    gval, gb = g.ls.export(R.X_VALS), g.ls.export(R.X_RHS)
+    sc = np.repeat(_rowscale(val, rp, len(rp) - 1), np.diff(rp))
+    assert (np.abs(gval - val).reshape(-1, 4).max(axis=1) / sc).max() < 1e-12
+    assert np.abs(gb - b).max() <= 1e-12 * np.abs(b).max()
+    np.testing.assert_allclose(nrm, o.residual_norm(), rtol=1e-12)
+    # shared-input setup: decoupling, reordering, C/F at level 0
+    gl = R.LinearSystem(c.nx, c.ny, c.nz, len(c.wells), rp, ci, [w.perf_cells[0] for w in c.wells], **opts)
+    gl.set(val, b, key)
+    gl.setup()
+    o.ls.setup()
+    _, _, dval, db, _ = o.ls.get()
+    np.testing.assert_array_equal(gl.export(R.X_VALS), dval)
+    for s in (0, 1, 137, o.ls.nsub - 1):
+        np.testing.assert_array_equal(gl.ras_ext(s), o.ls.sub(s)["ext"])
+    np.testing.assert_array_equal(gl.amg_level(0)["cf"], o.ls.amg().level(0)["cf"])
+    np.testing.assert_array_equal(gl.amg_level(1)["ci"], o.ls.amg().level(1)["ci"])
+    y, its, rel = gl.solve(1e-6)
+    r = db - o.ls.mv(y)
+    assert np.linalg.norm(r) <= 1.0001e-6 * np.linalg.norm(db), (its, rel)
