@@ -110,7 +110,7 @@ typedef struct sim_ls_s *sim_ls_t;
 
 /* Fill *o with the defaults: FP64, ABF, reordering on, standard Newton,
  * newton_tol 1e-8, lin_tol 1e-8, max_newton 20, restart 50, max_lin 100,
- * 8x8 tiles, theta 0.25, 25 levels, coarsest <= 128 rows, 6 cuts, dt 1. */
+ * 4x4 tiles, theta 0.25, 25 levels, coarsest <= 128 rows, 6 cuts, dt 1. */
 void sim_default_options(sim_options *o);
 
 /* Create a simulator (copies everything).  Builds transmissibilities,

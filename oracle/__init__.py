@@ -21,7 +21,7 @@ _LIB = os.path.join(_LIBDIR, "liboracle.so")
 _lib = None
 
 DEFAULT_OPTS = dict(decoupling=1, reorder=1, newton=0, newton_tol=1e-8, lin_tol=1e-8,
-                    max_newton=20, restart=50, max_lin=100, tile_x=8, tile_y=8,
+                    max_newton=20, restart=50, max_lin=100, tile_x=4, tile_y=4,
                     amg_theta=0.25, amg_max_levels=25, amg_coarse_max=128,
                     seed=0x5EED, max_cuts=6, dt=1.0)
 
@@ -306,6 +306,8 @@ class LinearSystem:
         return AMG(None, None, None, _handle=self._lib.or_ls_amg(self.h), _owner=self)
 
     def sub(self, s):
+        if not 0 <= s < self.nsub:
+            raise IndexError(f"subdomain {s} of {self.nsub}")
         out = np.zeros(3, np.int32)
         self._lib.or_ls_sub_sizes(self.h, s, _i(out))
         nown, next_, nnz = (int(x) for x in out)

@@ -159,7 +159,7 @@ void or_potential_rank(int m, const double *key, const int *idx, int *order)
 static void build_subs(or_lsys *ls)
 {
   free_subs(ls);
-  int tx = ls->o.tile_x > 0 ? ls->o.tile_x : 8, ty = ls->o.tile_y > 0 ? ls->o.tile_y : 8;
+  int tx = ls->o.tile_x > 0 ? ls->o.tile_x : 4, ty = ls->o.tile_y > 0 ? ls->o.tile_y : 4;
   int ntx = (ls->nx + tx - 1) / tx, nty = (ls->ny + ty - 1) / ty;
   ls->nsub = ntx * nty;
   ls->sub = xc(ls->nsub, sizeof(or_sub));

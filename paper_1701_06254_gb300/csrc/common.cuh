@@ -155,6 +155,11 @@ struct ras_data {
   dbuf<int> nlev;               // per subdomain: #L levels, #U levels
   dbuf<int> lvl_ptr;            // per subdomain: offsets of the L and U level groups
   int max_lvl_ptr = 0;
+  // shared-memory apply: one packed blob per subdomain (see ras.cu)
+  bool smem_path = false;
+  size_t smem_bytes = 0;        // largest blob + local vector
+  dbuf<long long> blob_off;     // nsub + 1 byte offsets
+  dbuf<unsigned char> blob;
 };
 
 // ---------------------------------------------------------- linear system --
@@ -198,7 +203,7 @@ void ls_setup(sim_ls_s *ls);
 int ls_solve(sim_ls_s *ls, double tol, int *its, double *relres);   // solution in ls->y
 void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32);
 void ls_spmv64(sim_ls_s *ls, const double *x, double *y);
-template <class T> void ls_ras_apply(sim_ls_s *ls, const T *f, T *x);
+template <class T, class Tin> void ls_ras_apply(sim_ls_s *ls, const Tin *f, T *x, bool accumulate);
 void ras_build_static(sim_ls_s *ls);
 void ras_setup(sim_ls_s *ls);
 

@@ -185,29 +185,17 @@ __global__ void k_add_p(int n, const T *e, T *x) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) x[2 * (size_t)i] += e[i];
 }
-template <class Ti, class T>
-__global__ void k_ras_in_cast(size_t m, const Ti *a, T *b) {
-  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i < m) b[i] = (T)a[i];
-}
-template <class T>
-__global__ void k_add_vec(size_t m, const T *a, T *b) {
-  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i < m) b[i] += a[i];
-}
 
 // CPR-FPF (Algorithm 2): z = R^{-1} v; r = v - A z; z += Pi_p M(A_pp)^{-1} Pi_r r;
 // r = v - A z; z += R^{-1} r.  FP64 preconditioner: A is the decoupled FP64
 // matrix; mixed: FP32 matrix, factors, hierarchy and vectors (FP64 coarsest).
 void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32) {
   cudaStream_t s = ls->st;
-  int n = ls->n, nu = 2 * ls->nb;
+  int n = ls->n;
   amg_level &L0 = ls->amg.lev[0];
   if (ls->o.precision == SIM_PREC_MIXED) {
-    float *z = z32, *r = ls->x32b.p, *t = ls->x32c.p;
-    k_ras_in_cast<double, float><<<grid_for(nu, 256), 256, 0, s>>>(nu, v, t);
-    RS_LAUNCHED(1);
-    ls_ras_apply<float>(ls, t, z);                                                     // 1
+    float *z = z32, *r = ls->x32b.p;
+    ls_ras_apply<float, double>(ls, v, z, false);                                      // 1
     { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, double, float>(ls, ls->val32.p, z, v, r, s); }  // 2
     k_gather_p<float, float><<<grid_for(n, 256), 256, 0, s>>>(n, r, L0.f32.p);
     RS_LAUNCHED(1);
@@ -215,12 +203,10 @@ void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32) {
     k_add_p<float><<<grid_for(n, 256), 256, 0, s>>>(n, L0.x32.p, z);
     RS_LAUNCHED(1);
     { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, double, float>(ls, ls->val32.p, z, v, r, s); }  // 4
-    ls_ras_apply<float>(ls, r, t);                                                     // 5
-    k_add_vec<float><<<grid_for(nu, 256), 256, 0, s>>>(nu, t, z);
-    RS_LAUNCHED(1);
+    ls_ras_apply<float, float>(ls, r, z, true);                                        // 5
   } else {
-    double *z = z64, *r = ls->x64a.p, *t = ls->x64b.p;
-    ls_ras_apply<double>(ls, v, z);
+    double *z = z64, *r = ls->x64a.p;
+    ls_ras_apply<double, double>(ls, v, z, false);
     { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<double, double, double, double>(ls, ls->val.p, z, v, r, s); }
     k_gather_p<double, double><<<grid_for(n, 256), 256, 0, s>>>(n, r, L0.f.p);
     RS_LAUNCHED(1);
@@ -228,9 +214,7 @@ void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32) {
     k_add_p<double><<<grid_for(n, 256), 256, 0, s>>>(n, L0.x.p, z);
     RS_LAUNCHED(1);
     { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<double, double, double, double>(ls, ls->val.p, z, v, r, s); }
-    ls_ras_apply<double>(ls, r, t);
-    k_add_vec<double><<<grid_for(nu, 256), 256, 0, s>>>(nu, t, z);
-    RS_LAUNCHED(1);
+    ls_ras_apply<double, double>(ls, r, z, true);
   }
 }
 

@@ -12,6 +12,36 @@
 #include <cfloat>
 #include <climits>
 
+// Packed per-subdomain factors for the shared-memory apply.  Rows are in
+// position (reordered) order; the diagonal blocks are dropped from the
+// entry arrays (their inverses are stored instead), so row i's L entries
+// are [rp[i], dg[i]) and its U entries [dg[i], rp[i+1]).  Lrow lists the rows
+// of L levels >= 1 level by level (Llev gives the level boundaries), Urow
+// all rows by U level.  gidx holds 2 * global row + owned flag.
+//   16 B header {m, L rows, L levels with rows, U levels}
+//   gidx int32[m] | rp u16[m+1] | dg u16[m] | Lrow u16[m] | Llev u16[m+1]
+//   | Urow u16[m] | Ulev u16[m+1] | cols u16[e] | vals VB[e] | dinv VB[m]
+// every section starts on a 16-byte boundary.
+#define RAS_SMEM_BUDGET (200 * 1024)
+struct blob_layout { int gidx, rp, dg, lrow, llev, urow, ulev, cols, vals, dinv, total; };
+__host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
+__host__ __device__ inline blob_layout blob_lay(int m, int e, int vb) {
+  blob_layout L;
+  int o = 16;
+  L.gidx = o; o = al16(o + 4 * m);
+  L.rp = o; o = al16(o + 2 * (m + 1));
+  L.dg = o; o = al16(o + 2 * m);
+  L.lrow = o; o = al16(o + 2 * m);
+  L.llev = o; o = al16(o + 2 * (m + 1));
+  L.urow = o; o = al16(o + 2 * m);
+  L.ulev = o; o = al16(o + 2 * (m + 1));
+  L.cols = o; o = al16(o + 2 * e);
+  L.vals = o; o = al16(o + vb * e);
+  L.dinv = o; o = al16(o + vb * m);
+  L.total = o;
+  return L;
+}
+
 // ------------------------------------------------- static partition (host)
 void ras_build_static(sim_ls_s *ls) {
   ras_data &R = ls->ras;
@@ -84,6 +114,24 @@ void ras_build_static(sim_ls_s *ls) {
   int m = 1;
   while (m < maxcells) m <<= 1;
   R.max_lvl_ptr = m;   // sort width (power of two >= most cells in a subdomain)
+  // shared-memory apply: blob sizes are static (rows and entries per
+  // subdomain do not change with the ordering)
+  {
+    int vb = ls->o.precision == SIM_PREC_MIXED ? 16 : 32;
+    std::vector<long long> boff(nsub + 1, 0);
+    size_t mx = 0;
+    bool fits16 = true;
+    for (int s2 = 0; s2 < nsub; s2++) {
+      int ms = sub_ptr[s2 + 1] - sub_ptr[s2], nz = lrp_ptr[s2 + 1] - lrp_ptr[s2];
+      if (ms >= 65535 || nz >= 65535) fits16 = false;
+      blob_layout L = blob_lay(ms, nz - ms, vb);
+      boff[s2 + 1] = boff[s2] + L.total;
+      mx = std::max(mx, (size_t)L.total + (size_t)ms * (vb / 2));
+    }
+    R.smem_bytes = mx;
+    R.smem_path = fits16 && mx <= RAS_SMEM_BUDGET;
+    if (R.smem_path) { h2d(R.blob_off, boff, st); R.blob.alloc(boff[nsub]); }
+  }
   if ((size_t)m * 12 > 200 * 1024) RS_FAIL(SIM_ERR_ARG, "RAS: %d cells per subdomain is too many (reduce tile_x/tile_y)", maxcells);
   if ((size_t)R.max_ext * 16 > 200 * 1024) RS_FAIL(SIM_ERR_ARG, "RAS: subdomain too large");
 }
@@ -265,6 +313,7 @@ __global__ void k_ras_factor(const int *sub_ptr, const int *lrp_ptr, const int *
   }
 }
 
+void ras_pack(sim_ls_s *ls);
 void ras_setup(sim_ls_s *ls) {
   ras_data &R = ls->ras;
   cudaStream_t s = ls->st;
@@ -289,6 +338,7 @@ void ras_setup(sim_ls_s *ls) {
     k_ras_factor<double><<<R.nsub, 128, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.frp.p, R.fci.p, R.fdiag.p, fsrc.p,
                                                 ls->val.p, R.lvl_rows.p, R.nlev.p, R.lvl_ptr.p, R.fval.p, R.dinv.p);
   RS_LAUNCHED(4);
+  ras_pack(ls);
   RS_CHECK_LAUNCH();
 }
 
@@ -347,22 +397,207 @@ __global__ void k_ras_apply(const int *sub_ptr, const int *ext, const uint8_t *o
   }
 }
 
-template <class T> void ls_ras_apply(sim_ls_s *ls, const T *f, T *x) {
-  ras_data &R = ls->ras;
-  size_t smem = (size_t)R.max_ext * 2 * sizeof(T);
-  static bool attr = false;
-  if (!attr) {
-    RS_CUDA(cudaFuncSetAttribute(k_ras_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    RS_CUDA(cudaFuncSetAttribute(k_ras_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
+// pack the factors of each subdomain into its blob (one block per subdomain)
+template <class T>
+__global__ void k_ras_pack(const int *sub_ptr, const int *lrp_ptr, const int *ext, const uint8_t *owned,
+                           const int *perm, const int *frp, const int *fci, const int *fdiag, const T *fv,
+                           const T *dinv, const int *lvl_rows, const int *nlev, const int *lvl_ptr,
+                           const long long *blob_off, unsigned char *blobs) {
+  int s = blockIdx.x, base = sub_ptr[s], m = sub_ptr[s + 1] - base, pbase = lrp_ptr[s], fbase = base + s;
+  int e = (lrp_ptr[s + 1] - pbase) - m;
+  blob_layout Lb = blob_lay(m, e, 4 * (int)sizeof(T));
+  unsigned char *b = blobs + blob_off[s];
+  int *gidx = (int *)(b + Lb.gidx);
+  uint16_t *rp = (uint16_t *)(b + Lb.rp), *dg = (uint16_t *)(b + Lb.dg);
+  uint16_t *lrow = (uint16_t *)(b + Lb.lrow), *llev = (uint16_t *)(b + Lb.llev);
+  uint16_t *urow = (uint16_t *)(b + Lb.urow), *ulev = (uint16_t *)(b + Lb.ulev);
+  uint16_t *cols = (uint16_t *)(b + Lb.cols);
+  T *vals = (T *)(b + Lb.vals), *dv = (T *)(b + Lb.dinv);
+  const int *pL = lvl_ptr + 2 * (base + s), *pU = pL + (m + 1);
+  const int *rL = lvl_rows + 2 * base, *rU = rL + m;
+  int nL = nlev[2 * s], nU = nlev[2 * s + 1];
+  int nLrows = pL[nL] - pL[1 < nL ? 1 : nL];
+  if (threadIdx.x == 0) {
+    int *hdr = (int *)b;
+    hdr[0] = m; hdr[1] = nLrows; hdr[2] = nL > 1 ? nL - 1 : 0; hdr[3] = nU;
   }
-  bool mixed = sizeof(T) == 4;
-  rs_timed tm(ls, SIM_T_RAS);
-  k_ras_apply<T><<<R.nsub, 256, smem, ls->st>>>(R.sub_ptr.p, R.ext.p, R.owned.p, R.lrp_ptr.p, R.frp.p, R.fci.p,
-                                                R.fdiag.p, R.perm.p, R.lvl_rows.p, R.nlev.p, R.lvl_ptr.p,
-                                                mixed ? (const T *)R.fval32.p : (const T *)R.fval.p,
-                                                mixed ? (const T *)R.dinv32.p : (const T *)R.dinv.p, f, x);
+  for (int pos = threadIdx.x; pos < m; pos += blockDim.x) {
+    int x = perm[base + pos];
+    gidx[pos] = (ext[base + x] << 1) | (owned[base + x] ? 1 : 0);
+    int r0 = frp[fbase + pos], r1 = frp[fbase + pos + 1], qd = fdiag[base + pos] - pbase;
+    rp[pos] = (uint16_t)(r0 - pos);
+    dg[pos] = (uint16_t)(qd - pos);
+    if (pos == m - 1) rp[m] = (uint16_t)(r1 - m);
+    for (int q = r0; q < r1; q++) {
+      if (q == qd) continue;
+      int j = q - pos - (q > qd ? 1 : 0);
+      cols[j] = (uint16_t)fci[pbase + q];
+      const T *src = fv + 4 * (size_t)(pbase + q);
+      vals[4 * j] = src[0]; vals[4 * j + 1] = src[1]; vals[4 * j + 2] = src[2]; vals[4 * j + 3] = src[3];
+    }
+    const T *d = dinv + 4 * (size_t)(base + pos);
+    dv[4 * pos] = d[0]; dv[4 * pos + 1] = d[1]; dv[4 * pos + 2] = d[2]; dv[4 * pos + 3] = d[3];
+  }
+  int l0 = 1 < nL ? pL[1] : 0;
+  for (int r = threadIdx.x; r < nLrows; r += blockDim.x) lrow[r] = (uint16_t)rL[l0 + r];
+  for (int k = threadIdx.x; k < nL; k += blockDim.x) llev[k] = (uint16_t)(pL[k + 1] - l0);
+  for (int r = threadIdx.x; r < m; r += blockDim.x) urow[r] = (uint16_t)rU[r];
+  for (int k = threadIdx.x; k <= nU; k += blockDim.x) ulev[k] = (uint16_t)pU[k];
+}
+
+template <class T> struct v2_t;
+template <> struct v2_t<float> { typedef float2 type; };
+template <> struct v2_t<double> { typedef double2 type; };
+
+// x = R(A)^{-1} f with the subdomain's packed factors held in shared
+// memory: one block per subdomain copies its blob with 16-byte loads,
+// gathers the extended right-hand side, runs the level-scheduled L and U
+// solves on chip and writes (or adds) the owned rows.
+template <class T, class Tin, bool ACC>
+__global__ void __launch_bounds__(128) k_ras_apply_smem(const long long *blob_off, const unsigned char *blobs,
+                                                        const Tin *__restrict__ f, T *__restrict__ x) {
+  extern __shared__ uint4 sm4[];
+  typedef typename v2_t<T>::type T2;
+  int s = blockIdx.x;
+  const unsigned char *b = blobs + blob_off[s];
+  int total = (int)(blob_off[s + 1] - blob_off[s]);
+  const uint4 *src = reinterpret_cast<const uint4 *>(b);
+  for (int i = threadIdx.x; i < total / 16; i += blockDim.x) sm4[i] = __ldg(src + i);
+  __syncthreads();
+  const unsigned char *sb = reinterpret_cast<const unsigned char *>(sm4);
+  const int *hdr = (const int *)sb;
+  int m = hdr[0], nLrows = hdr[1], nLl = hdr[2], nU = hdr[3];
+  (void)nLrows;
+  int e_count = 0;
+  blob_layout Lb = blob_lay(m, 0, 4 * (int)sizeof(T));
+  const uint16_t *rp = (const uint16_t *)(sb + Lb.rp);
+  e_count = rp[m];
+  Lb = blob_lay(m, e_count, 4 * (int)sizeof(T));
+  const int *gidx = (const int *)(sb + Lb.gidx);
+  const uint16_t *dg = (const uint16_t *)(sb + Lb.dg);
+  const uint16_t *lrow = (const uint16_t *)(sb + Lb.lrow), *llev = (const uint16_t *)(sb + Lb.llev);
+  const uint16_t *urow = (const uint16_t *)(sb + Lb.urow), *ulev = (const uint16_t *)(sb + Lb.ulev);
+  const uint16_t *cols = (const uint16_t *)(sb + Lb.cols);
+  const T *vals = (const T *)(sb + Lb.vals), *dv = (const T *)(sb + Lb.dinv);
+  T2 *y = reinterpret_cast<T2 *>(sm4 + total / 16);
+  for (int pos = threadIdx.x; pos < m; pos += blockDim.x) {
+    int g = gidx[pos] >> 1;
+    T2 v; v.x = (T)f[2 * (size_t)g]; v.y = (T)f[2 * (size_t)g + 1];
+    y[pos] = v;
+  }
+  __syncthreads();
+  for (int k = 0; k < nLl; k++) {
+    for (int r = llev[k] + threadIdx.x; r < llev[k + 1]; r += blockDim.x) {
+      int i = lrow[r];
+      T2 a = y[i];
+      for (int q = rp[i]; q < dg[i]; q++) {
+        const T *B = vals + 4 * q; T2 c = y[cols[q]];
+        a.x -= B[0] * c.x + B[1] * c.y; a.y -= B[2] * c.x + B[3] * c.y;
+      }
+      y[i] = a;
+    }
+    __syncthreads();
+  }
+  for (int k = 0; k < nU; k++) {
+    for (int r = ulev[k] + threadIdx.x; r < ulev[k + 1]; r += blockDim.x) {
+      int i = urow[r];
+      T2 a = y[i];
+      for (int q = dg[i]; q < rp[i + 1]; q++) {
+        const T *B = vals + 4 * q; T2 c = y[cols[q]];
+        a.x -= B[0] * c.x + B[1] * c.y; a.y -= B[2] * c.x + B[3] * c.y;
+      }
+      const T *D = dv + 4 * i;
+      T2 o; o.x = D[0] * a.x + D[1] * a.y; o.y = D[2] * a.x + D[3] * a.y;
+      y[i] = o;
+    }
+    __syncthreads();
+  }
+  for (int pos = threadIdx.x; pos < m; pos += blockDim.x) {
+    int gi = gidx[pos];
+    if (gi & 1) {
+      size_t g = (size_t)(gi >> 1);
+      T2 v = y[pos];
+      if (ACC) { x[2 * g] += v.x; x[2 * g + 1] += v.y; }
+      else { x[2 * g] = v.x; x[2 * g + 1] = v.y; }
+    }
+  }
+}
+
+void ras_pack(sim_ls_s *ls) {
+  ras_data &R = ls->ras;
+  if (!R.smem_path) return;
+  if (ls->o.precision == SIM_PREC_MIXED)
+    k_ras_pack<float><<<R.nsub, 128, 0, ls->st>>>(R.sub_ptr.p, R.lrp_ptr.p, R.ext.p, R.owned.p, R.perm.p, R.frp.p,
+                                                  R.fci.p, R.fdiag.p, R.fval32.p, R.dinv32.p, R.lvl_rows.p,
+                                                  R.nlev.p, R.lvl_ptr.p, R.blob_off.p, R.blob.p);
+  else
+    k_ras_pack<double><<<R.nsub, 128, 0, ls->st>>>(R.sub_ptr.p, R.lrp_ptr.p, R.ext.p, R.owned.p, R.perm.p, R.frp.p,
+                                                   R.fci.p, R.fdiag.p, R.fval.p, R.dinv.p, R.lvl_rows.p,
+                                                   R.nlev.p, R.lvl_ptr.p, R.blob_off.p, R.blob.p);
   RS_LAUNCHED(1);
 }
-template void ls_ras_apply<double>(sim_ls_s *, const double *, double *);
-template void ls_ras_apply<float>(sim_ls_s *, const float *, float *);
+
+template <class T, class Tin>
+__global__ void k_cast_acc(size_t m, const Tin *a, T *b, bool acc) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < m) b[i] = acc ? b[i] + (T)a[i] : (T)a[i];
+}
+
+template <class T, class Tin> void ls_ras_apply(sim_ls_s *ls, const Tin *f, T *x, bool accumulate) {
+  ras_data &R = ls->ras;
+  cudaStream_t s = ls->st;
+  if (R.smem_path) {
+    static bool attr = false;
+    if (!attr) {
+      RS_CUDA(cudaFuncSetAttribute(k_ras_apply_smem<float, float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RAS_SMEM_BUDGET));
+      RS_CUDA(cudaFuncSetAttribute(k_ras_apply_smem<float, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RAS_SMEM_BUDGET));
+      RS_CUDA(cudaFuncSetAttribute(k_ras_apply_smem<float, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RAS_SMEM_BUDGET));
+      RS_CUDA(cudaFuncSetAttribute(k_ras_apply_smem<float, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RAS_SMEM_BUDGET));
+      RS_CUDA(cudaFuncSetAttribute(k_ras_apply_smem<double, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RAS_SMEM_BUDGET));
+      RS_CUDA(cudaFuncSetAttribute(k_ras_apply_smem<double, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RAS_SMEM_BUDGET));
+      attr = true;
+    }
+    rs_timed tm(ls, SIM_T_RAS);
+    if (accumulate)
+      k_ras_apply_smem<T, Tin, true><<<R.nsub, 128, R.smem_bytes, s>>>(R.blob_off.p, R.blob.p, f, x);
+    else
+      k_ras_apply_smem<T, Tin, false><<<R.nsub, 128, R.smem_bytes, s>>>(R.blob_off.p, R.blob.p, f, x);
+    RS_LAUNCHED(1);
+    return;
+  }
+  // global-memory path (subdomains too large for shared memory)
+  size_t nu = 2 * (size_t)ls->nb;
+  static thread_local dbuf<T> tin, tout;
+  const T *fin = reinterpret_cast<const T *>(f);
+  if (sizeof(Tin) != sizeof(T)) {
+    tin.ensure(nu);
+    k_cast_acc<T, Tin><<<grid_for(nu, 256), 256, 0, s>>>(nu, f, tin.p, false);
+    RS_LAUNCHED(1);
+    fin = tin.p;
+  }
+  T *xout = x;
+  if (accumulate) { tout.ensure(nu); xout = tout.p; }
+  size_t smem = (size_t)R.max_ext * 2 * sizeof(T);
+  static bool attr2 = false;
+  if (!attr2) {
+    RS_CUDA(cudaFuncSetAttribute(k_ras_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    RS_CUDA(cudaFuncSetAttribute(k_ras_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr2 = true;
+  }
+  bool mixed = sizeof(T) == 4;
+  {
+    rs_timed tm(ls, SIM_T_RAS);
+    k_ras_apply<T><<<R.nsub, 256, smem, s>>>(R.sub_ptr.p, R.ext.p, R.owned.p, R.lrp_ptr.p, R.frp.p, R.fci.p,
+                                             R.fdiag.p, R.perm.p, R.lvl_rows.p, R.nlev.p, R.lvl_ptr.p,
+                                             mixed ? (const T *)R.fval32.p : (const T *)R.fval.p,
+                                             mixed ? (const T *)R.dinv32.p : (const T *)R.dinv.p, fin, xout);
+    RS_LAUNCHED(1);
+  }
+  if (accumulate) {
+    k_cast_acc<T, T><<<grid_for(nu, 256), 256, 0, s>>>(nu, xout, x, true);
+    RS_LAUNCHED(1);
+  }
+}
+template void ls_ras_apply<double, double>(sim_ls_s *, const double *, double *, bool);
+template void ls_ras_apply<float, float>(sim_ls_s *, const float *, float *, bool);
+template void ls_ras_apply<float, double>(sim_ls_s *, const double *, float *, bool);

@@ -50,21 +50,29 @@ __device__ __forceinline__ double corey(double x, double e) {
   return pow(x, e);
 }
 
+// Values that decide an integer (the upstream cell via the potential, the
+// relative-permeability clamp, the producer cut-off via the density) are
+// formed with round-to-nearest operations in the order of the plain
+// formulas, so equal inputs give equal decisions in any implementation that
+// evaluates the same formulas in IEEE arithmetic.
+__device__ __forceinline__ double rho_of(const fluid_c &f, int a, double p) {
+  return mul_rn(f.rho_ref[a], add_rn(1.0, mul_rn(f.c_f[a], sub_rn(p, f.p_ref))));
+}
 __device__ __forceinline__ void cell_props(const fluid_c &f, double phir, double z, double p, double sw, cprops &P) {
   double dp = p - f.p_ref;
   P.phi = phir * (1.0 + f.c_r * dp);
   P.dphi = phir * f.c_r;
-  double span = 1.0 - f.swc - f.sor;
-  double sh = (sw - f.swc) / span, dsh = 1.0 / span;
+  double span = sub_rn(sub_rn(1.0, f.swc), f.sor);
+  double sh = div_rn(sub_rn(sw, f.swc), span), dsh = 1.0 / span;
   if (sh < 0.0) { sh = 0.0; dsh = 0.0; } else if (sh > 1.0) { sh = 1.0; dsh = 0.0; }
   P.kr[0] = f.krw_max * corey(sh, f.nw);
   P.dkr[0] = f.krw_max * f.nw * corey(sh, f.nw - 1.0) * dsh;
   P.kr[1] = f.kro_max * corey(1.0 - sh, f.no);
   P.dkr[1] = -f.kro_max * f.no * corey(1.0 - sh, f.no - 1.0) * dsh;
-  double gz5 = f.g * z * RS_PA2BAR;
+  double gz5 = mul_rn(mul_rn(f.g, z), RS_PA2BAR);
 #pragma unroll
   for (int a = 0; a < 2; a++) {
-    P.rho[a] = f.rho_ref[a] * (1.0 + f.c_f[a] * dp);
+    P.rho[a] = rho_of(f, a, p);
     P.drho[a] = f.rho_ref[a] * f.c_f[a];
     P.mu[a] = f.mu_ref[a] + f.c_mu[a] * dp;
     P.dmu[a] = f.c_mu[a];
@@ -72,7 +80,7 @@ __device__ __forceinline__ void cell_props(const fluid_c &f, double phir, double
     P.m[a] = P.rho[a] * P.kr[a] * imu;
     P.dmp[a] = P.drho[a] * P.kr[a] * imu - P.rho[a] * P.kr[a] * P.dmu[a] * imu * imu;
     P.dms[a] = P.rho[a] * P.dkr[a] * imu;
-    P.pot[a] = p - P.rho[a] * gz5;
+    P.pot[a] = sub_rn(p, mul_rn(P.rho[a], gz5));
     P.dpot[a] = 1.0 - P.drho[a] * gz5;
   }
 }
@@ -183,11 +191,11 @@ k_assemble(int nx, int ny, int nz, fluid_c f, double top, double dz, double vol_
   for (int a2 = cpp[c]; a2 < cpp[c + 1]; a2++) {
     int q = cpi[a2], w = pwell[q];
     double wi = pwi[q];
-    double dz5 = f.g * (z - wzref[w]) * RS_PA2BAR;
+    double dz5 = mul_rn(mul_rn(f.g, sub_rn(z, wzref[w])), RS_PA2BAR);
     double W[4] = {0, 0, 0, 0};
     for (int a = 0; a < 2; a++) {
       int e = 1 - a;
-      double dd = (pbh[w] - pc) + P.rho[a] * dz5, dd_dp = -1.0 + P.drho[a] * dz5;
+      double dd = add_rn(sub_rn(pbh[w], pc), mul_rn(P.rho[a], dz5)), dd_dp = -1.0 + P.drho[a] * dz5;
       double q_ = 0, dqdp = 0, dqds = 0, dqdb = 0;
       if (wkind[w] == SIM_PROD) {
         if (dd <= 0.0) {
@@ -234,8 +242,8 @@ __global__ void k_wells(int n, int nw, fluid_c f, double top, double dz, int nxy
       cprops P;
       double z = depth(top, dz, c / nxy);
       cell_props(f, phi[c], z, p[c], s[c], P);
-      double dz5 = f.g * (z - wzref[w]) * RS_PA2BAR;
-      double dd = (pbh[w] - p[c]) + P.rho[0] * dz5, dd_dp = -1.0 + P.drho[0] * dz5;
+      double dz5 = mul_rn(mul_rn(f.g, sub_rn(z, wzref[w])), RS_PA2BAR);
+      double dd = add_rn(sub_rn(pbh[w], p[c]), mul_rn(P.rho[0], dz5)), dd_dp = -1.0 + P.drho[0] * dz5;
       double q_ = 0, dqdp = 0, dqds = 0, dqdb = 0;
       if (wkind[w] == SIM_PROD) {
         if (dd <= 0.0) { q_ = pwi[q] * P.m[0] * dd; dqdp = pwi[q] * (P.dmp[0] * dd + P.m[0] * dd_dp);
@@ -323,20 +331,20 @@ __global__ void k_hydrostatic(int n, int nxy, fluid_c f, double top, double dz, 
                               double *s) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
-  double G0 = f.g * top * RS_PA2BAR;
-  double rho0 = f.rho_ref[1] * (1.0 + f.c_f[1] * (p_datum - f.p_ref));
-  double pot = p_datum - rho0 * G0;
-  double G = f.g * depth(top, dz, c / nxy) * RS_PA2BAR;
-  double a = 1.0 - f.rho_ref[1] * f.c_f[1] * G;
-  double r = pot + f.rho_ref[1] * (1.0 - f.c_f[1] * f.p_ref) * G;
-  p[c] = r / a;
+  double G0 = mul_rn(mul_rn(f.g, top), RS_PA2BAR);
+  double rho0 = rho_of(f, 1, p_datum);
+  double pot = sub_rn(p_datum, mul_rn(rho0, G0));
+  double G = mul_rn(mul_rn(f.g, depth(top, dz, c / nxy)), RS_PA2BAR);
+  double a = sub_rn(1.0, mul_rn(mul_rn(f.rho_ref[1], f.c_f[1]), G));
+  double r = add_rn(pot, mul_rn(mul_rn(f.rho_ref[1], sub_rn(1.0, mul_rn(f.c_f[1], f.p_ref))), G));
+  p[c] = div_rn(r, a);
   s[c] = sw0;
 }
 __global__ void k_init_pb(int nw, const int *wctrl, const double *wtarget, const int *wpptr, const int *pcell,
                           const double *p, double *pb) {
   int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= nw) return;
-  pb[w] = wctrl[w] == SIM_BHP ? wtarget[w] : p[pcell[wpptr[w]]] + 10.0;
+  pb[w] = wctrl[w] == SIM_BHP ? wtarget[w] : add_rn(p[pcell[wpptr[w]]], 10.0);
 }
 
 // ------------------------------------------------------------- host side --
@@ -768,11 +776,11 @@ extern "C" sim_status sim_ls_apply(sim_ls_t ls, int op, const double *x, double 
     if (mixed) {
       dbuf<float> a, b2; a.alloc(nu); b2.alloc(nu);
       k_cast_d2f_<<<grid_for(nu, 256), 256, 0, s>>>(nu, xin.p, a.p);
-      ls_ras_apply<float>(ls, a.p, b2.p);
+      ls_ras_apply<float, float>(ls, a.p, b2.p, false);
       k_cast_f2d<<<grid_for(nu, 256), 256, 0, s>>>(nu, b2.p, yout.p);
       RS_LAUNCHED(2);
       RS_CUDA(cudaStreamSynchronize(s));
-    } else ls_ras_apply<double>(ls, xin.p, yout.p);
+    } else ls_ras_apply<double, double>(ls, xin.p, yout.p, false);
   } else if (op == SIM_OP_VCYCLE) {
     amg_level &L0 = ls->amg.lev[0];
     if (mixed) {

@@ -37,7 +37,7 @@ def test_default_options_and_error_path_without_gpu():
     """sim_default_options and argument validation run on the host only."""
     import paper_1701_06254_gb300 as R
     o = R.make_options()
-    assert o.restart == 50 and o.max_lin == 100 and o.tile_x == 8 and o.amg_coarse_max == 128
+    assert o.restart == 50 and o.max_lin == 100 and o.tile_x == 4 and o.amg_coarse_max == 128
     assert abs(o.amg_theta - 0.25) < 1e-15 and o.decoupling == R.DEC_ABF
     L = R.lib()
     h = ctypes.c_void_p()
