@@ -167,6 +167,8 @@ def main():
     ap.add_argument("--roofline", default="ras", choices=["ras", "spmv64", "spmv_prec"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--breakdown", action="store_true",
+                    help="time every kernel family with CUDA events (adds event records between launches)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -193,7 +195,7 @@ def main():
     for _ in range(args.warmup):
         sim.advance(1)
     fam = {"ras": R.T_RAS, "spmv64": R.T_SPMV64, "spmv_prec": R.T_SPMV_PREC}[args.roofline]
-    sim.ls.kernel_timer(fam)
+    sim.ls.kernel_timer(range(1, R.T_NFAMILIES) if args.breakdown else [fam])
     st0 = sim.stats()
     clocks = Clocks(local)
     torch.cuda.synchronize()
@@ -216,7 +218,13 @@ def main():
         ms = float(t.item())
         dist.barrier()
     st1 = sim.stats()
-    nk, kms = sim.ls.kernel_time()
+    nk, kms = sim.ls.kernel_time(fam)
+    breakdown = None
+    if args.breakdown:
+        breakdown = {}
+        for f, name in R.T_NAMES.items():
+            n_, t_ = sim.ls.kernel_time(f)
+            breakdown[name] = {"launches": n_, "ms_per_step": t_ / args.steps, "share": t_ / ms}
     value = world * case.n * args.steps / (ms / 1e3)
     newton_per_step = (st1["newton"] - st0["newton"]) / args.steps
     its_per_newton = (st1["linear_its"] - st0["linear_its"]) / max(1, st1["newton"] - st0["newton"])
@@ -281,6 +289,8 @@ def main():
                        "l2": "working set larger than L2 (no flush needed)",
                        "newton_per_step": newton_per_step, "fgmres_its_per_newton": its_per_newton},
             "roofline": roof, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
+            "phases_ms_per_step": {k: (st1[k] - st0[k]) / args.steps for k in ("ms_assemble", "ms_setup", "ms_solve")},
+            "kernel_breakdown": breakdown,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -95,6 +95,7 @@ typedef struct {
   int max_cuts;        /* time-step halvings allowed per step                      */
   double dt;           /* time step, days                                          */
   void *cuda_stream;   /* cudaStream_t or NULL                                     */
+  double sat_chop;     /* max |ds_w| applied per Newton update, 0 = full step      */
 } sim_options;
 
 /* Statistics, cumulative since creation. */
@@ -110,7 +111,8 @@ typedef struct sim_ls_s *sim_ls_t;
 
 /* Fill *o with the defaults: FP64, ABF, reordering on, standard Newton,
  * newton_tol 1e-8, lin_tol 1e-8, max_newton 20, restart 50, max_lin 100,
- * 4x4 tiles, theta 0.25, 25 levels, coarsest <= 128 rows, 6 cuts, dt 1. */
+ * 4x4 tiles, theta 0.25, 25 levels, coarsest <= 128 rows, 6 cuts, dt 1,
+ * no saturation chop. */
 void sim_default_options(sim_options *o);
 
 /* Create a simulator (copies everything).  Builds transmissibilities,
@@ -218,13 +220,16 @@ enum {
 };
 sim_status sim_ls_export(sim_ls_t ls, int what, int index, void *dst, size_t bytes, size_t *needed);
 
-/* Per-kernel timing (CUDA events on the library stream) for one named
- * kernel family: 0 off, else SIM_T_* below.  sim_kernel_time returns the
- * number of timed launches and their summed milliseconds. */
+/* Per-kernel-family timing with CUDA events recorded on the library stream
+ * around each launch of the enabled families.  mask: bit (1 << SIM_T_*) per
+ * family, 0 = off; enabling resets the counters.  sim_kernel_time returns,
+ * for one family, the number of timed launches and their summed
+ * milliseconds. */
 enum { SIM_T_NONE = 0, SIM_T_SPMV64 = 1, SIM_T_SPMV_PREC = 2, SIM_T_RAS = 3, SIM_T_VCYCLE = 4,
-       SIM_T_ORTHO = 5, SIM_T_ASSEMBLE = 6 };
-sim_status sim_kernel_timer(sim_ls_t ls, int which);
-sim_status sim_kernel_time(sim_ls_t ls, long long *launches, double *ms);
+       SIM_T_ORTHO = 5, SIM_T_ASSEMBLE = 6, SIM_T_AMG_SETUP = 7, SIM_T_RAS_SETUP = 8, SIM_T_DECOUPLE = 9,
+       SIM_T_NFAMILIES = 10 };
+sim_status sim_kernel_timer(sim_ls_t ls, unsigned mask);
+sim_status sim_kernel_time(sim_ls_t ls, int which, long long *launches, double *ms);
 
 /* Number of this library's kernel launches issued so far (all handles). */
 long long sim_launch_count(void);

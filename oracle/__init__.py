@@ -23,7 +23,7 @@ _lib = None
 DEFAULT_OPTS = dict(decoupling=1, reorder=1, newton=0, newton_tol=1e-8, lin_tol=1e-8,
                     max_newton=20, restart=50, max_lin=100, tile_x=4, tile_y=4,
                     amg_theta=0.25, amg_max_levels=25, amg_coarse_max=128,
-                    seed=0x5EED, max_cuts=6, dt=1.0)
+                    seed=0x5EED, max_cuts=6, dt=1.0, sat_chop=0.0)
 
 
 def build(force: bool = False) -> str:
@@ -68,7 +68,7 @@ class Opts(C.Structure):
                 ("max_newton", C.c_int), ("restart", C.c_int), ("max_lin", C.c_int),
                 ("tile_x", C.c_int), ("tile_y", C.c_int), ("amg_theta", C.c_double),
                 ("amg_max_levels", C.c_int), ("amg_coarse_max", C.c_int),
-                ("seed", C.c_uint64), ("max_cuts", C.c_int), ("dt", C.c_double)]
+                ("seed", C.c_uint64), ("max_cuts", C.c_int), ("dt", C.c_double), ("sat_chop", C.c_double)]
 
 
 def make_opts(**kw) -> Opts:
@@ -128,6 +128,7 @@ def _sig(lib):
         "or_potential_rank": (None, [C.c_int, _dp, _ip, _ip]),
         "or_splitmix64": (C.c_uint64, [C.c_uint64]),
         "or_forcing": (C.c_double, [C.c_int, C.c_double, C.c_double, C.c_double]),
+        "or_reorth_count": (C.c_long, []),
     }
     for name, (res, args) in s.items():
         f = getattr(lib, name)
@@ -339,7 +340,7 @@ class Sim:
         self._lib = lib()
         self.case = case
         o = dict(newton=0 if case.newton == "standard" else 1, newton_tol=case.newton_tol,
-                 lin_tol=case.lin_tol, dt=case.dt)
+                 lin_tol=case.lin_tol, dt=case.dt, sat_chop=case.sat_chop)
         o.update(opts)
         self.opts = make_opts(**o)
         g, fl, wells, keep = _case_structs(case)

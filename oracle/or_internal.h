@@ -50,6 +50,7 @@ typedef struct {
   uint64_t seed;
   int max_cuts;
   double dt;
+  double sat_chop;       /* max |ds_w| per Newton update, 0 = full step */
 } or_opts;
 
 /* ---- compressed sparse rows (scalar) ---- */

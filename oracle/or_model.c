@@ -416,9 +416,14 @@ int or_sim_newton(or_sim *S, int *iters)
     S->n_lin += its; S->last_its = its; S->last_relres = rel;
     if (rc == 2) { *iters = l; return 2; }
     bprev = bn; rprev = rel * bn;
-    for (int c = 0; c < S->n; c++) {           /* x^{l+1} = x^l + y (full step) */
+    for (int c = 0; c < S->n; c++) {           /* x^{l+1} = x^l + y */
+      double ds = S->y[2 * c + 1];
+      if (S->o.sat_chop > 0.0) {                 /* optional saturation chop */
+        if (ds > S->o.sat_chop) ds = S->o.sat_chop;
+        if (ds < -S->o.sat_chop) ds = -S->o.sat_chop;
+      }
       S->p[c] += S->y[2 * c];
-      S->s[c] += S->y[2 * c + 1];
+      S->s[c] += ds;
       if (S->s[c] < 0.0) S->s[c] = 0.0;
       if (S->s[c] > 1.0) S->s[c] = 1.0;
     }

@@ -365,11 +365,13 @@ void or_cpr_apply(or_lsys *ls, const double *f, double *x)
 /* ---------------- flexible GMRES(m), right preconditioned ---------------- */
 
 static double dot(const double *a, const double *b, int m) { double s = 0; for (int i = 0; i < m; i++) s += a[i] * b[i]; return s; }
+static long S_reorth = 0;   /* second Gram-Schmidt passes taken (statistics) */
+long or_reorth_count(void) { return S_reorth; }
 
 /* Solves the (decoupled) system A y = b from y = 0 until
    ||b - A y||_2 <= tol ||b||_2 (eq. 24) or max_lin iterations.  Arnoldi
-   with classical Gram-Schmidt applied twice; Givens rotations on the
-   Hessenberg matrix.  Returns 0 (converged), 1 (iteration limit) or
+   with classical Gram-Schmidt and a conditional second pass; Givens
+   rotations on the Hessenberg matrix.  Returns 0 (converged), 1 (iteration limit) or
    2 (non-finite value). */
 int or_lsys_solve(or_lsys *ls, double tol, double *y, int *its_out, double *relres)
 {
@@ -391,12 +393,21 @@ int or_lsys_solve(or_lsys *ls, double tol, double *y, int *its_out, double *relr
       double *vj = &V[(size_t)j * nu], *zj = &Z[(size_t)j * nu];
       or_cpr_apply(ls, vj, zj);
       or_bsr_mv(ls, zj, w);
+      /* classical Gram-Schmidt; a second pass only when the first one
+         removed most of w (||w_1|| < ||w|| / sqrt(2): Daniel, Gragg,
+         Kaufman and Stewart's criterion) */
+      double wn2 = dot(w, w, nu);
       for (int k = 0; k <= j; k++) h[k] = dot(&V[(size_t)k * nu], w, nu);
       for (int i = 0; i < nu; i++) { double s = 0; for (int k = 0; k <= j; k++) s += h[k] * V[(size_t)k * nu + i]; w[i] -= s; }
-      for (int k = 0; k <= j; k++) h2[k] = dot(&V[(size_t)k * nu], w, nu);
-      for (int i = 0; i < nu; i++) { double s = 0; for (int k = 0; k <= j; k++) s += h2[k] * V[(size_t)k * nu + i]; w[i] -= s; }
-      for (int k = 0; k <= j; k++) h[k] += h2[k];
-      double hn = sqrt(dot(w, w, nu));
+      double hn2 = dot(w, w, nu);
+      if (hn2 < 0.5 * wn2) {
+        for (int k = 0; k <= j; k++) h2[k] = dot(&V[(size_t)k * nu], w, nu);
+        for (int i = 0; i < nu; i++) { double s = 0; for (int k = 0; k <= j; k++) s += h2[k] * V[(size_t)k * nu + i]; w[i] -= s; }
+        for (int k = 0; k <= j; k++) h[k] += h2[k];
+        hn2 = dot(w, w, nu);
+        S_reorth++;
+      }
+      double hn = sqrt(hn2);
       if (hn != hn) { rc = 2; goto out; }
       if (hn > 0.0) for (int i = 0; i < nu; i++) V[(size_t)(j + 1) * nu + i] = w[i] / hn;
       /* apply the previous rotations to column j, then a new one */

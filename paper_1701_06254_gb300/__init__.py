@@ -21,6 +21,9 @@ PREC_FP64, PREC_MIXED = 0, 1
 DEC_NONE, DEC_ABF, DEC_QI = 0, 1, 2
 OP_SPMV, OP_RAS, OP_VCYCLE, OP_CPR = 0, 1, 2, 3
 T_NONE, T_SPMV64, T_SPMV_PREC, T_RAS, T_VCYCLE, T_ORTHO, T_ASSEMBLE = 0, 1, 2, 3, 4, 5, 6
+T_AMG_SETUP, T_RAS_SETUP, T_DECOUPLE, T_NFAMILIES = 7, 8, 9, 10
+T_NAMES = {1: "spmv64", 2: "spmv_prec", 3: "ras_apply", 4: "vcycle", 5: "ortho", 6: "assemble",
+           7: "amg_setup", 8: "ras_setup", 9: "decouple"}
 X_VALS, X_RHS, X_SOLUTION, X_ROWPTR, X_COLS, X_KEY = 0, 1, 2, 3, 4, 5
 X_AMG_SIZES, X_AMG_RP, X_AMG_CI, X_AMG_V, X_AMG_CF, X_AMG_PRP, X_AMG_PCI, X_AMG_PV = 10, 11, 12, 13, 14, 15, 16, 17
 X_RAS_SIZES, X_RAS_EXT, X_RAS_LEVELS = 20, 21, 22
@@ -61,7 +64,8 @@ class Options(C.Structure):
                 ("newton_tol", C.c_double), ("lin_tol", C.c_double), ("max_newton", C.c_int),
                 ("restart", C.c_int), ("max_lin", C.c_int), ("tile_x", C.c_int), ("tile_y", C.c_int),
                 ("amg_theta", C.c_double), ("amg_max_levels", C.c_int), ("amg_coarse_max", C.c_int),
-                ("seed", C.c_uint64), ("max_cuts", C.c_int), ("dt", C.c_double), ("cuda_stream", C.c_void_p)]
+                ("seed", C.c_uint64), ("max_cuts", C.c_int), ("dt", C.c_double), ("cuda_stream", C.c_void_p),
+                ("sat_chop", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -112,8 +116,8 @@ def lib():
             "sim_ls_solve": (I, [P, D, P, C.POINTER(I), C.POINTER(D)]),
             "sim_ls_apply": (I, [P, I, P, P]),
             "sim_ls_export": (I, [P, I, I, P, C.c_size_t, C.POINTER(C.c_size_t)]),
-            "sim_kernel_timer": (I, [P, I]),
-            "sim_kernel_time": (I, [P, C.POINTER(C.c_longlong), C.POINTER(D)]),
+            "sim_kernel_timer": (I, [P, C.c_uint]),
+            "sim_kernel_time": (I, [P, I, C.POINTER(C.c_longlong), C.POINTER(D)]),
             "sim_launch_count": (C.c_longlong, []),
             "sim_last_error": (C.c_char_p, []),
         }
@@ -144,7 +148,8 @@ def launch_count():
 
 
 OPT_KEYS = ("precision", "decoupling", "reorder", "newton", "newton_tol", "lin_tol", "max_newton", "restart",
-            "max_lin", "tile_x", "tile_y", "amg_theta", "amg_max_levels", "amg_coarse_max", "seed", "max_cuts", "dt")
+            "max_lin", "tile_x", "tile_y", "amg_theta", "amg_max_levels", "amg_coarse_max", "seed", "max_cuts", "dt",
+            "sat_chop")
 
 
 def make_options(stream=None, **kw):
@@ -244,12 +249,16 @@ class LinearSystem:
         v = self.export(X_RAS_SIZES, s, np.int32)
         return int(v[0]), int(v[1]), int(v[2])
 
-    def kernel_timer(self, which):
-        _check(self._L.sim_kernel_timer(self.h, which))
+    def kernel_timer(self, families):
+        """Enable CUDA-event timing for the given T_* families (iterable)."""
+        mask = 0
+        for f in families:
+            mask |= 1 << f
+        _check(self._L.sim_kernel_timer(self.h, mask))
 
-    def kernel_time(self):
+    def kernel_time(self, which):
         n, ms = C.c_longlong(), C.c_double()
-        _check(self._L.sim_kernel_time(self.h, C.byref(n), C.byref(ms)))
+        _check(self._L.sim_kernel_time(self.h, which, C.byref(n), C.byref(ms)))
         return n.value, ms.value
 
 
@@ -275,7 +284,7 @@ class Sim:
         self._L = lib()
         self.case = case
         o = dict(newton=0 if case.newton == "standard" else 1, newton_tol=case.newton_tol, lin_tol=case.lin_tol,
-                 dt=case.dt)
+                 dt=case.dt, sat_chop=case.sat_chop)
         o.update(opts)
         self.opts = make_options(stream, **o)
         g, fl, wells, keep = _case_structs(case)

@@ -91,7 +91,7 @@ struct rs_opts {
   int max_levels, coarse_max;
   uint64_t seed;
   int max_cuts;
-  double dt;
+  double dt, sat_chop;
 };
 rs_opts rs_opts_from(const sim_options *o);
 
@@ -181,18 +181,19 @@ struct sim_ls_s {
   dbuf<float> x32a, x32b, x32c; // CPR work (FP32)
   double *hpin = nullptr;       // pinned host scalars
   bool have_setup = false;
-  // timing
-  int timer_which = 0;
-  long long timer_launches = 0;
-  double timer_ms = 0;
+  // timing: events in pairs, the family of each pair in ev_fam
+  unsigned timer_mask = 0;
+  long long timer_launches[SIM_T_NFAMILIES] = {0};
+  double timer_ms[SIM_T_NFAMILIES] = {0};
   std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_fam;
   int ev_used = 0;
   void timer_flush();
   ~sim_ls_s();
 };
 
 struct rs_timed {                       // brackets launches of one kernel family
-  sim_ls_s *ls; bool on;
+  sim_ls_s *ls; bool on; int fam;
   rs_timed(sim_ls_s *l, int which);
   ~rs_timed();
 };

@@ -11,26 +11,27 @@
 #include <cmath>
 
 // ------------------------------------------------------------ timers -----
-rs_timed::rs_timed(sim_ls_s *l, int which) : ls(l), on(l->timer_which == which && which != 0) {
+rs_timed::rs_timed(sim_ls_s *l, int which) : ls(l), on(which > 0 && (l->timer_mask >> which) & 1u), fam(which) {
   if (!on) return;
   if (ls->ev_used + 2 > (int)ls->ev.size()) ls->timer_flush();
   if (ls->ev_used + 2 > (int)ls->ev.size()) {
-    for (int k = 0; k < 64; k++) { cudaEvent_t e; RS_CUDA(cudaEventCreate(&e)); ls->ev.push_back(e); }
+    for (int k = 0; k < 64; k++) { cudaEvent_t e; RS_CUDA(cudaEventCreate(&e)); ls->ev.push_back(e); ls->ev_fam.push_back(0); }
   }
+  ls->ev_fam[ls->ev_used] = fam;
   RS_CUDA(cudaEventRecord(ls->ev[ls->ev_used], ls->st));
 }
 rs_timed::~rs_timed() {
   if (!on) return;
   cudaEventRecord(ls->ev[ls->ev_used + 1], ls->st);
   ls->ev_used += 2;
-  ls->timer_launches++;
+  ls->timer_launches[fam]++;
 }
 void sim_ls_s::timer_flush() {
   if (!ev_used) return;
   cudaEventSynchronize(ev[ev_used - 1]);
   for (int k = 0; k < ev_used; k += 2) {
     float ms = 0; cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
-    timer_ms += ms;
+    timer_ms[ev_fam[k]] += ms;
   }
   ev_used = 0;
 }
@@ -255,6 +256,7 @@ void ls_init(sim_ls_s *ls, int nx, int ny, int nz, int nw, const int *rp, const 
   ls->x64a.alloc(nu); ls->x64b.alloc(nu);
   if (o.precision == SIM_PREC_MIXED) { ls->x32b.alloc(nu); ls->x32c.alloc(nu); }
   RS_CUDA(cudaHostAlloc((void **)&ls->hpin, 64 * sizeof(double), cudaHostAllocMapped));
+  for (int k = 0; k < 64; k++) ls->hpin[k] = 0.0;
   RS_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -262,6 +264,8 @@ void ls_setup(sim_ls_s *ls) {
   cudaStream_t s = ls->st;
   float *v32 = ls->o.precision == SIM_PREC_MIXED ? ls->val32.p : nullptr;
   unsigned g = grid_for(ls->nb, 128);
+  {
+  rs_timed tm(ls, SIM_T_DECOUPLE);
   if (ls->o.decoupling == SIM_DEC_ABF)
     k_abf<<<g, 128, 0, s>>>(ls->n, ls->nb, ls->rp.p, ls->dpos.p, ls->val.p, ls->b.p, ls->dmat.p, v32);
   else if (ls->o.decoupling == SIM_DEC_QI)
@@ -274,80 +278,93 @@ void ls_setup(sim_ls_s *ls) {
   csr_dev<double> &A0 = ls->amg.lev[0].A;
   k_extract_app<<<grid_for(A0.nnz, 256), 256, 0, s>>>(A0.nnz, ls->app_src.p, ls->val.p, A0.v.p);
   RS_LAUNCHED(1);
+  }
   RS_CHECK_LAUNCH();
-  ras_setup(ls);
-  amg_setup(ls->amg, ls->o, s);
+  { rs_timed tm(ls, SIM_T_RAS_SETUP); ras_setup(ls); }
+  { rs_timed tm(ls, SIM_T_AMG_SETUP); amg_setup(ls->amg, ls->o, s); }
   ls->have_setup = true;
 }
 
 // ------------------------------------------------------------ FGMRES -----
-// Classical Gram-Schmidt, applied twice.  Each pass is one sweep over the
-// rows: a block owns a fixed row range, every thread accumulates its part of
+// Classical Gram-Schmidt with a conditional second pass (Daniel, Gragg,
+// Kaufman and Stewart): the second projection runs only when the first one
+// left ||w_1||^2 < ||w||^2 / 2.  The test is taken on the device; the
+// kernels of the second pass read the flag and return at once when it is
+// clear, so the host never waits on it.  Each pass is one sweep over the
+// rows: a block owns a fixed row range, threads accumulate their part of
 // each dot product, warps reduce with shuffles and the block writes one
 // partial per vector; a second kernel adds the partials in block order, so
-// the result does not depend on scheduling.
+// results do not depend on scheduling.
 #define ORTHO_BS 256
 #define ORTHO_MAXV 64
 static int ortho_blocks(int nu) { int b = (nu + 8191) / 8192; return b < 1 ? 1 : (b > 608 ? 608 : b); }
 
-// mode 0: dots d_k = V_k . w;  mode 1: w -= sum_k h_k V_k, then dots with the new w;
-// mode 2: w -= sum_k h_k V_k, then ||w||^2 (partial index 0).
+// MODE 0: d_k = V_k . w (k < nv) and, if with_norm, d_nv = w . w
+// MODE 2: w -= sum_k h_k V_k, then d_0 = ||w||^2
 template <int MODE>
 __global__ void __launch_bounds__(ORTHO_BS) k_ortho(int nu, int nv, const double *__restrict__ V, double *w,
-                                                    const double *__restrict__ h, double *part) {
-  __shared__ double sred[ORTHO_MAXV][ORTHO_BS / 32];
+                                                    const double *__restrict__ h, double *part, int with_norm,
+                                                    const int *cond) {
+  if (cond && *cond == 0) return;
+  __shared__ double sred[ORTHO_MAXV + 1][ORTHO_BS / 32];
   __shared__ double sh[ORTHO_MAXV];
   int nblk = gridDim.x, chunk = (nu + nblk - 1) / nblk;
   int i0 = blockIdx.x * chunk, i1 = min(nu, i0 + chunk);
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (MODE != 0) { for (int k = threadIdx.x; k < nv; k += blockDim.x) sh[k] = h[k]; __syncthreads(); }
-  if (MODE != 0) {
+  if (MODE == 2) {
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) sh[k] = h[k];
+    __syncthreads();
+    double s2 = 0.0;
     for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       double s = 0.0;
       for (int k = 0; k < nv; k++) s += sh[k] * V[(size_t)k * nu + i];
-      w[i] -= s;
+      double wi = w[i] - s;
+      w[i] = wi;
+      s2 += wi * wi;
     }
-    __syncthreads();
-  }
-  if (MODE == 2) {
-    double s = 0.0;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += w[i] * w[i];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) sred[0][wid] = s;
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    if (lane == 0) sred[0][wid] = s2;
     __syncthreads();
     if (threadIdx.x == 0) { double t = 0; for (int k = 0; k < ORTHO_BS / 32; k++) t += sred[0][k]; part[blockIdx.x] = t; }
-    return;
-  }
-  for (int k = 0; k < (MODE == 2 ? 0 : nv); k++) {
-    double s = 0.0;
-    const double *vk = V + (size_t)k * nu;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += vk[i] * w[i];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) sred[k][wid] = s;
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-    double t = 0; for (int q = 0; q < ORTHO_BS / 32; q++) t += sred[k][q];
-    part[(size_t)k * nblk + blockIdx.x] = t;
+  } else {
+    int nd = nv + (with_norm ? 1 : 0);
+    for (int k = 0; k < nd; k++) {
+      double s = 0.0;
+      const double *vk = k < nv ? V + (size_t)k * nu : w;
+      for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += vk[i] * w[i];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) sred[k][wid] = s;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nd; k += blockDim.x) {
+      double t = 0; for (int q = 0; q < ORTHO_BS / 32; q++) t += sred[k][q];
+      part[(size_t)k * nblk + blockIdx.x] = t;
+    }
   }
 }
-__global__ void k_reduce_parts(int nv, int nblk, const double *part, double *out) {
+__global__ void k_reduce_parts(int nv, int nblk, const double *part, double *out, const int *cond) {
+  if (cond && *cond == 0) return;
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nv) return;
   double t = 0;
   for (int b = 0; b < nblk; b++) t += part[(size_t)k * nblk + b];
   out[k] = t;
 }
+// flag = ||w_1||^2 < ||w||^2 / 2
+__global__ void k_dgks(const double *w2_before, const double *w2_after, int *flag) {
+  *flag = (*w2_after < 0.5 * *w2_before) ? 1 : 0;
+}
 
 // Hessenberg column j: h = h1 + h2, h_{j+1,j} = ||w||; previous Givens
 // rotations, a new one, and the residual estimate |g_{j+1}|.
 // G layout: [0..m*(m+1)) H column-major (m+1 per column), cs[m], sn[m], g[m+1]
-__global__ void k_arnoldi_col(int j, int m, const double *h1, const double *h2, const double *nrm2, double *G,
-                              double *hnorm, volatile double *host) {
+__global__ void k_arnoldi_col(int j, int m, const double *h1, const double *h2, const double *nrm_a,
+                              const double *nrm_b, const int *flag, double *G, double *hnorm, volatile double *host) {
   double *H = G, *cs = G + (size_t)m * (m + 1), *sn = cs + m, *g = sn + m;
   double *col = H + (size_t)j * (m + 1);
-  for (int k = 0; k <= j; k++) col[k] = h1[k] + h2[k];
-  double hn = sqrt(*nrm2);
+  bool re = *flag != 0;
+  for (int k = 0; k <= j; k++) col[k] = re ? h1[k] + h2[k] : h1[k];
+  double hn = sqrt(re ? *nrm_b : *nrm_a);
   *hnorm = hn;
   for (int k = 0; k < j; k++) {
     double t = cs[k] * col[k] + sn[k] * col[k + 1];
@@ -361,6 +378,7 @@ __global__ void k_arnoldi_col(int j, int m, const double *h1, const double *h2, 
   g[j] = cs[j] * g[j];
   host[0] = fabs(g[j + 1]);
   host[1] = hn;
+  host[2] += re ? 1.0 : 0.0;
 }
 __global__ void k_scale(int nu, const double *w, const double *hn, double *v) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -399,10 +417,11 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres) {
   ls->V.ensure((size_t)(m + 1) * nu);
   if (mixed) ls->Z32.ensure((size_t)m * nu); else ls->Z.ensure((size_t)m * nu);
   int nblk = ortho_blocks(nu);
-  ls->partial.ensure((size_t)ORTHO_MAXV * nblk + 8);
-  ls->hbuf.ensure((size_t)(m + 1) * (m + 1) + 4 * (m + 1) + 4 * ORTHO_MAXV + 8);
-  double *G = ls->hbuf.p, *h1 = G + (size_t)(m + 1) * (m + 1) + 3 * (m + 1), *h2 = h1 + ORTHO_MAXV,
-         *nrm = h2 + ORTHO_MAXV, *hn = nrm + 1, *yk = hn + 1;
+  ls->partial.ensure((size_t)(ORTHO_MAXV + 1) * nblk + 8);
+  ls->hbuf.ensure((size_t)(m + 1) * (m + 1) + 4 * (m + 1) + 4 * ORTHO_MAXV + 16);
+  double *G = ls->hbuf.p, *h1 = G + (size_t)(m + 1) * (m + 1) + 3 * (m + 1), *h2 = h1 + ORTHO_MAXV + 1,
+         *nrm = h2 + ORTHO_MAXV, *nrm_b = nrm + 1, *hn = nrm_b + 1, *yk = hn + 1;
+  int *flag = reinterpret_cast<int *>(yk + ORTHO_MAXV);
   volatile double *hp = ls->hpin;
   double *hp_dev;
   RS_CUDA(cudaHostGetDevicePointer((void **)&hp_dev, ls->hpin, 0));
@@ -432,15 +451,18 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres) {
       {
         rs_timed tm(ls, SIM_T_ORTHO);
         int nv = j + 1;
-        k_ortho<0><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, ls->V.p, ls->w.p, nullptr, ls->partial.p);
-        k_reduce_parts<<<1, 64, 0, s>>>(nv, nblk, ls->partial.p, h1);
-        k_ortho<1><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, ls->V.p, ls->w.p, h1, ls->partial.p);
-        k_reduce_parts<<<1, 64, 0, s>>>(nv, nblk, ls->partial.p, h2);
-        k_ortho<2><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, ls->V.p, ls->w.p, h2, ls->partial.p);
-        k_reduce_parts<<<1, 64, 0, s>>>(1, nblk, ls->partial.p, nrm);
-        k_arnoldi_col<<<1, 1, 0, s>>>(j, m, h1, h2, nrm, G, hn, hp_dev);
+        k_ortho<0><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, ls->V.p, ls->w.p, nullptr, ls->partial.p, 1, nullptr);
+        k_reduce_parts<<<1, 96, 0, s>>>(nv + 1, nblk, ls->partial.p, h1, nullptr);     // h1[nv] = ||w||^2
+        k_ortho<2><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, ls->V.p, ls->w.p, h1, ls->partial.p, 0, nullptr);
+        k_reduce_parts<<<1, 32, 0, s>>>(1, nblk, ls->partial.p, nrm, nullptr);
+        k_dgks<<<1, 1, 0, s>>>(h1 + nv, nrm, flag);
+        k_ortho<0><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, ls->V.p, ls->w.p, nullptr, ls->partial.p, 0, flag);
+        k_reduce_parts<<<1, 96, 0, s>>>(nv, nblk, ls->partial.p, h2, flag);
+        k_ortho<2><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, ls->V.p, ls->w.p, h2, ls->partial.p, 0, flag);
+        k_reduce_parts<<<1, 32, 0, s>>>(1, nblk, ls->partial.p, nrm_b, flag);
+        k_arnoldi_col<<<1, 1, 0, s>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, hp_dev);
         k_scale<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->w.p, hn, ls->V.p + (size_t)(j + 1) * nu);
-        RS_LAUNCHED(8);
+        RS_LAUNCHED(11);
       }
       RS_CHECK_LAUNCH();
       RS_CUDA(cudaStreamSynchronize(s));
@@ -455,10 +477,7 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres) {
     if (mixed) k_xupdate<float><<<grid_for(nu, 256), 256, 0, s>>>(nu, jend, yk, ls->Z32.p, ls->y.p);
     else k_xupdate<double><<<grid_for(nu, 256), 256, 0, s>>>(nu, jend, yk, ls->Z.p, ls->y.p);
     RS_LAUNCHED(2);
-    {
-      rs_timed tm(ls, SIM_T_SPMV64);
-      spmv<double, double, double, double>(ls, ls->val.p, ls->y.p, ls->b.p, ls->r.p, s);
-    }
+    spmv<double, double, double, double>(ls, ls->val.p, ls->y.p, ls->b.p, ls->r.p, s);   // true residual
     beta = rs_norm2(ls->r.p, nu, s);
     ls->timer_flush();
     if (!std::isfinite(beta)) { rc = 2; break; }

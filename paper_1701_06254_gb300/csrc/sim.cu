@@ -306,11 +306,14 @@ __global__ void k_max_part(int m, const double *part, double *out) {
   *out = mx;
 }
 
-__global__ void k_update(int n, int nw, const double *y, double *p, double *s, double *pb) {
+// x += y (Algorithm 1), with the optional saturation chop, then s_w in [0, 1]
+__global__ void k_update(int n, int nw, double chop, const double *y, double *p, double *s, double *pb) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < n) {
     p[c] += y[2 * (size_t)c];
-    double v = s[c] + y[2 * (size_t)c + 1];
+    double ds = y[2 * (size_t)c + 1];
+    if (chop > 0.0) ds = ds > chop ? chop : (ds < -chop ? -chop : ds);
+    double v = s[c] + ds;
     s[c] = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
   } else if (c < n + nw) {
     pb[c - n] += y[2 * (size_t)c];
@@ -423,7 +426,7 @@ static int s_newton(sim_s *h, int *iters) {
     h->stats.last_its = its; h->stats.last_relres = rel;
     if (rc == 2) { *iters = l; return 2; }
     bprev = bn; rprev = rel * bn;
-    k_update<<<grid_for(h->n + h->nw, 256), 256, 0, h->st>>>(h->n, h->nw, h->ls->y.p, h->p.p, h->s.p, h->pb.p);
+    k_update<<<grid_for(h->n + h->nw, 256), 256, 0, h->st>>>(h->n, h->nw, h->o.sat_chop, h->ls->y.p, h->p.p, h->s.p, h->pb.p);
     RS_LAUNCHED(1);
     h->stats.newton++;
     RS_CUDA(cudaEventRecord(h->e0, h->st));
@@ -651,7 +654,7 @@ extern "C" sim_status sim_newton_step(sim_t h, int *converged, sim_stats *st) {
     int rc = ls_solve(h->ls, h->o.lin_tol, &its, &rel);
     h->stats.linear_its += its; h->stats.linear_solves++; h->stats.last_its = its; h->stats.last_relres = rel;
     if (rc == 2) RS_FAIL(SIM_ERR_NAN, "linear solve produced a non-finite value");
-    k_update<<<grid_for(h->n + h->nw, 256), 256, 0, h->st>>>(h->n, h->nw, h->ls->y.p, h->p.p, h->s.p, h->pb.p);
+    k_update<<<grid_for(h->n + h->nw, 256), 256, 0, h->st>>>(h->n, h->nw, h->o.sat_chop, h->ls->y.p, h->p.p, h->s.p, h->pb.p);
     RS_LAUNCHED(1);
     h->stats.newton++;
   }
@@ -895,18 +898,20 @@ extern "C" sim_status sim_ls_export(sim_ls_t ls, int what, int index, void *dst,
   ABI_END
 }
 
-extern "C" sim_status sim_kernel_timer(sim_ls_t ls, int which) {
+extern "C" sim_status sim_kernel_timer(sim_ls_t ls, unsigned mask) {
   ABI_BEGIN
   if (!ls) RS_FAIL(SIM_ERR_ARG, "NULL handle");
   ls->timer_flush();
-  ls->timer_which = which; ls->timer_launches = 0; ls->timer_ms = 0;
+  ls->timer_mask = mask;
+  for (int k = 0; k < SIM_T_NFAMILIES; k++) { ls->timer_launches[k] = 0; ls->timer_ms[k] = 0; }
   ABI_END
 }
-extern "C" sim_status sim_kernel_time(sim_ls_t ls, long long *launches, double *ms) {
+extern "C" sim_status sim_kernel_time(sim_ls_t ls, int which, long long *launches, double *ms) {
   ABI_BEGIN
-  if (!ls) RS_FAIL(SIM_ERR_ARG, "NULL handle");
+  if (!ls || which < 0 || which >= SIM_T_NFAMILIES) RS_FAIL(SIM_ERR_ARG, "sim_kernel_time: bad argument");
+  RS_CUDA(cudaStreamSynchronize(ls->st));
   ls->timer_flush();
-  if (launches) *launches = ls->timer_launches;
-  if (ms) *ms = ls->timer_ms;
+  if (launches) *launches = ls->timer_launches[which];
+  if (ms) *ms = ls->timer_ms[which];
   ABI_END
 }

@@ -156,6 +156,7 @@ rs_opts rs_opts_from(const sim_options *o) {
   r.tile_x = o->tile_x > 0 ? o->tile_x : 4; r.tile_y = o->tile_y > 0 ? o->tile_y : 4;
   r.theta = o->amg_theta; r.max_levels = o->amg_max_levels < 1 ? 1 : (o->amg_max_levels > 32 ? 32 : o->amg_max_levels);
   r.coarse_max = o->amg_coarse_max; r.seed = o->seed; r.max_cuts = o->max_cuts; r.dt = o->dt;
+  r.sat_chop = o->sat_chop > 0.0 ? o->sat_chop : 0.0;
   return r;
 }
 
@@ -163,5 +164,5 @@ extern "C" void sim_default_options(sim_options *o) {
   o->precision = SIM_PREC_FP64; o->decoupling = SIM_DEC_ABF; o->reorder = 1; o->newton = SIM_NEWTON_STANDARD;
   o->newton_tol = 1e-8; o->lin_tol = 1e-8; o->max_newton = 20; o->restart = 50; o->max_lin = 100;
   o->tile_x = 4; o->tile_y = 4; o->amg_theta = 0.25; o->amg_max_levels = 25; o->amg_coarse_max = 128;
-  o->seed = 0x5EED; o->max_cuts = 6; o->dt = 1.0; o->cuda_stream = nullptr;
+  o->seed = 0x5EED; o->max_cuts = 6; o->dt = 1.0; o->cuda_stream = nullptr; o->sat_chop = 0.0;
 }

@@ -78,6 +78,7 @@ class Case:
     newton: str = "standard"   # or "inexact"
     newton_tol: float = 1e-8
     lin_tol: float = 1e-8
+    sat_chop: float = 0.0      # max |ds_w| per Newton update (0: full step)
     opts: dict = field(default_factory=dict)
 
     @property
@@ -153,7 +154,7 @@ def case1(seed: int = 1, nx=100, ny=100, nz=20) -> Case:
     phi = 0.1 + 0.2 * cdf
     c = Case(f"cfg1_{nx}x{ny}x{nz}", nx, ny, nz, 20.0, 20.0, 5.0, 2000.0,
              kh.copy(), kh.copy(), 0.1 * kh, phi, Fluid(), [], dt=5.0, n_steps=30,
-             newton="inexact", newton_tol=1e-8, lin_tol=1e-6)
+             newton="inexact", newton_tol=1e-8, lin_tol=1e-6, sat_chop=0.1)
     c.wells = [Well(INJ, WRATE, 500.0, c.column(i, j))
                for (i, j) in ((0, 0), (nx - 1, 0), (0, ny - 1), (nx - 1, ny - 1))]
     c.wells.append(Well(PROD, BHP, 150.0, c.column(nx // 2, ny // 2)))
@@ -177,7 +178,7 @@ def case2(seed: int = 2, nx=200, ny=200, nz=25) -> Case:
     phi = np.where(sand, 0.25, 0.10)
     c = Case(f"cfg2_{nx}x{ny}x{nz}", nx, ny, nz, 20.0, 20.0, 5.0, 2000.0,
              kh.copy(), kh.copy(), 0.1 * kh, phi, Fluid(), [], dt=10.0, n_steps=50,
-             newton="standard", newton_tol=1e-6, lin_tol=1e-6)
+             newton="standard", newton_tol=1e-6, lin_tol=1e-6, sat_chop=0.1)
     pi = [round(x * nx / 200.0) for x in (33, 100, 166)]
     pj = [round(x * ny / 200.0) for x in (33, 100, 166)]
     for j in pj:

@@ -226,6 +226,14 @@ def test_whole_run_cfg0_mixed_precision():
     _run_compare(I.case0(), 10, precision=R.PREC_MIXED)
 
 
+def test_whole_run_channelised_case_mixed_with_chop():
+    """The 1M-cell case's physics (channelised facies, 13 wells, 10-day
+    steps, saturation chop 0.1) on a 42x38x8 grid: several RAS tiles with a
+    ragged edge, mixed precision, 3 steps."""
+    c = I.case2(nx=42, ny=38, nz=8)
+    _run_compare(c, 3, precision=R.PREC_MIXED)
+
+
 def test_whole_run_inexact_newton():
     c = I.small_case(10, 8, 4, seed=51, dt=5.0)
     c.newton, c.newton_tol = "inexact", 1e-7
