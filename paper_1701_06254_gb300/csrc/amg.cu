@@ -51,7 +51,7 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 }
 
 __global__ void k_pmis_init(int n, const int *rp, const int *ci, const uint8_t *S, const int *tpos,
-                            uint64_t seed, int level, double *w, int8_t *cf) {
+                            uint64_t seed, int level, double *w, int8_t *cf, int *undecided) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int cnt = 0;
@@ -60,10 +60,14 @@ __global__ void k_pmis_init(int n, const int *rp, const int *ci, const uint8_t *
   double h = (double)(z >> 11) * (1.0 / 9007199254740992.0);
   w[i] = add_rn((double)cnt, h);
   cf[i] = cnt == 0 ? (int8_t)-1 : (int8_t)0;
+  if (cnt) atomicAdd(undecided, 1);
 }
 
+// skip: the previous round's undecided count (nullptr in the first round);
+// a round after the last undecided point was decided does nothing
 __global__ void k_pmis_select(int n, const int *rp, const int *ci, const uint8_t *S, const int *tpos,
-                              const double *w, const int8_t *cf, int8_t *newc) {
+                              const double *w, const int8_t *cf, int8_t *newc, const int *skip) {
+  if (skip && *skip == 0) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int8_t best = 0;
@@ -81,7 +85,8 @@ __global__ void k_pmis_select(int n, const int *rp, const int *ci, const uint8_t
 }
 
 __global__ void k_pmis_update(int n, const int *rp, const int *ci, const uint8_t *S, int8_t *cf,
-                              const int8_t *newc, int *undecided) {
+                              const int8_t *newc, int *undecided, const int *skip) {
+  if (skip && *skip == 0) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (cf[i] != 0) return;
@@ -332,7 +337,7 @@ static void csr_cast(const csr_dev<double> &a, csr_dev<float> &b, cudaStream_t s
 }
 
 void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
-  h.flag.ensure(4);
+  h.flag.ensure(4 + 1025);
   bool mixed = o.precision == SIM_PREC_MIXED;
   int l = 0;
   for (;;) {
@@ -347,27 +352,35 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
     L.cf.ensure(n); L.strong.ensure(L.A.nnz); L.tpos.ensure(L.A.nnz);
     L.nc = 0; L.rounds = 0;
     if (n <= o.coarse_max || l == o.max_levels - 1) { h.coarse_dense = 1; break; }
-    rs_fill_i(h.flag.p, 0, 4, s);
+    rs_fill_i(h.flag.p, 0, 4 + 1025, s);
     k_tpos<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.tpos.p, h.flag.p + 1);
     k_strength<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, o.theta, L.strong.p);
     h.hashw.ensure(n); h.newc.ensure(n);
     k_pmis_init<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, o.seed, l,
-                                                 h.hashw.p, L.cf.p);
+                                                 h.hashw.p, L.cf.p, h.flag.p + 4);
     RS_LAUNCHED(3);
     RS_CHECK_LAUNCH();
     if (d2h(h.flag.p + 1, 1, s)[0]) RS_FAIL(SIM_ERR_ARG, "AMG: level %d pattern is not structurally symmetric", l);
-    for (;;) {
-      int und;
-      rs_fill_i(h.flag.p, 0, 1, s);
-      k_pmis_select<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, h.hashw.p,
-                                                     L.cf.p, h.newc.p);
-      k_pmis_update<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, h.newc.p, h.flag.p);
-      RS_LAUNCHED(2);
+    // rounds in batches of PMIS_BATCH: cnt[0] = undecided points after the
+    // initialisation, cnt[r + 1] = after round r; round r runs only while
+    // cnt[r] > 0, so the rounds past the last one do nothing
+    const int PMIS_BATCH = 4;
+    int *cnt = h.flag.p + 4;
+    for (int done = 0;;) {
+      for (int r = done; r < done + PMIS_BATCH; r++) {
+        k_pmis_select<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, h.hashw.p,
+                                                       L.cf.p, h.newc.p, cnt + r);
+        k_pmis_update<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, h.newc.p,
+                                                       cnt + r + 1, cnt + r);
+      }
+      RS_LAUNCHED(2 * PMIS_BATCH);
       RS_CHECK_LAUNCH();
-      L.rounds++;
-      und = d2h(h.flag.p, 1, s)[0];
-      if (!und) break;
-      if (L.rounds > 1000) RS_FAIL(SIM_ERR_TIMEOUT, "AMG: PMIS did not finish in 1000 rounds");
+      std::vector<int> und = d2h(cnt + done, PMIS_BATCH + 1, s);
+      int z = -1;
+      for (int r = 0; r <= PMIS_BATCH; r++) if (und[r] == 0) { z = r; break; }
+      if (z >= 0) { L.rounds = done + z; break; }
+      done += PMIS_BATCH;
+      if (done + PMIS_BATCH >= 1024) RS_FAIL(SIM_ERR_TIMEOUT, "AMG: PMIS did not finish in 1024 rounds");
     }
     static thread_local dbuf<int> scratch;   // C flags, then coarse index of each C point
     scratch.ensure(n + 1);

@@ -180,6 +180,7 @@ struct sim_ls_s {
   dbuf<double> x64a, x64b;      // CPR work (FP64)
   dbuf<float> x32a, x32b, x32c; // CPR work (FP32)
   double *hpin = nullptr;       // pinned host scalars
+  int *errw = nullptr, *errw_dev = nullptr;   // device error word (host-mapped)
   bool have_setup = false;
   // timing: events in pairs, the family of each pair in ev_fam
   unsigned timer_mask = 0;

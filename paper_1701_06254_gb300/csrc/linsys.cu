@@ -38,6 +38,7 @@ void sim_ls_s::timer_flush() {
 sim_ls_s::~sim_ls_s() {
   for (auto e : ev) cudaEventDestroy(e);
   if (hpin) cudaFreeHost(hpin);
+  if (errw) cudaFreeHost(errw);
 }
 
 // ---------------------------------------------------------- decoupling ---
@@ -257,6 +258,9 @@ void ls_init(sim_ls_s *ls, int nx, int ny, int nz, int nw, const int *rp, const 
   if (o.precision == SIM_PREC_MIXED) { ls->x32b.alloc(nu); ls->x32c.alloc(nu); }
   RS_CUDA(cudaHostAlloc((void **)&ls->hpin, 64 * sizeof(double), cudaHostAllocMapped));
   for (int k = 0; k < 64; k++) ls->hpin[k] = 0.0;
+  RS_CUDA(cudaHostAlloc((void **)&ls->errw, 16 * sizeof(int), cudaHostAllocMapped));
+  for (int k = 0; k < 16; k++) ls->errw[k] = 0;
+  RS_CUDA(cudaHostGetDevicePointer((void **)&ls->errw_dev, ls->errw, 0));
   RS_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -297,51 +301,96 @@ void ls_setup(sim_ls_s *ls) {
 // results do not depend on scheduling.
 #define ORTHO_BS 256
 #define ORTHO_MAXV 64
-static int ortho_blocks(int nu) { int b = (nu + 8191) / 8192; return b < 1 ? 1 : (b > 608 ? 608 : b); }
+static int ortho_blocks(int nu) { int b = (nu + 2047) / 2048; return b < 1 ? 1 : (b > 1216 ? 1216 : b); }
 
-// MODE 0: d_k = V_k . w (k < nv) and, if with_norm, d_nv = w . w
-// MODE 2: w -= sum_k h_k V_k, then d_0 = ||w||^2
-template <int MODE>
-__global__ void __launch_bounds__(ORTHO_BS) k_ortho(int nu, int nv, const double *__restrict__ V, double *w,
-                                                    const double *__restrict__ h, double *part, int with_norm,
-                                                    const int *cond) {
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// d_k = V_k . w for k < nv and, if with_norm, d_nv = w . w.  Every thread
+// keeps one accumulator per basis vector in registers (MAXV of them, the
+// compile-time bound of nv), so the nv loads of a row are independent.
+template <int MAXV>
+__global__ void __launch_bounds__(ORTHO_BS) k_ortho_dots(int nu, int nv, const double *__restrict__ V,
+                                                         const double *__restrict__ w, double *part, int with_norm,
+                                                         const int *cond) {
   if (cond && *cond == 0) return;
-  __shared__ double sred[ORTHO_MAXV + 1][ORTHO_BS / 32];
-  __shared__ double sh[ORTHO_MAXV];
+  __shared__ double sred[MAXV + 1][ORTHO_BS / 32];
+  double acc[MAXV + 1];
+#pragma unroll
+  for (int k = 0; k <= MAXV; k++) acc[k] = 0.0;
   int nblk = gridDim.x, chunk = (nu + nblk - 1) / nblk;
   int i0 = blockIdx.x * chunk, i1 = min(nu, i0 + chunk);
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    double wi = w[i];
+#pragma unroll
+    for (int k = 0; k < MAXV; k++)
+      if (k < nv) acc[k] += __ldg(V + (size_t)k * nu + i) * wi;
+    acc[MAXV] += wi * wi;
+  }
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (MODE == 2) {
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) sh[k] = h[k];
-    __syncthreads();
-    double s2 = 0.0;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      double s = 0.0;
-      for (int k = 0; k < nv; k++) s += sh[k] * V[(size_t)k * nu + i];
-      double wi = w[i] - s;
-      w[i] = wi;
-      s2 += wi * wi;
-    }
-    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_down_sync(0xffffffffu, s2, o);
-    if (lane == 0) sred[0][wid] = s2;
-    __syncthreads();
-    if (threadIdx.x == 0) { double t = 0; for (int k = 0; k < ORTHO_BS / 32; k++) t += sred[0][k]; part[blockIdx.x] = t; }
-  } else {
-    int nd = nv + (with_norm ? 1 : 0);
-    for (int k = 0; k < nd; k++) {
-      double s = 0.0;
-      const double *vk = k < nv ? V + (size_t)k * nu : w;
-      for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += vk[i] * w[i];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) sred[k][wid] = s;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < nd; k += blockDim.x) {
-      double t = 0; for (int q = 0; q < ORTHO_BS / 32; q++) t += sred[k][q];
-      part[(size_t)k * nblk + blockIdx.x] = t;
+#pragma unroll
+  for (int k = 0; k <= MAXV; k++) {
+    if (k < nv || k == MAXV) {
+      double v = warp_sum_d(acc[k]);
+      if (lane == 0) sred[k][wid] = v;
     }
   }
+  __syncthreads();
+  int nd = nv + (with_norm ? 1 : 0);
+  for (int k = threadIdx.x; k < nd; k += blockDim.x) {
+    int src = k < nv ? k : MAXV;
+    double t = 0; for (int q = 0; q < ORTHO_BS / 32; q++) t += sred[src][q];
+    part[(size_t)k * nblk + blockIdx.x] = t;
+  }
 }
+
+// w -= sum_k h_k V_k (independent loads of the nv basis entries of a row),
+// then d_0 = ||w||^2
+template <int MAXV>
+__global__ void __launch_bounds__(ORTHO_BS) k_ortho_update(int nu, int nv, const double *__restrict__ V, double *w,
+                                                           const double *__restrict__ h, double *part,
+                                                           const int *cond) {
+  if (cond && *cond == 0) return;
+  __shared__ double sred[ORTHO_BS / 32];
+  double hk[MAXV];
+#pragma unroll
+  for (int k = 0; k < MAXV; k++) hk[k] = k < nv ? h[k] : 0.0;
+  int nblk = gridDim.x, chunk = (nu + nblk - 1) / nblk;
+  int i0 = blockIdx.x * chunk, i1 = min(nu, i0 + chunk);
+  double n2 = 0.0;
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    double sacc = 0.0;
+#pragma unroll
+    for (int k = 0; k < MAXV; k++)
+      if (k < nv) sacc += hk[k] * __ldg(V + (size_t)k * nu + i);
+    double wi = w[i] - sacc;
+    w[i] = wi;
+    n2 += wi * wi;
+  }
+  n2 = warp_sum_d(n2);
+  if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = n2;
+  __syncthreads();
+  if (threadIdx.x == 0) { double t = 0; for (int q = 0; q < ORTHO_BS / 32; q++) t += sred[q]; part[blockIdx.x] = t; }
+}
+
+static void ortho_dots(int nu, int nv, const double *V, const double *w, double *part, int with_norm, const int *cond,
+                       int nblk, cudaStream_t s) {
+  if (nv <= 8) k_ortho_dots<8><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, part, with_norm, cond);
+  else if (nv <= 16) k_ortho_dots<16><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, part, with_norm, cond);
+  else if (nv <= 32) k_ortho_dots<32><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, part, with_norm, cond);
+  else k_ortho_dots<64><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, part, with_norm, cond);
+}
+static void ortho_update(int nu, int nv, const double *V, double *w, const double *h, double *part, const int *cond,
+                         int nblk, cudaStream_t s) {
+  if (nv <= 8) k_ortho_update<8><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, h, part, cond);
+  else if (nv <= 16) k_ortho_update<16><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, h, part, cond);
+  else if (nv <= 32) k_ortho_update<32><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, h, part, cond);
+  else k_ortho_update<64><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, h, part, cond);
+}
+
 __global__ void k_reduce_parts(int nv, int nblk, const double *part, double *out, const int *cond) {
   if (cond && *cond == 0) return;
   int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -451,14 +500,14 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres) {
       {
         rs_timed tm(ls, SIM_T_ORTHO);
         int nv = j + 1;
-        k_ortho<0><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, ls->V.p, ls->w.p, nullptr, ls->partial.p, 1, nullptr);
+        ortho_dots(nu, nv, ls->V.p, ls->w.p, ls->partial.p, 1, nullptr, nblk, s);
         k_reduce_parts<<<1, 96, 0, s>>>(nv + 1, nblk, ls->partial.p, h1, nullptr);     // h1[nv] = ||w||^2
-        k_ortho<2><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, ls->V.p, ls->w.p, h1, ls->partial.p, 0, nullptr);
+        ortho_update(nu, nv, ls->V.p, ls->w.p, h1, ls->partial.p, nullptr, nblk, s);
         k_reduce_parts<<<1, 32, 0, s>>>(1, nblk, ls->partial.p, nrm, nullptr);
         k_dgks<<<1, 1, 0, s>>>(h1 + nv, nrm, flag);
-        k_ortho<0><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, ls->V.p, ls->w.p, nullptr, ls->partial.p, 0, flag);
+        ortho_dots(nu, nv, ls->V.p, ls->w.p, ls->partial.p, 0, flag, nblk, s);
         k_reduce_parts<<<1, 96, 0, s>>>(nv, nblk, ls->partial.p, h2, flag);
-        k_ortho<2><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, ls->V.p, ls->w.p, h2, ls->partial.p, 0, flag);
+        ortho_update(nu, nv, ls->V.p, ls->w.p, h2, ls->partial.p, flag, nblk, s);
         k_reduce_parts<<<1, 32, 0, s>>>(1, nblk, ls->partial.p, nrm_b, flag);
         k_arnoldi_col<<<1, 1, 0, s>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, hp_dev);
         k_scale<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->w.p, hn, ls->V.p + (size_t)(j + 1) * nu);
@@ -467,6 +516,7 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres) {
       RS_CHECK_LAUNCH();
       RS_CUDA(cudaStreamSynchronize(s));
       ls->timer_flush();
+      if (ls->errw[0]) RS_FAIL(SIM_ERR_TIMEOUT, "RAS apply: bulk copy wait gave up (code %d)", ls->errw[0]);
       double est = hp[0], hnv = hp[1];
       its++;
       jend = j + 1;

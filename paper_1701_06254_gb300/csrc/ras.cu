@@ -449,48 +449,107 @@ template <class T> struct v2_t;
 template <> struct v2_t<float> { typedef float2 type; };
 template <> struct v2_t<double> { typedef double2 type; };
 
+// ------------------------------------------------ bulk copies (TMA) ------
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: gives up after `limit` polls, records `code` in *err and
+// returns false (the hardware copies themselves cannot stall forever; the
+// bound only turns a fault into an error status instead of a hang)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, int *err, int code) {
+  for (int it = 0; it < (1 << 22); it++)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicExch(err, code);
+  return false;
+}
+
 // x = R(A)^{-1} f with the subdomain's packed factors held in shared
-// memory: one block per subdomain copies its blob with 16-byte loads,
-// gathers the extended right-hand side, runs the level-scheduled L and U
-// solves on chip and writes (or adds) the owned rows.
+// memory.  One block per subdomain: thread 0 starts two bulk copies of the
+// blob (header + gather indices first, the factors second); the block
+// gathers the extended right-hand side as soon as the first part lands,
+// then runs the level-scheduled L and U solves on chip and writes (or adds)
+// the owned rows.
+#define RAS_BS 64
 template <class T, class Tin, bool ACC>
-__global__ void __launch_bounds__(128) k_ras_apply_smem(const long long *blob_off, const unsigned char *blobs,
-                                                        const Tin *__restrict__ f, T *__restrict__ x) {
+__global__ void __launch_bounds__(RAS_BS) k_ras_apply_smem(const long long *blob_off, const unsigned char *blobs,
+                                                           const Tin *__restrict__ f, T *__restrict__ x, int *err) {
   extern __shared__ uint4 sm4[];
+  __shared__ uint64_t bar[2];
   typedef typename v2_t<T>::type T2;
   int s = blockIdx.x;
   const unsigned char *b = blobs + blob_off[s];
   int total = (int)(blob_off[s + 1] - blob_off[s]);
-  const uint4 *src = reinterpret_cast<const uint4 *>(b);
-  for (int i = threadIdx.x; i < total / 16; i += blockDim.x) sm4[i] = __ldg(src + i);
+  unsigned char *sb = reinterpret_cast<unsigned char *>(sm4);
+  // the first section (header + gidx) ends where rp starts; its size depends only on m
+  int m0 = ((const int *)b)[0];
+  int head = blob_lay(m0, 0, 4 * (int)sizeof(T)).rp;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
   __syncthreads();
-  const unsigned char *sb = reinterpret_cast<const unsigned char *>(sm4);
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(&bar[0], (unsigned)head);
+    bulk_g2s(sb, b, (unsigned)head, &bar[0]);
+    mbar_arrive_expect_tx(&bar[1], (unsigned)(total - head));
+    for (int off = head; off < total; off += 32768) {
+      int len = total - off < 32768 ? total - off : 32768;
+      bulk_g2s(sb + off, b + off, (unsigned)len, &bar[1]);
+    }
+  }
+  bool ok0 = mbar_wait_bounded(&bar[0], 0, err, 1);
   const int *hdr = (const int *)sb;
-  int m = hdr[0], nLrows = hdr[1], nLl = hdr[2], nU = hdr[3];
-  (void)nLrows;
-  int e_count = 0;
+  int m = m0, nLl = hdr[2], nU = hdr[3];
+  const int *gidx = (const int *)(sb + 16);
+  T2 *y = reinterpret_cast<T2 *>(sm4 + total / 16);
+  if (ok0)
+    for (int pos = threadIdx.x; pos < m; pos += blockDim.x) {
+      int g = gidx[pos] >> 1;
+      T2 v; v.x = (T)f[2 * (size_t)g]; v.y = (T)f[2 * (size_t)g + 1];
+      y[pos] = v;
+    }
+  bool ok1 = mbar_wait_bounded(&bar[1], 0, err, 2);
+  // uniform decision (and the barrier after the gather): on a timeout the
+  // error is recorded and nothing is written
+  if (!__syncthreads_and(ok0 && ok1)) return;
   blob_layout Lb = blob_lay(m, 0, 4 * (int)sizeof(T));
   const uint16_t *rp = (const uint16_t *)(sb + Lb.rp);
-  e_count = rp[m];
-  Lb = blob_lay(m, e_count, 4 * (int)sizeof(T));
-  const int *gidx = (const int *)(sb + Lb.gidx);
+  Lb = blob_lay(m, rp[m], 4 * (int)sizeof(T));
   const uint16_t *dg = (const uint16_t *)(sb + Lb.dg);
   const uint16_t *lrow = (const uint16_t *)(sb + Lb.lrow), *llev = (const uint16_t *)(sb + Lb.llev);
   const uint16_t *urow = (const uint16_t *)(sb + Lb.urow), *ulev = (const uint16_t *)(sb + Lb.ulev);
   const uint16_t *cols = (const uint16_t *)(sb + Lb.cols);
   const T *vals = (const T *)(sb + Lb.vals), *dv = (const T *)(sb + Lb.dinv);
-  T2 *y = reinterpret_cast<T2 *>(sm4 + total / 16);
-  for (int pos = threadIdx.x; pos < m; pos += blockDim.x) {
-    int g = gidx[pos] >> 1;
-    T2 v; v.x = (T)f[2 * (size_t)g]; v.y = (T)f[2 * (size_t)g + 1];
-    y[pos] = v;
-  }
-  __syncthreads();
   for (int k = 0; k < nLl; k++) {
     for (int r = llev[k] + threadIdx.x; r < llev[k + 1]; r += blockDim.x) {
       int i = lrow[r];
       T2 a = y[i];
-      for (int q = rp[i]; q < dg[i]; q++) {
+      int q1 = dg[i];
+      for (int q = rp[i]; q < q1; q++) {
         const T *B = vals + 4 * q; T2 c = y[cols[q]];
         a.x -= B[0] * c.x + B[1] * c.y; a.y -= B[2] * c.x + B[3] * c.y;
       }
@@ -502,7 +561,8 @@ __global__ void __launch_bounds__(128) k_ras_apply_smem(const long long *blob_of
     for (int r = ulev[k] + threadIdx.x; r < ulev[k + 1]; r += blockDim.x) {
       int i = urow[r];
       T2 a = y[i];
-      for (int q = dg[i]; q < rp[i + 1]; q++) {
+      int q1 = rp[i + 1];
+      for (int q = dg[i]; q < q1; q++) {
         const T *B = vals + 4 * q; T2 c = y[cols[q]];
         a.x -= B[0] * c.x + B[1] * c.y; a.y -= B[2] * c.x + B[3] * c.y;
       }
@@ -559,9 +619,9 @@ template <class T, class Tin> void ls_ras_apply(sim_ls_s *ls, const Tin *f, T *x
     }
     rs_timed tm(ls, SIM_T_RAS);
     if (accumulate)
-      k_ras_apply_smem<T, Tin, true><<<R.nsub, 128, R.smem_bytes, s>>>(R.blob_off.p, R.blob.p, f, x);
+      k_ras_apply_smem<T, Tin, true><<<R.nsub, RAS_BS, R.smem_bytes, s>>>(R.blob_off.p, R.blob.p, f, x, ls->errw_dev);
     else
-      k_ras_apply_smem<T, Tin, false><<<R.nsub, 128, R.smem_bytes, s>>>(R.blob_off.p, R.blob.p, f, x);
+      k_ras_apply_smem<T, Tin, false><<<R.nsub, RAS_BS, R.smem_bytes, s>>>(R.blob_off.p, R.blob.p, f, x, ls->errw_dev);
     RS_LAUNCHED(1);
     return;
   }
