@@ -391,13 +391,19 @@ static void ortho_update(int nu, int nv, const double *V, double *w, const doubl
   else k_ortho_update<64><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, h, part, cond);
 }
 
+// out[k] = sum over blocks of part[k][*]: one warp per k, lanes add a fixed
+// stride of the partials, then a fixed shuffle tree (deterministic)
 __global__ void k_reduce_parts(int nv, int nblk, const double *part, double *out, const int *cond) {
   if (cond && *cond == 0) return;
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (k >= nv) return;
   double t = 0;
-  for (int b = 0; b < nblk; b++) t += part[(size_t)k * nblk + b];
-  out[k] = t;
+  for (int b = lane; b < nblk; b += 32) t += part[(size_t)k * nblk + b];
+  t = warp_sum_d(t);
+  if (lane == 0) out[k] = t;
+}
+static void reduce_parts(int nv, int nblk, const double *part, double *out, const int *cond, cudaStream_t s) {
+  k_reduce_parts<<<(nv + 3) / 4, 128, 0, s>>>(nv, nblk, part, out, cond);
 }
 // flag = ||w_1||^2 < ||w||^2 / 2
 __global__ void k_dgks(const double *w2_before, const double *w2_after, int *flag) {
@@ -501,14 +507,14 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres) {
         rs_timed tm(ls, SIM_T_ORTHO);
         int nv = j + 1;
         ortho_dots(nu, nv, ls->V.p, ls->w.p, ls->partial.p, 1, nullptr, nblk, s);
-        k_reduce_parts<<<1, 96, 0, s>>>(nv + 1, nblk, ls->partial.p, h1, nullptr);     // h1[nv] = ||w||^2
+        reduce_parts(nv + 1, nblk, ls->partial.p, h1, nullptr, s);     // h1[nv] = ||w||^2
         ortho_update(nu, nv, ls->V.p, ls->w.p, h1, ls->partial.p, nullptr, nblk, s);
-        k_reduce_parts<<<1, 32, 0, s>>>(1, nblk, ls->partial.p, nrm, nullptr);
+        reduce_parts(1, nblk, ls->partial.p, nrm, nullptr, s);
         k_dgks<<<1, 1, 0, s>>>(h1 + nv, nrm, flag);
         ortho_dots(nu, nv, ls->V.p, ls->w.p, ls->partial.p, 0, flag, nblk, s);
-        k_reduce_parts<<<1, 96, 0, s>>>(nv, nblk, ls->partial.p, h2, flag);
+        reduce_parts(nv, nblk, ls->partial.p, h2, flag, s);
         ortho_update(nu, nv, ls->V.p, ls->w.p, h2, ls->partial.p, flag, nblk, s);
-        k_reduce_parts<<<1, 32, 0, s>>>(1, nblk, ls->partial.p, nrm_b, flag);
+        reduce_parts(1, nblk, ls->partial.p, nrm_b, flag, s);
         k_arnoldi_col<<<1, 1, 0, s>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, hp_dev);
         k_scale<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->w.p, hn, ls->V.p + (size_t)(j + 1) * nu);
         RS_LAUNCHED(11);

@@ -301,9 +301,11 @@ __global__ void k_norm_part(int n, int nw, double dt_vol_inv, const fluid_c f, c
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 __global__ void k_max_part(int m, const double *part, double *out) {
+  int lane = threadIdx.x;
   double mx = 0.0;
-  for (int k = 0; k < m; k++) { double x = part[k]; if (!(x <= mx)) mx = x; }
-  *out = mx;
+  for (int k = lane; k < m; k += 32) { double x = part[k]; if (!(x <= mx)) mx = x; }
+  for (int o = 16; o > 0; o >>= 1) { double y = __shfl_down_sync(0xffffffffu, mx, o); if (!(y <= mx)) mx = y; }
+  if (lane == 0) *out = mx;
 }
 
 // x += y (Algorithm 1), with the optional saturation chop, then s_w in [0, 1]
@@ -380,7 +382,7 @@ static double s_norm(sim_s *h) {
   h->red.ensure(nb + 1);
   double dvi = h->dt / (h->dx * h->dy * h->dz);
   k_norm_part<<<nb, 256, 0, s>>>(h->n, h->nw, dvi, h->fl, h->phi.p, h->ls->b.p, h->red.p);
-  k_max_part<<<1, 1, 0, s>>>(nb, h->red.p, h->red.p + nb);
+  k_max_part<<<1, 32, 0, s>>>(nb, h->red.p, h->red.p + nb);
   RS_LAUNCHED(2);
   return d2h(h->red.p + nb, 1, s)[0];
 }
