@@ -96,8 +96,8 @@ def ras_bytes(ls, precision):
     position/row index arrays, the gather of the extended rows and the
     restricted scatter of the owned rows."""
     import paper_1701_06254_gb300 as R
-    vb = 16 if precision == "mixed" else 32
-    xb = 4 if precision == "mixed" else 8
+    vb = {"mixed": 16, "mixed_bf16": 8, "fp64": 32}[precision]
+    xb = 8 if precision == "fp64" else 4
     nsub = ls.ras_count()
     nnz = nxt = own = 0
     for s in range(nsub):
@@ -162,7 +162,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="cfg2")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_bf16", "fp64"])
     ap.add_argument("--max-lin", type=int, default=200)
     ap.add_argument("--roofline", default="ras", choices=["ras", "spmv64", "spmv_prec"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -188,7 +188,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    prec = R.PREC_MIXED if args.precision == "mixed" else R.PREC_FP64
+    prec = {"mixed": R.PREC_MIXED, "mixed_bf16": R.PREC_MIXED_BF16, "fp64": R.PREC_FP64}[args.precision]
     opts = dict(precision=prec, max_lin=args.max_lin)
     sim = R.Sim(case, **opts)
     sim.init_hydrostatic()
@@ -235,9 +235,9 @@ def main():
     if args.roofline == "ras":
         bpl = ras_bytes(sim.ls, args.precision)
     elif args.roofline == "spmv64":
-        bpl = spmv_bytes(nb, nnzb, 32, 4 if args.precision == "mixed" else 8, 0, 8)
+        bpl = spmv_bytes(nb, nnzb, 32, 8 if args.precision == "fp64" else 4, 0, 8)
     else:
-        bpl = spmv_bytes(nb, nnzb, 16, 4, 8, 4) if args.precision == "mixed" else spmv_bytes(nb, nnzb, 32, 8, 8, 8)
+        bpl = spmv_bytes(nb, nnzb, 32, 8, 8, 8) if args.precision == "fp64" else spmv_bytes(nb, nnzb, 16, 4, 8, 4)
     peak, src = peaks()
     achieved = bpl / (kms / nk * 1e-3) / 1e9 if nk else 0.0
     roof = {"kernel": args.roofline, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -282,7 +282,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": {"mixed": "f64+f32", "mixed_bf16": "f64+f32+bf16", "fp64": "f64"}[args.precision], "data": "synthetic",
             "config": {"workload": case.name, "cells": case.n, "wells": len(case.wells), "dt_days": case.dt,
                        "relres": case.lin_tol, "precision": args.precision, "learned_warm_start": False,
                        "parallelism": "replicas" if world > 1 else "single",

@@ -53,7 +53,9 @@ enum { SIM_INJ = 0, SIM_PROD = 1 };                            /* well kind     
 enum { SIM_BHP = 0, SIM_WRATE = 1, SIM_ORATE = 2, SIM_LRATE = 3 }; /* eqs. (11)-(14)   */
 enum { SIM_DEC_NONE = 0, SIM_DEC_ABF = 1, SIM_DEC_QI = 2 };    /* eq. (29) operator   */
 enum { SIM_NEWTON_STANDARD = 0, SIM_NEWTON_INEXACT = 1 };      /* Algorithm 1         */
-enum { SIM_PREC_FP64 = 0, SIM_PREC_MIXED = 1 };                /* preconditioner type */
+/* preconditioner precision: FP64; FP32 (AMG, RAS factors, CPR vectors; FP64
+ * coarsest solve); FP32 with the RAS factor values stored in BF16 */
+enum { SIM_PREC_FP64 = 0, SIM_PREC_MIXED = 1, SIM_PREC_MIXED_BF16 = 2 };
 
 typedef struct { int nx, ny, nz; double dx, dy, dz, top_depth; } sim_grid;
 
@@ -81,7 +83,7 @@ typedef struct {
 } sim_well;
 
 typedef struct {
-  int precision;       /* SIM_PREC_FP64 or SIM_PREC_MIXED (FP32 AMG + FP32 RAS)    */
+  int precision;       /* SIM_PREC_FP64, SIM_PREC_MIXED or SIM_PREC_MIXED_BF16      */
   int decoupling;      /* SIM_DEC_*                                                */
   int reorder;         /* 1: local potential reordering in each RAS subdomain     */
   int newton;          /* SIM_NEWTON_*                                             */

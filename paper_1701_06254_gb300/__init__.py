@@ -17,7 +17,7 @@ from . import inputs  # noqa: F401  (synthetic workloads)
 
 _lib = None
 
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_MIXED_BF16 = 0, 1, 2
 DEC_NONE, DEC_ABF, DEC_QI = 0, 1, 2
 OP_SPMV, OP_RAS, OP_VCYCLE, OP_CPR = 0, 1, 2, 3
 T_NONE, T_SPMV64, T_SPMV_PREC, T_RAS, T_VCYCLE, T_ORTHO, T_ASSEMBLE = 0, 1, 2, 3, 4, 5, 6

@@ -338,7 +338,7 @@ static void csr_cast(const csr_dev<double> &a, csr_dev<float> &b, cudaStream_t s
 
 void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
   h.flag.ensure(4 + 1025);
-  bool mixed = o.precision == SIM_PREC_MIXED;
+  bool mixed = o.precision != SIM_PREC_FP64;
   int l = 0;
   for (;;) {
     amg_level &L = h.lev[l];

@@ -195,7 +195,7 @@ void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32) {
   cudaStream_t s = ls->st;
   int n = ls->n;
   amg_level &L0 = ls->amg.lev[0];
-  if (ls->o.precision == SIM_PREC_MIXED) {
+  if (ls->o.precision != SIM_PREC_FP64) {
     float *z = z32, *r = ls->x32b.p;
     ls_ras_apply<float, double>(ls, v, z, false);                                      // 1
     { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, double, float>(ls, ls->val32.p, z, v, r, s); }  // 2
@@ -246,7 +246,7 @@ void ls_init(sim_ls_s *ls, int nx, int ny, int nz, int nw, const int *rp, const 
   h2d(ls->rp, ls->h_rp, st); h2d(ls->ci, ls->h_ci, st); h2d(ls->dpos, dpos, st);
   ls->val.alloc(4 * (size_t)ls->nnzb); ls->b.alloc(2 * (size_t)nb); ls->key.alloc(ls->n);
   ls->dmat.alloc(4 * (size_t)nb);
-  if (o.precision == SIM_PREC_MIXED) ls->val32.alloc(4 * (size_t)ls->nnzb);
+  if (o.precision != SIM_PREC_FP64) ls->val32.alloc(4 * (size_t)ls->nnzb);
   h2d(ls->app_src, app_src, st);
   csr_dev<double> &A0 = ls->amg.lev[0].A;
   A0.n = A0.m = ls->n; A0.nnz = (int)app_src.size();
@@ -255,7 +255,7 @@ void ls_init(sim_ls_s *ls, int nx, int ny, int nz, int nw, const int *rp, const 
   size_t nu = 2 * (size_t)nb;
   ls->y.alloc(nu); ls->w.alloc(nu); ls->r.alloc(nu);
   ls->x64a.alloc(nu); ls->x64b.alloc(nu);
-  if (o.precision == SIM_PREC_MIXED) { ls->x32b.alloc(nu); ls->x32c.alloc(nu); }
+  if (o.precision != SIM_PREC_FP64) { ls->x32b.alloc(nu); ls->x32c.alloc(nu); }
   RS_CUDA(cudaHostAlloc((void **)&ls->hpin, 64 * sizeof(double), cudaHostAllocMapped));
   for (int k = 0; k < 64; k++) ls->hpin[k] = 0.0;
   RS_CUDA(cudaHostAlloc((void **)&ls->errw, 16 * sizeof(int), cudaHostAllocMapped));
@@ -266,7 +266,7 @@ void ls_init(sim_ls_s *ls, int nx, int ny, int nz, int nw, const int *rp, const 
 
 void ls_setup(sim_ls_s *ls) {
   cudaStream_t s = ls->st;
-  float *v32 = ls->o.precision == SIM_PREC_MIXED ? ls->val32.p : nullptr;
+  float *v32 = ls->o.precision != SIM_PREC_FP64 ? ls->val32.p : nullptr;
   unsigned g = grid_for(ls->nb, 128);
   {
   rs_timed tm(ls, SIM_T_DECOUPLE);
@@ -301,7 +301,9 @@ void ls_setup(sim_ls_s *ls) {
 // results do not depend on scheduling.
 #define ORTHO_BS 256
 #define ORTHO_MAXV 64
-static int ortho_blocks(int nu) { int b = (nu + 2047) / 2048; return b < 1 ? 1 : (b > 1216 ? 1216 : b); }
+// two blocks per SM: each thread covers many rows, so the per-thread dot
+// accumulators are reduced across the block only once per many FMAs
+static int ortho_blocks(int nu) { int b = (nu + 8191) / 8192; return b < 1 ? 1 : (b > 304 ? 304 : b); }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -376,19 +378,25 @@ __global__ void __launch_bounds__(ORTHO_BS) k_ortho_update(int nu, int nv, const
   if (threadIdx.x == 0) { double t = 0; for (int q = 0; q < ORTHO_BS / 32; q++) t += sred[q]; part[blockIdx.x] = t; }
 }
 
+// MAXV = nv rounded up to a multiple of 4 (the compiler issues the FMAs of
+// a fully unrolled MAXV loop even for k >= nv, so the bound must be tight)
+#define ORTHO_CASE(N, KERNEL, ...) case N: KERNEL<N><<<nblk, ORTHO_BS, 0, s>>>(__VA_ARGS__); break;
+#define ORTHO_SWITCH(KERNEL, ...)                                                                         \
+  switch ((nv + 3) & ~3) {                                                                                \
+    ORTHO_CASE(4, KERNEL, __VA_ARGS__) ORTHO_CASE(8, KERNEL, __VA_ARGS__) ORTHO_CASE(12, KERNEL, __VA_ARGS__)  \
+    ORTHO_CASE(16, KERNEL, __VA_ARGS__) ORTHO_CASE(20, KERNEL, __VA_ARGS__) ORTHO_CASE(24, KERNEL, __VA_ARGS__) \
+    ORTHO_CASE(28, KERNEL, __VA_ARGS__) ORTHO_CASE(32, KERNEL, __VA_ARGS__) ORTHO_CASE(36, KERNEL, __VA_ARGS__) \
+    ORTHO_CASE(40, KERNEL, __VA_ARGS__) ORTHO_CASE(44, KERNEL, __VA_ARGS__) ORTHO_CASE(48, KERNEL, __VA_ARGS__) \
+    ORTHO_CASE(52, KERNEL, __VA_ARGS__) ORTHO_CASE(56, KERNEL, __VA_ARGS__) ORTHO_CASE(60, KERNEL, __VA_ARGS__) \
+    default: KERNEL<64><<<nblk, ORTHO_BS, 0, s>>>(__VA_ARGS__); break;                                     \
+  }
 static void ortho_dots(int nu, int nv, const double *V, const double *w, double *part, int with_norm, const int *cond,
                        int nblk, cudaStream_t s) {
-  if (nv <= 8) k_ortho_dots<8><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, part, with_norm, cond);
-  else if (nv <= 16) k_ortho_dots<16><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, part, with_norm, cond);
-  else if (nv <= 32) k_ortho_dots<32><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, part, with_norm, cond);
-  else k_ortho_dots<64><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, part, with_norm, cond);
+  ORTHO_SWITCH(k_ortho_dots, nu, nv, V, w, part, with_norm, cond)
 }
 static void ortho_update(int nu, int nv, const double *V, double *w, const double *h, double *part, const int *cond,
                          int nblk, cudaStream_t s) {
-  if (nv <= 8) k_ortho_update<8><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, h, part, cond);
-  else if (nv <= 16) k_ortho_update<16><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, h, part, cond);
-  else if (nv <= 32) k_ortho_update<32><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, h, part, cond);
-  else k_ortho_update<64><<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, h, part, cond);
+  ORTHO_SWITCH(k_ortho_update, nu, nv, V, w, h, part, cond)
 }
 
 // out[k] = sum over blocks of part[k][*]: one warp per k, lanes add a fixed
@@ -437,12 +445,12 @@ __global__ void k_arnoldi_col(int j, int m, const double *h1, const double *h2, 
 }
 __global__ void k_scale(int nu, const double *w, const double *hn, double *v) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double s = *hn;
-  if (i < nu) v[i] = s > 0.0 ? w[i] / s : 0.0;
+  double s = *hn, inv = s > 0.0 ? 1.0 / s : 0.0;     // one division per thread, not per entry
+  if (i < nu) v[i] = w[i] * inv;
 }
 __global__ void k_start(int nu, const double *r, double beta, double *v0, double *G, int m) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nu) v0[i] = r[i] / beta;
+  if (i < nu) v0[i] = r[i] * (1.0 / beta);
   if (i == 0) { double *g = G + (size_t)m * (m + 1) + 2 * m; for (int k = 0; k <= m; k++) g[k] = 0.0; g[0] = beta; }
 }
 __global__ void k_hsolve(int jend, int m, const double *G, double *yk) {
@@ -468,7 +476,7 @@ __global__ void k_xupdate(int nu, int jend, const double *yk, const Tz *Z, doubl
 int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres) {
   cudaStream_t s = ls->st;
   int nu = 2 * ls->nb, m = std::min(ls->o.restart, ORTHO_MAXV - 1), maxit = ls->o.max_lin;
-  bool mixed = ls->o.precision == SIM_PREC_MIXED;
+  bool mixed = ls->o.precision != SIM_PREC_FP64;
   ls->V.ensure((size_t)(m + 1) * nu);
   if (mixed) ls->Z32.ensure((size_t)m * nu); else ls->Z.ensure((size_t)m * nu);
   int nblk = ortho_blocks(nu);

@@ -8,6 +8,7 @@
 // the reordered factors, the factorisation and both triangular solves run
 // level by level inside that block.
 #include "common.cuh"
+#include <cuda_bf16.h>
 #include <algorithm>
 #include <cfloat>
 #include <climits>
@@ -109,7 +110,7 @@ void ras_build_static(sim_ls_s *ls) {
   R.fci.alloc(nnz_tot); R.fdiag.alloc(next_tot);
   R.lvl.alloc(2 * next_tot); R.lvl_rows.alloc(2 * next_tot); R.nlev.alloc(2 * nsub);
   R.lvl_ptr.alloc(2 * (next_tot + nsub));
-  if (ls->o.precision == SIM_PREC_MIXED) { R.fval32.alloc(4 * nnz_tot); R.dinv32.alloc(4 * next_tot); }
+  if (ls->o.precision != SIM_PREC_FP64) { R.fval32.alloc(4 * nnz_tot); R.dinv32.alloc(4 * next_tot); }
   else { R.fval.alloc(4 * nnz_tot); R.dinv.alloc(4 * next_tot); }
   int m = 1;
   while (m < maxcells) m <<= 1;
@@ -117,7 +118,7 @@ void ras_build_static(sim_ls_s *ls) {
   // shared-memory apply: blob sizes are static (rows and entries per
   // subdomain do not change with the ordering)
   {
-    int vb = ls->o.precision == SIM_PREC_MIXED ? 16 : 32;
+    int vb = ls->o.precision == SIM_PREC_FP64 ? 32 : (ls->o.precision == SIM_PREC_MIXED_BF16 ? 8 : 16);
     std::vector<long long> boff(nsub + 1, 0);
     size_t mx = 0;
     bool fits16 = true;
@@ -331,7 +332,7 @@ void ras_setup(sim_ls_s *ls) {
                                        R.ipos.p, R.frp.p, R.fci.p, R.fdiag.p, fsrc.p);
   k_ras_levels<<<R.nsub, 32, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.frp.p, R.fci.p, R.lvl.p, R.lvl_rows.p, R.nlev.p,
                                      R.lvl_ptr.p);
-  if (ls->o.precision == SIM_PREC_MIXED)
+  if (ls->o.precision != SIM_PREC_FP64)
     k_ras_factor<float><<<R.nsub, 128, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.frp.p, R.fci.p, R.fdiag.p, fsrc.p,
                                                ls->val.p, R.lvl_rows.p, R.nlev.p, R.lvl_ptr.p, R.fval32.p, R.dinv32.p);
   else
@@ -398,21 +399,31 @@ __global__ void k_ras_apply(const int *sub_ptr, const int *ext, const uint8_t *o
 }
 
 // pack the factors of each subdomain into its blob (one block per subdomain)
-template <class T>
+template <class TB> __device__ __forceinline__ TB to_blob(float v);
+template <> __device__ __forceinline__ float to_blob<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 to_blob<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <class TB> __device__ __forceinline__ TB to_blob_d(double v) { return to_blob<TB>((float)v); }
+template <> __device__ __forceinline__ double to_blob_d<double>(double v) { return v; }
+__device__ __forceinline__ float from_blob(float v) { return v; }
+__device__ __forceinline__ double from_blob(double v) { return v; }
+__device__ __forceinline__ float from_blob(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// T: factor type (FP32 or FP64), TB: stored value type (T, or BF16)
+template <class T, class TB>
 __global__ void k_ras_pack(const int *sub_ptr, const int *lrp_ptr, const int *ext, const uint8_t *owned,
                            const int *perm, const int *frp, const int *fci, const int *fdiag, const T *fv,
                            const T *dinv, const int *lvl_rows, const int *nlev, const int *lvl_ptr,
                            const long long *blob_off, unsigned char *blobs) {
   int s = blockIdx.x, base = sub_ptr[s], m = sub_ptr[s + 1] - base, pbase = lrp_ptr[s], fbase = base + s;
   int e = (lrp_ptr[s + 1] - pbase) - m;
-  blob_layout Lb = blob_lay(m, e, 4 * (int)sizeof(T));
+  blob_layout Lb = blob_lay(m, e, 4 * (int)sizeof(TB));
   unsigned char *b = blobs + blob_off[s];
   int *gidx = (int *)(b + Lb.gidx);
   uint16_t *rp = (uint16_t *)(b + Lb.rp), *dg = (uint16_t *)(b + Lb.dg);
   uint16_t *lrow = (uint16_t *)(b + Lb.lrow), *llev = (uint16_t *)(b + Lb.llev);
   uint16_t *urow = (uint16_t *)(b + Lb.urow), *ulev = (uint16_t *)(b + Lb.ulev);
   uint16_t *cols = (uint16_t *)(b + Lb.cols);
-  T *vals = (T *)(b + Lb.vals), *dv = (T *)(b + Lb.dinv);
+  TB *vals = (TB *)(b + Lb.vals), *dv = (TB *)(b + Lb.dinv);
   const int *pL = lvl_ptr + 2 * (base + s), *pU = pL + (m + 1);
   const int *rL = lvl_rows + 2 * base, *rU = rL + m;
   int nL = nlev[2 * s], nU = nlev[2 * s + 1];
@@ -433,10 +444,10 @@ __global__ void k_ras_pack(const int *sub_ptr, const int *lrp_ptr, const int *ex
       int j = q - pos - (q > qd ? 1 : 0);
       cols[j] = (uint16_t)fci[pbase + q];
       const T *src = fv + 4 * (size_t)(pbase + q);
-      vals[4 * j] = src[0]; vals[4 * j + 1] = src[1]; vals[4 * j + 2] = src[2]; vals[4 * j + 3] = src[3];
+      for (int t = 0; t < 4; t++) vals[4 * j + t] = to_blob_d<TB>(src[t]);
     }
     const T *d = dinv + 4 * (size_t)(base + pos);
-    dv[4 * pos] = d[0]; dv[4 * pos + 1] = d[1]; dv[4 * pos + 2] = d[2]; dv[4 * pos + 3] = d[3];
+    for (int t = 0; t < 4; t++) dv[4 * pos + t] = to_blob_d<TB>(d[t]);
   }
   int l0 = 1 < nL ? pL[1] : 0;
   for (int r = threadIdx.x; r < nLrows; r += blockDim.x) lrow[r] = (uint16_t)rL[l0 + r];
@@ -493,7 +504,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity
 // then runs the level-scheduled L and U solves on chip and writes (or adds)
 // the owned rows.
 #define RAS_BS 64
-template <class T, class Tin, bool ACC>
+template <class T, class Tin, bool ACC, class TB>
 __global__ void __launch_bounds__(RAS_BS) k_ras_apply_smem(const long long *blob_off, const unsigned char *blobs,
                                                            const Tin *__restrict__ f, T *__restrict__ x, int *err) {
   extern __shared__ uint4 sm4[];
@@ -505,7 +516,7 @@ __global__ void __launch_bounds__(RAS_BS) k_ras_apply_smem(const long long *blob
   unsigned char *sb = reinterpret_cast<unsigned char *>(sm4);
   // the first section (header + gidx) ends where rp starts; its size depends only on m
   int m0 = ((const int *)b)[0];
-  int head = blob_lay(m0, 0, 4 * (int)sizeof(T)).rp;
+  int head = blob_lay(m0, 0, 4 * (int)sizeof(TB)).rp;
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -526,32 +537,40 @@ __global__ void __launch_bounds__(RAS_BS) k_ras_apply_smem(const long long *blob
   int m = m0, nLl = hdr[2], nU = hdr[3];
   const int *gidx = (const int *)(sb + 16);
   T2 *y = reinterpret_cast<T2 *>(sm4 + total / 16);
-  if (ok0)
-    for (int pos = threadIdx.x; pos < m; pos += blockDim.x) {
-      int g = gidx[pos] >> 1;
-      T2 v; v.x = (T)f[2 * (size_t)g]; v.y = (T)f[2 * (size_t)g + 1];
-      y[pos] = v;
+  typedef typename v2_t<Tin>::type Tin2;
+  const Tin2 *f2 = reinterpret_cast<const Tin2 *>(f);
+  if (ok0)   // gather, 8 independent loads in flight per thread
+    for (int p0 = threadIdx.x; p0 < m; p0 += 8 * blockDim.x) {
+      Tin2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; u++) { int pos = p0 + u * blockDim.x; if (pos < m) v[u] = f2[gidx[pos] >> 1]; }
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        int pos = p0 + u * blockDim.x;
+        if (pos < m) { T2 t; t.x = (T)v[u].x; t.y = (T)v[u].y; y[pos] = t; }
+      }
     }
   bool ok1 = mbar_wait_bounded(&bar[1], 0, err, 2);
   // uniform decision (and the barrier after the gather): on a timeout the
   // error is recorded and nothing is written
   if (!__syncthreads_and(ok0 && ok1)) return;
-  blob_layout Lb = blob_lay(m, 0, 4 * (int)sizeof(T));
+  blob_layout Lb = blob_lay(m, 0, 4 * (int)sizeof(TB));
   const uint16_t *rp = (const uint16_t *)(sb + Lb.rp);
-  Lb = blob_lay(m, rp[m], 4 * (int)sizeof(T));
+  Lb = blob_lay(m, rp[m], 4 * (int)sizeof(TB));
   const uint16_t *dg = (const uint16_t *)(sb + Lb.dg);
   const uint16_t *lrow = (const uint16_t *)(sb + Lb.lrow), *llev = (const uint16_t *)(sb + Lb.llev);
   const uint16_t *urow = (const uint16_t *)(sb + Lb.urow), *ulev = (const uint16_t *)(sb + Lb.ulev);
   const uint16_t *cols = (const uint16_t *)(sb + Lb.cols);
-  const T *vals = (const T *)(sb + Lb.vals), *dv = (const T *)(sb + Lb.dinv);
+  const TB *vals = (const TB *)(sb + Lb.vals), *dv = (const TB *)(sb + Lb.dinv);
   for (int k = 0; k < nLl; k++) {
     for (int r = llev[k] + threadIdx.x; r < llev[k + 1]; r += blockDim.x) {
       int i = lrow[r];
       T2 a = y[i];
       int q1 = dg[i];
       for (int q = rp[i]; q < q1; q++) {
-        const T *B = vals + 4 * q; T2 c = y[cols[q]];
-        a.x -= B[0] * c.x + B[1] * c.y; a.y -= B[2] * c.x + B[3] * c.y;
+        const TB *B = vals + 4 * q; T2 c = y[cols[q]];
+        T b0 = from_blob(B[0]), b1 = from_blob(B[1]), b2 = from_blob(B[2]), b3 = from_blob(B[3]);
+        a.x -= b0 * c.x + b1 * c.y; a.y -= b2 * c.x + b3 * c.y;
       }
       y[i] = a;
     }
@@ -563,11 +582,13 @@ __global__ void __launch_bounds__(RAS_BS) k_ras_apply_smem(const long long *blob
       T2 a = y[i];
       int q1 = rp[i + 1];
       for (int q = dg[i]; q < q1; q++) {
-        const T *B = vals + 4 * q; T2 c = y[cols[q]];
-        a.x -= B[0] * c.x + B[1] * c.y; a.y -= B[2] * c.x + B[3] * c.y;
+        const TB *B = vals + 4 * q; T2 c = y[cols[q]];
+        T b0 = from_blob(B[0]), b1 = from_blob(B[1]), b2 = from_blob(B[2]), b3 = from_blob(B[3]);
+        a.x -= b0 * c.x + b1 * c.y; a.y -= b2 * c.x + b3 * c.y;
       }
-      const T *D = dv + 4 * i;
-      T2 o; o.x = D[0] * a.x + D[1] * a.y; o.y = D[2] * a.x + D[3] * a.y;
+      const TB *D = dv + 4 * i;
+      T2 o;
+      o.x = from_blob(D[0]) * a.x + from_blob(D[1]) * a.y; o.y = from_blob(D[2]) * a.x + from_blob(D[3]) * a.y;
       y[i] = o;
     }
     __syncthreads();
@@ -586,12 +607,16 @@ __global__ void __launch_bounds__(RAS_BS) k_ras_apply_smem(const long long *blob
 void ras_pack(sim_ls_s *ls) {
   ras_data &R = ls->ras;
   if (!R.smem_path) return;
-  if (ls->o.precision == SIM_PREC_MIXED)
-    k_ras_pack<float><<<R.nsub, 128, 0, ls->st>>>(R.sub_ptr.p, R.lrp_ptr.p, R.ext.p, R.owned.p, R.perm.p, R.frp.p,
+  if (ls->o.precision == SIM_PREC_MIXED_BF16)
+    k_ras_pack<float, __nv_bfloat16><<<R.nsub, 128, 0, ls->st>>>(R.sub_ptr.p, R.lrp_ptr.p, R.ext.p, R.owned.p, R.perm.p,
+                                                  R.frp.p, R.fci.p, R.fdiag.p, R.fval32.p, R.dinv32.p, R.lvl_rows.p,
+                                                  R.nlev.p, R.lvl_ptr.p, R.blob_off.p, R.blob.p);
+  else if (ls->o.precision != SIM_PREC_FP64)
+    k_ras_pack<float, float><<<R.nsub, 128, 0, ls->st>>>(R.sub_ptr.p, R.lrp_ptr.p, R.ext.p, R.owned.p, R.perm.p, R.frp.p,
                                                   R.fci.p, R.fdiag.p, R.fval32.p, R.dinv32.p, R.lvl_rows.p,
                                                   R.nlev.p, R.lvl_ptr.p, R.blob_off.p, R.blob.p);
   else
-    k_ras_pack<double><<<R.nsub, 128, 0, ls->st>>>(R.sub_ptr.p, R.lrp_ptr.p, R.ext.p, R.owned.p, R.perm.p, R.frp.p,
+    k_ras_pack<double, double><<<R.nsub, 128, 0, ls->st>>>(R.sub_ptr.p, R.lrp_ptr.p, R.ext.p, R.owned.p, R.perm.p, R.frp.p,
                                                    R.fci.p, R.fdiag.p, R.fval.p, R.dinv.p, R.lvl_rows.p,
                                                    R.nlev.p, R.lvl_ptr.p, R.blob_off.p, R.blob.p);
   RS_LAUNCHED(1);
@@ -603,25 +628,42 @@ __global__ void k_cast_acc(size_t m, const Tin *a, T *b, bool acc) {
   if (i < m) b[i] = acc ? b[i] + (T)a[i] : (T)a[i];
 }
 
+template <class T, class Tin, class TB>
+static void ras_apply_go(sim_ls_s *ls, const Tin *f, T *x, bool acc) {
+  ras_data &R = ls->ras;
+  if (acc) k_ras_apply_smem<T, Tin, true, TB><<<R.nsub, RAS_BS, R.smem_bytes, ls->st>>>(R.blob_off.p, R.blob.p, f, x, ls->errw_dev);
+  else k_ras_apply_smem<T, Tin, false, TB><<<R.nsub, RAS_BS, R.smem_bytes, ls->st>>>(R.blob_off.p, R.blob.p, f, x, ls->errw_dev);
+}
+template <class T, class Tin> static void ras_apply_launch(sim_ls_s *ls, const Tin *f, T *x, bool acc);
+template <> void ras_apply_launch<double, double>(sim_ls_s *ls, const double *f, double *x, bool acc) {
+  ras_apply_go<double, double, double>(ls, f, x, acc);
+}
+template <> void ras_apply_launch<float, float>(sim_ls_s *ls, const float *f, float *x, bool acc) {
+  if (ls->o.precision == SIM_PREC_MIXED_BF16) ras_apply_go<float, float, __nv_bfloat16>(ls, f, x, acc);
+  else ras_apply_go<float, float, float>(ls, f, x, acc);
+}
+template <> void ras_apply_launch<float, double>(sim_ls_s *ls, const double *f, float *x, bool acc) {
+  if (ls->o.precision == SIM_PREC_MIXED_BF16) ras_apply_go<float, double, __nv_bfloat16>(ls, f, x, acc);
+  else ras_apply_go<float, double, float>(ls, f, x, acc);
+}
+
 template <class T, class Tin> void ls_ras_apply(sim_ls_s *ls, const Tin *f, T *x, bool accumulate) {
   ras_data &R = ls->ras;
   cudaStream_t s = ls->st;
   if (R.smem_path) {
     static bool attr = false;
     if (!attr) {
-      RS_CUDA(cudaFuncSetAttribute(k_ras_apply_smem<float, float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RAS_SMEM_BUDGET));
-      RS_CUDA(cudaFuncSetAttribute(k_ras_apply_smem<float, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RAS_SMEM_BUDGET));
-      RS_CUDA(cudaFuncSetAttribute(k_ras_apply_smem<float, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RAS_SMEM_BUDGET));
-      RS_CUDA(cudaFuncSetAttribute(k_ras_apply_smem<float, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RAS_SMEM_BUDGET));
-      RS_CUDA(cudaFuncSetAttribute(k_ras_apply_smem<double, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RAS_SMEM_BUDGET));
-      RS_CUDA(cudaFuncSetAttribute(k_ras_apply_smem<double, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RAS_SMEM_BUDGET));
+#define RAS_ATTR(...) RS_CUDA(cudaFuncSetAttribute(k_ras_apply_smem<__VA_ARGS__>, cudaFuncAttributeMaxDynamicSharedMemorySize, RAS_SMEM_BUDGET))
+      RAS_ATTR(float, float, false, float); RAS_ATTR(float, float, true, float);
+      RAS_ATTR(float, double, false, float); RAS_ATTR(float, double, true, float);
+      RAS_ATTR(float, float, false, __nv_bfloat16); RAS_ATTR(float, float, true, __nv_bfloat16);
+      RAS_ATTR(float, double, false, __nv_bfloat16); RAS_ATTR(float, double, true, __nv_bfloat16);
+      RAS_ATTR(double, double, false, double); RAS_ATTR(double, double, true, double);
+#undef RAS_ATTR
       attr = true;
     }
     rs_timed tm(ls, SIM_T_RAS);
-    if (accumulate)
-      k_ras_apply_smem<T, Tin, true><<<R.nsub, RAS_BS, R.smem_bytes, s>>>(R.blob_off.p, R.blob.p, f, x, ls->errw_dev);
-    else
-      k_ras_apply_smem<T, Tin, false><<<R.nsub, RAS_BS, R.smem_bytes, s>>>(R.blob_off.p, R.blob.p, f, x, ls->errw_dev);
+    ras_apply_launch<T, Tin>(ls, f, x, accumulate);
     RS_LAUNCHED(1);
     return;
   }

@@ -775,7 +775,7 @@ extern "C" sim_status sim_ls_apply(sim_ls_t ls, int op, const double *x, double 
   dbuf<double> xin, yout;
   xin.alloc(m); yout.alloc(m);
   RS_CUDA(cudaMemcpyAsync(xin.p, x, m * sizeof(double), cudaMemcpyDefault, s));
-  bool mixed = ls->o.precision == SIM_PREC_MIXED;
+  bool mixed = ls->o.precision != SIM_PREC_FP64;
   if (op == SIM_OP_SPMV) ls_spmv64(ls, xin.p, yout.p);
   else if (op == SIM_OP_RAS) {
     if (mixed) {

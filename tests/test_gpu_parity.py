@@ -190,6 +190,15 @@ def test_mixed_precision_operators_track_fp64():
         assert np.abs(yg - yo).max() <= 1e-3 * np.abs(yo).max(), op
     yg, itsg, relg = gl.solve(1e-8)
     assert relg <= 1e-8
+    gb = R.LinearSystem(c.nx, c.ny, c.nz, 2, *_shared_system(c, 600)[2][:2], [w.perf_cells[0] for w in c.wells],
+                        precision=R.PREC_MIXED_BF16)
+    gb.set(*_shared_system(c, 600)[2][2:])
+    gb.setup()
+    yb = gb.apply(R.OP_RAS, x)
+    yo = o.ls.ras(x)
+    assert np.abs(yb - yo).max() <= 3e-2 * np.abs(yo).max()
+    yb, itsb, relb = gb.solve(1e-8)
+    assert relb <= 1e-8
 
 
 def _run_compare(case, nsteps, **opts):
@@ -232,6 +241,12 @@ def test_whole_run_channelised_case_mixed_with_chop():
     ragged edge, mixed precision, 3 steps."""
     c = I.case2(nx=42, ny=38, nz=8)
     _run_compare(c, 3, precision=R.PREC_MIXED)
+
+
+def test_whole_run_cfg0_bf16_ras():
+    """RAS factor values stored in BF16 (FP32 arithmetic): the converged
+    Newton states still match the FP64 oracle."""
+    _run_compare(I.case0(), 5, precision=R.PREC_MIXED_BF16)
 
 
 def test_whole_run_inexact_newton():
