@@ -119,6 +119,7 @@ void ras_build_static(sim_ls_s *ls) {
   // subdomain do not change with the ordering)
   {
     int vb = ls->o.precision == SIM_PREC_FP64 ? 32 : (ls->o.precision == SIM_PREC_MIXED_BF16 ? 8 : 16);
+    int yb = ls->o.precision == SIM_PREC_FP64 ? 16 : 8;   // local vector: double2 or float2 per row
     std::vector<long long> boff(nsub + 1, 0);
     size_t mx = 0;
     bool fits16 = true;
@@ -127,7 +128,7 @@ void ras_build_static(sim_ls_s *ls) {
       if (ms >= 65535 || nz >= 65535) fits16 = false;
       blob_layout L = blob_lay(ms, nz - ms, vb);
       boff[s2 + 1] = boff[s2] + L.total;
-      mx = std::max(mx, (size_t)L.total + (size_t)ms * (vb / 2));
+      mx = std::max(mx, (size_t)L.total + (size_t)ms * yb);
     }
     R.smem_bytes = mx;
     R.smem_path = fits16 && mx <= RAS_SMEM_BUDGET;
