@@ -301,102 +301,80 @@ void ls_setup(sim_ls_s *ls) {
 // results do not depend on scheduling.
 #define ORTHO_BS 256
 #define ORTHO_MAXV 64
-// two blocks per SM: each thread covers many rows, so the per-thread dot
-// accumulators are reduced across the block only once per many FMAs
-static int ortho_blocks(int nu) { int b = (nu + 8191) / 8192; return b < 1 ? 1 : (b > 304 ? 304 : b); }
+// Each block owns a fixed chunk of ORTHO_CH rows and keeps its slice of w in
+// shared memory.  Basis vectors are streamed one at a time (vector-outer,
+// rows-inner): loads are coalesced and independent, unrolled 8 ways, and
+// every dot product needs one accumulator per thread.
+#define ORTHO_CH 4096
+static int ortho_blocks(int nu) { return (nu + ORTHO_CH - 1) / ORTHO_CH; }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ double block_sum_d(double v, double *sred) {   // result valid in thread 0
+  v = warp_sum_d(v);
+  if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) for (int q = 0; q < ORTHO_BS / 32; q++) t += sred[q];
+  __syncthreads();
+  return t;
+}
 
-// d_k = V_k . w for k < nv and, if with_norm, d_nv = w . w.  Every thread
-// keeps one accumulator per basis vector in registers (MAXV of them, the
-// compile-time bound of nv), so the nv loads of a row are independent.
-template <int MAXV>
+// part[k][b] = V_k . w over the block's rows (k < nv); with_norm: part[nv][b] = w . w
 __global__ void __launch_bounds__(ORTHO_BS) k_ortho_dots(int nu, int nv, const double *__restrict__ V,
                                                          const double *__restrict__ w, double *part, int with_norm,
                                                          const int *cond) {
   if (cond && *cond == 0) return;
-  __shared__ double sred[MAXV + 1][ORTHO_BS / 32];
-  double acc[MAXV + 1];
-#pragma unroll
-  for (int k = 0; k <= MAXV; k++) acc[k] = 0.0;
-  int nblk = gridDim.x, chunk = (nu + nblk - 1) / nblk;
-  int i0 = blockIdx.x * chunk, i1 = min(nu, i0 + chunk);
-  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    double wi = w[i];
-#pragma unroll
-    for (int k = 0; k < MAXV; k++)
-      if (k < nv) acc[k] += __ldg(V + (size_t)k * nu + i) * wi;
-    acc[MAXV] += wi * wi;
-  }
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k <= MAXV; k++) {
-    if (k < nv || k == MAXV) {
-      double v = warp_sum_d(acc[k]);
-      if (lane == 0) sred[k][wid] = v;
-    }
-  }
+  __shared__ double ws[ORTHO_CH];
+  __shared__ double sred[ORTHO_BS / 32];
+  int nblk = gridDim.x, i0 = blockIdx.x * ORTHO_CH, len = min(ORTHO_CH, nu - i0);
+  for (int t = threadIdx.x; t < len; t += ORTHO_BS) ws[t] = w[i0 + t];
   __syncthreads();
-  int nd = nv + (with_norm ? 1 : 0);
-  for (int k = threadIdx.x; k < nd; k += blockDim.x) {
-    int src = k < nv ? k : MAXV;
-    double t = 0; for (int q = 0; q < ORTHO_BS / 32; q++) t += sred[src][q];
-    part[(size_t)k * nblk + blockIdx.x] = t;
+  for (int k = 0; k < nv + (with_norm ? 1 : 0); k++) {
+    double acc = 0.0;
+    if (k < nv) {
+      const double *vk = V + (size_t)k * nu + i0;
+#pragma unroll 8
+      for (int t = threadIdx.x; t < len; t += ORTHO_BS) acc += __ldg(vk + t) * ws[t];
+    } else {
+      for (int t = threadIdx.x; t < len; t += ORTHO_BS) acc += ws[t] * ws[t];
+    }
+    double tot = block_sum_d(acc, sred);
+    if (threadIdx.x == 0) part[(size_t)k * nblk + blockIdx.x] = tot;
   }
 }
 
-// w -= sum_k h_k V_k (independent loads of the nv basis entries of a row),
-// then d_0 = ||w||^2
-template <int MAXV>
+// w -= sum_k h_k V_k over the block's rows, then part[0][b] = ||w||^2
 __global__ void __launch_bounds__(ORTHO_BS) k_ortho_update(int nu, int nv, const double *__restrict__ V, double *w,
                                                            const double *__restrict__ h, double *part,
                                                            const int *cond) {
   if (cond && *cond == 0) return;
+  __shared__ double ws[ORTHO_CH];
   __shared__ double sred[ORTHO_BS / 32];
-  double hk[MAXV];
-#pragma unroll
-  for (int k = 0; k < MAXV; k++) hk[k] = k < nv ? h[k] : 0.0;
-  int nblk = gridDim.x, chunk = (nu + nblk - 1) / nblk;
-  int i0 = blockIdx.x * chunk, i1 = min(nu, i0 + chunk);
-  double n2 = 0.0;
-  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    double sacc = 0.0;
-#pragma unroll
-    for (int k = 0; k < MAXV; k++)
-      if (k < nv) sacc += hk[k] * __ldg(V + (size_t)k * nu + i);
-    double wi = w[i] - sacc;
-    w[i] = wi;
-    n2 += wi * wi;
+  int i0 = blockIdx.x * ORTHO_CH, len = min(ORTHO_CH, nu - i0);
+  for (int t = threadIdx.x; t < len; t += ORTHO_BS) ws[t] = w[i0 + t];
+  for (int k = 0; k < nv; k++) {        // each thread updates only its own rows: no barrier needed
+    double hk = h[k];
+    const double *vk = V + (size_t)k * nu + i0;
+#pragma unroll 8
+    for (int t = threadIdx.x; t < len; t += ORTHO_BS) ws[t] -= hk * __ldg(vk + t);
   }
-  n2 = warp_sum_d(n2);
-  if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = n2;
-  __syncthreads();
-  if (threadIdx.x == 0) { double t = 0; for (int q = 0; q < ORTHO_BS / 32; q++) t += sred[q]; part[blockIdx.x] = t; }
+  double n2 = 0.0;
+  for (int t = threadIdx.x; t < len; t += ORTHO_BS) { double v = ws[t]; w[i0 + t] = v; n2 += v * v; }
+  double tot = block_sum_d(n2, sred);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-// MAXV = nv rounded up to a multiple of 4 (the compiler issues the FMAs of
-// a fully unrolled MAXV loop even for k >= nv, so the bound must be tight)
-#define ORTHO_CASE(N, KERNEL, ...) case N: KERNEL<N><<<nblk, ORTHO_BS, 0, s>>>(__VA_ARGS__); break;
-#define ORTHO_SWITCH(KERNEL, ...)                                                                         \
-  switch ((nv + 3) & ~3) {                                                                                \
-    ORTHO_CASE(4, KERNEL, __VA_ARGS__) ORTHO_CASE(8, KERNEL, __VA_ARGS__) ORTHO_CASE(12, KERNEL, __VA_ARGS__)  \
-    ORTHO_CASE(16, KERNEL, __VA_ARGS__) ORTHO_CASE(20, KERNEL, __VA_ARGS__) ORTHO_CASE(24, KERNEL, __VA_ARGS__) \
-    ORTHO_CASE(28, KERNEL, __VA_ARGS__) ORTHO_CASE(32, KERNEL, __VA_ARGS__) ORTHO_CASE(36, KERNEL, __VA_ARGS__) \
-    ORTHO_CASE(40, KERNEL, __VA_ARGS__) ORTHO_CASE(44, KERNEL, __VA_ARGS__) ORTHO_CASE(48, KERNEL, __VA_ARGS__) \
-    ORTHO_CASE(52, KERNEL, __VA_ARGS__) ORTHO_CASE(56, KERNEL, __VA_ARGS__) ORTHO_CASE(60, KERNEL, __VA_ARGS__) \
-    default: KERNEL<64><<<nblk, ORTHO_BS, 0, s>>>(__VA_ARGS__); break;                                     \
-  }
 static void ortho_dots(int nu, int nv, const double *V, const double *w, double *part, int with_norm, const int *cond,
                        int nblk, cudaStream_t s) {
-  ORTHO_SWITCH(k_ortho_dots, nu, nv, V, w, part, with_norm, cond)
+  k_ortho_dots<<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, part, with_norm, cond);
 }
 static void ortho_update(int nu, int nv, const double *V, double *w, const double *h, double *part, const int *cond,
                          int nblk, cudaStream_t s) {
-  ORTHO_SWITCH(k_ortho_update, nu, nv, V, w, h, part, cond)
+  k_ortho_update<<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, h, part, cond);
 }
 
 // out[k] = sum over blocks of part[k][*]: one warp per k, lanes add a fixed
@@ -428,7 +406,8 @@ __global__ void k_arnoldi_col(int j, int m, const double *h1, const double *h2, 
   bool re = *flag != 0;
   for (int k = 0; k <= j; k++) col[k] = re ? h1[k] + h2[k] : h1[k];
   double hn = sqrt(re ? *nrm_b : *nrm_a);
-  *hnorm = hn;
+  hnorm[0] = hn;
+  hnorm[1] = hn > 0.0 ? 1.0 / hn : 0.0;
   for (int k = 0; k < j; k++) {
     double t = cs[k] * col[k] + sn[k] * col[k + 1];
     col[k + 1] = -sn[k] * col[k] + cs[k] * col[k + 1];
@@ -443,10 +422,9 @@ __global__ void k_arnoldi_col(int j, int m, const double *h1, const double *h2, 
   host[1] = hn;
   host[2] += re ? 1.0 : 0.0;
 }
-__global__ void k_scale(int nu, const double *w, const double *hn, double *v) {
+__global__ void k_scale(int nu, const double *w, const double *inv_hn, double *v) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double s = *hn, inv = s > 0.0 ? 1.0 / s : 0.0;     // one division per thread, not per entry
-  if (i < nu) v[i] = w[i] * inv;
+  if (i < nu) v[i] = w[i] * *inv_hn;       // 1 / h_{j+1,j} formed once by k_arnoldi_col
 }
 __global__ void k_start(int nu, const double *r, double beta, double *v0, double *G, int m) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -483,7 +461,7 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres) {
   ls->partial.ensure((size_t)(ORTHO_MAXV + 1) * nblk + 8);
   ls->hbuf.ensure((size_t)(m + 1) * (m + 1) + 4 * (m + 1) + 4 * ORTHO_MAXV + 16);
   double *G = ls->hbuf.p, *h1 = G + (size_t)(m + 1) * (m + 1) + 3 * (m + 1), *h2 = h1 + ORTHO_MAXV + 1,
-         *nrm = h2 + ORTHO_MAXV, *nrm_b = nrm + 1, *hn = nrm_b + 1, *yk = hn + 1;
+         *nrm = h2 + ORTHO_MAXV, *nrm_b = nrm + 1, *hn = nrm_b + 1, *yk = hn + 2;
   int *flag = reinterpret_cast<int *>(yk + ORTHO_MAXV);
   volatile double *hp = ls->hpin;
   double *hp_dev;
@@ -524,7 +502,7 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres) {
         ortho_update(nu, nv, ls->V.p, ls->w.p, h2, ls->partial.p, flag, nblk, s);
         reduce_parts(1, nblk, ls->partial.p, nrm_b, flag, s);
         k_arnoldi_col<<<1, 1, 0, s>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, hp_dev);
-        k_scale<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->w.p, hn, ls->V.p + (size_t)(j + 1) * nu);
+        k_scale<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->w.p, hn + 1, ls->V.p + (size_t)(j + 1) * nu);
         RS_LAUNCHED(11);
       }
       RS_CHECK_LAUNCH();
