@@ -162,7 +162,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="cfg2")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_bf16", "fp64"])
+    ap.add_argument("--precision", default="mixed_bf16", choices=["mixed", "mixed_bf16", "fp64"],
+                    help="preconditioner precision: FP32 AMG/ILU with BF16 RAS values (the 1M-cell case's "
+                         "setting), FP32 throughout, or FP64")
     ap.add_argument("--max-lin", type=int, default=200)
     ap.add_argument("--roofline", default="ras", choices=["ras", "spmv64", "spmv_prec"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -229,6 +231,13 @@ def main():
     newton_per_step = (st1["newton"] - st0["newton"]) / args.steps
     its_per_newton = (st1["linear_its"] - st0["linear_its"]) / max(1, st1["newton"] - st0["newton"])
 
+    # level structure of the reordered subdomain factors (sets the latency of the RAS solves)
+    nsub = sim.ls.ras_count()
+    lv = [sim.ls.ras_levels(s_)[:2] for s_ in range(0, nsub, max(1, nsub // 64))]
+    ras_levels = {"subdomains": nsub, "sampled": len(lv),
+                  "L_mean": float(np.mean([a for a, _ in lv])), "L_max": int(max(a for a, _ in lv)),
+                  "U_mean": float(np.mean([b_ for _, b_ in lv])), "U_max": int(max(b_ for _, b_ in lv))}
+
     # roofline of the chosen kernel family (algorithmic bytes / event time)
     rp = sim.ls.export(R.X_ROWPTR, 0, np.int32)
     nb, nnzb = len(rp) - 1, int(rp[-1])
@@ -287,7 +296,8 @@ def main():
                        "relres": case.lin_tol, "precision": args.precision, "learned_warm_start": False,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "working set larger than L2 (no flush needed)",
-                       "newton_per_step": newton_per_step, "fgmres_its_per_newton": its_per_newton},
+                       "newton_per_step": newton_per_step, "fgmres_its_per_newton": its_per_newton,
+                       "ras_levels": ras_levels},
             "roofline": roof, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
             "phases_ms_per_step": {k: (st1[k] - st0[k]) / args.steps for k in ("ms_assemble", "ms_setup", "ms_solve")},
             "kernel_breakdown": breakdown,

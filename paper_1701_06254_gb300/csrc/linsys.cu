@@ -305,7 +305,7 @@ void ls_setup(sim_ls_s *ls) {
 // shared memory.  Basis vectors are streamed one at a time (vector-outer,
 // rows-inner): loads are coalesced and independent, unrolled 8 ways, and
 // every dot product needs one accumulator per thread.
-#define ORTHO_CH 4096
+#define ORTHO_CH 8192
 static int ortho_blocks(int nu) { return (nu + ORTHO_CH - 1) / ORTHO_CH; }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(ORTHO_BS) k_ortho_dots(int nu, int nv, const d
                                                          const double *__restrict__ w, double *part, int with_norm,
                                                          const int *cond) {
   if (cond && *cond == 0) return;
-  __shared__ double ws[ORTHO_CH];
+  extern __shared__ double ws[];             // ORTHO_CH doubles (dynamic: 64 KB)
   __shared__ double sred[ORTHO_BS / 32];
   int nblk = gridDim.x, i0 = blockIdx.x * ORTHO_CH, len = min(ORTHO_CH, nu - i0);
   for (int t = threadIdx.x; t < len; t += ORTHO_BS) ws[t] = w[i0 + t];
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(ORTHO_BS) k_ortho_update(int nu, int nv, const
                                                            const double *__restrict__ h, double *part,
                                                            const int *cond) {
   if (cond && *cond == 0) return;
-  __shared__ double ws[ORTHO_CH];
+  extern __shared__ double ws[];
   __shared__ double sred[ORTHO_BS / 32];
   int i0 = blockIdx.x * ORTHO_CH, len = min(ORTHO_CH, nu - i0);
   for (int t = threadIdx.x; t < len; t += ORTHO_BS) ws[t] = w[i0 + t];
@@ -368,13 +368,22 @@ __global__ void __launch_bounds__(ORTHO_BS) k_ortho_update(int nu, int nv, const
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
+static void ortho_attr() {
+  static bool done = false;
+  if (done) return;
+  RS_CUDA(cudaFuncSetAttribute(k_ortho_dots, cudaFuncAttributeMaxDynamicSharedMemorySize, ORTHO_CH * 8));
+  RS_CUDA(cudaFuncSetAttribute(k_ortho_update, cudaFuncAttributeMaxDynamicSharedMemorySize, ORTHO_CH * 8));
+  done = true;
+}
 static void ortho_dots(int nu, int nv, const double *V, const double *w, double *part, int with_norm, const int *cond,
                        int nblk, cudaStream_t s) {
-  k_ortho_dots<<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, part, with_norm, cond);
+  ortho_attr();
+  k_ortho_dots<<<nblk, ORTHO_BS, ORTHO_CH * 8, s>>>(nu, nv, V, w, part, with_norm, cond);
 }
 static void ortho_update(int nu, int nv, const double *V, double *w, const double *h, double *part, const int *cond,
                          int nblk, cudaStream_t s) {
-  k_ortho_update<<<nblk, ORTHO_BS, 0, s>>>(nu, nv, V, w, h, part, cond);
+  ortho_attr();
+  k_ortho_update<<<nblk, ORTHO_BS, ORTHO_CH * 8, s>>>(nu, nv, V, w, h, part, cond);
 }
 
 // out[k] = sum over blocks of part[k][*]: one warp per k, lanes add a fixed
