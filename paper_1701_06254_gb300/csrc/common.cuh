@@ -157,6 +157,7 @@ struct ras_data {
   int max_lvl_ptr = 0;
   // shared-memory apply: one packed blob per subdomain (see ras.cu)
   bool smem_path = false;
+  bool built = false;           // a setup has run (level sets exportable)
   size_t smem_bytes = 0;        // largest blob + local vector
   dbuf<long long> blob_off;     // nsub + 1 byte offsets
   dbuf<unsigned char> blob;

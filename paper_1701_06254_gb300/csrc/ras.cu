@@ -341,6 +341,7 @@ void ras_setup(sim_ls_s *ls) {
                                                 ls->val.p, R.lvl_rows.p, R.nlev.p, R.lvl_ptr.p, R.fval.p, R.dinv.p);
   RS_LAUNCHED(4);
   ras_pack(ls);
+  R.built = true;
   RS_CHECK_LAUNCH();
 }
 

@@ -879,7 +879,7 @@ extern "C" sim_status sim_ls_export(sim_ls_t ls, int what, int index, void *dst,
     }
     case SIM_X_RAS_EXT: case SIM_X_RAS_LEVELS: {
       if (index < 0 || index >= ls->ras.nsub) RS_FAIL(SIM_ERR_ARG, "sim_ls_export: no subdomain %d", index);
-      if (!ls->have_setup) RS_FAIL(SIM_ERR_STATE, "sim_ls_export: no setup yet");
+      if (!ls->ras.built) RS_FAIL(SIM_ERR_STATE, "sim_ls_export: no setup yet");
       std::vector<int> sp = d2h(ls->ras.sub_ptr.p + index, 2, s);
       int base = sp[0], m = sp[1] - sp[0];
       if (what == SIM_X_RAS_EXT) {
