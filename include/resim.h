@@ -196,6 +196,14 @@ sim_status sim_ls_solve(sim_ls_t ls, double tol, double *y, int *iters, double *
 enum { SIM_OP_SPMV = 0, SIM_OP_RAS = 1, SIM_OP_VCYCLE = 2, SIM_OP_CPR = 3 };
 sim_status sim_ls_apply(sim_ls_t ls, int op, const double *x, double *y);
 
+/* ||b - A x||_2 for the current system (the decoupled one after
+ * sim_ls_setup): x is 2 values per block row, host or device; the norm is
+ * returned in host memory.  Uses device scratch that the library allocates
+ * (the residual vector and per-block partial sums); synchronises the
+ * stream.  The sum is deterministic (fixed order).  Errors: SIM_ERR_ARG for
+ * NULL arguments, SIM_ERR_CUDA / SIM_ERR_OOM from the runtime. */
+sim_status sim_ls_residual_norm(sim_ls_t ls, const double *x, double *norm);
+
 /* Copy internal arrays to host memory for inspection.  what / index:
  *  SIM_X_VALS, 0      decoupled block values (4*nnzb doubles)
  *  SIM_X_RHS, 0       decoupled right-hand side (2*nb doubles)

@@ -116,6 +116,7 @@ def lib():
             "sim_ls_solve": (I, [P, D, P, C.POINTER(I), C.POINTER(D)]),
             "sim_ls_apply": (I, [P, I, P, P]),
             "sim_ls_export": (I, [P, I, I, P, C.c_size_t, C.POINTER(C.c_size_t)]),
+            "sim_ls_residual_norm": (I, [P, P, C.POINTER(D)]),
             "sim_kernel_timer": (I, [P, C.c_uint]),
             "sim_kernel_time": (I, [P, I, C.POINTER(C.c_longlong), C.POINTER(D)]),
             "sim_launch_count": (C.c_longlong, []),
@@ -206,6 +207,13 @@ class LinearSystem:
         y = np.zeros_like(x)
         _check(self._L.sim_ls_apply(self.h, op, _ptr(x), _ptr(y)))
         return y
+
+    def residual_norm(self, x):
+        """||b - A x||_2 of the current (decoupled after setup) system."""
+        x = np.ascontiguousarray(x, np.float64) if isinstance(x, np.ndarray) else x
+        nrm = C.c_double()
+        _check(self._L.sim_ls_residual_norm(self.h, _ptr(x), C.byref(nrm)))
+        return nrm.value
 
     def export(self, what, index=0, dtype=np.float64):
         need = C.c_size_t()

@@ -206,6 +206,7 @@ void ls_setup(sim_ls_s *ls);
 int ls_solve(sim_ls_s *ls, double tol, int *its, double *relres);   // solution in ls->y
 void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32);
 void ls_spmv64(sim_ls_s *ls, const double *x, double *y);
+double ls_residual_norm(sim_ls_s *ls, const double *x_dev);
 template <class T, class Tin> void ls_ras_apply(sim_ls_s *ls, const Tin *f, T *x, bool accumulate);
 void ras_build_static(sim_ls_s *ls);
 void ras_setup(sim_ls_s *ls);

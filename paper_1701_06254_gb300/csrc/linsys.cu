@@ -305,7 +305,7 @@ void ls_setup(sim_ls_s *ls) {
 // shared memory.  Basis vectors are streamed one at a time (vector-outer,
 // rows-inner): loads are coalesced and independent, unrolled 8 ways, and
 // every dot product needs one accumulator per thread.
-#define ORTHO_CH 8192
+#define ORTHO_CH 4096
 static int ortho_blocks(int nu) { return (nu + ORTHO_CH - 1) / ORTHO_CH; }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(ORTHO_BS) k_ortho_dots(int nu, int nv, const d
                                                          const double *__restrict__ w, double *part, int with_norm,
                                                          const int *cond) {
   if (cond && *cond == 0) return;
-  extern __shared__ double ws[];             // ORTHO_CH doubles (dynamic: 64 KB)
+  extern __shared__ double ws[];             // ORTHO_CH doubles (dynamic)
   __shared__ double sred[ORTHO_BS / 32];
   int nblk = gridDim.x, i0 = blockIdx.x * ORTHO_CH, len = min(ORTHO_CH, nu - i0);
   for (int t = threadIdx.x; t < len; t += ORTHO_BS) ws[t] = w[i0 + t];
@@ -538,4 +538,14 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres) {
   *its_out = its;
   *relres = beta / bn;
   return rc;
+}
+
+// ------------------------------------------------ residual norm (API) ----
+// ||b - A x||_2: residual vector in a library-owned buffer, then the
+// deterministic two-stage sum of squares.
+double ls_residual_norm(sim_ls_s *ls, const double *x_dev) {
+  size_t nu = 2 * (size_t)ls->nb;
+  ls->r.ensure(nu);
+  spmv<double, double, double, double>(ls, ls->val.p, x_dev, ls->b.p, ls->r.p, ls->st);
+  return rs_norm2(ls->r.p, (int)nu, ls->st);
 }

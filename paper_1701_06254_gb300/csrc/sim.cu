@@ -813,6 +813,17 @@ extern "C" sim_status sim_ls_apply(sim_ls_t ls, int op, const double *x, double 
   ABI_END
 }
 
+extern "C" sim_status sim_ls_residual_norm(sim_ls_t ls, const double *x, double *norm) {
+  ABI_BEGIN
+  if (!ls || !x || !norm) RS_FAIL(SIM_ERR_ARG, "sim_ls_residual_norm: NULL argument");
+  size_t nu = 2 * (size_t)ls->nb;
+  dbuf<double> xd;
+  xd.alloc(nu);
+  RS_CUDA(cudaMemcpyAsync(xd.p, x, nu * sizeof(double), cudaMemcpyDefault, ls->st));
+  *norm = ls_residual_norm(ls, xd.p);
+  ABI_END
+}
+
 template <class T>
 static void put(void *dst, size_t bytes, size_t *needed, const T *src_dev, size_t count, cudaStream_t s) {
   size_t need = count * sizeof(T);

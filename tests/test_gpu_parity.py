@@ -268,6 +268,17 @@ def test_edge_grids_run(mk):
     _run_compare(c, 2)
 
 
+def test_residual_norm_entry_point():
+    """sim_ls_residual_norm equals the oracle's ||b - A x|| on the decoupled system."""
+    c = I.small_case(7, 6, 3, seed=81)
+    o, gl, _ = _shared_system(c, 800)
+    o.ls.setup(); gl.setup()
+    _, _, _, db, _ = o.ls.get()
+    x = np.random.default_rng(8).standard_normal(2 * (c.n + 2))
+    ref = np.linalg.norm(db - o.ls.mv(x))
+    assert abs(gl.residual_norm(x) - ref) <= 1e-12 * ref
+
+
 def test_zero_rhs_and_errors():
     c = I.small_case(4, 4, 2, seed=71)
     o, gl, (rp, ci, val, b, key) = _shared_system(c, 700)
