@@ -204,6 +204,26 @@ sim_status sim_ls_apply(sim_ls_t ls, int op, const double *x, double *y);
  * NULL arguments, SIM_ERR_CUDA / SIM_ERR_OOM from the runtime. */
 sim_status sim_ls_residual_norm(sim_ls_t ls, const double *x, double *norm);
 
+/* The same norm as sim_ls_residual_norm for callers that must not allocate
+ * memory: code that runs under another allocator's budget (for example a
+ * framework whose caching allocator already holds the device memory, where a
+ * fresh cudaMalloc can fail), and latency-sensitive loops in which the
+ * device-wide synchronisation of cudaMalloc / cudaFree is unacceptable.
+ * There is no counterpart of this entry point in the paper.
+ *
+ * Nothing is allocated: the per-block partial sums use a fixed device array
+ * inside the library (4096 doubles, 32 KB, held by every GPU that loads the
+ * library until the process exits).  Limit: n + n_wells <= 4096 * 4096
+ * block rows; larger systems get SIM_ERR_ARG.  x (2 per block row) and
+ * norm (one double) must be device memory (SIM_ERR_ARG otherwise); the
+ * result is written to *norm on the handle's stream and the call does not
+ * synchronise.  The first call on a device looks up the array's device
+ * address (once per device, with that device current).  All calls share the
+ * array: calls whose work overlaps on the GPU (another stream, another
+ * thread, another handle) race on it and must be ordered by the caller.
+ * Each call overwrites every partial it reads, so no clearing is needed. */
+sim_status sim_ls_residual_norm_noalloc(sim_ls_t ls, const double *x_dev, double *norm_dev);
+
 /* Copy internal arrays to host memory for inspection.  what / index:
  *  SIM_X_VALS, 0      decoupled block values (4*nnzb doubles)
  *  SIM_X_RHS, 0       decoupled right-hand side (2*nb doubles)

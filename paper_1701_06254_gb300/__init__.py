@@ -117,6 +117,7 @@ def lib():
             "sim_ls_apply": (I, [P, I, P, P]),
             "sim_ls_export": (I, [P, I, I, P, C.c_size_t, C.POINTER(C.c_size_t)]),
             "sim_ls_residual_norm": (I, [P, P, C.POINTER(D)]),
+            "sim_ls_residual_norm_noalloc": (I, [P, P, P]),
             "sim_kernel_timer": (I, [P, C.c_uint]),
             "sim_kernel_time": (I, [P, I, C.POINTER(C.c_longlong), C.POINTER(D)]),
             "sim_launch_count": (C.c_longlong, []),
@@ -214,6 +215,11 @@ class LinearSystem:
         nrm = C.c_double()
         _check(self._L.sim_ls_residual_norm(self.h, _ptr(x), C.byref(nrm)))
         return nrm.value
+
+    def residual_norm_noalloc(self, x_dev, norm_dev):
+        """Same norm without allocating: x_dev and norm_dev are CUDA tensors;
+        the result is written to norm_dev on the library stream."""
+        _check(self._L.sim_ls_residual_norm_noalloc(self.h, _ptr(x_dev), _ptr(norm_dev)))
 
     def export(self, what, index=0, dtype=np.float64):
         need = C.c_size_t()
