@@ -91,19 +91,30 @@ class Clocks:
 
 
 def ras_bytes(ls, precision):
-    """Algorithmic bytes of one RAS apply: each factor block and its column
-    index once (L and U together), the inverse diagonal blocks, the
-    position/row index arrays, the gather of the extended rows and the
-    restricted scatter of the owned rows."""
-    import paper_1701_06254_gb300 as R
+    """Algorithmic bytes of one RAS apply with the packed per-subdomain
+    factors: every off-diagonal factor block (values + 2-byte column) and
+    every row's record (gather index, six 2-byte row/level indices, inverse
+    diagonal block) read once, the extended right-hand side gathered and the
+    owned rows written.  The two applications of Algorithm 2 differ in their
+    vectors (FP64 in / FP32 out, FP32 in / FP32 accumulated), so the
+    vector bytes are their average."""
     vb = {"mixed": 16, "mixed_bf16": 8, "fp64": 32}[precision]
-    xb = 8 if precision == "fp64" else 4
     nsub = ls.ras_count()
     nnz = nxt = own = 0
     for s in range(nsub):
         o, e, z = ls.ras_sizes(s)
         own += o; nxt += e; nnz += z
-    return nnz * (vb + 4) + nxt * (vb + 4 * 4) + nxt * 2 * xb + own * 2 * xb
+    off = nnz - nxt
+    if precision == "fp64":
+        gather, scatter = 16.0, 24.0          # double2 in; write, or read + write
+    else:
+        gather, scatter = 12.0, 12.0          # double2 / float2 in; float2 write, or read + write
+    return off * (vb + 2) + nxt * (4 + 12 + vb) + nxt * gather + own * scatter
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
+# ncu capture summarised in profiles/ (null once the kernel changes)
+NCU_TRAFFIC = {("ras", "mixed_bf16"): 172.3e6}
 
 
 def spmv_bytes(nb, nnzb, val_b, x_b, f_b, y_b):
@@ -166,6 +177,7 @@ def main():
                     help="preconditioner precision: FP32 AMG/ILU with BF16 RAS values (the 1M-cell case's "
                          "setting), FP32 throughout, or FP64")
     ap.add_argument("--max-lin", type=int, default=200)
+    ap.add_argument("--tile", default="4x4", help="RAS subdomain tile, columns x rows of cells")
     ap.add_argument("--roofline", default="ras", choices=["ras", "spmv64", "spmv_prec"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -191,7 +203,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     prec = {"mixed": R.PREC_MIXED, "mixed_bf16": R.PREC_MIXED_BF16, "fp64": R.PREC_FP64}[args.precision]
-    opts = dict(precision=prec, max_lin=args.max_lin)
+    tx, ty = (int(v) for v in args.tile.split("x"))
+    opts = dict(precision=prec, max_lin=args.max_lin, tile_x=tx, tile_y=ty)
     sim = R.Sim(case, **opts)
     sim.init_hydrostatic()
     for _ in range(args.warmup):
@@ -250,7 +263,8 @@ def main():
     peak, src = peaks()
     achieved = bpl / (kms / nk * 1e-3) / 1e9 if nk else 0.0
     roof = {"kernel": args.roofline, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": src, "traffic": None, "launches": nk,
+            "frac": achieved / peak, "peak_source": src, "traffic": NCU_TRAFFIC.get((args.roofline, args.precision)),
+            "launches": nk,
             "ms_per_launch": kms / nk if nk else None, "algorithmic_bytes_per_launch": bpl}
 
     # end to end through the public API with host buffers
@@ -294,6 +308,7 @@ def main():
             "vs_baseline": None, "dtype": {"mixed": "f64+f32", "mixed_bf16": "f64+f32+bf16", "fp64": "f64"}[args.precision], "data": "synthetic",
             "config": {"workload": case.name, "cells": case.n, "wells": len(case.wells), "dt_days": case.dt,
                        "relres": case.lin_tol, "precision": args.precision, "learned_warm_start": False,
+                       "ras_tile": args.tile,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "working set larger than L2 (no flush needed)",
                        "newton_per_step": newton_per_step, "fgmres_its_per_newton": its_per_newton,
