@@ -261,6 +261,42 @@ enum { SIM_T_NONE = 0, SIM_T_SPMV64 = 1, SIM_T_SPMV_PREC = 2, SIM_T_RAS = 3, SIM
 sim_status sim_kernel_timer(sim_ls_t ls, unsigned mask);
 sim_status sim_kernel_time(sim_ls_t ls, int which, long long *launches, double *ms);
 
+/* ---- ensembles: many independent models advanced together ----
+ *
+ * Not in the paper, whose experiments run one model at a time.  A batch
+ * holds n_members simulators (each created as by sim_create from grids[k],
+ * rocks[k], fluids[k], wells[k][0..n_wells[k]) and opts[k]; opts[k].cuda_stream
+ * is ignored: every member gets a non-blocking stream of its own).  Members
+ * share no data, so a member's results are those of the same model run
+ * alone.  The batch owns the members; sim_batch_member lends one (valid until
+ * sim_batch_destroy) for sim_init_hydrostatic, sim_set_state, sim_get_state,
+ * sim_get_stats and the rest of the single-model calls.  n_workers host
+ * threads (0 = 8) advance the members concurrently, largest grids first.
+ * Errors: SIM_ERR_ARG, SIM_ERR_OOM, SIM_ERR_CUDA; a member that fails to be
+ * created fails the whole call (nothing is left allocated). */
+typedef struct sim_batch_s *sim_batch_t;
+sim_status sim_batch_create(sim_batch_t *out, int n_members, const sim_grid *grids, const sim_rock *rocks,
+                            const sim_fluid *fluids, const sim_well *const *wells, const int *n_wells,
+                            const sim_options *opts, int n_workers);
+void sim_batch_destroy(sim_batch_t b);
+sim_status sim_batch_member(sim_batch_t b, int k, sim_t *member);
+sim_status sim_batch_size(sim_batch_t b, int *n_members, int *n_workers);
+
+/* Advance every member by n_steps time steps (sim_advance on each).  stats
+ * (n_members, may be NULL) receives each member's cumulative statistics and
+ * status (n_members, may be NULL) each member's return code.  Returns the
+ * first failing member's code (in member order) with its message, after all
+ * members have run; SIM_OK when every member completed its steps. */
+sim_status sim_batch_advance(sim_batch_t b, int n_steps, sim_stats *stats, sim_status *status);
+
+/* Pick the worker count: for each of candidates[0..n_candidates) advance the
+ * `sample` largest members (sample < 1: twice the largest candidate) by one
+ * time step, timing it on the host (seconds[c], may be NULL), then restore
+ * those members' states and statistics exactly.  The fastest count becomes
+ * the batch's worker count and is returned in *chosen. */
+sim_status sim_batch_autotune(sim_batch_t b, const int *candidates, int n_candidates, int sample, int *chosen,
+                              double *seconds);
+
 /* Number of this library's kernel launches issued so far (all handles). */
 long long sim_launch_count(void);
 

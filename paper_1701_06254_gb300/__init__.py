@@ -120,6 +120,13 @@ def lib():
             "sim_ls_residual_norm_noalloc": (I, [P, P, P]),
             "sim_kernel_timer": (I, [P, C.c_uint]),
             "sim_kernel_time": (I, [P, I, C.POINTER(C.c_longlong), C.POINTER(D)]),
+            "sim_batch_create": (I, [C.POINTER(P), I, C.POINTER(Grid), C.POINTER(Rock), C.POINTER(Fluid),
+                                     C.POINTER(C.POINTER(Well)), C.POINTER(I), C.POINTER(Options), I]),
+            "sim_batch_destroy": (None, [P]),
+            "sim_batch_member": (I, [P, I, C.POINTER(P)]),
+            "sim_batch_size": (I, [P, C.POINTER(I), C.POINTER(I)]),
+            "sim_batch_advance": (I, [P, I, C.POINTER(Stats), C.POINTER(I)]),
+            "sim_batch_autotune": (I, [P, C.POINTER(I), I, I, C.POINTER(I), C.POINTER(D)]),
             "sim_launch_count": (C.c_longlong, []),
             "sim_last_error": (C.c_char_p, []),
         }
@@ -363,3 +370,90 @@ class Sim:
         st = Stats()
         _check(self._L.sim_get_stats(self.h, C.byref(st)))
         return st.as_dict()
+
+
+class _Member(Sim):
+    """A batch member: the single-model calls on a handle the batch owns."""
+
+    def __init__(self, batch, k, case, h):
+        self._L = batch._L
+        self.case = case
+        self.h = h
+        self._owned = False
+        self.n, self.nw = case.n, len(case.wells)
+        self.ls = LinearSystem(_handle=self._L.sim_linear_system(h), _owner=self)
+        self.ls.n, self.ls.nw, self.ls.nb = self.n, self.nw, self.n + self.nw
+        self._batch = batch                    # keeps the batch (and so the handle) alive
+
+    def __del__(self):
+        pass
+
+
+class Batch:
+    """An ensemble of independent models advanced together on one GPU
+    (sim_batch_* entry points).  cases: a list of inputs.Case; options are
+    taken from each case as Sim does, plus the keyword overrides."""
+
+    def __init__(self, cases, workers=0, **opts):
+        self._L = lib()
+        self.cases = list(cases)
+        m = len(self.cases)
+        grids, rocks, fluids = (Grid * m)(), (Rock * m)(), (Fluid * m)()
+        wptr = (C.POINTER(Well) * m)()
+        nwell = (C.c_int * m)()
+        ops = (Options * m)()
+        self._keep = []
+        for k, case in enumerate(self.cases):
+            o = dict(newton=0 if case.newton == "standard" else 1, newton_tol=case.newton_tol,
+                     lin_tol=case.lin_tol, dt=case.dt, sat_chop=case.sat_chop)
+            o.update(opts)
+            ops[k] = make_options(None, **o)
+            g, fl, wells, keep = _case_structs(case)
+            arrs = [np.ascontiguousarray(a, np.float64) for a in (case.kx, case.ky, case.kz, case.phi)]
+            grids[k], fluids[k] = g, fl
+            rocks[k] = Rock(*(_ptr(a) for a in arrs))
+            wptr[k] = C.cast(wells, C.POINTER(Well))
+            nwell[k] = len(case.wells)
+            self._keep += [wells, keep, arrs]
+        h = C.c_void_p()
+        _check(self._L.sim_batch_create(C.byref(h), m, grids, rocks, fluids, wptr, nwell, ops, workers))
+        self.h = h
+        self._keep = None                      # everything was copied at creation
+        self.members = []
+        for k, case in enumerate(self.cases):
+            mh = C.c_void_p()
+            _check(self._L.sim_batch_member(h, k, C.byref(mh)))
+            self.members.append(_Member(self, k, case, mh))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.members = []
+            self._L.sim_batch_destroy(self.h)
+            self.h = None
+
+    def __len__(self):
+        return len(self.cases)
+
+    @property
+    def workers(self):
+        w = C.c_int()
+        _check(self._L.sim_batch_size(self.h, None, C.byref(w)))
+        return w.value
+
+    def init_hydrostatic(self):
+        for mem in self.members:
+            mem.init_hydrostatic()
+
+    def advance(self, n_steps):
+        m = len(self.cases)
+        st = (Stats * m)()
+        rc = (C.c_int * m)()
+        _check(self._L.sim_batch_advance(self.h, n_steps, st, rc))
+        return [s.as_dict() for s in st]
+
+    def autotune(self, candidates=(2, 4, 8, 16), sample=0):
+        c = (C.c_int * len(candidates))(*candidates)
+        sec = (C.c_double * len(candidates))()
+        chosen = C.c_int()
+        _check(self._L.sim_batch_autotune(self.h, c, len(candidates), sample, C.byref(chosen), sec))
+        return chosen.value, dict(zip(candidates, list(sec)))

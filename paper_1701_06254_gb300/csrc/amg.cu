@@ -337,6 +337,7 @@ static void csr_cast(const csr_dev<double> &a, csr_dev<float> &b, cudaStream_t s
 }
 
 void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
+  h.drop_graphs();                                  // buffers below may move
   h.flag.ensure(4 + 1025);
   bool mixed = o.precision != SIM_PREC_FP64;
   int l = 0;
@@ -502,7 +503,7 @@ template <> struct lvl_ptrs<float> {
 };
 
 template <class T>
-void amg_vcycle(amg_hier &h, int l, cudaStream_t s) {
+int amg_vcycle(amg_hier &h, int l, cudaStream_t s) {
   typedef lvl_ptrs<T> LP;
   amg_level &L = h.lev[l];
   const auto &A = LP::A(L);
@@ -511,18 +512,18 @@ void amg_vcycle(amg_hier &h, int l, cudaStream_t s) {
     if (h.coarse_dense) {
       k_dense_apply<T><<<grid_for(n, 8), 256, 0, s>>>(n, h.lu.p, LP::f(L), LP::x(L));
       RS_LAUNCHED(1);
-    } else {
-      T *x = LP::x(L), *t = LP::t(L);
-      k_vc_pre<T><<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), x, LP::r(L));
-      RS_LAUNCHED(1);
-      for (int it = 1; it < 10; it++) {
-        k_jacobi<T><<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), x, t);
-        std::swap(x, t);
-        RS_LAUNCHED(1);
-      }
-      if (x != LP::x(L)) RS_CUDA(cudaMemcpyAsync(LP::x(L), x, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      return 1;
     }
-    return;
+    T *x = LP::x(L), *t = LP::t(L);
+    k_vc_pre<T><<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), x, LP::r(L));
+    RS_LAUNCHED(1);
+    for (int it = 1; it < 10; it++) {
+      k_jacobi<T><<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), x, t);
+      std::swap(x, t);
+      RS_LAUNCHED(1);
+    }
+    if (x != LP::x(L)) RS_CUDA(cudaMemcpyAsync(LP::x(L), x, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    return 10;
   }
   amg_level &Cl = h.lev[l + 1];
   const auto &P = LP::P(L);
@@ -530,13 +531,46 @@ void amg_vcycle(amg_hier &h, int l, cudaStream_t s) {
   k_vc_pre<T><<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), LP::x(L), LP::r(L));
   RS_LAUNCHED(1);
   csr_spmv<T>(R.rp.p, R.ci.p, R.v.p, LP::r(L), LP::f(Cl), R.n, s);
-  amg_vcycle<T>(h, l + 1, s);
+  int k = amg_vcycle<T>(h, l + 1, s);
   k_prolong_add<T><<<grid_for(n, 256), 256, 0, s>>>(n, P.rp.p, P.ci.p, P.v.p, LP::x(Cl), LP::x(L), LP::t(L));
   k_vc_post<T><<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), LP::t(L), LP::x(L));
   RS_LAUNCHED(2);
+  return k + 4;
 }
-template void amg_vcycle<double>(amg_hier &, int, cudaStream_t);
-template void amg_vcycle<float>(amg_hier &, int, cudaStream_t);
+template int amg_vcycle<double>(amg_hier &, int, cudaStream_t);
+template int amg_vcycle<float>(amg_hier &, int, cudaStream_t);
+
+// One V-cycle from level 0 as a single graph launch: every buffer it touches
+// is fixed between two setups, so the whole recursion (about four kernels per
+// level) is recorded once per hierarchy and replayed, which removes the
+// per-kernel launch gaps that dominate the small coarse levels.
+template <class T>
+void amg_vcycle_graph(amg_hier &h, cudaStream_t s) {
+  int pi = sizeof(T) == 4 ? 1 : 0;
+  if (!h.vc_exec[pi]) {
+    if (!h.cap) RS_CUDA(cudaStreamCreateWithFlags(&h.cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    RS_CUDA(cudaStreamBeginCapture(h.cap, cudaStreamCaptureModeThreadLocal));
+    int k = 0;
+    try {
+      k = amg_vcycle<T>(h, 0, h.cap);
+    } catch (...) {
+      cudaStreamEndCapture(h.cap, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    rs_launches -= k;                              // recorded, not launched
+    RS_CUDA(cudaStreamEndCapture(h.cap, &g));
+    cudaError_t e = cudaGraphInstantiate(&h.vc_exec[pi], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { h.vc_exec[pi] = nullptr; RS_CUDA(e); }
+    h.vc_launches[pi] = k;
+  }
+  RS_CUDA(cudaGraphLaunch(h.vc_exec[pi], s));
+  RS_LAUNCHED(h.vc_launches[pi]);
+}
+template void amg_vcycle_graph<double>(amg_hier &, cudaStream_t);
+template void amg_vcycle_graph<float>(amg_hier &, cudaStream_t);
 
 template <class T>
 __global__ void k_csr_spmv(int n, const int *rp, const int *ci, const T *v, const T *x, T *y) {

@@ -6,6 +6,7 @@
 #include <stddef.h>
 #include <string>
 #include <vector>
+#include <atomic>
 #include "../../include/resim.h"
 
 #define RS_CDARCY (9.869233e-16 * 1e5 / 1e-3 * 86400.0)   // k[mD] A/L dp[bar]/mu[cP] -> m3/day
@@ -28,7 +29,7 @@ struct rs_error {                       // thrown inside the library, caught at 
 #define RS_CHECK_LAUNCH() RS_CUDA(cudaGetLastError())
 #define RS_FAIL(code, ...) do { rs_set_error(__VA_ARGS__); throw rs_error(code); } while (0)
 
-extern unsigned long long rs_launches;     // kernel launches issued (all handles)
+extern std::atomic<unsigned long long> rs_launches;     // kernel launches issued (all handles)
 #define RS_LAUNCHED(k) (rs_launches += (k))
 
 // ---------------------------------------------------------------- memory --
@@ -121,10 +122,20 @@ struct amg_hier {
   dbuf<int> flag;               // device counters / error words
   dbuf<double> hashw;           // PMIS weights
   dbuf<int8_t> newc;
+  // the V-cycle of the current hierarchy as a CUDA graph ([0] FP64, [1] FP32),
+  // captured on first use after a setup; the capture stream only records
+  cudaGraphExec_t vc_exec[2] = {nullptr, nullptr};
+  int vc_launches[2] = {0, 0};
+  cudaStream_t cap = nullptr;
+  void drop_graphs() {
+    for (auto &e : vc_exec) if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+  }
+  ~amg_hier() { drop_graphs(); if (cap) cudaStreamDestroy(cap); }
 };
 
 void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s);   // level 0 A must be filled
-template <class T> void amg_vcycle(amg_hier &h, int l, cudaStream_t s);  // f -> x of level l
+template <class T> int amg_vcycle(amg_hier &h, int l, cudaStream_t s);   // f -> x of level l; returns launches
+template <class T> void amg_vcycle_graph(amg_hier &h, cudaStream_t s);   // level 0, replayed as one graph
 
 // ---------------------------------------------------------------- RAS -----
 struct ras_data {
@@ -216,3 +227,7 @@ template <class Tv, class Tx, class Ty>
 void bsr_spmv(const int *rp, const int *ci, const Tv *val, const Tx *x, Ty *y, const Ty *f, int nb, cudaStream_t s);
 template <class T>
 void csr_spmv(const int *rp, const int *ci, const T *v, const T *x, T *y, int n, cudaStream_t s);
+
+// simulator internals used by the ensemble driver (batch.cu)
+void sim_dims(sim_t h, int *n, int *n_wells);
+void sim_put_stats(sim_t h, const sim_stats *st);

@@ -201,7 +201,7 @@ void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32) {
     { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, double, float>(ls, ls->val32.p, z, v, r, s); }  // 2
     k_gather_p<float, float><<<grid_for(n, 256), 256, 0, s>>>(n, r, L0.f32.p);
     RS_LAUNCHED(1);
-    { rs_timed tm(ls, SIM_T_VCYCLE); amg_vcycle<float>(ls->amg, 0, s); }               // 3
+    { rs_timed tm(ls, SIM_T_VCYCLE); amg_vcycle_graph<float>(ls->amg, s); }               // 3
     k_add_p<float><<<grid_for(n, 256), 256, 0, s>>>(n, L0.x32.p, z);
     RS_LAUNCHED(1);
     { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, double, float>(ls, ls->val32.p, z, v, r, s); }  // 4
@@ -212,7 +212,7 @@ void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32) {
     { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<double, double, double, double>(ls, ls->val.p, z, v, r, s); }
     k_gather_p<double, double><<<grid_for(n, 256), 256, 0, s>>>(n, r, L0.f.p);
     RS_LAUNCHED(1);
-    { rs_timed tm(ls, SIM_T_VCYCLE); amg_vcycle<double>(ls->amg, 0, s); }
+    { rs_timed tm(ls, SIM_T_VCYCLE); amg_vcycle_graph<double>(ls->amg, s); }
     k_add_p<double><<<grid_for(n, 256), 256, 0, s>>>(n, L0.x.p, z);
     RS_LAUNCHED(1);
     { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<double, double, double, double>(ls, ls->val.p, z, v, r, s); }
@@ -302,9 +302,8 @@ void ls_setup(sim_ls_s *ls) {
 #define ORTHO_BS 256
 #define ORTHO_MAXV 64
 // Each block owns a fixed chunk of ORTHO_CH rows and keeps its slice of w in
-// shared memory.  Basis vectors are streamed one at a time (vector-outer,
-// rows-inner): loads are coalesced and independent, unrolled 8 ways, and
-// every dot product needs one accumulator per thread.
+// shared memory.  Basis vectors are streamed vector-outer, rows-inner, so
+// loads are coalesced and independent.
 #define ORTHO_CH 4096
 static int ortho_blocks(int nu) { return (nu + ORTHO_CH - 1) / ORTHO_CH; }
 
@@ -323,27 +322,69 @@ __device__ __forceinline__ double block_sum_d(double v, double *sred) {   // res
   return t;
 }
 
+// Basis vectors are taken ORTHO_G at a time: a thread keeps one accumulator
+// per vector of the group and issues the group's loads for a row together.
+#define ORTHO_G 8
+
+// Sum of a[0..7] over the warp for each of the 8 slots at once: at every
+// halving step a lane keeps half of its slots and adds the partner's copy of
+// them (9 shuffles and 9 adds for 8 sums, instead of 5 of each per sum).
+// Afterwards lane l holds the total of slot ((l>>4)&1)*4 + ((l>>3)&1)*2 + ((l>>2)&1).
+__device__ __forceinline__ double warp_sum8_d(const double *a, int lane) {
+  double b4[4], b2[2];
+  bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    double keep = u16 ? a[q + 4] : a[q], give = u16 ? a[q] : a[q + 4];
+    b4[q] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+  }
+#pragma unroll
+  for (int q = 0; q < 2; q++) {
+    double keep = u8 ? b4[q + 2] : b4[q], give = u8 ? b4[q] : b4[q + 2];
+    b2[q] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+  }
+  double keep = u4 ? b2[1] : b2[0], give = u4 ? b2[0] : b2[1];
+  double t = keep + __shfl_xor_sync(0xffffffffu, give, 4);
+  t += __shfl_xor_sync(0xffffffffu, t, 2);
+  t += __shfl_xor_sync(0xffffffffu, t, 1);
+  return t;
+}
+
 // part[k][b] = V_k . w over the block's rows (k < nv); with_norm: part[nv][b] = w . w
 __global__ void __launch_bounds__(ORTHO_BS) k_ortho_dots(int nu, int nv, const double *__restrict__ V,
                                                          const double *__restrict__ w, double *part, int with_norm,
                                                          const int *cond) {
   if (cond && *cond == 0) return;
   extern __shared__ double ws[];             // ORTHO_CH doubles (dynamic)
-  __shared__ double sred[ORTHO_BS / 32];
+  __shared__ double red[2][ORTHO_BS / 32][ORTHO_G];
   int nblk = gridDim.x, i0 = blockIdx.x * ORTHO_CH, len = min(ORTHO_CH, nu - i0);
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < len; t += ORTHO_BS) ws[t] = w[i0 + t];
   __syncthreads();
-  for (int k = 0; k < nv + (with_norm ? 1 : 0); k++) {
-    double acc = 0.0;
-    if (k < nv) {
-      const double *vk = V + (size_t)k * nu + i0;
-#pragma unroll 8
-      for (int t = threadIdx.x; t < len; t += ORTHO_BS) acc += __ldg(vk + t) * ws[t];
-    } else {
-      for (int t = threadIdx.x; t < len; t += ORTHO_BS) acc += ws[t] * ws[t];
+  int nt = nv + (with_norm ? 1 : 0);
+  for (int k0 = 0, grp = 0; k0 < nt; k0 += ORTHO_G, grp ^= 1) {
+    const double *vp[ORTHO_G];
+    double acc[ORTHO_G];
+#pragma unroll
+    for (int g = 0; g < ORTHO_G; g++) {
+      int k = k0 + g;                          // vector nv is w itself (its squared norm)
+      vp[g] = k < nv ? V + (size_t)k * nu + i0 : (k == nv ? w + i0 : nullptr);
+      acc[g] = 0.0;
     }
-    double tot = block_sum_d(acc, sred);
-    if (threadIdx.x == 0) part[(size_t)k * nblk + blockIdx.x] = tot;
+    for (int t = threadIdx.x; t < len; t += ORTHO_BS) {
+      double wt = ws[t];
+#pragma unroll
+      for (int g = 0; g < ORTHO_G; g++)
+        if (vp[g]) acc[g] += __ldg(vp[g] + t) * wt;
+    }
+    double tot = warp_sum8_d(acc, lane);
+    if ((lane & 3) == 0) red[grp][warp][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = tot;
+    __syncthreads();                           // red[grp] is rewritten two groups later, after another barrier
+    if (threadIdx.x < ORTHO_G && k0 + threadIdx.x < nt) {
+      double s = 0.0;
+      for (int q = 0; q < ORTHO_BS / 32; q++) s += red[grp][q][threadIdx.x];
+      part[(size_t)(k0 + threadIdx.x) * nblk + blockIdx.x] = s;
+    }
   }
 }
 
@@ -356,11 +397,22 @@ __global__ void __launch_bounds__(ORTHO_BS) k_ortho_update(int nu, int nv, const
   __shared__ double sred[ORTHO_BS / 32];
   int i0 = blockIdx.x * ORTHO_CH, len = min(ORTHO_CH, nu - i0);
   for (int t = threadIdx.x; t < len; t += ORTHO_BS) ws[t] = w[i0 + t];
-  for (int k = 0; k < nv; k++) {        // each thread updates only its own rows: no barrier needed
-    double hk = h[k];
-    const double *vk = V + (size_t)k * nu + i0;
-#pragma unroll 8
-    for (int t = threadIdx.x; t < len; t += ORTHO_BS) ws[t] -= hk * __ldg(vk + t);
+  for (int k0 = 0; k0 < nv; k0 += ORTHO_G) {   // each thread updates only its own rows: no barrier needed
+    const double *vp[ORTHO_G];
+    double hk[ORTHO_G];
+#pragma unroll
+    for (int g = 0; g < ORTHO_G; g++) {
+      int k = k0 + g;
+      vp[g] = k < nv ? V + (size_t)k * nu + i0 : nullptr;
+      hk[g] = k < nv ? h[k] : 0.0;
+    }
+    for (int t = threadIdx.x; t < len; t += ORTHO_BS) {
+      double s = ws[t];
+#pragma unroll
+      for (int g = 0; g < ORTHO_G; g++)       // same order as one vector at a time: w - h_0 v_0 - h_1 v_1 ...
+        if (vp[g]) s -= hk[g] * __ldg(vp[g] + t);
+      ws[t] = s;
+    }
   }
   double n2 = 0.0;
   for (int t = threadIdx.x; t < len; t += ORTHO_BS) { double v = ws[t]; w[i0 + t] = v; n2 += v * v; }

@@ -707,6 +707,9 @@ extern "C" sim_status sim_get_stats(sim_t h, sim_stats *st) {
   ABI_END
 }
 
+void sim_dims(sim_t h, int *n, int *n_wells) { *n = h->n; *n_wells = h->nw; }
+void sim_put_stats(sim_t h, const sim_stats *st) { h->stats = *st; }
+
 extern "C" sim_ls_t sim_linear_system(sim_t h) { return h ? h->ls : nullptr; }
 
 // ---------------------------------------------------- linear-system ABI --

@@ -4,7 +4,7 @@
 #include <cstdio>
 
 static thread_local char g_err[1024] = "";
-unsigned long long rs_launches = 0;
+std::atomic<unsigned long long> rs_launches{0};
 
 void rs_set_error(const char *fmt, ...) {
   va_list ap; va_start(ap, fmt);
@@ -12,7 +12,7 @@ void rs_set_error(const char *fmt, ...) {
   va_end(ap);
 }
 extern "C" const char *sim_last_error(void) { return g_err; }
-extern "C" long long sim_launch_count(void) { return (long long)rs_launches; }
+extern "C" long long sim_launch_count(void) { return (long long)rs_launches.load(); }
 
 // ------------------------------------------------------------------ scan --
 #define SCAN_BS 256

@@ -190,6 +190,31 @@ def case2(seed: int = 2, nx=200, ny=200, nz=25) -> Case:
     return c
 
 
+def ensemble_member(k: int, seed0: int = 2000, size_lo=(32, 32, 8), size_hi=(128, 128, 32),
+                    n_steps: int = 20) -> Case:
+    """Member k of the ensemble workload: the correlated-layer physics of
+    case1 on a grid drawn from U{32..128} x U{32..128} x U{8..32} (seed
+    seed0 + k), five-spot wells with the injection rates scaled to the grid's
+    areal size, 10-day steps.  size_lo / size_hi narrow the draw for tests."""
+    rng = np.random.default_rng(seed0 + k)
+    nx = int(rng.integers(size_lo[0], size_hi[0] + 1))
+    ny = int(rng.integers(size_lo[1], size_hi[1] + 1))
+    nz = int(rng.integers(size_lo[2], size_hi[2] + 1))
+    c = case1(seed=seed0 + k, nx=nx, ny=ny, nz=nz)
+    c.name = f"ens{k}_{nx}x{ny}x{nz}"
+    for w in c.wells:
+        if w.kind == INJ:
+            w.target = 500.0 * (nx * ny) / (100.0 * 100.0)
+    c.dt, c.n_steps = 10.0, n_steps
+    return c
+
+
+def ensemble(members: int = 128, seed0: int = 2000, **kw) -> list:
+    """The ensemble workload: `members` independent models (default 128,
+    seeds 2000..2127, about 16M cells in all)."""
+    return [ensemble_member(k, seed0, **kw) for k in range(members)]
+
+
 def small_case(nx=6, ny=5, nz=3, seed=7, sigma=1.0, gravity=True, dt=1.0) -> Case:
     """Tiny heterogeneous case used by parity tests: i.i.d. log-normal k,
     one rate injector and one BHP producer in opposite corner columns."""
