@@ -305,8 +305,11 @@ void or_sim_assemble(or_sim *S)
   /* wells, eq. (10): per perforation q_a = WI rho_a kr_a/mu_a dPw with the
      drawdown dPw = p_b - p + rho_a g (z - z_ref) (z = depth).
      Producer: own phase mobility, outflow only (q = 0 when dPw > 0).
-     Injector: water only, with the total cell mobility (kr_w/mu_w +
-     kr_o/mu_o), so water can enter a cell at connate saturation. */
+     Injector, dPw >= 0: water only, with the total cell mobility (kr_w/mu_w
+     + kr_o/mu_o), so water can enter a cell at connate saturation.
+     Injector, dPw < 0 (crossflow into the wellbore): the flow is upstream
+     from the cell as for the faces (eq. 18), each phase with its own
+     mobility, so no phase leaves a cell where it is immobile. */
   for (int w = 0; w < S->nw; w++) {
     int wr = n + w;
     double *Jww = &ls->val[4 * (size_t)bpos(ls, wr, wr)];
@@ -329,7 +332,12 @@ void or_sim_assemble(or_sim *S)
             dqds = wi * P[c].dms[a] * dd;
             dqdb = wi * P[c].m[a];
           }
-        } else if (a == 0) {
+        } else if (dd < 0.0) {        /* injector crossflow: as a producer perforation */
+          q_ = wi * P[c].m[a] * dd;
+          dqdp = wi * (P[c].dmp[a] * dd + P[c].m[a] * dd_dp);
+          dqds = wi * P[c].dms[a] * dd;
+          dqdb = wi * P[c].m[a];
+        } else if (a == 0) {          /* at dd = 0: q = 0 with the injecting-side derivative */
           double lt = P[c].kr[0] / P[c].mu[0] + P[c].kr[1] / P[c].mu[1];
           double lt_p = -P[c].kr[0] * P[c].dmu[0] / (P[c].mu[0] * P[c].mu[0])
                         - P[c].kr[1] * P[c].dmu[1] / (P[c].mu[1] * P[c].mu[1]);
@@ -494,6 +502,7 @@ void or_sim_well_rates(const or_sim *S, double *qw, double *qo)
       for (int a = 0; a < 2; a++) {
         double dd = (S->pb[w] - S->p[c]) + P.rho[a] * dz5, q_ = 0;
         if (S->wkind[w] == OR_PROD) { if (dd <= 0.0) q_ = S->pwi[q] * P.m[a] * dd; }
+        else if (dd < 0.0) q_ = S->pwi[q] * P.m[a] * dd;
         else if (a == 0) q_ = S->pwi[q] * P.rho[0] * (P.kr[0] / P.mu[0] + P.kr[1] / P.mu[1]) * dd;
         if (a == 0) qw[w] += q_; else qo[w] += q_;
       }

@@ -113,15 +113,19 @@ def _dense_J(rp, ci, val, nb):
     return J
 
 
-@pytest.mark.parametrize("seed", [5, 6])
-def test_jacobian_matches_finite_differences(oracle_lib, seed):
+@pytest.mark.parametrize("seed,crossflow", [(5, False), (6, False), (7, True)])
+def test_jacobian_matches_finite_differences(oracle_lib, seed, crossflow):
     """Analytic 2x2-block Jacobian vs central differences of the residual
     (eq. 17 with upstreaming eq. 18 and wells eq. 10) at a random state
-    away from relative-permeability and upstream kinks."""
+    away from relative-permeability and upstream kinks; with crossflow the
+    injector's wellbore pressure is below every cell's, so its perforations
+    produce from the cells (upstream = cell)."""
     c = I.small_case(3, 3, 2, seed=seed)
     s = oracle_lib.Sim(c)
     p0, s0, pb0 = I.random_state(c, seed + 10)
     p1, s1, pb1 = I.random_state(c, seed + 20)
+    if crossflow:
+        pb1 = np.array([100.0 if w.kind == I.INJ else pb for w, pb in zip(c.wells, pb1)])
     s.set_state(p0, s0, pb0); s.store_old()
     s.set_dt(1.5)
     s.set_state(p1, s1, pb1); s.assemble()
