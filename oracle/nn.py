@@ -134,23 +134,30 @@ def init_params(seed=0):
     return P
 
 
-def forward(P, F):
-    """Network output Y (nz,ny,nx,8) for features F (nz,ny,nx,8) and the cache."""
-    cache = {}
+def forward(P, F, rnd=None):
+    """Network output Y (nz,ny,nx,8) for features F (nz,ny,nx,8) and the cache.
+
+    rnd (default: none) is applied where a kernel stores an activation in a
+    narrower type (the input, every ReLU output and every pooled tensor), so
+    the oracle can take the same storage precision as the implementation
+    under test; the arithmetic between those points stays FP64."""
+    r = rnd if rnd is not None else (lambda a: a)
+    cache = {"rnd": r}
 
     def layer(name, X, relu=True):
         W, b = P[name]
         Z = conv(X, W, b)
-        A = np.maximum(Z, 0.0) if relu else Z
+        A = r(np.maximum(Z, 0.0)) if relu else Z
         cache[name] = (X, A)
         return A
 
+    F = r(F)
     s0 = F.shape[:3]
     s1 = coarse_shape(s0); s2 = coarse_shape(s1); s3 = coarse_shape(s2)
     e0 = layer("c01", layer("c00", F))
-    e1 = layer("c11", layer("c10", pool(e0)))
-    e2 = layer("c21", layer("c20", pool(e1)))
-    b3 = layer("c31", layer("c30", pool(e2)))
+    e1 = layer("c11", layer("c10", r(pool(e0))))
+    e2 = layer("c21", layer("c20", r(pool(e1))))
+    b3 = layer("c31", layer("c30", r(pool(e2))))
     b2 = layer("d21", layer("d20", np.concatenate([up(b3, s2), e2], axis=-1)))
     b1 = layer("d11", layer("d10", np.concatenate([up(b2, s1), e1], axis=-1)))
     b0 = layer("d01", layer("d00", np.concatenate([up(b1, s0), e0], axis=-1)))
@@ -167,38 +174,42 @@ def loss(Y, T):
 
 
 def backward(P, cache, Y, T):
-    """Gradients {name: (dW, db)} of loss(Y, T) for the forward pass cached."""
+    """Gradients {name: (dW, db)} of loss(Y, T) for the forward pass cached.
+    The cache's rounding (see forward) is applied where a kernel stores a
+    gradient tensor: the loss gradient, every data gradient, and the sums
+    formed at up-sampling and pooling joins."""
+    r = cache["rnd"]
     n = Y.shape[0] * Y.shape[1] * Y.shape[2]
     G = np.zeros_like(Y)
-    G[..., :N_PRED] = (Y[..., :N_PRED] - T[..., :N_PRED]) / n
+    G[..., :N_PRED] = r((Y[..., :N_PRED] - T[..., :N_PRED]) / n)
     grads = {}
     s0, s1, s2, s3 = cache["shapes"]
 
-    def layer_back(name, dA):
+    def layer_back(name, dA, below_relu=True):
+        # dA arrives already multiplied by this layer's ReLU mask (the
+        # mask is applied where the gradient of its output is formed)
         X, A = cache[name]
-        relu = [r for nm, _, _, r in LAYERS if nm == name][0]
-        dZ = dA * (A > 0) if relu else dA
-        dX, dW, db = conv_backward(X, P[name][0], dZ)
+        dX, dW, db = conv_backward(X, P[name][0], dA)
         grads[name] = (dW, db)
-        return dX
+        return r(dX * (X > 0)) if below_relu else r(dX)
 
-    db0 = layer_back("h", G)
+    def masked(name, dA):
+        return dA * (cache[name][1] > 0)
+
+    db0 = layer_back("h", G)                        # input of h is a ReLU output
     dcat0 = layer_back("d00", layer_back("d01", db0))
-    de0 = dcat0[..., 32:]
-    db1 = up_backward(dcat0[..., :32], s1)
+    db1 = r(up_backward(dcat0[..., :32], s1))
     dcat1 = layer_back("d10", layer_back("d11", db1))
-    de1 = dcat1[..., 32:]
-    db2 = up_backward(dcat1[..., :32], s2)
+    db2 = r(up_backward(dcat1[..., :32], s2))
     dcat2 = layer_back("d20", layer_back("d21", db2))
-    de2 = dcat2[..., 32:]
-    db3 = up_backward(dcat2[..., :32], s3)
-    dp3 = layer_back("c30", layer_back("c31", db3))
-    de2 = de2 + pool_backward(s2, dp3)
-    dp2 = layer_back("c20", layer_back("c21", de2))
-    de1 = de1 + pool_backward(s1, dp2)
-    dp1 = layer_back("c10", layer_back("c11", de1))
-    de0 = de0 + pool_backward(s0, dp1)
-    layer_back("c00", layer_back("c01", de0))
+    db3 = r(up_backward(dcat2[..., :32], s3))
+    dp3 = layer_back("c30", layer_back("c31", db3), below_relu=False)
+    de2 = r(masked("c21", dcat2[..., 32:] + pool_backward(s2, dp3)))
+    dp2 = layer_back("c20", layer_back("c21", de2), below_relu=False)
+    de1 = r(masked("c11", dcat1[..., 32:] + pool_backward(s1, dp2)))
+    dp1 = layer_back("c10", layer_back("c11", de1), below_relu=False)
+    de0 = r(masked("c01", dcat0[..., 32:] + pool_backward(s0, dp1)))
+    layer_back("c00", layer_back("c01", de0), below_relu=False)
     return grads
 
 
