@@ -9,6 +9,7 @@ Krylov basis) is larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
   python bench.py --impl reference     # the CPU oracle on the same workload
+  python bench.py --workload ensemble  # 128 independent models (~16.6M cells) on one GPU
 """
 from __future__ import annotations
 
@@ -166,6 +167,80 @@ def run_reference(args, case, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_ensemble(args, rank, world, local):
+    """--members independent models (grids drawn from U{32..128}^2 x U{8..32},
+    seeds 2000 + k) advanced together by the ensemble driver.  Each rank of a
+    multi-GPU run takes the same number of members with its own seeds (weak
+    scaling, no collective on the data path).  Members run on streams of their
+    own, so the timed region is bracketed by device-wide synchronisations and
+    read on the host clock."""
+    from paper_1701_06254_gb300 import inputs as I
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the single-model workload; "
+                              "run it without --workload ensemble"}), flush=True)
+        return
+    import torch
+    import paper_1701_06254_gb300 as R
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prec = {"mixed": R.PREC_MIXED, "mixed_bf16": R.PREC_MIXED_BF16, "fp64": R.PREC_FP64}[args.precision]
+    cases = I.ensemble(args.members, seed0=2000 + rank * args.members)
+    cells = sum(c.n for c in cases)
+    auto = args.workers == "auto"
+    batch = R.Batch(cases, workers=0 if auto else int(args.workers), precision=prec, max_lin=args.max_lin)
+    batch.init_hydrostatic()
+    tuned = None
+    if auto:
+        chosen, secs = batch.autotune(candidates=(4, 8, 16, 32))
+        tuned = {"chosen": chosen, "seconds_per_candidate": secs}
+    for _ in range(args.warmup):
+        batch.advance(1)
+    st0 = [m.stats() for m in batch.members]
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    l0 = R.launch_count()
+    clocks.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        batch.advance(1)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    ck = clocks.stop()
+    launches = R.launch_count() - l0
+    if dist:
+        t = torch.tensor([sec], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec = float(t.item())
+    st1 = [m.stats() for m in batch.members]
+    newton = sum(b["newton"] - a["newton"] for a, b in zip(st0, st1))
+    lin = sum(b["linear_its"] - a["linear_its"] for a, b in zip(st0, st1))
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * cells * args.steps / sec, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"mixed": "f64+f32", "mixed_bf16": "f64+f32+bf16", "fp64": "f64"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": f"ensemble_{args.members}", "members": args.members, "cells": cells,
+                       "precision": args.precision, "workers": batch.workers, "autotune": tuned,
+                       "timer": "host clock between device-wide synchronisations (members on their own streams)",
+                       "newton_per_member_step": newton / (len(cases) * args.steps),
+                       "fgmres_its_per_newton": lin / max(newton, 1),
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "working set larger than L2 (no flush needed)"},
+            "roofline": None, "gpu_launches": launches, "e2e": None, "cpu_baseline": None, "clocks": ck,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -179,6 +254,10 @@ def main():
     ap.add_argument("--max-lin", type=int, default=200)
     ap.add_argument("--tile", default="4x4", help="RAS subdomain tile, columns x rows of cells")
     ap.add_argument("--roofline", default="ras", choices=["ras", "spmv64", "spmv_prec"])
+    ap.add_argument("--workload", default="single", choices=["single", "ensemble"],
+                    help="single: the 1M-cell case; ensemble: --members independent models advanced together")
+    ap.add_argument("--members", type=int, default=128)
+    ap.add_argument("--workers", default="auto", help="ensemble host workers, or 'auto' for the autotuner")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--breakdown", action="store_true",
@@ -190,6 +269,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     from paper_1701_06254_gb300 import inputs as I
+    if args.workload == "ensemble":
+        run_ensemble(args, rank, world, local)
+        return
     case = I.CASES[args.config]()
     if args.impl == "reference":
         run_reference(args, case, rank)

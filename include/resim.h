@@ -106,6 +106,7 @@ typedef struct {
   double last_relres, last_norm, t;
   int last_its, last_newton;
   double ms_assemble, ms_setup, ms_solve;   /* CUDA-event time, cumulative */
+  long long ws_used, ws_fallback;           /* learned initial guesses kept / rejected */
 } sim_stats;
 
 typedef struct sim_s *sim_t;
@@ -296,6 +297,67 @@ sim_status sim_batch_advance(sim_batch_t b, int n_steps, sim_stats *stats, sim_s
  * the batch's worker count and is returned in *chosen. */
 sim_status sim_batch_autotune(sim_batch_t b, const int *candidates, int n_candidates, int sample, int *chosen,
                               double *seconds);
+
+/* ---- learned warm start: a 3D convolutional network that predicts the
+ *      Newton update, used as the FGMRES initial guess ----
+ *
+ * Not in the paper.  The network is a U-Net over 4 resolution levels
+ * (3x3x3 convolutions, 32 channels, ReLU, average-pool down, nearest up,
+ * skip concatenation) on the simulator's grid; all its contractions run
+ * as BF16 tensor-core MMAs with FP32 accumulation, for inference and for
+ * training (forward, data and weight gradients, Adam with FP32 master
+ * weights).  It is grid-size agnostic: weights trained on one grid apply to
+ * any other.  Inputs per cell (8 channels): the decoupled right-hand side
+ * (pressure and saturation rows, each over its rms), (ln k - 4) / 2,
+ * 4 (s_w - 0.5), the previous solve's update (each component over its rms),
+ * two zeros.  Output: the update's two components over (rms y_prev /
+ * rms b_prev) * rms b.  A handle is used by one caller at a time (calls on
+ * it are serialised internally). */
+typedef struct sim_ws_s *sim_ws_t;
+sim_status sim_ws_create(sim_ws_t *out, unsigned long long seed);   /* He-normal weights from seed */
+void sim_ws_destroy(sim_ws_t ws);
+
+/* Parameters in layer order (c00 c01 c10 c11 c20 c21 c30 c31 d20 d21 d10 d11
+ * d00 d01 h), each as W[27][Co][Ci] (tap t = (dx+1) + 3 (dy+1) + 9 (dz+1))
+ * then b[Co].  which = 0: the FP32 master weights; 1: the accumulated
+ * gradients divided by the number of samples accumulated.  dst == NULL
+ * returns the count in *needed. */
+sim_status sim_ws_params(sim_ws_t ws, int which, float *dst, size_t n, size_t *needed);
+/* Replace the weights (same layout, exactly the count) and reset Adam. */
+sim_status sim_ws_set_params(sim_ws_t ws, const float *src, size_t n);
+
+/* Network output for one grid: feat [nz][ny][nx][8] FP32 (rounded to BF16 on
+ * the device), y [nz][ny][nx][8] FP32 (channels 0-1 are the prediction).
+ * Host or device pointers. */
+sim_status sim_ws_forward(sim_ws_t ws, int nx, int ny, int nz, const float *feat, float *y);
+/* Forward, loss 0.5/n sum over cells of |y[0:2] - target|^2 (target
+ * [n][2]), and backward: gradients are added to the accumulated ones. */
+sim_status sim_ws_backward(sim_ws_t ws, int nx, int ny, int nz, const float *feat, const float *target,
+                           double *loss);
+sim_status sim_ws_zero_grad(sim_ws_t ws);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) with the mean accumulated
+ * gradient, then the gradients are cleared. */
+sim_status sim_ws_adam(sim_ws_t ws, double lr);
+
+/* Record: every linear solve of h that has a previous update appends its
+ * (features, target) pair, the target being the solve's update, to ws's
+ * dataset (device memory).  NULL stops recording. */
+sim_status sim_ws_record(sim_t h, sim_ws_t ws);
+sim_status sim_ws_dataset(sim_ws_t ws, int *n_samples);
+/* Train on the dataset: `epochs` passes in a seeded random order, an Adam
+ * step every `batch` samples; *mean_loss = mean loss of the last epoch.
+ * SIM_ERR_STATE when nothing was recorded. */
+sim_status sim_ws_train(sim_ws_t ws, int epochs, int batch, double lr, unsigned long long seed, double *mean_loss);
+sim_status sim_ws_eval(sim_ws_t ws, double *mean_loss);
+
+/* Attach a network to a simulator (NULL detaches): from the second solve on,
+ * every linear solve starts from the predicted update if its residual
+ * ||b - J y|| on the decoupled system is below ||b|| (the zero guess's),
+ * else from zero.  The stopping test stays ||b - J y|| <= tol ||b||, so the
+ * converged update meets the same tolerance either way.  sim_stats counts
+ * the guesses kept (ws_used) and rejected (ws_fallback).
+ * sim_init_hydrostatic clears the previous-update history. */
+sim_status sim_ws_attach(sim_t h, sim_ws_t ws);
 
 /* Number of this library's kernel launches issued so far (all handles). */
 long long sim_launch_count(void);

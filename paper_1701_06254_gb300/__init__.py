@@ -72,7 +72,8 @@ class Stats(C.Structure):
     _fields_ = [("steps", C.c_longlong), ("newton", C.c_longlong), ("linear_its", C.c_longlong),
                 ("cuts", C.c_longlong), ("linear_solves", C.c_longlong), ("last_relres", C.c_double),
                 ("last_norm", C.c_double), ("t", C.c_double), ("last_its", C.c_int), ("last_newton", C.c_int),
-                ("ms_assemble", C.c_double), ("ms_setup", C.c_double), ("ms_solve", C.c_double)]
+                ("ms_assemble", C.c_double), ("ms_setup", C.c_double), ("ms_solve", C.c_double),
+                ("ws_used", C.c_longlong), ("ws_fallback", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -127,6 +128,19 @@ def lib():
             "sim_batch_size": (I, [P, C.POINTER(I), C.POINTER(I)]),
             "sim_batch_advance": (I, [P, I, C.POINTER(Stats), C.POINTER(I)]),
             "sim_batch_autotune": (I, [P, C.POINTER(I), I, I, C.POINTER(I), C.POINTER(D)]),
+            "sim_ws_create": (I, [C.POINTER(P), C.c_uint64]),
+            "sim_ws_destroy": (None, [P]),
+            "sim_ws_params": (I, [P, I, P, C.c_size_t, C.POINTER(C.c_size_t)]),
+            "sim_ws_set_params": (I, [P, P, C.c_size_t]),
+            "sim_ws_forward": (I, [P, I, I, I, P, P]),
+            "sim_ws_backward": (I, [P, I, I, I, P, P, C.POINTER(D)]),
+            "sim_ws_zero_grad": (I, [P]),
+            "sim_ws_adam": (I, [P, D]),
+            "sim_ws_record": (I, [P, P]),
+            "sim_ws_dataset": (I, [P, C.POINTER(I)]),
+            "sim_ws_train": (I, [P, I, I, D, C.c_uint64, C.POINTER(D)]),
+            "sim_ws_eval": (I, [P, C.POINTER(D)]),
+            "sim_ws_attach": (I, [P, P]),
             "sim_launch_count": (C.c_longlong, []),
             "sim_last_error": (C.c_char_p, []),
         }
@@ -371,6 +385,16 @@ class Sim:
         _check(self._L.sim_get_stats(self.h, C.byref(st)))
         return st.as_dict()
 
+    def attach_warm_start(self, ws):
+        """Use a WarmStart network for the initial guess of every solve (None detaches)."""
+        self._ws = ws
+        _check(self._L.sim_ws_attach(self.h, ws.h if ws is not None else None))
+
+    def record_to(self, ws):
+        """Append every solve's (features, update) pair to ws's dataset (None stops)."""
+        self._rec = ws
+        _check(self._L.sim_ws_record(self.h, ws.h if ws is not None else None))
+
 
 class _Member(Sim):
     """A batch member: the single-model calls on a handle the batch owns."""
@@ -457,3 +481,68 @@ class Batch:
         chosen = C.c_int()
         _check(self._L.sim_batch_autotune(self.h, c, len(candidates), sample, C.byref(chosen), sec))
         return chosen.value, dict(zip(candidates, list(sec)))
+
+
+class WarmStart:
+    """The learned warm start's network (sim_ws_* entry points)."""
+
+    def __init__(self, seed=0):
+        self._L = lib()
+        h = C.c_void_p()
+        _check(self._L.sim_ws_create(C.byref(h), seed))
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self._L.sim_ws_destroy(self.h)
+            self.h = None
+
+    def params(self, which=0):
+        """Flat FP32 vector: per layer W[27][Co][Ci] then b[Co] (which=1: mean gradients)."""
+        n = C.c_size_t()
+        _check(self._L.sim_ws_params(self.h, which, None, 0, C.byref(n)))
+        out = np.zeros(n.value, np.float32)
+        _check(self._L.sim_ws_params(self.h, which, _ptr(out), n.value, None))
+        return out
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, np.float32)
+        _check(self._L.sim_ws_set_params(self.h, _ptr(a), a.size))
+
+    def forward(self, feat):
+        """feat (nz, ny, nx, 8) -> output (nz, ny, nx, 8), FP32."""
+        f = np.ascontiguousarray(feat, np.float32)
+        nz, ny, nx = f.shape[:3]
+        y = np.zeros((nz, ny, nx, 8), np.float32)
+        _check(self._L.sim_ws_forward(self.h, nx, ny, nz, _ptr(f), _ptr(y)))
+        return y
+
+    def backward(self, feat, target):
+        """Forward + loss + backward for one sample; gradients accumulate."""
+        f = np.ascontiguousarray(feat, np.float32)
+        t = np.ascontiguousarray(target, np.float32)
+        nz, ny, nx = f.shape[:3]
+        loss = C.c_double()
+        _check(self._L.sim_ws_backward(self.h, nx, ny, nz, _ptr(f), _ptr(t), C.byref(loss)))
+        return loss.value
+
+    def zero_grad(self):
+        _check(self._L.sim_ws_zero_grad(self.h))
+
+    def adam(self, lr):
+        _check(self._L.sim_ws_adam(self.h, lr))
+
+    def dataset_size(self):
+        n = C.c_int()
+        _check(self._L.sim_ws_dataset(self.h, C.byref(n)))
+        return n.value
+
+    def train(self, epochs, batch=4, lr=1e-3, seed=0):
+        loss = C.c_double()
+        _check(self._L.sim_ws_train(self.h, epochs, batch, lr, seed, C.byref(loss)))
+        return loss.value
+
+    def eval(self):
+        loss = C.c_double()
+        _check(self._L.sim_ws_eval(self.h, C.byref(loss)))
+        return loss.value

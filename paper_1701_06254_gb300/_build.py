@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libresim.so")
-UNITS = ["util.cu", "amg.cu", "ras.cu", "linsys.cu", "sim.cu", "batch.cu", "noalloc.cu"]
+UNITS = ["util.cu", "amg.cu", "ras.cu", "linsys.cu", "sim.cu", "batch.cu", "nn.cu", "noalloc.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]

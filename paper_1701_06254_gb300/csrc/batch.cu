@@ -129,8 +129,9 @@ extern "C" sim_status sim_batch_advance(sim_batch_t b, int n_steps, sim_stats *s
 
 // copy of one member's state and statistics, on the device
 struct saved_member {
-  dbuf<double> p, s, pb;
+  dbuf<double> p, s, pb, y, sc;
   double t = 0.0;
+  int have = 0;
   sim_stats stats;
 };
 
@@ -144,6 +145,8 @@ static void save_member(sim_t h, saved_member &sv) {
   sv.p.ensure(n); sv.s.ensure(n); sv.pb.ensure(std::max(nw, 1));
   if (sim_get_state(h, sv.p.p, sv.s.p, nw ? sv.pb.p : nullptr, &sv.t) != SIM_OK)
     RS_FAIL(SIM_ERR_CUDA, "autotune: %s", sim_last_error());
+  sv.y.ensure(2 * (size_t)(n + nw)); sv.sc.ensure(8);
+  sv.have = sim_history(h, sv.y.p, sv.sc.p, 0, true);
 }
 
 static void restore_member(sim_t h, const saved_member &sv) {
@@ -152,6 +155,7 @@ static void restore_member(sim_t h, const saved_member &sv) {
   if (sim_set_state(h, sv.p.p, sv.s.p, nw ? sv.pb.p : nullptr, sv.t) != SIM_OK)
     RS_FAIL(SIM_ERR_CUDA, "autotune: %s", sim_last_error());
   sim_put_stats(h, &sv.stats);
+  sim_history(h, sv.y.p, sv.sc.p, sv.have, false);
 }
 
 extern "C" sim_status sim_batch_autotune(sim_batch_t b, const int *candidates, int n_candidates, int sample,

@@ -214,7 +214,8 @@ struct rs_timed {                       // brackets launches of one kernel famil
 void ls_init(sim_ls_s *ls, int nx, int ny, int nz, int nw, const int *rp, const int *ci,
              const int *well_cell0, const rs_opts &o, cudaStream_t st);
 void ls_setup(sim_ls_s *ls);
-int ls_solve(sim_ls_s *ls, double tol, int *its, double *relres);   // solution in ls->y
+// solution in ls->y; x0: ls->y holds the initial guess (else zero)
+int ls_solve(sim_ls_s *ls, double tol, int *its, double *relres, bool x0 = false);
 void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32);
 void ls_spmv64(sim_ls_s *ls, const double *x, double *y);
 double ls_residual_norm(sim_ls_s *ls, const double *x_dev);
@@ -231,3 +232,12 @@ void csr_spmv(const int *rp, const int *ci, const T *v, const T *x, T *y, int n,
 // simulator internals used by the ensemble driver (batch.cu)
 void sim_dims(sim_t h, int *n, int *n_wells);
 void sim_put_stats(sim_t h, const sim_stats *st);
+int sim_history(sim_t h, double *y, double *sc, int have, bool save);
+
+// learned warm start (nn.cu)
+struct sim_ws_s;
+void ws_rms2(int n, const double *v, double *out, cudaStream_t s);
+void ws_predict(sim_ws_s *w, int nx, int ny, int nz, int nb, const double *b, const double *kx, const double *sw,
+                const double *yp, const double *sc, double *y, cudaStream_t s);
+void ws_record(sim_ws_s *w, int nx, int ny, int nz, const double *b, const double *kx, const double *sw,
+               const double *yp, const double *sc, const double *y, cudaStream_t s);

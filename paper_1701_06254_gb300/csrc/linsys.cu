@@ -512,7 +512,7 @@ __global__ void k_xupdate(int nu, int jend, const double *yk, const Tz *Z, doubl
   x[i] += s;
 }
 
-int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres) {
+int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
   cudaStream_t s = ls->st;
   int nu = 2 * ls->nb, m = std::min(ls->o.restart, ORTHO_MAXV - 1), maxit = ls->o.max_lin;
   bool mixed = ls->o.precision != SIM_PREC_FP64;
@@ -527,12 +527,20 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres) {
   volatile double *hp = ls->hpin;
   double *hp_dev;
   RS_CUDA(cudaHostGetDevicePointer((void **)&hp_dev, ls->hpin, 0));
-  rs_fill_d(ls->y.p, 0.0, nu, s);
   double bn = rs_norm2(ls->b.p, nu, s);
-  if (bn == 0.0) { *its_out = 0; *relres = 0.0; return 0; }
-  if (!std::isfinite(bn)) { *its_out = 0; *relres = NAN; return 2; }
-  RS_CUDA(cudaMemcpyAsync(ls->r.p, ls->b.p, nu * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (bn == 0.0) { rs_fill_d(ls->y.p, 0.0, nu, s); *its_out = 0; *relres = 0.0; return 0; }
+  if (!std::isfinite(bn)) { rs_fill_d(ls->y.p, 0.0, nu, s); *its_out = 0; *relres = NAN; return 2; }
   double beta = bn;
+  if (x0) {                      // initial guess in y: r = b - A y
+    spmv<double, double, double, double>(ls, ls->val.p, ls->y.p, ls->b.p, ls->r.p, s);
+    beta = rs_norm2(ls->r.p, nu, s);
+  }
+  if (!x0 || !std::isfinite(beta)) {
+    rs_fill_d(ls->y.p, 0.0, nu, s);
+    RS_CUDA(cudaMemcpyAsync(ls->r.p, ls->b.p, nu * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    beta = bn;
+  }
+  if (beta <= tol * bn) { *its_out = 0; *relres = beta / bn; return 0; }
   int its = 0, rc = 1;
   for (;;) {
     k_start<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->r.p, beta, ls->V.p, G, m);

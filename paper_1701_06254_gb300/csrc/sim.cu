@@ -36,6 +36,12 @@ struct sim_s {
   double t = 0.0, dt = 1.0;
   sim_ls_s *ls = nullptr;
   sim_stats stats;
+  // learned warm start: the network used for initial guesses, the one that
+  // records (features, target) pairs, the previous solve's update and the
+  // scales [rms b_p, rms b_s, rms y_prev_p, rms y_prev_s, rms b_prev_p, rms b_prev_s]
+  sim_ws_s *ws = nullptr, *rec = nullptr;
+  dbuf<double> yprev, wsc;
+  bool have_prev = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   ~sim_s() { delete ls; if (e0) cudaEventDestroy(e0); if (e1) cudaEventDestroy(e1); }
 };
@@ -187,7 +193,8 @@ k_assemble(int nx, int ny, int nz, fluid_c f, double top, double dz, double vol_
     reinterpret_cast<double2 *>(Bo)[1] = make_double2(O[2], O[3]);
   }
   // perforations of this cell (eq. 10): producer per phase, outflow only;
-  // injector water only with the total mobility
+  // injector water only with the total mobility; crossflow into an
+  // injector's wellbore is upstream from the cell, like a producer
   for (int a2 = cpp[c]; a2 < cpp[c + 1]; a2++) {
     int q = cpi[a2], w = pwell[q];
     double wi = pwi[q];
@@ -197,12 +204,12 @@ k_assemble(int nx, int ny, int nz, fluid_c f, double top, double dz, double vol_
       int e = 1 - a;
       double dd = add_rn(sub_rn(pbh[w], pc), mul_rn(P.rho[a], dz5)), dd_dp = -1.0 + P.drho[a] * dz5;
       double q_ = 0, dqdp = 0, dqds = 0, dqdb = 0;
-      if (wkind[w] == SIM_PROD) {
+      if (wkind[w] == SIM_PROD || dd < 0.0) {     // producer, or injector crossflow: upstream = cell
         if (dd <= 0.0) {
           q_ = wi * P.m[a] * dd; dqdp = wi * (P.dmp[a] * dd + P.m[a] * dd_dp);
           dqds = wi * P.dms[a] * dd; dqdb = wi * P.m[a];
         }
-      } else if (a == 0) {
+      } else if (a == 0) {                          // injection; at dd = 0 the injecting-side derivative
         double lt = P.kr[0] / P.mu[0] + P.kr[1] / P.mu[1];
         double lt_p = -P.kr[0] * P.dmu[0] / (P.mu[0] * P.mu[0]) - P.kr[1] * P.dmu[1] / (P.mu[1] * P.mu[1]);
         double lt_s = P.dkr[0] / P.mu[0] + P.dkr[1] / P.mu[1];
@@ -245,7 +252,7 @@ __global__ void k_wells(int n, int nw, fluid_c f, double top, double dz, int nxy
       double dz5 = mul_rn(mul_rn(f.g, sub_rn(z, wzref[w])), RS_PA2BAR);
       double dd = add_rn(sub_rn(pbh[w], p[c]), mul_rn(P.rho[0], dz5)), dd_dp = -1.0 + P.drho[0] * dz5;
       double q_ = 0, dqdp = 0, dqds = 0, dqdb = 0;
-      if (wkind[w] == SIM_PROD) {
+      if (wkind[w] == SIM_PROD || dd < 0.0) {
         if (dd <= 0.0) { q_ = pwi[q] * P.m[0] * dd; dqdp = pwi[q] * (P.dmp[0] * dd + P.m[0] * dd_dp);
                          dqds = pwi[q] * P.dms[0] * dd; dqdb = pwi[q] * P.m[0]; }
       } else {
@@ -403,6 +410,36 @@ static float ev_ms(sim_s *h) {
 
 // Algorithm 1 for one time step at h->dt.  0 = converged, 1 = iteration cap,
 // 2 = non-finite value.
+// One linear solve of the Newton system on the device (after ls_setup),
+// with the learned initial guess when a network is attached and a previous
+// update exists: the prediction is kept only when its residual on the
+// decoupled system is smaller than that of the zero guess.  Recording and the
+// previous-update history follow the solve.
+static int s_solve(sim_s *h, double eta, double bn, int *its, double *rel) {
+  sim_ls_s *ls = h->ls;
+  cudaStream_t st = h->st;
+  int nb = ls->nb, nu = 2 * nb;
+  bool x0 = false;
+  if ((h->ws || h->rec) && h->have_prev) ws_rms2(h->n, ls->b.p, h->wsc.p, st);
+  if (h->ws && h->have_prev) {
+    ws_predict(h->ws, h->nx, h->ny, h->nz, nb, ls->b.p, h->kx.p, h->s.p, h->yprev.p, h->wsc.p, ls->y.p, st);
+    double rn = ls_residual_norm(ls, ls->y.p);
+    if (std::isfinite(rn) && rn < bn) { x0 = true; h->stats.ws_used++; }
+    else h->stats.ws_fallback++;
+  }
+  int rc = ls_solve(ls, eta, its, rel, x0);
+  if (rc == 2) return rc;
+  if (h->rec && h->have_prev)
+    ws_record(h->rec, h->nx, h->ny, h->nz, ls->b.p, h->kx.p, h->s.p, h->yprev.p, h->wsc.p, ls->y.p, st);
+  if (h->ws || h->rec) {
+    RS_CUDA(cudaMemcpyAsync(h->yprev.p, ls->y.p, nu * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    ws_rms2(h->n, ls->y.p, h->wsc.p + 2, st);
+    ws_rms2(h->n, ls->b.p, h->wsc.p + 4, st);
+    h->have_prev = true;
+  }
+  return rc;
+}
+
 static int s_newton(sim_s *h, int *iters) {
   RS_CUDA(cudaEventRecord(h->e0, h->st));
   s_props_assemble(h);
@@ -422,7 +459,7 @@ static int s_newton(sim_s *h, int *iters) {
     double eta = h->o.newton == SIM_NEWTON_INEXACT ? s_forcing(l, bn, rprev, bprev) : h->o.lin_tol;
     int its; double rel;
     RS_CUDA(cudaEventRecord(h->e0, h->st));
-    int rc = ls_solve(h->ls, eta, &its, &rel);
+    int rc = s_solve(h, eta, bn, &its, &rel);
     h->stats.ms_solve += ev_ms(h);
     h->stats.linear_its += its; h->stats.linear_solves++;
     h->stats.last_its = its; h->stats.last_relres = rel;
@@ -584,6 +621,7 @@ extern "C" sim_status sim_init_hydrostatic(sim_t h, double p_datum, double sw0) 
     RS_LAUNCHED(1);
   }
   h->t = 0.0;
+  h->have_prev = false;
   s_store_old(h);
   RS_CHECK_LAUNCH();
   RS_CUDA(cudaStreamSynchronize(h->st));
@@ -635,7 +673,8 @@ extern "C" sim_status sim_linear_solve(sim_t h, double tol, int *iters, double *
   if (!h) RS_FAIL(SIM_ERR_ARG, "NULL handle");
   ls_setup(h->ls);
   int its; double rel;
-  int rc = ls_solve(h->ls, tol, &its, &rel);
+  double bn = rs_norm2(h->ls->b.p, 2 * h->ls->nb, h->st);
+  int rc = s_solve(h, tol, bn, &its, &rel);
   if (iters) *iters = its;
   if (relres) *relres = rel;
   if (rc == 2) RS_FAIL(SIM_ERR_NAN, "linear solve produced a non-finite value");
@@ -653,7 +692,8 @@ extern "C" sim_status sim_newton_step(sim_t h, int *converged, sim_stats *st) {
   if (nr > h->o.newton_tol) {
     ls_setup(h->ls);
     int its; double rel;
-    int rc = ls_solve(h->ls, h->o.lin_tol, &its, &rel);
+    double bn = rs_norm2(h->ls->b.p, 2 * h->ls->nb, h->st);
+    int rc = s_solve(h, h->o.lin_tol, bn, &its, &rel);
     h->stats.linear_its += its; h->stats.linear_solves++; h->stats.last_its = its; h->stats.last_relres = rel;
     if (rc == 2) RS_FAIL(SIM_ERR_NAN, "linear solve produced a non-finite value");
     k_update<<<grid_for(h->n + h->nw, 256), 256, 0, h->st>>>(h->n, h->nw, h->o.sat_chop, h->ls->y.p, h->p.p, h->s.p, h->pb.p);
@@ -709,6 +749,42 @@ extern "C" sim_status sim_get_stats(sim_t h, sim_stats *st) {
 
 void sim_dims(sim_t h, int *n, int *n_wells) { *n = h->n; *n_wells = h->nw; }
 void sim_put_stats(sim_t h, const sim_stats *st) { h->stats = *st; }
+// warm-start history (previous update and scales): save into / restore from
+// caller-owned device buffers of 2 nb and 8 doubles
+int sim_history(sim_t h, double *y, double *sc, int have, bool save) {
+  size_t nu = 2 * (size_t)h->ls->nb;
+  if (save) {
+    if (h->have_prev) {
+      RS_CUDA(cudaMemcpyAsync(y, h->yprev.p, nu * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+      RS_CUDA(cudaMemcpyAsync(sc, h->wsc.p, 8 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    }
+    RS_CUDA(cudaStreamSynchronize(h->st));
+    return h->have_prev ? 1 : 0;
+  }
+  if (have) {
+    RS_CUDA(cudaMemcpyAsync(h->yprev.p, y, nu * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    RS_CUDA(cudaMemcpyAsync(h->wsc.p, sc, 8 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    RS_CUDA(cudaStreamSynchronize(h->st));
+  }
+  h->have_prev = have != 0;
+  return have;
+}
+
+extern "C" sim_status sim_ws_attach(sim_t h, sim_ws_t ws) {
+  ABI_BEGIN
+  if (!h) RS_FAIL(SIM_ERR_ARG, "NULL handle");
+  if (ws) { h->yprev.ensure(2 * (size_t)h->ls->nb); h->wsc.ensure(8); }
+  h->ws = ws;
+  ABI_END
+}
+
+extern "C" sim_status sim_ws_record(sim_t h, sim_ws_t ws) {
+  ABI_BEGIN
+  if (!h) RS_FAIL(SIM_ERR_ARG, "NULL handle");
+  if (ws) { h->yprev.ensure(2 * (size_t)h->ls->nb); h->wsc.ensure(8); }
+  h->rec = ws;
+  ABI_END
+}
 
 extern "C" sim_ls_t sim_linear_system(sim_t h) { return h ? h->ls : nullptr; }
 

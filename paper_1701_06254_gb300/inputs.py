@@ -117,7 +117,8 @@ def _grf(rng, nx, ny, nz, lx, ly, lz):
     f = rng.standard_normal((nz, ny, nx))
     for axis, ell in ((2, lx), (1, ly), (0, lz)):
         w = _gauss_kernel(max(ell / 2.0, 1e-3))
-        f = np.apply_along_axis(lambda v: np.convolve(v, w, mode="same"), axis, f)
+        r = (len(w) - 1) // 2            # centred "same" window, also when the kernel is longer than the axis
+        f = np.apply_along_axis(lambda v: np.convolve(v, w)[r:r + len(v)], axis, f)
     f = (f - f.mean()) / f.std()
     return f.ravel()
 
@@ -192,19 +193,17 @@ def case2(seed: int = 2, nx=200, ny=200, nz=25) -> Case:
 
 def ensemble_member(k: int, seed0: int = 2000, size_lo=(32, 32, 8), size_hi=(128, 128, 32),
                     n_steps: int = 20) -> Case:
-    """Member k of the ensemble workload: the correlated-layer physics of
-    case1 on a grid drawn from U{32..128} x U{32..128} x U{8..32} (seed
-    seed0 + k), five-spot wells with the injection rates scaled to the grid's
-    areal size, 10-day steps.  size_lo / size_hi narrow the draw for tests."""
+    """Member k of the ensemble workload: the channelised two-facies field,
+    wells and Newton settings of case2 on a grid drawn from
+    U{32..128} x U{32..128} x U{8..32} (seed seed0 + k; correlation lengths,
+    well positions and injection rates scale with the grid), 10-day steps.
+    size_lo / size_hi narrow the draw for tests."""
     rng = np.random.default_rng(seed0 + k)
     nx = int(rng.integers(size_lo[0], size_hi[0] + 1))
     ny = int(rng.integers(size_lo[1], size_hi[1] + 1))
     nz = int(rng.integers(size_lo[2], size_hi[2] + 1))
-    c = case1(seed=seed0 + k, nx=nx, ny=ny, nz=nz)
+    c = case2(seed=seed0 + k, nx=nx, ny=ny, nz=nz)
     c.name = f"ens{k}_{nx}x{ny}x{nz}"
-    for w in c.wells:
-        if w.kind == INJ:
-            w.target = 500.0 * (nx * ny) / (100.0 * 100.0)
     c.dt, c.n_steps = 10.0, n_steps
     return c
 

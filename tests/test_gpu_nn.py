@@ -1,0 +1,157 @@
+"""The learned warm start's network on the GPU (BF16 tensor-core kernels,
+FP32 accumulation) against the FP64 network oracle (oracle/nn.py).
+
+Both sides start from the same parameters: the GPU's FP32 master weights,
+which the oracle takes rounded to BF16 exactly as the kernels do.  The
+oracle also rounds to BF16 at the points where the kernels store an
+activation or a gradient, so the remaining differences come from FP32
+accumulation order and the occasional rounding-boundary flip they cause:
+the forward output must match to 1e-2 relative (Frobenius), every
+parameter gradient to 3e-2; Adam's update (FP32) to 1e-5.  Without the
+emulated rounding (plain FP64 oracle) the output still agrees to 5e-2.
+Odd grid sizes make every pooling level ragged.
+"""
+import numpy as np
+import pytest
+
+import paper_1701_06254_gb300 as R
+from paper_1701_06254_gb300 import inputs as I
+from oracle import nn
+
+pytestmark = pytest.mark.gpu
+
+
+def _to_dict(flat):
+    P, q = {}, 0
+    for name, ci, co, _ in nn.LAYERS:
+        W = flat[q:q + 27 * co * ci].reshape(27, co, ci).astype(np.float64); q += 27 * co * ci
+        b = flat[q:q + co].astype(np.float64); q += co
+        P[name] = (W, b)
+    assert q == flat.size
+    return P
+
+
+def _to_flat(P):
+    return np.concatenate([np.concatenate([P[name][0].ravel(), P[name][1].ravel()]) for name, *_ in nn.LAYERS])
+
+
+def _bf16_weights(P):
+    return {k: (nn.bf16_round(W), b) for k, (W, b) in P.items()}
+
+
+def _setup(shape=(5, 7, 9), seed=3):
+    ws = R.WarmStart(seed=seed)
+    rng = np.random.default_rng(seed)
+    flat = ws.params()
+    # non-zero biases so that they are exercised
+    P = _to_dict(flat)
+    for k in P:
+        P[k] = (P[k][0], 0.05 * rng.standard_normal(P[k][1].shape))
+    flat = _to_flat(P).astype(np.float32)
+    ws.set_params(flat)
+    P = _to_dict(flat)
+    F = nn.bf16_round(rng.standard_normal(shape + (8,)))
+    T = rng.standard_normal(shape + (2,))
+    return ws, P, F, T
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def test_forward_matches_oracle():
+    ws, P, F, T = _setup()
+    y = ws.forward(F.astype(np.float32))
+    yo, _ = nn.forward(_bf16_weights(P), F, rnd=nn.bf16_round)
+    assert _rel(y, yo) <= 1e-2, _rel(y, yo)
+    yp, _ = nn.forward(_bf16_weights(P), F)
+    assert _rel(y, yp) <= 5e-2, _rel(y, yp)
+
+
+def test_backward_matches_oracle():
+    ws, P, F, T = _setup(shape=(6, 5, 11), seed=4)
+    ws.zero_grad()
+    loss = ws.backward(F.astype(np.float32), T.astype(np.float32))
+    g = _to_dict(ws.params(which=1))
+    Pb = _bf16_weights(P)
+    yo, cache = nn.forward(Pb, F, rnd=nn.bf16_round)
+    To = np.zeros(yo.shape); To[..., :2] = T
+    go = nn.backward(Pb, cache, yo, To)
+    assert loss == pytest.approx(nn.loss(yo, To), rel=2e-2)
+    for name, *_ in nn.LAYERS:
+        for k in range(2):
+            e = _rel(g[name][k], go[name][k])
+            assert e <= 3e-2, (name, "W" if k == 0 else "b", e)
+
+
+def test_adam_step_matches_oracle():
+    ws, P, F, T = _setup(shape=(4, 6, 5), seed=5)
+    ws.zero_grad()
+    ws.backward(F.astype(np.float32), T.astype(np.float32))
+    g = ws.params(which=1).astype(np.float64)
+    p0 = ws.params().astype(np.float64)
+    ws.adam(1e-3)
+    p1 = ws.params().astype(np.float64)
+    pe, _, _ = nn.adam_step(p0, g, np.zeros_like(p0), np.zeros_like(p0), 1, 1e-3)
+    assert np.max(np.abs(p1 - pe)) <= 1e-5 * 1e-3 + 1e-6 * np.max(np.abs(p0)), np.max(np.abs(p1 - pe))
+
+
+def test_gradients_accumulate_over_samples():
+    ws, P, F, T = _setup(shape=(3, 4, 5), seed=6)
+    ws.zero_grad()
+    ws.backward(F.astype(np.float32), T.astype(np.float32))
+    g1 = ws.params(which=1)
+    ws.backward(F.astype(np.float32), T.astype(np.float32))
+    g2 = ws.params(which=1)             # mean over two identical samples
+    np.testing.assert_allclose(g2, g1, rtol=1e-5, atol=1e-9)
+
+
+def _run(case, steps, ws=None, rec=None, **opts):
+    g = R.Sim(case, **opts)
+    g.init_hydrostatic()
+    if ws is not None:
+        g.attach_warm_start(ws)
+    if rec is not None:
+        g.record_to(rec)
+    g.advance(steps)
+    return g
+
+
+def test_training_on_recorded_solves_lowers_the_loss():
+    ws = R.WarmStart(seed=11)
+    for k in range(3):
+        c = I.ensemble_member(k, seed0=5100, size_lo=(12, 12, 4), size_hi=(16, 16, 6))
+        _run(c, 3, rec=ws, precision=R.PREC_MIXED)
+    n = ws.dataset_size()
+    assert n >= 6
+    l0 = ws.eval()
+    l1 = ws.train(epochs=30, batch=2, lr=2e-3, seed=1)
+    assert np.isfinite(l1) and ws.eval() < 0.5 * l0, (l0, l1, ws.eval())
+
+
+def test_warm_start_keeps_the_converged_solution():
+    """With a network attached (trained briefly), every solve still meets its
+    tolerance: the run matches the FP64 oracle with the whole-run tolerances,
+    and every solve after the first took the prediction or the fallback."""
+    import oracle
+    ws = R.WarmStart(seed=12)
+    for k in range(2):
+        _run(I.ensemble_member(k, seed0=5200, size_lo=(12, 12, 4), size_hi=(16, 16, 6)), 3, rec=ws,
+             precision=R.PREC_MIXED)
+    ws.train(epochs=20, batch=2, lr=2e-3, seed=2)
+    c = I.ensemble_member(7, seed0=5200, size_lo=(12, 12, 4), size_hi=(16, 16, 6))
+    o = oracle.Sim(c)
+    o.init_hydrostatic()
+    g = R.Sim(c, precision=R.PREC_MIXED)
+    g.init_hydrostatic()
+    g.attach_warm_start(ws)
+    for k in range(3):
+        assert o.advance(1) == 0
+        g.advance(1)
+        po, so, _, to = o.get_state()
+        pg, sg, _, tg = g.get_state()
+        assert tg == to
+        assert np.max(np.abs(pg - po) / np.abs(po)) <= 1e-6, k
+        assert np.max(np.abs(sg - so)) <= 1e-6, k
+    st = g.stats()
+    assert st["ws_used"] + st["ws_fallback"] == st["linear_solves"] - 1
