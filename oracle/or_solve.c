@@ -394,13 +394,14 @@ int or_lsys_solve(or_lsys *ls, double tol, double *y, int *its_out, double *relr
       or_cpr_apply(ls, vj, zj);
       or_bsr_mv(ls, zj, w);
       /* classical Gram-Schmidt; a second pass only when the first one
-         removed most of w (||w_1|| < ||w|| / sqrt(2): Daniel, Gragg,
-         Kaufman and Stewart's criterion) */
+         removed nearly all of w (||w_1|| < 1e-2 ||w||, the Daniel, Gragg,
+         Kaufman and Stewart test with a small threshold: a pass that keeps
+         at least 1% of w loses at most ~100 eps of orthogonality) */
       double wn2 = dot(w, w, nu);
       for (int k = 0; k <= j; k++) h[k] = dot(&V[(size_t)k * nu], w, nu);
       for (int i = 0; i < nu; i++) { double s = 0; for (int k = 0; k <= j; k++) s += h[k] * V[(size_t)k * nu + i]; w[i] -= s; }
       double hn2 = dot(w, w, nu);
-      if (hn2 < 0.5 * wn2) {
+      if (hn2 < 1e-4 * wn2) {
         for (int k = 0; k <= j; k++) h2[k] = dot(&V[(size_t)k * nu], w, nu);
         for (int i = 0; i < nu; i++) { double s = 0; for (int k = 0; k <= j; k++) s += h2[k] * V[(size_t)k * nu + i]; w[i] -= s; }
         for (int k = 0; k <= j; k++) h[k] += h2[k];
