@@ -167,6 +167,30 @@ def run_reference(args, case, rank):
     print(json.dumps(line), flush=True)
 
 
+def train_warm_start(R, args, opts):
+    """Record the solves of --ws-members 64x64x16 models with the 1M-cell
+    case's physics (seeds 3000 + k, --ws-steps steps each), train the
+    network on them for --ws-epochs epochs (outside the timed region)."""
+    from paper_1701_06254_gb300 import inputs as I
+    t0 = time.perf_counter()
+    ws = R.WarmStart(seed=7)
+    for k in range(args.ws_members):
+        c = I.ensemble_member(k, seed0=3000, size_lo=(64, 64, 16), size_hi=(64, 64, 16))
+        g = R.Sim(c, **opts)
+        g.init_hydrostatic()
+        g.record_to(ws)
+        g.advance(args.ws_steps)
+        del g
+    t1 = time.perf_counter()
+    n = ws.dataset_size()
+    l0 = ws.eval()
+    loss = ws.train(epochs=args.ws_epochs, batch=4, lr=1e-3, seed=1)
+    t2 = time.perf_counter()
+    return ws, {"train_grid": "64x64x16", "members": args.ws_members, "steps": args.ws_steps, "samples": n,
+                "epochs": args.ws_epochs, "loss_before": l0, "loss_after": ws.eval(), "last_epoch_loss": loss,
+                "record_s": t1 - t0, "train_s": t2 - t1}
+
+
 def run_ensemble(args, rank, world, local):
     """--members independent models (grids drawn from U{32..128}^2 x U{8..32},
     seeds 2000 + k) advanced together by the ensemble driver.  Each rank of a
@@ -258,6 +282,11 @@ def main():
                     help="single: the 1M-cell case; ensemble: --members independent models advanced together")
     ap.add_argument("--members", type=int, default=128)
     ap.add_argument("--workers", default="auto", help="ensemble host workers, or 'auto' for the autotuner")
+    ap.add_argument("--learned", action="store_true",
+                    help="train the warm-start network on recorded 64x64x16 solves first and attach it")
+    ap.add_argument("--ws-members", type=int, default=8)
+    ap.add_argument("--ws-steps", type=int, default=5)
+    ap.add_argument("--ws-epochs", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--breakdown", action="store_true",
@@ -287,8 +316,14 @@ def main():
     prec = {"mixed": R.PREC_MIXED, "mixed_bf16": R.PREC_MIXED_BF16, "fp64": R.PREC_FP64}[args.precision]
     tx, ty = (int(v) for v in args.tile.split("x"))
     opts = dict(precision=prec, max_lin=args.max_lin, tile_x=tx, tile_y=ty)
+    ws_info = False
+    ws = None
+    if args.learned:
+        ws, ws_info = train_warm_start(R, args, opts)
     sim = R.Sim(case, **opts)
     sim.init_hydrostatic()
+    if ws is not None:
+        sim.attach_warm_start(ws)
     for _ in range(args.warmup):
         sim.advance(1)
     fam = {"ras": R.T_RAS, "spmv64": R.T_SPMV64, "spmv_prec": R.T_SPMV_PREC}[args.roofline]
@@ -389,7 +424,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"mixed": "f64+f32", "mixed_bf16": "f64+f32+bf16", "fp64": "f64"}[args.precision], "data": "synthetic",
             "config": {"workload": case.name, "cells": case.n, "wells": len(case.wells), "dt_days": case.dt,
-                       "relres": case.lin_tol, "precision": args.precision, "learned_warm_start": False,
+                       "relres": case.lin_tol, "precision": args.precision, "learned_warm_start": ws_info,
                        "ras_tile": args.tile,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "working set larger than L2 (no flush needed)",
@@ -397,6 +432,9 @@ def main():
                        "ras_levels": ras_levels},
             "roofline": roof, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
             "phases_ms_per_step": {k: (st1[k] - st0[k]) / args.steps for k in ("ms_assemble", "ms_setup", "ms_solve")},
+            "warm_start": ({"used": st1["ws_used"] - st0["ws_used"], "fallback": st1["ws_fallback"] - st0["ws_fallback"],
+                            "mean_r0": (st1["ws_r0"] - st0["ws_r0"]) / max(1, st1["linear_solves"] - st0["linear_solves"])}
+                           if ws is not None else None),
             "kernel_breakdown": breakdown,
         }
         print(json.dumps(line), flush=True)

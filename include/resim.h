@@ -106,7 +106,8 @@ typedef struct {
   double last_relres, last_norm, t;
   int last_its, last_newton;
   double ms_assemble, ms_setup, ms_solve;   /* CUDA-event time, cumulative */
-  long long ws_used, ws_fallback;           /* learned initial guesses kept / rejected */
+  long long ws_used, ws_fallback;           /* warm starts with / without the network's term */
+  double ws_r0;                             /* sum over warm-started solves of ||b - A x0|| / ||b|| */
 } sim_stats;
 
 typedef struct sim_s *sim_t;
@@ -308,13 +309,16 @@ sim_status sim_batch_autotune(sim_batch_t b, const int *candidates, int n_candid
  * training (forward, data and weight gradients, Adam with FP32 master
  * weights).  It is grid-size agnostic: weights trained on one grid apply to
  * any other.  Inputs per cell (8 channels): the decoupled right-hand side
- * (pressure and saturation rows, each over its rms), (ln k - 4) / 2,
- * 4 (s_w - 0.5), the previous solve's update (each component over its rms),
- * two zeros.  Output: the update's two components over (rms y_prev /
- * rms b_prev) * rms b.  A handle is used by one caller at a time (calls on
- * it are serialised internally). */
+ * b (pressure and saturation rows, each over its rms over the cells),
+ * (ln k - 4) / 2, 4 (s_w - 0.5), one application of the CPR preconditioner
+ * z1 = M^-1 b (each component over its rms), and the previous solve's update
+ * (each component over its rms; zero before the first solve).  Output: a
+ * correction to z1, each component in units of the rms of z1's, so the
+ * predicted update is z1 + rms(z1) * output (well rows: z1).  The head layer
+ * starts at zero: an untrained network predicts z1.  A handle is used by one
+ * caller at a time (calls on it are serialised internally). */
 typedef struct sim_ws_s *sim_ws_t;
-sim_status sim_ws_create(sim_ws_t *out, unsigned long long seed);   /* He-normal weights from seed */
+sim_status sim_ws_create(sim_ws_t *out, unsigned long long seed);   /* He-normal weights from seed, zero head */
 void sim_ws_destroy(sim_ws_t ws);
 
 /* Parameters in layer order (c00 c01 c10 c11 c20 c21 c30 c31 d20 d21 d10 d11
@@ -339,9 +343,9 @@ sim_status sim_ws_zero_grad(sim_ws_t ws);
  * gradient, then the gradients are cleared. */
 sim_status sim_ws_adam(sim_ws_t ws, double lr);
 
-/* Record: every linear solve of h that has a previous update appends its
- * (features, target) pair, the target being the solve's update, to ws's
- * dataset (device memory).  NULL stops recording. */
+/* Record: every linear solve of h appends its (features, target) pair, the
+ * target being (update - z1) / rms(z1), to ws's dataset (device memory).
+ * NULL stops recording. */
 sim_status sim_ws_record(sim_t h, sim_ws_t ws);
 sim_status sim_ws_dataset(sim_ws_t ws, int *n_samples);
 /* Train on the dataset: `epochs` passes in a seeded random order, an Adam
@@ -350,13 +354,15 @@ sim_status sim_ws_dataset(sim_ws_t ws, int *n_samples);
 sim_status sim_ws_train(sim_ws_t ws, int epochs, int batch, double lr, unsigned long long seed, double *mean_loss);
 sim_status sim_ws_eval(sim_ws_t ws, double *mean_loss);
 
-/* Attach a network to a simulator (NULL detaches): from the second solve on,
- * every linear solve starts from the predicted update if its residual
- * ||b - J y|| on the decoupled system is below ||b|| (the zero guess's),
- * else from zero.  The stopping test stays ||b - J y|| <= tol ||b||, so the
- * converged update meets the same tolerance either way.  sim_stats counts
- * the guesses kept (ws_used) and rejected (ws_fallback).
- * sim_init_hydrostatic clears the previous-update history. */
+/* Attach a network to a simulator (NULL detaches).  Every linear solve then
+ * starts from the least-squares combination, on the decoupled system, of
+ * z1 = M^-1 b, the network's correction and (at the first Newton iteration
+ * of a time step) the previous step's first update: the x0 in their span
+ * with the smallest ||b - J x0||.  The network's term is kept only when it
+ * lowers that residual (ws_used), else it is dropped (ws_fallback); the
+ * guess is never worse than zero.  The stopping test stays
+ * ||b - J y|| <= tol ||b||, so the converged update meets the same
+ * tolerance either way.  sim_init_hydrostatic clears the history. */
 sim_status sim_ws_attach(sim_t h, sim_ws_t ws);
 
 /* Number of this library's kernel launches issued so far (all handles). */

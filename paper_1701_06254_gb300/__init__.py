@@ -73,7 +73,7 @@ class Stats(C.Structure):
                 ("cuts", C.c_longlong), ("linear_solves", C.c_longlong), ("last_relres", C.c_double),
                 ("last_norm", C.c_double), ("t", C.c_double), ("last_its", C.c_int), ("last_newton", C.c_int),
                 ("ms_assemble", C.c_double), ("ms_setup", C.c_double), ("ms_solve", C.c_double),
-                ("ws_used", C.c_longlong), ("ws_fallback", C.c_longlong)]
+                ("ws_used", C.c_longlong), ("ws_fallback", C.c_longlong), ("ws_r0", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -145,7 +145,7 @@ static void save_member(sim_t h, saved_member &sv) {
   sv.p.ensure(n); sv.s.ensure(n); sv.pb.ensure(std::max(nw, 1));
   if (sim_get_state(h, sv.p.p, sv.s.p, nw ? sv.pb.p : nullptr, &sv.t) != SIM_OK)
     RS_FAIL(SIM_ERR_CUDA, "autotune: %s", sim_last_error());
-  sv.y.ensure(2 * (size_t)(n + nw)); sv.sc.ensure(8);
+  sv.y.ensure(4 * (size_t)(n + nw)); sv.sc.ensure(8);
   sv.have = sim_history(h, sv.y.p, sv.sc.p, 0, true);
 }
 

@@ -78,6 +78,7 @@ int rs_scan(const int *in, int *out, int n, cudaStream_t s);
 // deterministic reductions (fixed association order for a given n)
 void rs_dot_partials(const double *x, const double *y, int n, double *partials, int nblk, cudaStream_t s);
 double rs_norm2(const double *x, int n, cudaStream_t s);   // syncs
+void rs_dots(const double *const *x, const double *const *y, int m, int n, double *out, cudaStream_t s);  // syncs
 void rs_fill_i(int *p, int v, size_t n, cudaStream_t s);
 void rs_fill_d(double *p, double v, size_t n, cudaStream_t s);
 void rs_fill_f(float *p, float v, size_t n, cudaStream_t s);
@@ -218,6 +219,7 @@ void ls_setup(sim_ls_s *ls);
 int ls_solve(sim_ls_s *ls, double tol, int *its, double *relres, bool x0 = false);
 void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32);
 void ls_spmv64(sim_ls_s *ls, const double *x, double *y);
+void ls_spmv64_untimed(sim_ls_s *ls, const double *x, double *y);
 double ls_residual_norm(sim_ls_s *ls, const double *x_dev);
 template <class T, class Tin> void ls_ras_apply(sim_ls_s *ls, const Tin *f, T *x, bool accumulate);
 void ras_build_static(sim_ls_s *ls);
@@ -232,12 +234,12 @@ void csr_spmv(const int *rp, const int *ci, const T *v, const T *x, T *y, int n,
 // simulator internals used by the ensemble driver (batch.cu)
 void sim_dims(sim_t h, int *n, int *n_wells);
 void sim_put_stats(sim_t h, const sim_stats *st);
-int sim_history(sim_t h, double *y, double *sc, int have, bool save);
+int sim_history(sim_t h, double *y, double *sc, int have, bool save);   // y: 2 vectors of 2 nb
 
 // learned warm start (nn.cu)
 struct sim_ws_s;
 void ws_rms2(int n, const double *v, double *out, cudaStream_t s);
-void ws_predict(sim_ws_s *w, int nx, int ny, int nz, int nb, const double *b, const double *kx, const double *sw,
-                const double *yp, const double *sc, double *y, cudaStream_t s);
-void ws_record(sim_ws_s *w, int nx, int ny, int nz, const double *b, const double *kx, const double *sw,
-               const double *yp, const double *sc, const double *y, cudaStream_t s);
+void ws_predict(sim_ws_s *w, int nx, int ny, int nz, int nb, const double *b, const double *z1, const double *kx,
+                const double *sw, const double *yp, const double *sc, double *y, cudaStream_t s);
+void ws_record(sim_ws_s *w, int nx, int ny, int nz, const double *b, const double *z1, const double *kx,
+               const double *sw, const double *yp, const double *sc, const double *y, cudaStream_t s);

@@ -37,11 +37,12 @@ struct sim_s {
   sim_ls_s *ls = nullptr;
   sim_stats stats;
   // learned warm start: the network used for initial guesses, the one that
-  // records (features, target) pairs, the previous solve's update and the
-  // scales [rms b_p, rms b_s, rms y_prev_p, rms y_prev_s, rms b_prev_p, rms b_prev_s]
+  // records (features, target) pairs, the previous solve's update, z1 = M^-1 b
+  // and the scales [rms b_p, rms b_s, rms z1_p, rms z1_s, rms y_prev_p, rms y_prev_s]
   sim_ws_s *ws = nullptr, *rec = nullptr;
-  dbuf<double> yprev, wsc;
-  bool have_prev = false;
+  dbuf<double> yprev, wsc, z1, dws, u, yfirst;
+  dbuf<float> z1f;
+  bool have_prev = false, have_first = false, first_pending = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   ~sim_s() { delete ls; if (e0) cudaEventDestroy(e0); if (e1) cudaEventDestroy(e1); }
 };
@@ -410,32 +411,143 @@ static float ev_ms(sim_s *h) {
 
 // Algorithm 1 for one time step at h->dt.  0 = converged, 1 = iteration cap,
 // 2 = non-finite value.
-// One linear solve of the Newton system on the device (after ls_setup),
-// with the learned initial guess when a network is attached and a previous
-// update exists: the prediction is kept only when its residual on the
-// decoupled system is smaller than that of the zero guess.  Recording and the
-// previous-update history follow the solve.
+__global__ void k_f2d(size_t n, const float *a, double *b) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+
+// x = sum_k beta_k c_k (k < m <= 3)
+__global__ void k_lincomb(int nu, int m, const double *c0, const double *c1, const double *c2, double b0, double b1,
+                          double b2, double *x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nu) return;
+  double v = b0 * c0[i];
+  if (m > 1) v += b1 * c1[i];
+  if (m > 2) v += b2 * c2[i];
+  x[i] = v;
+}
+
+// Least squares over the span of m candidate guesses: G beta = r with
+// G_ij = (A c_i).(A c_j), r_i = (A c_i).b; returns ||b - A x||^2 =
+// ||b||^2 - r.beta.  Cholesky with candidates whose pivot is below 1e-12 of
+// their diagonal dropped (beta = 0).
+static double ls_fit(int m, const double G[3][3], const double r[3], double bb, double beta[3]) {
+  double L[3][3] = {{0}}, z[3] = {0};
+  bool keep[3] = {false, false, false};
+  for (int i = 0; i < m; i++) {
+    double d = G[i][i];
+    for (int k = 0; k < i; k++) if (keep[k]) d -= L[i][k] * L[i][k];
+    keep[i] = G[i][i] > 0.0 && d > 1e-12 * G[i][i];
+    if (!keep[i]) continue;
+    L[i][i] = std::sqrt(d);
+    for (int j = i + 1; j < m; j++) {
+      double v = G[j][i];
+      for (int k = 0; k < i; k++) if (keep[k]) v -= L[j][k] * L[i][k];
+      L[j][i] = v / L[i][i];
+    }
+  }
+  for (int i = 0; i < m; i++) {
+    if (!keep[i]) continue;
+    double v = r[i];
+    for (int k = 0; k < i; k++) if (keep[k]) v -= L[i][k] * z[k];
+    z[i] = v / L[i][i];
+  }
+  for (int i = m - 1; i >= 0; i--) {
+    beta[i] = 0.0;
+    if (!keep[i]) continue;
+    double v = z[i];
+    for (int k = i + 1; k < m; k++) if (keep[k]) v -= L[k][i] * beta[k];
+    beta[i] = v / L[i][i];
+  }
+  double rb = 0.0;
+  for (int i = 0; i < m; i++) rb += r[i] * beta[i];
+  return bb - rb;
+}
+
+// One linear solve of the Newton system on the device (after ls_setup).
+// With a network attached, the initial guess is the least-squares
+// combination, on the decoupled system, of z1 = M^-1 b (one application of
+// the CPR preconditioner), the network's correction d and, at the first
+// Newton iteration of a step, the previous step's first update.  The
+// network's term is kept only when it lowers ||b - A x0|| below what the
+// other candidates reach without it (otherwise the plain combination is the
+// fallback); any such combination has ||b - A x0|| <= ||b||, the zero guess's.
+// Recording needs z1 and the rms scales of b, z1 and the previous update.
 static int s_solve(sim_s *h, double eta, double bn, int *its, double *rel) {
   sim_ls_s *ls = h->ls;
   cudaStream_t st = h->st;
   int nb = ls->nb, nu = 2 * nb;
   bool x0 = false;
-  if ((h->ws || h->rec) && h->have_prev) ws_rms2(h->n, ls->b.p, h->wsc.p, st);
-  if (h->ws && h->have_prev) {
-    ws_predict(h->ws, h->nx, h->ny, h->nz, nb, ls->b.p, h->kx.p, h->s.p, h->yprev.p, h->wsc.p, ls->y.p, st);
-    double rn = ls_residual_norm(ls, ls->y.p);
-    if (std::isfinite(rn) && rn < bn) { x0 = true; h->stats.ws_used++; }
+  bool learn = h->ws || h->rec;
+  bool first = h->first_pending;
+  h->first_pending = false;
+  if (learn) {
+    h->z1.ensure(nu);
+    if (ls->o.precision != SIM_PREC_FP64) {
+      h->z1f.ensure(nu);
+      ls_cpr(ls, ls->b.p, nullptr, h->z1f.p);
+      k_f2d<<<grid_for(nu, 256), 256, 0, st>>>((size_t)nu, h->z1f.p, h->z1.p);
+      RS_LAUNCHED(1);
+    } else {
+      ls_cpr(ls, ls->b.p, h->z1.p, nullptr);
+    }
+    ws_rms2(h->n, ls->b.p, h->wsc.p, st);
+    ws_rms2(h->n, h->z1.p, h->wsc.p + 2, st);
+    if (!h->have_prev) RS_CUDA(cudaMemsetAsync(h->wsc.p + 4, 0, 2 * sizeof(double), st));
+  }
+  if (h->ws) {
+    h->dws.ensure(nu); h->u.ensure(3 * (size_t)nu);
+    ws_predict(h->ws, h->nx, h->ny, h->nz, nb, ls->b.p, h->z1.p, h->kx.p, h->s.p, h->yprev.p, h->wsc.p, h->dws.p, st);
+    // candidates: 0 = z1, 1 = previous step's first update (if any), then d
+    const double *c[3];
+    int m = 0;
+    c[m++] = h->z1.p;
+    if (first && h->have_first) c[m++] = h->yfirst.p;
+    int id = m;
+    c[m++] = h->dws.p;
+    double *u[3];
+    for (int k = 0; k < m; k++) { u[k] = h->u.p + (size_t)k * nu; ls_spmv64_untimed(ls, c[k], u[k]); }
+    const double *xs[9], *ys[9];
+    int q = 0;
+    for (int i = 0; i < m; i++) for (int j = 0; j <= i; j++) { xs[q] = u[i]; ys[q] = u[j]; q++; }
+    for (int i = 0; i < m; i++) { xs[q] = u[i]; ys[q] = ls->b.p; q++; }
+    double dv[9];
+    rs_dots(xs, ys, q, nu, dv, st);
+    double G[3][3] = {{0}}, r[3] = {0};
+    q = 0;
+    for (int i = 0; i < m; i++) for (int j = 0; j <= i; j++) { G[i][j] = G[j][i] = dv[q]; q++; }
+    for (int i = 0; i < m; i++) r[i] = dv[q++];
+    double bb = bn * bn, beta_p[3] = {0, 0, 0}, beta_d[3] = {0, 0, 0};
+    double res_p = ls_fit(id, G, r, bb, beta_p);       // without the network's term
+    double res_d = ls_fit(m, G, r, bb, beta_d);        // with it
+    const double *beta = beta_p;
+    double res = res_p;
+    if (std::isfinite(res_d) && res_d < res_p * (1.0 - 1e-6)) { beta = beta_d; res = res_d; h->stats.ws_used++; }
     else h->stats.ws_fallback++;
+    int mm = beta == beta_d ? m : id;
+    if (std::isfinite(res) && res < bb) {
+      k_lincomb<<<grid_for(nu, 256), 256, 0, st>>>(nu, mm, c[0], mm > 1 ? c[1] : c[0], mm > 2 ? c[2] : c[0],
+                                                   beta[0], beta[1], beta[2], ls->y.p);
+      RS_LAUNCHED(1);
+      x0 = true;
+      h->stats.ws_r0 += std::sqrt(std::max(res, 0.0)) / bn;
+    } else {
+      h->stats.ws_r0 += 1.0;
+    }
   }
   int rc = ls_solve(ls, eta, its, rel, x0);
   if (rc == 2) return rc;
-  if (h->rec && h->have_prev)
-    ws_record(h->rec, h->nx, h->ny, h->nz, ls->b.p, h->kx.p, h->s.p, h->yprev.p, h->wsc.p, ls->y.p, st);
-  if (h->ws || h->rec) {
+  if (h->rec)
+    ws_record(h->rec, h->nx, h->ny, h->nz, ls->b.p, h->z1.p, h->kx.p, h->s.p, h->yprev.p, h->wsc.p, ls->y.p, st);
+  if (learn) {
     RS_CUDA(cudaMemcpyAsync(h->yprev.p, ls->y.p, nu * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    ws_rms2(h->n, ls->y.p, h->wsc.p + 2, st);
-    ws_rms2(h->n, ls->b.p, h->wsc.p + 4, st);
+    ws_rms2(h->n, ls->y.p, h->wsc.p + 4, st);
     h->have_prev = true;
+    if (first) {
+      h->yfirst.ensure(nu);
+      RS_CUDA(cudaMemcpyAsync(h->yfirst.p, ls->y.p, nu * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      h->have_first = true;
+    }
   }
   return rc;
 }
@@ -621,7 +733,7 @@ extern "C" sim_status sim_init_hydrostatic(sim_t h, double p_datum, double sw0) 
     RS_LAUNCHED(1);
   }
   h->t = 0.0;
-  h->have_prev = false;
+  h->have_prev = h->have_first = false;
   s_store_old(h);
   RS_CHECK_LAUNCH();
   RS_CUDA(cudaStreamSynchronize(h->st));
@@ -654,6 +766,7 @@ extern "C" sim_status sim_begin_step(sim_t h, double dt) {
   ABI_BEGIN
   if (!h || !(dt > 0)) RS_FAIL(SIM_ERR_ARG, "sim_begin_step: bad argument");
   h->dt = dt;
+  h->first_pending = true;
   s_store_old(h);
   RS_CHECK_LAUNCH();
   ABI_END
@@ -720,6 +833,7 @@ extern "C" sim_status sim_advance(sim_t h, int n_steps, sim_stats *st) {
       if (nw) RS_CUDA(cudaMemcpyAsync(h->pb0.p, h->pb.p, nw * sizeof(double), cudaMemcpyDeviceToDevice, s));
       s_store_old(h);
       h->dt = dt;
+      h->first_pending = true;
       int its;
       int r = s_newton(h, &its);
       h->stats.last_newton = its;
@@ -758,15 +872,21 @@ int sim_history(sim_t h, double *y, double *sc, int have, bool save) {
       RS_CUDA(cudaMemcpyAsync(y, h->yprev.p, nu * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
       RS_CUDA(cudaMemcpyAsync(sc, h->wsc.p, 8 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     }
+    if (h->have_first) RS_CUDA(cudaMemcpyAsync(y + nu, h->yfirst.p, nu * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     RS_CUDA(cudaStreamSynchronize(h->st));
-    return h->have_prev ? 1 : 0;
+    return (h->have_prev ? 1 : 0) | (h->have_first ? 2 : 0);
   }
-  if (have) {
+  if (have & 1) {
     RS_CUDA(cudaMemcpyAsync(h->yprev.p, y, nu * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     RS_CUDA(cudaMemcpyAsync(h->wsc.p, sc, 8 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-    RS_CUDA(cudaStreamSynchronize(h->st));
   }
-  h->have_prev = have != 0;
+  if (have & 2) {
+    h->yfirst.ensure(nu);
+    RS_CUDA(cudaMemcpyAsync(h->yfirst.p, y + nu, nu * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  }
+  RS_CUDA(cudaStreamSynchronize(h->st));
+  h->have_prev = (have & 1) != 0;
+  h->have_first = (have & 2) != 0;
   return have;
 }
 

@@ -136,6 +136,22 @@ double rs_norm2(const double *x, int n, cudaStream_t s) {
   return sqrt(r);
 }
 
+// out[k] = x[k] . y[k] for k < m (m <= 16), one synchronisation for all
+void rs_dots(const double *const *x, const double *const *y, int m, int n, double *out, cudaStream_t s) {
+  static thread_local dbuf<double> part;
+  int nb = dot_blocks(n);
+  part.ensure((size_t)(nb + 1) * m);
+  for (int k = 0; k < m; k++) {
+    double *pk = part.p + (size_t)k * (nb + 1);
+    k_dot_partials<<<nb, 256, 0, s>>>(x[k], y[k], n, pk);
+    k_sum_partials<<<1, 256, 0, s>>>(pk, nb, pk + nb);
+  }
+  RS_LAUNCHED(2 * m);
+  RS_CHECK_LAUNCH();
+  std::vector<double> h = d2h(part.p, (size_t)(nb + 1) * m, s);
+  for (int k = 0; k < m; k++) out[k] = h[(size_t)k * (nb + 1) + nb];
+}
+
 template <class T> __global__ void k_fill(T *p, T v, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
 }
