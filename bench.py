@@ -191,6 +191,37 @@ def train_warm_start(R, args, opts):
                 "record_s": t1 - t0, "train_s": t2 - t1}
 
 
+def measure_variant(R, torch, case, opts, args, ws=None):
+    """One more configuration of the same workload, timed like the main run
+    (W warm-up steps, K timed steps between CUDA events on the device)."""
+    sim = R.Sim(case, **opts)
+    sim.init_hydrostatic()
+    if ws is not None:
+        sim.attach_warm_start(ws)
+    for _ in range(args.warmup):
+        sim.advance(1)
+    st0 = sim.stats()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        sim.advance(1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st1 = sim.stats()
+    dn = st1["newton"] - st0["newton"]
+    dl = max(1, st1["linear_solves"] - st0["linear_solves"])
+    out = {"value": case.n * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+           "newton_per_step": dn / args.steps, "fgmres_its_per_newton": (st1["linear_its"] - st0["linear_its"]) / max(1, dn)}
+    if ws is not None:
+        out["warm_start"] = {"network_term_kept": st1["ws_used"] - st0["ws_used"],
+                             "network_term_dropped": st1["ws_fallback"] - st0["ws_fallback"],
+                             "mean_r0_over_b": (st1["ws_r0"] - st0["ws_r0"]) / dl}
+    del sim
+    return out
+
+
 def run_ensemble(args, rank, world, local):
     """--members independent models (grids drawn from U{32..128}^2 x U{8..32},
     seeds 2000 + k) advanced together by the ensemble driver.  Each rank of a
@@ -287,6 +318,8 @@ def main():
     ap.add_argument("--ws-members", type=int, default=8)
     ap.add_argument("--ws-steps", type=int, default=5)
     ap.add_argument("--ws-epochs", type=int, default=10)
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the plain-FP64 and mixed+learned comparison runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--breakdown", action="store_true",
@@ -410,6 +443,19 @@ def main():
         e2e = {"value": world * case.n * args.steps / te, "unit": UNIT,
                "h2d_bytes_per_step": (2 * case.n + nw) * 8, "d2h_bytes_per_step": (2 * case.n + nw) * 8}
 
+    # the method's two reference points on the same workload: plain FP64
+    # CPR-FGMRES and the mixed-precision path with the learned warm start
+    variants = None
+    if not args.no_variants:
+        variants = {"plain_fp64": measure_variant(R, torch, case, dict(opts, precision=R.PREC_FP64), args)}
+        if ws is None:
+            ws, info = train_warm_start(R, args, opts)
+        else:
+            info = ws_info
+        lv = measure_variant(R, torch, case, opts, args, ws)
+        lv["training"] = info
+        variants[args.precision + "_learned"] = lv
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_it, its = oracle_newton_iteration(case, dict(max_lin=args.max_lin))
@@ -436,6 +482,7 @@ def main():
                             "mean_r0": (st1["ws_r0"] - st0["ws_r0"]) / max(1, st1["linear_solves"] - st0["linear_solves"])}
                            if ws is not None else None),
             "kernel_breakdown": breakdown,
+            "variants": variants,
         }
         print(json.dumps(line), flush=True)
     if dist:

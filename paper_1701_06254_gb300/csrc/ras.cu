@@ -409,6 +409,40 @@ template <> __device__ __forceinline__ double to_blob_d<double>(double v) { retu
 __device__ __forceinline__ float from_blob(float v) { return v; }
 __device__ __forceinline__ double from_blob(double v) { return v; }
 __device__ __forceinline__ float from_blob(__nv_bfloat16 v) { return __bfloat162float(v); }
+// one 2x2 block of the packed factors in a single shared-memory load
+__device__ __forceinline__ void blk4(const __nv_bfloat16 *B, float &b0, float &b1, float &b2, float &b3) {
+  uint2 u = *reinterpret_cast<const uint2 *>(B);
+  __nv_bfloat162 lo = *reinterpret_cast<__nv_bfloat162 *>(&u.x), hi = *reinterpret_cast<__nv_bfloat162 *>(&u.y);
+  b0 = __low2float(lo); b1 = __high2float(lo); b2 = __low2float(hi); b3 = __high2float(hi);
+}
+__device__ __forceinline__ void blk4(const float *B, float &b0, float &b1, float &b2, float &b3) {
+  float4 v = *reinterpret_cast<const float4 *>(B);
+  b0 = v.x; b1 = v.y; b2 = v.z; b3 = v.w;
+}
+__device__ __forceinline__ void blk4(const double *B, double &b0, double &b1, double &b2, double &b3) {
+  double2 u = reinterpret_cast<const double2 *>(B)[0], v = reinterpret_cast<const double2 *>(B)[1];
+  b0 = u.x; b1 = u.y; b2 = v.x; b3 = v.y;
+}
+// a -= sum over q in [q0, q1) of B_q y[cols[q]], in the order of q; the
+// entries are taken four at a time so that their column and block loads,
+// then their y loads, are in flight together
+template <class T, class T2, class TB>
+__device__ __forceinline__ void row_sub(T2 &a, int q0, int q1, const uint16_t *cols, const TB *vals, const T2 *y) {
+  for (int q = q0; q < q1; q += 4) {
+    int c[4];
+    T bb[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+      if (q + u < q1) { c[u] = cols[q + u]; blk4(vals + 4 * (q + u), bb[u][0], bb[u][1], bb[u][2], bb[u][3]); }
+    T2 yc[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+      if (q + u < q1) yc[u] = y[c[u]];
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+      if (q + u < q1) { a.x -= bb[u][0] * yc[u].x + bb[u][1] * yc[u].y; a.y -= bb[u][2] * yc[u].x + bb[u][3] * yc[u].y; }
+  }
+}
 
 // T: factor type (FP32 or FP64), TB: stored value type (T, or BF16)
 template <class T, class TB>
@@ -568,12 +602,7 @@ __global__ void __launch_bounds__(RAS_BS) k_ras_apply_smem(const long long *blob
     for (int r = llev[k] + threadIdx.x; r < llev[k + 1]; r += blockDim.x) {
       int i = lrow[r];
       T2 a = y[i];
-      int q1 = dg[i];
-      for (int q = rp[i]; q < q1; q++) {
-        const TB *B = vals + 4 * q; T2 c = y[cols[q]];
-        T b0 = from_blob(B[0]), b1 = from_blob(B[1]), b2 = from_blob(B[2]), b3 = from_blob(B[3]);
-        a.x -= b0 * c.x + b1 * c.y; a.y -= b2 * c.x + b3 * c.y;
-      }
+      row_sub<T, T2, TB>(a, rp[i], dg[i], cols, vals, y);
       y[i] = a;
     }
     __syncthreads();
@@ -582,15 +611,11 @@ __global__ void __launch_bounds__(RAS_BS) k_ras_apply_smem(const long long *blob
     for (int r = ulev[k] + threadIdx.x; r < ulev[k + 1]; r += blockDim.x) {
       int i = urow[r];
       T2 a = y[i];
-      int q1 = rp[i + 1];
-      for (int q = dg[i]; q < q1; q++) {
-        const TB *B = vals + 4 * q; T2 c = y[cols[q]];
-        T b0 = from_blob(B[0]), b1 = from_blob(B[1]), b2 = from_blob(B[2]), b3 = from_blob(B[3]);
-        a.x -= b0 * c.x + b1 * c.y; a.y -= b2 * c.x + b3 * c.y;
-      }
-      const TB *D = dv + 4 * i;
+      T d0, d1, d2, d3;
+      blk4(dv + 4 * i, d0, d1, d2, d3);
+      row_sub<T, T2, TB>(a, dg[i], rp[i + 1], cols, vals, y);
       T2 o;
-      o.x = from_blob(D[0]) * a.x + from_blob(D[1]) * a.y; o.y = from_blob(D[2]) * a.x + from_blob(D[3]) * a.y;
+      o.x = d0 * a.x + d1 * a.y; o.y = d2 * a.x + d3 * a.y;
       y[i] = o;
     }
     __syncthreads();
