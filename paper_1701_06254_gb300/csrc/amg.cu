@@ -161,13 +161,24 @@ __global__ void k_sort_rows(int n, const int *rp, int *ci, double *v) {
 // C = A B, one warp per row of C: expand every product A_ik B_kj with its
 // sequence number (row of A ascending, then row of B ascending), sort the
 // (column, sequence) keys in shared memory, and sum each column's products
-// in sequence order starting from 0.  The symbolic pass only counts.
-__global__ void k_expand_count(int n, const int *arp, const int *aci, const int *brp, int *mx) {
+// in sequence order starting from 0.  One pass: each row is written at the
+// offset of its product count (an upper bound of its length) into a scratch
+// array, then the rows are packed.
+__global__ void k_row_products(int n, const int *arp, const int *aci, const int *brp, int *prod, int *mx) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int s = 0;
   for (int q = arp[i]; q < arp[i + 1]; q++) { int k = aci[q]; s += brp[k + 1] - brp[k]; }
+  prod[i] = s;
   atomicMax(mx, s);
+}
+// C row i = scratch[toff[i] .. toff[i] + clen[i]), one warp per row
+__global__ void k_pack_rows(int n, const int *toff, const int *clen, const int *crp, const int *tci, const double *tv,
+                            int *cci, double *cv) {
+  int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= n) return;
+  int a = toff[row], b = crp[row], len = clen[row];
+  for (int t = lane; t < len; t += 32) { cci[b + t] = tci[a + t]; cv[b + t] = tv[a + t]; }
 }
 
 template <bool NUMERIC>
@@ -228,16 +239,19 @@ __global__ void k_spgemm(int n, const int *arp, const int *aci, const double *av
       }
       running += __popc(mask);
     }
-    if (!NUMERIC && lane == 0) clen[row] = running;
+    if (clen && lane == 0) clen[row] = running;
     __syncwarp();
   }
 }
 
 static void spgemm(const csr_dev<double> &A, const csr_dev<double> &B, csr_dev<double> &C, dbuf<int> &flag,
                    cudaStream_t s) {
+  static thread_local dbuf<int> toff, clen, tci;
+  static thread_local dbuf<double> tv;
   int n = A.n;
+  toff.ensure(n + 1); clen.ensure(n + 1);
   rs_fill_i(flag.p, 0, 1, s);
-  k_expand_count<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, B.rp.p, flag.p);
+  k_row_products<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, B.rp.p, toff.p, flag.p);
   RS_LAUNCHED(1);
   int mx = d2h(flag.p, 1, s)[0];
   int cap = 32;
@@ -248,22 +262,22 @@ static void spgemm(const csr_dev<double> &A, const csr_dev<double> &B, csr_dev<d
   size_t smem = per_warp * warps;
   static bool attr = false;
   if (!attr) {
-    RS_CUDA(cudaFuncSetAttribute(k_spgemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     RS_CUDA(cudaFuncSetAttribute(k_spgemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr = true;
   }
+  int total = rs_scan(toff.p, toff.p, n, s);          // row offsets into the scratch arrays
+  tci.ensure(std::max(total, 1)); tv.ensure(std::max(total, 1));
   unsigned grid = (unsigned)std::min<size_t>((n + warps - 1) / warps, 152 * 64);
   C.n = n; C.m = B.m;
   C.rp.ensure(n + 1);
-  k_spgemm<false><<<grid, warps * 32, smem, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, nullptr, C.rp.p,
-                                                 nullptr, nullptr, cap);
+  k_spgemm<true><<<grid, warps * 32, smem, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, toff.p, clen.p,
+                                                tci.p, tv.p, cap);
   RS_LAUNCHED(1);
   RS_CHECK_LAUNCH();
-  C.nnz = rs_scan(C.rp.p, C.rp.p, n, s);
+  C.nnz = rs_scan(clen.p, C.rp.p, n, s);
   RS_CUDA(cudaMemcpyAsync(C.rp.p + n, &C.nnz, sizeof(int), cudaMemcpyHostToDevice, s));
   C.ci.ensure(C.nnz); C.v.ensure(C.nnz);
-  k_spgemm<true><<<grid, warps * 32, smem, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, C.rp.p, nullptr,
-                                                C.ci.p, C.v.p, cap);
+  k_pack_rows<<<grid_for(n, 8), 256, 0, s>>>(n, toff.p, clen.p, C.rp.p, tci.p, tv.p, C.ci.p, C.v.p);
   RS_LAUNCHED(1);
   RS_CHECK_LAUNCH();
   RS_CUDA(cudaStreamSynchronize(s));   // C.nnz host value lives on this stack frame's caller

@@ -409,12 +409,21 @@ __global__ void __launch_bounds__(ORTHO_BS) k_ortho_update(int nu, int nv, const
       vp[g] = k < nv ? V + (size_t)k * nu + i0 : nullptr;
       hk[g] = k < nv ? h[k] : 0.0;
     }
-    for (int t = threadIdx.x; t < len; t += ORTHO_BS) {
-      double s = ws[t];
+    // two rows per thread per iteration: their 16 loads are in flight together
+    for (int t = threadIdx.x; t < len; t += 2 * ORTHO_BS) {
+      int t2 = t + ORTHO_BS;
+      bool two = t2 < len;
+      double v0[ORTHO_G], v1[ORTHO_G];
+#pragma unroll
+      for (int g = 0; g < ORTHO_G; g++) {
+        if (vp[g]) { v0[g] = __ldg(vp[g] + t); if (two) v1[g] = __ldg(vp[g] + t2); }
+      }
+      double s0 = ws[t], s1 = two ? ws[t2] : 0.0;
 #pragma unroll
       for (int g = 0; g < ORTHO_G; g++)       // same order as one vector at a time: w - h_0 v_0 - h_1 v_1 ...
-        if (vp[g]) s -= hk[g] * __ldg(vp[g] + t);
-      ws[t] = s;
+        if (vp[g]) { s0 -= hk[g] * v0[g]; if (two) s1 -= hk[g] * v1[g]; }
+      ws[t] = s0;
+      if (two) ws[t2] = s1;
     }
   }
   double n2 = 0.0;
