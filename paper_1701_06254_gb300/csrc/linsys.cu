@@ -7,13 +7,16 @@
 // field-split system of eqs. (20)-(23) under a fixed permutation; each well
 // row is padded to a 2x2 block with a dummy unknown whose equation is 1*x = 0.
 #include "common.cuh"
+#define ORTHO_MAXV 64            // FGMRES restart length limit (m + 1 basis vectors)
 #include <algorithm>
 #include <cmath>
 
 // ------------------------------------------------------------ timers -----
 rs_timed::rs_timed(sim_ls_s *l, int which) : ls(l), on(which > 0 && (l->timer_mask >> which) & 1u), fam(which) {
   if (!on) return;
-  if (ls->ev_used + 2 > (int)ls->ev.size()) ls->timer_flush();
+  // the pool grows (flushing, which waits on the newest event, only past
+  // 8192 events) so that timing does not make the host wait on the device
+  if (ls->ev_used + 2 > (int)ls->ev.size() && ls->ev.size() >= 8192) ls->timer_flush();
   if (ls->ev_used + 2 > (int)ls->ev.size()) {
     for (int k = 0; k < 64; k++) { cudaEvent_t e; RS_CUDA(cudaEventCreate(&e)); ls->ev.push_back(e); ls->ev_fam.push_back(0); }
   }
@@ -38,6 +41,7 @@ void sim_ls_s::timer_flush() {
 sim_ls_s::~sim_ls_s() {
   for (auto e : ev) cudaEventDestroy(e);
   if (hpin) cudaFreeHost(hpin);
+  for (auto e : itev) if (e) cudaEventDestroy(e);
   if (errw) cudaFreeHost(errw);
 }
 
@@ -259,8 +263,9 @@ void ls_init(sim_ls_s *ls, int nx, int ny, int nz, int nw, const int *rp, const 
   ls->y.alloc(nu); ls->w.alloc(nu); ls->r.alloc(nu);
   ls->x64a.alloc(nu); ls->x64b.alloc(nu);
   if (o.precision != SIM_PREC_FP64) { ls->x32b.alloc(nu); ls->x32c.alloc(nu); }
-  RS_CUDA(cudaHostAlloc((void **)&ls->hpin, 64 * sizeof(double), cudaHostAllocMapped));
-  for (int k = 0; k < 64; k++) ls->hpin[k] = 0.0;
+  RS_CUDA(cudaHostAlloc((void **)&ls->hpin, 4 * (ORTHO_MAXV + 2) * sizeof(double), cudaHostAllocMapped));
+  for (int k = 0; k < 4 * (ORTHO_MAXV + 2); k++) ls->hpin[k] = 0.0;
+  for (auto &e : ls->itev) RS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   RS_CUDA(cudaHostAlloc((void **)&ls->errw, 16 * sizeof(int), cudaHostAllocMapped));
   for (int k = 0; k < 16; k++) ls->errw[k] = 0;
   RS_CUDA(cudaHostGetDevicePointer((void **)&ls->errw_dev, ls->errw, 0));
@@ -303,7 +308,6 @@ void ls_setup(sim_ls_s *ls) {
 // partial per vector; a second kernel adds the partials in block order, so
 // results do not depend on scheduling.
 #define ORTHO_BS 256
-#define ORTHO_MAXV 64
 // Each block owns a fixed chunk of ORTHO_CH rows and keeps its slice of w in
 // shared memory.  Basis vectors are streamed vector-outer, rows-inner, so
 // loads are coalesced and independent.
@@ -493,7 +497,7 @@ __global__ void k_arnoldi_col(int j, int m, const double *h1, const double *h2, 
   g[j] = cs[j] * g[j];
   host[0] = fabs(g[j + 1]);
   host[1] = hn;
-  host[2] += re ? 1.0 : 0.0;
+  host[2] = re ? 1.0 : 0.0;
 }
 __global__ void k_scale(int nu, const double *w, const double *inv_hn, double *v) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -554,46 +558,58 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
   }
   if (beta <= tol * bn) { *its_out = 0; *relres = beta / bn; return 0; }
   int its = 0, rc = 1;
+  // One Arnoldi step j (CPR, SpMV, orthogonalisation, Givens); its residual
+  // estimate and h_{j+1,j} land in pinned slot j.  Step j + 1 is enqueued
+  // before the host waits on step j, so the device never idles on the host's
+  // convergence test; when step j converges, step j + 1 has run for nothing
+  // and nothing reads its results (column j + 1 of H, g[j + 1], Z_{j+1}).
+  auto enqueue = [&](int j) {
+    double *vj = ls->V.p + (size_t)j * nu;
+    if (mixed) {
+      float *zj = ls->Z32.p + (size_t)j * nu;
+      ls_cpr(ls, vj, nullptr, zj);
+      rs_timed tm(ls, SIM_T_SPMV64);
+      spmv<double, float, double, double>(ls, ls->val.p, zj, (const double *)nullptr, ls->w.p, s);
+    } else {
+      double *zj = ls->Z.p + (size_t)j * nu;
+      ls_cpr(ls, vj, zj, nullptr);
+      ls_spmv64(ls, zj, ls->w.p);
+    }
+    {
+      rs_timed tm(ls, SIM_T_ORTHO);
+      int nv = j + 1;
+      ortho_dots(nu, nv, ls->V.p, ls->w.p, ls->partial.p, 1, nullptr, nblk, s);
+      reduce_parts(nv + 1, nblk, ls->partial.p, h1, nullptr, s);     // h1[nv] = ||w||^2
+      ortho_update(nu, nv, ls->V.p, ls->w.p, h1, ls->partial.p, nullptr, nblk, s);
+      reduce_parts(1, nblk, ls->partial.p, nrm, nullptr, s);
+      k_dgks<<<1, 1, 0, s>>>(h1 + nv, nrm, flag);
+      ortho_dots(nu, nv, ls->V.p, ls->w.p, ls->partial.p, 0, flag, nblk, s);
+      reduce_parts(nv, nblk, ls->partial.p, h2, flag, s);
+      ortho_update(nu, nv, ls->V.p, ls->w.p, h2, ls->partial.p, flag, nblk, s);
+      reduce_parts(1, nblk, ls->partial.p, nrm_b, flag, s);
+      k_arnoldi_col<<<1, 1, 0, s>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, hp_dev + 4 * j);
+      k_scale<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->w.p, hn + 1, ls->V.p + (size_t)(j + 1) * nu);
+      RS_LAUNCHED(11);
+    }
+    RS_CHECK_LAUNCH();
+    RS_CUDA(cudaEventRecord(ls->itev[j & 1], s));
+  };
   for (;;) {
     k_start<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->r.p, beta, ls->V.p, G, m);
     RS_LAUNCHED(1);
     int jend = 0;
+    enqueue(0);
     for (int j = 0; j < m; j++) {
-      double *vj = ls->V.p + (size_t)j * nu;
-      if (mixed) {
-        float *zj = ls->Z32.p + (size_t)j * nu;
-        ls_cpr(ls, vj, nullptr, zj);
-        rs_timed tm(ls, SIM_T_SPMV64);
-        spmv<double, float, double, double>(ls, ls->val.p, zj, (const double *)nullptr, ls->w.p, s);
-      } else {
-        double *zj = ls->Z.p + (size_t)j * nu;
-        ls_cpr(ls, vj, zj, nullptr);
-        ls_spmv64(ls, zj, ls->w.p);
-      }
-      {
-        rs_timed tm(ls, SIM_T_ORTHO);
-        int nv = j + 1;
-        ortho_dots(nu, nv, ls->V.p, ls->w.p, ls->partial.p, 1, nullptr, nblk, s);
-        reduce_parts(nv + 1, nblk, ls->partial.p, h1, nullptr, s);     // h1[nv] = ||w||^2
-        ortho_update(nu, nv, ls->V.p, ls->w.p, h1, ls->partial.p, nullptr, nblk, s);
-        reduce_parts(1, nblk, ls->partial.p, nrm, nullptr, s);
-        k_dgks<<<1, 1, 0, s>>>(h1 + nv, nrm, flag);
-        ortho_dots(nu, nv, ls->V.p, ls->w.p, ls->partial.p, 0, flag, nblk, s);
-        reduce_parts(nv, nblk, ls->partial.p, h2, flag, s);
-        ortho_update(nu, nv, ls->V.p, ls->w.p, h2, ls->partial.p, flag, nblk, s);
-        reduce_parts(1, nblk, ls->partial.p, nrm_b, flag, s);
-        k_arnoldi_col<<<1, 1, 0, s>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, hp_dev);
-        k_scale<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->w.p, hn + 1, ls->V.p + (size_t)(j + 1) * nu);
-        RS_LAUNCHED(11);
-      }
-      RS_CHECK_LAUNCH();
-      RS_CUDA(cudaStreamSynchronize(s));
-      ls->timer_flush();
+      if (j + 1 < m) enqueue(j + 1);
+      RS_CUDA(cudaEventSynchronize(ls->itev[j & 1]));
       if (ls->errw[0]) RS_FAIL(SIM_ERR_TIMEOUT, "RAS apply: bulk copy wait gave up (code %d)", ls->errw[0]);
-      double est = hp[0], hnv = hp[1];
+      double est = hp[4 * j], hnv = hp[4 * j + 1];
       its++;
       jend = j + 1;
-      if (!std::isfinite(est) || !std::isfinite(hnv)) { *its_out = its; *relres = NAN; return 2; }
+      if (!std::isfinite(est) || !std::isfinite(hnv)) {
+        RS_CUDA(cudaStreamSynchronize(s));
+        *its_out = its; *relres = NAN; return 2;
+      }
       if (est <= tol * bn || its >= maxit || hnv == 0.0) break;
     }
     k_hsolve<<<1, 1, 0, s>>>(jend, m, G, yk);
