@@ -193,7 +193,6 @@ struct sim_ls_s {
   dbuf<double> x64a, x64b;      // CPR work (FP64)
   dbuf<float> x32a, x32b, x32c; // CPR work (FP32)
   double *hpin = nullptr;       // pinned host scalars: 4 per Arnoldi step (estimate, h_{j+1,j}, second pass)
-  cudaEvent_t itev[2] = {nullptr, nullptr};   // end of Arnoldi steps j (even / odd)
   int *errw = nullptr, *errw_dev = nullptr;   // device error word (host-mapped)
   bool have_setup = false;
   // timing: events in pairs, the family of each pair in ev_fam

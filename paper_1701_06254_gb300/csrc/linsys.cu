@@ -41,7 +41,6 @@ void sim_ls_s::timer_flush() {
 sim_ls_s::~sim_ls_s() {
   for (auto e : ev) cudaEventDestroy(e);
   if (hpin) cudaFreeHost(hpin);
-  for (auto e : itev) if (e) cudaEventDestroy(e);
   if (errw) cudaFreeHost(errw);
 }
 
@@ -265,7 +264,6 @@ void ls_init(sim_ls_s *ls, int nx, int ny, int nz, int nw, const int *rp, const 
   if (o.precision != SIM_PREC_FP64) { ls->x32b.alloc(nu); ls->x32c.alloc(nu); }
   RS_CUDA(cudaHostAlloc((void **)&ls->hpin, 4 * (ORTHO_MAXV + 2) * sizeof(double), cudaHostAllocMapped));
   for (int k = 0; k < 4 * (ORTHO_MAXV + 2); k++) ls->hpin[k] = 0.0;
-  for (auto &e : ls->itev) RS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   RS_CUDA(cudaHostAlloc((void **)&ls->errw, 16 * sizeof(int), cudaHostAllocMapped));
   for (int k = 0; k < 16; k++) ls->errw[k] = 0;
   RS_CUDA(cudaHostGetDevicePointer((void **)&ls->errw_dev, ls->errw, 0));
@@ -559,10 +557,7 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
   if (beta <= tol * bn) { *its_out = 0; *relres = beta / bn; return 0; }
   int its = 0, rc = 1;
   // One Arnoldi step j (CPR, SpMV, orthogonalisation, Givens); its residual
-  // estimate and h_{j+1,j} land in pinned slot j.  Step j + 1 is enqueued
-  // before the host waits on step j, so the device never idles on the host's
-  // convergence test; when step j converges, step j + 1 has run for nothing
-  // and nothing reads its results (column j + 1 of H, g[j + 1], Z_{j+1}).
+  // estimate and h_{j+1,j} land in pinned slot j
   auto enqueue = [&](int j) {
     double *vj = ls->V.p + (size_t)j * nu;
     if (mixed) {
@@ -592,24 +587,19 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
       RS_LAUNCHED(11);
     }
     RS_CHECK_LAUNCH();
-    RS_CUDA(cudaEventRecord(ls->itev[j & 1], s));
   };
   for (;;) {
     k_start<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->r.p, beta, ls->V.p, G, m);
     RS_LAUNCHED(1);
     int jend = 0;
-    enqueue(0);
     for (int j = 0; j < m; j++) {
-      if (j + 1 < m) enqueue(j + 1);
-      RS_CUDA(cudaEventSynchronize(ls->itev[j & 1]));
+      enqueue(j);
+      RS_CUDA(cudaStreamSynchronize(s));
       if (ls->errw[0]) RS_FAIL(SIM_ERR_TIMEOUT, "RAS apply: bulk copy wait gave up (code %d)", ls->errw[0]);
       double est = hp[4 * j], hnv = hp[4 * j + 1];
       its++;
       jend = j + 1;
-      if (!std::isfinite(est) || !std::isfinite(hnv)) {
-        RS_CUDA(cudaStreamSynchronize(s));
-        *its_out = its; *relres = NAN; return 2;
-      }
+      if (!std::isfinite(est) || !std::isfinite(hnv)) { *its_out = its; *relres = NAN; return 2; }
       if (est <= tol * bn || its >= maxit || hnv == 0.0) break;
     }
     k_hsolve<<<1, 1, 0, s>>>(jend, m, G, yk);
