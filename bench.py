@@ -200,6 +200,8 @@ def measure_variant(R, torch, case, opts, args, ws=None):
         sim.attach_warm_start(ws)
     for _ in range(args.warmup):
         sim.advance(1)
+    if ws is not None:
+        sim.ls.kernel_timer([R.T_WARMSTART, R.T_NETWORK])
     st0 = sim.stats()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -215,7 +217,9 @@ def measure_variant(R, torch, case, opts, args, ws=None):
     out = {"value": case.n * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
            "newton_per_step": dn / args.steps, "fgmres_its_per_newton": (st1["linear_its"] - st0["linear_its"]) / max(1, dn)}
     if ws is not None:
-        out["warm_start"] = {"network_term_kept": st1["ws_used"] - st0["ws_used"],
+        out["warm_start"] = {"ms_per_step": sim.ls.kernel_time(R.T_WARMSTART)[1] / args.steps,
+                             "network_ms_per_step": sim.ls.kernel_time(R.T_NETWORK)[1] / args.steps,
+                             "network_term_kept": st1["ws_used"] - st0["ws_used"],
                              "network_term_dropped": st1["ws_fallback"] - st0["ws_fallback"],
                              "mean_r0_over_b": (st1["ws_r0"] - st0["ws_r0"]) / dl}
     del sim

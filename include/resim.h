@@ -259,7 +259,8 @@ sim_status sim_ls_export(sim_ls_t ls, int what, int index, void *dst, size_t byt
  * milliseconds. */
 enum { SIM_T_NONE = 0, SIM_T_SPMV64 = 1, SIM_T_SPMV_PREC = 2, SIM_T_RAS = 3, SIM_T_VCYCLE = 4,
        SIM_T_ORTHO = 5, SIM_T_ASSEMBLE = 6, SIM_T_AMG_SETUP = 7, SIM_T_RAS_SETUP = 8, SIM_T_DECOUPLE = 9,
-       SIM_T_NFAMILIES = 10 };
+       SIM_T_WARMSTART = 10 /* the whole learned initial guess */, SIM_T_NETWORK = 11 /* its network forward */,
+       SIM_T_NFAMILIES = 12 };
 sim_status sim_kernel_timer(sim_ls_t ls, unsigned mask);
 sim_status sim_kernel_time(sim_ls_t ls, int which, long long *launches, double *ms);
 

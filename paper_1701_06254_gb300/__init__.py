@@ -21,9 +21,9 @@ PREC_FP64, PREC_MIXED, PREC_MIXED_BF16 = 0, 1, 2
 DEC_NONE, DEC_ABF, DEC_QI = 0, 1, 2
 OP_SPMV, OP_RAS, OP_VCYCLE, OP_CPR = 0, 1, 2, 3
 T_NONE, T_SPMV64, T_SPMV_PREC, T_RAS, T_VCYCLE, T_ORTHO, T_ASSEMBLE = 0, 1, 2, 3, 4, 5, 6
-T_AMG_SETUP, T_RAS_SETUP, T_DECOUPLE, T_NFAMILIES = 7, 8, 9, 10
+T_AMG_SETUP, T_RAS_SETUP, T_DECOUPLE, T_WARMSTART, T_NETWORK, T_NFAMILIES = 7, 8, 9, 10, 11, 12
 T_NAMES = {1: "spmv64", 2: "spmv_prec", 3: "ras_apply", 4: "vcycle", 5: "ortho", 6: "assemble",
-           7: "amg_setup", 8: "ras_setup", 9: "decouple"}
+           7: "amg_setup", 8: "ras_setup", 9: "decouple", 10: "warm_start", 11: "network"}
 X_VALS, X_RHS, X_SOLUTION, X_ROWPTR, X_COLS, X_KEY = 0, 1, 2, 3, 4, 5
 X_AMG_SIZES, X_AMG_RP, X_AMG_CI, X_AMG_V, X_AMG_CF, X_AMG_PRP, X_AMG_PCI, X_AMG_PV = 10, 11, 12, 13, 14, 15, 16, 17
 X_RAS_SIZES, X_RAS_EXT, X_RAS_LEVELS = 20, 21, 22

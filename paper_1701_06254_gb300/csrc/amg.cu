@@ -498,6 +498,50 @@ __global__ void k_dense_apply(int n, const double *invT, const T *f, T *x) {
   if (lane == 0) x[i] = (T)s;
 }
 
+// The same four sweeps with L lanes per row (L = 4..32): a row's entries are
+// read by consecutive lanes (coalesced), each lane sums a strided part of the
+// row and the parts are combined with shuffles.  MODE 0: pre-smoothing
+// (x = D^-1 f, r = f - A x); 1: y = A x; 2: t = x + P e; 3: post-smoothing
+// (x = t + D^-1 (f - A t)).
+template <class T, int L, int MODE>
+__global__ void k_vc_lanes(int n, const int *__restrict__ rp, const int *__restrict__ ci, const T *__restrict__ v,
+                           const T *__restrict__ dinv, const T *__restrict__ f, const T *__restrict__ u, T *o1, T *o2) {
+  int g = (blockIdx.x * blockDim.x + threadIdx.x) / L, k = threadIdx.x % L;
+  int i = g < n ? g : n - 1;                       // whole groups stay in the shuffles
+  int q0 = rp[i], q1 = rp[i + 1];
+  T s = 0;
+  for (int q = q0 + k; q < q1; q += L) {
+    int j = ci[q];
+    T xj = MODE == 0 ? f[j] * dinv[j] : u[j];
+    s += v[q] * xj;
+  }
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, L);
+  if (k != 0 || g >= n) return;
+  if (MODE == 0) { o1[i] = f[i] * dinv[i]; o2[i] = f[i] - s; }
+  else if (MODE == 1) o1[i] = s;
+  else if (MODE == 2) o1[i] = f[i] + s;            // f = x (the smoothed iterate), u = e
+  else o1[i] = u[i] + dinv[i] * (f[i] - s);        // u = t
+}
+
+// lanes per row for a level's average row length
+static int lanes_for(long long nnz, int n) {
+  double avg = n ? (double)nnz / n : 0.0;
+  return avg <= 5.0 ? 4 : avg <= 12.0 ? 8 : avg <= 24.0 ? 16 : 32;
+}
+
+template <class T, int MODE>
+static void vc_sweep(int L, int n, const int *rp, const int *ci, const T *v, const T *dinv, const T *f, const T *u,
+                     T *o1, T *o2, cudaStream_t s) {
+  if (n <= 0) return;
+  unsigned g = grid_for((size_t)n * L, 256);
+  if (L == 4) k_vc_lanes<T, 4, MODE><<<g, 256, 0, s>>>(n, rp, ci, v, dinv, f, u, o1, o2);
+  else if (L == 8) k_vc_lanes<T, 8, MODE><<<g, 256, 0, s>>>(n, rp, ci, v, dinv, f, u, o1, o2);
+  else if (L == 16) k_vc_lanes<T, 16, MODE><<<g, 256, 0, s>>>(n, rp, ci, v, dinv, f, u, o1, o2);
+  else k_vc_lanes<T, 32, MODE><<<g, 256, 0, s>>>(n, rp, ci, v, dinv, f, u, o1, o2);
+  RS_LAUNCHED(1);
+}
+
 template <class T> struct lvl_ptrs;
 template <> struct lvl_ptrs<double> {
   static const csr_dev<double> &A(amg_level &L) { return L.A; }
@@ -542,6 +586,15 @@ int amg_vcycle(amg_hier &h, int l, cudaStream_t s) {
   amg_level &Cl = h.lev[l + 1];
   const auto &P = LP::P(L);
   const auto &R = LP::R(L);
+  if (h.lanes) {
+    int la = lanes_for(A.nnz, n), lr = lanes_for(R.nnz, R.n), lp = lanes_for(P.nnz, n);
+    vc_sweep<T, 0>(la, n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), nullptr, LP::x(L), LP::r(L), s);
+    vc_sweep<T, 1>(lr, R.n, R.rp.p, R.ci.p, R.v.p, nullptr, nullptr, LP::r(L), LP::f(Cl), nullptr, s);
+    int k = amg_vcycle<T>(h, l + 1, s);
+    vc_sweep<T, 2>(lp, n, P.rp.p, P.ci.p, P.v.p, nullptr, LP::x(L), LP::x(Cl), LP::t(L), nullptr, s);
+    vc_sweep<T, 3>(la, n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), LP::t(L), LP::x(L), nullptr, s);
+    return k + 4;
+  }
   k_vc_pre<T><<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), LP::x(L), LP::r(L));
   RS_LAUNCHED(1);
   csr_spmv<T>(R.rp.p, R.ci.p, R.v.p, LP::r(L), LP::f(Cl), R.n, s);

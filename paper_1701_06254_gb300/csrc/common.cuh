@@ -118,6 +118,7 @@ struct amg_hier {
   int nlev = 0;
   amg_level lev[32];
   int coarse_dense = 1;
+  int lanes = 0;                // V-cycle sweeps with several lanes per row (else one thread per row)
   dbuf<double> lu;              // dense LU of the coarsest level
   dbuf<int> piv;
   dbuf<int> flag;               // device counters / error words
@@ -197,6 +198,7 @@ struct sim_ls_s {
   bool have_setup = false;
   // timing: events in pairs, the family of each pair in ev_fam
   unsigned timer_mask = 0;
+  int ev_open = 0;               // timer brackets not yet closed
   long long timer_launches[SIM_T_NFAMILIES] = {0};
   double timer_ms[SIM_T_NFAMILIES] = {0};
   std::vector<cudaEvent_t> ev;
@@ -207,9 +209,10 @@ struct sim_ls_s {
 };
 
 struct rs_timed {                       // brackets launches of one kernel family
-  sim_ls_s *ls; bool on; int fam;
+  sim_ls_s *ls; bool on; int fam; int slot = 0;
   rs_timed(sim_ls_s *l, int which);
-  ~rs_timed();
+  ~rs_timed() { stop(); }
+  void stop();                          // end the bracket early (idempotent)
 };
 
 void ls_init(sim_ls_s *ls, int nx, int ny, int nz, int nw, const int *rp, const int *ci,

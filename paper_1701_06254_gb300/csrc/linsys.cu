@@ -14,24 +14,27 @@
 // ------------------------------------------------------------ timers -----
 rs_timed::rs_timed(sim_ls_s *l, int which) : ls(l), on(which > 0 && (l->timer_mask >> which) & 1u), fam(which) {
   if (!on) return;
-  // the pool grows (flushing, which waits on the newest event, only past
-  // 8192 events) so that timing does not make the host wait on the device
-  if (ls->ev_used + 2 > (int)ls->ev.size() && ls->ev.size() >= 8192) ls->timer_flush();
+  // each bracket takes its own pair of events at once, so brackets may nest;
+  // the pool only grows (it is read back when the solve's work is complete)
   if (ls->ev_used + 2 > (int)ls->ev.size()) {
     for (int k = 0; k < 64; k++) { cudaEvent_t e; RS_CUDA(cudaEventCreate(&e)); ls->ev.push_back(e); ls->ev_fam.push_back(0); }
   }
-  ls->ev_fam[ls->ev_used] = fam;
-  RS_CUDA(cudaEventRecord(ls->ev[ls->ev_used], ls->st));
-}
-rs_timed::~rs_timed() {
-  if (!on) return;
-  cudaEventRecord(ls->ev[ls->ev_used + 1], ls->st);
+  slot = ls->ev_used;
   ls->ev_used += 2;
+  ls->ev_open++;
+  ls->ev_fam[slot] = fam;
+  RS_CUDA(cudaEventRecord(ls->ev[slot], ls->st));
+}
+void rs_timed::stop() {
+  if (!on) return;
+  on = false;
+  cudaEventRecord(ls->ev[slot + 1], ls->st);
+  ls->ev_open--;
   ls->timer_launches[fam]++;
 }
 void sim_ls_s::timer_flush() {
-  if (!ev_used) return;
-  cudaEventSynchronize(ev[ev_used - 1]);
+  if (!ev_used || ev_open) return;          // only when every bracket is closed
+  cudaStreamSynchronize(st);
   for (int k = 0; k < ev_used; k += 2) {
     float ms = 0; cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
     timer_ms[ev_fam[k]] += ms;

@@ -481,6 +481,7 @@ static int s_solve(sim_s *h, double eta, double bn, int *its, double *rel) {
   bool learn = h->ws || h->rec;
   bool first = h->first_pending;
   h->first_pending = false;
+  rs_timed tm_ws(ls, h->ws ? SIM_T_WARMSTART : 0);
   if (learn) {
     h->z1.ensure(nu);
     if (ls->o.precision != SIM_PREC_FP64) {
@@ -497,7 +498,10 @@ static int s_solve(sim_s *h, double eta, double bn, int *its, double *rel) {
   }
   if (h->ws) {
     h->dws.ensure(nu); h->u.ensure(3 * (size_t)nu);
-    ws_predict(h->ws, h->nx, h->ny, h->nz, nb, ls->b.p, h->z1.p, h->kx.p, h->s.p, h->yprev.p, h->wsc.p, h->dws.p, st);
+    {
+      rs_timed tm_net(ls, SIM_T_NETWORK);
+      ws_predict(h->ws, h->nx, h->ny, h->nz, nb, ls->b.p, h->z1.p, h->kx.p, h->s.p, h->yprev.p, h->wsc.p, h->dws.p, st);
+    }
     // candidates: 0 = z1, 1 = previous step's first update (if any), then d
     const double *c[3];
     int m = 0;
@@ -535,6 +539,7 @@ static int s_solve(sim_s *h, double eta, double bn, int *its, double *rel) {
       h->stats.ws_r0 += 1.0;
     }
   }
+  tm_ws.stop();
   int rc = ls_solve(ls, eta, its, rel, x0);
   if (rc == 2) return rc;
   if (h->rec)
