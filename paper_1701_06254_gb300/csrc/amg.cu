@@ -524,16 +524,36 @@ __global__ void k_vc_lanes(int n, const int *__restrict__ rp, const int *__restr
   else o1[i] = u[i] + dinv[i] * (f[i] - s);        // u = t
 }
 
-// lanes per row for a level's average row length
+// lanes per row for a matrix's average row length: one thread per row for
+// short rows (their loads already coalesce across neighbouring rows), more
+// lanes as rows grow (a single thread walking a 40-entry row is latency-bound)
 static int lanes_for(long long nnz, int n) {
   double avg = n ? (double)nnz / n : 0.0;
-  return avg <= 5.0 ? 4 : avg <= 12.0 ? 8 : avg <= 24.0 ? 16 : 32;
+  return avg <= 8.0 ? 1 : avg <= 12.0 ? 8 : avg <= 24.0 ? 16 : 32;
 }
+
+template <class T>
+__global__ void k_vc_pre(int n, const int *rp, const int *ci, const T *v, const T *dinv, const T *f, T *x, T *r);
+template <class T>
+__global__ void k_prolong_add(int n, const int *rp, const int *ci, const T *v, const T *e, const T *x, T *t);
+template <class T>
+__global__ void k_vc_post(int n, const int *rp, const int *ci, const T *v, const T *dinv, const T *f, const T *t, T *x);
+template <class T>
+__global__ void k_csr_spmv(int n, const int *rp, const int *ci, const T *v, const T *x, T *y);
 
 template <class T, int MODE>
 static void vc_sweep(int L, int n, const int *rp, const int *ci, const T *v, const T *dinv, const T *f, const T *u,
                      T *o1, T *o2, cudaStream_t s) {
   if (n <= 0) return;
+  if (L == 1) {
+    unsigned g = grid_for(n, 256);
+    if (MODE == 0) k_vc_pre<T><<<g, 256, 0, s>>>(n, rp, ci, v, dinv, f, o1, o2);
+    else if (MODE == 1) k_csr_spmv<T><<<g, 256, 0, s>>>(n, rp, ci, v, u, o1);
+    else if (MODE == 2) k_prolong_add<T><<<g, 256, 0, s>>>(n, rp, ci, v, u, f, o1);
+    else k_vc_post<T><<<g, 256, 0, s>>>(n, rp, ci, v, dinv, f, u, o1);
+    RS_LAUNCHED(1);
+    return;
+  }
   unsigned g = grid_for((size_t)n * L, 256);
   if (L == 4) k_vc_lanes<T, 4, MODE><<<g, 256, 0, s>>>(n, rp, ci, v, dinv, f, u, o1, o2);
   else if (L == 8) k_vc_lanes<T, 8, MODE><<<g, 256, 0, s>>>(n, rp, ci, v, dinv, f, u, o1, o2);
@@ -586,22 +606,12 @@ int amg_vcycle(amg_hier &h, int l, cudaStream_t s) {
   amg_level &Cl = h.lev[l + 1];
   const auto &P = LP::P(L);
   const auto &R = LP::R(L);
-  if (h.lanes) {
-    int la = lanes_for(A.nnz, n), lr = lanes_for(R.nnz, R.n), lp = lanes_for(P.nnz, n);
-    vc_sweep<T, 0>(la, n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), nullptr, LP::x(L), LP::r(L), s);
-    vc_sweep<T, 1>(lr, R.n, R.rp.p, R.ci.p, R.v.p, nullptr, nullptr, LP::r(L), LP::f(Cl), nullptr, s);
-    int k = amg_vcycle<T>(h, l + 1, s);
-    vc_sweep<T, 2>(lp, n, P.rp.p, P.ci.p, P.v.p, nullptr, LP::x(L), LP::x(Cl), LP::t(L), nullptr, s);
-    vc_sweep<T, 3>(la, n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), LP::t(L), LP::x(L), nullptr, s);
-    return k + 4;
-  }
-  k_vc_pre<T><<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), LP::x(L), LP::r(L));
-  RS_LAUNCHED(1);
-  csr_spmv<T>(R.rp.p, R.ci.p, R.v.p, LP::r(L), LP::f(Cl), R.n, s);
+  int la = lanes_for(A.nnz, n), lr = lanes_for(R.nnz, R.n), lp = lanes_for(P.nnz, n);
+  vc_sweep<T, 0>(la, n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), nullptr, LP::x(L), LP::r(L), s);
+  vc_sweep<T, 1>(lr, R.n, R.rp.p, R.ci.p, R.v.p, nullptr, nullptr, LP::r(L), LP::f(Cl), nullptr, s);
   int k = amg_vcycle<T>(h, l + 1, s);
-  k_prolong_add<T><<<grid_for(n, 256), 256, 0, s>>>(n, P.rp.p, P.ci.p, P.v.p, LP::x(Cl), LP::x(L), LP::t(L));
-  k_vc_post<T><<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), LP::t(L), LP::x(L));
-  RS_LAUNCHED(2);
+  vc_sweep<T, 2>(lp, n, P.rp.p, P.ci.p, P.v.p, nullptr, LP::x(L), LP::x(Cl), LP::t(L), nullptr, s);
+  vc_sweep<T, 3>(la, n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), LP::t(L), LP::x(L), nullptr, s);
   return k + 4;
 }
 template int amg_vcycle<double>(amg_hier &, int, cudaStream_t);

@@ -118,7 +118,6 @@ struct amg_hier {
   int nlev = 0;
   amg_level lev[32];
   int coarse_dense = 1;
-  int lanes = 0;                // V-cycle sweeps with several lanes per row (else one thread per row)
   dbuf<double> lu;              // dense LU of the coarsest level
   dbuf<int> piv;
   dbuf<int> flag;               // device counters / error words
