@@ -24,18 +24,29 @@
 //   | Urow u16[m] | Ulev u16[m+1] | cols u16[e] | vals VB[e] | dinv VB[m]
 // every section starts on a 16-byte boundary.
 #define RAS_SMEM_BUDGET (200 * 1024)
-struct blob_layout { int gidx, rp, dg, lrow, llev, urow, ulev, cols, vals, dinv, total; };
+// Packed per-subdomain factors (one "blob", 16-byte aligned sections):
+//   header: m, rows walked by the L sweep, L levels walked, U levels, e, eL
+//   gidx[m]   global row of each local row (bit 0: owned)
+//   llev, ulev  level boundaries (uint16) into lrec / urec
+//   lrec, urec  one uint32 per row of a level: local row (low 16 bits) and
+//               the offset of its first off-diagonal entry (high 16 bits);
+//               a row's entries end where the next record's begin (a
+//               sentinel record closes each list)
+//   cols[e], vals[e]  off-diagonal blocks in the order of the records: the L
+//               sweep's rows first (level by level), then the U sweep's
+//   dinv[m]   inverse diagonal blocks, by local row
+// Sizes use m for every level count, so the layout depends only on (m, e).
+struct blob_layout { int gidx, llev, ulev, lrec, urec, cols, vals, dinv, total; };
+#define BLOB_HDR 32
 __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
 __host__ __device__ inline blob_layout blob_lay(int m, int e, int vb) {
   blob_layout L;
-  int o = 16;
+  int o = BLOB_HDR;
   L.gidx = o; o = al16(o + 4 * m);
-  L.rp = o; o = al16(o + 2 * (m + 1));
-  L.dg = o; o = al16(o + 2 * m);
-  L.lrow = o; o = al16(o + 2 * m);
   L.llev = o; o = al16(o + 2 * (m + 1));
-  L.urow = o; o = al16(o + 2 * m);
   L.ulev = o; o = al16(o + 2 * (m + 1));
+  L.lrec = o; o = al16(o + 4 * (m + 1));
+  L.urec = o; o = al16(o + 4 * (m + 1));
   L.cols = o; o = al16(o + 2 * e);
   L.vals = o; o = al16(o + vb * e);
   L.dinv = o; o = al16(o + vb * m);
@@ -450,46 +461,81 @@ __global__ void k_ras_pack(const int *sub_ptr, const int *lrp_ptr, const int *ex
                            const int *perm, const int *frp, const int *fci, const int *fdiag, const T *fv,
                            const T *dinv, const int *lvl_rows, const int *nlev, const int *lvl_ptr,
                            const long long *blob_off, unsigned char *blobs) {
+  __shared__ int part[129];
   int s = blockIdx.x, base = sub_ptr[s], m = sub_ptr[s + 1] - base, pbase = lrp_ptr[s], fbase = base + s;
   int e = (lrp_ptr[s + 1] - pbase) - m;
   blob_layout Lb = blob_lay(m, e, 4 * (int)sizeof(TB));
   unsigned char *b = blobs + blob_off[s];
   int *gidx = (int *)(b + Lb.gidx);
-  uint16_t *rp = (uint16_t *)(b + Lb.rp), *dg = (uint16_t *)(b + Lb.dg);
-  uint16_t *lrow = (uint16_t *)(b + Lb.lrow), *llev = (uint16_t *)(b + Lb.llev);
-  uint16_t *urow = (uint16_t *)(b + Lb.urow), *ulev = (uint16_t *)(b + Lb.ulev);
+  uint16_t *llev = (uint16_t *)(b + Lb.llev), *ulev = (uint16_t *)(b + Lb.ulev);
+  uint32_t *lrec = (uint32_t *)(b + Lb.lrec), *urec = (uint32_t *)(b + Lb.urec);
   uint16_t *cols = (uint16_t *)(b + Lb.cols);
   TB *vals = (TB *)(b + Lb.vals), *dv = (TB *)(b + Lb.dinv);
   const int *pL = lvl_ptr + 2 * (base + s), *pU = pL + (m + 1);
   const int *rL = lvl_rows + 2 * base, *rU = rL + m;
   int nL = nlev[2 * s], nU = nlev[2 * s + 1];
-  int nLrows = pL[nL] - pL[1 < nL ? 1 : nL];
-  if (threadIdx.x == 0) {
-    int *hdr = (int *)b;
-    hdr[0] = m; hdr[1] = nLrows; hdr[2] = nL > 1 ? nL - 1 : 0; hdr[3] = nU;
+  int l0 = 1 < nL ? pL[1] : 0;                      // level 0 of L has no entries: not walked
+  int nLl = nL > 1 ? nL - 1 : 0, nLrows = nL > 1 ? pL[nL] - l0 : 0;
+  // row i's entries in the factor: [frp, diag) lower, (diag, frp next) upper
+  auto lo0 = [&](int i) { return frp[fbase + i]; };
+  auto dgl = [&](int i) { return fdiag[base + i] - pbase; };
+  auto hi1 = [&](int i) { return frp[fbase + i + 1]; };
+  const int nt = blockDim.x, t = threadIdx.x;
+  // records of the L sweep's rows (level order), entries placed in that order
+  int eL = 0;
+  {
+    int per = (nLrows + nt - 1) / nt, r0 = t * per, r1 = min(nLrows, r0 + per), sum = 0;
+    for (int r = r0; r < r1; r++) { int i = rL[l0 + r]; sum += dgl(i) - lo0(i); }
+    part[t] = sum;
+    __syncthreads();
+    if (t == 0) { int acc = 0; for (int k = 0; k < nt; k++) { int v = part[k]; part[k] = acc; acc += v; } part[nt] = acc; }
+    __syncthreads();
+    int off = part[t];
+    for (int r = r0; r < r1; r++) {
+      int i = rL[l0 + r], q0 = lo0(i), qd = dgl(i);
+      lrec[r] = (uint32_t)i | ((uint32_t)off << 16);
+      for (int q = q0; q < qd; q++, off++) {
+        cols[off] = (uint16_t)fci[pbase + q];
+        const T *src = fv + 4 * (size_t)(pbase + q);
+        for (int u = 0; u < 4; u++) vals[4 * off + u] = to_blob_d<TB>(src[u]);
+      }
+    }
+    eL = part[nt];
+    __syncthreads();
   }
-  for (int pos = threadIdx.x; pos < m; pos += blockDim.x) {
+  // records of the U sweep's rows (level order), after the L entries
+  {
+    int per = (m + nt - 1) / nt, r0 = t * per, r1 = min(m, r0 + per), sum = 0;
+    for (int r = r0; r < r1; r++) { int i = rU[r]; sum += hi1(i) - dgl(i) - 1; }
+    part[t] = sum;
+    __syncthreads();
+    if (t == 0) { int acc = 0; for (int k = 0; k < nt; k++) { int v = part[k]; part[k] = acc; acc += v; } part[nt] = acc; }
+    __syncthreads();
+    int off = eL + part[t];
+    for (int r = r0; r < r1; r++) {
+      int i = rU[r], qd = dgl(i), q1 = hi1(i);
+      urec[r] = (uint32_t)i | ((uint32_t)off << 16);
+      for (int q = qd + 1; q < q1; q++, off++) {
+        cols[off] = (uint16_t)fci[pbase + q];
+        const T *src = fv + 4 * (size_t)(pbase + q);
+        for (int u = 0; u < 4; u++) vals[4 * off + u] = to_blob_d<TB>(src[u]);
+      }
+    }
+  }
+  if (t == 0) {
+    int *hdr = (int *)b;
+    hdr[0] = m; hdr[1] = nLrows; hdr[2] = nLl; hdr[3] = nU; hdr[4] = e; hdr[5] = eL; hdr[6] = 0; hdr[7] = 0;
+    lrec[nLrows] = (uint32_t)eL << 16;               // sentinels: where the last row's entries end
+    urec[m] = (uint32_t)e << 16;
+  }
+  for (int pos = t; pos < m; pos += nt) {
     int x = perm[base + pos];
     gidx[pos] = (ext[base + x] << 1) | (owned[base + x] ? 1 : 0);
-    int r0 = frp[fbase + pos], r1 = frp[fbase + pos + 1], qd = fdiag[base + pos] - pbase;
-    rp[pos] = (uint16_t)(r0 - pos);
-    dg[pos] = (uint16_t)(qd - pos);
-    if (pos == m - 1) rp[m] = (uint16_t)(r1 - m);
-    for (int q = r0; q < r1; q++) {
-      if (q == qd) continue;
-      int j = q - pos - (q > qd ? 1 : 0);
-      cols[j] = (uint16_t)fci[pbase + q];
-      const T *src = fv + 4 * (size_t)(pbase + q);
-      for (int t = 0; t < 4; t++) vals[4 * j + t] = to_blob_d<TB>(src[t]);
-    }
     const T *d = dinv + 4 * (size_t)(base + pos);
-    for (int t = 0; t < 4; t++) dv[4 * pos + t] = to_blob_d<TB>(d[t]);
+    for (int u = 0; u < 4; u++) dv[4 * pos + u] = to_blob_d<TB>(d[u]);
   }
-  int l0 = 1 < nL ? pL[1] : 0;
-  for (int r = threadIdx.x; r < nLrows; r += blockDim.x) lrow[r] = (uint16_t)rL[l0 + r];
-  for (int k = threadIdx.x; k < nL; k += blockDim.x) llev[k] = (uint16_t)(pL[k + 1] - l0);
-  for (int r = threadIdx.x; r < m; r += blockDim.x) urow[r] = (uint16_t)rU[r];
-  for (int k = threadIdx.x; k <= nU; k += blockDim.x) ulev[k] = (uint16_t)pU[k];
+  for (int k = t; k <= nLl; k += nt) llev[k] = (uint16_t)(pL[k + 1] - l0);
+  for (int k = t; k <= nU; k += nt) ulev[k] = (uint16_t)pU[k];
 }
 
 template <class T> struct v2_t;
@@ -550,9 +596,9 @@ __global__ void __launch_bounds__(RAS_BS) k_ras_apply_smem(const long long *blob
   const unsigned char *b = blobs + blob_off[s];
   int total = (int)(blob_off[s + 1] - blob_off[s]);
   unsigned char *sb = reinterpret_cast<unsigned char *>(sm4);
-  // the first section (header + gidx) ends where rp starts; its size depends only on m
+  // the first section (header + gidx) ends where llev starts; its size depends only on m
   int m0 = ((const int *)b)[0];
-  int head = blob_lay(m0, 0, 4 * (int)sizeof(TB)).rp;
+  int head = blob_lay(m0, 0, 4 * (int)sizeof(TB)).llev;
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -570,8 +616,8 @@ __global__ void __launch_bounds__(RAS_BS) k_ras_apply_smem(const long long *blob
   }
   bool ok0 = mbar_wait_bounded(&bar[0], 0, err, 1);
   const int *hdr = (const int *)sb;
-  int m = m0, nLl = hdr[2], nU = hdr[3];
-  const int *gidx = (const int *)(sb + 16);
+  int m = m0, nLl = hdr[2], nU = hdr[3], e = hdr[4];
+  const int *gidx = (const int *)(sb + BLOB_HDR);
   T2 *y = reinterpret_cast<T2 *>(sm4 + total / 16);
   typedef typename v2_t<Tin>::type Tin2;
   const Tin2 *f2 = reinterpret_cast<const Tin2 *>(f);
@@ -590,30 +636,31 @@ __global__ void __launch_bounds__(RAS_BS) k_ras_apply_smem(const long long *blob
   // uniform decision (and the barrier after the gather): on a timeout the
   // error is recorded and nothing is written
   if (!__syncthreads_and(ok0 && ok1)) return;
-  blob_layout Lb = blob_lay(m, 0, 4 * (int)sizeof(TB));
-  const uint16_t *rp = (const uint16_t *)(sb + Lb.rp);
-  Lb = blob_lay(m, rp[m], 4 * (int)sizeof(TB));
-  const uint16_t *dg = (const uint16_t *)(sb + Lb.dg);
-  const uint16_t *lrow = (const uint16_t *)(sb + Lb.lrow), *llev = (const uint16_t *)(sb + Lb.llev);
-  const uint16_t *urow = (const uint16_t *)(sb + Lb.urow), *ulev = (const uint16_t *)(sb + Lb.ulev);
+  blob_layout Lb = blob_lay(m, e, 4 * (int)sizeof(TB));
+  const uint16_t *llev = (const uint16_t *)(sb + Lb.llev), *ulev = (const uint16_t *)(sb + Lb.ulev);
+  const uint32_t *lrec = (const uint32_t *)(sb + Lb.lrec), *urec = (const uint32_t *)(sb + Lb.urec);
   const uint16_t *cols = (const uint16_t *)(sb + Lb.cols);
   const TB *vals = (const TB *)(sb + Lb.vals), *dv = (const TB *)(sb + Lb.dinv);
+  // a level's rows are consecutive records; each record gives the row and
+  // where its entries start, the next record where they end
   for (int k = 0; k < nLl; k++) {
     for (int r = llev[k] + threadIdx.x; r < llev[k + 1]; r += blockDim.x) {
-      int i = lrow[r];
+      uint32_t rec = lrec[r], nxt = lrec[r + 1];
+      int i = rec & 0xffffu;
       T2 a = y[i];
-      row_sub<T, T2, TB>(a, rp[i], dg[i], cols, vals, y);
+      row_sub<T, T2, TB>(a, (int)(rec >> 16), (int)(nxt >> 16), cols, vals, y);
       y[i] = a;
     }
     __syncthreads();
   }
   for (int k = 0; k < nU; k++) {
     for (int r = ulev[k] + threadIdx.x; r < ulev[k + 1]; r += blockDim.x) {
-      int i = urow[r];
+      uint32_t rec = urec[r], nxt = urec[r + 1];
+      int i = rec & 0xffffu;
       T2 a = y[i];
       T d0, d1, d2, d3;
       blk4(dv + 4 * i, d0, d1, d2, d3);
-      row_sub<T, T2, TB>(a, dg[i], rp[i + 1], cols, vals, y);
+      row_sub<T, T2, TB>(a, (int)(rec >> 16), (int)(nxt >> 16), cols, vals, y);
       T2 o;
       o.x = d0 * a.x + d1 * a.y; o.y = d2 * a.x + d3 * a.y;
       y[i] = o;
