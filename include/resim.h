@@ -306,8 +306,9 @@ sim_status sim_batch_autotune(sim_batch_t b, const int *candidates, int n_candid
  * Not in the paper.  The network is a U-Net over 4 resolution levels
  * (3x3x3 convolutions, 32 channels, ReLU, average-pool down, nearest up,
  * skip concatenation) on the simulator's grid; all its contractions run
- * as BF16 tensor-core MMAs with FP32 accumulation, for inference and for
- * training (forward, data and weight gradients, Adam with FP32 master
+ * as BF16 tensor-core MMAs with FP32 accumulation (mma.sync, or tcgen05
+ * with TMEM accumulators for the forward and data-gradient convolutions, see
+ * sim_ws_use_tcgen05), for inference and for training (Adam with FP32 master
  * weights).  It is grid-size agnostic: weights trained on one grid apply to
  * any other.  Inputs per cell (8 channels): the decoupled right-hand side
  * b (pressure and saturation rows, each over its rms over the cells),
@@ -321,6 +322,12 @@ sim_status sim_batch_autotune(sim_batch_t b, const int *candidates, int n_candid
 typedef struct sim_ws_s *sim_ws_t;
 sim_status sim_ws_create(sim_ws_t *out, unsigned long long seed);   /* He-normal weights from seed, zero head */
 void sim_ws_destroy(sim_ws_t ws);
+/* Convolution kernels: on = tcgen05 MMAs with TMEM accumulators for the
+ * forward and data-gradient passes; off (default, faster with the current
+ * per-tap staging) = the mma.sync kernels.  The head layer and the weight
+ * gradients always use mma.sync.  Both compute the same contraction in BF16
+ * with FP32 accumulation. */
+sim_status sim_ws_use_tcgen05(sim_ws_t ws, int on);
 
 /* Parameters in layer order (c00 c01 c10 c11 c20 c21 c30 c31 d20 d21 d10 d11
  * d00 d01 h), each as W[27][Co][Ci] (tap t = (dx+1) + 3 (dy+1) + 9 (dz+1))

@@ -130,6 +130,7 @@ def lib():
             "sim_batch_autotune": (I, [P, C.POINTER(I), I, I, C.POINTER(I), C.POINTER(D)]),
             "sim_ws_create": (I, [C.POINTER(P), C.c_uint64]),
             "sim_ws_destroy": (None, [P]),
+            "sim_ws_use_tcgen05": (I, [P, I]),
             "sim_ws_params": (I, [P, I, P, C.c_size_t, C.POINTER(C.c_size_t)]),
             "sim_ws_set_params": (I, [P, P, C.c_size_t]),
             "sim_ws_forward": (I, [P, I, I, I, P, P]),
@@ -528,6 +529,10 @@ class WarmStart:
 
     def zero_grad(self):
         _check(self._L.sim_ws_zero_grad(self.h))
+
+    def use_tcgen05(self, on=True):
+        """tcgen05 or mma.sync (default) kernels for the forward / data-gradient convolutions."""
+        _check(self._L.sim_ws_use_tcgen05(self.h, 1 if on else 0))
 
     def adam(self, lr):
         _check(self._L.sim_ws_adam(self.h, lr))

@@ -211,6 +211,202 @@ __global__ void __launch_bounds__(128) k_conv(int nx, int ny, int nz, const bf16
     }
 }
 
+// ------------------------------------------ implicit-GEMM conv, tcgen05 ---
+// The same contraction on the 5th-generation tensor cores: per CTA a tile of
+// 128 voxels (M) against CO output channels (N = 32 or 64), K = 27 taps x CI.
+// For every tap the CTA gathers the 128 shifted input rows (cp.async,
+// zero-filled outside the grid) and the tap's CO x CI weights into shared
+// memory in the K-major, no-swizzle core-matrix layout (8 rows x 16 bytes per
+// 128-byte core matrix; the two 8-element halves of a 16-wide K block 128 B
+// apart, 8-row groups 256 B apart), then one thread issues CI/16
+// tcgen05.mma.kind::f16 (BF16 x BF16 -> FP32) into a TMEM accumulator of
+// 128 lanes x CO columns.  Two stages: a stage is refilled once the MMAs that
+// read it have committed to that stage's mbarrier.  The epilogue reads the
+// accumulator with tcgen05.ld (thread = voxel row) and applies bias / ReLU or
+// the data-gradient mask.  Every wait is bounded; on a timeout the kernel
+// records an error and writes nothing.
+__device__ __forceinline__ uint64_t tc_desc(unsigned saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)(128 >> 4) << 16;             // leading byte offset: the K halves of a block
+  d |= (uint64_t)(256 >> 4) << 32;             // stride byte offset: consecutive 8-row groups
+  d |= (uint64_t)1 << 46;                      // descriptor version; no swizzle, base offset 0
+  return d;
+}
+__device__ __forceinline__ uint32_t tc_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, unsigned parity) {
+  for (int it = 0; it < (1 << 24); it++) {
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float *v) {
+  uint32_t r[32];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+               "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                 "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                 "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 32; c++) v[c] = __uint_as_float(r[c]);
+}
+
+template <int CI, int CO>
+struct tc_smem {
+  static constexpr int KB = CI / 16;
+  static constexpr int A_BYTES = KB * (CBM / 8) * 256, B_BYTES = KB * (CO / 8) * 256;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int NS = 4;                   // stages: 2 taps of copies ahead + 2 of MMA slack
+  static constexpr int BYTES = NS * STAGE;
+};
+
+// MODE as for k_conv: 0 forward (bias, ReLU flag), 2 data gradient with mask,
+// 3 data gradient.  Persistent: each CTA walks tiles blockIdx.x, +gridDim.x, ...
+// with one TMEM allocation; taps flow through NS shared-memory stages, a
+// stage being refilled once the MMAs that read it have committed.
+template <int CI, int CO, int MODE>
+__global__ void __launch_bounds__(128) k_conv_tc(int nx, int ny, int nz, const bf16 *__restrict__ X, int ldx, int offx,
+                                                 const bf16 *__restrict__ Wt, const float *__restrict__ bias, int relu,
+                                                 bf16 *out, int ldo, int offo, const bf16 *__restrict__ mask, int ldm,
+                                                 int offm, int *err) {
+  typedef tc_smem<CI, CO> S;
+  constexpr int CH = CI / 8, AJ = CBM * CH / 128, BJ = (CO * CH + 127) / 128, NS = S::NS;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  __shared__ uint64_t bar[NS];
+  __shared__ uint32_t tslot;
+  const int V = nx * ny * nz, nxy = nx * ny, ntile = (V + CBM - 1) / CBM;
+  const int t = threadIdx.x, warp = t >> 5;
+  auto coff = [](int r, int ch) { return (r >> 3) * 256 + (ch & 1) * 128 + (r & 7) * 16; };
+  if (t == 0) {
+    for (int k = 0; k < NS; k++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[k])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)), "n"(CO) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = tslot, idesc = tc_idesc(CO);
+  bool ok = true;
+  long long g0 = 0;                               // taps issued by this CTA before the current tile
+  for (int tile = blockIdx.x; tile < ntile && ok; tile += gridDim.x, g0 += 27) {
+    const int v0 = tile * CBM;
+    int vx[AJ], vy[AJ], vz[AJ], vrow[AJ], vch[AJ];
+#pragma unroll
+    for (int j = 0; j < AJ; j++) {
+      int q = j * 128 + t;
+      vrow[j] = q / CH; vch[j] = q % CH;
+      int v = v0 + vrow[j];
+      if (v < V) { vz[j] = v / nxy; int r = v - vz[j] * nxy; vy[j] = r / nx; vx[j] = r - vy[j] * nx; }
+      else { vx[j] = -1000000; vy[j] = 0; vz[j] = 0; }
+    }
+    // tap u of this tile is global tap g0 + u: stage (g0 + u) % NS, and its
+    // commit is completion number (g0 + u) / NS of that stage's barrier
+    auto load = [&](int u) {
+      long long g = g0 + u;
+      int stage = (int)(g % NS);
+      if (g >= NS) ok = ok && tc_wait(&bar[stage], (unsigned)(((g - NS) / NS) & 1));   // MMAs of g - NS done
+      int dx = u % 3 - 1, dy = (u / 3) % 3 - 1, dz = u / 9 - 1;
+      unsigned char *a = smraw + stage * S::STAGE, *b = a + S::A_BYTES;
+#pragma unroll
+      for (int j = 0; j < AJ; j++) {
+        int x = vx[j] + dx, y = vy[j] + dy, z = vz[j] + dz;
+        bool in = x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz;
+        const bf16 *src = in ? X + ((size_t)(x + nx * (y + ny * z)) * ldx + offx + vch[j] * 8) : X;
+        cp_async16(a + (vch[j] >> 1) * (CBM / 8) * 256 + coff(vrow[j], vch[j]), src, in ? 16 : 0);
+      }
+      const bf16 *w = Wt + (size_t)u * CO * CI;
+#pragma unroll
+      for (int j = 0; j < BJ; j++) {
+        int q = j * 128 + t;
+        if (q < CO * CH) {
+          int o = q / CH, ch = q % CH;
+          cp_async16(b + (ch >> 1) * (CO / 8) * 256 + coff(o, ch), w + o * CI + ch * 8, 16);
+        }
+      }
+    };
+    // copies run LA = NS - 2 taps ahead, so the stage refilled at tap t was
+    // last read by the MMAs of tap t - 2, which have had a whole tap to finish
+    constexpr int LA = NS - 2;
+#pragma unroll 1
+    for (int u = 0; u < LA; u++) { load(u); cp_commit(); }
+    for (int tap = 0; tap < 27; tap++) {
+      int u = tap + LA;
+      if (u < 27) load(u);
+      cp_commit();                                // (possibly empty) group: one per tap
+      cp_wait<LA>();                              // this tap's copies have landed
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      ok = __syncthreads_and(ok);
+      if (t == 0 && ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        long long g = g0 + tap;
+        int stage = (int)(g % NS);
+        unsigned char *a = smraw + stage * S::STAGE, *b = a + S::A_BYTES;
+#pragma unroll
+        for (int kb = 0; kb < S::KB; kb++) {
+          uint64_t da = tc_desc(smem_u32(a + kb * (CBM / 8) * 256)), db = tc_desc(smem_u32(b + kb * (CO / 8) * 256));
+          uint32_t acc = (tap > 0 || kb > 0) ? 1u : 0u;
+          asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                       ::"r"(taddr), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(smem_u32(&bar[stage])) : "memory");
+      }
+    }
+    // the tile's last MMAs have committed
+    {
+      long long g = g0 + 26;
+      ok = ok && tc_wait(&bar[(int)(g % NS)], (unsigned)((g / NS) & 1));
+    }
+    ok = __syncthreads_and(ok);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      int v = v0 + t;                             // TMEM lane = row = thread
+#pragma unroll
+      for (int c0 = 0; c0 < CO; c0 += 32) {
+        float acc[32];
+        tc_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
+        if (v < V) {
+          if (MODE == 0) {
+#pragma unroll
+            for (int c = 0; c < 32; c++) { acc[c] += bias[c0 + c]; if (relu) acc[c] = fmaxf(acc[c], 0.f); }
+          } else if (MODE == 2) {
+            const bf16 *mk = mask + (size_t)v * ldm + offm + c0;
+#pragma unroll
+            for (int c = 0; c < 32; c++) if (!(__bfloat162float(mk[c]) > 0.f)) acc[c] = 0.f;
+          }
+          uint4 pk[4];
+          __nv_bfloat162 *h2 = reinterpret_cast<__nv_bfloat162 *>(pk);
+#pragma unroll
+          for (int c = 0; c < 16; c++) h2[c] = __floats2bfloat162_rn(acc[2 * c], acc[2 * c + 1]);
+          uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)v * ldo + offo + c0);
+#pragma unroll
+          for (int u = 0; u < 4; u++) dst[u] = pk[u];
+        }
+      }
+    }
+    // the accumulator is read before the next tile's first MMA overwrites it
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  if (!ok && t == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "n"(CO) : "memory");
+}
+
 // ------------------------------------------------------ weight gradient ---
 // part[tap][chunk][o][c] = sum over the chunk's voxels v of dZ[v, o] X[v + d(tap), c]
 // (o < CO, c < CI), and for the centre tap bpart[chunk][o] = sum_v dZ[v, o].
@@ -524,6 +720,8 @@ struct sim_ws_s {
   size_t max_samples = 1u << 30;
   unsigned long long seed = 0;
   std::mutex use;                         // one caller at a time (activations are shared)
+  bool tc = false;                        // tcgen05 convolutions (else mma.sync, the faster here)
+  dbuf<int> err;                          // set by a kernel whose bounded wait gave up
   ~sim_ws_s() { if (st) cudaStreamDestroy(st); }
 };
 
@@ -567,12 +765,38 @@ static void conv_launch(sim_ws_s *w, dims d, const bf16 *X, int ldx, int offx, c
   RS_LAUNCHED(1);
 }
 
+template <int CI, int CO, int MODE>
+static void conv_tc_launch(sim_ws_s *w, dims d, const bf16 *X, int ldx, int offx, const bf16 *Wt, const float *bias,
+                           int relu, void *out, int ldo, int offo, const bf16 *mask, int ldm, int offm) {
+  static int per_sm = 0;                      // resident CTAs per SM for this instantiation
+  static int sms = 0;
+  int bytes = tc_smem<CI, CO>::BYTES;
+  if (!per_sm) {
+    RS_CUDA(cudaFuncSetAttribute(k_conv_tc<CI, CO, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    int dev = 0;
+    RS_CUDA(cudaGetDevice(&dev));
+    RS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    RS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<CI, CO, MODE>, 128, bytes));
+    if (per_sm < 1) per_sm = 1;
+  }
+  unsigned tiles = grid_for(d.V(), CBM), cap = (unsigned)(sms * per_sm), grid = tiles < cap ? tiles : cap;
+  k_conv_tc<CI, CO, MODE><<<grid, 128, bytes, w->st>>>(d.nx, d.ny, d.nz, X, ldx, offx, Wt, bias, relu,
+                                                                        reinterpret_cast<bf16 *>(out), ldo, offo, mask,
+                                                                        ldm, offm, w->err.p);
+  RS_LAUNCHED(1);
+}
+
 // forward conv of layer l: in (ld, off) -> out (ldo, offo)
 static void fwd(sim_ws_s *w, int l, dims d, const bf16 *X, int ldx, int offx, void *out, int ldo, int offo) {
   const bf16 *Wt = w->Wf.p + w->wfoff[l];
   const float *b = w->P.p + w->boff[l];
   int ci = LAYERS[l].ci;
   if (l == HEAD) conv_launch<32, 1, 1>(w, d, X, ldx, offx, Wt, b, 0, out, ldo, offo, nullptr, 0, 0);
+  else if (w->tc) {
+    if (ci == 16) conv_tc_launch<16, 32, 0>(w, d, X, ldx, offx, Wt, b, 1, out, ldo, offo, nullptr, 0, 0);
+    else if (ci == 32) conv_tc_launch<32, 32, 0>(w, d, X, ldx, offx, Wt, b, 1, out, ldo, offo, nullptr, 0, 0);
+    else conv_tc_launch<64, 32, 0>(w, d, X, ldx, offx, Wt, b, 1, out, ldo, offo, nullptr, 0, 0);
+  }
   else if (ci == 16) conv_launch<16, 4, 0>(w, d, X, ldx, offx, Wt, b, 1, out, ldo, offo, nullptr, 0, 0);
   else if (ci == 32) conv_launch<32, 4, 0>(w, d, X, ldx, offx, Wt, b, 1, out, ldo, offo, nullptr, 0, 0);
   else conv_launch<64, 4, 0>(w, d, X, ldx, offx, Wt, b, 1, out, ldo, offo, nullptr, 0, 0);
@@ -584,6 +808,19 @@ static void bwd_data(sim_ws_s *w, int l, dims d, const bf16 *dZ, int ldz, int of
                      const bf16 *mask, int ldm, int offm) {
   const bf16 *Wt = w->Wb.p + w->wboff[l];
   int ci = LAYERS[l].ci;
+  if (w->tc && l != C00) {
+    if (l == HEAD) {
+      if (mask) conv_tc_launch<16, 32, 2>(w, d, dZ, ldz, offz, Wt, nullptr, 0, out, ldo, offo, mask, ldm, offm);
+      else conv_tc_launch<16, 32, 3>(w, d, dZ, ldz, offz, Wt, nullptr, 0, out, ldo, offo, mask, ldm, offm);
+    } else if (ci == 64) {
+      if (mask) conv_tc_launch<32, 64, 2>(w, d, dZ, ldz, offz, Wt, nullptr, 0, out, ldo, offo, mask, ldm, offm);
+      else conv_tc_launch<32, 64, 3>(w, d, dZ, ldz, offz, Wt, nullptr, 0, out, ldo, offo, mask, ldm, offm);
+    } else {
+      if (mask) conv_tc_launch<32, 32, 2>(w, d, dZ, ldz, offz, Wt, nullptr, 0, out, ldo, offo, mask, ldm, offm);
+      else conv_tc_launch<32, 32, 3>(w, d, dZ, ldz, offz, Wt, nullptr, 0, out, ldo, offo, mask, ldm, offm);
+    }
+    return;
+  }
   if (l == HEAD) {     // input: dY with 16 channels; output 32
     if (mask) conv_launch<16, 4, 2>(w, d, dZ, ldz, offz, Wt, nullptr, 0, out, ldo, offo, mask, ldm, offm);
     else conv_launch<16, 4, 3>(w, d, dZ, ldz, offz, Wt, nullptr, 0, out, ldo, offo, mask, ldm, offm);
@@ -768,6 +1005,17 @@ static size_t export_count() {
   return n;
 }
 
+// a tensor-core kernel whose bounded wait gave up leaves a flag; report it
+static void check_err(sim_ws_s *w) {
+  int e = 0;
+  RS_CUDA(cudaMemcpyAsync(&e, w->err.p, sizeof(int), cudaMemcpyDeviceToHost, w->st));
+  RS_CUDA(cudaStreamSynchronize(w->st));
+  if (e) {
+    RS_CUDA(cudaMemsetAsync(w->err.p, 0, sizeof(int), w->st));
+    RS_FAIL(SIM_ERR_TIMEOUT, "warm-start network: a tensor-core pipeline wait gave up");
+  }
+}
+
 extern "C" sim_status sim_ws_create(sim_ws_t *out, unsigned long long seed) {
   ABI_BEGIN
   if (!out) RS_FAIL(SIM_ERR_ARG, "sim_ws_create: NULL argument");
@@ -795,6 +1043,8 @@ extern "C" sim_status sim_ws_create(sim_ws_t *out, unsigned long long seed) {
   RS_CUDA(cudaMemsetAsync(w->M.p, 0, w->np * sizeof(float), w->st));
   RS_CUDA(cudaMemsetAsync(w->Vm.p, 0, w->np * sizeof(float), w->st));
   w->lsum.alloc(2);
+  w->err.alloc(1);
+  RS_CUDA(cudaMemsetAsync(w->err.p, 0, sizeof(int), w->st));
   zero_grad(w.get());
   ws_pack(w.get());
   RS_CUDA(cudaStreamSynchronize(w->st));
@@ -803,6 +1053,14 @@ extern "C" sim_status sim_ws_create(sim_ws_t *out, unsigned long long seed) {
 }
 
 extern "C" void sim_ws_destroy(sim_ws_t w) { delete w; }
+
+extern "C" sim_status sim_ws_use_tcgen05(sim_ws_t w, int on) {
+  ABI_BEGIN
+  if (!w) RS_FAIL(SIM_ERR_ARG, "NULL handle");
+  std::lock_guard<std::mutex> guard(w->use);
+  w->tc = on != 0;
+  ABI_END
+}
 
 // which = 0: master parameters, 1: accumulated gradients (divided by the
 // number of samples accumulated, i.e. the mean over the batch)
@@ -867,6 +1125,7 @@ extern "C" sim_status sim_ws_forward(sim_ws_t w, int nx, int ny, int nz, const f
   forward(w);
   RS_CUDA(cudaMemcpyAsync(y, w->Y.p, (size_t)d.V() * COUT_HEAD * sizeof(float), cudaMemcpyDefault, w->st));
   RS_CUDA(cudaStreamSynchronize(w->st));
+  check_err(w);
   ABI_END
 }
 
@@ -888,6 +1147,7 @@ extern "C" sim_status sim_ws_backward(sim_ws_t w, int nx, int ny, int nz, const 
   double l = 0.0;
   RS_CUDA(cudaMemcpyAsync(&l, w->lsum.p, sizeof(double), cudaMemcpyDeviceToHost, w->st));
   RS_CUDA(cudaStreamSynchronize(w->st));
+  check_err(w);
   if (loss) *loss = l;
   ABI_END
 }
@@ -942,6 +1202,7 @@ extern "C" sim_status sim_ws_train(sim_ws_t w, int epochs, int batch, double lr,
     double l = 0.0;
     RS_CUDA(cudaMemcpyAsync(&l, w->lsum.p, sizeof(double), cudaMemcpyDeviceToHost, w->st));
     RS_CUDA(cudaStreamSynchronize(w->st));
+    check_err(w);
     last = l / n;
   }
   if (mean_loss) *mean_loss = last;
@@ -968,6 +1229,7 @@ extern "C" sim_status sim_ws_eval(sim_ws_t w, double *mean_loss) {
   double l = 0.0;
   RS_CUDA(cudaMemcpyAsync(&l, w->lsum.p, sizeof(double), cudaMemcpyDeviceToHost, w->st));
   RS_CUDA(cudaStreamSynchronize(w->st));
+  check_err(w);
   *mean_loss = l / n;
   ABI_END
 }

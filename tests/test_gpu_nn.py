@@ -9,7 +9,9 @@ accumulation order and the occasional rounding-boundary flip they cause:
 the forward output must match to 1e-2 relative (Frobenius), every
 parameter gradient to 3e-2; Adam's update (FP32) to 1e-5.  Without the
 emulated rounding (plain FP64 oracle) the output still agrees to 5e-2.
-Odd grid sizes make every pooling level ragged.
+Odd grid sizes make every pooling level ragged.  The forward and backward
+checks run with the tcgen05 convolution kernels and with the mma.sync ones
+(the default).
 """
 import numpy as np
 import pytest
@@ -39,8 +41,9 @@ def _bf16_weights(P):
     return {k: (nn.bf16_round(W), b) for k, (W, b) in P.items()}
 
 
-def _setup(shape=(5, 7, 9), seed=3):
+def _setup(shape=(5, 7, 9), seed=3, tc=True):
     ws = R.WarmStart(seed=seed)
+    ws.use_tcgen05(tc)
     rng = np.random.default_rng(seed)
     flat = ws.params()
     # non-zero biases so that they are exercised
@@ -59,8 +62,9 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
-def test_forward_matches_oracle():
-    ws, P, F, T = _setup()
+@pytest.mark.parametrize("tc", [True, False], ids=["tcgen05", "mma_sync"])
+def test_forward_matches_oracle(tc):
+    ws, P, F, T = _setup(tc=tc)
     y = ws.forward(F.astype(np.float32))
     yo, _ = nn.forward(_bf16_weights(P), F, rnd=nn.bf16_round)
     assert _rel(y, yo) <= 1e-2, _rel(y, yo)
@@ -68,8 +72,9 @@ def test_forward_matches_oracle():
     assert _rel(y, yp) <= 5e-2, _rel(y, yp)
 
 
-def test_backward_matches_oracle():
-    ws, P, F, T = _setup(shape=(6, 5, 11), seed=4)
+@pytest.mark.parametrize("tc", [True, False], ids=["tcgen05", "mma_sync"])
+def test_backward_matches_oracle(tc):
+    ws, P, F, T = _setup(shape=(6, 5, 11), seed=4, tc=tc)
     ws.zero_grad()
     loss = ws.backward(F.astype(np.float32), T.astype(np.float32))
     g = _to_dict(ws.params(which=1))
@@ -187,3 +192,20 @@ def test_warm_start_iteration_savings():
           f"warm start {per_ws:.2f} ({learned['linear_solves']} solves, mean ||r0||/||b|| "
           f"{learned['ws_r0'] / learned['linear_solves']:.3f}, network term kept in {learned['ws_used']})")
     assert per_ws <= per_plain, (per_ws, per_plain)
+
+
+def test_tcgen05_and_mma_sync_agree_on_a_large_grid():
+    """Several 128-voxel tiles with a ragged last one: the two kernel
+    families give the same network output to BF16 rounding."""
+    rng = np.random.default_rng(9)
+    F = nn.bf16_round(rng.standard_normal((6, 23, 37, 8))).astype(np.float32)
+    a = R.WarmStart(seed=21)
+    P = _to_dict(a.params())
+    for k in P:
+        P[k] = (P[k][0], 0.05 * rng.standard_normal(P[k][1].shape))
+    a.set_params(_to_flat(P).astype(np.float32))
+    a.use_tcgen05(True)
+    ya = a.forward(F)
+    a.use_tcgen05(False)
+    yb = a.forward(F)
+    assert _rel(ya, yb) <= 1e-2, _rel(ya, yb)
