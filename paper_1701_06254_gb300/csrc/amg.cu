@@ -98,6 +98,57 @@ __global__ void k_pmis_update(int n, const int *rp, const int *ci, const uint8_t
   atomicAdd(undecided, 1);
 }
 
+// The same two PMIS steps with L lanes per row (coarse levels have rows of
+// 20-40 entries, which one thread would walk serially): the lanes split the
+// row's entries and combine their verdicts with ballots, so the outcome is
+// the same boolean as the one-thread version.
+template <int L>
+__global__ void k_pmis_select_lanes(int n, const int *rp, const int *ci, const uint8_t *S, const int *tpos,
+                                    const double *w, const int8_t *cf, int8_t *newc, const int *skip) {
+  if (skip && *skip == 0) return;
+  int g = (blockIdx.x * blockDim.x + threadIdx.x) / L, k = threadIdx.x % L;
+  int i = g < n ? g : n - 1;
+  bool cand = cf[i] == 0, beaten = false;
+  if (cand) {
+    double wi = w[i];
+    for (int q = rp[i] + k; q < rp[i + 1]; q += L) {
+      int j = ci[q];
+      if (j == i || !(S[q] || S[tpos[q]]) || cf[j] != 0) continue;
+      double wj = w[j];
+      if (wj > wi || (wj == wi && j < i)) { beaten = true; break; }
+    }
+  }
+  unsigned lanes = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) / L * L));
+  bool any = __ballot_sync(0xffffffffu, beaten) & lanes;
+  if (k == 0 && g < n) newc[i] = (cand && !any) ? 1 : 0;
+}
+
+template <int L>
+__global__ void k_pmis_update_lanes(int n, const int *rp, const int *ci, const uint8_t *S, int8_t *cf,
+                                    const int8_t *newc, int *undecided, const int *skip) {
+  if (skip && *skip == 0) return;
+  int g = (blockIdx.x * blockDim.x + threadIdx.x) / L, k = threadIdx.x % L;
+  int i = g < n ? g : n - 1;
+  bool open = cf[i] == 0 && !newc[i], hit = false;
+  if (open)
+    for (int q = rp[i] + k; q < rp[i + 1]; q += L) {
+      int j = ci[q];
+      if (S[q] && (cf[j] == 1 || newc[j])) { hit = true; break; }
+    }
+  unsigned lanes = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) / L * L));
+  bool any = __ballot_sync(0xffffffffu, hit) & lanes;
+  if (k != 0 || g >= n || cf[i] != 0) return;
+  if (newc[i]) { cf[i] = 1; return; }
+  if (any) { cf[i] = -1; return; }
+  atomicAdd(undecided, 1);
+}
+
+// lanes per row for the PMIS steps: one thread for short rows
+static int pmis_lanes(long long nnz, int n) {
+  double avg = n ? (double)nnz / n : 0.0;
+  return avg <= 8.0 ? 1 : avg <= 12.0 ? 8 : avg <= 24.0 ? 16 : 32;
+}
+
 __global__ void k_cflag(int n, const int8_t *cf, int *flag) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) flag[i] = cf[i] == 1;
@@ -381,12 +432,26 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
     // cnt[r] > 0, so the rounds past the last one do nothing
     const int PMIS_BATCH = 4;
     int *cnt = h.flag.p + 4;
+    const int lanes = pmis_lanes(L.A.nnz, n);
     for (int done = 0;;) {
       for (int r = done; r < done + PMIS_BATCH; r++) {
-        k_pmis_select<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, h.hashw.p,
-                                                       L.cf.p, h.newc.p, cnt + r);
-        k_pmis_update<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, h.newc.p,
-                                                       cnt + r + 1, cnt + r);
+        if (lanes == 1) {
+          k_pmis_select<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, h.hashw.p,
+                                                         L.cf.p, h.newc.p, cnt + r);
+          k_pmis_update<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, h.newc.p,
+                                                         cnt + r + 1, cnt + r);
+        } else {
+          unsigned gl = grid_for((size_t)n * lanes, 128);
+#define PMIS_LANES(LL)                                                                                          \
+          if (lanes == LL) {                                                                                    \
+            k_pmis_select_lanes<LL><<<gl, 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, h.hashw.p,  \
+                                                       L.cf.p, h.newc.p, cnt + r);                              \
+            k_pmis_update_lanes<LL><<<gl, 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, h.newc.p,     \
+                                                       cnt + r + 1, cnt + r);                                   \
+          }
+          PMIS_LANES(8) PMIS_LANES(16) PMIS_LANES(32)
+#undef PMIS_LANES
+        }
       }
       RS_LAUNCHED(2 * PMIS_BATCH);
       RS_CHECK_LAUNCH();

@@ -236,41 +236,34 @@ __global__ void k_ras_pattern(const int *sub_ptr, const int *lrp_ptr, const int 
 // level sets of the L and U factors; rows of a level in ascending position
 __global__ void k_ras_levels(const int *sub_ptr, const int *lrp_ptr, const int *frp, const int *fci, int *lvl,
                              int *lvl_rows, int *nlev, int *lvl_ptr) {
+  // the L levels (forward over the rows) and the U levels (backward) are
+  // independent: thread 0 walks one, thread 32 (another warp) the other
   int s = blockIdx.x, base = sub_ptr[s], m = sub_ptr[s + 1] - base, pbase = lrp_ptr[s], fbase = base + s;
-  if (threadIdx.x != 0) return;
-  int *L = lvl + 2 * base, *U = L + m;
-  int nL = 0, nU = 0;
-  for (int i = 0; i < m; i++) {
+  bool upper;
+  if (threadIdx.x == 0) upper = false;
+  else if (threadIdx.x == 32) upper = true;
+  else return;
+  int *Lv = lvl + 2 * base + (upper ? m : 0);
+  int nl = 0;
+  for (int t = 0; t < m; t++) {
+    int i = upper ? m - 1 - t : t;
     int lv = 0;
     for (int q = pbase + frp[fbase + i]; q < pbase + frp[fbase + i + 1]; q++) {
       int c = fci[q];
-      if (c < i && L[c] + 1 > lv) lv = L[c] + 1;
+      if ((upper ? c > i : c < i) && Lv[c] + 1 > lv) lv = Lv[c] + 1;
     }
-    L[i] = lv; if (lv + 1 > nL) nL = lv + 1;
+    Lv[i] = lv; if (lv + 1 > nl) nl = lv + 1;
   }
-  for (int i = m - 1; i >= 0; i--) {
-    int lv = 0;
-    for (int q = pbase + frp[fbase + i]; q < pbase + frp[fbase + i + 1]; q++) {
-      int c = fci[q];
-      if (c > i && U[c] + 1 > lv) lv = U[c] + 1;
-    }
-    U[i] = lv; if (lv + 1 > nU) nU = lv + 1;
-  }
-  nlev[2 * s] = nL; nlev[2 * s + 1] = nU;
-  int *pL = lvl_ptr + 2 * (base + s), *pU = pL + (m + 1);
-  int *rL = lvl_rows + 2 * base, *rU = rL + m;
-  for (int l = 0; l <= nL; l++) pL[l] = 0;
-  for (int l = 0; l <= nU; l++) pU[l] = 0;
-  for (int i = 0; i < m; i++) { pL[L[i] + 1]++; pU[U[i] + 1]++; }
-  for (int l = 0; l < nL; l++) pL[l + 1] += pL[l];
-  for (int l = 0; l < nU; l++) pU[l + 1] += pU[l];
+  nlev[2 * s + (upper ? 1 : 0)] = nl;
+  int *pp = lvl_ptr + 2 * (base + s) + (upper ? m + 1 : 0);
+  int *rr = lvl_rows + 2 * base + (upper ? m : 0);
+  for (int l = 0; l <= nl; l++) pp[l] = 0;
+  for (int i = 0; i < m; i++) pp[Lv[i] + 1]++;
+  for (int l = 0; l < nl; l++) pp[l + 1] += pp[l];
   // fill: rows in ascending position within a level (counts reused as cursors)
-  for (int i = 0; i < m; i++) rL[pL[L[i]]++] = i;
-  for (int i = 0; i < m; i++) rU[pU[U[i]]++] = i;
-  for (int l = nL; l > 0; l--) pL[l] = pL[l - 1];
-  pL[0] = 0;
-  for (int l = nU; l > 0; l--) pU[l] = pU[l - 1];
-  pU[0] = 0;
+  for (int i = 0; i < m; i++) rr[pp[Lv[i]]++] = i;
+  for (int l = nl; l > 0; l--) pp[l] = pp[l - 1];
+  pp[0] = 0;
 }
 
 template <class T> __device__ __forceinline__ void inv2x2(const T *M, T *I) {
@@ -342,7 +335,7 @@ void ras_setup(sim_ls_s *ls) {
   fsrc.ensure(R.lci.n);
   k_ras_pattern<<<R.nsub, 256, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.lrp.p, R.lrlen.p, R.lci.p, R.lsrc.p, R.perm.p,
                                        R.ipos.p, R.frp.p, R.fci.p, R.fdiag.p, fsrc.p);
-  k_ras_levels<<<R.nsub, 32, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.frp.p, R.fci.p, R.lvl.p, R.lvl_rows.p, R.nlev.p,
+  k_ras_levels<<<R.nsub, 64, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.frp.p, R.fci.p, R.lvl.p, R.lvl_rows.p, R.nlev.p,
                                      R.lvl_ptr.p);
   if (ls->o.precision != SIM_PREC_FP64)
     k_ras_factor<float><<<R.nsub, 128, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.frp.p, R.fci.p, R.fdiag.p, fsrc.p,
