@@ -312,7 +312,7 @@ void ls_setup(sim_ls_s *ls) {
 // Each block owns a fixed chunk of ORTHO_CH rows and keeps its slice of w in
 // shared memory.  Basis vectors are streamed vector-outer, rows-inner, so
 // loads are coalesced and independent.
-#define ORTHO_CH 4096
+#define ORTHO_CH 2048
 static int ortho_blocks(int nu) { return (nu + ORTHO_CH - 1) / ORTHO_CH; }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
