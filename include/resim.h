@@ -264,6 +264,18 @@ enum { SIM_T_NONE = 0, SIM_T_SPMV64 = 1, SIM_T_SPMV_PREC = 2, SIM_T_RAS = 3, SIM
 sim_status sim_kernel_timer(sim_ls_t ls, unsigned mask);
 sim_status sim_kernel_time(sim_ls_t ls, int which, long long *launches, double *ms);
 
+/* Launch mode of the FGMRES Arnoldi step (Algorithm 1's inner loop: CPR
+ * application, SpMV, Gram-Schmidt, Givens update).  The paper has no
+ * counterpart: it concerns only how the kernels are issued.  on = 1 (the
+ * default): each step is one replay of a CUDA graph recorded at the first
+ * solve after a setup, whose kernels read the step index from device memory;
+ * on = 0: every kernel is launched on its own.  Both issue the same kernels
+ * on the same data, so results are bit-identical; kernel timers work in both
+ * (graph brackets are event nodes).  Subdomains too large for the shared-
+ * memory RAS kernel always use separate launches.  Errors: SIM_ERR_ARG for a
+ * NULL handle. */
+sim_status sim_ls_step_graph(sim_ls_t ls, int on);
+
 /* ---- ensembles: many independent models advanced together ----
  *
  * Not in the paper, whose experiments run one model at a time.  A batch

@@ -120,6 +120,7 @@ def lib():
             "sim_ls_residual_norm": (I, [P, P, C.POINTER(D)]),
             "sim_ls_residual_norm_noalloc": (I, [P, P, P]),
             "sim_kernel_timer": (I, [P, C.c_uint]),
+            "sim_ls_step_graph": (I, [P, C.c_int]),
             "sim_kernel_time": (I, [P, I, C.POINTER(C.c_longlong), C.POINTER(D)]),
             "sim_batch_create": (I, [C.POINTER(P), I, C.POINTER(Grid), C.POINTER(Rock), C.POINTER(Fluid),
                                      C.POINTER(C.POINTER(Well)), C.POINTER(I), C.POINTER(Options), I]),
@@ -291,6 +292,11 @@ class LinearSystem:
         for f in families:
             mask |= 1 << f
         _check(self._L.sim_kernel_timer(self.h, mask))
+
+    def step_graph(self, on):
+        """Issue each Arnoldi step as one CUDA graph replay (True, the
+        default) or as separate kernel launches (False); same results."""
+        _check(self._L.sim_ls_step_graph(self.h, 1 if on else 0))
 
     def kernel_time(self, which):
         n, ms = C.c_longlong(), C.c_double()

@@ -193,6 +193,26 @@ struct sim_ls_s {
   dbuf<double> x64a, x64b;      // CPR work (FP64)
   dbuf<float> x32a, x32b, x32c; // CPR work (FP32)
   double *hpin = nullptr;       // pinned host scalars: 4 per Arnoldi step (estimate, h_{j+1,j}, second pass)
+  // one Arnoldi step as a CUDA graph (recorded after each setup)
+  bool graph_on = true;
+  cudaGraphExec_t it_exec = nullptr;
+  long long it_launches = 0;
+  const void *it_sig[9] = {};   // buffers, restart length and precision it was recorded with
+  cudaStream_t cap = nullptr;
+  bool capturing = false;
+  dbuf<int> jd;                 // the step index the graph's kernels read
+  dbuf<double> vcur, zcur64;
+  dbuf<float> zcur32;
+  // timer brackets recorded inside the graph (event nodes): pairs of events
+  // and the family of each pair, read back after every replay
+  std::vector<cudaEvent_t> gev;
+  std::vector<int> gev_fam;
+  void drop_graph() {
+    if (it_exec) { cudaGraphExecDestroy(it_exec); it_exec = nullptr; }
+    for (auto e : gev) cudaEventDestroy(e);
+    gev.clear(); gev_fam.clear();
+  }
+  void graph_timers();          // after a replay has completed
   int *errw = nullptr, *errw_dev = nullptr;   // device error word (host-mapped)
   bool have_setup = false;
   // timing: events in pairs, the family of each pair in ev_fam
@@ -208,7 +228,7 @@ struct sim_ls_s {
 };
 
 struct rs_timed {                       // brackets launches of one kernel family
-  sim_ls_s *ls; bool on; int fam; int slot = 0;
+  sim_ls_s *ls; bool on; int fam; int slot = 0; bool in_graph = false;
   rs_timed(sim_ls_s *l, int which);
   ~rs_timed() { stop(); }
   void stop();                          // end the bracket early (idempotent)

@@ -10,10 +10,21 @@
 #define ORTHO_MAXV 64            // FGMRES restart length limit (m + 1 basis vectors)
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 // ------------------------------------------------------------ timers -----
 rs_timed::rs_timed(sim_ls_s *l, int which) : ls(l), on(which > 0 && (l->timer_mask >> which) & 1u), fam(which) {
   if (!on) return;
+  if (ls->capturing) {          // recorded into the Arnoldi-step graph as event nodes
+    in_graph = true;
+    cudaEvent_t a, b;
+    RS_CUDA(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); RS_CUDA(cudaGetLastError()); }
+    slot = (int)ls->gev.size();
+    ls->gev.push_back(a); ls->gev.push_back(b); ls->gev_fam.push_back(fam);
+    RS_CUDA(cudaEventRecordWithFlags(a, ls->st, cudaEventRecordExternal));
+    return;
+  }
   // each bracket takes its own pair of events at once, so brackets may nest;
   // the pool only grows (it is read back when the solve's work is complete)
   if (ls->ev_used + 2 > (int)ls->ev.size()) {
@@ -28,6 +39,7 @@ rs_timed::rs_timed(sim_ls_s *l, int which) : ls(l), on(which > 0 && (l->timer_ma
 void rs_timed::stop() {
   if (!on) return;
   on = false;
+  if (in_graph) { cudaEventRecordWithFlags(ls->gev[slot + 1], ls->st, cudaEventRecordExternal); return; }
   cudaEventRecord(ls->ev[slot + 1], ls->st);
   ls->ev_open--;
   ls->timer_launches[fam]++;
@@ -41,7 +53,17 @@ void sim_ls_s::timer_flush() {
   }
   ev_used = 0;
 }
+void sim_ls_s::graph_timers() {
+  for (size_t k = 0; k + 1 < gev.size(); k += 2) {
+    float ms = 0;
+    RS_CUDA(cudaEventElapsedTime(&ms, gev[k], gev[k + 1]));
+    timer_ms[gev_fam[k / 2]] += ms;
+    timer_launches[gev_fam[k / 2]]++;
+  }
+}
 sim_ls_s::~sim_ls_s() {
+  drop_graph();
+  if (cap) cudaStreamDestroy(cap);
   for (auto e : ev) cudaEventDestroy(e);
   if (hpin) cudaFreeHost(hpin);
   if (errw) cudaFreeHost(errw);
@@ -210,7 +232,7 @@ void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32) {
     { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, double, float>(ls, ls->val32.p, z, v, r, s); }  // 2
     k_gather_p<float, float><<<grid_for(n, 256), 256, 0, s>>>(n, r, L0.f32.p);
     RS_LAUNCHED(1);
-    { rs_timed tm(ls, SIM_T_VCYCLE); amg_vcycle_graph<float>(ls->amg, s); }               // 3
+    { rs_timed tm(ls, SIM_T_VCYCLE); if (ls->capturing) amg_vcycle<float>(ls->amg, 0, s); else amg_vcycle_graph<float>(ls->amg, s); }  // 3
     k_add_p<float><<<grid_for(n, 256), 256, 0, s>>>(n, L0.x32.p, z);
     RS_LAUNCHED(1);
     { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, double, float>(ls, ls->val32.p, z, v, r, s); }  // 4
@@ -221,7 +243,7 @@ void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32) {
     { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<double, double, double, double>(ls, ls->val.p, z, v, r, s); }
     k_gather_p<double, double><<<grid_for(n, 256), 256, 0, s>>>(n, r, L0.f.p);
     RS_LAUNCHED(1);
-    { rs_timed tm(ls, SIM_T_VCYCLE); amg_vcycle_graph<double>(ls->amg, s); }
+    { rs_timed tm(ls, SIM_T_VCYCLE); if (ls->capturing) amg_vcycle<double>(ls->amg, 0, s); else amg_vcycle_graph<double>(ls->amg, s); }
     k_add_p<double><<<grid_for(n, 256), 256, 0, s>>>(n, L0.x.p, z);
     RS_LAUNCHED(1);
     { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<double, double, double, double>(ls, ls->val.p, z, v, r, s); }
@@ -275,6 +297,7 @@ void ls_init(sim_ls_s *ls, int nx, int ny, int nz, int nw, const int *rp, const 
 
 void ls_setup(sim_ls_s *ls) {
   cudaStream_t s = ls->st;
+  ls->drop_graph();                         // buffers of the hierarchy may move
   float *v32 = ls->o.precision != SIM_PREC_FP64 ? ls->val32.p : nullptr;
   unsigned g = grid_for(ls->nb, 128);
   {
@@ -361,8 +384,9 @@ __device__ __forceinline__ double warp_sum8_d(const double *a, int lane) {
 // part[k][b] = V_k . w over the block's rows (k < nv); with_norm: part[nv][b] = w . w
 __global__ void __launch_bounds__(ORTHO_BS) k_ortho_dots(int nu, int nv, const double *__restrict__ V,
                                                          const double *__restrict__ w, double *part, int with_norm,
-                                                         const int *cond) {
+                                                         const int *cond, const int *jd) {
   if (cond && *cond == 0) return;
+  if (jd) nv = *jd + 1;                        // graph replay: the step index lives on the device
   extern __shared__ double ws[];             // ORTHO_CH doubles (dynamic)
   __shared__ double red[2][ORTHO_BS / 32][ORTHO_G];
   int nblk = gridDim.x, i0 = blockIdx.x * ORTHO_CH, len = min(ORTHO_CH, nu - i0);
@@ -399,8 +423,9 @@ __global__ void __launch_bounds__(ORTHO_BS) k_ortho_dots(int nu, int nv, const d
 // w -= sum_k h_k V_k over the block's rows, then part[0][b] = ||w||^2
 __global__ void __launch_bounds__(ORTHO_BS) k_ortho_update(int nu, int nv, const double *__restrict__ V, double *w,
                                                            const double *__restrict__ h, double *part,
-                                                           const int *cond) {
+                                                           const int *cond, const int *jd) {
   if (cond && *cond == 0) return;
+  if (jd) nv = *jd + 1;
   extern __shared__ double ws[];
   __shared__ double sred[ORTHO_BS / 32];
   int i0 = blockIdx.x * ORTHO_CH, len = min(ORTHO_CH, nu - i0);
@@ -445,20 +470,22 @@ static void ortho_attr() {
   done = true;
 }
 static void ortho_dots(int nu, int nv, const double *V, const double *w, double *part, int with_norm, const int *cond,
-                       int nblk, cudaStream_t s) {
+                       int nblk, cudaStream_t s, const int *jd = nullptr) {
   ortho_attr();
-  k_ortho_dots<<<nblk, ORTHO_BS, ORTHO_CH * 8, s>>>(nu, nv, V, w, part, with_norm, cond);
+  k_ortho_dots<<<nblk, ORTHO_BS, ORTHO_CH * 8, s>>>(nu, nv, V, w, part, with_norm, cond, jd);
 }
 static void ortho_update(int nu, int nv, const double *V, double *w, const double *h, double *part, const int *cond,
-                         int nblk, cudaStream_t s) {
+                         int nblk, cudaStream_t s, const int *jd = nullptr) {
   ortho_attr();
-  k_ortho_update<<<nblk, ORTHO_BS, ORTHO_CH * 8, s>>>(nu, nv, V, w, h, part, cond);
+  k_ortho_update<<<nblk, ORTHO_BS, ORTHO_CH * 8, s>>>(nu, nv, V, w, h, part, cond, jd);
 }
 
 // out[k] = sum over blocks of part[k][*]: one warp per k, lanes add a fixed
 // stride of the partials, then a fixed shuffle tree (deterministic)
-__global__ void k_reduce_parts(int nv, int nblk, const double *part, double *out, const int *cond) {
+__global__ void k_reduce_parts(int nv, int nblk, const double *part, double *out, const int *cond, const int *jd,
+                               int extra) {
   if (cond && *cond == 0) return;
+  if (jd) nv = *jd + 1 + extra;
   int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (k >= nv) return;
   double t = 0;
@@ -466,11 +493,14 @@ __global__ void k_reduce_parts(int nv, int nblk, const double *part, double *out
   t = warp_sum_d(t);
   if (lane == 0) out[k] = t;
 }
-static void reduce_parts(int nv, int nblk, const double *part, double *out, const int *cond, cudaStream_t s) {
-  k_reduce_parts<<<(nv + 3) / 4, 128, 0, s>>>(nv, nblk, part, out, cond);
+static void reduce_parts(int nv, int nblk, const double *part, double *out, const int *cond, cudaStream_t s,
+                         const int *jd = nullptr, int extra = 0) {
+  int cover = jd ? ORTHO_MAXV + 1 : nv;        // graph replay: enough warps for any step
+  k_reduce_parts<<<(cover + 3) / 4, 128, 0, s>>>(nv, nblk, part, out, cond, jd, extra);
 }
 // flag = ||w_1||^2 < 1e-4 ||w||^2 (the first pass kept less than 1% of w)
-__global__ void k_dgks(const double *w2_before, const double *w2_after, int *flag) {
+__global__ void k_dgks(const double *w2_before, const double *w2_after, int *flag, const double *h1, const int *jd) {
+  if (jd) w2_before = h1 + *jd + 1;            // ||w||^2 follows the step's dot products
   *flag = (*w2_after < 1e-4 * *w2_before) ? 1 : 0;
 }
 
@@ -478,7 +508,9 @@ __global__ void k_dgks(const double *w2_before, const double *w2_after, int *fla
 // rotations, a new one, and the residual estimate |g_{j+1}|.
 // G layout: [0..m*(m+1)) H column-major (m+1 per column), cs[m], sn[m], g[m+1]
 __global__ void k_arnoldi_col(int j, int m, const double *h1, const double *h2, const double *nrm_a,
-                              const double *nrm_b, const int *flag, double *G, double *hnorm, volatile double *host) {
+                              const double *nrm_b, const int *flag, double *G, double *hnorm, volatile double *host,
+                              const int *jd) {
+  if (jd) { j = *jd; host += 4 * j; }          // graph replay: pinned slot j
   double *H = G, *cs = G + (size_t)m * (m + 1), *sn = cs + m, *g = sn + m;
   double *col = H + (size_t)j * (m + 1);
   bool re = *flag != 0;
@@ -500,10 +532,23 @@ __global__ void k_arnoldi_col(int j, int m, const double *h1, const double *h2, 
   host[1] = hn;
   host[2] = re ? 1.0 : 0.0;
 }
-__global__ void k_scale(int nu, const double *w, const double *inv_hn, double *v) {
+__global__ void k_scale(int nu, const double *w, const double *inv_hn, double *v, const int *jd) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (jd) v += (size_t)(*jd + 1) * nu;     // graph replay: v is the basis, the target is V_{j+1}
   if (i < nu) v[i] = w[i] * *inv_hn;       // 1 / h_{j+1,j} formed once by k_arnoldi_col
 }
+// graph replay helpers: the step's basis vector in and preconditioned vector out
+// of fixed buffers, and the step counter
+__global__ void k_basis_get(int nu, const double *V, const int *jd, double *vcur) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nu) vcur[i] = V[(size_t)*jd * nu + i];
+}
+template <class T>
+__global__ void k_basis_put(int nu, const T *zcur, T *Z, const int *jd) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nu) Z[(size_t)*jd * nu + i] = zcur[i];
+}
+__global__ void k_step_inc(int *jd) { (*jd)++; }
 __global__ void k_start(int nu, const double *r, double beta, double *v0, double *G, int m) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nu) v0[i] = r[i] * (1.0 / beta);
@@ -580,24 +625,117 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
       reduce_parts(nv + 1, nblk, ls->partial.p, h1, nullptr, s);     // h1[nv] = ||w||^2
       ortho_update(nu, nv, ls->V.p, ls->w.p, h1, ls->partial.p, nullptr, nblk, s);
       reduce_parts(1, nblk, ls->partial.p, nrm, nullptr, s);
-      k_dgks<<<1, 1, 0, s>>>(h1 + nv, nrm, flag);
+      k_dgks<<<1, 1, 0, s>>>(h1 + nv, nrm, flag, nullptr, nullptr);
       ortho_dots(nu, nv, ls->V.p, ls->w.p, ls->partial.p, 0, flag, nblk, s);
       reduce_parts(nv, nblk, ls->partial.p, h2, flag, s);
       ortho_update(nu, nv, ls->V.p, ls->w.p, h2, ls->partial.p, flag, nblk, s);
       reduce_parts(1, nblk, ls->partial.p, nrm_b, flag, s);
-      k_arnoldi_col<<<1, 1, 0, s>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, hp_dev + 4 * j);
-      k_scale<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->w.p, hn + 1, ls->V.p + (size_t)(j + 1) * nu);
+      k_arnoldi_col<<<1, 1, 0, s>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, hp_dev + 4 * j, nullptr);
+      k_scale<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->w.p, hn + 1, ls->V.p + (size_t)(j + 1) * nu, nullptr);
       RS_LAUNCHED(11);
     }
     RS_CHECK_LAUNCH();
   };
+  // The same Arnoldi step as one CUDA graph, replayed for every j: the step
+  // index lives on the device (jd), the basis vector is copied into a fixed
+  // buffer and the preconditioned vector out of one, and the kernels that
+  // depend on j read it from jd.  Recorded once per setup (the hierarchy's
+  // buffers may move at a setup); kernel timers become event nodes of the
+  // graph, read after each replay.
+  // The recording holds raw pointers: record again whenever one of the
+  // solver's own buffers, the restart length or the precision has changed.
+  bool use_graph = ls->graph_on && ls->ras.smem_path;
+  const void *sig[9] = {ls->V.p, ls->Z.p, ls->Z32.p, ls->w.p, ls->partial.p, ls->hbuf.p,
+                        (const void *)(size_t)m, (const void *)(size_t)ls->o.precision,
+                        (const void *)(size_t)ls->timer_mask};
+  if (use_graph && ls->it_exec && memcmp(sig, ls->it_sig, sizeof(sig)) != 0) ls->drop_graph();
+  if (use_graph && !ls->it_exec) {
+    ls->drop_graph();
+    ortho_attr();
+    ls->jd.ensure(1);
+    ls->vcur.ensure(nu);
+    if (mixed) ls->zcur32.ensure(nu); else ls->zcur64.ensure(nu);
+    if (!ls->cap) RS_CUDA(cudaStreamCreateWithFlags(&ls->cap, cudaStreamNonBlocking));
+    cudaStream_t keep = ls->st;
+    cudaGraph_t g = nullptr;
+    RS_CUDA(cudaStreamBeginCapture(ls->cap, cudaStreamCaptureModeRelaxed));
+    ls->st = ls->cap;
+    ls->capturing = true;
+    try {
+      cudaStream_t c = ls->cap;
+      const int *jd = ls->jd.p;
+      k_basis_get<<<grid_for(nu, 256), 256, 0, c>>>(nu, ls->V.p, jd, ls->vcur.p);
+      if (mixed) {
+        ls_cpr(ls, ls->vcur.p, nullptr, ls->zcur32.p);
+        {
+          rs_timed tm(ls, SIM_T_SPMV64);
+          spmv<double, float, double, double>(ls, ls->val.p, ls->zcur32.p, (const double *)nullptr, ls->w.p, c);
+        }
+        k_basis_put<float><<<grid_for(nu, 256), 256, 0, c>>>(nu, ls->zcur32.p, ls->Z32.p, jd);
+      } else {
+        ls_cpr(ls, ls->vcur.p, ls->zcur64.p, nullptr);
+        ls_spmv64(ls, ls->zcur64.p, ls->w.p);
+        k_basis_put<double><<<grid_for(nu, 256), 256, 0, c>>>(nu, ls->zcur64.p, ls->Z.p, jd);
+      }
+      rs_timed tm(ls, SIM_T_ORTHO);
+      ortho_dots(nu, 0, ls->V.p, ls->w.p, ls->partial.p, 1, nullptr, nblk, c, jd);
+      reduce_parts(0, nblk, ls->partial.p, h1, nullptr, c, jd, 1);
+      ortho_update(nu, 0, ls->V.p, ls->w.p, h1, ls->partial.p, nullptr, nblk, c, jd);
+      reduce_parts(1, nblk, ls->partial.p, nrm, nullptr, c);
+      k_dgks<<<1, 1, 0, c>>>(nullptr, nrm, flag, h1, jd);
+      ortho_dots(nu, 0, ls->V.p, ls->w.p, ls->partial.p, 0, flag, nblk, c, jd);
+      reduce_parts(0, nblk, ls->partial.p, h2, flag, c, jd, 0);
+      ortho_update(nu, 0, ls->V.p, ls->w.p, h2, ls->partial.p, flag, nblk, c, jd);
+      reduce_parts(1, nblk, ls->partial.p, nrm_b, flag, c);
+      k_arnoldi_col<<<1, 1, 0, c>>>(0, m, h1, h2, nrm, nrm_b, flag, G, hn, hp_dev, jd);
+      k_scale<<<grid_for(nu, 256), 256, 0, c>>>(nu, ls->w.p, hn + 1, ls->V.p, jd);
+      tm.stop();
+      k_step_inc<<<1, 1, 0, c>>>(ls->jd.p);
+      RS_LAUNCHED(14);
+      RS_CHECK_LAUNCH();
+    } catch (...) {
+      ls->st = keep; ls->capturing = false;
+      cudaStreamEndCapture(ls->cap, &g);
+      if (g) cudaGraphDestroy(g);
+      ls->drop_graph();
+      throw;
+    }
+    ls->st = keep;
+    ls->capturing = false;
+    RS_CUDA(cudaStreamEndCapture(ls->cap, &g));
+    // kernels recorded (counted by the node list: other handles may launch
+    // concurrently, so the global counter's difference is not this graph's)
+    size_t nn = 0;
+    cudaError_t e = cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    long long nk = 0;
+    if (e == cudaSuccess && nn) e = cudaGraphGetNodes(g, nodes.data(), &nn);
+    for (size_t q = 0; e == cudaSuccess && q < nn; q++) {
+      cudaGraphNodeType t;
+      e = cudaGraphNodeGetType(nodes[q], &t);
+      if (t == cudaGraphNodeTypeKernel) nk++;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ls->it_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { ls->it_exec = nullptr; ls->drop_graph(); RS_CUDA(e); }
+    memcpy(ls->it_sig, sig, sizeof(sig));
+    ls->it_launches = nk;
+    rs_launches -= (unsigned long long)nk;             // recorded, not launched
+  }
   for (;;) {
     k_start<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->r.p, beta, ls->V.p, G, m);
     RS_LAUNCHED(1);
     int jend = 0;
+    if (use_graph) RS_CUDA(cudaMemsetAsync(ls->jd.p, 0, sizeof(int), s));
     for (int j = 0; j < m; j++) {
-      enqueue(j);
+      if (use_graph) {
+        RS_CUDA(cudaGraphLaunch(ls->it_exec, s));
+        RS_LAUNCHED(ls->it_launches);
+      } else {
+        enqueue(j);
+      }
       RS_CUDA(cudaStreamSynchronize(s));
+      if (use_graph) ls->graph_timers();
       if (ls->errw[0]) RS_FAIL(SIM_ERR_TIMEOUT, "RAS apply: bulk copy wait gave up (code %d)", ls->errw[0]);
       double est = hp[4 * j], hnv = hp[4 * j + 1];
       its++;

@@ -1123,6 +1123,13 @@ extern "C" sim_status sim_kernel_timer(sim_ls_t ls, unsigned mask) {
   for (int k = 0; k < SIM_T_NFAMILIES; k++) { ls->timer_launches[k] = 0; ls->timer_ms[k] = 0; }
   ABI_END
 }
+extern "C" sim_status sim_ls_step_graph(sim_ls_t ls, int on) {
+  ABI_BEGIN
+  if (!ls) RS_FAIL(SIM_ERR_ARG, "NULL handle");
+  ls->graph_on = on != 0;
+  if (!ls->graph_on) ls->drop_graph();
+  ABI_END
+}
 extern "C" sim_status sim_kernel_time(sim_ls_t ls, int which, long long *launches, double *ms) {
   ABI_BEGIN
   if (!ls || which < 0 || which >= SIM_T_NFAMILIES) RS_FAIL(SIM_ERR_ARG, "sim_kernel_time: bad argument");
