@@ -544,6 +544,15 @@ __global__ void k_vc_post(int n, const int *rp, const int *ci, const T *v, const
   x[i] = t[i] + dinv[i] * s;
 }
 template <class T>
+__global__ void k_restrict_x(int n, const int *rp, const int *ci, const T *v, const T *u, const T *dinv, T *y, T *x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T s = 0;
+  for (int q = rp[i]; q < rp[i + 1]; q++) s += v[q] * u[ci[q]];
+  y[i] = s;
+  x[i] = s * dinv[i];
+}
+template <class T>
 __global__ void k_jacobi(int n, const int *rp, const int *ci, const T *v, const T *dinv, const T *f, const T *x, T *y) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -566,8 +575,9 @@ __global__ void k_dense_apply(int n, const double *invT, const T *f, T *x) {
 // The same four sweeps with L lanes per row (L = 4..32): a row's entries are
 // read by consecutive lanes (coalesced), each lane sums a strided part of the
 // row and the parts are combined with shuffles.  MODE 0: pre-smoothing
-// (x = D^-1 f, r = f - A x); 1: y = A x; 2: t = x + P e; 3: post-smoothing
-// (x = t + D^-1 (f - A t)).
+// (x = D^-1 f, r = f - A x; with u given, u already holds D^-1 f); 1: y = A x
+// (and, with o2 given, o2 = D_c^-1 y for the coarse level's pre-smoothing);
+// 2: t = x + P e; 3: post-smoothing (x = t + D^-1 (f - A t)).
 template <class T, int L, int MODE>
 __global__ void k_vc_lanes(int n, const int *__restrict__ rp, const int *__restrict__ ci, const T *__restrict__ v,
                            const T *__restrict__ dinv, const T *__restrict__ f, const T *__restrict__ u, T *o1, T *o2) {
@@ -575,16 +585,17 @@ __global__ void k_vc_lanes(int n, const int *__restrict__ rp, const int *__restr
   int i = g < n ? g : n - 1;                       // whole groups stay in the shuffles
   int q0 = rp[i], q1 = rp[i + 1];
   T s = 0;
+#pragma unroll 4
   for (int q = q0 + k; q < q1; q += L) {
     int j = ci[q];
-    T xj = MODE == 0 ? f[j] * dinv[j] : u[j];
+    T xj = MODE == 0 && !u ? f[j] * dinv[j] : u[j];
     s += v[q] * xj;
   }
 #pragma unroll
   for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, L);
   if (k != 0 || g >= n) return;
-  if (MODE == 0) { o1[i] = f[i] * dinv[i]; o2[i] = f[i] - s; }
-  else if (MODE == 1) o1[i] = s;
+  if (MODE == 0) { if (!u) o1[i] = f[i] * dinv[i]; o2[i] = f[i] - s; }   // with u, o1 = u holds it already
+  else if (MODE == 1) { o1[i] = s; if (o2) o2[i] = s * dinv[i]; }
   else if (MODE == 2) o1[i] = f[i] + s;            // f = x (the smoothed iterate), u = e
   else o1[i] = u[i] + dinv[i] * (f[i] - s);        // u = t
 }
@@ -592,9 +603,11 @@ __global__ void k_vc_lanes(int n, const int *__restrict__ rp, const int *__restr
 // lanes per row for a matrix's average row length: one thread per row for
 // short rows (their loads already coalesce across neighbouring rows), more
 // lanes as rows grow (a single thread walking a 40-entry row is latency-bound)
+// (measured on the 1M-cell hierarchy: 4 lanes for 9-24 entries per row and
+// 16 beyond beat 8/16/32, which left most lanes of a group idle)
 static int lanes_for(long long nnz, int n) {
   double avg = n ? (double)nnz / n : 0.0;
-  return avg <= 8.0 ? 1 : avg <= 12.0 ? 8 : avg <= 24.0 ? 16 : 32;
+  return avg <= 8.0 ? 1 : avg <= 24.0 ? 4 : 16;
 }
 
 template <class T>
@@ -613,6 +626,7 @@ static void vc_sweep(int L, int n, const int *rp, const int *ci, const T *v, con
   if (L == 1) {
     unsigned g = grid_for(n, 256);
     if (MODE == 0) k_vc_pre<T><<<g, 256, 0, s>>>(n, rp, ci, v, dinv, f, o1, o2);
+    else if (MODE == 1 && o2) k_restrict_x<T><<<g, 256, 0, s>>>(n, rp, ci, v, u, dinv, o1, o2);
     else if (MODE == 1) k_csr_spmv<T><<<g, 256, 0, s>>>(n, rp, ci, v, u, o1);
     else if (MODE == 2) k_prolong_add<T><<<g, 256, 0, s>>>(n, rp, ci, v, u, f, o1);
     else k_vc_post<T><<<g, 256, 0, s>>>(n, rp, ci, v, dinv, f, u, o1);
@@ -672,8 +686,13 @@ int amg_vcycle(amg_hier &h, int l, cudaStream_t s) {
   const auto &P = LP::P(L);
   const auto &R = LP::R(L);
   int la = lanes_for(A.nnz, n), lr = lanes_for(R.nnz, R.n), lp = lanes_for(P.nnz, n);
-  vc_sweep<T, 0>(la, n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), nullptr, LP::x(L), LP::r(L), s);
-  vc_sweep<T, 1>(lr, R.n, R.rp.p, R.ci.p, R.v.p, nullptr, nullptr, LP::r(L), LP::f(Cl), nullptr, s);
+  // below level 0 the restriction has already formed x = D^-1 f (pre-smoothing
+  // then gathers one vector instead of two; same products, same values)
+  vc_sweep<T, 0>(la, n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), l > 0 ? LP::x(L) : nullptr, LP::x(L),
+                 LP::r(L), s);
+  // the coarse level's D^-1 f, unless that level is solved directly
+  bool cx = !(l + 1 == h.nlev - 1 && h.coarse_dense);
+  vc_sweep<T, 1>(lr, R.n, R.rp.p, R.ci.p, R.v.p, LP::dinv(Cl), nullptr, LP::r(L), LP::f(Cl), cx ? LP::x(Cl) : nullptr, s);
   int k = amg_vcycle<T>(h, l + 1, s);
   vc_sweep<T, 2>(lp, n, P.rp.p, P.ci.p, P.v.p, nullptr, LP::x(L), LP::x(Cl), LP::t(L), nullptr, s);
   vc_sweep<T, 3>(la, n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), LP::t(L), LP::x(L), nullptr, s);
