@@ -12,6 +12,7 @@
 // a plain sequential evaluation of the same formulas on the same input.
 #include "common.cuh"
 #include <algorithm>
+#include <climits>
 
 // ------------------------------------------------------------ pattern -----
 __global__ void k_tpos(int n, const int *rp, const int *ci, int *tpos, int *err) {
@@ -209,27 +210,80 @@ __global__ void k_sort_rows(int n, const int *rp, int *ci, double *v) {
 }
 
 // -------------------------------------------------------------- SpGEMM ----
-// C = A B, one warp per row of C: expand every product A_ik B_kj with its
+// C = A B.  Rows of A with at most SPG_KMAX entries: k_spgemm_merge.  Longer
+// rows, one warp per row of C: expand every product A_ik B_kj with its
 // sequence number (row of A ascending, then row of B ascending), sort the
 // (column, sequence) keys in shared memory, and sum each column's products
 // in sequence order starting from 0.  One pass: each row is written at the
 // offset of its product count (an upper bound of its length) into a scratch
 // array, then the rows are packed.
+// products per row of C; mx = 1 + the most products of a row that the
+// sorting kernel handles (rows with more than SPG_KMAX entries in A), 0 if
+// there is none
+#define SPG_KMAX 8
 __global__ void k_row_products(int n, const int *arp, const int *aci, const int *brp, int *prod, int *mx) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int s = 0;
   for (int q = arp[i]; q < arp[i + 1]; q++) { int k = aci[q]; s += brp[k + 1] - brp[k]; }
   prod[i] = s;
-  atomicMax(mx, s);
+  if (arp[i + 1] - arp[i] > SPG_KMAX) atomicMax(mx, s + 1);   // + 1: "a long row exists" even with 0 products
 }
-// C row i = scratch[toff[i] .. toff[i] + clen[i]), one warp per row
+// C row i = scratch[toff[i] .. toff[i] + clen[i]), eight lanes per row
 __global__ void k_pack_rows(int n, const int *toff, const int *clen, const int *crp, const int *tci, const double *tv,
                             int *cci, double *cv) {
-  int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 3, lane = threadIdx.x & 7;
   if (row >= n) return;
   int a = toff[row], b = crp[row], len = clen[row];
-  for (int t = lane; t < len; t += 32) { cci[b + t] = tci[a + t]; cv[b + t] = tv[a + t]; }
+  for (int t = lane; t < len; t += 8) { cci[b + t] = tci[a + t]; cv[b + t] = tv[a + t]; }
+}
+
+// C = A B for the rows of A with at most K entries, one thread per row: a
+// k-way merge of the k rows of B that the row of A selects (each sorted by
+// column, its head kept in registers).  The smallest head column is the next
+// column of C; its products are summed in the order of the row of A,
+// starting from 0, which is the order of the sorted expansion below, so both
+// kernels give the same bits.  Only short rows of A take this path (the
+// finest level's stencil rows and its restriction): a thread walks its row
+// of C serially, which loses to the warp-per-row sort once rows of A and C
+// grow (measured on the coarser levels of the 1M-cell hierarchy).
+template <int K>
+__global__ void __launch_bounds__(128) k_spgemm_merge(int n, const int *arp, const int *aci, const double *av,
+                                                      const int *brp, const int *bci, const double *bv,
+                                                      const int *toff, int *clen, int *cci, double *cv) {
+  int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  int a0 = arp[row], k = arp[row + 1] - a0;
+  if (k > K) return;
+  int pos[K], end[K], col[K];
+  double a[K];
+#pragma unroll
+  for (int q = 0; q < K; q++) {
+    col[q] = INT_MAX; pos[q] = 0; end[q] = 0; a[q] = 0.0;
+    if (q < k) {
+      int kk = aci[a0 + q];
+      pos[q] = brp[kk]; end[q] = brp[kk + 1]; a[q] = av[a0 + q];
+      if (pos[q] < end[q]) col[q] = bci[pos[q]];
+    }
+  }
+  int out = toff[row], cnt = 0;
+  for (;;) {
+    int c = INT_MAX;
+#pragma unroll
+    for (int q = 0; q < K; q++) c = min(c, col[q]);
+    if (c == INT_MAX) break;
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < K; q++)
+      if (col[q] == c) {
+        s = add_rn(s, mul_rn(a[q], bv[pos[q]]));
+        pos[q]++;
+        col[q] = pos[q] < end[q] ? bci[pos[q]] : INT_MAX;
+      }
+    cci[out + cnt] = c; cv[out + cnt] = s;
+    cnt++;
+  }
+  clen[row] = cnt;
 }
 
 template <bool NUMERIC>
@@ -242,6 +296,7 @@ __global__ void k_spgemm(int n, const int *arp, const int *aci, const double *av
   const unsigned FULL = 0xffffffffu;
   for (int row = blockIdx.x * warps + wid; row < n; row += gridDim.x * warps) {
     int a0 = arp[row], a1 = arp[row + 1], base = 0;
+    if (a1 - a0 <= SPG_KMAX) continue;               // the merge kernel's row
     for (int q0 = a0; q0 < a1; q0 += 32) {
       int q = q0 + lane, len = 0, k = 0;
       if (q < a1) { k = aci[q]; len = brp[k + 1] - brp[k]; }
@@ -304,7 +359,7 @@ static void spgemm(const csr_dev<double> &A, const csr_dev<double> &B, csr_dev<d
   rs_fill_i(flag.p, 0, 1, s);
   k_row_products<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, B.rp.p, toff.p, flag.p);
   RS_LAUNCHED(1);
-  int mx = d2h(flag.p, 1, s)[0];
+  int mx1 = d2h(flag.p, 1, s)[0], mx = std::max(mx1 - 1, 0);
   int cap = 32;
   while (cap < mx) cap <<= 1;
   size_t per_warp = (size_t)cap * 16;
@@ -318,17 +373,23 @@ static void spgemm(const csr_dev<double> &A, const csr_dev<double> &B, csr_dev<d
   }
   int total = rs_scan(toff.p, toff.p, n, s);          // row offsets into the scratch arrays
   tci.ensure(std::max(total, 1)); tv.ensure(std::max(total, 1));
-  unsigned grid = (unsigned)std::min<size_t>((n + warps - 1) / warps, 152 * 64);
   C.n = n; C.m = B.m;
   C.rp.ensure(n + 1);
-  k_spgemm<true><<<grid, warps * 32, smem, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, toff.p, clen.p,
-                                                tci.p, tv.p, cap);
+  unsigned gm = grid_for(n, 128);
+  k_spgemm_merge<SPG_KMAX><<<gm, 128, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, toff.p, clen.p, tci.p,
+                                              tv.p);
   RS_LAUNCHED(1);
+  if (mx1 > 0) {                                       // rows of A longer than SPG_KMAX
+    unsigned grid = (unsigned)std::min<size_t>((n + warps - 1) / warps, 152 * 64);
+    k_spgemm<true><<<grid, warps * 32, smem, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, toff.p, clen.p,
+                                                  tci.p, tv.p, cap);
+    RS_LAUNCHED(1);
+  }
   RS_CHECK_LAUNCH();
   C.nnz = rs_scan(clen.p, C.rp.p, n, s);
   RS_CUDA(cudaMemcpyAsync(C.rp.p + n, &C.nnz, sizeof(int), cudaMemcpyHostToDevice, s));
   C.ci.ensure(C.nnz); C.v.ensure(C.nnz);
-  k_pack_rows<<<grid_for(n, 8), 256, 0, s>>>(n, toff.p, clen.p, C.rp.p, tci.p, tv.p, C.ci.p, C.v.p);
+  k_pack_rows<<<grid_for((size_t)n * 8, 256), 256, 0, s>>>(n, toff.p, clen.p, C.rp.p, tci.p, tv.p, C.ci.p, C.v.p);
   RS_LAUNCHED(1);
   RS_CHECK_LAUNCH();
   RS_CUDA(cudaStreamSynchronize(s));   // C.nnz host value lives on this stack frame's caller
