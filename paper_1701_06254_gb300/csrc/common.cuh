@@ -197,12 +197,13 @@ struct sim_ls_s {
   bool graph_on = true;
   cudaGraphExec_t it_exec = nullptr;
   long long it_launches = 0;
-  const void *it_sig[9] = {};   // buffers, restart length and precision it was recorded with
+  const void *it_sig[10] = {};   // buffers, restart length and precision it was recorded with
   cudaStream_t cap = nullptr;
   bool capturing = false;
   dbuf<int> jd;                 // the step index the graph's kernels read
   dbuf<double> vcur, zcur64;
-  dbuf<float> zcur32;
+  dbuf<float> zcur32, vcur32;
+  dbuf<float> w2, isp;          // double-float w planes; split 1 / h_{j+1,j}
   // timer brackets recorded inside the graph (event nodes): pairs of events
   // and the family of each pair, read back after every replay
   std::vector<cudaEvent_t> gev;
@@ -240,6 +241,7 @@ void ls_setup(sim_ls_s *ls);
 // solution in ls->y; x0: ls->y holds the initial guess (else zero)
 int ls_solve(sim_ls_s *ls, double tol, int *its, double *relres, bool x0 = false);
 void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32);
+void ls_cpr32(sim_ls_s *ls, const float *v, float *z);
 void ls_spmv64(sim_ls_s *ls, const double *x, double *y);
 void ls_spmv64_untimed(sim_ls_s *ls, const double *x, double *y);
 double ls_residual_norm(sim_ls_s *ls, const double *x_dev);

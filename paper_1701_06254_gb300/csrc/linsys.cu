@@ -251,6 +251,25 @@ void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32) {
   }
 }
 
+// CPR-FPF with an FP32 input vector (mixed precision with the double-float
+// basis, whose hi plane is the FP32 value of a basis vector): the same steps
+// as ls_cpr's mixed branch.
+void ls_cpr32(sim_ls_s *ls, const float *v, float *z) {
+  cudaStream_t s = ls->st;
+  int n = ls->n;
+  amg_level &L0 = ls->amg.lev[0];
+  float *r = ls->x32b.p;
+  ls_ras_apply<float, float>(ls, v, z, false);                                         // 1
+  { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, float, float>(ls, ls->val32.p, z, v, r, s); }   // 2
+  k_gather_p<float, float><<<grid_for(n, 256), 256, 0, s>>>(n, r, L0.f32.p);
+  RS_LAUNCHED(1);
+  { rs_timed tm(ls, SIM_T_VCYCLE); if (ls->capturing) amg_vcycle<float>(ls->amg, 0, s); else amg_vcycle_graph<float>(ls->amg, s); }  // 3
+  k_add_p<float><<<grid_for(n, 256), 256, 0, s>>>(n, L0.x32.p, z);
+  RS_LAUNCHED(1);
+  { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, float, float>(ls, ls->val32.p, z, v, r, s); }   // 4
+  ls_ras_apply<float, float>(ls, r, z, true);                                          // 5
+}
+
 // ------------------------------------------------------------ init -------
 void ls_init(sim_ls_s *ls, int nx, int ny, int nz, int nw, const int *rp, const int *ci, const int *well_cell0,
              const rs_opts &o, cudaStream_t st) {
@@ -336,6 +355,7 @@ void ls_setup(sim_ls_s *ls) {
 // shared memory.  Basis vectors are streamed vector-outer, rows-inner, so
 // loads are coalesced and independent.
 #define ORTHO_CH 2048
+#define ORTHO_CH_DF 8192
 static int ortho_blocks(int nu) { return (nu + ORTHO_CH - 1) / ORTHO_CH; }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -462,11 +482,255 @@ __global__ void __launch_bounds__(ORTHO_BS) k_ortho_update(int nu, int nv, const
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
+// ------------------------------------------------ double-float basis ----
+// Mixed precision keeps the Arnoldi basis and the vector being
+// orthogonalised as unevaluated sums hi + lo of two FP32 numbers (about 48
+// significant bits), stored as two planes per vector (hi[nu], then lo[nu]).
+// The Gram-Schmidt dot products and updates then run on the FP32 pipes:
+// Dekker's product (an FMA yields the rounding error of a product) and
+// Knuth's two-sum carry the low parts, instead of FP64 multiply-adds, whose
+// rate bounds the FP64 kernels above.  Scalars (h, norms, Givens) stay
+// FP64; the preconditioner reads a basis vector in FP32, which is its hi
+// plane.
+__device__ __forceinline__ void df_two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void df_fast(float a, float b, float &s, float &e) {   // |a| >= |b|
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// (ah + al)(bh + bl) = p + e up to the dropped al bl
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &p, float &e) {
+  p = __fmul_rn(ah, bh);
+  e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+}
+__device__ __forceinline__ void df_add(float &h, float &l, float h2, float l2) {
+  float s, e;
+  df_two_sum(h, h2, s, e);
+  e = __fadd_rn(e, __fadd_rn(l, l2));
+  df_fast(s, e, h, l);
+}
+__device__ __forceinline__ void df_split(double x, float &h, float &l) {
+  h = __double2float_rn(x);
+  l = __double2float_rn(x - (double)h);
+}
+// running sum s + c of products p + e
+__device__ __forceinline__ void df_acc(float &s, float &c, float p, float e) {
+  float t, err;
+  df_two_sum(s, p, t, err);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+// warp_sum8_d for pairs: lane l ends with the total of the same slot
+__device__ __forceinline__ void warp_sum8_df(const float *ah, const float *al, int lane, float &rh, float &rl) {
+  float bh[4], bl[4], ch[2], cl[2];
+  bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    float kh = u16 ? ah[q + 4] : ah[q], kl = u16 ? al[q + 4] : al[q];
+    float gh = u16 ? ah[q] : ah[q + 4], gl = u16 ? al[q] : al[q + 4];
+    gh = __shfl_xor_sync(0xffffffffu, gh, 16); gl = __shfl_xor_sync(0xffffffffu, gl, 16);
+    df_add(kh, kl, gh, gl);
+    bh[q] = kh; bl[q] = kl;
+  }
+#pragma unroll
+  for (int q = 0; q < 2; q++) {
+    float kh = u8 ? bh[q + 2] : bh[q], kl = u8 ? bl[q + 2] : bl[q];
+    float gh = u8 ? bh[q] : bh[q + 2], gl = u8 ? bl[q] : bl[q + 2];
+    gh = __shfl_xor_sync(0xffffffffu, gh, 8); gl = __shfl_xor_sync(0xffffffffu, gl, 8);
+    df_add(kh, kl, gh, gl);
+    ch[q] = kh; cl[q] = kl;
+  }
+  float kh = u4 ? ch[1] : ch[0], kl = u4 ? cl[1] : cl[0];
+  float gh = u4 ? ch[0] : ch[1], gl = u4 ? cl[0] : cl[1];
+  gh = __shfl_xor_sync(0xffffffffu, gh, 4); gl = __shfl_xor_sync(0xffffffffu, gl, 4);
+  df_add(kh, kl, gh, gl);
+#pragma unroll
+  for (int o = 2; o > 0; o >>= 1) {
+    float oh = __shfl_xor_sync(0xffffffffu, kh, o), ol = __shfl_xor_sync(0xffffffffu, kl, o);
+    df_add(kh, kl, oh, ol);
+  }
+  rh = kh; rl = kl;
+}
+__device__ __forceinline__ double warp_sum_df(float h, float l) {        // result in every lane
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+    df_add(h, l, oh, ol);
+  }
+  return (double)h + (double)l;
+}
+
+// k_ortho_dots on pair planes: V vector k at V + 2k nu (hi) and + (2k+1) nu
+// (lo), w at w (hi) and w + nu (lo).  Vector offsets are 32-bit (the basis
+// holds at most 2 (ORTHO_MAXV + 1) nu < 2^31 floats) and each thread takes
+// two rows per iteration, so that 32 loads are in flight together.
+__global__ void __launch_bounds__(ORTHO_BS, 4) k_ortho_dots_df(int nu, int ch, int nv, const float *__restrict__ V,
+                                                               const float *__restrict__ w, double *part,
+                                                               int with_norm, const int *cond, const int *jd) {
+  if (cond && *cond == 0) return;
+  if (jd) nv = *jd + 1;
+  extern __shared__ float2 wp[];               // ORTHO_CH pairs (dynamic)
+  __shared__ double red[2][ORTHO_BS / 32][ORTHO_G];
+  int nblk = gridDim.x, i0 = blockIdx.x * ch, len = min(ch, nu - i0);
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < len; t += ORTHO_BS) wp[t] = make_float2(w[i0 + t], w[(size_t)nu + i0 + t]);
+  __syncthreads();
+  const float *vb = V + i0;
+  int nt = nv + (with_norm ? 1 : 0);
+  for (int k0 = 0, grp = 0; k0 < nt; k0 += ORTHO_G, grp ^= 1) {
+    float as[ORTHO_G], ac[ORTHO_G];
+#pragma unroll
+    for (int g = 0; g < ORTHO_G; g++) { as[g] = 0.0f; ac[g] = 0.0f; }
+    int ng = min(ORTHO_G, nv - k0);            // basis vectors in this group; slot nv - k0 is w's norm
+    for (int t = threadIdx.x; t < len; t += 2 * ORTHO_BS) {
+      int t2 = t + ORTHO_BS;
+      bool two = t2 < len;
+      float ah[ORTHO_G], al[ORTHO_G], bh[ORTHO_G], bl[ORTHO_G];
+#pragma unroll
+      for (int g = 0; g < ORTHO_G; g++)
+        if (g < ng) {
+          int o = 2 * (k0 + g) * nu;
+          ah[g] = __ldg(vb + o + t); al[g] = __ldg(vb + o + nu + t);
+          if (two) { bh[g] = __ldg(vb + o + t2); bl[g] = __ldg(vb + o + nu + t2); }
+        }
+      float2 x = wp[t], y = two ? wp[t2] : make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int g = 0; g < ORTHO_G; g++) {
+        float p, e;
+        if (g < ng) {
+          df_mul(ah[g], al[g], x.x, x.y, p, e); df_acc(as[g], ac[g], p, e);
+          if (two) { df_mul(bh[g], bl[g], y.x, y.y, p, e); df_acc(as[g], ac[g], p, e); }
+        } else if (k0 + g == nv && with_norm) {
+          df_mul(x.x, x.y, x.x, x.y, p, e); df_acc(as[g], ac[g], p, e);
+          if (two) { df_mul(y.x, y.y, y.x, y.y, p, e); df_acc(as[g], ac[g], p, e); }
+        }
+      }
+    }
+    float hh[ORTHO_G], ll[ORTHO_G];
+#pragma unroll
+    for (int g = 0; g < ORTHO_G; g++) df_fast(as[g], ac[g], hh[g], ll[g]);
+    float rh, rl;
+    warp_sum8_df(hh, ll, lane, rh, rl);
+    if ((lane & 3) == 0)
+      red[grp][warp][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = (double)rh + (double)rl;
+    __syncthreads();                           // red[grp] is rewritten two groups later, after another barrier
+    if (threadIdx.x < ORTHO_G && k0 + threadIdx.x < nt) {
+      double sum = 0.0;
+      for (int q = 0; q < ORTHO_BS / 32; q++) sum += red[grp][q][threadIdx.x];
+      part[(size_t)(k0 + threadIdx.x) * nblk + blockIdx.x] = sum;
+    }
+  }
+}
+
+// k_ortho_update on pair planes: w -= sum_k h_k V_k (h FP64, split once per
+// block), then part[0][b] = ||w||^2 over the block's rows; two rows per
+// thread per iteration
+__global__ void __launch_bounds__(ORTHO_BS, 4) k_ortho_update_df(int nu, int ch, int nv, const float *__restrict__ V,
+                                                                 float *w, const double *__restrict__ h, double *part,
+                                                                 const int *cond, const int *jd) {
+  if (cond && *cond == 0) return;
+  if (jd) nv = *jd + 1;
+  extern __shared__ float2 wp[];
+  __shared__ float2 hs[ORTHO_MAXV + 1];
+  __shared__ double sred[ORTHO_BS / 32];
+  int i0 = blockIdx.x * ch, len = min(ch, nu - i0);
+  for (int t = threadIdx.x; t < nv; t += ORTHO_BS) { float a, b; df_split(h[t], a, b); hs[t] = make_float2(a, b); }
+  for (int t = threadIdx.x; t < len; t += ORTHO_BS) wp[t] = make_float2(w[i0 + t], w[(size_t)nu + i0 + t]);
+  __syncthreads();
+  const float *vb = V + i0;
+  for (int k0 = 0; k0 < nv; k0 += ORTHO_G) {   // each thread updates only its own rows: no barrier needed
+    int ng = min(ORTHO_G, nv - k0);
+    for (int t = threadIdx.x; t < len; t += 2 * ORTHO_BS) {
+      int t2 = t + ORTHO_BS;
+      bool two = t2 < len;
+      float ah[ORTHO_G], al[ORTHO_G], bh[ORTHO_G], bl[ORTHO_G];
+#pragma unroll
+      for (int g = 0; g < ORTHO_G; g++)
+        if (g < ng) {
+          int o = 2 * (k0 + g) * nu;
+          ah[g] = __ldg(vb + o + t); al[g] = __ldg(vb + o + nu + t);
+          if (two) { bh[g] = __ldg(vb + o + t2); bl[g] = __ldg(vb + o + nu + t2); }
+        }
+      float2 x = wp[t], y = two ? wp[t2] : make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int g = 0; g < ORTHO_G; g++)       // w - h_0 v_0 - h_1 v_1 ..., one vector at a time
+        if (g < ng) {
+          float2 hk = hs[k0 + g];
+          float p, e, s2, err;
+          df_mul(hk.x, hk.y, ah[g], al[g], p, e);
+          df_two_sum(x.x, -p, s2, err);
+          err = __fadd_rn(err, __fsub_rn(x.y, e));
+          df_fast(s2, err, x.x, x.y);
+          if (two) {
+            df_mul(hk.x, hk.y, bh[g], bl[g], p, e);
+            df_two_sum(y.x, -p, s2, err);
+            err = __fadd_rn(err, __fsub_rn(y.y, e));
+            df_fast(s2, err, y.x, y.y);
+          }
+        }
+      wp[t] = x;
+      if (two) wp[t2] = y;
+    }
+  }
+  float ns = 0.0f, nc = 0.0f;
+  for (int t = threadIdx.x; t < len; t += ORTHO_BS) {
+    float2 x = wp[t];
+    w[i0 + t] = x.x;
+    w[(size_t)nu + i0 + t] = x.y;
+    float p, e;
+    df_mul(x.x, x.y, x.x, x.y, p, e);
+    df_acc(ns, nc, p, e);
+  }
+  float nh, nl;
+  df_fast(ns, nc, nh, nl);
+  double wt = warp_sum_df(nh, nl);
+  if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = wt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int q = 0; q < ORTHO_BS / 32; q++) tot += sred[q];
+    part[blockIdx.x] = tot;
+  }
+}
+// w (FP64, from the SpMV) into pair planes
+__global__ void k_split_w(int nu, const double *w64, float *w) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nu) { float h, l; df_split(w64[i], h, l); w[i] = h; w[(size_t)nu + i] = l; }
+}
+// V_{j+1} = w / h_{j+1,j}, the reciprocal split once by k_arnoldi_col (isp)
+__global__ void k_scale_df(int nu, const float *w, const float *isp, float *V, int j1, const int *jd) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (jd) j1 = *jd + 1;
+  if (i >= nu) return;
+  float p, e, h, l;
+  df_mul(w[i], w[(size_t)nu + i], isp[0], isp[1], p, e);
+  df_fast(p, e, h, l);
+  V[(size_t)(2 * j1) * nu + i] = h;
+  V[(size_t)(2 * j1 + 1) * nu + i] = l;
+}
+__global__ void k_start_df(int nu, const double *r, double beta, float *V, double *G, int m) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nu) { float h, l; df_split(r[i] * (1.0 / beta), h, l); V[i] = h; V[(size_t)nu + i] = l; }
+  if (i == 0) { double *g = G + (size_t)m * (m + 1) + 2 * m; for (int k = 0; k <= m; k++) g[k] = 0.0; g[0] = beta; }
+}
+// graph replay: the step's basis vector (hi plane) into a fixed buffer
+__global__ void k_basis_get_df(int nu, const float *V, const int *jd, float *vcur) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nu) vcur[i] = V[(size_t)(2 * *jd) * nu + i];
+}
+
 static void ortho_attr() {
   static bool done = false;
   if (done) return;
   RS_CUDA(cudaFuncSetAttribute(k_ortho_dots, cudaFuncAttributeMaxDynamicSharedMemorySize, ORTHO_CH * 8));
   RS_CUDA(cudaFuncSetAttribute(k_ortho_update, cudaFuncAttributeMaxDynamicSharedMemorySize, ORTHO_CH * 8));
+  RS_CUDA(cudaFuncSetAttribute(k_ortho_dots_df, cudaFuncAttributeMaxDynamicSharedMemorySize, ORTHO_CH_DF * 8));
+  RS_CUDA(cudaFuncSetAttribute(k_ortho_update_df, cudaFuncAttributeMaxDynamicSharedMemorySize, ORTHO_CH_DF * 8));
   done = true;
 }
 static void ortho_dots(int nu, int nv, const double *V, const double *w, double *part, int with_norm, const int *cond,
@@ -478,6 +742,28 @@ static void ortho_update(int nu, int nv, const double *V, double *w, const doubl
                          int nblk, cudaStream_t s, const int *jd = nullptr) {
   ortho_attr();
   k_ortho_update<<<nblk, ORTHO_BS, ORTHO_CH * 8, s>>>(nu, nv, V, w, h, part, cond, jd);
+}
+
+// double-float kernels: one wave of 4 blocks per SM, each owning an equal
+// chunk of rows (a multiple of 64, at most ORTHO_CH_DF), its slice of w in
+// shared memory
+static int ortho_blocks_df(int nu, int *ch) {
+  int nblk = 152 * 4;
+  int c = ((nu + nblk - 1) / nblk + 63) & ~63;
+  if (c > ORTHO_CH_DF) { c = ORTHO_CH_DF; nblk = (nu + c - 1) / c; }
+  else nblk = (nu + c - 1) / c;
+  *ch = c;
+  return std::max(nblk, 1);
+}
+static void ortho_dots_df(int nu, int ch, int nv, const float *V, const float *w, double *part, int with_norm,
+                          const int *cond, int nblk, cudaStream_t s, const int *jd = nullptr) {
+  ortho_attr();
+  k_ortho_dots_df<<<nblk, ORTHO_BS, (size_t)ch * 8, s>>>(nu, ch, nv, V, w, part, with_norm, cond, jd);
+}
+static void ortho_update_df(int nu, int ch, int nv, const float *V, float *w, const double *h, double *part,
+                            const int *cond, int nblk, cudaStream_t s, const int *jd = nullptr) {
+  ortho_attr();
+  k_ortho_update_df<<<nblk, ORTHO_BS, (size_t)ch * 8, s>>>(nu, ch, nv, V, w, h, part, cond, jd);
 }
 
 // out[k] = sum over blocks of part[k][*]: one warp per k, lanes add a fixed
@@ -509,7 +795,7 @@ __global__ void k_dgks(const double *w2_before, const double *w2_after, int *fla
 // G layout: [0..m*(m+1)) H column-major (m+1 per column), cs[m], sn[m], g[m+1]
 __global__ void k_arnoldi_col(int j, int m, const double *h1, const double *h2, const double *nrm_a,
                               const double *nrm_b, const int *flag, double *G, double *hnorm, volatile double *host,
-                              const int *jd) {
+                              const int *jd, float *isp) {
   if (jd) { j = *jd; host += 4 * j; }          // graph replay: pinned slot j
   double *H = G, *cs = G + (size_t)m * (m + 1), *sn = cs + m, *g = sn + m;
   double *col = H + (size_t)j * (m + 1);
@@ -518,6 +804,7 @@ __global__ void k_arnoldi_col(int j, int m, const double *h1, const double *h2, 
   double hn = sqrt(re ? *nrm_b : *nrm_a);
   hnorm[0] = hn;
   hnorm[1] = hn > 0.0 ? 1.0 / hn : 0.0;
+  if (isp) { float a, b; df_split(hnorm[1], a, b); isp[0] = a; isp[1] = b; }
   for (int k = 0; k < j; k++) {
     double t = cs[k] * col[k] + sn[k] * col[k + 1];
     col[k + 1] = -sn[k] * col[k] + cs[k] * col[k + 1];
@@ -577,10 +864,13 @@ __global__ void k_xupdate(int nu, int jend, const double *yk, const Tz *Z, doubl
 int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
   cudaStream_t s = ls->st;
   int nu = 2 * ls->nb, m = std::min(ls->o.restart, ORTHO_MAXV - 1), maxit = ls->o.max_lin;
+  // df: double-float Arnoldi basis (its kernels use 32-bit offsets into the
+  // 2 (m + 1) nu floats of the basis; larger systems keep the FP64 basis)
   bool mixed = ls->o.precision != SIM_PREC_FP64;
+  bool df = mixed && 2.0 * (m + 1) * (double)nu < 2147483647.0;
   ls->V.ensure((size_t)(m + 1) * nu);
   if (mixed) ls->Z32.ensure((size_t)m * nu); else ls->Z.ensure((size_t)m * nu);
-  int nblk = ortho_blocks(nu);
+  int chd = 0, nblk = df ? ortho_blocks_df(nu, &chd) : ortho_blocks(nu);
   ls->partial.ensure((size_t)(ORTHO_MAXV + 1) * nblk + 8);
   ls->hbuf.ensure((size_t)(m + 1) * (m + 1) + 4 * (m + 1) + 4 * ORTHO_MAXV + 16);
   double *G = ls->hbuf.p, *h1 = G + (size_t)(m + 1) * (m + 1) + 3 * (m + 1), *h2 = h1 + ORTHO_MAXV + 1,
@@ -604,35 +894,69 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
   }
   if (beta <= tol * bn) { *its_out = 0; *relres = beta / bn; return 0; }
   int its = 0, rc = 1;
+  // Orthogonalisation of w against V_0..V_j (classical Gram-Schmidt with a
+  // second pass under cancellation), the Hessenberg column with its Givens
+  // rotations, and V_{j+1}.  jdp: the step index is read on the device (graph
+  // replay) instead of j.  Mixed precision: double-float planes.
+  float *V32 = reinterpret_cast<float *>(ls->V.p);
+  if (df) { ls->w2.ensure(2 * (size_t)nu); ls->isp.ensure(2); }
+  auto ortho_tail = [&](cudaStream_t c, int j, const int *jdp) {
+    int nv = jdp ? 0 : j + 1;
+    double *part = ls->partial.p;
+    if (df) {
+      float *w2 = ls->w2.p;
+      k_split_w<<<grid_for(nu, 256), 256, 0, c>>>(nu, ls->w.p, w2);
+      ortho_dots_df(nu, chd, nv, V32, w2, part, 1, nullptr, nblk, c, jdp);
+      reduce_parts(nv + 1, nblk, part, h1, nullptr, c, jdp, 1);          // h1[nv] = ||w||^2
+      ortho_update_df(nu, chd, nv, V32, w2, h1, part, nullptr, nblk, c, jdp);
+      reduce_parts(1, nblk, part, nrm, nullptr, c);
+      k_dgks<<<1, 1, 0, c>>>(h1 + nv, nrm, flag, h1, jdp);
+      ortho_dots_df(nu, chd, nv, V32, w2, part, 0, flag, nblk, c, jdp);
+      reduce_parts(nv, nblk, part, h2, flag, c, jdp, 0);
+      ortho_update_df(nu, chd, nv, V32, w2, h2, part, flag, nblk, c, jdp);
+      reduce_parts(1, nblk, part, nrm_b, flag, c);
+      k_arnoldi_col<<<1, 1, 0, c>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, jdp ? hp_dev : hp_dev + 4 * j, jdp,
+                                    ls->isp.p);
+      k_scale_df<<<grid_for(nu, 256), 256, 0, c>>>(nu, w2, ls->isp.p, V32, j + 1, jdp);
+      RS_LAUNCHED(12);
+    } else {
+      ortho_dots(nu, nv, ls->V.p, ls->w.p, part, 1, nullptr, nblk, c, jdp);
+      reduce_parts(nv + 1, nblk, part, h1, nullptr, c, jdp, 1);
+      ortho_update(nu, nv, ls->V.p, ls->w.p, h1, part, nullptr, nblk, c, jdp);
+      reduce_parts(1, nblk, part, nrm, nullptr, c);
+      k_dgks<<<1, 1, 0, c>>>(h1 + nv, nrm, flag, h1, jdp);
+      ortho_dots(nu, nv, ls->V.p, ls->w.p, part, 0, flag, nblk, c, jdp);
+      reduce_parts(nv, nblk, part, h2, flag, c, jdp, 0);
+      ortho_update(nu, nv, ls->V.p, ls->w.p, h2, part, flag, nblk, c, jdp);
+      reduce_parts(1, nblk, part, nrm_b, flag, c);
+      k_arnoldi_col<<<1, 1, 0, c>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, jdp ? hp_dev : hp_dev + 4 * j, jdp,
+                                    nullptr);
+      k_scale<<<grid_for(nu, 256), 256, 0, c>>>(nu, ls->w.p, hn + 1, jdp ? ls->V.p : ls->V.p + (size_t)(j + 1) * nu,
+                                                jdp);
+      RS_LAUNCHED(11);
+    }
+  };
   // One Arnoldi step j (CPR, SpMV, orthogonalisation, Givens); its residual
   // estimate and h_{j+1,j} land in pinned slot j
   auto enqueue = [&](int j) {
-    double *vj = ls->V.p + (size_t)j * nu;
-    if (mixed) {
+    if (df) {
       float *zj = ls->Z32.p + (size_t)j * nu;
-      ls_cpr(ls, vj, nullptr, zj);
+      ls_cpr32(ls, V32 + (size_t)(2 * j) * nu, zj);
+      rs_timed tm(ls, SIM_T_SPMV64);
+      spmv<double, float, double, double>(ls, ls->val.p, zj, (const double *)nullptr, ls->w.p, s);
+    } else if (mixed) {          // FP64 basis with the FP32 preconditioner
+      float *zj = ls->Z32.p + (size_t)j * nu;
+      ls_cpr(ls, ls->V.p + (size_t)j * nu, nullptr, zj);
       rs_timed tm(ls, SIM_T_SPMV64);
       spmv<double, float, double, double>(ls, ls->val.p, zj, (const double *)nullptr, ls->w.p, s);
     } else {
       double *zj = ls->Z.p + (size_t)j * nu;
-      ls_cpr(ls, vj, zj, nullptr);
+      ls_cpr(ls, ls->V.p + (size_t)j * nu, zj, nullptr);
       ls_spmv64(ls, zj, ls->w.p);
     }
     {
       rs_timed tm(ls, SIM_T_ORTHO);
-      int nv = j + 1;
-      ortho_dots(nu, nv, ls->V.p, ls->w.p, ls->partial.p, 1, nullptr, nblk, s);
-      reduce_parts(nv + 1, nblk, ls->partial.p, h1, nullptr, s);     // h1[nv] = ||w||^2
-      ortho_update(nu, nv, ls->V.p, ls->w.p, h1, ls->partial.p, nullptr, nblk, s);
-      reduce_parts(1, nblk, ls->partial.p, nrm, nullptr, s);
-      k_dgks<<<1, 1, 0, s>>>(h1 + nv, nrm, flag, nullptr, nullptr);
-      ortho_dots(nu, nv, ls->V.p, ls->w.p, ls->partial.p, 0, flag, nblk, s);
-      reduce_parts(nv, nblk, ls->partial.p, h2, flag, s);
-      ortho_update(nu, nv, ls->V.p, ls->w.p, h2, ls->partial.p, flag, nblk, s);
-      reduce_parts(1, nblk, ls->partial.p, nrm_b, flag, s);
-      k_arnoldi_col<<<1, 1, 0, s>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, hp_dev + 4 * j, nullptr);
-      k_scale<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->w.p, hn + 1, ls->V.p + (size_t)(j + 1) * nu, nullptr);
-      RS_LAUNCHED(11);
+      ortho_tail(s, j, nullptr);
     }
     RS_CHECK_LAUNCH();
   };
@@ -645,15 +969,15 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
   // The recording holds raw pointers: record again whenever one of the
   // solver's own buffers, the restart length or the precision has changed.
   bool use_graph = ls->graph_on && ls->ras.smem_path;
-  const void *sig[9] = {ls->V.p, ls->Z.p, ls->Z32.p, ls->w.p, ls->partial.p, ls->hbuf.p,
-                        (const void *)(size_t)m, (const void *)(size_t)ls->o.precision,
-                        (const void *)(size_t)ls->timer_mask};
+  const void *sig[10] = {ls->V.p, ls->Z.p, ls->Z32.p, ls->w.p, ls->partial.p, ls->hbuf.p,
+                         (const void *)(size_t)m, (const void *)(size_t)ls->o.precision,
+                         (const void *)(size_t)ls->timer_mask, ls->w2.p};
   if (use_graph && ls->it_exec && memcmp(sig, ls->it_sig, sizeof(sig)) != 0) ls->drop_graph();
   if (use_graph && !ls->it_exec) {
     ls->drop_graph();
     ortho_attr();
     ls->jd.ensure(1);
-    ls->vcur.ensure(nu);
+    if (df) ls->vcur32.ensure(nu); else ls->vcur.ensure(nu);
     if (mixed) ls->zcur32.ensure(nu); else ls->zcur64.ensure(nu);
     if (!ls->cap) RS_CUDA(cudaStreamCreateWithFlags(&ls->cap, cudaStreamNonBlocking));
     cudaStream_t keep = ls->st;
@@ -664,8 +988,16 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
     try {
       cudaStream_t c = ls->cap;
       const int *jd = ls->jd.p;
-      k_basis_get<<<grid_for(nu, 256), 256, 0, c>>>(nu, ls->V.p, jd, ls->vcur.p);
-      if (mixed) {
+      if (df) {
+        k_basis_get_df<<<grid_for(nu, 256), 256, 0, c>>>(nu, V32, jd, ls->vcur32.p);
+        ls_cpr32(ls, ls->vcur32.p, ls->zcur32.p);
+        {
+          rs_timed tm(ls, SIM_T_SPMV64);
+          spmv<double, float, double, double>(ls, ls->val.p, ls->zcur32.p, (const double *)nullptr, ls->w.p, c);
+        }
+        k_basis_put<float><<<grid_for(nu, 256), 256, 0, c>>>(nu, ls->zcur32.p, ls->Z32.p, jd);
+      } else if (mixed) {
+        k_basis_get<<<grid_for(nu, 256), 256, 0, c>>>(nu, ls->V.p, jd, ls->vcur.p);
         ls_cpr(ls, ls->vcur.p, nullptr, ls->zcur32.p);
         {
           rs_timed tm(ls, SIM_T_SPMV64);
@@ -673,25 +1005,16 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
         }
         k_basis_put<float><<<grid_for(nu, 256), 256, 0, c>>>(nu, ls->zcur32.p, ls->Z32.p, jd);
       } else {
+        k_basis_get<<<grid_for(nu, 256), 256, 0, c>>>(nu, ls->V.p, jd, ls->vcur.p);
         ls_cpr(ls, ls->vcur.p, ls->zcur64.p, nullptr);
         ls_spmv64(ls, ls->zcur64.p, ls->w.p);
         k_basis_put<double><<<grid_for(nu, 256), 256, 0, c>>>(nu, ls->zcur64.p, ls->Z.p, jd);
       }
       rs_timed tm(ls, SIM_T_ORTHO);
-      ortho_dots(nu, 0, ls->V.p, ls->w.p, ls->partial.p, 1, nullptr, nblk, c, jd);
-      reduce_parts(0, nblk, ls->partial.p, h1, nullptr, c, jd, 1);
-      ortho_update(nu, 0, ls->V.p, ls->w.p, h1, ls->partial.p, nullptr, nblk, c, jd);
-      reduce_parts(1, nblk, ls->partial.p, nrm, nullptr, c);
-      k_dgks<<<1, 1, 0, c>>>(nullptr, nrm, flag, h1, jd);
-      ortho_dots(nu, 0, ls->V.p, ls->w.p, ls->partial.p, 0, flag, nblk, c, jd);
-      reduce_parts(0, nblk, ls->partial.p, h2, flag, c, jd, 0);
-      ortho_update(nu, 0, ls->V.p, ls->w.p, h2, ls->partial.p, flag, nblk, c, jd);
-      reduce_parts(1, nblk, ls->partial.p, nrm_b, flag, c);
-      k_arnoldi_col<<<1, 1, 0, c>>>(0, m, h1, h2, nrm, nrm_b, flag, G, hn, hp_dev, jd);
-      k_scale<<<grid_for(nu, 256), 256, 0, c>>>(nu, ls->w.p, hn + 1, ls->V.p, jd);
+      ortho_tail(c, 0, jd);
       tm.stop();
       k_step_inc<<<1, 1, 0, c>>>(ls->jd.p);
-      RS_LAUNCHED(14);
+      RS_LAUNCHED(3);
       RS_CHECK_LAUNCH();
     } catch (...) {
       ls->st = keep; ls->capturing = false;
@@ -723,7 +1046,8 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
     rs_launches -= (unsigned long long)nk;             // recorded, not launched
   }
   for (;;) {
-    k_start<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->r.p, beta, ls->V.p, G, m);
+    if (df) k_start_df<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->r.p, beta, V32, G, m);
+    else k_start<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->r.p, beta, ls->V.p, G, m);
     RS_LAUNCHED(1);
     int jend = 0;
     if (use_graph) RS_CUDA(cudaMemsetAsync(ls->jd.p, 0, sizeof(int), s));
