@@ -136,6 +136,44 @@ __global__ void k_extract_app(int nnz, const int *src, const double *val, double
   if (k < nnz) v[k] = val[4 * (size_t)src[k]];
 }
 
+// ------------------------------------------------ double-float helpers ---
+// Unevaluated sums hi + lo of two FP32 numbers (about 48 significant bits):
+// Knuth's two-sum, and Dekker's product with the FMA giving a product's
+// rounding error exactly.
+__device__ __forceinline__ void df_two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void df_fast(float a, float b, float &s, float &e) {   // |a| >= |b|
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// (ah + al)(bh + bl) = p + e up to the dropped al bl
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &p, float &e) {
+  p = __fmul_rn(ah, bh);
+  e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+}
+__device__ __forceinline__ void df_add(float &h, float &l, float h2, float l2) {
+  float s, e;
+  df_two_sum(h, h2, s, e);
+  e = __fadd_rn(e, __fadd_rn(l, l2));
+  df_fast(s, e, h, l);
+}
+__device__ __forceinline__ void df_split(double x, float &h, float &l) {
+  h = __double2float_rn(x);
+  l = __double2float_rn(x - (double)h);
+}
+// running sum s + c of products p + e
+__device__ __forceinline__ void df_acc(float &s, float &c, float p, float e) {
+  float t, err;
+  df_two_sum(s, p, t, err);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
 // ------------------------------------------------------------- SpMV ------
 template <class T> struct vec2_t;
 template <> struct vec2_t<double> { typedef double2 type; };
@@ -197,6 +235,67 @@ static void spmv(const sim_ls_s *ls, const Tv *val, const Tx *x, const Tf *f, Ty
   unsigned g = grid_for(ls->nb, SPMV_WARPS * 32);
   k_bsr_spmv<Tv, Tx, Tf, Ty><<<g, SPMV_WARPS * 32, 0, s>>>(ls->nb, ls->rp.p, ls->ci.p, val, x, f, y);
   RS_LAUNCHED(1);
+}
+
+// w = A z for the double-float basis: the decoupled matrix as hi (val32) +
+// lo (vallo) FP32 planes, z FP32 (exact), each block's products and each
+// row's sum carried as double-float on the FP32 pipes (the FP64 SpMV above is
+// bound by the FP64 rate).  Same traversal as k_bsr_spmv; w goes straight into
+// its hi / lo planes (w, w + 2 nb).
+__global__ void __launch_bounds__(SPMV_WARPS * 32)
+k_bsr_spmv_df(int nb, const int *__restrict__ rp, const int *__restrict__ ci, const float *__restrict__ vh,
+              const float *__restrict__ vl, const float *__restrict__ x, float *__restrict__ w) {
+  __shared__ float2 prod[SPMV_WARPS][SPMV_CHUNK][2];
+  int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int r0 = (blockIdx.x * SPMV_WARPS + wid) * 32;
+  if (r0 >= nb) return;
+  int r = r0 + lane, rend = min(r0 + 32, nb);
+  int q0 = rp[r0], q1 = rp[rend];
+  int myq0 = r < nb ? rp[r] : q1, myq1 = r < nb ? rp[r + 1] : q1;
+  float a0h = 0.0f, a0l = 0.0f, a1h = 0.0f, a1l = 0.0f;
+  for (int c0 = q0; c0 < q1; c0 += SPMV_CHUNK) {
+    int c1 = min(c0 + SPMV_CHUNK, q1);
+    for (int q = c0 + lane; q < c1; q += 32) {
+      int c = __ldg(ci + q);
+      float2 xv = reinterpret_cast<const float2 *>(x)[c];
+      float4 bh = __ldg(reinterpret_cast<const float4 *>(vh) + q);
+      float4 bl = __ldg(reinterpret_cast<const float4 *>(vl) + q);
+      float p0, e0, p1, e1, h, l;
+      // row 0 of the block: b0 x0 + b1 x1
+      p0 = __fmul_rn(bh.x, xv.x); e0 = __fmaf_rn(bh.x, xv.x, -p0); e0 = __fmaf_rn(bl.x, xv.x, e0);
+      p1 = __fmul_rn(bh.y, xv.y); e1 = __fmaf_rn(bh.y, xv.y, -p1); e1 = __fmaf_rn(bl.y, xv.y, e1);
+      df_fast(p0, e0, h, l); df_add(h, l, p1, e1);
+      prod[wid][q - c0][0] = make_float2(h, l);
+      // row 1: b2 x0 + b3 x1
+      p0 = __fmul_rn(bh.z, xv.x); e0 = __fmaf_rn(bh.z, xv.x, -p0); e0 = __fmaf_rn(bl.z, xv.x, e0);
+      p1 = __fmul_rn(bh.w, xv.y); e1 = __fmaf_rn(bh.w, xv.y, -p1); e1 = __fmaf_rn(bl.w, xv.y, e1);
+      df_fast(p0, e0, h, l); df_add(h, l, p1, e1);
+      prod[wid][q - c0][1] = make_float2(h, l);
+    }
+    __syncwarp();
+    int s0 = max(myq0, c0), s1 = min(myq1, c1);
+    for (int q = s0; q < s1; q++) {
+      float2 u = prod[wid][q - c0][0], v = prod[wid][q - c0][1];
+      df_add(a0h, a0l, u.x, u.y);
+      df_add(a1h, a1l, v.x, v.y);
+    }
+    __syncwarp();
+  }
+  if (r < nb) {
+    size_t nu = 2 * (size_t)nb;
+    reinterpret_cast<float2 *>(w)[r] = make_float2(a0h, a1h);
+    reinterpret_cast<float2 *>(w + nu)[r] = make_float2(a0l, a1l);
+  }
+}
+static void spmv_df(const sim_ls_s *ls, const float *x, float *w, cudaStream_t s) {
+  unsigned g = grid_for(ls->nb, SPMV_WARPS * 32);
+  k_bsr_spmv_df<<<g, SPMV_WARPS * 32, 0, s>>>(ls->nb, ls->rp.p, ls->ci.p, ls->val32.p, ls->vallo.p, x, w);
+  RS_LAUNCHED(1);
+}
+// lo plane of the decoupled matrix: val - (double)val32
+__global__ void k_val_lo(size_t m, const double *val, const float *val32, float *lo) {
+  size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (k < m) lo[k] = __double2float_rn(val[k] - (double)val32[k]);
 }
 
 void ls_spmv64(sim_ls_s *ls, const double *x, double *y) {
@@ -330,6 +429,12 @@ void ls_setup(sim_ls_s *ls) {
     if (v32) rs_cast_d2f(ls->val.p, v32, 4 * (size_t)ls->nnzb, s);
   }
   RS_LAUNCHED(1);
+  if (v32) {                                 // the double-float SpMV's lo plane
+    size_t m4 = 4 * (size_t)ls->nnzb;
+    ls->vallo.ensure(m4);
+    k_val_lo<<<grid_for(m4, 256), 256, 0, s>>>(m4, ls->val.p, v32, ls->vallo.p);
+    RS_LAUNCHED(1);
+  }
   csr_dev<double> &A0 = ls->amg.lev[0].A;
   k_extract_app<<<grid_for(A0.nnz, 256), 256, 0, s>>>(A0.nnz, ls->app_src.p, ls->val.p, A0.v.p);
   RS_LAUNCHED(1);
@@ -492,39 +597,6 @@ __global__ void __launch_bounds__(ORTHO_BS) k_ortho_update(int nu, int nv, const
 // rate bounds the FP64 kernels above.  Scalars (h, norms, Givens) stay
 // FP64; the preconditioner reads a basis vector in FP32, which is its hi
 // plane.
-__device__ __forceinline__ void df_two_sum(float a, float b, float &s, float &e) {
-  s = __fadd_rn(a, b);
-  float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void df_fast(float a, float b, float &s, float &e) {   // |a| >= |b|
-  s = __fadd_rn(a, b);
-  e = __fsub_rn(b, __fsub_rn(s, a));
-}
-// (ah + al)(bh + bl) = p + e up to the dropped al bl
-__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &p, float &e) {
-  p = __fmul_rn(ah, bh);
-  e = __fmaf_rn(ah, bh, -p);
-  e = __fmaf_rn(ah, bl, e);
-  e = __fmaf_rn(al, bh, e);
-}
-__device__ __forceinline__ void df_add(float &h, float &l, float h2, float l2) {
-  float s, e;
-  df_two_sum(h, h2, s, e);
-  e = __fadd_rn(e, __fadd_rn(l, l2));
-  df_fast(s, e, h, l);
-}
-__device__ __forceinline__ void df_split(double x, float &h, float &l) {
-  h = __double2float_rn(x);
-  l = __double2float_rn(x - (double)h);
-}
-// running sum s + c of products p + e
-__device__ __forceinline__ void df_acc(float &s, float &c, float p, float e) {
-  float t, err;
-  df_two_sum(s, p, t, err);
-  s = t;
-  c = __fadd_rn(c, __fadd_rn(err, e));
-}
 // warp_sum8_d for pairs: lane l ends with the total of the same slot
 __device__ __forceinline__ void warp_sum8_df(const float *ah, const float *al, int lane, float &rh, float &rl) {
   float bh[4], bl[4], ch[2], cl[2];
@@ -696,11 +768,6 @@ __global__ void __launch_bounds__(ORTHO_BS, 4) k_ortho_update_df(int nu, int ch,
     for (int q = 0; q < ORTHO_BS / 32; q++) tot += sred[q];
     part[blockIdx.x] = tot;
   }
-}
-// w (FP64, from the SpMV) into pair planes
-__global__ void k_split_w(int nu, const double *w64, float *w) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nu) { float h, l; df_split(w64[i], h, l); w[i] = h; w[(size_t)nu + i] = l; }
 }
 // V_{j+1} = w / h_{j+1,j}, the reciprocal split once by k_arnoldi_col (isp)
 __global__ void k_scale_df(int nu, const float *w, const float *isp, float *V, int j1, const int *jd) {
@@ -904,8 +971,7 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
     int nv = jdp ? 0 : j + 1;
     double *part = ls->partial.p;
     if (df) {
-      float *w2 = ls->w2.p;
-      k_split_w<<<grid_for(nu, 256), 256, 0, c>>>(nu, ls->w.p, w2);
+      float *w2 = ls->w2.p;                    // written by the double-float SpMV
       ortho_dots_df(nu, chd, nv, V32, w2, part, 1, nullptr, nblk, c, jdp);
       reduce_parts(nv + 1, nblk, part, h1, nullptr, c, jdp, 1);          // h1[nv] = ||w||^2
       ortho_update_df(nu, chd, nv, V32, w2, h1, part, nullptr, nblk, c, jdp);
@@ -918,7 +984,7 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
       k_arnoldi_col<<<1, 1, 0, c>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, jdp ? hp_dev : hp_dev + 4 * j, jdp,
                                     ls->isp.p);
       k_scale_df<<<grid_for(nu, 256), 256, 0, c>>>(nu, w2, ls->isp.p, V32, j + 1, jdp);
-      RS_LAUNCHED(12);
+      RS_LAUNCHED(11);
     } else {
       ortho_dots(nu, nv, ls->V.p, ls->w.p, part, 1, nullptr, nblk, c, jdp);
       reduce_parts(nv + 1, nblk, part, h1, nullptr, c, jdp, 1);
@@ -943,7 +1009,7 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
       float *zj = ls->Z32.p + (size_t)j * nu;
       ls_cpr32(ls, V32 + (size_t)(2 * j) * nu, zj);
       rs_timed tm(ls, SIM_T_SPMV64);
-      spmv<double, float, double, double>(ls, ls->val.p, zj, (const double *)nullptr, ls->w.p, s);
+      spmv_df(ls, zj, ls->w2.p, s);
     } else if (mixed) {          // FP64 basis with the FP32 preconditioner
       float *zj = ls->Z32.p + (size_t)j * nu;
       ls_cpr(ls, ls->V.p + (size_t)j * nu, nullptr, zj);
@@ -993,7 +1059,7 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
         ls_cpr32(ls, ls->vcur32.p, ls->zcur32.p);
         {
           rs_timed tm(ls, SIM_T_SPMV64);
-          spmv<double, float, double, double>(ls, ls->val.p, ls->zcur32.p, (const double *)nullptr, ls->w.p, c);
+          spmv_df(ls, ls->zcur32.p, ls->w2.p, c);
         }
         k_basis_put<float><<<grid_for(nu, 256), 256, 0, c>>>(nu, ls->zcur32.p, ls->Z32.p, jd);
       } else if (mixed) {
