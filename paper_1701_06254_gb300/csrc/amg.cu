@@ -30,6 +30,23 @@ __global__ void k_tpos(int n, const int *rp, const int *ci, int *tpos, int *err)
   }
 }
 
+// the same with one warp per row (levels with long rows: a thread walking
+// 40 binary searches one after another was latency-bound)
+__global__ void k_tpos_warp(int n, const int *rp, const int *ci, int *tpos, int *err) {
+  int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= n) return;
+  for (int q = rp[i] + lane; q < rp[i + 1]; q += 32) {
+    int j = ci[q], lo = rp[j], hi = rp[j + 1] - 1, pos = -1;
+    while (lo <= hi) {
+      int mid = (lo + hi) >> 1, c = ci[mid];
+      if (c == i) { pos = mid; break; }
+      if (c < i) lo = mid + 1; else hi = mid - 1;
+    }
+    if (pos < 0) atomicExch(err, 1);
+    tpos[q] = pos < 0 ? q : pos;
+  }
+}
+
 __global__ void k_strength(int n, const int *rp, const int *ci, const double *v, double theta, uint8_t *S) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -206,6 +223,37 @@ __global__ void k_sort_rows(int n, const int *rp, int *ci, double *v) {
     int c = ci[a]; double x = v[a]; int b = a - 1;
     while (b >= a0 && ci[b] > c) { ci[b + 1] = ci[b]; v[b + 1] = v[b]; b--; }
     ci[b + 1] = c; v[b + 1] = x;
+  }
+}
+
+// one warp per row: rows of at most 32 entries by a bitonic network across
+// the lanes (columns within a row are distinct, so the order is unique),
+// longer rows by the first lane as above
+__global__ void k_sort_rows_warp(int n, const int *rp, int *ci, double *v) {
+  int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= n) return;
+  int a0 = rp[i], len = rp[i + 1] - a0;
+  if (len <= 32) {
+    int c = lane < len ? ci[a0 + lane] : INT_MAX;
+    double x = lane < len ? v[a0 + lane] : 0.0;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        int oc = __shfl_xor_sync(0xffffffffu, c, j);
+        double ox = __shfl_xor_sync(0xffffffffu, x, j);
+        bool up = (lane & k) == 0, lower = (lane & j) == 0;
+        bool take = lower == up ? oc < c : oc > c;     // keep the smaller key on the ascending side
+        if (take) { c = oc; x = ox; }
+      }
+    if (lane < len) { ci[a0 + lane] = c; v[a0 + lane] = x; }
+  } else if (lane == 0) {
+    int a1 = a0 + len;
+    for (int a = a0 + 1; a < a1; a++) {
+      int c = ci[a]; double x = v[a]; int b = a - 1;
+      while (b >= a0 && ci[b] > c) { ci[b + 1] = ci[b]; v[b + 1] = v[b]; b--; }
+      ci[b + 1] = c; v[b + 1] = x;
+    }
   }
 }
 
@@ -453,6 +501,48 @@ __global__ void k_dense_lu_inv(int n, double *a, int *piv, double *inv) {
   }
 }
 
+// k_dense_lu_inv with the matrix in shared memory (n <= 128: at most
+// 128 KB); the same operations in the same order
+__global__ void k_dense_lu_inv_smem(int n, const double *ag, int *piv, double *inv) {
+  extern __shared__ double sa[];
+  __shared__ double smx[512]; __shared__ int sid[512]; __shared__ int spiv[128];
+  int t = threadIdx.x, nt = blockDim.x;
+  for (int e = t; e < n * n; e += nt) sa[e] = ag[e];
+  __syncthreads();
+  for (int k = 0; k < n; k++) {
+    double best = -1.0; int bi = n;
+    for (int i = k + t; i < n; i += nt) { double x = fabs(sa[i * n + k]); if (x > best) { best = x; bi = i; } }
+    smx[t] = best; sid[t] = bi;
+    __syncthreads();
+    for (int o = nt >> 1; o > 0; o >>= 1) {
+      if (t < o) {
+        double x = smx[t + o]; int xi = sid[t + o];
+        if (x > smx[t] || (x == smx[t] && xi < sid[t])) { smx[t] = x; sid[t] = xi; }
+      }
+      __syncthreads();
+    }
+    int p = sid[0];
+    if (t == 0) { piv[k] = p; spiv[k] = p; }
+    if (p != k)
+      for (int j = t; j < n; j += nt) { double x = sa[k * n + j]; sa[k * n + j] = sa[p * n + j]; sa[p * n + j] = x; }
+    __syncthreads();
+    for (int i = k + 1 + t; i < n; i += nt) sa[i * n + k] = div_rn(sa[i * n + k], sa[k * n + k]);
+    __syncthreads();
+    for (int e = t; e < (n - k - 1) * (n - k - 1); e += nt) {
+      int i = k + 1 + e / (n - k - 1), j = k + 1 + e % (n - k - 1);
+      sa[i * n + j] = sub_rn(sa[i * n + j], mul_rn(sa[i * n + k], sa[k * n + j]));
+    }
+    __syncthreads();
+  }
+  for (int c = t; c < n; c += nt) {
+    double *x = inv + (size_t)c * n;            // stored transposed: inv[c][i] = (A^{-1})_{ic}
+    for (int i = 0; i < n; i++) x[i] = (i == c) ? 1.0 : 0.0;
+    for (int k = 0; k < n; k++) if (spiv[k] != k) { double y = x[k]; x[k] = x[spiv[k]]; x[spiv[k]] = y; }
+    for (int i = 0; i < n; i++) { double s = x[i]; for (int j = 0; j < i; j++) s -= sa[i * n + j] * x[j]; x[i] = s; }
+    for (int i = n - 1; i >= 0; i--) { double s = x[i]; for (int j = i + 1; j < n; j++) s -= sa[i * n + j] * x[j]; x[i] = s / sa[i * n + i]; }
+  }
+}
+
 // ----------------------------------------------------------- host setup ---
 static void csr_cast(const csr_dev<double> &a, csr_dev<float> &b, cudaStream_t s) {
   b.n = a.n; b.m = a.m; b.nnz = a.nnz;
@@ -480,7 +570,8 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
     L.nc = 0; L.rounds = 0;
     if (n <= o.coarse_max || l == o.max_levels - 1) { h.coarse_dense = 1; break; }
     rs_fill_i(h.flag.p, 0, 4 + 1025, s);
-    k_tpos<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.tpos.p, h.flag.p + 1);
+    if (L.A.nnz > 8LL * n) k_tpos_warp<<<grid_for((size_t)n * 32, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.tpos.p, h.flag.p + 1);
+    else k_tpos<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.tpos.p, h.flag.p + 1);
     k_strength<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, o.theta, L.strong.p);
     h.hashw.ensure(n); h.newc.ensure(n);
     k_pmis_init<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, o.seed, l,
@@ -554,7 +645,7 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
     RS_CUDA(cudaMemcpyAsync(L.R.rp.p + nc, &L.R.nnz, sizeof(int), cudaMemcpyHostToDevice, s));
     k_transpose_fill<<<grid_for(n, 256), 256, 0, s>>>(n, L.P.rp.p, L.P.ci.p, L.P.v.p, L.R.rp.p, fill.p, L.R.ci.p,
                                                       L.R.v.p);
-    k_sort_rows<<<grid_for(nc, 128), 128, 0, s>>>(nc, L.R.rp.p, L.R.ci.p, L.R.v.p);
+    k_sort_rows_warp<<<grid_for((size_t)nc * 32, 128), 128, 0, s>>>(nc, L.R.rp.p, L.R.ci.p, L.R.v.p);
     RS_LAUNCHED(2);
     // A_{l+1} = R (A P)
     static thread_local csr_dev<double> AP;
@@ -572,7 +663,16 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
     static thread_local dbuf<double> a;
     a.ensure((size_t)n * n); h.lu.ensure((size_t)n * n); h.piv.ensure(n);
     k_dense_build<<<grid_for(n, 128), 128, 0, s>>>(n, C.A.rp.p, C.A.ci.p, C.A.v.p, a.p);
-    k_dense_lu_inv<<<1, 512, 0, s>>>(n, a.p, h.piv.p, h.lu.p);
+    if (n <= 128) {
+      static bool attr = false;
+      if (!attr) {
+        RS_CUDA(cudaFuncSetAttribute(k_dense_lu_inv_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 8));
+        attr = true;
+      }
+      k_dense_lu_inv_smem<<<1, 512, (size_t)n * n * 8, s>>>(n, a.p, h.piv.p, h.lu.p);
+    } else {
+      k_dense_lu_inv<<<1, 512, 0, s>>>(n, a.p, h.piv.p, h.lu.p);
+    }
     RS_LAUNCHED(2);
   }
   RS_CHECK_LAUNCH();
