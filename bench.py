@@ -227,6 +227,32 @@ def measure_variant(R, torch, case, opts, args, ws=None):
     return out
 
 
+# ---- cross-rank reductions (one process per GPU; gloo on CPU in the tests)
+def rank_max(x, dist, device):
+    """Largest x over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_sum(x, dist, device):
+    """Sum of x over all ranks (units processed by the whole job)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def ensemble_seed0(rank, members):
+    """First member seed of a rank: ranks draw disjoint seed ranges."""
+    return 2000 + rank * members
+
+
 def run_ensemble(args, rank, world, local):
     """--members independent models (grids drawn from U{32..128}^2 x U{8..32},
     seeds 2000 + k) advanced together by the ensemble driver.  Each rank of a
@@ -248,7 +274,7 @@ def run_ensemble(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     prec = {"mixed": R.PREC_MIXED, "mixed_bf16": R.PREC_MIXED_BF16, "fp64": R.PREC_FP64}[args.precision]
-    cases = I.ensemble(args.members, seed0=2000 + rank * args.members)
+    cases = I.ensemble(args.members, seed0=ensemble_seed0(rank, args.members))
     cells = sum(c.n for c in cases)
     auto = args.workers == "auto"
     batch = R.Batch(cases, workers=0 if auto else int(args.workers), precision=prec, max_lin=args.max_lin)
@@ -273,21 +299,20 @@ def run_ensemble(args, rank, world, local):
     sec = time.perf_counter() - t0
     ck = clocks.stop()
     launches = R.launch_count() - l0
-    if dist:
-        t = torch.tensor([sec], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec = float(t.item())
+    sec = rank_max(sec, dist, "cuda")
+    cells_all = rank_sum(cells, dist, "cuda")           # each rank's members differ in size
     st1 = [m.stats() for m in batch.members]
     newton = sum(b["newton"] - a["newton"] for a, b in zip(st0, st1))
     lin = sum(b["linear_its"] - a["linear_its"] for a, b in zip(st0, st1))
     if rank == 0:
         line = {
-            "metric": METRIC, "value": world * cells * args.steps / sec, "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": cells_all * args.steps / sec, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"mixed": "f64+f32", "mixed_bf16": "f64+f32+bf16", "fp64": "f64"}[args.precision],
             "data": "synthetic",
             "config": {"workload": f"ensemble_{args.members}", "members": args.members, "cells": cells,
+                       "cells_all_ranks": int(cells_all),
                        "precision": args.precision, "workers": batch.workers, "autotune": tuned,
                        "timer": "host clock between device-wide synchronisations (members on their own streams)",
                        "newton_per_member_step": newton / (len(cases) * args.steps),
@@ -395,10 +420,8 @@ def main():
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
     launches = R.launch_count() - l0
+    ms = rank_max(ms, dist, "cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     st1 = sim.stats()
     nk, kms = sim.ls.kernel_time(fam)
@@ -451,10 +474,7 @@ def main():
             tt = sim.get_state((hp, hs, hb))[3]
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = rank_max(te, dist, "cuda")
         e2e = {"value": world * case.n * args.steps / te, "unit": UNIT,
                "h2d_bytes_per_step": (2 * case.n + nw) * 8, "d2h_bytes_per_step": (2 * case.n + nw) * 8}
 
