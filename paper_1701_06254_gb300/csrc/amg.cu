@@ -161,10 +161,11 @@ __global__ void k_pmis_update_lanes(int n, const int *rp, const int *ci, const u
   atomicAdd(undecided, 1);
 }
 
-// lanes per row for the PMIS steps: one thread for short rows
+// lanes per row for the PMIS steps: one thread for short rows, then the
+// V-cycle's counts (4 lanes for 9-24 entries, 16 beyond)
 static int pmis_lanes(long long nnz, int n) {
   double avg = n ? (double)nnz / n : 0.0;
-  return avg <= 8.0 ? 1 : avg <= 12.0 ? 8 : avg <= 24.0 ? 16 : 32;
+  return avg <= 8.0 ? 1 : avg <= 24.0 ? 4 : 16;
 }
 
 __global__ void k_cflag(int n, const int8_t *cf, int *flag) {
@@ -601,7 +602,7 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
             k_pmis_update_lanes<LL><<<gl, 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, h.newc.p,     \
                                                        cnt + r + 1, cnt + r);                                   \
           }
-          PMIS_LANES(8) PMIS_LANES(16) PMIS_LANES(32)
+          PMIS_LANES(4) PMIS_LANES(16)
 #undef PMIS_LANES
         }
       }
