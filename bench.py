@@ -122,6 +122,31 @@ def spmv_bytes(nb, nnzb, val_b, x_b, f_b, y_b):
     return nnzb * (val_b + 4) + (nb + 1) * 4 + 2 * nb * (x_b + f_b + y_b)
 
 
+def vcycle_bytes(ls, precision):
+    """Algorithmic bytes of one V-cycle: on every level but the coarsest the
+    pre- and post-smoothing sweeps each read A_l (value + column) and its row
+    pointers once, the restriction reads R = P^T, the prolongation P, and
+    each sweep reads / writes its vectors once (pre: f, D^-1 in, x, r out;
+    restriction: r in, f_c, D_c^-1 f_c out and D_c^-1 in; prolongation: x,
+    e in, t out; post: f, t, D^-1 in, x out); the coarsest level reads its
+    dense FP64 inverse."""
+    vb = 8 if precision == "fp64" else 4
+    total = 0
+    nlev = ls.amg_nlev()
+    for l in range(nlev):
+        d = ls.amg_level(l)
+        n, nnz = d["n"], d["nnz"]
+        if l == nlev - 1:
+            total += (n * n * 8 + 2 * n * vb) if d["coarse_dense"] else 10 * (nnz * (vb + 4) + (n + 1) * 4 + 4 * n * vb)
+            break
+        nc, nnzP = d["nc"], d["nnzP"]
+        a = nnz * (vb + 4) + (n + 1) * 4
+        total += 2 * a + 8 * n * vb                              # pre + post: matrix twice, 8 vectors
+        total += nnzP * (vb + 4) + (nc + 1) * 4 + n * vb + 3 * nc * vb      # restriction
+        total += nnzP * (vb + 4) + (n + 1) * 4 + 2 * n * vb + nc * vb       # prolongation
+    return total
+
+
 def oracle_newton_iteration(case, opts):
     """One Newton iteration of the CPU oracle on the first time step of the
     case (assembly + decoupling + reordering + RAS/AMG setup + CPR-FGMRES)."""
@@ -352,6 +377,8 @@ def main():
                     help="skip the plain-FP64 and mixed+learned comparison runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra-rooflines", action="store_true",
+                    help="skip the extra step that times the SpMVs and the V-cycle for their rooflines")
     ap.add_argument("--breakdown", action="store_true",
                     help="time every kernel family with CUDA events (adds event records between launches)")
     args = ap.parse_args()
@@ -450,13 +477,32 @@ def main():
     elif args.roofline == "spmv64":
         bpl = spmv_bytes(nb, nnzb, 32, 8 if args.precision == "fp64" else 4, 0, 8)
     else:
-        bpl = spmv_bytes(nb, nnzb, 32, 8, 8, 8) if args.precision == "fp64" else spmv_bytes(nb, nnzb, 16, 4, 8, 4)
+        bpl = spmv_bytes(nb, nnzb, 32, 8, 8, 8) if args.precision == "fp64" else spmv_bytes(nb, nnzb, 16, 4, 4, 4)
     peak, src = peaks()
     achieved = bpl / (kms / nk * 1e-3) / 1e9 if nk else 0.0
     roof = {"kernel": args.roofline, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": src, "traffic": NCU_TRAFFIC.get((args.roofline, args.precision)),
             "launches": nk,
             "ms_per_launch": kms / nk if nk else None, "algorithmic_bytes_per_launch": bpl}
+
+    # the other memory-bound kernels: one more step with their timers on
+    # (a pass of its own, so that the timed steps carry one timer family only)
+    rooflines = None
+    if not args.no_extra_rooflines:
+        others = [("spmv_prec", R.T_SPMV_PREC,
+                   spmv_bytes(nb, nnzb, 32, 8, 8, 8) if args.precision == "fp64" else spmv_bytes(nb, nnzb, 16, 4, 4, 4)),
+                  ("spmv_w", R.T_SPMV64, spmv_bytes(nb, nnzb, 32, 8 if args.precision == "fp64" else 4, 0, 8)),
+                  ("vcycle", R.T_VCYCLE, vcycle_bytes(sim.ls, args.precision))]
+        sim.ls.kernel_timer([f for _, f, _ in others])
+        sim.advance(1)
+        rooflines = {}
+        for name, f, b in others:
+            n_, t_ = sim.ls.kernel_time(f)
+            ach = b / (t_ / n_ * 1e-3) / 1e9 if n_ else 0.0
+            rooflines[name] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                               "ms_per_launch": t_ / n_ if n_ else None, "algorithmic_bytes_per_launch": b,
+                               "launches": n_}
+        sim.ls.kernel_timer(fams)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -511,7 +557,8 @@ def main():
                        "l2": "working set larger than L2 (no flush needed)",
                        "newton_per_step": newton_per_step, "fgmres_its_per_newton": its_per_newton,
                        "ras_levels": ras_levels},
-            "roofline": roof, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
+            "roofline": roof, "rooflines_other": rooflines, "gpu_launches": launches, "e2e": e2e,
+            "cpu_baseline": cpu, "clocks": ck,
             "phases_ms_per_step": {k: (st1[k] - st0[k]) / args.steps for k in ("ms_assemble", "ms_setup", "ms_solve")},
             "warm_start": ({"used": st1["ws_used"] - st0["ws_used"], "fallback": st1["ws_fallback"] - st0["ws_fallback"],
                             "mean_r0": (st1["ws_r0"] - st0["ws_r0"]) / max(1, st1["linear_solves"] - st0["linear_solves"])}

@@ -201,6 +201,7 @@ k_bsr_spmv(int nb, const int *__restrict__ rp, const int *__restrict__ ci, const
   typedef typename vec2_t<Tx>::type X2;
   for (int c0 = q0; c0 < q1; c0 += SPMV_CHUNK) {
     int c1 = min(c0 + SPMV_CHUNK, q1);
+#pragma unroll 4
     for (int q = c0 + lane; q < c1; q += 32) {
       int c = __ldg(ci + q);
       X2 xv = reinterpret_cast<const X2 *>(x)[c];
@@ -255,6 +256,7 @@ k_bsr_spmv_df(int nb, const int *__restrict__ rp, const int *__restrict__ ci, co
   float a0h = 0.0f, a0l = 0.0f, a1h = 0.0f, a1l = 0.0f;
   for (int c0 = q0; c0 < q1; c0 += SPMV_CHUNK) {
     int c1 = min(c0 + SPMV_CHUNK, q1);
+#pragma unroll 4
     for (int q = c0 + lane; q < c1; q += 32) {
       int c = __ldg(ci + q);
       float2 xv = reinterpret_cast<const float2 *>(x)[c];
