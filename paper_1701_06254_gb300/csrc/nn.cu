@@ -211,6 +211,133 @@ __global__ void __launch_bounds__(128) k_conv(int nx, int ny, int nz, const bf16
     }
 }
 
+// ------------------------------------------- halo-tiled forward conv ------
+// The forward contraction (MODE 0 / 1 of k_conv) with the input read once per
+// tile: a CTA owns an 8 x 4 x 4 box of output voxels (row r = x + 8 y + 32 z,
+// warp w = z-slice w), stages the 10 x 6 x 6 input halo in shared memory
+// (cp.async, zero-filled outside the grid) and, for each of the 27 taps,
+// reads its A fragments straight from the halo with per-lane ldmatrix row
+// addresses (the shifted voxel of each output row), so only the tap's
+// weights stream per tap (two stages).  k_conv gathers 128 shifted rows per
+// tap instead, 27 reads of the input per tile.  MMAs are issued in the same
+// tap / K order as k_conv.
+constexpr int HX = 8, HY = 4, HZ = 4;                         // output box
+constexpr int HHX = HX + 2, HHY = HY + 2, HHZ = HZ + 2, HNV = HHX * HHY * HHZ;
+template <int CI, int NT>
+struct halo_smem {
+  static constexpr int AST = CI + 8, BST = CI + 8, CO = NT * 8;
+  static constexpr int A_EL = HNV * AST, B_EL = CO * BST;
+  static constexpr int BYTES = (A_EL + 2 * B_EL) * 2;
+};
+template <int CI, int NT, int MODE>
+__global__ void __launch_bounds__(128) k_conv_halo(int nx, int ny, int nz, const bf16 *__restrict__ X, int ldx,
+                                                   int offx, const bf16 *__restrict__ Wt,
+                                                   const float *__restrict__ bias, int relu, void *out, int ldo,
+                                                   int offo) {
+  typedef halo_smem<CI, NT> S;
+  constexpr int CO = NT * 8, CH = CI / 8;
+  constexpr int BJ = (CO * CH + 127) / 128;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  bf16 *sA = reinterpret_cast<bf16 *>(smraw);
+  bf16 *sB = sA + S::A_EL;
+  const int tx = (nx + HX - 1) / HX, ty = (ny + HY - 1) / HY;
+  const int bx = blockIdx.x % tx, by = (blockIdx.x / tx) % ty, bz = blockIdx.x / (tx * ty);
+  const int X0 = bx * HX, Y0 = by * HY, Z0 = bz * HZ;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  // the halo: HNV voxels x CH chunks of 16 bytes
+  for (int q = t; q < HNV * CH; q += 128) {
+    int h = q / CH, ch = q % CH;
+    int hx = h % HHX, hy = (h / HHX) % HHY, hz = h / (HHX * HHY);
+    int x = X0 + hx - 1, y = Y0 + hy - 1, z = Z0 + hz - 1;
+    bool ok = x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz;
+    const bf16 *src = ok ? X + ((size_t)(x + nx * (y + ny * z)) * ldx + offx + ch * 8) : X;
+    cp_async16(sA + h * S::AST + ch * 8, src, ok ? 16 : 0);
+  }
+  auto loadw = [&](int stage, int tap) {
+    bf16 *b = sB + stage * S::B_EL;
+    const bf16 *w = Wt + (size_t)tap * CO * CI;
+#pragma unroll
+    for (int j = 0; j < BJ; j++) {
+      int q = j * 128 + t;
+      if (q < CO * CH) {
+        int o = q / CH, ch = q % CH;
+        cp_async16(b + o * S::BST + ch * 8, w + o * CI + ch * 8, 16);
+      }
+    }
+  };
+  loadw(0, 0);
+  cp_commit();
+  // halo row of output row (warp, mt, lane & 15) at the centre tap
+  int hbase[2];
+#pragma unroll
+  for (int mt = 0; mt < 2; mt++) {
+    int r = warp * 32 + mt * 16 + (lane & 15);
+    int x = r % HX, y = (r / HX) % HY, z = r / (HX * HY);
+    hbase[mt] = (x + 1) + HHX * ((y + 1) + HHY * (z + 1));
+  }
+  float acc[2][NT][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+    for (int nt = 0; nt < NT; nt++)
+#pragma unroll
+      for (int e = 0; e < 4; e++) acc[mt][nt][e] = 0.f;
+  for (int tap = 0; tap < 27; tap++) {
+    if (tap + 1 < 27) { loadw((tap + 1) & 1, tap + 1); cp_commit(); cp_wait<1>(); }
+    else cp_wait<0>();
+    __syncthreads();
+    const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
+    const int shift = dx + HHX * (dy + HHY * dz);
+    const bf16 *b = sB + (tap & 1) * S::B_EL;
+#pragma unroll
+    for (int ks = 0; ks < CI / 16; ks++) {
+      unsigned af[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; mt++)
+        ldsm_x4(af[mt], sA + (hbase[mt] + shift) * S::AST + ks * 16 + (lane >> 4) * 8);
+      unsigned bfr[NT][2];
+      if constexpr (NT == 1) {
+        ldsm_x2(bfr[0], b + (lane & 7) * S::BST + ks * 16 + ((lane >> 3) & 1) * 8);
+      } else {
+#pragma unroll
+        for (int np = 0; np < NT / 2; np++) {
+          unsigned r[4];
+          ldsm_x4(r, b + (np * 16 + (lane & 7) + ((lane >> 4) << 3)) * S::BST + ks * 16 + ((lane >> 3) & 1) * 8);
+          bfr[2 * np][0] = r[0]; bfr[2 * np][1] = r[1];
+          bfr[2 * np + 1][0] = r[2]; bfr[2 * np + 1][1] = r[3];
+        }
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+        for (int nt = 0; nt < NT; nt++) mma16816(acc[mt][nt], af[mt], bfr[nt]);
+    }
+    __syncthreads();                                  // the weight stage is reloaded two taps later
+  }
+#pragma unroll
+  for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+    for (int hh = 0; hh < 2; hh++) {
+      int r = warp * 32 + mt * 16 + (lane >> 2) + hh * 8;
+      int x = X0 + r % HX, y = Y0 + (r / HX) % HY, z = Z0 + r / (HX * HY);
+      if (x >= nx || y >= ny || z >= nz) continue;
+      size_t v = (size_t)x + (size_t)nx * (y + (size_t)ny * z);
+#pragma unroll
+      for (int nt = 0; nt < NT; nt++) {
+        int o = nt * 8 + (lane & 3) * 2;
+        float y0 = acc[mt][nt][2 * hh] + bias[o], y1 = acc[mt][nt][2 * hh + 1] + bias[o + 1];
+        if (MODE == 0 && relu) { y0 = fmaxf(y0, 0.f); y1 = fmaxf(y1, 0.f); }
+        if (MODE == 1) {
+          float *op = reinterpret_cast<float *>(out) + v * ldo + offo + o;
+          op[0] = y0; op[1] = y1;
+        } else {
+          *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<bf16 *>(out) + v * ldo + offo + o) =
+              __floats2bfloat162_rn(y0, y1);
+        }
+      }
+    }
+}
+
 // ------------------------------------------ implicit-GEMM conv, tcgen05 ---
 // The same contraction on the 5th-generation tensor cores: per CTA a tile of
 // 128 voxels (M) against CO output channels (N = 32 or 64), K = 27 taps x CI.
@@ -765,6 +892,21 @@ static void conv_launch(sim_ws_s *w, dims d, const bf16 *X, int ldx, int offx, c
   RS_LAUNCHED(1);
 }
 
+template <int CI, int NT, int MODE>
+static void conv_halo_launch(sim_ws_s *w, dims d, const bf16 *X, int ldx, int offx, const bf16 *Wt, const float *bias,
+                             int relu, void *out, int ldo, int offo) {
+  static bool attr = false;
+  int bytes = halo_smem<CI, NT>::BYTES;
+  if (!attr) {
+    RS_CUDA(cudaFuncSetAttribute(k_conv_halo<CI, NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    attr = true;
+  }
+  unsigned tiles = (unsigned)(((d.nx + HX - 1) / HX) * ((d.ny + HY - 1) / HY) * ((d.nz + HZ - 1) / HZ));
+  k_conv_halo<CI, NT, MODE><<<tiles, 128, bytes, w->st>>>(d.nx, d.ny, d.nz, X, ldx, offx, Wt, bias, relu, out, ldo,
+                                                           offo);
+  RS_LAUNCHED(1);
+}
+
 template <int CI, int CO, int MODE>
 static void conv_tc_launch(sim_ws_s *w, dims d, const bf16 *X, int ldx, int offx, const bf16 *Wt, const float *bias,
                            int relu, void *out, int ldo, int offo, const bf16 *mask, int ldm, int offm) {
@@ -791,15 +933,15 @@ static void fwd(sim_ws_s *w, int l, dims d, const bf16 *X, int ldx, int offx, vo
   const bf16 *Wt = w->Wf.p + w->wfoff[l];
   const float *b = w->P.p + w->boff[l];
   int ci = LAYERS[l].ci;
-  if (l == HEAD) conv_launch<32, 1, 1>(w, d, X, ldx, offx, Wt, b, 0, out, ldo, offo, nullptr, 0, 0);
+  if (l == HEAD) conv_halo_launch<32, 1, 1>(w, d, X, ldx, offx, Wt, b, 0, out, ldo, offo);
   else if (w->tc) {
     if (ci == 16) conv_tc_launch<16, 32, 0>(w, d, X, ldx, offx, Wt, b, 1, out, ldo, offo, nullptr, 0, 0);
     else if (ci == 32) conv_tc_launch<32, 32, 0>(w, d, X, ldx, offx, Wt, b, 1, out, ldo, offo, nullptr, 0, 0);
     else conv_tc_launch<64, 32, 0>(w, d, X, ldx, offx, Wt, b, 1, out, ldo, offo, nullptr, 0, 0);
   }
-  else if (ci == 16) conv_launch<16, 4, 0>(w, d, X, ldx, offx, Wt, b, 1, out, ldo, offo, nullptr, 0, 0);
-  else if (ci == 32) conv_launch<32, 4, 0>(w, d, X, ldx, offx, Wt, b, 1, out, ldo, offo, nullptr, 0, 0);
-  else conv_launch<64, 4, 0>(w, d, X, ldx, offx, Wt, b, 1, out, ldo, offo, nullptr, 0, 0);
+  else if (ci == 16) conv_halo_launch<16, 4, 0>(w, d, X, ldx, offx, Wt, b, 1, out, ldo, offo);
+  else if (ci == 32) conv_halo_launch<32, 4, 0>(w, d, X, ldx, offx, Wt, b, 1, out, ldo, offo);
+  else conv_halo_launch<64, 4, 0>(w, d, X, ldx, offx, Wt, b, 1, out, ldo, offo);
 }
 
 // data gradient of layer l: dZ (ldz, offz) -> dX (ldo, offo), masked by the
