@@ -261,11 +261,13 @@ def test_whole_run_inexact_newton():
     lambda: I.small_case(2, 1, 1, seed=61),
     lambda: I.small_case(17, 9, 2, seed=62),
 ])
-def test_edge_grids_run(mk):
+@pytest.mark.parametrize("prec", [R.PREC_FP64, R.PREC_MIXED_BF16], ids=["fp64", "bf16"])
+def test_edge_grids_run(mk, prec):
     """Degenerate and ragged grids: a single cell without wells, two cells,
-    tiles that do not divide the grid."""
+    tiles that do not divide the grid; in FP64 and in mixed precision (the
+    double-float Krylov basis and SpMV with a single ragged block)."""
     c = mk()
-    _run_compare(c, 2)
+    _run_compare(c, 2, precision=prec)
 
 
 def test_residual_norm_entry_point():
