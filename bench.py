@@ -115,7 +115,8 @@ def ras_bytes(ls, precision):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # ncu capture summarised in profiles/ (null once the kernel changes)
-NCU_TRAFFIC = {("ras", "mixed_bf16"): 172.9e6, ("spmv_prec", "mixed_bf16"): 172.7e6}
+NCU_TRAFFIC = {("ras", "mixed_bf16"): 172.9e6, ("spmv_prec", "mixed_bf16"): 164.3e6,
+               ("spmv64", "mixed_bf16"): 273.4e6}
 
 
 def spmv_bytes(nb, nnzb, val_b, x_b, f_b, y_b):
@@ -499,9 +500,10 @@ def main():
         for name, f, b in others:
             n_, t_ = sim.ls.kernel_time(f)
             ach = b / (t_ / n_ * 1e-3) / 1e9 if n_ else 0.0
+            key = {"spmv_prec": "spmv_prec", "spmv_w": "spmv64"}.get(name)
             rooflines[name] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                                "ms_per_launch": t_ / n_ if n_ else None, "algorithmic_bytes_per_launch": b,
-                               "launches": n_}
+                               "launches": n_, "traffic": NCU_TRAFFIC.get((key, args.precision))}
         sim.ls.kernel_timer(fams)
 
     # end to end through the public API with host buffers
