@@ -327,9 +327,46 @@ def run_ensemble(args, rank, world, local):
     launches = R.launch_count() - l0
     sec = rank_max(sec, dist, "cuda")
     cells_all = rank_sum(cells, dist, "cuda")           # each rank's members differ in size
+    workers_used = batch.workers
     st1 = [m.stats() for m in batch.members]
     newton = sum(b["newton"] - a["newton"] for a, b in zip(st0, st1))
     lin = sum(b["linear_its"] - a["linear_its"] for a, b in zip(st0, st1))
+    # the same ensemble with the learned warm start: the network is trained
+    # first (outside the timing) and every member gets its own copy of it
+    # (same parameters; a network serves one caller at a time, so members
+    # sharing one would queue on it)
+    variants = None
+    if not args.no_variants:
+        del batch
+        ws, info = train_warm_start(R, args, dict(precision=prec, max_lin=args.max_lin))
+        params = ws.params()
+        b2 = R.Batch(cases, workers=workers_used, precision=prec, max_lin=args.max_lin)
+        b2.init_hydrostatic()
+        copies = []
+        for m in b2.members:
+            w = R.WarmStart(seed=7)
+            w.set_params(params)
+            copies.append(w)
+            m.attach_warm_start(w)
+        for _ in range(args.warmup):
+            b2.advance(1)
+        s0 = [m.stats() for m in b2.members]
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t1 = time.perf_counter()
+        for _ in range(args.steps):
+            b2.advance(1)
+        torch.cuda.synchronize()
+        sec2 = rank_max(time.perf_counter() - t1, dist, "cuda")
+        s1 = [m.stats() for m in b2.members]
+        n2 = sum(b["newton"] - a["newton"] for a, b in zip(s0, s1))
+        variants = {"learned": {"value": cells_all * args.steps / sec2, "ms_per_step": sec2 * 1e3 / args.steps,
+                                "fgmres_its_per_newton": sum(b["linear_its"] - a["linear_its"]
+                                                             for a, b in zip(s0, s1)) / max(n2, 1),
+                                "network_term_kept": sum(b["ws_used"] - a["ws_used"] for a, b in zip(s0, s1)),
+                                "fallback": sum(b["ws_fallback"] - a["ws_fallback"] for a, b in zip(s0, s1)),
+                                "training": info}}
     if rank == 0:
         line = {
             "metric": METRIC, "value": cells_all * args.steps / sec, "unit": UNIT, "n_gpus": world,
@@ -339,13 +376,14 @@ def run_ensemble(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": f"ensemble_{args.members}", "members": args.members, "cells": cells,
                        "cells_all_ranks": int(cells_all),
-                       "precision": args.precision, "workers": batch.workers, "autotune": tuned,
+                       "precision": args.precision, "workers": workers_used, "autotune": tuned,
                        "timer": "host clock between device-wide synchronisations (members on their own streams)",
                        "newton_per_member_step": newton / (len(cases) * args.steps),
                        "fgmres_its_per_newton": lin / max(newton, 1),
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "working set larger than L2 (no flush needed)"},
             "roofline": None, "gpu_launches": launches, "e2e": None, "cpu_baseline": None, "clocks": ck,
+            "variants": variants,
         }
         print(json.dumps(line), flush=True)
     if dist:
