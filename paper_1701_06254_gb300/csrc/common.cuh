@@ -144,6 +144,7 @@ struct ras_data {
   // static (host-built at creation): per subdomain, ext rows in natural
   // order (cells ascending then wells ascending)
   dbuf<int> sub_ptr;            // nsub+1 offsets into ext arrays
+  dbuf<int> order;              // apply launch order: most L + U levels first
   dbuf<int> ext;                // global row of each ext entry
   dbuf<uint8_t> owned;          // 1 if the ext entry is owned
   dbuf<int> ncell;              // cells among ext entries, per subdomain

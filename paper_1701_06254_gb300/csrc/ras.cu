@@ -266,6 +266,32 @@ __global__ void k_ras_levels(const int *sub_ptr, const int *lrp_ptr, const int *
   pp[0] = 0;
 }
 
+// launch order of the apply: subdomains by descending L + U level count
+// (a CTA's time grows with its levels; starting the longest first keeps them
+// out of the last wave).  One block: counting sort on the clamped key; the
+// order within a key is whatever the atomics give (each subdomain writes only
+// its own rows, so the order changes no result).
+#define RAS_KEYS 4096
+__global__ void __launch_bounds__(1024) k_ras_lpt(int nsub, const int *nlev, int *order) {
+  __shared__ int cnt[RAS_KEYS];
+  for (int k = threadIdx.x; k < RAS_KEYS; k += blockDim.x) cnt[k] = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < nsub; s += blockDim.x) {
+    int key = min(nlev[2 * s] + nlev[2 * s + 1], RAS_KEYS - 1);
+    atomicAdd(&cnt[RAS_KEYS - 1 - key], 1);                 // descending keys
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {                                   // exclusive scan (4096 entries)
+    int run = 0;
+    for (int k = 0; k < RAS_KEYS; k++) { int c = cnt[k]; cnt[k] = run; run += c; }
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < nsub; s += blockDim.x) {
+    int key = min(nlev[2 * s] + nlev[2 * s + 1], RAS_KEYS - 1);
+    order[atomicAdd(&cnt[RAS_KEYS - 1 - key], 1)] = s;
+  }
+}
+
 template <class T> __device__ __forceinline__ void inv2x2(const T *M, T *I) {
   T det = M[0] * M[3] - M[1] * M[2];
   T r = T(1) / det;
@@ -344,6 +370,9 @@ void ras_setup(sim_ls_s *ls) {
     k_ras_factor<double><<<R.nsub, 128, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.frp.p, R.fci.p, R.fdiag.p, fsrc.p,
                                                 ls->val.p, R.lvl_rows.p, R.nlev.p, R.lvl_ptr.p, R.fval.p, R.dinv.p);
   RS_LAUNCHED(4);
+  R.order.ensure(R.nsub);
+  k_ras_lpt<<<1, 1024, 0, s>>>(R.nsub, R.nlev.p, R.order.p);
+  RS_LAUNCHED(1);
   ras_pack(ls);
   R.built = true;
   RS_CHECK_LAUNCH();
@@ -580,12 +609,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity
 // the owned rows.
 #define RAS_BS 64
 template <class T, class Tin, bool ACC, class TB>
-__global__ void __launch_bounds__(RAS_BS) k_ras_apply_smem(const long long *blob_off, const unsigned char *blobs,
+__global__ void __launch_bounds__(RAS_BS) k_ras_apply_smem(const long long *blob_off, const unsigned char *blobs, const int *order,
                                                            const Tin *__restrict__ f, T *__restrict__ x, int *err) {
   extern __shared__ uint4 sm4[];
   __shared__ uint64_t bar[2];
   typedef typename v2_t<T>::type T2;
-  int s = blockIdx.x;
+  int s = order[blockIdx.x];                 // longest subdomains first
   const unsigned char *b = blobs + blob_off[s];
   int total = (int)(blob_off[s + 1] - blob_off[s]);
   unsigned char *sb = reinterpret_cast<unsigned char *>(sm4);
@@ -698,8 +727,8 @@ __global__ void k_cast_acc(size_t m, const Tin *a, T *b, bool acc) {
 template <class T, class Tin, class TB>
 static void ras_apply_go(sim_ls_s *ls, const Tin *f, T *x, bool acc) {
   ras_data &R = ls->ras;
-  if (acc) k_ras_apply_smem<T, Tin, true, TB><<<R.nsub, RAS_BS, R.smem_bytes, ls->st>>>(R.blob_off.p, R.blob.p, f, x, ls->errw_dev);
-  else k_ras_apply_smem<T, Tin, false, TB><<<R.nsub, RAS_BS, R.smem_bytes, ls->st>>>(R.blob_off.p, R.blob.p, f, x, ls->errw_dev);
+  if (acc) k_ras_apply_smem<T, Tin, true, TB><<<R.nsub, RAS_BS, R.smem_bytes, ls->st>>>(R.blob_off.p, R.blob.p, R.order.p, f, x, ls->errw_dev);
+  else k_ras_apply_smem<T, Tin, false, TB><<<R.nsub, RAS_BS, R.smem_bytes, ls->st>>>(R.blob_off.p, R.blob.p, R.order.p, f, x, ls->errw_dev);
 }
 template <class T, class Tin> static void ras_apply_launch(sim_ls_s *ls, const Tin *f, T *x, bool acc);
 template <> void ras_apply_launch<double, double>(sim_ls_s *ls, const double *f, double *x, bool acc) {
