@@ -303,8 +303,8 @@ template <class T> __device__ __forceinline__ void inv2x2(const T *M, T *I) {
 template <class T>
 __global__ void k_ras_factor(const int *sub_ptr, const int *lrp_ptr, const int *frp, const int *fci, const int *fdiag,
                              const int *fsrc, const double *val, const int *lvl_rows, const int *nlev,
-                             const int *lvl_ptr, T *fv, T *dinv) {
-  int s = blockIdx.x, base = sub_ptr[s], m = sub_ptr[s + 1] - base, pbase = lrp_ptr[s], fbase = base + s;
+                             const int *lvl_ptr, T *fv, T *dinv, const int *order) {
+  int s = order[blockIdx.x], base = sub_ptr[s], m = sub_ptr[s + 1] - base, pbase = lrp_ptr[s], fbase = base + s;
   int q0 = pbase + frp[fbase], q1 = pbase + frp[fbase + m];
   for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {   // gather values in factor order
     const double *src = val + 4 * (size_t)fsrc[q];
@@ -363,16 +363,19 @@ void ras_setup(sim_ls_s *ls) {
                                        R.ipos.p, R.frp.p, R.fci.p, R.fdiag.p, fsrc.p);
   k_ras_levels<<<R.nsub, 64, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.frp.p, R.fci.p, R.lvl.p, R.lvl_rows.p, R.nlev.p,
                                      R.lvl_ptr.p);
-  if (ls->o.precision != SIM_PREC_FP64)
-    k_ras_factor<float><<<R.nsub, 128, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.frp.p, R.fci.p, R.fdiag.p, fsrc.p,
-                                               ls->val.p, R.lvl_rows.p, R.nlev.p, R.lvl_ptr.p, R.fval32.p, R.dinv32.p);
-  else
-    k_ras_factor<double><<<R.nsub, 128, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.frp.p, R.fci.p, R.fdiag.p, fsrc.p,
-                                                ls->val.p, R.lvl_rows.p, R.nlev.p, R.lvl_ptr.p, R.fval.p, R.dinv.p);
-  RS_LAUNCHED(4);
+  // longest subdomains first for the factorisation and the applies (their
+  // CTAs' times grow with the level counts)
   R.order.ensure(R.nsub);
   k_ras_lpt<<<1, 1024, 0, s>>>(R.nsub, R.nlev.p, R.order.p);
-  RS_LAUNCHED(1);
+  if (ls->o.precision != SIM_PREC_FP64)
+    k_ras_factor<float><<<R.nsub, 128, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.frp.p, R.fci.p, R.fdiag.p, fsrc.p,
+                                               ls->val.p, R.lvl_rows.p, R.nlev.p, R.lvl_ptr.p, R.fval32.p, R.dinv32.p,
+                                               R.order.p);
+  else
+    k_ras_factor<double><<<R.nsub, 128, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.frp.p, R.fci.p, R.fdiag.p, fsrc.p,
+                                                ls->val.p, R.lvl_rows.p, R.nlev.p, R.lvl_ptr.p, R.fval.p, R.dinv.p,
+                                                R.order.p);
+  RS_LAUNCHED(5);
   ras_pack(ls);
   R.built = true;
   RS_CHECK_LAUNCH();
@@ -482,9 +485,9 @@ template <class T, class TB>
 __global__ void k_ras_pack(const int *sub_ptr, const int *lrp_ptr, const int *ext, const uint8_t *owned,
                            const int *perm, const int *frp, const int *fci, const int *fdiag, const T *fv,
                            const T *dinv, const int *lvl_rows, const int *nlev, const int *lvl_ptr,
-                           const long long *blob_off, unsigned char *blobs) {
+                           const long long *blob_off, unsigned char *blobs, const int *order) {
   __shared__ int part[129];
-  int s = blockIdx.x, base = sub_ptr[s], m = sub_ptr[s + 1] - base, pbase = lrp_ptr[s], fbase = base + s;
+  int s = order[blockIdx.x], base = sub_ptr[s], m = sub_ptr[s + 1] - base, pbase = lrp_ptr[s], fbase = base + s;
   int e = (lrp_ptr[s + 1] - pbase) - m;
   blob_layout Lb = blob_lay(m, e, 4 * (int)sizeof(TB));
   unsigned char *b = blobs + blob_off[s];
@@ -706,15 +709,15 @@ void ras_pack(sim_ls_s *ls) {
   if (ls->o.precision == SIM_PREC_MIXED_BF16)
     k_ras_pack<float, __nv_bfloat16><<<R.nsub, 128, 0, ls->st>>>(R.sub_ptr.p, R.lrp_ptr.p, R.ext.p, R.owned.p, R.perm.p,
                                                   R.frp.p, R.fci.p, R.fdiag.p, R.fval32.p, R.dinv32.p, R.lvl_rows.p,
-                                                  R.nlev.p, R.lvl_ptr.p, R.blob_off.p, R.blob.p);
+                                                  R.nlev.p, R.lvl_ptr.p, R.blob_off.p, R.blob.p, R.order.p);
   else if (ls->o.precision != SIM_PREC_FP64)
     k_ras_pack<float, float><<<R.nsub, 128, 0, ls->st>>>(R.sub_ptr.p, R.lrp_ptr.p, R.ext.p, R.owned.p, R.perm.p, R.frp.p,
                                                   R.fci.p, R.fdiag.p, R.fval32.p, R.dinv32.p, R.lvl_rows.p,
-                                                  R.nlev.p, R.lvl_ptr.p, R.blob_off.p, R.blob.p);
+                                                  R.nlev.p, R.lvl_ptr.p, R.blob_off.p, R.blob.p, R.order.p);
   else
     k_ras_pack<double, double><<<R.nsub, 128, 0, ls->st>>>(R.sub_ptr.p, R.lrp_ptr.p, R.ext.p, R.owned.p, R.perm.p, R.frp.p,
                                                    R.fci.p, R.fdiag.p, R.fval.p, R.dinv.p, R.lvl_rows.p,
-                                                   R.nlev.p, R.lvl_ptr.p, R.blob_off.p, R.blob.p);
+                                                   R.nlev.p, R.lvl_ptr.p, R.blob_off.p, R.blob.p, R.order.p);
   RS_LAUNCHED(1);
 }
 
