@@ -865,25 +865,37 @@ __global__ void k_dgks(const double *w2_before, const double *w2_after, int *fla
 __global__ void k_arnoldi_col(int j, int m, const double *h1, const double *h2, const double *nrm_a,
                               const double *nrm_b, const int *flag, double *G, double *hnorm, volatile double *host,
                               const int *jd, float *isp) {
+  // one warp: the column's inputs and the previous rotations are loaded
+  // into shared memory in parallel, then lane 0 applies the rotations (a
+  // serial recurrence) from there
+  __shared__ double sc[ORTHO_MAXV + 1], scs[ORTHO_MAXV], ssn[ORTHO_MAXV];
   if (jd) { j = *jd; host += 4 * j; }          // graph replay: pinned slot j
   double *H = G, *cs = G + (size_t)m * (m + 1), *sn = cs + m, *g = sn + m;
   double *col = H + (size_t)j * (m + 1);
+  const int lane = threadIdx.x;
   bool re = *flag != 0;
-  for (int k = 0; k <= j; k++) col[k] = re ? h1[k] + h2[k] : h1[k];
+  for (int k = lane; k <= j; k += 32) sc[k] = re ? h1[k] + h2[k] : h1[k];
+  for (int k = lane; k < j; k += 32) { scs[k] = cs[k]; ssn[k] = sn[k]; }
+  __syncwarp();
+  if (lane != 0) return;
   double hn = sqrt(re ? *nrm_b : *nrm_a);
   hnorm[0] = hn;
   hnorm[1] = hn > 0.0 ? 1.0 / hn : 0.0;
   if (isp) { float a, b; df_split(hnorm[1], a, b); isp[0] = a; isp[1] = b; }
+  sc[j + 1] = 0.0;
   for (int k = 0; k < j; k++) {
-    double t = cs[k] * col[k] + sn[k] * col[k + 1];
-    col[k + 1] = -sn[k] * col[k] + cs[k] * col[k + 1];
-    col[k] = t;
+    double t = scs[k] * sc[k] + ssn[k] * sc[k + 1];
+    sc[k + 1] = -ssn[k] * sc[k] + scs[k] * sc[k + 1];
+    sc[k] = t;
   }
-  double rr = sqrt(col[j] * col[j] + hn * hn);
-  cs[j] = col[j] / rr; sn[j] = hn / rr;
+  double rr = sqrt(sc[j] * sc[j] + hn * hn);
+  double cj = sc[j] / rr, sj = hn / rr;
+  cs[j] = cj; sn[j] = sj;
+  for (int k = 0; k < j; k++) col[k] = sc[k];
   col[j] = rr; col[j + 1] = 0.0;
-  g[j + 1] = -sn[j] * g[j];
-  g[j] = cs[j] * g[j];
+  double gj = g[j];
+  g[j + 1] = -sj * gj;
+  g[j] = cj * gj;
   host[0] = fabs(g[j + 1]);
   host[1] = hn;
   host[2] = re ? 1.0 : 0.0;
@@ -983,7 +995,7 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
       reduce_parts(nv, nblk, part, h2, flag, c, jdp, 0);
       ortho_update_df(nu, chd, nv, V32, w2, h2, part, flag, nblk, c, jdp);
       reduce_parts(1, nblk, part, nrm_b, flag, c);
-      k_arnoldi_col<<<1, 1, 0, c>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, jdp ? hp_dev : hp_dev + 4 * j, jdp,
+      k_arnoldi_col<<<1, 32, 0, c>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, jdp ? hp_dev : hp_dev + 4 * j, jdp,
                                     ls->isp.p);
       k_scale_df<<<grid_for(nu, 256), 256, 0, c>>>(nu, w2, ls->isp.p, V32, j + 1, jdp);
       RS_LAUNCHED(11);
@@ -997,7 +1009,7 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
       reduce_parts(nv, nblk, part, h2, flag, c, jdp, 0);
       ortho_update(nu, nv, ls->V.p, ls->w.p, h2, part, flag, nblk, c, jdp);
       reduce_parts(1, nblk, part, nrm_b, flag, c);
-      k_arnoldi_col<<<1, 1, 0, c>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, jdp ? hp_dev : hp_dev + 4 * j, jdp,
+      k_arnoldi_col<<<1, 32, 0, c>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, jdp ? hp_dev : hp_dev + 4 * j, jdp,
                                     nullptr);
       k_scale<<<grid_for(nu, 256), 256, 0, c>>>(nu, ls->w.p, hn + 1, jdp ? ls->V.p : ls->V.p + (size_t)(j + 1) * nu,
                                                 jdp);
