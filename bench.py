@@ -96,9 +96,10 @@ def ras_bytes(ls, precision):
     factors: every off-diagonal factor block (values + 2-byte column) and
     every row's record (gather index, six 2-byte row/level indices, inverse
     diagonal block) read once, the extended right-hand side gathered and the
-    owned rows written.  The two applications of Algorithm 2 differ in their
-    vectors (FP64 in / FP32 out, FP32 in / FP32 accumulated), so the
-    vector bytes are their average."""
+    owned rows written.  In mixed precision both applications of Algorithm 2
+    read an FP32 input (the basis vector's hi plane, then the FP32 residual);
+    the first overwrites its output, the second accumulates into it, so the
+    output bytes are their average."""
     vb = {"mixed": 16, "mixed_bf16": 8, "fp64": 32}[precision]
     nsub = ls.ras_count()
     nnz = nxt = own = 0
@@ -109,13 +110,13 @@ def ras_bytes(ls, precision):
     if precision == "fp64":
         gather, scatter = 16.0, 24.0          # double2 in; write, or read + write
     else:
-        gather, scatter = 12.0, 12.0          # double2 / float2 in; float2 write, or read + write
+        gather, scatter = 8.0, 12.0           # float2 in; float2 write, or read + write
     return off * (vb + 2) + nxt * (4 + 12 + vb) + nxt * gather + own * scatter
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # ncu capture summarised in profiles/ (null once the kernel changes)
-NCU_TRAFFIC = {("ras", "mixed_bf16"): 172.9e6, ("spmv_prec", "mixed_bf16"): 164.3e6,
+NCU_TRAFFIC = {("ras", "mixed_bf16"): 167.8e6, ("spmv_prec", "mixed_bf16"): 164.3e6,
                ("spmv64", "mixed_bf16"): 273.4e6}
 
 
