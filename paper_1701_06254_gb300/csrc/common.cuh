@@ -205,6 +205,7 @@ struct sim_ls_s {
   dbuf<double> vcur, zcur64;
   dbuf<float> zcur32, vcur32;
   dbuf<float> w2, isp;          // double-float w planes; split 1 / h_{j+1,j}
+  dbuf<int> ticket;             // last-block ticket of the Gram-Schmidt sweeps (zero between launches)
   dbuf<float> vallo;            // lo plane of the decoupled matrix (hi: val32)
   // timer brackets recorded inside the graph (event nodes): pairs of events
   // and the family of each pair, read back after every replay

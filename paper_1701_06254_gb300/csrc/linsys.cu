@@ -639,13 +639,38 @@ __device__ __forceinline__ double warp_sum_df(float h, float l) {        // resu
   return (double)h + (double)l;
 }
 
+// The block that finishes last (atomic ticket) sums the per-block partials
+// part[k][b] into out[k] for k < nout, exactly as k_reduce_parts does (warp
+// per k, lanes over a fixed stride of blocks, shuffle tree), and resets the
+// ticket: the separate reduction launch between the sweeps disappears.
+__device__ __forceinline__ bool last_block(int *ticket) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  return last;
+}
+__device__ __forceinline__ void reduce_tail(int nout, int nblk, const double *part, double *out, int *ticket) {
+  __threadfence();
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = warp; k < nout; k += nw) {
+    double t = 0;
+    for (int b = lane; b < nblk; b += 32) t += __ldcg(part + (size_t)k * nblk + b);
+    t = warp_sum_d(t);
+    if (lane == 0) out[k] = t;
+  }
+  if (threadIdx.x == 0) *ticket = 0;
+}
+
 // k_ortho_dots on pair planes: V vector k at V + 2k nu (hi) and + (2k+1) nu
 // (lo), w at w (hi) and w + nu (lo).  Vector offsets are 32-bit (the basis
 // holds at most 2 (ORTHO_MAXV + 1) nu < 2^31 floats) and each thread takes
 // two rows per iteration, so that 32 loads are in flight together.
 __global__ void __launch_bounds__(ORTHO_BS, 4) k_ortho_dots_df(int nu, int ch, int nv, const float *__restrict__ V,
                                                                const float *__restrict__ w, double *part,
-                                                               int with_norm, const int *cond, const int *jd) {
+                                                               int with_norm, const int *cond, const int *jd,
+                                                               int *ticket, double *out) {
   if (cond && *cond == 0) return;
   if (jd) nv = *jd + 1;
   extern __shared__ float2 wp[];               // ORTHO_CH pairs (dynamic)
@@ -699,6 +724,7 @@ __global__ void __launch_bounds__(ORTHO_BS, 4) k_ortho_dots_df(int nu, int ch, i
       part[(size_t)(k0 + threadIdx.x) * nblk + blockIdx.x] = sum;
     }
   }
+  if (last_block(ticket)) reduce_tail(nt, nblk, part, out, ticket);   // out[k] = V_k . w (and ||w||^2)
 }
 
 // k_ortho_update on pair planes: w -= sum_k h_k V_k (h FP64, split once per
@@ -706,7 +732,8 @@ __global__ void __launch_bounds__(ORTHO_BS, 4) k_ortho_dots_df(int nu, int ch, i
 // thread per iteration
 __global__ void __launch_bounds__(ORTHO_BS, 4) k_ortho_update_df(int nu, int ch, int nv, const float *__restrict__ V,
                                                                  float *w, const double *__restrict__ h, double *part,
-                                                                 const int *cond, const int *jd) {
+                                                                 const int *cond, const int *jd, int *ticket,
+                                                                 double *nrm, int *flag, const double *h1) {
   if (cond && *cond == 0) return;
   if (jd) nv = *jd + 1;
   extern __shared__ float2 wp[];
@@ -770,6 +797,12 @@ __global__ void __launch_bounds__(ORTHO_BS, 4) k_ortho_update_df(int nu, int ch,
     for (int q = 0; q < ORTHO_BS / 32; q++) tot += sred[q];
     part[blockIdx.x] = tot;
   }
+  if (last_block(ticket)) {
+    reduce_tail(1, gridDim.x, part, nrm, ticket);        // nrm = ||w||^2 after the pass
+    // first pass: flag the second one when it kept less than 1% of w
+    // (||w_1||^2 < 1e-4 ||w||^2, as k_dgks); ||w||^2 sits after the dot products
+    if (flag && threadIdx.x == 0) { __threadfence(); *flag = (*(volatile double *)nrm < 1e-4 * h1[nv]) ? 1 : 0; }
+  }
 }
 // V_{j+1} = w / h_{j+1,j}, the reciprocal split once by k_arnoldi_col (isp)
 __global__ void k_scale_df(int nu, const float *w, const float *isp, float *V, int j1, const int *jd) {
@@ -825,14 +858,15 @@ static int ortho_blocks_df(int nu, int *ch) {
   return std::max(nblk, 1);
 }
 static void ortho_dots_df(int nu, int ch, int nv, const float *V, const float *w, double *part, int with_norm,
-                          const int *cond, int nblk, cudaStream_t s, const int *jd = nullptr) {
+                          const int *cond, int nblk, cudaStream_t s, const int *jd, int *ticket, double *out) {
   ortho_attr();
-  k_ortho_dots_df<<<nblk, ORTHO_BS, (size_t)ch * 8, s>>>(nu, ch, nv, V, w, part, with_norm, cond, jd);
+  k_ortho_dots_df<<<nblk, ORTHO_BS, (size_t)ch * 8, s>>>(nu, ch, nv, V, w, part, with_norm, cond, jd, ticket, out);
 }
 static void ortho_update_df(int nu, int ch, int nv, const float *V, float *w, const double *h, double *part,
-                            const int *cond, int nblk, cudaStream_t s, const int *jd = nullptr) {
+                            const int *cond, int nblk, cudaStream_t s, const int *jd, int *ticket, double *nrm,
+                            int *flag, const double *h1) {
   ortho_attr();
-  k_ortho_update_df<<<nblk, ORTHO_BS, (size_t)ch * 8, s>>>(nu, ch, nv, V, w, h, part, cond, jd);
+  k_ortho_update_df<<<nblk, ORTHO_BS, (size_t)ch * 8, s>>>(nu, ch, nv, V, w, h, part, cond, jd, ticket, nrm, flag, h1);
 }
 
 // out[k] = sum over blocks of part[k][*]: one warp per k, lanes add a fixed
@@ -980,25 +1014,26 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
   // rotations, and V_{j+1}.  jdp: the step index is read on the device (graph
   // replay) instead of j.  Mixed precision: double-float planes.
   float *V32 = reinterpret_cast<float *>(ls->V.p);
-  if (df) { ls->w2.ensure(2 * (size_t)nu); ls->isp.ensure(2); }
+  if (df) {
+    ls->w2.ensure(2 * (size_t)nu); ls->isp.ensure(2);
+    if (!ls->ticket.p) { ls->ticket.ensure(1); RS_CUDA(cudaMemsetAsync(ls->ticket.p, 0, sizeof(int), s)); }
+  }
   auto ortho_tail = [&](cudaStream_t c, int j, const int *jdp) {
     int nv = jdp ? 0 : j + 1;
     double *part = ls->partial.p;
     if (df) {
       float *w2 = ls->w2.p;                    // written by the double-float SpMV
-      ortho_dots_df(nu, chd, nv, V32, w2, part, 1, nullptr, nblk, c, jdp);
-      reduce_parts(nv + 1, nblk, part, h1, nullptr, c, jdp, 1);          // h1[nv] = ||w||^2
-      ortho_update_df(nu, chd, nv, V32, w2, h1, part, nullptr, nblk, c, jdp);
-      reduce_parts(1, nblk, part, nrm, nullptr, c);
-      k_dgks<<<1, 1, 0, c>>>(h1 + nv, nrm, flag, h1, jdp);
-      ortho_dots_df(nu, chd, nv, V32, w2, part, 0, flag, nblk, c, jdp);
-      reduce_parts(nv, nblk, part, h2, flag, c, jdp, 0);
-      ortho_update_df(nu, chd, nv, V32, w2, h2, part, flag, nblk, c, jdp);
-      reduce_parts(1, nblk, part, nrm_b, flag, c);
+      // the reductions, and the test for a second pass, run in the last
+      // block of each sweep
+      int *tk = ls->ticket.p;
+      ortho_dots_df(nu, chd, nv, V32, w2, part, 1, nullptr, nblk, c, jdp, tk, h1);   // h1[nv] = ||w||^2
+      ortho_update_df(nu, chd, nv, V32, w2, h1, part, nullptr, nblk, c, jdp, tk, nrm, flag, h1);
+      ortho_dots_df(nu, chd, nv, V32, w2, part, 0, flag, nblk, c, jdp, tk, h2);
+      ortho_update_df(nu, chd, nv, V32, w2, h2, part, flag, nblk, c, jdp, tk, nrm_b, nullptr, nullptr);
       k_arnoldi_col<<<1, 32, 0, c>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, jdp ? hp_dev : hp_dev + 4 * j, jdp,
                                     ls->isp.p);
       k_scale_df<<<grid_for(nu, 256), 256, 0, c>>>(nu, w2, ls->isp.p, V32, j + 1, jdp);
-      RS_LAUNCHED(11);
+      RS_LAUNCHED(6);
     } else {
       ortho_dots(nu, nv, ls->V.p, ls->w.p, part, 1, nullptr, nblk, c, jdp);
       reduce_parts(nv + 1, nblk, part, h1, nullptr, c, jdp, 1);
