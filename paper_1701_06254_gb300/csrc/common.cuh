@@ -41,7 +41,10 @@ template <class T> struct dbuf {            // owning device buffer
     if (m) RS_CUDA(cudaMalloc((void **)&p, m * sizeof(T)));
     n = m;
   }
-  void ensure(size_t m) { if (m > n) alloc(m); }
+  // grow with a quarter of headroom: sizes that follow the data (AMG levels,
+  // SpGEMM scratch) creep up between Newton iterations, and every regrowth is
+  // a cudaFree (which waits for the device) and a cudaMalloc
+  void ensure(size_t m) { if (m > n) alloc(m + m / 4); }
   void free() { if (p) cudaFree(p); p = nullptr; n = 0; }
   ~dbuf() { free(); }
   dbuf() = default;
