@@ -175,6 +175,23 @@ def test_fgmres_matches_oracle(mk, opts):
     assert np.abs(yg - yo).max() <= 1e-7 * np.abs(yo).max()
 
 
+@pytest.mark.parametrize("mk,opts", SYS)
+def test_mixed_fgmres_reaches_tight_tolerance(mk, opts):
+    """The mixed-precision solver keeps its Krylov basis in double-float
+    (hi + lo FP32, about 48 significant bits): far below the benchmark's
+    relres 1e-6 it still converges, to a true residual of 1e-10, to the FP64
+    oracle's solution, in at most 25% more iterations than the oracle's FP64
+    solver (the FP32 preconditioner is weaker)."""
+    c = mk()
+    o, gl, _ = _shared_system(c, 500, precision=R.PREC_MIXED_BF16, **opts)
+    o.ls.setup(); gl.setup()
+    rco, yo, itso, relo = o.ls.solve(1e-10)
+    yg, itsg, relg = gl.solve(1e-10)
+    assert rco == 0 and relg <= 1e-10, relg
+    assert itsg <= 1.25 * itso + 2, (itsg, itso)
+    assert np.abs(yg - yo).max() <= 1e-7 * np.abs(yo).max()
+
+
 def test_mixed_precision_operators_track_fp64():
     """FP32 RAS / AMG / CPR stay within single-precision distance of the
     FP64 oracle; the integer setup work is unchanged (done in FP64)."""
