@@ -1,0 +1,55 @@
+"""The algorithmic byte counts behind bench.py's roofline fractions, on small
+hand-made sizes (no GPU): each formula against its terms written out."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_spmv_bytes():
+    # 10 block rows, 30 blocks: values + column per block, row pointers,
+    # two unknowns per row for each vector
+    assert bench.spmv_bytes(10, 30, 16, 4, 4, 4) == 30 * 20 + 11 * 4 + 20 * 12
+    assert bench.spmv_bytes(10, 30, 32, 4, 0, 8) == 30 * 36 + 11 * 4 + 20 * 12
+
+
+class _FakeAMG:
+    """Two levels: a 100-row level with 700 entries and 400-entry P to 30
+    coarse rows, and a dense 30-row coarsest level."""
+
+    def amg_nlev(self):
+        return 2
+
+    def amg_level(self, l):
+        if l == 0:
+            return dict(n=100, nnz=700, nc=30, nnzP=400, coarse_dense=0)
+        return dict(n=30, nnz=300, nc=0, nnzP=0, coarse_dense=1)
+
+
+def test_vcycle_bytes_fp32():
+    vb = 4
+    a = 700 * (vb + 4) + 101 * 4
+    level0 = 2 * a + 8 * 100 * vb                                   # pre + post smoothing
+    level0 += 400 * (vb + 4) + 31 * 4 + 100 * vb + 3 * 30 * vb      # restriction (R = P^T)
+    level0 += 400 * (vb + 4) + 101 * 4 + 2 * 100 * vb + 30 * vb     # prolongation
+    coarsest = 30 * 30 * 8 + 2 * 30 * vb                            # dense FP64 inverse
+    assert bench.vcycle_bytes(_FakeAMG(), "mixed_bf16") == level0 + coarsest
+
+
+class _FakeRAS:
+    """Two subdomains: (owned rows, extended rows, local entries)."""
+
+    def ras_count(self):
+        return 2
+
+    def ras_sizes(self, s):
+        return [(16, 40, 200), (12, 30, 150)][s]
+
+
+def test_ras_bytes_bf16():
+    own, nxt, nnz = 28, 70, 350
+    off = nnz - nxt                                  # off-diagonal blocks
+    expect = off * (8 + 2) + nxt * (4 + 12 + 8) + nxt * 8.0 + own * 12.0
+    assert bench.ras_bytes(_FakeRAS(), "mixed_bf16") == expect
