@@ -304,7 +304,9 @@ def run_ensemble(args, rank, world, local):
     cases = I.ensemble(args.members, seed0=ensemble_seed0(rank, args.members))
     cells = sum(c.n for c in cases)
     auto = args.workers == "auto"
-    batch = R.Batch(cases, workers=0 if auto else int(args.workers), precision=prec, max_lin=args.max_lin)
+    dec = {"abf": R.DEC_ABF, "qi": R.DEC_QI, "none": R.DEC_NONE}[args.decoupling]
+    batch = R.Batch(cases, workers=0 if auto else int(args.workers), precision=prec, max_lin=args.max_lin,
+                    decoupling=dec)
     batch.init_hydrostatic()
     tuned = None
     if auto:
@@ -339,9 +341,9 @@ def run_ensemble(args, rank, world, local):
     variants = None
     if not args.no_variants:
         del batch
-        ws, info = train_warm_start(R, args, dict(precision=prec, max_lin=args.max_lin))
+        ws, info = train_warm_start(R, args, dict(precision=prec, max_lin=args.max_lin, decoupling=dec))
         params = ws.params()
-        b2 = R.Batch(cases, workers=workers_used, precision=prec, max_lin=args.max_lin)
+        b2 = R.Batch(cases, workers=workers_used, precision=prec, max_lin=args.max_lin, decoupling=dec)
         b2.init_hydrostatic()
         copies = []
         for m in b2.members:
@@ -377,7 +379,8 @@ def run_ensemble(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": f"ensemble_{args.members}", "members": args.members, "cells": cells,
                        "cells_all_ranks": int(cells_all),
-                       "precision": args.precision, "workers": workers_used, "autotune": tuned,
+                       "precision": args.precision, "decoupling": args.decoupling, "workers": workers_used,
+                       "autotune": tuned,
                        "timer": "host clock between device-wide synchronisations (members on their own streams)",
                        "newton_per_member_step": newton / (len(cases) * args.steps),
                        "fgmres_its_per_newton": lin / max(newton, 1),
@@ -403,6 +406,10 @@ def main():
                          "setting), FP32 throughout, or FP64")
     ap.add_argument("--max-lin", type=int, default=200)
     ap.add_argument("--tile", default="4x4", help="RAS subdomain tile, columns x rows of cells")
+    ap.add_argument("--decoupling", default="qi", choices=["abf", "qi", "none"],
+                    help="decoupling of the Newton system (eq. 29): Quasi-IMPES (default, with the potential "
+                         "reordering the paper's configuration for its SPE10 runs), ABF or none")
+    ap.add_argument("--no-reorder", action="store_true", help="switch off the local potential reordering")
     ap.add_argument("--roofline", default="ras", choices=["ras", "spmv64", "spmv_prec"])
     ap.add_argument("--workload", default="single", choices=["single", "ensemble"],
                     help="single: the 1M-cell case; ensemble: --members independent models advanced together")
@@ -445,7 +452,9 @@ def main():
         dist.init_process_group("nccl")
     prec = {"mixed": R.PREC_MIXED, "mixed_bf16": R.PREC_MIXED_BF16, "fp64": R.PREC_FP64}[args.precision]
     tx, ty = (int(v) for v in args.tile.split("x"))
-    opts = dict(precision=prec, max_lin=args.max_lin, tile_x=tx, tile_y=ty)
+    opts = dict(precision=prec, max_lin=args.max_lin, tile_x=tx, tile_y=ty,
+                decoupling={"abf": R.DEC_ABF, "qi": R.DEC_QI, "none": R.DEC_NONE}[args.decoupling],
+                reorder=0 if args.no_reorder else 1)
     ws_info = False
     ws = None
     if args.learned:
@@ -593,7 +602,7 @@ def main():
             "vs_baseline": None, "dtype": {"mixed": "f64+f32", "mixed_bf16": "f64+f32+bf16", "fp64": "f64"}[args.precision], "data": "synthetic",
             "config": {"workload": case.name, "cells": case.n, "wells": len(case.wells), "dt_days": case.dt,
                        "relres": case.lin_tol, "precision": args.precision, "learned_warm_start": ws_info,
-                       "ras_tile": args.tile,
+                       "ras_tile": args.tile, "decoupling": args.decoupling, "reorder": not args.no_reorder,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "working set larger than L2 (no flush needed)",
                        "newton_per_step": newton_per_step, "fgmres_its_per_newton": its_per_newton,

@@ -346,3 +346,35 @@ def test_full_size_cfg2_parity():
     y, its, rel = gl.solve(1e-6)
     r = db - o.ls.mv(y)
     assert np.linalg.norm(r) <= 1.0001e-6 * np.linalg.norm(db), (its, rel)
+
+
+# ---- Quasi-IMPES decoupling (the paper's choice for its large SPE10 runs) ----
+@pytest.mark.parametrize("mk,opts", SYS[:3])
+def test_quasi_impes_matches_oracle(mk, opts):
+    """QI decoupling on shared FP64 input: the decoupled matrix and right-hand
+    side bit for bit (both sides evaluate the same round-to-nearest
+    operations), the level-0 C/F split bit for bit, RAS / CPR applications to
+    1e-10, FGMRES iterations within one."""
+    c = mk()
+    o, gl, _ = _shared_system(c, 410, decoupling=R.DEC_QI, **opts)
+    o.ls.setup(); gl.setup()
+    _, _, dval, db, _ = o.ls.get()
+    np.testing.assert_array_equal(gl.export(R.X_VALS), dval)
+    np.testing.assert_array_equal(gl.export(R.X_RHS), db)
+    np.testing.assert_array_equal(gl.amg_level(0)["cf"], o.ls.amg().level(0)["cf"])
+    x = np.random.default_rng(41).standard_normal(2 * (c.n + len(c.wells)))
+    for op, fo in ((R.OP_RAS, o.ls.ras), (R.OP_CPR, o.ls.cpr)):
+        yg, yo = gl.apply(op, x), fo(x)
+        assert np.abs(yg - yo).max() <= 1e-10 * np.abs(yo).max(), op
+    rco, yo, itso, relo = o.ls.solve(1e-10)
+    yg, itsg, relg = gl.solve(1e-10)
+    assert rco == 0 and relg <= 1e-10
+    assert abs(itsg - itso) <= 1
+    assert np.abs(yg - yo).max() <= 1e-7 * np.abs(yo).max()
+
+
+def test_whole_run_channelised_case_quasi_impes_mixed():
+    """The 1M-cell case's physics on a 42x38x8 grid with QI decoupling, mixed
+    precision and BF16 RAS values: three steps against the oracle (QI, FP64)."""
+    c = I.case2(nx=42, ny=38, nz=8)
+    _run_compare(c, 3, precision=R.PREC_MIXED_BF16, decoupling=R.DEC_QI)
