@@ -29,6 +29,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "cell-timesteps/s at 1M cells, relres 1e-6: mixed+learned vs plain FP64; %HBM peak"
+# decoupling codes, the same in the CUDA library (SIM_DEC_*) and the oracle
+DECOUPLING = {"none": 0, "abf": 1, "qi": 2}
+
+
+def oracle_opts(args):
+    """The oracle's options for the configuration the GPU arm runs."""
+    return dict(max_lin=args.max_lin, decoupling=DECOUPLING[args.decoupling], reorder=0 if args.no_reorder else 1)
 UNIT = "cell-timesteps/s"
 
 
@@ -176,15 +183,14 @@ def oracle_full_step(case, opts):
 def run_reference(args, case, rank):
     if rank != 0:
         return
-    opts = dict(max_lin=args.max_lin)
-    dt, rc, st = oracle_full_step(case, opts)
+    dt, rc, st = oracle_full_step(case, oracle_opts(args))
     value = case.n / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": 1, "warmup": 0, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": case.name, "cells": case.n, "dt_days": case.dt, "relres": case.lin_tol,
-                   "precision": "fp64"},
+                   "precision": "fp64", "decoupling": args.decoupling, "reorder": not args.no_reorder},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"the CPU oracle's complete first time step of {case.name} "
                                    f"({st['newton']} Newton iterations, {st['lin']} FGMRES iterations, rc={rc}); "
@@ -304,7 +310,7 @@ def run_ensemble(args, rank, world, local):
     cases = I.ensemble(args.members, seed0=ensemble_seed0(rank, args.members))
     cells = sum(c.n for c in cases)
     auto = args.workers == "auto"
-    dec = {"abf": R.DEC_ABF, "qi": R.DEC_QI, "none": R.DEC_NONE}[args.decoupling]
+    dec = DECOUPLING[args.decoupling]
     batch = R.Batch(cases, workers=0 if auto else int(args.workers), precision=prec, max_lin=args.max_lin,
                     decoupling=dec)
     batch.init_hydrostatic()
@@ -453,7 +459,7 @@ def main():
     prec = {"mixed": R.PREC_MIXED, "mixed_bf16": R.PREC_MIXED_BF16, "fp64": R.PREC_FP64}[args.precision]
     tx, ty = (int(v) for v in args.tile.split("x"))
     opts = dict(precision=prec, max_lin=args.max_lin, tile_x=tx, tile_y=ty,
-                decoupling={"abf": R.DEC_ABF, "qi": R.DEC_QI, "none": R.DEC_NONE}[args.decoupling],
+                decoupling=DECOUPLING[args.decoupling],
                 reorder=0 if args.no_reorder else 1)
     ws_info = False
     ws = None
@@ -589,7 +595,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_it, its = oracle_newton_iteration(case, dict(max_lin=args.max_lin))
+        t_it, its = oracle_newton_iteration(case, oracle_opts(args))
         cpu = {"value": case.n / (t_it * max(newton_per_step, 1.0)), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"one Newton iteration of the first time step of {case.name} by the FP64 CPU oracle "
                          f"(assembly + setup + {its} FGMRES iterations, {t_it:.1f} s), scaled by the GPU run's "

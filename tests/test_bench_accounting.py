@@ -53,3 +53,15 @@ def test_ras_bytes_bf16():
     off = nnz - nxt                                  # off-diagonal blocks
     expect = off * (8 + 2) + nxt * (4 + 12 + 8) + nxt * 8.0 + own * 12.0
     assert bench.ras_bytes(_FakeRAS(), "mixed_bf16") == expect
+
+
+
+def test_decoupling_codes_agree():
+    """bench.py's decoupling codes are those of the CUDA library's header and
+    of the oracle's (both arms must run the same configuration)."""
+    import re
+    lib = open(os.path.join(ROOT, "include", "resim.h")).read()
+    orc = open(os.path.join(ROOT, "oracle", "or_internal.h")).read()
+    for name, code in bench.DECOUPLING.items():
+        assert int(re.search(r"SIM_DEC_%s = (\d+)" % name.upper(), lib).group(1)) == code
+        assert int(re.search(r"OR_DEC_%s = (\d+)" % name.upper(), orc).group(1)) == code
