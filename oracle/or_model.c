@@ -12,9 +12,9 @@
  *     transmissibility eq. (16), discrete residual eq. (17), upstreaming
  *     eq. (18), F(x) = 0 eqs. (19)-(23);
  *   Sec. "Nonlinear methods": Algorithm 1 (inexact Newton), eqs. (24)-(27).
- * Readings where the paper is silent (units, gravity sign, relative
- * permeability form, well index, tie rules, scaling, time-step cuts) are the
- * ones listed in the design doc and restated at each use below.
+ * Where the paper is silent (units, gravity sign, relative permeability
+ * form, well index, tie rules, scaling, time-step cuts) the reading taken is
+ * stated at each use below.
  */
 #include "or_internal.h"
 #include <math.h>
