@@ -97,6 +97,13 @@ def test_decoupling_keeps_solution(oracle_lib, dec):
             assert np.all(np.abs(D - np.eye(2)) <= bound)
         else:
             assert abs(D[0, 1]) <= 1e-12 * abs(J[2 * i, 2 * i + 1])
+            # only the pressure row changes, by a multiple of its own
+            # cell's saturation row
+            np.testing.assert_array_equal(J2[2 * i + 1], J[2 * i + 1])
+            assert b2[2 * i + 1] == b[2 * i + 1]
+            ratio = J[2 * i, 2 * i + 1] / J[2 * i + 1, 2 * i + 1]
+            np.testing.assert_allclose(J2[2 * i], J[2 * i] - ratio * J[2 * i + 1],
+                                       rtol=0, atol=1e-13 * np.abs(J[2 * i]).max())
     np.testing.assert_array_equal(J2[2 * c.n:], J[2 * c.n:])
 
 
