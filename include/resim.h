@@ -89,8 +89,8 @@ typedef struct {
   int newton;          /* SIM_NEWTON_*                                             */
   double newton_tol;   /* scaled max-residual tolerance                            */
   double lin_tol;      /* relative linear residual (standard Newton)               */
-  int max_newton, restart, max_lin;
-  int tile_x, tile_y;  /* RAS subdomain = tile_x x tile_y cell columns             */
+  int max_newton, restart, max_lin; /* restart, max_lin <= 0: default; restart <= 63 */
+  int tile_x, tile_y;  /* RAS subdomain = tile_x x tile_y cell columns (<= 0: 4)  */
   double amg_theta;
   int amg_max_levels, amg_coarse_max;
   uint64_t seed;       /* PMIS hash seed                                           */
@@ -122,7 +122,11 @@ void sim_default_options(sim_options *o);
 /* Create a simulator (copies everything).  Builds transmissibilities,
  * well indices, the 2x2 block sparsity pattern (cells, then one padded
  * block row per well) and the RAS partition; allocates device memory.
- * Errors: SIM_ERR_ARG for bad sizes/controls, SIM_ERR_OOM, SIM_ERR_CUDA. */
+ * Errors: SIM_ERR_ARG for bad sizes/controls or option values (an unknown
+ * precision, decoupling, reorder or Newton code; a tolerance that is
+ * negative or not finite; amg_theta outside [0, 1]; a negative max_newton,
+ * max_cuts or amg_coarse_max; dt not finite and > 0), all checked before any
+ * device work; SIM_ERR_OOM, SIM_ERR_CUDA. */
 sim_status sim_create(sim_t *out, const sim_grid *g, const sim_rock *r, const sim_fluid *f,
                       const sim_well *wells, int n_wells, const sim_options *o);
 void sim_destroy(sim_t h);
@@ -172,7 +176,9 @@ sim_ls_t sim_linear_system(sim_t h);
 /* A 2x2-block system over n = nx*ny*nz cells plus n_wells padded well rows.
  * rowptr (n+n_wells+1), cols (nnzb): host arrays, columns sorted per row;
  * well_cell0[w] = first perforated cell of well w (fixes its subdomain).
- * The pattern must be structurally symmetric. */
+ * The pattern must be structurally symmetric.  Errors: SIM_ERR_ARG for
+ * NULL arrays, sizes < 1 and the option values sim_create rejects (dt is
+ * not used here), SIM_ERR_OOM, SIM_ERR_CUDA. */
 sim_status sim_ls_create(sim_ls_t *out, int nx, int ny, int nz, int n_wells,
                          const int *rowptr, const int *cols, const int *well_cell0,
                          const sim_options *o);

@@ -48,6 +48,8 @@ extern "C" sim_status sim_batch_create(sim_batch_t *out, int n_members, const si
   if (!out || n_members < 1 || !grids || !rocks || !fluids || !wells || !n_wells || !opts || n_workers < 0)
     RS_FAIL(SIM_ERR_ARG, "sim_batch_create: bad argument");
   *out = nullptr;
+  for (int k = 0; k < n_members; k++)
+    if (const char *e = rs_opts_invalid(&opts[k])) RS_FAIL(SIM_ERR_ARG, "sim_batch_create: member %d: %s", k, e);
   std::unique_ptr<sim_batch_s> b(new sim_batch_s());
   RS_CUDA(cudaGetDevice(&b->dev));
   b->workers = n_workers > 0 ? n_workers : 8;

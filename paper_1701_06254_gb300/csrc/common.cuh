@@ -98,6 +98,7 @@ struct rs_opts {
   int max_cuts;
   double dt, sat_chop;
 };
+const char *rs_opts_invalid(const sim_options *o);
 rs_opts rs_opts_from(const sim_options *o);
 
 // ---------------------------------------------------------------- AMG -----

@@ -621,6 +621,19 @@ extern "C" sim_status sim_create(sim_t *out, const sim_grid *g, const sim_rock *
     RS_FAIL(SIM_ERR_ARG, "sim_create: bad grid");
   if ((long long)g->nx * g->ny * g->nz > 400000000LL) RS_FAIL(SIM_ERR_ARG, "sim_create: grid too large");
   if (!r->kx || !r->ky || !r->kz || !r->phi) RS_FAIL(SIM_ERR_ARG, "sim_create: NULL rock array");
+  if (const char *e = rs_opts_invalid(o)) RS_FAIL(SIM_ERR_ARG, "sim_create: %s", e);
+  if (!(o->dt > 0.0 && o->dt < HUGE_VAL)) RS_FAIL(SIM_ERR_ARG, "sim_create: dt must be finite and > 0");
+  for (int w = 0; w < n_wells; w++) {           // host-side well checks before any device work
+    const sim_well &W = wells[w];
+    if (W.kind != SIM_INJ && W.kind != SIM_PROD) RS_FAIL(SIM_ERR_ARG, "well %d: bad kind", w);
+    if (W.control == SIM_WRATE && W.kind != SIM_INJ) RS_FAIL(SIM_ERR_ARG, "well %d: water-rate control needs an injector", w);
+    if (W.control != SIM_BHP && W.control != SIM_WRATE) RS_FAIL(SIM_ERR_ARG, "well %d: control not supported", w);
+    if (W.n_perf < 1 || !W.perf_cell) RS_FAIL(SIM_ERR_ARG, "well %d: no perforations", w);
+    if (!(W.target > 0)) RS_FAIL(SIM_ERR_ARG, "well %d: target must be positive", w);
+    for (int q = 0; q < W.n_perf; q++)
+      if (W.perf_cell[q] < 0 || W.perf_cell[q] >= g->nx * g->ny * g->nz)
+        RS_FAIL(SIM_ERR_ARG, "well %d: perforation outside the grid", w);
+  }
   sim_s *h = new sim_s();
   std::unique_ptr<sim_s> guard(h);
   h->nx = g->nx; h->ny = g->ny; h->nz = g->nz; h->n = g->nx * g->ny * g->nz; h->nw = n_wells;
@@ -920,6 +933,7 @@ extern "C" sim_status sim_ls_create(sim_ls_t *out, int nx, int ny, int nz, int n
   if (!out || !rowptr || !cols || !o || nx < 1 || ny < 1 || nz < 1 || n_wells < 0 || (n_wells && !well_cell0))
     RS_FAIL(SIM_ERR_ARG, "sim_ls_create: bad argument");
   *out = nullptr;
+  if (const char *e = rs_opts_invalid(o)) RS_FAIL(SIM_ERR_ARG, "sim_ls_create: %s", e);
   std::unique_ptr<sim_ls_s> ls(new sim_ls_s());
   ls_init(ls.get(), nx, ny, nz, n_wells, rowptr, cols, well_cell0, rs_opts_from(o), (cudaStream_t)o->cuda_stream);
   *out = ls.release();

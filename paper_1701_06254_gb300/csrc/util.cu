@@ -1,6 +1,7 @@
 // Utilities: error text, launch counter, scans, deterministic reductions.
 #include "common.cuh"
 #include <cstdarg>
+#include <cmath>
 #include <cstdio>
 
 static thread_local char g_err[1024] = "";
@@ -163,6 +164,22 @@ __global__ void k_d2f(const double *a, float *b, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) b[i] = (float)a[i];
 }
 void rs_cast_d2f(const double *a, float *b, size_t n, cudaStream_t s) { if (n) { k_d2f<<<gs(n), 256, 0, s>>>(a, b, n); RS_LAUNCHED(1); } }
+
+// The option values that select a method or bound a loop, checked on the
+// host before any device work: nullptr when all are valid, else a message
+// naming the first bad one.  restart, max_lin and the tile sizes select
+// their defaults when <= 0 (see rs_opts_from) and are not checked here.
+const char *rs_opts_invalid(const sim_options *o) {
+  if (o->precision < SIM_PREC_FP64 || o->precision > SIM_PREC_MIXED_BF16) return "unknown precision";
+  if (o->decoupling < SIM_DEC_NONE || o->decoupling > SIM_DEC_QI) return "unknown decoupling";
+  if (o->reorder != 0 && o->reorder != 1) return "reorder must be 0 or 1";
+  if (o->newton != SIM_NEWTON_STANDARD && o->newton != SIM_NEWTON_INEXACT) return "unknown Newton variant";
+  if (!(o->newton_tol >= 0.0 && o->newton_tol < HUGE_VAL)) return "newton_tol must be finite and >= 0";
+  if (!(o->lin_tol >= 0.0 && o->lin_tol < HUGE_VAL)) return "lin_tol must be finite and >= 0";
+  if (!(o->amg_theta >= 0.0 && o->amg_theta <= 1.0)) return "amg_theta must lie in [0, 1]";
+  if (o->max_newton < 0 || o->max_cuts < 0 || o->amg_coarse_max < 0) return "negative iteration or size limit";
+  return nullptr;
+}
 
 rs_opts rs_opts_from(const sim_options *o) {
   rs_opts r;

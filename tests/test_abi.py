@@ -1,8 +1,12 @@
 """Host-side checks of the C-ABI library (no GPU calls): it builds for
 sm_103a, loads, and exports every entry point that include/resim.h declares."""
+import copy
 import ctypes
+import dataclasses
 import os
 import re
+
+import numpy as np
 
 import pytest
 
@@ -46,3 +50,81 @@ def test_default_options_and_error_path_without_gpu():
     assert b"NULL" in L.sim_last_error()
     rc = L.sim_ls_create(ctypes.byref(h), 0, 1, 1, 0, None, None, None, ctypes.byref(o))
     assert rc == 1
+
+
+def _create(R, case, **kw):
+    """sim_create on a case, with option fields overridden; returns the status
+    and the library's error text."""
+    L = R.lib()
+    o = R.make_options(dt=case.dt)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    g, fl, wells, keep = R._case_structs(case)
+    arrs = [np.ascontiguousarray(a, np.float64) for a in (case.kx, case.ky, case.kz, case.phi)]
+    rock = R.Rock(*(a.ctypes.data for a in arrs))
+    h = ctypes.c_void_p()
+    rc = L.sim_create(ctypes.byref(h), ctypes.byref(g), ctypes.byref(rock), ctypes.byref(fl), wells,
+                      len(case.wells), ctypes.byref(o))
+    return rc, L.sim_last_error().decode()
+
+
+@pytest.mark.parametrize("field,value,text", [
+    ("precision", 3, "precision"), ("precision", -1, "precision"), ("decoupling", 3, "decoupling"),
+    ("reorder", 2, "reorder"), ("newton", 2, "Newton"), ("newton_tol", -1e-8, "newton_tol"),
+    ("newton_tol", float("nan"), "newton_tol"), ("lin_tol", float("inf"), "lin_tol"),
+    ("amg_theta", 1.5, "amg_theta"), ("amg_theta", float("nan"), "amg_theta"),
+    ("max_newton", -1, "limit"), ("max_cuts", -2, "limit"), ("amg_coarse_max", -1, "limit"),
+    ("dt", 0.0, "dt"), ("dt", float("inf"), "dt")])
+def test_bad_options_are_rejected_before_device_work(field, value, text):
+    """Every rejected option value returns SIM_ERR_ARG with its name in the
+    message, on a machine without a GPU as on one with it: the checks run
+    before any allocation."""
+    import paper_1701_06254_gb300 as R
+    from paper_1701_06254_gb300 import inputs as I
+    rc, msg = _create(R, I.case0(), **{field: value})
+    assert rc == 1 and text in msg, (rc, msg)
+
+
+def test_bad_wells_are_rejected_before_device_work():
+    import paper_1701_06254_gb300 as R
+    from paper_1701_06254_gb300 import inputs as I
+    base = I.case0()
+    bad = [
+        (dict(kind=5), "bad kind"),
+        (dict(kind=I.PROD, control=I.WRATE), "needs an injector"),
+        (dict(control=7), "not supported"),
+        (dict(target=0.0), "positive"),
+        (dict(perf_cells=np.array([base.n], np.int32)), "outside the grid"),
+        (dict(perf_cells=np.array([-1], np.int32)), "outside the grid"),
+    ]
+    for change, text in bad:
+        c = copy.deepcopy(base)
+        c.wells[0] = dataclasses.replace(c.wells[0], **change)
+        rc, msg = _create(R, c)
+        assert rc == 1 and text in msg, (change, rc, msg)
+
+
+def test_ls_create_checks_options():
+    import paper_1701_06254_gb300 as R
+    L = R.lib()
+    o = R.make_options(decoupling=9)
+    rp = np.array([0, 1], np.int32)
+    ci = np.array([0], np.int32)
+    h = ctypes.c_void_p()
+    rc = L.sim_ls_create(ctypes.byref(h), 1, 1, 1, 0, rp.ctypes.data, ci.ctypes.data, None, ctypes.byref(o))
+    assert rc == 1 and b"decoupling" in L.sim_last_error()
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    """On a machine without a usable GPU the product path raises; it never
+    computes on the host."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_1701_06254_gb300 as R
+    from paper_1701_06254_gb300 import inputs as I
+    with pytest.raises(R.SimError) as e:
+        R.Sim(I.case0())
+    assert e.value.code == 2                          # SIM_ERR_CUDA
+    with pytest.raises(R.SimError):
+        R.WarmStart(seed=1)
