@@ -152,7 +152,9 @@ sim_status sim_assemble(sim_t h, double *scaled_norm);
 /* Solve J y = b for the assembled system: decouple (eq. 29), reorder
  * (eqs. 30-32), build RAS and AMG, run FGMRES(restart) with CPR-FPF
  * (Algorithm 2) to ||b - J y|| <= tol ||b|| on the decoupled system or
- * max_lin iterations.  y stays on the device (see sim_export). */
+ * max_lin iterations.  y stays on the device (read it with sim_ls_export,
+ * SIM_X_SOLUTION, on sim_linear_system(h)).
+ * SIM_ERR_ARG when tol is negative or not finite. */
 sim_status sim_linear_solve(sim_t h, double tol, int *iters, double *relres);
 
 /* One Newton iteration of Algorithm 1 at the current step length:
@@ -194,7 +196,7 @@ sim_status sim_ls_setup(sim_ls_t ls);
 
 /* FGMRES from y = 0 on the (decoupled) system; y: 2 per block row, host
  * or device.  SIM_ERR_NOT_CONVERGED is NOT returned for an iteration cap:
- * check *relres. */
+ * check *relres.  SIM_ERR_ARG when tol is negative or not finite. */
 sim_status sim_ls_solve(sim_ls_t ls, double tol, double *y, int *iters, double *relres);
 
 /* Apply one operator of the set-up system to x (2 per block row; for

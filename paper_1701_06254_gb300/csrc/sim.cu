@@ -801,6 +801,7 @@ extern "C" sim_status sim_assemble(sim_t h, double *scaled_norm) {
 
 extern "C" sim_status sim_linear_solve(sim_t h, double tol, int *iters, double *relres) {
   ABI_BEGIN
+  if (!(tol >= 0.0 && tol < HUGE_VAL)) RS_FAIL(SIM_ERR_ARG, "sim_linear_solve: tol must be finite and >= 0");
   if (!h) RS_FAIL(SIM_ERR_ARG, "NULL handle");
   ls_setup(h->ls);
   int its; double rel;
@@ -963,6 +964,7 @@ extern "C" sim_status sim_ls_setup(sim_ls_t ls) {
 
 extern "C" sim_status sim_ls_solve(sim_ls_t ls, double tol, double *y, int *iters, double *relres) {
   ABI_BEGIN
+  if (!(tol >= 0.0 && tol < HUGE_VAL)) RS_FAIL(SIM_ERR_ARG, "sim_ls_solve: tol must be finite and >= 0");
   if (!ls) RS_FAIL(SIM_ERR_ARG, "NULL handle");
   if (!ls->have_setup) RS_FAIL(SIM_ERR_STATE, "sim_ls_solve before sim_ls_setup");
   int its; double rel;

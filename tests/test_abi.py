@@ -128,3 +128,16 @@ def test_no_cpu_fallback_without_a_gpu():
     assert e.value.code == 2                          # SIM_ERR_CUDA
     with pytest.raises(R.SimError):
         R.WarmStart(seed=1)
+
+
+def test_solve_tolerances_are_checked_on_the_host():
+    import paper_1701_06254_gb300 as R
+    L = R.lib()
+    its, rel = ctypes.c_int(), ctypes.c_double()
+    for tol in (-1.0, float("nan"), float("inf")):
+        assert L.sim_ls_solve(None, tol, None, ctypes.byref(its), ctypes.byref(rel)) == 1
+        assert b"tol" in L.sim_last_error()
+        assert L.sim_linear_solve(None, tol, ctypes.byref(its), ctypes.byref(rel)) == 1
+        assert b"tol" in L.sim_last_error()
+    assert L.sim_ls_solve(None, 1e-8, None, None, None) == 1           # NULL handle
+    assert b"NULL" in L.sim_last_error()
