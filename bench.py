@@ -1,13 +1,15 @@
 """Benchmark: cell-timesteps/s of the GPU CPR-FGMRES Newton path.
 
 A step is one time step of the 200x200x25 channelised case (1M cells,
-13 wells, dt = 10 days): Newton iterations with assembly, ABF decoupling,
-per-subdomain potential reordering, RAS/BILU(0) and PMIS-AMG setup and
+13 wells, dt = 10 days): Newton iterations with assembly, Quasi-IMPES
+decoupling (ABF with --decoupling abf), per-subdomain potential reordering,
+RAS/BILU(0) and PMIS-AMG setup and
 CPR-FGMRES solves to relres 1e-6, all on the device.  Inputs are resident
 in HBM when the timed region starts; the working set (2x2 BSR Jacobian,
 Krylov basis) is larger than L2.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed_bf16|mixed|fp64]
+                  [--decoupling qi|abf|none] [--no-reorder] [--breakdown]
   python bench.py --impl reference     # the CPU oracle on the same workload
   python bench.py --workload ensemble  # 128 independent models (~16.6M cells) on one GPU
 """
@@ -36,6 +38,8 @@ DECOUPLING = {"none": 0, "abf": 1, "qi": 2}
 def oracle_opts(args):
     """The oracle's options for the configuration the GPU arm runs."""
     return dict(max_lin=args.max_lin, decoupling=DECOUPLING[args.decoupling], reorder=0 if args.no_reorder else 1)
+
+
 UNIT = "cell-timesteps/s"
 
 
