@@ -141,3 +141,22 @@ def test_solve_tolerances_are_checked_on_the_host():
         assert b"tol" in L.sim_last_error()
     assert L.sim_ls_solve(None, 1e-8, None, None, None) == 1           # NULL handle
     assert b"NULL" in L.sim_last_error()
+
+
+def test_every_workload_passes_the_host_checks():
+    """The workloads the tests and the benchmark run get past every host-side
+    check (without a GPU sim_create then stops at its first CUDA call)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_1701_06254_gb300 as R
+    from paper_1701_06254_gb300 import inputs as I
+    cases = [I.case0(), I.case1(nx=20, ny=20, nz=4), I.case2(nx=24, ny=24, nz=5), I.ensemble_member(0),
+             I.small_case()]
+    for c in cases:
+        for prec in (R.PREC_FP64, R.PREC_MIXED, R.PREC_MIXED_BF16):
+            for dec in (R.DEC_NONE, R.DEC_ABF, R.DEC_QI):
+                o = dict(newton=0 if c.newton == "standard" else 1, newton_tol=c.newton_tol, lin_tol=c.lin_tol,
+                         sat_chop=c.sat_chop, precision=prec, decoupling=dec)
+                rc, msg = _create(R, c, **o)
+                assert rc == 2, (c.name, prec, dec, rc, msg)
