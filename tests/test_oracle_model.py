@@ -54,6 +54,25 @@ def test_linear_pressure_profile(oracle_lib):
     np.testing.assert_allclose(qw, [1000.0 * q, -1000.0 * q], rtol=1e-10)
 
 
+def test_series_flow_through_heterogeneous_cells(oracle_lib):
+    """Steady incompressible single-phase water through cells of different
+    permeability in series: the same rate q crosses every face, and the
+    pressure drop between neighbouring cell centres is the sum of the two
+    half-cell resistances, q mu_w (dx / (2 k_i) + dx / (2 k_i+1)) / (C_D A)
+    (Darcy's law, eq. (1), on each half cell)."""
+    q, mu_w, dx, A, n = 10.0, 0.5, 10.0, 100.0, 30
+    c = line_case(n, dx, 100.0, q, 100.0, 0.8)
+    k = np.exp(np.random.default_rng(8).normal(math.log(100.0), 1.0, n))
+    c.kx, c.ky, c.kz = k, k.copy(), k.copy()
+    c.dy = c.dz = 10.0
+    s = oracle_lib.Sim(c, newton_tol=1e-13, lin_tol=1e-13, max_lin=200)
+    s.init_hydrostatic()
+    assert s.advance(1) == 0
+    p = s.get_state()[0]
+    drop = q * mu_w * (dx / (2.0 * k[:-1]) + dx / (2.0 * k[1:])) / (CDARCY * A)
+    np.testing.assert_allclose(-np.diff(p), drop, rtol=1e-9)
+
+
 def test_peaceman_isotropic_square(oracle_lib):
     """Peaceman's equivalent radius for an isotropic square cell is
     0.14 sqrt(dx^2 + dy^2) = 0.198 dx (the classical result)."""

@@ -174,6 +174,37 @@ def test_subdomains_partition_and_overlap(oracle_lib):
     assert s.ls.nsub == 3 * 3
 
 
+def test_ras_is_restricted_schwarz_with_exact_local_solves(oracle_lib):
+    """The RAS stage of Algorithm 2 is sum_s R~_s^T A_s^{-1} R_s: each
+    subdomain solves on its extended rows and keeps only the rows it owns.
+    On a heterogeneous 1D line in natural order every extended matrix is
+    block tridiagonal, so BILU(0) is its exact LU, and the output at a
+    subdomain's owned unknowns equals a dense solve of its extended system."""
+    n = 40
+    kk = np.exp(np.random.default_rng(3).normal(np.log(100.0), 1.0, n))
+    c = I.Case("line", n, 1, 1, 10.0, 10.0, 10.0, 1000.0, kk, kk.copy(), kk.copy(),
+               np.full(n, 0.2), I.Fluid(g=0.0), [], dt=1.0, n_steps=1)
+    s = _system(oracle_lib, c, 80, tile_x=4, tile_y=1, reorder=0)
+    s.ls.setup()
+    assert s.ls.nsub == 10
+    rp, ci, val, b, key = s.ls.get()
+    J = _dense_J(rp, ci, val, n)
+    f = np.random.default_rng(4).standard_normal(2 * n)
+    x = s.ls.ras(f)
+    expect = np.full(2 * n, np.nan)
+    for k in range(s.ls.nsub):
+        d = s.ls.sub(k)
+        ext = list(d["ext"])
+        assert len(ext) == len(d["own"]) + (k > 0) + (k < s.ls.nsub - 1)     # overlap 1
+        idx = np.array([2 * g + e for g in ext for e in (0, 1)])
+        y = np.linalg.solve(J[np.ix_(idx, idx)], f[idx])
+        for g in d["own"]:
+            a = ext.index(g)
+            expect[2 * g:2 * g + 2] = y[2 * a:2 * a + 2]
+    assert not np.isnan(expect).any()
+    np.testing.assert_allclose(x, expect, rtol=1e-10, atol=1e-12 * np.abs(expect).max())
+
+
 def test_reordered_saturation_block_is_lower_triangular(oracle_lib):
     """Upstream weighting makes each cell's water equation depend only on
     the saturations of cells with a higher potential, so after the
