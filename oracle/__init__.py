@@ -36,11 +36,17 @@ def build(force: bool = False) -> str:
             return _LIB
     os.makedirs(_LIBDIR, exist_ok=True)
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=gnu11", "-fPIC", "-shared",
-           "-o", tmp] + [os.path.join(_HERE, s) for s in _SRC] + ["-lm"]
-    subprocess.run(cmd, check=True)
+    compile_sources(_HERE, tmp)
     os.replace(tmp, _LIB)
     return _LIB
+
+
+def compile_sources(src_dir: str, out: str) -> None:
+    """gcc the oracle's C files found in src_dir into the shared library out
+    (also used by the tests that build a copy with a planted mistake)."""
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=gnu11", "-fPIC", "-shared",
+           "-o", out] + [os.path.join(src_dir, s) for s in _SRC] + ["-lm"]
+    subprocess.run(cmd, check=True)
 
 
 class Grid(C.Structure):

@@ -1,0 +1,120 @@
+"""The oracle's pins catch plausible mistakes (no GPU needed).
+
+Each case plants one mistake in a private copy of the oracle's C sources
+(a dropped term, a wrong sign, a transposed operand or index, a reversed
+comparison, a wrong constant), builds that copy into its own library, and
+runs the pin that should expose it with the copy in place of the oracle:
+the pin must fail.  The real oracle is untouched; the planted copies live
+in pytest's temporary directory.
+
+Mistakes that would make the C code read out of bounds or loop forever are
+not planted (they would end the test process rather than fail a pin).
+"""
+import ctypes
+import importlib
+import os
+
+import pytest
+
+# (name, source file, text that occurs once, its replacement, pin module, pin name, pin arguments)
+MUTATIONS = [
+    # model and discretisation, eqs. (3)-(18)
+    ("accumulation: dropped d(phi)/dp term", "or_model.c",
+     "J[0] += vt * (P[c].dphi * P[c].rho[1] + P[c].phi * P[c].drho[1]) * so;",
+     "J[0] += vt * (P[c].phi * P[c].drho[1]) * so;",
+     "test_oracle_model", "test_jacobian_matches_finite_differences", dict(seed=5, crossflow=False)),
+    ("flux: wrong sign of dF/dp_d", "or_model.c",
+     "+ Tm * P[d].dpot[a];", "- Tm * P[d].dpot[a];",
+     "test_oracle_model", "test_jacobian_matches_finite_differences", dict(seed=6, crossflow=False)),
+    ("flux: oil and water rows swapped", "or_model.c",
+     "int e = 1 - a;                       /* equation row: oil 0, water 1 */",
+     "int e = a;",
+     "test_oracle_model", "test_linear_pressure_profile", {}),
+    ("flux: downstream instead of upstream mobility, eq. (18)", "or_model.c",
+     "int upc = P[c].pot[a] >= P[d].pot[a];", "int upc = P[c].pot[a] < P[d].pot[a];",
+     "test_oracle_model", "test_buckley_leverett_front", {}),
+    ("potential: gravity term with the wrong sign, eq. (5)", "or_model.c",
+     "P->pot[a] = p - P->rho[a] * gz5;", "P->pot[a] = p + P->rho[a] * gz5;",
+     "test_oracle_model", "test_hydrostatic_initial_state_is_at_rest", {}),
+    ("transmissibility: arithmetic instead of harmonic mean", "or_model.c",
+     "S->ft[nf++] = OR_CDARCY * (g->dy * g->dz) / (g->dx / (2.0 * kx[c]) + g->dx / (2.0 * kx[d]));",
+     "S->ft[nf++] = OR_CDARCY * (g->dy * g->dz) * (kx[c] + kx[d]) / (2.0 * g->dx);",
+     "test_oracle_model", "test_series_flow_through_heterogeneous_cells", {}),
+    ("well index: Peaceman radius constant halved", "or_model.c",
+     "double ro = 0.28 *", "double ro = 0.14 *",
+     "test_oracle_model", "test_peaceman_isotropic_square", {}),
+    ("well: drawdown with the wrong sign, eq. (10)", "or_model.c",
+     "double dd = (S->pb[w] - S->p[c]) + P[c].rho[a] * dz5;",
+     "double dd = (S->p[c] - S->pb[w]) + P[c].rho[a] * dz5;",
+     "test_oracle_model", "test_linear_pressure_profile", {}),
+    ("old accumulation: oil stored with the water density", "or_model.c",
+     "S->acc0[2 * c + 0] = P.phi * P.rho[1] * (1.0 - S->s[c]);",
+     "S->acc0[2 * c + 0] = P.phi * P.rho[0] * (1.0 - S->s[c]);",
+     "test_oracle_model", "test_mass_balance_identity", dict(seed=3)),
+    ("forcing term: divided by the new residual norm, eq. (26)", "or_model.c",
+     "double eta = (bn - rprev) / bprev;", "double eta = (bn - rprev) / bn;",
+     "test_oracle_model", "test_forcing_term_choice_two", {}),
+    # processing, eqs. (29)-(32)
+    ("ABF: inverse of the diagonal block transposed", "or_solve.c",
+     "double i00 = d / det, i01 = -b / det, i10 = -c / det, i11 = a / det;",
+     "double i00 = d / det, i01 = -c / det, i10 = -b / det, i11 = a / det;",
+     "test_oracle_solver", "test_decoupling_keeps_solution", dict(dec=1)),
+    ("Quasi-IMPES: ratio inverted", "or_solve.c",
+     "double ratio = ls->val[4 * (size_t)qd + 1] / ls->val[4 * (size_t)qd + 3];",
+     "double ratio = ls->val[4 * (size_t)qd + 3] / ls->val[4 * (size_t)qd + 1];",
+     "test_oracle_solver", "test_decoupling_keeps_solution", dict(dec=2)),
+    ("reordering: ascending instead of descending potential, eq. (30)", "or_solve.c",
+     "if (ka > kb) return -1;                 /* descending potential */\n  if (ka < kb) return 1;",
+     "if (ka < kb) return -1;\n  if (ka > kb) return 1;",
+     "test_oracle_solver", "test_potential_reordering_worked_example", {}),
+    ("RAS: overlap rows written back (not restricted)", "or_solve.c",
+     "    for (int b = 0; b < S->nown; b++) {\n      int g = S->own[b], a = S->opos[b];\n",
+     "    for (int a = 0; a < m; a++) {\n      int g = S->ext[a];\n",
+     "test_oracle_solver", "test_ras_is_restricted_schwarz_with_exact_local_solves", {}),
+    ("GMRES: Givens rotation with the wrong sign", "or_solve.c",
+     "h[k + 1] = -sn[k] * h[k] + cs[k] * h[k + 1];", "h[k + 1] = sn[k] * h[k] + cs[k] * h[k + 1];",
+     "test_oracle_solver", "test_fgmres_iterations_equal_minimal_residual_gmres", dict(tile=(2, 2), coarse=8)),
+    ("GMRES: Hessenberg transposed in the back substitution", "or_solve.c",
+     "s -= H[(size_t)k * m + l] * yy[l];", "s -= H[(size_t)l * m + k] * yy[l];",
+     "test_oracle_solver", "test_fgmres_iterations_equal_minimal_residual_gmres", dict(tile=(3, 2), coarse=128)),
+    # AMG (Algorithm 2, pressure stage)
+    ("strength: comparison reversed", "or_amg.c",
+     "-A->v[q] >= thr", "-A->v[q] <= thr",
+     "test_oracle_solver", "test_strength_hand_example", {}),
+    ("interpolation: alpha inverted", "or_amg.c",
+     "alpha = sneg / snegc;", "alpha = snegc / sneg;",
+     "test_oracle_solver", "test_interpolation_and_galerkin_product", {}),
+    ("interpolation: weights with the wrong sign", "or_amg.c",
+     "P->v[o++] = -(alpha * A->v[q]) / dg;", "P->v[o++] = (alpha * A->v[q]) / dg;",
+     "test_oracle_solver", "test_interpolation_and_galerkin_product", {}),
+    ("V-cycle: coarse-grid correction subtracted", "or_amg.c",
+     "for (int i = 0; i < n; i++) x[i] += t[i];", "for (int i = 0; i < n; i++) x[i] -= t[i];",
+     "test_oracle_solver", "test_vcycle_convergence_on_poisson", {}),
+]
+
+
+@pytest.fixture(scope="module")
+def oracle_mod():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+@pytest.mark.parametrize("name,src,old,new,mod,pin,kw", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pin_catches_planted_mistake(oracle_mod, tmp_path, monkeypatch, name, src, old, new, mod, pin, kw):
+    here = os.path.dirname(oracle_mod.__file__)
+    for f in oracle_mod._SRC + ["or_internal.h"]:
+        text = open(os.path.join(here, f)).read()
+        if f == src:
+            assert text.count(old) == 1, f"{name}: the text to replace occurs {text.count(old)} times in {src}"
+            text = text.replace(old, new)
+        (tmp_path / f).write_text(text)
+    so = str(tmp_path / "liboracle_planted.so")
+    oracle_mod.compile_sources(str(tmp_path), so)
+    lib = ctypes.CDLL(so)
+    oracle_mod._sig(lib)
+    fn = getattr(importlib.import_module(mod), pin)
+    fn(oracle_mod, **kw)                                  # the real oracle passes the pin ...
+    monkeypatch.setattr(oracle_mod, "_lib", lib)
+    with pytest.raises(AssertionError):                   # ... the planted copy fails it
+        fn(oracle_mod, **kw)

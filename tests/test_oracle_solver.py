@@ -148,6 +148,43 @@ def test_fgmres_cpr_matches_dense_solve(oracle_lib, tile, coarse):
     assert np.linalg.norm(y - ystar) <= 1e-11 * cond * np.linalg.norm(ystar)
 
 
+@pytest.mark.parametrize("tile,coarse", [((2, 2), 8), ((3, 2), 128)])
+def test_fgmres_iterations_equal_minimal_residual_gmres(oracle_lib, tile, coarse):
+    """With a fixed preconditioner M (the CPR of Algorithm 2 is linear once
+    set up), FGMRES(m) before its first restart is right-preconditioned
+    GMRES: iterate k minimises ||b - A x|| over x in M K_k(A M, b).  So it
+    reaches the tolerance at the same iteration as a plain Arnoldi process
+    whose small least-squares problem is solved by numpy's lstsq (rounding
+    may move the crossing by one)."""
+    c = I.small_case(6, 5, 3, seed=12)
+    s = _system(oracle_lib, c, 60, tile_x=tile[0], tile_y=tile[1], amg_coarse_max=coarse)
+    s.ls.setup()
+    rp, ci, val, b, key = s.ls.get()
+    nb = c.n + 2
+    A = _dense_J(rp, ci, val, nb)
+    tol = 1e-10
+    rc, y, its, rel = s.ls.solve(tol)
+    assert rc == 0 and its < 50                       # converged inside the first cycle
+    beta = np.linalg.norm(b)
+    V = [b / beta]
+    H = np.zeros((52, 51))
+    its_ref = None
+    for j in range(50):
+        w = A @ s.ls.cpr(V[j])
+        for k in range(j + 1):                        # modified Gram-Schmidt
+            H[k, j] = V[k] @ w
+            w = w - H[k, j] * V[k]
+        H[j + 1, j] = np.linalg.norm(w)
+        V.append(w / H[j + 1, j])
+        e1 = np.zeros(j + 2)
+        e1[0] = beta
+        yk = np.linalg.lstsq(H[:j + 2, :j + 1], e1, rcond=None)[0]
+        if np.linalg.norm(e1 - H[:j + 2, :j + 1] @ yk) <= tol * beta:
+            its_ref = j + 1
+            break
+    assert its_ref is not None and abs(its - its_ref) <= 1, (its, its_ref)
+
+
 def test_subdomains_partition_and_overlap(oracle_lib):
     """Owned sets partition the unknowns; the extended set of each
     subdomain is its owned rows plus their graph neighbours (overlap 1);
