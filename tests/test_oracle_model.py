@@ -54,6 +54,26 @@ def test_linear_pressure_profile(oracle_lib):
     np.testing.assert_allclose(qw, [1000.0 * q, -1000.0 * q], rtol=1e-10)
 
 
+def test_pressure_dependent_viscosity(oracle_lib):
+    """Eq. (7) with c_mu != 0, steady incompressible single-phase water: the
+    same rate crosses every face, each face's mobility is taken from its
+    upstream cell (eq. 18), so the drop across the face between cells i and
+    i+1 is q mu_w(p_i) / T with mu_w(p) = mu_ref + c_mu (p - p_ref)."""
+    q, dx, A, k, n = 10.0, 10.0, 100.0, 100.0, 40
+    fl = incompressible_fluid()
+    fl.c_mu = (5e-4, 0.0)
+    c = line_case(n, dx, k, q, 100.0, 0.8, fluid=fl)
+    c.dy = c.dz = 10.0
+    s = oracle_lib.Sim(c, newton_tol=1e-13, lin_tol=1e-13, max_lin=200)
+    s.init_hydrostatic()
+    assert s.advance(1) == 0
+    p = s.get_state()[0]
+    mu = 0.5 + 5e-4 * (p[:-1] - fl.p_ref)
+    T = CDARCY * k * A / dx
+    np.testing.assert_allclose(-np.diff(p), q * mu / T, rtol=1e-9)
+    assert np.ptp(mu) > 0.005                                     # the viscosity does vary
+
+
 def test_series_flow_through_heterogeneous_cells(oracle_lib):
     """Steady incompressible single-phase water through cells of different
     permeability in series: the same rate q crosses every face, and the
@@ -181,6 +201,14 @@ def test_hydrostatic_initial_state_is_at_rest(oracle_lib):
     s.init_hydrostatic()
     p0, s0, _, _ = s.get_state()
     assert np.all(np.diff(p0.reshape(5, 16)[:, 0]) > 0)       # pressure rises with depth
+    # eq. (5) with eq. (6): p_k - rho_o(p_k) g z_k = p_datum - rho_o(p_datum) g z_top at every
+    # cell centre z_k = top + (k + 1/2) dz (depth positive downwards, bar)
+    f = c.fluid
+    rho = lambda p: f.rho_ref[1] * (1.0 + f.c_f[1] * (p - f.p_ref))
+    z = c.top + (np.arange(5) + 0.5) * c.dz
+    pk = p0.reshape(5, 16)[:, 0]
+    np.testing.assert_allclose(pk - rho(pk) * f.g * z * 1e-5,
+                               c.p_init - rho(c.p_init) * f.g * c.top * 1e-5, rtol=1e-13)
     assert s.advance(2) == 0
     p1, s1, _, _ = s.get_state()
     np.testing.assert_allclose(p1, p0, rtol=1e-12)
@@ -203,17 +231,32 @@ def test_forcing_term_choice_two(oracle_lib):
 # gives s_hat_f = 1/sqrt(5): S_f = 0.2 + 0.6/sqrt(5) = 0.468328, and the
 # front travels at q/(phi A) * df_w/dS_w(S_f) = q/(phi A) * 2.696723.
 # ---------------------------------------------------------------------------
-def _fw(s, muw=0.5, muo=2.0):
+def _fw(s, muw=0.5, muo=2.0, nw=2.0, no=2.0):
+    """Fractional flow of water, Corey relative permeabilities, S_wc = S_or = 0.2."""
     sh = np.clip((s - 0.2) / 0.6, 0, 1)
-    lw, lo = sh ** 2 / muw, (1 - sh) ** 2 / muo
+    lw, lo = sh ** nw / muw, (1 - sh) ** no / muo
     return lw / (lw + lo)
 
 
-def _dfw(s, muw=0.5, muo=2.0):
+def _dfw(s, muw=0.5, muo=2.0, nw=2.0, no=2.0):
     sh = np.clip((s - 0.2) / 0.6, 0, 1)
-    lw, lo = sh ** 2 / muw, (1 - sh) ** 2 / muo
-    dlw, dlo = 2 * sh / muw / 0.6, -2 * (1 - sh) / muo / 0.6
+    lw, lo = sh ** nw / muw, (1 - sh) ** no / muo
+    dlw, dlo = nw * sh ** (nw - 1) / muw / 0.6, -no * (1 - sh) ** (no - 1) / muo / 0.6
     return (dlw * (lw + lo) - lw * (dlw + dlo)) / (lw + lo) ** 2
+
+
+def _welge_front(nw, no):
+    """Front saturation of the Buckley-Leverett solution: the tangent from
+    (S_wc, 0) to f_w, f_w'(S_f) (S_f - S_wc) = f_w(S_f), found by bisection
+    (the left side exceeds the right below S_f)."""
+    lo, hi = 0.2 + 1e-9, 0.8 - 1e-9
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if _dfw(mid, nw=nw, no=no) * (mid - 0.2) > _fw(mid, nw=nw, no=no):
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
 
 
 def test_welge_constants():
@@ -273,6 +316,30 @@ def test_buckley_leverett_front(oracle_lib):
         np.testing.assert_allclose(((sw - 0.2) * 0.2 * (100.0 / nx)).sum(), 0.02 * t_end, rtol=1e-6)
     assert 0.0 < gaps[1] < gaps[0] <= 3.5, gaps
     assert gaps[1] <= 2.5, gaps
+
+
+def test_buckley_leverett_front_unequal_exponents(oracle_lib):
+    """Corey exponents n_w = 3, n_o = 2: the front travels at
+    f_w'(S_f) = 2.345 pore volumes per unit q t / (phi A) (Welge tangent),
+    so at t = 150 d it sits at 35.2 m; upwinding smears the computed front
+    ahead of it by at most a few cells, and the water injected is all in
+    place."""
+    sf = _welge_front(3.0, 2.0)
+    speed = _fw(sf, nw=3.0, no=2.0) / (sf - 0.2)
+    assert speed == pytest.approx(2.345018, abs=1e-5)
+    nx, t_end, L, q, phi = 200, 150.0, 100.0, 0.02, 0.2
+    fl = incompressible_fluid()
+    fl.nw = 3.0
+    c = line_case(nx, L / nx, 100.0, q, 100.0, 0.2, dt=t_end / 300, phi=phi, fluid=fl)
+    s = oracle_lib.Sim(c, newton_tol=1e-9, lin_tol=1e-10, max_lin=200)
+    s.init_hydrostatic()
+    assert s.advance(300) == 0
+    sw = s.get_state()[1]
+    x = (np.arange(nx) + 0.5) * (L / nx)
+    xf = q * t_end / phi * speed
+    gap = x[np.nonzero(sw < 0.5 * (0.2 + sf))[0][0]] - xf
+    assert 0.0 < gap <= 2.5, gap
+    np.testing.assert_allclose(((sw - 0.2) * phi * (L / nx)).sum(), q * t_end, rtol=1e-6)
 
 
 def test_buckley_leverett_converges_under_refinement(oracle_lib):

@@ -47,6 +47,15 @@ MUTATIONS = [
      "double dd = (S->pb[w] - S->p[c]) + P[c].rho[a] * dz5;",
      "double dd = (S->p[c] - S->pb[w]) + P[c].rho[a] * dz5;",
      "test_oracle_model", "test_linear_pressure_profile", {}),
+    ("viscosity: pressure term with the wrong sign, eq. (7)", "or_model.c",
+     "P->mu[a] = f->mu_ref[a] + f->c_mu[a] * dp;", "P->mu[a] = f->mu_ref[a] - f->c_mu[a] * dp;",
+     "test_oracle_model", "test_pressure_dependent_viscosity", {}),
+    ("relative permeability: water exponent taken from oil", "or_model.c",
+     "P->kr[0] = f->krw_max * pow(sh, f->nw);", "P->kr[0] = f->krw_max * pow(sh, f->no);",
+     "test_oracle_model", "test_buckley_leverett_front_unequal_exponents", {}),
+    ("geometry: cell depth at the top face instead of the centre", "or_model.c",
+     "S->z[c] = g->top + ((double)k + 0.5) * g->dz;", "S->z[c] = g->top + ((double)k) * g->dz;",
+     "test_oracle_model", "test_hydrostatic_initial_state_is_at_rest", {}),
     ("old accumulation: oil stored with the water density", "or_model.c",
      "S->acc0[2 * c + 0] = P.phi * P.rho[1] * (1.0 - S->s[c]);",
      "S->acc0[2 * c + 0] = P.phi * P.rho[0] * (1.0 - S->s[c]);",
@@ -81,12 +90,18 @@ MUTATIONS = [
     ("strength: comparison reversed", "or_amg.c",
      "-A->v[q] >= thr", "-A->v[q] <= thr",
      "test_oracle_solver", "test_strength_hand_example", {}),
+    ("strength: a zero entry counts as strong", "or_amg.c",
+     "have && mx > 0.0 && ", "have && ",
+     "test_oracle_solver", "test_strength_hand_example", {}),
+    ("interpolation: positive entries not lumped into the diagonal", "or_amg.c",
+     "double dg = aii + spos,", "double dg = aii,",
+     "test_oracle_solver", "test_interpolation_and_galerkin_product", dict(positive=True)),
     ("interpolation: alpha inverted", "or_amg.c",
      "alpha = sneg / snegc;", "alpha = snegc / sneg;",
-     "test_oracle_solver", "test_interpolation_and_galerkin_product", {}),
+     "test_oracle_solver", "test_interpolation_and_galerkin_product", dict(positive=False)),
     ("interpolation: weights with the wrong sign", "or_amg.c",
      "P->v[o++] = -(alpha * A->v[q]) / dg;", "P->v[o++] = (alpha * A->v[q]) / dg;",
-     "test_oracle_solver", "test_interpolation_and_galerkin_product", {}),
+     "test_oracle_solver", "test_interpolation_and_galerkin_product", dict(positive=False)),
     ("V-cycle: coarse-grid correction subtracted", "or_amg.c",
      "for (int i = 0; i < n; i++) x[i] += t[i];", "for (int i = 0; i < n; i++) x[i] -= t[i];",
      "test_oracle_solver", "test_vcycle_convergence_on_poisson", {}),

@@ -330,6 +330,17 @@ def test_strength_hand_example(oracle_lib):
     L = h.level(0)
     s0 = L["strong"][rp[0]:rp[1]]
     np.testing.assert_array_equal(s0, [False, True, False, True, False])
+    # a row without negative off-diagonal entries has no strong connection,
+    # also when one of its stored entries is an exact zero (Galerkin products
+    # keep cancelled entries in the pattern)
+    M[4] = [-1.0, 0.0, 0.0, 0.0, 3.0]
+    M[3] = [-1.0, 0.0, 0.0, 3.0, 0.5]
+    rp, ci, v = _csr(M)
+    v[rp[4]] = 0.0                                           # stored zero at (4, 0)
+    h = oracle_lib.AMG(rp, ci, v, theta=0.25, coarse_max=1, max_levels=2)
+    st = h.level(0)["strong"]
+    assert not st[rp[4]:rp[5]].any()
+    np.testing.assert_array_equal(st[rp[3]:rp[4]], [True, False, False])
 
 
 @pytest.mark.parametrize("seed", range(6))
@@ -374,11 +385,18 @@ def test_pmis_invariants(oracle_lib, seed, symmetric):
     assert 0 < len(C) < n
 
 
-def test_interpolation_and_galerkin_product(oracle_lib):
+@pytest.mark.parametrize("positive", [False, True])
+def test_interpolation_and_galerkin_product(oracle_lib, positive):
     """Direct interpolation: C rows of P are unit rows; an F row of a
-    zero-row-sum matrix row sums to 1.  The coarse matrix equals the dense
+    zero-row-sum matrix row sums to 1, also when the row has positive
+    off-diagonal entries (they are lumped into the diagonal, so the
+    weights still reproduce constants).  The coarse matrix equals the dense
     product P^T A P."""
     M = _poisson3d(6)
+    if positive:                                 # weak positive couplings two cells apart along x
+        for c in range(M.shape[0]):
+            if c % 6 < 4:
+                M[c, c + 2] = M[c + 2, c] = 0.3
     # zero row sums in the interior: remove the Dirichlet-like excess on the boundary
     np.fill_diagonal(M, 0.0)
     np.fill_diagonal(M, -M.sum(axis=1))
@@ -396,9 +414,12 @@ def test_interpolation_and_galerkin_product(oracle_lib):
     Crows = np.nonzero(cf == 1)[0]
     np.testing.assert_array_equal(P[Crows], np.eye(nc)[np.arange(nc)])
     zero_sum = np.abs(M.sum(axis=1)) < 1e-14
+    checked = 0
     for i in np.nonzero((cf == -1) & zero_sum)[0]:
         if P[i].any():
             assert abs(P[i].sum() - 1.0) < 1e-14
+            checked += (M[i] > 0).sum() > 1 if positive else 1
+    assert checked > 10
     L1 = h.level(1)
     Ac = np.zeros((nc, nc))
     for i in range(nc):
