@@ -1,11 +1,12 @@
 """The oracle's pins catch plausible mistakes (no GPU needed).
 
-Each case plants one mistake in a private copy of the oracle's C sources
-(a dropped term, a wrong sign, a transposed operand or index, a reversed
-comparison, a wrong constant), builds that copy into its own library, and
-runs the pin that should expose it with the copy in place of the oracle:
-the pin must fail.  The real oracle is untouched; the planted copies live
-in pytest's temporary directory.
+Each case plants one mistake in a private copy of the oracle (a dropped
+term, a wrong sign, a transposed operand or index, a reversed comparison, a
+wrong constant): the C sources are copied, changed and built into their own
+library, or the network module's text is changed and executed as a module
+of its own.  The pin that should expose the mistake then runs with the copy
+in place of the oracle and must fail.  The real oracle is untouched; the
+planted C copies live in pytest's temporary directory.
 
 Mistakes that would make the C code read out of bounds or loop forever are
 not planted (they would end the test process rather than fail a pin).
@@ -133,3 +134,53 @@ def test_pin_catches_planted_mistake(oracle_mod, tmp_path, monkeypatch, name, sr
     monkeypatch.setattr(oracle_mod, "_lib", lib)
     with pytest.raises(AssertionError):                   # ... the planted copy fails it
         fn(oracle_mod, **kw)
+
+
+# the network oracle (numpy): (name, text that occurs once, its replacement, pin name, pin arguments)
+NN_MUTATIONS = [
+    ("conv: tap order z-fastest instead of x-fastest",
+     "OFFSETS = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]",
+     "OFFSETS = [(dx, dy, dz) for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1)]",
+     "test_conv_matches_brute_force", {}),
+    ("conv backward: gradient shifted the wrong way",
+     "dX += _shift(G @ W[t], -dx, -dy, -dz)", "dX += _shift(G @ W[t], dx, dy, dz)",
+     "test_conv_backward_is_the_adjoint", {}),
+    ("conv backward: weight gradient from the unshifted input",
+     "dW[t] = Gf.T @ S.reshape(-1, S.shape[-1])", "dW[t] = Gf.T @ X.reshape(-1, X.shape[-1])",
+     "test_conv_backward_is_the_adjoint", {}),
+    ("pool: divided by 8 at ragged edges", "    return S / cnt\n", "    return S / 8.0\n",
+     "test_pool_and_up_adjoints", dict(shape=(3, 5, 7))),
+    ("pool backward: not divided by the child count", "    Gs = G / cnt\n", "    Gs = G\n",
+     "test_pool_and_up_adjoints", dict(shape=(4, 6, 8))),
+    ("forward: skip concatenated before the up-sampled tensor",
+     "np.concatenate([up(b2, s1), e1], axis=-1)", "np.concatenate([e1, up(b2, s1)], axis=-1)",
+     "test_network_gradient_matches_finite_differences", {}),
+    ("backward: ReLU mask dropped on a skip gradient",
+     'de1 = r(masked("c11", dcat1[..., 32:] + pool_backward(s1, dp2)))',
+     'de1 = r(dcat1[..., 32:] + pool_backward(s1, dp2))',
+     "test_network_gradient_matches_finite_differences", {}),
+    ("loss: factor 1/2 dropped", "return 0.5 * float(np.sum(E * E)) / n", "return float(np.sum(E * E)) / n",
+     "test_loss_definition", {}),
+    ("Adam: second moment without its bias correction", "vh = v / (1.0 - beta2 ** t)", "vh = v / (1.0 - beta2)",
+     "test_adam_constant_gradient_every_step", {}),
+    ("Adam: first moment not accumulated", "m = beta1 * m + (1.0 - beta1) * g", "m = (1.0 - beta1) * g",
+     "test_adam_constant_gradient_every_step", {}),
+    ("bf16: ties rounded up instead of to even", "r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16",
+     "r = ((u + 0x8000) >> 16) << 16", "test_bf16_round_matches_torch", {}),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pin,kw", NN_MUTATIONS, ids=[m[0] for m in NN_MUTATIONS])
+def test_network_pin_catches_planted_mistake(monkeypatch, name, old, new, pin, kw):
+    import types
+    from oracle import nn
+    text = open(nn.__file__).read()
+    assert text.count(old) == 1, f"{name}: the text to replace occurs {text.count(old)} times"
+    planted = types.ModuleType("planted_nn")
+    exec(compile(text.replace(old, new), "planted_nn.py", "exec"), planted.__dict__)
+    tests = importlib.import_module("test_oracle_nn")
+    fn = getattr(tests, pin)
+    fn(**kw)                                              # the real network oracle passes the pin ...
+    monkeypatch.setattr(tests, "nn", planted)
+    with pytest.raises(AssertionError):                   # ... the planted copy fails it
+        fn(**kw)

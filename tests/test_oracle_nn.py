@@ -118,6 +118,18 @@ def test_adam_first_step_closed_form():
     np.testing.assert_allclose(p1, p - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-14)
 
 
+def test_adam_constant_gradient_every_step():
+    """With a constant gradient the bias-corrected moments are exactly g and
+    g^2 at every step t (m_t = (1 - beta1^t) g, v_t = (1 - beta2^t) g^2), so
+    each step moves p by lr g / (|g| + eps)."""
+    g = np.array([0.3, -4.0, 1e-3, 7.5])
+    p, m, v = np.zeros(4), np.zeros(4), np.zeros(4)
+    for t in range(1, 8):
+        p_new, m, v = nn.adam_step(p, g, m, v, t, lr=0.01)
+        np.testing.assert_allclose(p - p_new, 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+        p = p_new
+
+
 def test_bf16_round_matches_torch():
     torch = pytest.importorskip("torch")
     x = np.random.default_rng(6).standard_normal(10000) * np.exp(np.random.default_rng(7).uniform(-20, 20, 10000))
