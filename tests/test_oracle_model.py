@@ -215,6 +215,41 @@ def test_hydrostatic_initial_state_is_at_rest(oracle_lib):
     np.testing.assert_allclose(s1, s0, atol=1e-14)
 
 
+def test_saturation_chop_bounds_each_update(oracle_lib):
+    """With sat_chop > 0 each Newton iteration changes every cell's s_w by
+    at most sat_chop (the chop acts on the update before it is applied),
+    and on a first iteration far from equilibrium it does bind."""
+    c = I.small_case(6, 5, 3, seed=21, dt=30.0)
+    for chop in (0.02, 0.05):
+        s = oracle_lib.Sim(c, max_newton=1, sat_chop=chop)
+        s.init_hydrostatic(sw0=0.2)
+        s.store_old()
+        s.set_dt(30.0)
+        p0, s0, _, _ = s.get_state()
+        rc, its = s.newton()
+        p1, s1, _, _ = s.get_state()
+        assert rc == 1 and its == 1                      # one update applied, not yet converged
+        ds = np.abs(s1 - s0)
+        assert ds.max() <= chop * (1 + 1e-12)
+        assert np.isclose(ds.max(), chop, rtol=1e-12)    # the chop was active
+        assert np.abs(p1 - p0).max() > 0
+
+
+def test_time_step_cuts_cover_the_interval(oracle_lib):
+    """A step whose Newton iteration fails is retried with half the step
+    length until it converges, and the rest of the interval is covered with
+    the cut length: the clock advances by exactly dt, in more than one
+    sub-step, and the state is a converged one."""
+    c = I.small_case(6, 5, 3, seed=21, dt=30.0)
+    s = oracle_lib.Sim(c, max_newton=3)
+    s.init_hydrostatic(sw0=0.2)
+    assert s.advance(1) == 0
+    st = s.stats()
+    assert st["cuts"] >= 1 and st["steps"] >= 2, st
+    assert st["t"] == 30.0
+    assert st["norm"] <= c.newton_tol
+
+
 def test_forcing_term_choice_two(oracle_lib):
     """Eq. (26), second choice, with the clamp to [0.01, 0.1]; eta_0 = 0.1."""
     f = oracle_lib.forcing

@@ -64,6 +64,13 @@ MUTATIONS = [
     ("forcing term: divided by the new residual norm, eq. (26)", "or_model.c",
      "double eta = (bn - rprev) / bprev;", "double eta = (bn - rprev) / bn;",
      "test_oracle_model", "test_forcing_term_choice_two", {}),
+    ("Newton: saturation chop never applied", "or_model.c",
+     "if (S->o.sat_chop > 0.0) {                 /* optional saturation chop */",
+     "if (0) {",
+     "test_oracle_model", "test_saturation_chop_bounds_each_update", {}),
+    ("time loop: a cut step advances the clock by the full step", "or_model.c",
+     "if (r == 0) { S->t += dt; rem -= dt;", "if (r == 0) { S->t += S->o.dt; rem -= dt;",
+     "test_oracle_model", "test_time_step_cuts_cover_the_interval", {}),
     # processing, eqs. (29)-(32)
     ("ABF: inverse of the diagonal block transposed", "or_solve.c",
      "double i00 = d / det, i01 = -b / det, i10 = -c / det, i11 = a / det;",
