@@ -216,20 +216,9 @@ __global__ void k_transpose_fill(int n, const int *rp, const int *ci, const doub
     tci[o] = i; tv[o] = v[q];
   }
 }
-__global__ void k_sort_rows(int n, const int *rp, int *ci, double *v) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int a0 = rp[i], a1 = rp[i + 1];
-  for (int a = a0 + 1; a < a1; a++) {
-    int c = ci[a]; double x = v[a]; int b = a - 1;
-    while (b >= a0 && ci[b] > c) { ci[b + 1] = ci[b]; v[b + 1] = v[b]; b--; }
-    ci[b + 1] = c; v[b + 1] = x;
-  }
-}
-
 // one warp per row: rows of at most 32 entries by a bitonic network across
 // the lanes (columns within a row are distinct, so the order is unique),
-// longer rows by the first lane as above
+// longer rows by an insertion sort in the first lane
 __global__ void k_sort_rows_warp(int n, const int *rp, int *ci, double *v) {
   int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= n) return;
