@@ -168,6 +168,32 @@ def _ptr(a):
     return a.ctypes.data
 
 
+def _vec(a, n, name, dtype=np.float64, out=False, at_least=False):
+    """a as a buffer of n values of dtype for a C call: a numpy array (an
+    input is converted to a contiguous copy of that type; an output must
+    already be one) or a contiguous tensor with that element type.  A wrong
+    count, type or layout raises ValueError here instead of letting the
+    library read or write past the caller's buffer."""
+    dt = np.dtype(dtype)
+    if hasattr(a, "data_ptr"):
+        ok = (a.is_contiguous() and a.element_size() == dt.itemsize
+              and bool(a.is_floating_point()) == bool(np.issubdtype(dt, np.floating)))
+        cnt = a.numel()
+    else:
+        if out:
+            ok = isinstance(a, np.ndarray) and a.dtype == dt and a.flags.c_contiguous and a.flags.writeable
+        else:
+            a = np.ascontiguousarray(a, dt)
+            ok = True
+        cnt = a.size if ok else 0
+    if not ok:
+        raise ValueError(f"{name}: expected a contiguous, writable buffer of {dt.name} values" if out else
+                         f"{name}: expected a contiguous buffer of {dt.name} values")
+    if (cnt < n) if at_least else (cnt != n):
+        raise ValueError(f"{name}: expected {'at least ' if at_least else ''}{n} values, got {cnt}")
+    return a
+
+
 def launch_count():
     return lib().sim_launch_count()
 
@@ -211,9 +237,10 @@ class LinearSystem:
             self.h = None
 
     def set(self, val, b, key):
-        val = np.ascontiguousarray(val, np.float64) if isinstance(val, np.ndarray) else val
-        b = np.ascontiguousarray(b, np.float64) if isinstance(b, np.ndarray) else b
-        key = np.ascontiguousarray(key, np.float64) if isinstance(key, np.ndarray) else key
+        nnzb = getattr(self, "nnzb", None)
+        val = _vec(val, 4 * nnzb, "val") if nnzb is not None else _vec(val, 0, "val", at_least=True)
+        b = _vec(b, 2 * self.nb, "b")
+        key = _vec(key, self.n, "key")
         _check(self._L.sim_ls_set(self.h, _ptr(val), _ptr(b), _ptr(key)))
 
     def setup(self):
@@ -221,20 +248,22 @@ class LinearSystem:
 
     def solve(self, tol, y=None):
         nb = self._nb()
-        out = np.zeros(2 * nb) if y is None else y
+        out = np.zeros(2 * nb) if y is None else _vec(y, 2 * nb, "y", out=True)
         its, rel = C.c_int(), C.c_double()
         _check(self._L.sim_ls_solve(self.h, tol, _ptr(out), C.byref(its), C.byref(rel)))
         return out, its.value, rel.value
 
     def apply(self, op, x):
         x = np.ascontiguousarray(x, np.float64)
+        if op in (OP_SPMV, OP_RAS, OP_CPR, OP_VCYCLE):         # an unknown op is the library's to reject
+            x = _vec(x, self.n if op == OP_VCYCLE else 2 * self.nb, "x")
         y = np.zeros_like(x)
         _check(self._L.sim_ls_apply(self.h, op, _ptr(x), _ptr(y)))
         return y
 
     def residual_norm(self, x):
         """||b - A x||_2 of the current (decoupled after setup) system."""
-        x = np.ascontiguousarray(x, np.float64) if isinstance(x, np.ndarray) else x
+        x = _vec(x, 2 * self.nb, "x")
         nrm = C.c_double()
         _check(self._L.sim_ls_residual_norm(self.h, _ptr(x), C.byref(nrm)))
         return nrm.value
@@ -350,16 +379,16 @@ class Sim:
                                             self.case.sw_init if sw0 is None else sw0))
 
     def set_state(self, p, sw, pb, t=0.0):
-        conv = lambda a: np.ascontiguousarray(a, np.float64) if not hasattr(a, "data_ptr") else a
-        p, sw = conv(p), conv(sw)
-        pb = conv(pb if self.nw else np.zeros(1))
+        p, sw = _vec(p, self.n, "p"), _vec(sw, self.n, "sw")
+        pb = _vec(pb, self.nw, "pb", at_least=True) if self.nw else np.zeros(1)
         _check(self._L.sim_set_state(self.h, _ptr(p), _ptr(sw), _ptr(pb), t))
 
     def get_state(self, out=None):
         if out is None:
             p, sw, pb = np.zeros(self.n), np.zeros(self.n), np.zeros(max(self.nw, 1))
         else:
-            p, sw, pb = out
+            p, sw = _vec(out[0], self.n, "p", out=True), _vec(out[1], self.n, "sw", out=True)
+            pb = _vec(out[2], self.nw, "pb", out=True, at_least=True)
         t = C.c_double()
         _check(self._L.sim_get_state(self.h, _ptr(p), _ptr(sw), _ptr(pb), C.byref(t)))
         return p, sw, pb[:self.nw] if out is None else pb, t.value
@@ -516,18 +545,28 @@ class WarmStart:
         a = np.ascontiguousarray(flat, np.float32)
         _check(self._L.sim_ws_set_params(self.h, _ptr(a), a.size))
 
+    @staticmethod
+    def _grid(a, name):
+        a = np.ascontiguousarray(a, np.float32)
+        if a.ndim != 4 or a.shape[3] != 8 or min(a.shape[:3]) < 1:
+            raise ValueError(f"{name}: expected shape (nz, ny, nx, 8), got {a.shape}")
+        return a
+
     def forward(self, feat):
         """feat (nz, ny, nx, 8) -> output (nz, ny, nx, 8), FP32."""
-        f = np.ascontiguousarray(feat, np.float32)
+        f = self._grid(feat, "feat")
         nz, ny, nx = f.shape[:3]
         y = np.zeros((nz, ny, nx, 8), np.float32)
         _check(self._L.sim_ws_forward(self.h, nx, ny, nz, _ptr(f), _ptr(y)))
         return y
 
     def backward(self, feat, target):
-        """Forward + loss + backward for one sample; gradients accumulate."""
-        f = np.ascontiguousarray(feat, np.float32)
+        """Forward + loss + backward for one sample (feat (nz, ny, nx, 8),
+        target (nz, ny, nx, 2)); gradients accumulate."""
+        f = self._grid(feat, "feat")
         t = np.ascontiguousarray(target, np.float32)
+        if t.shape != f.shape[:3] + (2,):
+            raise ValueError(f"target: expected shape {f.shape[:3] + (2,)}, got {t.shape}")
         nz, ny, nx = f.shape[:3]
         loss = C.c_double()
         _check(self._L.sim_ws_backward(self.h, nx, ny, nz, _ptr(f), _ptr(t), C.byref(loss)))
