@@ -65,3 +65,39 @@ def test_decoupling_codes_agree():
     for name, code in bench.DECOUPLING.items():
         assert int(re.search(r"SIM_DEC_%s = (\d+)" % name.upper(), lib).group(1)) == code
         assert int(re.search(r"OR_DEC_%s = (\d+)" % name.upper(), orc).group(1)) == code
+
+
+def test_clock_record_parsing():
+    """The nvidia-smi samples taken during the timed region: median SM
+    clock, the maximum, and every throttle reason seen active at least once
+    (what decides whether a run is kept)."""
+    c = bench.Clocks(0)
+
+    class _Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    rows = [
+        "0, 2070, 2070, 310.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 402.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 398.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ]
+    c.f.write("\n".join(rows) + "\n")
+    c.f.flush()
+    c.p = _Done()
+    d = c.stop()
+    assert d["sm_mhz"] == 2070.0 and d["sm_max_mhz"] == 2070.0 and d["samples"] == 3
+    assert d["power_w_max"] == 402.0 and d["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_record_without_nvidia_smi():
+    c = bench.Clocks(0)
+    try:
+        assert c.stop() is None                   # never started: no record, no exception
+    finally:
+        c.f.close()
+        os.unlink(c.f.name)
