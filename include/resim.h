@@ -122,6 +122,7 @@ void sim_default_options(sim_options *o);
 /* Create a simulator (copies everything).  Builds transmissibilities,
  * well indices, the 2x2 block sparsity pattern (cells, then one padded
  * block row per well) and the RAS partition; allocates device memory.
+ * Grids of at most 50M cells (the solver setup keeps 32-bit counts).
  * Errors: SIM_ERR_ARG for bad sizes/controls or option values (an unknown
  * precision, decoupling, reorder or Newton code; a tolerance that is
  * negative or not finite; amg_theta outside [0, 1]; a negative max_newton,
@@ -179,8 +180,9 @@ sim_ls_t sim_linear_system(sim_t h);
  * rowptr (n+n_wells+1), cols (nnzb): host arrays, columns sorted per row;
  * well_cell0[w] = first perforated cell of well w (fixes its subdomain).
  * The pattern must be structurally symmetric.  Errors: SIM_ERR_ARG for
- * NULL arrays, sizes < 1 and the option values sim_create rejects (dt is
- * not used here), SIM_ERR_OOM, SIM_ERR_CUDA. */
+ * NULL arrays, sizes < 1 or above sim_create's 50M cells, and the option
+ * values sim_create rejects (dt is not used here), SIM_ERR_OOM,
+ * SIM_ERR_CUDA. */
 sim_status sim_ls_create(sim_ls_t *out, int nx, int ny, int nz, int n_wells,
                          const int *rowptr, const int *cols, const int *well_cell0,
                          const sim_options *o);

@@ -619,7 +619,11 @@ extern "C" sim_status sim_create(sim_t *out, const sim_grid *g, const sim_rock *
   *out = nullptr;
   if (g->nx < 1 || g->ny < 1 || g->nz < 1 || !(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0))
     RS_FAIL(SIM_ERR_ARG, "sim_create: bad grid");
-  if ((long long)g->nx * g->ny * g->nz > 400000000LL) RS_FAIL(SIM_ERR_ARG, "sim_create: grid too large");
+  // counts inside the setup are 32-bit: the largest, the Galerkin products of
+  // one AMG level, reach ~30 per cell on the channelised 1M-cell case, so
+  // 2^31 would be crossed near 70M cells; the limit keeps a margin below that
+  if ((long long)g->nx * g->ny * g->nz > 50000000LL)
+    RS_FAIL(SIM_ERR_ARG, "sim_create: grid too large (at most 50M cells: 32-bit counts in the solver setup)");
   if (!r->kx || !r->ky || !r->kz || !r->phi) RS_FAIL(SIM_ERR_ARG, "sim_create: NULL rock array");
   if (const char *e = rs_opts_invalid(o)) RS_FAIL(SIM_ERR_ARG, "sim_create: %s", e);
   if (!(o->dt > 0.0 && o->dt < HUGE_VAL)) RS_FAIL(SIM_ERR_ARG, "sim_create: dt must be finite and > 0");
@@ -935,6 +939,8 @@ extern "C" sim_status sim_ls_create(sim_ls_t *out, int nx, int ny, int nz, int n
     RS_FAIL(SIM_ERR_ARG, "sim_ls_create: bad argument");
   *out = nullptr;
   if (const char *e = rs_opts_invalid(o)) RS_FAIL(SIM_ERR_ARG, "sim_ls_create: %s", e);
+  if ((long long)nx * ny * nz > 50000000LL)                 // as in sim_create
+    RS_FAIL(SIM_ERR_ARG, "sim_ls_create: grid too large (at most 50M cells: 32-bit counts in the solver setup)");
   std::unique_ptr<sim_ls_s> ls(new sim_ls_s());
   ls_init(ls.get(), nx, ny, nz, n_wells, rowptr, cols, well_cell0, rs_opts_from(o), (cudaStream_t)o->cuda_stream);
   *out = ls.release();

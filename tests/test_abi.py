@@ -160,3 +160,14 @@ def test_every_workload_passes_the_host_checks():
                          sat_chop=c.sat_chop, precision=prec, decoupling=dec)
                 rc, msg = _create(R, c, **o)
                 assert rc == 2, (c.name, prec, dec, rc, msg)
+
+
+def test_grid_size_limit():
+    """Grids above 50M cells are refused before any device work (the solver
+    setup's counts are 32-bit)."""
+    import paper_1701_06254_gb300 as R
+    from paper_1701_06254_gb300 import inputs as I
+    c = I.case0()
+    c.nx, c.ny, c.nz = 400, 400, 320                    # 51.2M cells; the rock arrays are never read
+    rc, msg = _create(R, c)
+    assert rc == 1 and "too large" in msg, (rc, msg)
