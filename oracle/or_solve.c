@@ -349,15 +349,15 @@ void or_cpr_apply(or_lsys *ls, const double *f, double *x)
 {
   int nu = 2 * ls->nb, n = ls->n;
   double *r = xc(nu, 8), *t = xc(nu, 8), *pc = xc(n, 8), *xp = xc(n, 8);
-  or_ras_apply(ls, f, x);                                /* 1: x = R(A)^{-1} f     */
-  or_bsr_mv(ls, x, t);                                   /* 2: r = f - A x         */
+  or_ras_apply(ls, f, x);                                /* x = R(A)^{-1} f        */
+  or_bsr_mv(ls, x, t);                                   /* r = f - A x            */
   for (int i = 0; i < nu; i++) r[i] = f[i] - t[i];
   for (int c = 0; c < n; c++) pc[c] = r[2 * c];          /*    Pi_r r (eq. 34)     */
-  or_amg_vcycle(&ls->amg, 0, pc, xp);                    /* 3: M(A_pp)^{-1}        */
+  or_amg_vcycle(&ls->amg, 0, pc, xp);                    /* M(A_pp)^{-1}           */
   for (int c = 0; c < n; c++) x[2 * c] += xp[c];         /*    x += Pi_p (eq. 35)  */
-  or_bsr_mv(ls, x, t);                                   /* 4: r = f - A x         */
+  or_bsr_mv(ls, x, t);                                   /* r = f - A x            */
   for (int i = 0; i < nu; i++) r[i] = f[i] - t[i];
-  or_ras_apply(ls, r, t);                                /* 5: x += R(A)^{-1} r    */
+  or_ras_apply(ls, r, t);                                /* x += R(A)^{-1} r       */
   for (int i = 0; i < nu; i++) x[i] += t[i];
   free(r); free(t); free(pc); free(xp);
 }

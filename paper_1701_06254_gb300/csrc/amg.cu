@@ -1,5 +1,5 @@
 // Algebraic multigrid on the pressure block A_pp: the M(A_pp)^{-1} stage of
-// CPR-FPF (Algorithm 2, step 3) of arXiv 1701.06254.  The paper fixes no AMG
+// CPR-FPF (the pressure stage of Algorithm 2) of arXiv 1701.06254.  The paper fixes no AMG
 // component; this library uses
 //   strength   S_i = { j != i : -a_ij >= theta * max_{k != i}(-a_ik) }
 //   coarsening PMIS with weights |S^T_i| + h(i), h = splitmix64 hash in [0,1)

@@ -329,15 +329,15 @@ void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32) {
   amg_level &L0 = ls->amg.lev[0];
   if (ls->o.precision != SIM_PREC_FP64) {
     float *z = z32, *r = ls->x32b.p;
-    ls_ras_apply<float, double>(ls, v, z, false);                                      // 1
-    { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, double, float>(ls, ls->val32.p, z, v, r, s); }  // 2
+    ls_ras_apply<float, double>(ls, v, z, false);                                      // RAS
+    { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, double, float>(ls, ls->val32.p, z, v, r, s); }  // r = v - A z
     k_gather_p<float, float><<<grid_for(n, 256), 256, 0, s>>>(n, r, L0.f32.p);
     RS_LAUNCHED(1);
-    { rs_timed tm(ls, SIM_T_VCYCLE); if (ls->capturing) amg_vcycle<float>(ls->amg, 0, s); else amg_vcycle_graph<float>(ls->amg, s); }  // 3
+    { rs_timed tm(ls, SIM_T_VCYCLE); if (ls->capturing) amg_vcycle<float>(ls->amg, 0, s); else amg_vcycle_graph<float>(ls->amg, s); }  // pressure V-cycle
     k_add_p<float><<<grid_for(n, 256), 256, 0, s>>>(n, L0.x32.p, z);
     RS_LAUNCHED(1);
-    { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, double, float>(ls, ls->val32.p, z, v, r, s); }  // 4
-    ls_ras_apply<float, float>(ls, r, z, true);                                        // 5
+    { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, double, float>(ls, ls->val32.p, z, v, r, s); }  // r = v - A z
+    ls_ras_apply<float, float>(ls, r, z, true);                                        // RAS, added
   } else {
     double *z = z64, *r = ls->x64a.p;
     ls_ras_apply<double, double>(ls, v, z, false);
@@ -360,15 +360,15 @@ void ls_cpr32(sim_ls_s *ls, const float *v, float *z) {
   int n = ls->n;
   amg_level &L0 = ls->amg.lev[0];
   float *r = ls->x32b.p;
-  ls_ras_apply<float, float>(ls, v, z, false);                                         // 1
-  { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, float, float>(ls, ls->val32.p, z, v, r, s); }   // 2
+  ls_ras_apply<float, float>(ls, v, z, false);                                         // RAS
+  { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, float, float>(ls, ls->val32.p, z, v, r, s); }   // r = v - A z
   k_gather_p<float, float><<<grid_for(n, 256), 256, 0, s>>>(n, r, L0.f32.p);
   RS_LAUNCHED(1);
-  { rs_timed tm(ls, SIM_T_VCYCLE); if (ls->capturing) amg_vcycle<float>(ls->amg, 0, s); else amg_vcycle_graph<float>(ls->amg, s); }  // 3
+  { rs_timed tm(ls, SIM_T_VCYCLE); if (ls->capturing) amg_vcycle<float>(ls->amg, 0, s); else amg_vcycle_graph<float>(ls->amg, s); }  // pressure V-cycle
   k_add_p<float><<<grid_for(n, 256), 256, 0, s>>>(n, L0.x32.p, z);
   RS_LAUNCHED(1);
-  { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, float, float>(ls, ls->val32.p, z, v, r, s); }   // 4
-  ls_ras_apply<float, float>(ls, r, z, true);                                          // 5
+  { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, float, float>(ls, ls->val32.p, z, v, r, s); }   // r = v - A z
+  ls_ras_apply<float, float>(ls, r, z, true);                                          // RAS, added
 }
 
 // ------------------------------------------------------------ init -------
