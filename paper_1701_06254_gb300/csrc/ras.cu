@@ -4,9 +4,10 @@
 // eqs. (30)-(32) applied inside each subdomain.  A subdomain is a column
 // tile of tile_x x tile_y cells over all layers (a well goes with the tile
 // of its first perforated cell); its local system is the owned rows plus
-// their graph neighbours (overlap 1).  Each subdomain maps to one thread block: the potential sort, the level sets of
-// the reordered factors, the factorisation and both triangular solves run
-// level by level inside that block.
+// their graph neighbours (overlap 1).  Each subdomain maps to one thread
+// block: the potential sort, the level sets of the reordered factors, the
+// factorisation and both triangular solves run level by level inside that
+// block.
 #include "common.cuh"
 #include <cuda_bf16.h>
 #include <algorithm>
