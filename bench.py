@@ -410,7 +410,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="cfg2")
+    ap.add_argument("--config", default="channelised", choices=["lognormal", "fivespot", "channelised"],
+                    help="workload: the 1M-cell channelised case (default), the 200k-cell five-spot or the "
+                         "2,000-cell log-normal case")
     ap.add_argument("--precision", default="mixed_bf16", choices=["mixed", "mixed_bf16", "fp64"],
                     help="preconditioner precision: FP32 AMG/ILU with BF16 RAS values (the 1M-cell case's "
                          "setting), FP32 throughout, or FP64")

@@ -130,7 +130,7 @@ def case0(seed: int = 0) -> Case:
     nx, ny, nz = 20, 20, 5
     rng = np.random.default_rng(seed)
     kh = _lognormal_iid(rng, nx * ny * nz, math.log(100.0), 1.0)
-    c = Case("cfg0_20x20x5", nx, ny, nz, 20.0, 20.0, 5.0, 2000.0,
+    c = Case("lognormal_20x20x5", nx, ny, nz, 20.0, 20.0, 5.0, 2000.0,
              kh.copy(), kh.copy(), 0.1 * kh, np.full(nx * ny * nz, 0.2),
              Fluid(), [], dt=1.0, n_steps=10)
     c.wells = [Well(INJ, WRATE, 200.0, c.column(0, 0)),
@@ -153,7 +153,7 @@ def case1(seed: int = 1, nx=100, ny=100, nz=20) -> Case:
     zs = (lnk - lnk.mean()) / lnk.std()
     cdf = 0.5 * (1.0 + np.vectorize(math.erf)(zs / math.sqrt(2.0)))
     phi = 0.1 + 0.2 * cdf
-    c = Case(f"cfg1_{nx}x{ny}x{nz}", nx, ny, nz, 20.0, 20.0, 5.0, 2000.0,
+    c = Case(f"fivespot_{nx}x{ny}x{nz}", nx, ny, nz, 20.0, 20.0, 5.0, 2000.0,
              kh.copy(), kh.copy(), 0.1 * kh, phi, Fluid(), [], dt=5.0, n_steps=30,
              newton="inexact", newton_tol=1e-8, lin_tol=1e-6, sat_chop=0.1)
     c.wells = [Well(INJ, WRATE, 500.0, c.column(i, j))
@@ -177,7 +177,7 @@ def case2(seed: int = 2, nx=200, ny=200, nz=25) -> Case:
     lnk = np.where(sand, math.log(500.0), math.log(5.0)) + 0.5 * noise
     kh = np.exp(lnk)
     phi = np.where(sand, 0.25, 0.10)
-    c = Case(f"cfg2_{nx}x{ny}x{nz}", nx, ny, nz, 20.0, 20.0, 5.0, 2000.0,
+    c = Case(f"channelised_{nx}x{ny}x{nz}", nx, ny, nz, 20.0, 20.0, 5.0, 2000.0,
              kh.copy(), kh.copy(), 0.1 * kh, phi, Fluid(), [], dt=10.0, n_steps=50,
              newton="standard", newton_tol=1e-6, lin_tol=1e-6, sat_chop=0.1)
     pi = [round(x * nx / 200.0) for x in (33, 100, 166)]
@@ -241,4 +241,4 @@ def random_state(case: Case, seed: int, s_lo=0.3, s_hi=0.7, p_lo=170.0, p_hi=230
     return p, sw, pb
 
 
-CASES = {"cfg0": case0, "cfg1": case1, "cfg2": case2}
+CASES = {"lognormal": case0, "fivespot": case1, "channelised": case2}

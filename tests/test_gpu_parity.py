@@ -240,13 +240,13 @@ def _run_compare(case, nsteps, **opts):
     return o, g
 
 
-def test_whole_run_cfg0_fp64():
+def test_whole_run_lognormal_case_fp64():
     """The plain method on the 20x20x5 case: 10 steps of 1 day, standard
     Newton to 1e-8, CPR-FGMRES to 1e-8."""
     _run_compare(I.case0(), 10)
 
 
-def test_whole_run_cfg0_mixed_precision():
+def test_whole_run_lognormal_case_mixed_precision():
     """Same run with the FP32 preconditioner: the converged Newton states do
     not depend on the preconditioner precision, so the same tolerances hold."""
     _run_compare(I.case0(), 10, precision=R.PREC_MIXED)
@@ -260,7 +260,7 @@ def test_whole_run_channelised_case_mixed_with_chop():
     _run_compare(c, 3, precision=R.PREC_MIXED)
 
 
-def test_whole_run_cfg0_bf16_ras():
+def test_whole_run_lognormal_case_bf16_ras():
     """RAS factor values stored in BF16 (FP32 arithmetic): the converged
     Newton states still match the FP64 oracle."""
     _run_compare(I.case0(), 5, precision=R.PREC_MIXED_BF16)
@@ -315,7 +315,7 @@ def test_zero_rhs_and_errors():
     assert e.value.code == 5          # SIM_ERR_NAN
 
 
-def test_full_size_cfg2_parity():
+def test_full_size_channelised_parity():
     """The 1M-cell case in the benchmark's configuration (mixed precision):
     assembly over all cells, bit-exact ABF, reordering and level-0 C/F split,
     and the GPU solution's true residual checked with the oracle's SpMV."""
