@@ -160,6 +160,24 @@ def vcycle_bytes(ls, precision):
     return total
 
 
+def state_difference(a, b):
+    """Largest per-cell differences between two states (p, s_w) of the same
+    grid: relative in pressure (to b's), absolute in water saturation."""
+    pa, sa = (np.asarray(x, np.float64) for x in a[:2])
+    pb, sb = (np.asarray(x, np.float64) for x in b[:2])
+    return {"p_rel_max": float(np.max(np.abs(pa - pb) / np.abs(pb))), "sw_abs_max": float(np.max(np.abs(sa - sb)))}
+
+
+def _host_state(sim):
+    """(p, s_w) copied to the host, or None (never raises: a comparison is
+    reported, not required)."""
+    try:
+        p, sw = sim.get_state()[:2]
+        return np.array(p), np.array(sw)
+    except Exception:
+        return None
+
+
 def oracle_newton_iteration(case, opts):
     """One Newton iteration of the CPU oracle on the first time step of the
     case (assembly + decoupling + reordering + RAS/AMG setup + CPR-FGMRES)."""
@@ -260,6 +278,7 @@ def measure_variant(R, torch, case, opts, args, ws=None):
                              "network_term_kept": st1["ws_used"] - st0["ws_used"],
                              "network_term_dropped": st1["ws_fallback"] - st0["ws_fallback"],
                              "mean_r0_over_b": (st1["ws_r0"] - st0["ws_r0"]) / dl}
+    out["_state"] = _host_state(sim)          # dropped before printing
     del sim
     return out
 
@@ -512,6 +531,7 @@ def main():
     if dist:
         dist.barrier()
     st1 = sim.stats()
+    end_state = _host_state(sim)              # after the timed region; compared with the FP64 variant below
     nk, kms = sim.ls.kernel_time(fam)
     breakdown = None
     if args.breakdown:
@@ -598,6 +618,20 @@ def main():
         lv = measure_variant(R, torch, case, opts, args, ws)
         lv["training"] = info
         variants[args.precision + "_learned"] = lv
+    precision_error = None
+    if variants is not None:
+        ref = variants["plain_fp64"].pop("_state", None)
+        learned = variants[args.precision + "_learned"].pop("_state", None)
+        try:
+            if ref is not None and end_state is not None:
+                precision_error = {
+                    "reference": "the plain FP64 GPU method over the same warm-up and timed steps "
+                                 "(it matches the FP64 oracle to 1e-6 in the parity tests)",
+                    args.precision: state_difference(end_state, ref)}
+                if learned is not None:
+                    precision_error[args.precision + "_learned"] = state_difference(learned, ref)
+        except Exception as e:                # reported, never fatal
+            precision_error = {"error": str(e)[:200]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -627,6 +661,7 @@ def main():
                            if ws is not None else None),
             "kernel_breakdown": breakdown,
             "variants": variants,
+            "precision_error_vs_fp64": precision_error,
         }
         print(json.dumps(line), flush=True)
     if dist:

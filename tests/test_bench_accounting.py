@@ -101,3 +101,21 @@ def test_clock_record_without_nvidia_smi():
     finally:
         c.f.close()
         os.unlink(c.f.name)
+
+
+def test_state_difference():
+    """Mixed-precision and FP64 end states: relative in pressure, absolute
+    in saturation, largest over the cells."""
+    import numpy as np
+    ref = (np.array([200.0, 100.0, 150.0]), np.array([0.2, 0.5, 0.8]))
+    run = (np.array([200.0, 100.0002, 150.0]), np.array([0.2, 0.5, 0.8000003]))
+    d = bench.state_difference(run, ref)
+    assert abs(d["p_rel_max"] - 2e-6) < 1e-12 and abs(d["sw_abs_max"] - 3e-7) < 1e-12
+    assert bench.state_difference(ref, ref) == {"p_rel_max": 0.0, "sw_abs_max": 0.0}
+
+
+def test_host_state_never_raises():
+    class _Broken:
+        def get_state(self):
+            raise RuntimeError("no device")
+    assert bench._host_state(_Broken()) is None
