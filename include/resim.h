@@ -15,6 +15,10 @@
  * Conventions (every entry point):
  *  - Returns a sim_status; SIM_OK = 0.  No entry point aborts the process.
  *    sim_last_error() returns a thread-local message for the last failure.
+ *    Every entry point returns SIM_ERR_ARG for a NULL handle or a NULL
+ *    required pointer, SIM_ERR_CUDA when a CUDA runtime call fails,
+ *    SIM_ERR_OOM when a device allocation fails and SIM_ERR_STATE for a call
+ *    out of order; an entry point without an "Errors" note has only these.
  *  - Units: p in bar, t in days, lengths in m, permeability in mD,
  *    viscosity in cP, density in kg/m3, compressibility in 1/bar, well
  *    rates in standard m3/day.
