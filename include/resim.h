@@ -141,7 +141,8 @@ void sim_destroy(sim_t h);
  * above the oil pressure of their first perforated cell; t = 0. */
 sim_status sim_init_hydrostatic(sim_t h, double p_datum, double sw0);
 
-/* State in caller buffers: p, sw (n each), pb (n_wells); host or device. */
+/* State in caller buffers: p, sw (n each), pb (n_wells); host or device.
+ * sim_get_state skips any output passed as NULL. */
 sim_status sim_set_state(sim_t h, const double *p, const double *sw, const double *pb, double t);
 sim_status sim_get_state(sim_t h, double *p, double *sw, double *pb, double *t);
 
