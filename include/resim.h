@@ -32,6 +32,9 @@
  *    values synchronise that stream.
  *  - A handle is not thread-safe; distinct handles may be used from
  *    distinct threads.
+ *  - One process drives one GPU: kernel attributes (shared-memory sizes)
+ *    are set once per process, on the device current at first use.  Run one
+ *    process per GPU (as bench.py does under torchrun).
  */
 #ifndef RESIM_H
 #define RESIM_H
