@@ -110,6 +110,9 @@ MUTATIONS = [
     ("interpolation: weights with the wrong sign", "or_amg.c",
      "P->v[o++] = -(alpha * A->v[q]) / dg;", "P->v[o++] = (alpha * A->v[q]) / dg;",
      "test_oracle_solver", "test_interpolation_and_galerkin_product", dict(positive=False)),
+    ("coarsest solve: LU without row exchanges", "or_amg.c",
+     "if (fabs(a[(size_t)i * n + k]) > mx) {", "if (0) {",
+     "test_oracle_solver", "test_coarsest_only_hierarchy_is_a_dense_solve", dict(permuted=True)),
     ("V-cycle: coarse-grid correction subtracted", "or_amg.c",
      "for (int i = 0; i < n; i++) x[i] += t[i];", "for (int i = 0; i < n; i++) x[i] -= t[i];",
      "test_oracle_solver", "test_vcycle_convergence_on_poisson", {}),

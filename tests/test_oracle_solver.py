@@ -449,8 +449,15 @@ def test_vcycle_convergence_on_poisson(oracle_lib):
     assert rho < 0.7, rho         # measured 0.60 (PMIS + direct interpolation, one l1-Jacobi sweep)
 
 
-def test_coarsest_only_hierarchy_is_a_dense_solve(oracle_lib):
+@pytest.mark.parametrize("permuted", [False, True])
+def test_coarsest_only_hierarchy_is_a_dense_solve(oracle_lib, permuted):
+    """The coarsest level is solved exactly (LU with partial pivoting); the
+    row-permuted matrix has zeros on its diagonal, so the factorisation must
+    exchange rows."""
     A = _random_mmatrix(40, 9)
+    if permuted:
+        A = A[np.roll(np.arange(40), 7)]
+        assert (np.diag(A) == 0).sum() > 20
     rp, ci, v = _csr(A)
     h = oracle_lib.AMG(rp, ci, v, coarse_max=128)
     assert h.nlev == 1
