@@ -94,6 +94,12 @@ MUTATIONS = [
     ("GMRES: Hessenberg transposed in the back substitution", "or_solve.c",
      "s -= H[(size_t)k * m + l] * yy[l];", "s -= H[(size_t)l * m + k] * yy[l];",
      "test_oracle_solver", "test_fgmres_iterations_equal_minimal_residual_gmres", dict(tile=(3, 2), coarse=128)),
+    ("FGMRES restart: new basis from b instead of the residual", "or_solve.c",
+     "for (int i = 0; i < nu; i++) V[i] = r[i] / beta;", "for (int i = 0; i < nu; i++) V[i] = ls->b[i] / beta;",
+     "test_oracle_solver", "test_restarted_fgmres_matches_dense_solve", {}),
+    ("FGMRES restart: the cycle's correction replaces the iterate", "or_solve.c",
+     "s += yy[k] * Z[(size_t)k * nu + i]; y[i] += s; }", "s += yy[k] * Z[(size_t)k * nu + i]; y[i] = s; }",
+     "test_oracle_solver", "test_restarted_fgmres_matches_dense_solve", {}),
     # AMG (Algorithm 2, pressure stage)
     ("strength: comparison reversed", "or_amg.c",
      "-A->v[q] >= thr", "-A->v[q] <= thr",

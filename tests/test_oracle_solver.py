@@ -148,6 +148,23 @@ def test_fgmres_cpr_matches_dense_solve(oracle_lib, tile, coarse):
     assert np.linalg.norm(y - ystar) <= 1e-11 * cond * np.linalg.norm(ystar)
 
 
+def test_restarted_fgmres_matches_dense_solve(oracle_lib):
+    """FGMRES(m) with a short restart (m = 3): each cycle starts from the
+    true residual of the current iterate and adds its correction, so the
+    restarted solver still reaches the tolerance and the dense solution."""
+    c = I.small_case(6, 5, 3, seed=12)
+    s = _system(oracle_lib, c, 60, tile_x=2, tile_y=2, amg_coarse_max=8, restart=3, max_lin=600)
+    rp, ci, val, b, key = s.system()
+    nb = c.n + 2
+    ystar = np.linalg.solve(_dense_J(rp, ci, val, nb), b)
+    rc, y, its, rel = s.linear_solve(1e-10)
+    assert rc == 0 and its > 3, (rc, its)                  # converged, after restarts
+    _, _, val2, b2, _ = s.ls.get()
+    J2 = _dense_J(rp, ci, val2, nb)
+    assert np.linalg.norm(b2 - J2 @ y) <= 1.0001e-10 * np.linalg.norm(b2)
+    np.testing.assert_allclose(y, ystar, rtol=1e-6, atol=1e-9 * np.abs(ystar).max())
+
+
 @pytest.mark.parametrize("tile,coarse", [((2, 2), 8), ((3, 2), 128)])
 def test_fgmres_iterations_equal_minimal_residual_gmres(oracle_lib, tile, coarse):
     """With a fixed preconditioner M (the CPR of Algorithm 2 is linear once
