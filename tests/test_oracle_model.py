@@ -4,6 +4,7 @@ closed forms, invariants and finite differences (no GPU needed).
 Passages: eqs. (3)-(18) (model and discretisation), eq. (10) (wells),
 Algorithm 1 (Newton), eq. (26) (forcing term) of arXiv 1701.06254.
 """
+import copy
 import math
 
 import numpy as np
@@ -190,6 +191,39 @@ def test_jacobian_matches_finite_differences(oracle_lib, seed, crossflow):
     rowscale = np.abs(J).max(axis=1, keepdims=True)
     err = np.abs(Jfd - J) / rowscale
     assert err.max() < 1e-6, err.max()
+
+
+def _cell_residuals(oracle_lib, case, p, sw, pb):
+    s = oracle_lib.Sim(case)
+    s.set_state(p, sw, pb); s.store_old(); s.set_dt(1.0)
+    s.set_state(p, sw, pb); s.assemble()
+    return -s.system()[3][:2 * case.n].reshape(case.n, 2)     # rows: (oil, water) per cell
+
+
+def test_well_flow_directions(oracle_lib):
+    """Eq. (10) with the flow directions of reading R7: a producer whose
+    wellbore pressure is above its cells' takes nothing from them and puts
+    nothing in; an injector whose wellbore pressure is below its cells'
+    (crossflow) draws from them with each phase's own mobility, so a cell at
+    connate water saturation gives up oil but no water."""
+    c = I.small_case(4, 3, 3, seed=31)
+    bare = copy.deepcopy(c)
+    bare.wells = []
+    rng = np.random.default_rng(32)
+    p = 200.0 + rng.uniform(0.0, 5.0, c.n)
+    inj, prod = c.wells
+    sw = np.full(c.n, 0.5)
+    R = _cell_residuals(oracle_lib, c, p, sw, np.array([p.max() + 50.0, p.max() + 50.0]))
+    R0 = _cell_residuals(oracle_lib, bare, p, sw, np.zeros(0))
+    cells = np.array(prod.perf_cells)
+    np.testing.assert_array_equal(R[cells], R0[cells])           # the producer does nothing
+    assert np.all(R[np.array(inj.perf_cells), 1] != R0[np.array(inj.perf_cells), 1])   # the injector does inject
+    sw = np.full(c.n, c.fluid.swc)
+    R = _cell_residuals(oracle_lib, c, p, sw, np.array([p.min() - 50.0, p.min() - 50.0]))
+    R0 = _cell_residuals(oracle_lib, bare, p, sw, np.zeros(0))
+    cells = np.array(inj.perf_cells)
+    np.testing.assert_array_equal(R[cells, 1], R0[cells, 1])     # no water leaves at connate saturation
+    assert np.all(R[cells, 0] != R0[cells, 0])                   # oil does
 
 
 def test_hydrostatic_initial_state_is_at_rest(oracle_lib):

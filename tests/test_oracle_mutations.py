@@ -57,6 +57,12 @@ MUTATIONS = [
     ("geometry: cell depth at the top face instead of the centre", "or_model.c",
      "S->z[c] = g->top + ((double)k + 0.5) * g->dz;", "S->z[c] = g->top + ((double)k) * g->dz;",
      "test_oracle_model", "test_hydrostatic_initial_state_is_at_rest", {}),
+    ("well: a producer also injects", "or_model.c",
+     "if (dd <= 0.0) {            /* at dd = 0", "if (1) {            /* at dd = 0",
+     "test_oracle_model", "test_well_flow_directions", {}),
+    ("well: injector crossflow with the total mobility", "or_model.c",
+     "} else if (dd < 0.0) {        /* injector crossflow", "} else if (0) {        /* injector crossflow",
+     "test_oracle_model", "test_well_flow_directions", {}),
     ("old accumulation: oil stored with the water density", "or_model.c",
      "S->acc0[2 * c + 0] = P.phi * P.rho[1] * (1.0 - S->s[c]);",
      "S->acc0[2 * c + 0] = P.phi * P.rho[0] * (1.0 - S->s[c]);",
