@@ -110,6 +110,9 @@ MUTATIONS = [
     ("strength: comparison reversed", "or_amg.c",
      "-A->v[q] >= thr", "-A->v[q] <= thr",
      "test_oracle_solver", "test_strength_hand_example", {}),
+    ("strength: threshold from the largest magnitude", "or_amg.c",
+     "      double v = -A->v[q];\n", "      double v = fabs(A->v[q]);\n",
+     "test_oracle_solver", "test_strength_hand_example", {}),
     ("strength: a zero entry counts as strong", "or_amg.c",
      "have && mx > 0.0 && ", "have && ",
      "test_oracle_solver", "test_strength_hand_example", {}),

@@ -358,6 +358,12 @@ def test_strength_hand_example(oracle_lib):
     st = h.level(0)["strong"]
     assert not st[rp[4]:rp[5]].any()
     np.testing.assert_array_equal(st[rp[3]:rp[4]], [True, False, False])
+    # the threshold follows the most negative entry, not the largest in
+    # magnitude: next to a +2 entry, -0.3 is still strong (0.3 >= 0.25 * 1)
+    M[2] = [-1.0, 0.0, 4.0, -0.3, 2.0]
+    rp, ci, v = _csr(M)
+    h = oracle_lib.AMG(rp, ci, v, theta=0.25, coarse_max=1, max_levels=2)
+    np.testing.assert_array_equal(h.level(0)["strong"][rp[2]:rp[3]], [True, False, True, False])
 
 
 @pytest.mark.parametrize("seed", range(6))
