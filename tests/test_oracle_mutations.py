@@ -78,6 +78,9 @@ MUTATIONS = [
      "if (r == 0) { S->t += dt; rem -= dt;", "if (r == 0) { S->t += S->o.dt; rem -= dt;",
      "test_oracle_model", "test_time_step_cuts_cover_the_interval", {}),
     # processing, eqs. (29)-(32)
+    ("reordering key: water instead of oil potential", "or_model.c",
+     "for (int c = 0; c < n; c++) ls->key[c] = P[c].pot[1];", "for (int c = 0; c < n; c++) ls->key[c] = P[c].pot[0];",
+     "test_oracle_solver", "test_reordering_key_is_the_oil_potential", {}),
     ("ABF: inverse of the diagonal block transposed", "or_solve.c",
      "double i00 = d / det, i01 = -b / det, i10 = -c / det, i11 = a / det;",
      "double i00 = d / det, i01 = -c / det, i10 = -b / det, i11 = a / det;",

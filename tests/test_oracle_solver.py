@@ -202,6 +202,22 @@ def test_fgmres_iterations_equal_minimal_residual_gmres(oracle_lib, tile, coarse
     assert its_ref is not None and abs(its - its_ref) <= 1, (its, its_ref)
 
 
+def test_reordering_key_is_the_oil_potential(oracle_lib):
+    """The key of the local reordering is each cell's oil-phase potential,
+    eq. (5) with eq. (6): p - rho_o(p) g z at the cell centre (depth z,
+    positive downwards; bar)."""
+    c = I.small_case(4, 3, 5, seed=33)
+    s = _system(oracle_lib, c, 90)
+    key = s.system()[4]
+    p = s.get_state()[0]
+    f = c.fluid
+    z = c.top + (np.arange(c.n) // (c.nx * c.ny) + 0.5) * c.dz
+    rho_o = f.rho_ref[1] * (1.0 + f.c_f[1] * (p - f.p_ref))
+    np.testing.assert_allclose(key, p - rho_o * f.g * z * 1e-5, rtol=1e-13)
+    rho_w = f.rho_ref[0] * (1.0 + f.c_f[0] * (p - f.p_ref))
+    assert np.abs(key - (p - rho_w * f.g * z * 1e-5)).max() > 1.0    # the phases differ by bars here
+
+
 def test_subdomains_partition_and_overlap(oracle_lib):
     """Owned sets partition the unknowns; the extended set of each
     subdomain is its owned rows plus their graph neighbours (overlap 1);
