@@ -107,6 +107,24 @@ def test_peaceman_isotropic_square(oracle_lib):
     np.testing.assert_allclose(wi, expect, rtol=1e-13)
 
 
+def test_peaceman_anisotropic_invariances(oracle_lib):
+    """Peaceman's anisotropic well index does not depend on how the grid is
+    turned: exchanging kx with ky together with dx with dy leaves it
+    unchanged; and for kx = ky it reduces to the isotropic formula with
+    0.14 sqrt(dx^2 + dy^2) on a rectangular cell."""
+    def wi(kx, ky, dx, dy):
+        c = I.small_case(3, 3, 2, seed=1)
+        c.kx[:] = kx; c.ky[:] = ky; c.kz[:] = 0.1 * min(kx, ky)
+        c.dx, c.dy = dx, dy
+        return oracle_lib.Sim(c).well_index()
+    np.testing.assert_allclose(wi(100.0, 900.0, 10.0, 25.0), wi(900.0, 100.0, 25.0, 10.0), rtol=1e-13)
+    assert not np.allclose(wi(100.0, 900.0, 10.0, 25.0), wi(900.0, 100.0, 10.0, 25.0), rtol=1e-3)
+    k, dx, dy = 70.0, 10.0, 25.0
+    ro = 0.14 * math.sqrt(dx * dx + dy * dy)
+    c = I.small_case(3, 3, 2, seed=1)
+    np.testing.assert_allclose(wi(k, k, dx, dy), 2 * math.pi * CDARCY * k * c.dz / math.log(ro / 0.1), rtol=1e-13)
+
+
 def _closed_form_accumulation(case, p, sw):
     """phi rho_a s_a from eqs. (4), (6), (8) (oil, water), per cell."""
     f = case.fluid

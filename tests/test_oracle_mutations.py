@@ -44,6 +44,9 @@ MUTATIONS = [
     ("well index: Peaceman radius constant halved", "or_model.c",
      "double ro = 0.28 *", "double ro = 0.14 *",
      "test_oracle_model", "test_peaceman_isotropic_square", {}),
+    ("well index: permeability ratio inverted in one term", "or_model.c",
+     "double ro = 0.28 * sqrt(sqrt(b / a) * g->dx * g->dx", "double ro = 0.28 * sqrt(sqrt(a / b) * g->dx * g->dx",
+     "test_oracle_model", "test_peaceman_anisotropic_invariances", {}),
     ("well: drawdown with the wrong sign, eq. (10)", "or_model.c",
      "double dd = (S->pb[w] - S->p[c]) + P[c].rho[a] * dz5;",
      "double dd = (S->p[c] - S->pb[w]) + P[c].rho[a] * dz5;",
