@@ -75,22 +75,29 @@ def test_pressure_dependent_viscosity(oracle_lib):
     assert np.ptp(mu) > 0.005                                     # the viscosity does vary
 
 
-def test_series_flow_through_heterogeneous_cells(oracle_lib):
+@pytest.mark.parametrize("axis", ["x", "y", "z"])
+def test_series_flow_through_heterogeneous_cells(oracle_lib, axis):
     """Steady incompressible single-phase water through cells of different
-    permeability in series: the same rate q crosses every face, and the
-    pressure drop between neighbouring cell centres is the sum of the two
-    half-cell resistances, q mu_w (dx / (2 k_i) + dx / (2 k_i+1)) / (C_D A)
-    (Darcy's law, eq. (1), on each half cell)."""
-    q, mu_w, dx, A, n = 10.0, 0.5, 10.0, 100.0, 30
-    c = line_case(n, dx, 100.0, q, 100.0, 0.8)
-    k = np.exp(np.random.default_rng(8).normal(math.log(100.0), 1.0, n))
-    c.kx, c.ky, c.kz = k, k.copy(), k.copy()
-    c.dy = c.dz = 10.0
+    permeability in series, along each grid axis: the same rate q crosses
+    every face, and the pressure drop between neighbouring cell centres is
+    the sum of the two half-cell resistances, q mu_w (L / (2 k_i) +
+    L / (2 k_i+1)) / (C_D A), with k the permeability along the axis (the
+    other two components differ, and must not enter); Darcy's law, eq. (1),
+    on each half cell."""
+    q, mu_w, L, A, n = 10.0, 0.5, 10.0, 100.0, 30
+    rng = np.random.default_rng(8)
+    k = np.exp(rng.normal(math.log(100.0), 1.0, n))
+    other = np.exp(rng.normal(math.log(100.0), 1.0, n))
+    dims = {"x": (n, 1, 1), "y": (1, n, 1), "z": (1, 1, n)}[axis]
+    perm = {a: (k if a == axis else other.copy()) for a in "xyz"}
+    c = I.Case(f"line_{axis}", *dims, L, L, L, 1000.0, perm["x"], perm["y"], perm["z"], np.full(n, 0.2),
+               incompressible_fluid(), [], dt=1.0, n_steps=1, p_init=110.0, sw_init=0.8)
+    c.wells = [I.Well(I.INJ, I.WRATE, q, [0]), I.Well(I.PROD, I.BHP, 100.0, [n - 1])]
     s = oracle_lib.Sim(c, newton_tol=1e-13, lin_tol=1e-13, max_lin=200)
     s.init_hydrostatic()
     assert s.advance(1) == 0
     p = s.get_state()[0]
-    drop = q * mu_w * (dx / (2.0 * k[:-1]) + dx / (2.0 * k[1:])) / (CDARCY * A)
+    drop = q * mu_w * (L / (2.0 * k[:-1]) + L / (2.0 * k[1:])) / (CDARCY * A)
     np.testing.assert_allclose(-np.diff(p), drop, rtol=1e-9)
 
 

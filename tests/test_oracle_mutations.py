@@ -40,7 +40,14 @@ MUTATIONS = [
     ("transmissibility: arithmetic instead of harmonic mean", "or_model.c",
      "S->ft[nf++] = OR_CDARCY * (g->dy * g->dz) / (g->dx / (2.0 * kx[c]) + g->dx / (2.0 * kx[d]));",
      "S->ft[nf++] = OR_CDARCY * (g->dy * g->dz) * (kx[c] + kx[d]) / (2.0 * g->dx);",
-     "test_oracle_model", "test_series_flow_through_heterogeneous_cells", {}),
+     "test_oracle_model", "test_series_flow_through_heterogeneous_cells", dict(axis="x")),
+    ("transmissibility: y faces with the x permeability", "or_model.c",
+     "(g->dy / (2.0 * ky[c]) + g->dy / (2.0 * ky[d]))", "(g->dy / (2.0 * kx[c]) + g->dy / (2.0 * kx[d]))",
+     "test_oracle_model", "test_series_flow_through_heterogeneous_cells", dict(axis="y")),
+    ("transmissibility: z faces with the arithmetic mean", "or_model.c",
+     "OR_CDARCY * (g->dx * g->dy) / (g->dz / (2.0 * kz[c]) + g->dz / (2.0 * kz[d]))",
+     "OR_CDARCY * (g->dx * g->dy) * (kz[c] + kz[d]) / (2.0 * g->dz)",
+     "test_oracle_model", "test_series_flow_through_heterogeneous_cells", dict(axis="z")),
     ("well index: Peaceman radius constant halved", "or_model.c",
      "double ro = 0.28 *", "double ro = 0.14 *",
      "test_oracle_model", "test_peaceman_isotropic_square", {}),
