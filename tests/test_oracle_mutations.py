@@ -77,6 +77,10 @@ MUTATIONS = [
      "S->acc0[2 * c + 0] = P.phi * P.rho[1] * (1.0 - S->s[c]);",
      "S->acc0[2 * c + 0] = P.phi * P.rho[0] * (1.0 - S->s[c]);",
      "test_oracle_model", "test_mass_balance_identity", dict(seed=3)),
+    ("inexact Newton: the fixed tolerance instead of the forcing term", "or_model.c",
+     "double eta = (S->o.newton == OR_INEXACT) ? or_forcing(l, bn, rprev, bprev) : S->o.lin_tol;",
+     "double eta = S->o.lin_tol;",
+     "test_oracle_model", "test_inexact_newton_solves_loosely", {}),
     ("forcing term: divided by the new residual norm, eq. (26)", "or_model.c",
      "double eta = (bn - rprev) / bprev;", "double eta = (bn - rprev) / bn;",
      "test_oracle_model", "test_forcing_term_choice_two", {}),
