@@ -457,3 +457,72 @@ def test_buckley_leverett_converges_under_refinement(oracle_lib):
         x, sw, ex = _bl_run(oracle_lib, nx, nx, 150.0)
         errs.append(np.abs(sw - ex).mean())
     assert errs[0] > errs[1] > errs[2], errs
+
+
+# ---------------------------------------------------------------------------
+# The Newton convergence measure (Algorithm 1 tests ||b|| >= epsilon before
+# each solve; reading R13 fixes the norm): the largest |R| dt / (rho_ref V
+# phi) over the cells' two equations -- the change in saturation that the
+# residual mass stands for -- and the largest dimensionless well residual.
+
+def _one_cell_case(dx=30.0, dy=40.0, dz=7.0, phi=0.23, k=50.0, fluid=None, wells=()):
+    kk = np.full(1, k)
+    c = I.Case("one_cell", 1, 1, 1, dx, dy, dz, 1000.0, kk, kk.copy(), kk.copy(), np.full(1, phi),
+               fluid or incompressible_fluid(), list(wells), dt=1.0, n_steps=1, p_init=200.0, sw_init=0.3)
+    return c
+
+
+@pytest.mark.parametrize("c_w,c_o,expect", [(0.0, 0.0, 0.05), (1e-3, 0.0, 0.05 * 1.1), (0.0, 2e-3, 0.05 * 1.2)])
+def test_newton_measure_closed_cell(oracle_lib, c_w, c_o, expect):
+    """One closed cell without wells, rigid rock: s_w moves from 0.30 to
+    0.35 over a step of 2.5 days.  Each equation's residual is then only
+    its accumulation term, V/dt phi rho_a (s_a^{n+1} - s_a^n) (eq. 17), so
+    the measure is |Delta s_w| rho_a / rho_a,ref = 0.05 for an
+    incompressible phase and 0.05 (1 + c_a (p - p_ref)) for a compressible
+    one at p = p_ref + 100 bar (eq. 6): the larger of the two rows."""
+    fl = incompressible_fluid()
+    fl.c_f = (c_w, c_o)
+    fl.rho_ref = (1000.0, 800.0)
+    c = _one_cell_case(fluid=fl)
+    s = oracle_lib.Sim(c)
+    p = np.array([fl.p_ref + 100.0])
+    s.set_state(p, np.array([0.30]), np.zeros(0)); s.store_old()
+    s.set_state(p, np.array([0.35]), np.zeros(0)); s.set_dt(2.5)
+    s.assemble()
+    assert s.residual_norm() == pytest.approx(expect, rel=1e-12)
+
+
+def test_newton_measure_bhp_well_row(oracle_lib):
+    """A BHP producer whose wellbore pressure (210 bar) is above its cell's
+    (200 bar) takes nothing from it (reading R7), and the state equals the
+    old time level, so the cell rows vanish and the measure is the well row
+    of eq. (11) scaled by its target: |p_b - target| / target = 60/150."""
+    c = _one_cell_case(wells=[I.Well(I.PROD, I.BHP, 150.0, [0])])
+    s = oracle_lib.Sim(c)
+    p, sw = np.array([200.0]), np.array([0.3])
+    s.set_state(p, sw, np.array([210.0])); s.store_old(); s.set_dt(1.0)
+    s.assemble()
+    assert s.residual_norm() == pytest.approx(0.4, rel=1e-12)
+
+
+def test_newton_measure_water_rate_row(oracle_lib):
+    """A water-rate injector (eq. 12) 1 bar above its cell at connate
+    saturation (k_rw = 0, k_ro = 1): water enters with the total mobility
+    1/mu_o (reading R7), q_w = WI rho_w (p_b - p) / mu_o with Peaceman's
+    index for a square isotropic cell, 2 pi C_D k dz / ln(0.14 sqrt(2) dx /
+    r_w).  The cell is large, so its own scaled residual is negligible, and
+    the measure is the well row |q_w - rho_w q| / (rho_w q)."""
+    k, dx, dz, q = 1.0, 1000.0, 100.0, 0.1
+    c = _one_cell_case(dx=dx, dy=dx, dz=dz, k=k, wells=[I.Well(I.INJ, I.WRATE, q, [0])])
+    s = oracle_lib.Sim(c)
+    fl = c.fluid
+    p, sw = np.array([200.0]), np.array([fl.swc])
+    s.set_state(p, sw, np.array([201.0])); s.store_old(); s.set_dt(1.0)
+    s.assemble()
+    wi = 2 * math.pi * CDARCY * k * dz / math.log(0.14 * math.sqrt(2.0) * dx / 0.1)
+    qw = wi * fl.rho_ref[0] * 1.0 / fl.mu_ref[1]
+    expect = abs(qw - fl.rho_ref[0] * q) / (fl.rho_ref[0] * q)
+    assert expect > 1.0                                 # the well row dominates ...
+    cell = qw * 1.0 / (fl.rho_ref[0] * dx * dx * dz * 0.23)
+    assert cell < 1e-6                                  # ... the cell row does not
+    assert s.residual_norm() == pytest.approx(expect, rel=1e-12)

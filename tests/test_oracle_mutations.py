@@ -91,6 +91,23 @@ MUTATIONS = [
     ("time loop: a cut step advances the clock by the full step", "or_model.c",
      "if (r == 0) { S->t += dt; rem -= dt;", "if (r == 0) { S->t += S->o.dt; rem -= dt;",
      "test_oracle_model", "test_time_step_cuts_cover_the_interval", {}),
+    ("Newton measure: not scaled by the step length", "or_model.c",
+     "fabs(S->ls.b[2 * c + e]) * S->dt / (S->f.rho_ref[1 - e]", "fabs(S->ls.b[2 * c + e]) / (S->f.rho_ref[1 - e]",
+     "test_oracle_model", "test_newton_measure_closed_cell", dict(c_w=0.0, c_o=0.0, expect=0.05)),
+    ("Newton measure: each row scaled by the other phase's density", "or_model.c",
+     "S->dt / (S->f.rho_ref[1 - e] * S->vol[c]", "S->dt / (S->f.rho_ref[e] * S->vol[c]",
+     "test_oracle_model", "test_newton_measure_closed_cell", dict(c_w=0.0, c_o=0.0, expect=0.05)),
+    ("Newton measure: well rows left out", "or_model.c",
+     "    double rr = fabs(S->ls.b[2 * (S->n + w)]);\n    if (!(rr <= mx)) mx = rr;",
+     "    double rr = 0.0 * fabs(S->ls.b[2 * (S->n + w)]);\n    if (!(rr <= mx)) mx = rr;",
+     "test_oracle_model", "test_newton_measure_bhp_well_row", {}),
+    ("BHP well row: not scaled by its target, eq. (11)", "or_model.c",
+     "R[2 * wr] = (S->pb[w] - S->wtarget[w]) / S->wtarget[w];", "R[2 * wr] = (S->pb[w] - S->wtarget[w]);",
+     "test_oracle_model", "test_newton_measure_bhp_well_row", {}),
+    ("water-rate row: target in reservoir instead of mass units, eq. (12)", "or_model.c",
+     "double scale = (S->wctrl[w] == OR_WRATE) ? 1.0 / (S->f.rho_ref[0] * S->wtarget[w]) : 0.0;",
+     "double scale = (S->wctrl[w] == OR_WRATE) ? 1.0 / (S->wtarget[w]) : 0.0;",
+     "test_oracle_model", "test_newton_measure_water_rate_row", {}),
     # processing, eqs. (29)-(32)
     ("reordering key: water instead of oil potential", "or_model.c",
      "for (int c = 0; c < n; c++) ls->key[c] = P[c].pot[1];", "for (int c = 0; c < n; c++) ls->key[c] = P[c].pot[0];",
