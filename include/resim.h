@@ -234,14 +234,17 @@ sim_status sim_ls_residual_norm(sim_ls_t ls, const double *x, double *norm);
  * Nothing is allocated: the per-block partial sums use a fixed device array
  * inside the library (4096 doubles, 32 KB, held by every GPU that loads the
  * library until the process exits).  Limit: n + n_wells <= 4096 * 4096
- * block rows; larger systems get SIM_ERR_ARG.  x (2 per block row) and
- * norm (one double) must be device memory (SIM_ERR_ARG otherwise); the
+ * block rows; larger systems get SIM_ERR_ARG.  The handle, x (2 per block
+ * row) and norm (one double) must all be on the current device, and x and
+ * norm must be device memory (SIM_ERR_ARG otherwise, before any launch); the
  * result is written to *norm on the handle's stream and the call does not
- * synchronise.  The first call on a device looks up the array's device
- * address (once per device, with that device current).  All calls share the
- * array: calls whose work overlaps on the GPU (another stream, another
- * thread, another handle) race on it and must be ordered by the caller.
- * Each call overwrites every partial it reads, so no clearing is needed. */
+ * synchronise.  The first call on a handle looks up the array's device
+ * address (with the handle's device current) and keeps it in the handle;
+ * make that first call before capturing the stream into a CUDA graph.  All
+ * calls share the array: calls whose work overlaps on the GPU (another
+ * stream, another thread, another handle) race on it and must be ordered by
+ * the caller.  Each call overwrites every partial it reads, so no clearing
+ * is needed. */
 sim_status sim_ls_residual_norm_noalloc(sim_ls_t ls, const double *x_dev, double *norm_dev);
 
 /* Copy internal arrays to host memory for inspection.  what / index:

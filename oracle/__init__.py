@@ -58,14 +58,15 @@ class Fluid(C.Structure):
     _fields_ = [("rho_ref", C.c_double * 2), ("c_f", C.c_double * 2), ("mu_ref", C.c_double * 2),
                 ("c_mu", C.c_double * 2), ("p_ref", C.c_double), ("c_r", C.c_double),
                 ("swc", C.c_double), ("sor", C.c_double), ("nw", C.c_double), ("no", C.c_double),
-                ("krw_max", C.c_double), ("kro_max", C.c_double), ("g", C.c_double)]
+                ("krw_max", C.c_double), ("kro_max", C.c_double), ("g", C.c_double),
+                ("pc_n", C.c_int), ("pc_sw", C.POINTER(C.c_double)), ("pc_val", C.POINTER(C.c_double))]
 
 
 class Well(C.Structure):
     _fields_ = [("kind", C.c_int), ("control", C.c_int), ("target", C.c_double),
                 ("r_w", C.c_double), ("skin", C.c_double), ("z_ref", C.c_double),
                 ("n_perf", C.c_int), ("perf_cell", C.POINTER(C.c_int)),
-                ("wi", C.POINTER(C.c_double))]
+                ("wi", C.POINTER(C.c_double)), ("bhp_limit", C.c_double)]
 
 
 class Opts(C.Structure):
@@ -110,6 +111,8 @@ def _sig(lib):
         "or_sim_well_rates": (None, [P, _dp, _dp]),
         "or_sim_mass": (None, [P, _dp, _dp]),
         "or_sim_get_wi": (None, [P, _dp]),
+        "or_sim_set_well": (None, [P, C.c_int, C.c_int, C.c_double, C.c_double]),
+        "or_sim_well_controls": (None, [P, _ip, _dp]),
         "or_ls_create": (P, [C.c_int, C.c_int, C.c_int, C.c_int, _ip, _ip, _ip, C.POINTER(Opts)]),
         "or_ls_destroy": (None, [P]),
         "or_ls_set": (None, [P, _dp, _dp, _dp]),
@@ -328,14 +331,19 @@ class LinearSystem:
 def _case_structs(case):
     g = Grid(case.nx, case.ny, case.nz, case.dx, case.dy, case.dz, case.top)
     f = case.fluid
-    fl = Fluid((C.c_double * 2)(*f.rho_ref), (C.c_double * 2)(*f.c_f), (C.c_double * 2)(*f.mu_ref),
-               (C.c_double * 2)(*f.c_mu), f.p_ref, f.c_r, f.swc, f.sor, f.nw, f.no, f.krw_max, f.kro_max, f.g)
     keep = []
+    pcs = np.ascontiguousarray(getattr(f, "pc_sw", ()) or [0.0], np.float64)
+    pcv = np.ascontiguousarray(getattr(f, "pc", ()) or [0.0], np.float64)
+    keep += [pcs, pcv]
+    fl = Fluid((C.c_double * 2)(*f.rho_ref), (C.c_double * 2)(*f.c_f), (C.c_double * 2)(*f.mu_ref),
+               (C.c_double * 2)(*f.c_mu), f.p_ref, f.c_r, f.swc, f.sor, f.nw, f.no, f.krw_max, f.kro_max, f.g,
+               len(getattr(f, "pc", ()) or ()), _d(pcs), _d(pcv))
     wells = (Well * max(len(case.wells), 1))()
     for k, w in enumerate(case.wells):
         pc = np.ascontiguousarray(w.perf_cells, np.int32)
         keep.append(pc)
-        wells[k] = Well(w.kind, w.control, w.target, w.r_w, w.skin, case.well_z_ref(w), len(pc), _i(pc), None)
+        wells[k] = Well(w.kind, w.control, w.target, w.r_w, w.skin, case.well_z_ref(w), len(pc), _i(pc), None,
+                        getattr(w, "bhp_limit", 0.0) or 0.0)
     return g, fl, wells, keep
 
 
@@ -405,10 +413,22 @@ class Sim:
         return rc, y, its.value, rel.value
 
     def stats(self):
-        out = np.zeros(8)
+        out = np.zeros(9)
         self._lib.or_sim_stats(self.h, _d(out))
         return dict(steps=int(out[0]), newton=int(out[1]), lin=int(out[2]), cuts=int(out[3]),
-                    relres=out[4], its=int(out[5]), norm=out[6], t=out[7])
+                    relres=out[4], its=int(out[5]), norm=out[6], t=out[7], switches=int(out[8]))
+
+    def set_well(self, w, control, target, bhp_limit=0.0):
+        """A schedule change: well w's control, target and BHP limit from now on."""
+        if not 0 <= w < self.nw:
+            raise IndexError(f"well {w} of {self.nw}")
+        self._lib.or_sim_set_well(self.h, w, control, target, bhp_limit)
+
+    def well_controls(self):
+        """Current control and target of every well (after limit switching)."""
+        c = np.zeros(max(self.nw, 1), np.int32); tg = np.zeros(max(self.nw, 1))
+        self._lib.or_sim_well_controls(self.h, _i(c), _d(tg))
+        return c[:self.nw], tg[:self.nw]
 
     def well_rates(self):
         qw = np.zeros(max(self.nw, 1)); qo = np.zeros(max(self.nw, 1))

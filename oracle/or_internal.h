@@ -18,7 +18,7 @@
 #define OR_PA2BAR 1e-5
 
 enum { OR_INJ = 0, OR_PROD = 1 };
-enum { OR_BHP = 0, OR_WRATE = 1, OR_ORATE = 2, OR_LRATE = 3 };
+enum { OR_BHP = 0, OR_WRATE = 1, OR_ORATE = 2, OR_LRATE = 3, OR_SHUT = 4 };
 enum { OR_DEC_NONE = 0, OR_DEC_ABF = 1, OR_DEC_QI = 2 };
 enum { OR_STANDARD = 0, OR_INEXACT = 1 };
 
@@ -30,6 +30,8 @@ typedef struct {
 typedef struct {          /* index 0 = water, 1 = oil */
   double rho_ref[2], c_f[2], mu_ref[2], c_mu[2];
   double p_ref, c_r, swc, sor, nw, no, krw_max, kro_max, g;
+  int pc_n;                        /* capillary pressure table (eq. 9): points, 0 = p_c = 0 */
+  const double *pc_sw, *pc_val;    /* s_w ascending, p_c in bar */
 } or_fluid;
 
 typedef struct {
@@ -38,6 +40,7 @@ typedef struct {
   int n_perf;
   const int *perf_cell;
   const double *wi;       /* NULL -> Peaceman well index */
+  double bhp_limit;       /* rate wells: injector maximum / producer minimum p_b, 0 = none */
 } or_well;
 
 typedef struct {
@@ -105,6 +108,9 @@ typedef struct {
   double *kx, *ky, *kz, *phi, *z, *vol;
   or_fluid f;
   int nw; int *wkind, *wctrl; double *wtarget, *wzref;
+  int *wctrl0; double *wtarget0, *wlimit;  /* requested control and target, BHP limit */
+  int *wswitched;                          /* 1: on BHP at its limit instead of its rate */
+  double *pc_sw, *pc_val;                  /* copy of the capillary pressure table */
   int *pptr, *pcell; double *pwi;        /* perforations, CSR by well */
   int nf; int *fc, *fd; double *ft;      /* interior faces c < d, geometric transmissibility */
   or_opts o;
@@ -114,7 +120,7 @@ typedef struct {
   double t, dt;
   double *y;                             /* last Newton update (2 per block row) */
   /* statistics */
-  long n_newton, n_lin, n_steps, n_cuts;
+  long n_newton, n_lin, n_steps, n_cuts, n_switch;
   double last_relres; int last_its;
   double last_norm;
 } or_sim;

@@ -29,12 +29,30 @@ static void *xc(size_t n, size_t sz) { void *p = calloc(n ? n : 1, sz); if (!p) 
 /* ------------------------------------------------------------------ */
 typedef struct {
   double phi, dphi;                 /* porosity and d/dp              */
-  double rho[2], drho[2];           /* density (water, oil)           */
-  double mu[2], dmu[2];             /* viscosity                      */
+  double pc, dpc;                   /* capillary pressure and d/ds_w  */
+  double rho[2], drho[2], drhos[2]; /* density (water, oil), d/dp, d/ds_w */
+  double mu[2], dmu[2], dmus[2];    /* viscosity, d/dp, d/ds_w        */
   double kr[2], dkr[2];             /* rel. perm. and d/ds_w          */
   double m[2], dmp[2], dms[2];      /* mobility rho*kr/mu, d/dp, d/ds */
-  double pot[2], dpot[2];           /* potential eq. (5), d/dp        */
+  double pot[2], dpot[2], dpots[2]; /* potential eq. (5), d/dp, d/ds  */
 } props_t;
+
+/* Capillary pressure p_c(s_w) of eq. (9), "user input": the table's points
+   joined by straight lines, constant beyond its first and last points.  The
+   segment is the last k with sw[k] <= s; its slope is the derivative (0
+   outside the table). */
+static void capillary(const or_fluid *f, double s, double *pc, double *dpc)
+{
+  int n = f->pc_n;
+  if (n <= 0) { *pc = 0.0; *dpc = 0.0; return; }
+  if (n == 1 || s < f->pc_sw[0]) { *pc = f->pc_val[0]; *dpc = 0.0; return; }
+  if (s >= f->pc_sw[n - 1]) { *pc = f->pc_val[n - 1]; *dpc = 0.0; return; }
+  int k = 0;
+  while (s >= f->pc_sw[k + 1]) k++;
+  double slope = (f->pc_val[k + 1] - f->pc_val[k]) / (f->pc_sw[k + 1] - f->pc_sw[k]);
+  *pc = f->pc_val[k] + (s - f->pc_sw[k]) * slope;
+  *dpc = slope;
+}
 
 static void cell_props(const or_sim *S, int c, double p, double sw, props_t *P)
 {
@@ -42,6 +60,7 @@ static void cell_props(const or_sim *S, int c, double p, double sw, props_t *P)
   double dp = p - f->p_ref;
   P->phi = S->phi[c] * (1.0 + f->c_r * dp);                     /* eq. (4) */
   P->dphi = S->phi[c] * f->c_r;
+  capillary(f, sw, &P->pc, &P->dpc);
   double span = 1.0 - f->swc - f->sor;
   double sh = (sw - f->swc) / span, dsh = 1.0 / span;
   if (sh < 0.0) { sh = 0.0; dsh = 0.0; } else if (sh > 1.0) { sh = 1.0; dsh = 0.0; }
@@ -51,17 +70,24 @@ static void cell_props(const or_sim *S, int c, double p, double sw, props_t *P)
   P->dkr[1] = -f->kro_max * f->no * pow(1.0 - sh, f->no - 1.0) * dsh;
   double gz5 = f->g * S->z[c] * OR_PA2BAR;                      /* rho g z in bar per kg/m3 */
   for (int a = 0; a < 2; a++) {
-    P->rho[a] = f->rho_ref[a] * (1.0 + f->c_f[a] * (p - f->p_ref));   /* eq. (6) */
+    /* phase pressure, eq. (9): p_w = p_o - p_c(s_w), p_o = p */
+    double pa = a == 0 ? p - P->pc : p;
+    double dpa_s = a == 0 ? -P->dpc : 0.0;
+    P->rho[a] = f->rho_ref[a] * (1.0 + f->c_f[a] * (pa - f->p_ref));   /* eq. (6) */
     P->drho[a] = f->rho_ref[a] * f->c_f[a];
-    P->mu[a] = f->mu_ref[a] + f->c_mu[a] * dp;                   /* eq. (7) */
+    P->drhos[a] = P->drho[a] * dpa_s;
+    P->mu[a] = f->mu_ref[a] + f->c_mu[a] * (pa - f->p_ref);           /* eq. (7) */
     P->dmu[a] = f->c_mu[a];
+    P->dmus[a] = f->c_mu[a] * dpa_s;
     P->m[a] = P->rho[a] * P->kr[a] / P->mu[a];
     P->dmp[a] = P->drho[a] * P->kr[a] / P->mu[a] - P->rho[a] * P->kr[a] * P->dmu[a] / (P->mu[a] * P->mu[a]);
-    P->dms[a] = P->rho[a] * P->dkr[a] / P->mu[a];
+    P->dms[a] = P->rho[a] * P->dkr[a] / P->mu[a] + P->drhos[a] * P->kr[a] / P->mu[a]
+                - P->rho[a] * P->kr[a] * P->dmus[a] / (P->mu[a] * P->mu[a]);
     /* eq. (5) with z = depth (positive downwards): the potential falls
        with depth, so a hydrostatic column has a constant potential. */
-    P->pot[a] = p - P->rho[a] * gz5;
+    P->pot[a] = pa - P->rho[a] * gz5;
     P->dpot[a] = 1.0 - P->drho[a] * gz5;
+    P->dpots[a] = dpa_s - P->drhos[a] * gz5;
   }
 }
 
@@ -83,6 +109,11 @@ or_sim *or_sim_create(const or_grid *g, const double *kx, const double *ky, cons
 {
   or_sim *S = xc(1, sizeof(or_sim));
   S->g = *g; S->f = *f; S->o = *o;
+  if (f->pc_n > 0) {                       /* own copy of the capillary pressure table */
+    S->pc_sw = xc(f->pc_n, 8); S->pc_val = xc(f->pc_n, 8);
+    memcpy(S->pc_sw, f->pc_sw, 8 * (size_t)f->pc_n); memcpy(S->pc_val, f->pc_val, 8 * (size_t)f->pc_n);
+    S->f.pc_sw = S->pc_sw; S->f.pc_val = S->pc_val;
+  }
   int nx = g->nx, ny = g->ny, nz = g->nz, n = nx * ny * nz;
   S->n = n;
   S->kx = xc(n, 8); S->ky = xc(n, 8); S->kz = xc(n, 8); S->phi = xc(n, 8);
@@ -125,12 +156,14 @@ or_sim *or_sim_create(const or_grid *g, const double *kx, const double *ky, cons
   /* wells and perforations; Peaceman's well index when none is given */
   S->nw = nw;
   S->wkind = xc(nw, 4); S->wctrl = xc(nw, 4); S->wtarget = xc(nw, 8); S->wzref = xc(nw, 8);
+  S->wctrl0 = xc(nw, 4); S->wtarget0 = xc(nw, 8); S->wlimit = xc(nw, 8); S->wswitched = xc(nw, 4);
   S->pptr = xc(nw + 1, 4);
   for (int w = 0; w < nw; w++) S->pptr[w + 1] = S->pptr[w] + wells[w].n_perf;
   S->pcell = xc(S->pptr[nw], 4); S->pwi = xc(S->pptr[nw], 8);
   for (int w = 0; w < nw; w++) {
     S->wkind[w] = wells[w].kind; S->wctrl[w] = wells[w].control;
     S->wtarget[w] = wells[w].target; S->wzref[w] = wells[w].z_ref;
+    S->wctrl0[w] = wells[w].control; S->wtarget0[w] = wells[w].target; S->wlimit[w] = wells[w].bhp_limit;
     for (int q = 0; q < wells[w].n_perf; q++) {
       int c = wells[w].perf_cell[q];
       S->pcell[S->pptr[w] + q] = c;
@@ -196,10 +229,21 @@ void or_sim_destroy(or_sim *S)
   free(S->kx); free(S->ky); free(S->kz); free(S->phi); free(S->z); free(S->vol);
   free(S->fc); free(S->fd); free(S->ft);
   free(S->wkind); free(S->wctrl); free(S->wtarget); free(S->wzref);
+  free(S->wctrl0); free(S->wtarget0); free(S->wlimit); free(S->wswitched); free(S->pc_sw); free(S->pc_val);
   free(S->pptr); free(S->pcell); free(S->pwi);
   or_lsys_free(&S->ls);
   free(S->p); free(S->s); free(S->pb); free(S->acc0); free(S->y);
   free(S);
+}
+
+/* Wellbore pressure from which a rate-controlled (or shut) well starts:
+   10 bar above the oil pressure of its first perforated cell for an
+   injector, 10 bar below for a producer, so that it flows from the first
+   Newton iteration. */
+static double rate_start_pb(const or_sim *S, int w)
+{
+  double p0 = S->p[S->pcell[S->pptr[w]]];
+  return S->wkind[w] == OR_PROD ? p0 - 10.0 : p0 + 10.0;
 }
 
 /* Initial equilibrium: every cell gets the oil potential of the datum
@@ -220,8 +264,10 @@ void or_sim_init_hydrostatic(or_sim *S, double p_datum, double sw0)
     S->p[c] = r / a;
     S->s[c] = sw0;
   }
-  for (int w = 0; w < S->nw; w++)
-    S->pb[w] = (S->wctrl[w] == OR_BHP) ? S->wtarget[w] : S->p[S->pcell[S->pptr[w]]] + 10.0;
+  for (int w = 0; w < S->nw; w++) {
+    S->wctrl[w] = S->wctrl0[w]; S->wtarget[w] = S->wtarget0[w]; S->wswitched[w] = 0;
+    S->pb[w] = (S->wctrl[w] == OR_BHP) ? S->wtarget[w] : rate_start_pb(S, w);
+  }
   S->t = 0.0;
 }
 
@@ -250,6 +296,66 @@ void or_sim_store_old(or_sim *S)
   }
 }
 
+/* Mass rates of one perforation (eq. 10) for both phases (0 = water,
+   1 = oil; + = into the cell) and their derivatives with respect to the
+   cell's p and s_w and to p_b.  The drawdown of phase a is
+   dd = p_b - p_a + rho_a g (z - z_ref) (z = depth), p_a the phase pressure
+   of eq. (9).  Producer: each phase with its own mobility, outflow only
+   (q = 0 when dd > 0).  Injector, dd >= 0: water only, with the total cell
+   mobility (kr_w/mu_w + kr_o/mu_o), so water can enter a cell at connate
+   saturation.  Injector, dd < 0 (crossflow into the wellbore): upstream
+   from the cell as for the faces (eq. 18), each phase with its own
+   mobility.  A shut well has no flow. */
+static void perf_flow(const or_sim *S, int w, int c, double wi, const props_t *P,
+                      double q[2], double dqp[2], double dqs[2], double dqb[2])
+{
+  double dz5 = S->f.g * (S->z[c] - S->wzref[w]) * OR_PA2BAR;
+  for (int a = 0; a < 2; a++) {
+    q[a] = dqp[a] = dqs[a] = dqb[a] = 0.0;
+    if (S->wctrl[w] == OR_SHUT) continue;
+    double pa = a == 0 ? S->p[c] - P->pc : S->p[c];
+    double dd = (S->pb[w] - pa) + P->rho[a] * dz5;
+    double dd_dp = -1.0 + P->drho[a] * dz5;
+    double dd_ds = (a == 0 ? P->dpc : 0.0) + P->drhos[a] * dz5;
+    if (S->wkind[w] == OR_PROD) {
+      if (dd <= 0.0) {            /* at dd = 0: q = 0 with the flowing-side derivative */
+        q[a] = wi * P->m[a] * dd;
+        dqp[a] = wi * (P->dmp[a] * dd + P->m[a] * dd_dp);
+        dqs[a] = wi * (P->dms[a] * dd + P->m[a] * dd_ds);
+        dqb[a] = wi * P->m[a];
+      }
+    } else if (dd < 0.0) {        /* injector crossflow: as a producer perforation */
+      q[a] = wi * P->m[a] * dd;
+      dqp[a] = wi * (P->dmp[a] * dd + P->m[a] * dd_dp);
+      dqs[a] = wi * (P->dms[a] * dd + P->m[a] * dd_ds);
+      dqb[a] = wi * P->m[a];
+    } else if (a == 0) {          /* at dd = 0: q = 0 with the injecting-side derivative */
+      double lt = P->kr[0] / P->mu[0] + P->kr[1] / P->mu[1];
+      double lt_p = -P->kr[0] * P->dmu[0] / (P->mu[0] * P->mu[0])
+                    - P->kr[1] * P->dmu[1] / (P->mu[1] * P->mu[1]);
+      double lt_s = P->dkr[0] / P->mu[0] - P->kr[0] * P->dmus[0] / (P->mu[0] * P->mu[0])
+                    + P->dkr[1] / P->mu[1] - P->kr[1] * P->dmus[1] / (P->mu[1] * P->mu[1]);
+      q[a] = wi * P->rho[0] * lt * dd;
+      dqp[a] = wi * (P->drho[0] * lt * dd + P->rho[0] * lt_p * dd + P->rho[0] * lt * dd_dp);
+      dqs[a] = wi * (P->drhos[0] * lt * dd + P->rho[0] * lt_s * dd + P->rho[0] * lt * dd_ds);
+      dqb[a] = wi * P->rho[0] * lt;
+    }
+  }
+}
+
+/* Weights of the phase mass rates in a rate-controlled well's equation,
+   scaled by the target: eq. (12) water rate, eq. (13) oil rate, eq. (14)
+   liquid rate, each in surface volumes (mass / rho_ref) against the target
+   in sm3/day; production counts positive for a producer.  The equation is
+   sum_m (cw q_w,m + co q_o,m) - 1 = 0. */
+static void rate_weights(const or_sim *S, int w, double *cw, double *co)
+{
+  double sgn = S->wkind[w] == OR_PROD ? -1.0 : 1.0, T = S->wtarget[w];
+  *cw = *co = 0.0;
+  if (S->wctrl[w] == OR_WRATE || S->wctrl[w] == OR_LRATE) *cw = sgn / (S->f.rho_ref[0] * T);
+  if (S->wctrl[w] == OR_ORATE || S->wctrl[w] == OR_LRATE) *co = sgn / (S->f.rho_ref[1] * T);
+}
+
 /* ------------------------------------------------------------------ */
 /* Residual and Jacobian (eq. 17 with eq. 18 upstreaming and eq. 10    */
 /* wells).  Block row = (oil eq, water eq) of a cell; block column =   */
@@ -273,7 +379,7 @@ void or_sim_assemble(or_sim *S)
     J[0] += vt * (P[c].dphi * P[c].rho[1] + P[c].phi * P[c].drho[1]) * so;
     J[1] += vt * (-P[c].phi * P[c].rho[1]);
     J[2] += vt * (P[c].dphi * P[c].rho[0] + P[c].phi * P[c].drho[0]) * sw;
-    J[3] += vt * (P[c].phi * P[c].rho[0]);
+    J[3] += vt * (P[c].phi * P[c].rho[0] + P[c].phi * P[c].drhos[0] * sw);
   }
   /* face fluxes: flux into c from d is T m_u (Pot_d - Pot_c), with the
      upstream cell u = c if Pot_c >= Pot_d else d (per face, c < d); the
@@ -291,9 +397,9 @@ void or_sim_assemble(or_sim *S)
       double Tm = T * U->m[a];
       double F = Tm * dpot;
       double dFdpc = T * ((upc ? P[c].dmp[a] : 0.0) * dpot) - Tm * P[c].dpot[a];
-      double dFdsc = T * ((upc ? P[c].dms[a] : 0.0) * dpot);
+      double dFdsc = T * ((upc ? P[c].dms[a] : 0.0) * dpot) - Tm * P[c].dpots[a];
       double dFdpd = T * ((upc ? 0.0 : P[d].dmp[a]) * dpot) + Tm * P[d].dpot[a];
-      double dFdsd = T * ((upc ? 0.0 : P[d].dms[a]) * dpot);
+      double dFdsd = T * ((upc ? 0.0 : P[d].dms[a]) * dpot) + Tm * P[d].dpots[a];
       R[2 * c + e] -= F;
       R[2 * d + e] += F;
       Jcc[2 * e + 0] -= dFdpc; Jcc[2 * e + 1] -= dFdsc;
@@ -302,64 +408,40 @@ void or_sim_assemble(or_sim *S)
       Jdd[2 * e + 0] += dFdpd; Jdd[2 * e + 1] += dFdsd;
     }
   }
-  /* wells, eq. (10): per perforation q_a = WI rho_a kr_a/mu_a dPw with the
-     drawdown dPw = p_b - p + rho_a g (z - z_ref) (z = depth).
-     Producer: own phase mobility, outflow only (q = 0 when dPw > 0).
-     Injector, dPw >= 0: water only, with the total cell mobility (kr_w/mu_w
-     + kr_o/mu_o), so water can enter a cell at connate saturation.
-     Injector, dPw < 0 (crossflow into the wellbore): the flow is upstream
-     from the cell as for the faces (eq. 18), each phase with its own
-     mobility, so no phase leaves a cell where it is immobile. */
+  /* wells: perforation rates of eq. (10) in the cell equations; the well's
+     own row is its control: eq. (11) p_b = c scaled by c, or a rate
+     equation (12)-(14) scaled by the target mass rate; a shut well keeps
+     p_b (row 1 * p_b = current value). */
   for (int w = 0; w < S->nw; w++) {
     int wr = n + w;
     double *Jww = &ls->val[4 * (size_t)bpos(ls, wr, wr)];
-    double scale = (S->wctrl[w] == OR_WRATE) ? 1.0 / (S->f.rho_ref[0] * S->wtarget[w]) : 0.0;
+    double cw, co;
+    rate_weights(S, w, &cw, &co);
     for (int q = S->pptr[w]; q < S->pptr[w + 1]; q++) {
       int c = S->pcell[q];
-      double wi = S->pwi[q];
-      double dz5 = S->f.g * (S->z[c] - S->wzref[w]) * OR_PA2BAR;
       double *Jcc = &ls->val[4 * (size_t)bpos(ls, c, c)], *Jcw = &ls->val[4 * (size_t)bpos(ls, c, wr)];
       double *Jwc = &ls->val[4 * (size_t)bpos(ls, wr, c)];
+      double qa[2], dqp[2], dqs[2], dqb[2];
+      perf_flow(S, w, c, S->pwi[q], &P[c], qa, dqp, dqs, dqb);
       for (int a = 0; a < 2; a++) {
         int e = 1 - a;
-        double dd = (S->pb[w] - S->p[c]) + P[c].rho[a] * dz5;
-        double dd_dp = -1.0 + P[c].drho[a] * dz5;
-        double q_ = 0, dqdp = 0, dqds = 0, dqdb = 0;
-        if (S->wkind[w] == OR_PROD) {
-          if (dd <= 0.0) {            /* at dd = 0: q = 0 with the flowing-side derivative */
-            q_ = wi * P[c].m[a] * dd;
-            dqdp = wi * (P[c].dmp[a] * dd + P[c].m[a] * dd_dp);
-            dqds = wi * P[c].dms[a] * dd;
-            dqdb = wi * P[c].m[a];
-          }
-        } else if (dd < 0.0) {        /* injector crossflow: as a producer perforation */
-          q_ = wi * P[c].m[a] * dd;
-          dqdp = wi * (P[c].dmp[a] * dd + P[c].m[a] * dd_dp);
-          dqds = wi * P[c].dms[a] * dd;
-          dqdb = wi * P[c].m[a];
-        } else if (a == 0) {          /* at dd = 0: q = 0 with the injecting-side derivative */
-          double lt = P[c].kr[0] / P[c].mu[0] + P[c].kr[1] / P[c].mu[1];
-          double lt_p = -P[c].kr[0] * P[c].dmu[0] / (P[c].mu[0] * P[c].mu[0])
-                        - P[c].kr[1] * P[c].dmu[1] / (P[c].mu[1] * P[c].mu[1]);
-          double lt_s = P[c].dkr[0] / P[c].mu[0] + P[c].dkr[1] / P[c].mu[1];
-          q_ = wi * P[c].rho[0] * lt * dd;
-          dqdp = wi * (P[c].drho[0] * lt * dd + P[c].rho[0] * lt_p * dd + P[c].rho[0] * lt * dd_dp);
-          dqds = wi * P[c].rho[0] * lt_s * dd;
-          dqdb = wi * P[c].rho[0] * lt;
-        }
-        R[2 * c + e] -= q_;
-        Jcc[2 * e + 0] -= dqdp; Jcc[2 * e + 1] -= dqds;
-        Jcw[2 * e + 0] -= dqdb;
-        if (a == 0 && S->wctrl[w] == OR_WRATE) {   /* eq. (12), scaled by the target mass rate */
-          R[2 * wr] += scale * q_;
-          Jwc[0] += scale * dqdp; Jwc[1] += scale * dqds;
-          Jww[0] += scale * dqdb;
+        double cwt = a == 0 ? cw : co;
+        R[2 * c + e] -= qa[a];
+        Jcc[2 * e + 0] -= dqp[a]; Jcc[2 * e + 1] -= dqs[a];
+        Jcw[2 * e + 0] -= dqb[a];
+        if (cwt != 0.0) {
+          R[2 * wr] += cwt * qa[a];
+          Jwc[0] += cwt * dqp[a]; Jwc[1] += cwt * dqs[a];
+          Jww[0] += cwt * dqb[a];
         }
       }
     }
-    if (S->wctrl[w] == OR_WRATE) R[2 * wr] -= 1.0;
-    else { R[2 * wr] = (S->pb[w] - S->wtarget[w]) / S->wtarget[w];   /* eq. (11), scaled */
-           Jww[0] = 1.0 / S->wtarget[w]; }
+    if (S->wctrl[w] == OR_BHP) {
+      R[2 * wr] = (S->pb[w] - S->wtarget[w]) / S->wtarget[w];   /* eq. (11), scaled */
+      Jww[0] = 1.0 / S->wtarget[w];
+    } else if (S->wctrl[w] == OR_SHUT) {
+      R[2 * wr] = 0.0; Jww[0] = 1.0;
+    } else R[2 * wr] -= 1.0;
     Jww[3] = 1.0;                                                    /* padded dummy unknown */
   }
   for (int r = 0; r < 2 * ls->nb; r++) ls->b[r] = -R[r];
@@ -400,6 +482,57 @@ double or_forcing(int l, double bn, double rprev, double bprev)
   return eta;
 }
 
+/* Control switching with BHP limits (the paper's "various operation
+   constraints ... at different time stage"; reading R22).
+   Rate to BHP: after each Newton update, a rate-controlled well with a
+   limit whose wellbore pressure has passed it (injector above its maximum,
+   producer below its minimum) switches to BHP control at the limit, and
+   p_b is set to the limit.  Returns the number of wells switched. */
+static int limits_rate_to_bhp(or_sim *S)
+{
+  int k = 0;
+  for (int w = 0; w < S->nw; w++) {
+    int c = S->wctrl[w];
+    if (!(c == OR_WRATE || c == OR_ORATE || c == OR_LRATE) || !(S->wlimit[w] > 0.0)) continue;
+    int past = S->wkind[w] == OR_INJ ? S->pb[w] > S->wlimit[w] : S->pb[w] < S->wlimit[w];
+    if (!past) continue;
+    S->wctrl[w] = OR_BHP; S->wtarget[w] = S->wlimit[w]; S->pb[w] = S->wlimit[w];
+    S->wswitched[w] = 1; k++;
+  }
+  return k;
+}
+
+/* BHP back to rate: at the start of a time step, a well held at its limit
+   returns to its requested rate when, at the limit, it would deliver more
+   than that rate (the rate equation's residual is positive there). */
+static void limits_bhp_to_rate(or_sim *S)
+{
+  int any = 0;
+  for (int w = 0; w < S->nw; w++)
+    if (S->wswitched[w]) { S->wctrl[w] = S->wctrl0[w]; S->wtarget[w] = S->wtarget0[w]; any = 1; }
+  if (!any) return;
+  or_sim_assemble(S);
+  for (int w = 0; w < S->nw; w++) {
+    if (!S->wswitched[w]) continue;
+    double r = -S->ls.b[2 * (S->n + w)];
+    if (r > 0.0) S->wswitched[w] = 0;
+    else { S->wctrl[w] = OR_BHP; S->wtarget[w] = S->wlimit[w]; }
+  }
+}
+
+/* A new control for well w from now on (a schedule change between steps):
+   the control, its target (bar or sm3/day) and the BHP limit of a rate
+   control (0 = none).  A well put on a rate control starts from the
+   wellbore pressure rate_start_pb. */
+void or_sim_set_well(or_sim *S, int w, int control, double target, double limit)
+{
+  S->wctrl[w] = S->wctrl0[w] = control;
+  S->wtarget[w] = S->wtarget0[w] = target;
+  S->wlimit[w] = limit; S->wswitched[w] = 0;
+  if (control == OR_BHP) S->pb[w] = target;
+  else if (control != OR_SHUT) S->pb[w] = rate_start_pb(S, w);
+}
+
 static double nrm2(const double *v, int m) { double s = 0; for (int i = 0; i < m; i++) s += v[i] * v[i]; return sqrt(s); }
 
 /* One time step at S->dt by Algorithm 1.  Returns 0 on convergence, 1 when
@@ -437,6 +570,7 @@ int or_sim_newton(or_sim *S, int *iters)
     }
     for (int w = 0; w < S->nw; w++) S->pb[w] += S->y[2 * (S->n + w)];
     S->n_newton++;
+    S->n_switch += limits_rate_to_bhp(S);
     or_sim_assemble(S);
   }
 }
@@ -447,7 +581,8 @@ int or_sim_newton(or_sim *S, int *iters)
 int or_sim_advance(or_sim *S, int nsteps)
 {
   int n = S->n, nw = S->nw;
-  double *p0 = xc(n, 8), *s0 = xc(n, 8), *b0 = xc(nw ? nw : 1, 8);
+  double *p0 = xc(n, 8), *s0 = xc(n, 8), *b0 = xc(nw ? nw : 1, 8), *t0 = xc(nw ? nw : 1, 8);
+  int *c0 = xc(nw ? nw : 1, 4), *w0 = xc(nw ? nw : 1, 4);
   int rc = 0;
   for (int st = 0; st < nsteps && rc == 0; st++) {
     double rem = S->o.dt, h = S->o.dt;
@@ -458,17 +593,21 @@ int or_sim_advance(or_sim *S, int nsteps)
       if (nw) memcpy(b0, S->pb, 8 * (size_t)nw);
       or_sim_store_old(S);
       S->dt = dt;
+      limits_bhp_to_rate(S);
+      if (nw) { memcpy(c0, S->wctrl, 4 * (size_t)nw); memcpy(t0, S->wtarget, 8 * (size_t)nw);
+                memcpy(w0, S->wswitched, 4 * (size_t)nw); }
       int its;
       int r = or_sim_newton(S, &its);
       if (r == 0) { S->t += dt; rem -= dt; S->n_steps++; continue; }
       memcpy(S->p, p0, 8 * (size_t)n); memcpy(S->s, s0, 8 * (size_t)n);
-      if (nw) memcpy(S->pb, b0, 8 * (size_t)nw);
+      if (nw) { memcpy(S->pb, b0, 8 * (size_t)nw); memcpy(S->wctrl, c0, 4 * (size_t)nw);
+                memcpy(S->wtarget, t0, 8 * (size_t)nw); memcpy(S->wswitched, w0, 4 * (size_t)nw); }
       S->n_cuts++; cuts++;
       if (cuts > S->o.max_cuts) { rc = r; break; }
       h = 0.5 * h;
     }
   }
-  free(p0); free(s0); free(b0);
+  free(p0); free(s0); free(b0); free(t0); free(c0); free(w0);
   return rc;
 }
 
@@ -488,7 +627,11 @@ void or_sim_stats(const or_sim *S, double *out)
 {
   out[0] = (double)S->n_steps; out[1] = (double)S->n_newton; out[2] = (double)S->n_lin;
   out[3] = (double)S->n_cuts; out[4] = S->last_relres; out[5] = S->last_its; out[6] = S->last_norm;
-  out[7] = S->t;
+  out[7] = S->t; out[8] = (double)S->n_switch;
+}
+void or_sim_well_controls(const or_sim *S, int *ctrl, double *target)
+{
+  for (int w = 0; w < S->nw; w++) { ctrl[w] = S->wctrl[w]; target[w] = S->wtarget[w]; }
 }
 void or_sim_well_rates(const or_sim *S, double *qw, double *qo)
 {
@@ -498,14 +641,9 @@ void or_sim_well_rates(const or_sim *S, double *qw, double *qo)
     for (int q = S->pptr[w]; q < S->pptr[w + 1]; q++) {
       int c = S->pcell[q];
       props_t P; cell_props(S, c, S->p[c], S->s[c], &P);
-      double dz5 = S->f.g * (S->z[c] - S->wzref[w]) * OR_PA2BAR;
-      for (int a = 0; a < 2; a++) {
-        double dd = (S->pb[w] - S->p[c]) + P.rho[a] * dz5, q_ = 0;
-        if (S->wkind[w] == OR_PROD) { if (dd <= 0.0) q_ = S->pwi[q] * P.m[a] * dd; }
-        else if (dd < 0.0) q_ = S->pwi[q] * P.m[a] * dd;
-        else if (a == 0) q_ = S->pwi[q] * P.rho[0] * (P.kr[0] / P.mu[0] + P.kr[1] / P.mu[1]) * dd;
-        if (a == 0) qw[w] += q_; else qo[w] += q_;
-      }
+      double qa[2], d1[2], d2[2], d3[2];
+      perf_flow(S, w, c, S->pwi[q], &P, qa, d1, d2, d3);
+      qw[w] += qa[0]; qo[w] += qa[1];
     }
   }
 }

@@ -17,8 +17,9 @@ FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std
 
 
 def _deps():
-    files = [os.path.join(SRC, u) for u in UNITS] + [os.path.join(SRC, "common.cuh"),
-                                                     os.path.join(HERE, "..", "include", "resim.h")]
+    files = [os.path.join(SRC, u) for u in UNITS] + [os.path.join(SRC, f) for f in os.listdir(SRC)
+                                                     if f.endswith((".cuh", ".h"))] + \
+        [os.path.join(HERE, "..", "include", "resim.h")]
     return max(os.path.getmtime(f) for f in files)
 
 

@@ -223,6 +223,7 @@ struct sim_ls_s {
   void graph_timers();          // after a replay has completed
   int *errw = nullptr, *errw_dev = nullptr;   // device error word (host-mapped)
   bool have_setup = false;
+  double *noalloc_scratch = nullptr;   // device address of the allocation-free norm's array (noalloc.cu)
   // timing: events in pairs, the family of each pair in ev_fam
   unsigned timer_mask = 0;
   int ev_open = 0;               // timer brackets not yet closed

@@ -4,34 +4,30 @@
 // The array is one per device: every GPU that loads the library holds
 // NOALLOC_MAX_BLOCKS doubles (32 KB) until the process exits.  Host code
 // cannot take the array's address directly (in host code the symbol names a
-// host-side stand-in); the first call on each device looks the device
-// address up with cudaGetSymbolAddress and keeps it.
+// host-side stand-in); the first call on a handle looks the device address
+// up with cudaGetSymbolAddress, with the handle's device current, and keeps
+// it in the handle.  A device reset (cudaDeviceReset) invalidates every
+// handle on that device together with the address it kept; handles created
+// afterwards look the address up again.
 #include "common.cuh"
-#include <mutex>
-
-#define NOALLOC_ROWS_PER_BLOCK 4096        // block rows handled by one thread block
-#define NOALLOC_MAX_BLOCKS 4096            // scratch capacity: one partial per thread block
-#define NOALLOC_MAX_DEVICES 64
+#include "noalloc_limit.h"
 
 static __device__ __align__(256) double g_noalloc_partials[NOALLOC_MAX_BLOCKS];
 
-static std::mutex g_noalloc_lock;
-static double *g_noalloc_addr[NOALLOC_MAX_DEVICES];   // device address of the array, per device
-
-// device address of the scratch array on the current device, looked up on
-// the first call on that device (nullptr and an error text on failure)
-static double *noalloc_scratch(int dev) {
-  std::lock_guard<std::mutex> guard(g_noalloc_lock);
-  if (!g_noalloc_addr[dev]) {
+// device address of the scratch array for this handle's device (the
+// current one), looked up on the handle's first call; nullptr and an error
+// text on failure
+static double *noalloc_scratch(sim_ls_s *ls) {
+  if (!ls->noalloc_scratch) {
     double *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_partials);
     if (e != cudaSuccess || !p) {
       rs_set_error("sim_ls_residual_norm_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
       return nullptr;
     }
-    g_noalloc_addr[dev] = p;
+    ls->noalloc_scratch = p;
   }
-  return g_noalloc_addr[dev];
+  return ls->noalloc_scratch;
 }
 
 // partials[blk] = sum over the block's rows of |b_i - (A x)_i|^2; rows are
@@ -69,10 +65,11 @@ __global__ void k_partials_sqrt(int m, const double *partials, double *out) {
   if (threadIdx.x == 0) *out = sqrt(t);
 }
 
-static bool device_pointer(const void *p) {
+// the device that holds p (device or managed memory), or -1
+static int device_of(const void *p) {
   cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return -1; }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? a.device : -1;
 }
 
 // Error paths return directly (no exception objects): nothing on this
@@ -82,28 +79,36 @@ extern "C" sim_status sim_ls_residual_norm_noalloc(sim_ls_t ls, const double *x_
     rs_set_error("sim_ls_residual_norm_noalloc: NULL argument");
     return SIM_ERR_ARG;
   }
-  if (!device_pointer(x_dev) || !device_pointer(norm_dev)) {
-    rs_set_error("sim_ls_residual_norm_noalloc: x and norm must be device memory");
-    return SIM_ERR_ARG;
-  }
-  int nblocks = (ls->nb + NOALLOC_ROWS_PER_BLOCK - 1) / NOALLOC_ROWS_PER_BLOCK;
-  if (nblocks > NOALLOC_MAX_BLOCKS) {
+  long long nblocks = rs_noalloc_blocks(ls->nb);
+  if (nblocks < 0) {
     rs_set_error("sim_ls_residual_norm_noalloc: %d block rows exceed the limit of %d", ls->nb,
                  NOALLOC_MAX_BLOCKS * NOALLOC_ROWS_PER_BLOCK);
     return SIM_ERR_ARG;
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+  if (e != cudaSuccess || dev < 0) {
     rs_set_error("sim_ls_residual_norm_noalloc: no usable current device (%s)", cudaGetErrorString(e));
     return SIM_ERR_CUDA;
   }
-  double *scratch = noalloc_scratch(dev);
+  // the handle's matrix, x and norm must all live on the current device:
+  // a kernel launched here must not touch another GPU's memory
+  int dh = device_of(ls->rp.p), dx = device_of(x_dev), dn = device_of(norm_dev);
+  if (dx < 0 || dn < 0) {
+    rs_set_error("sim_ls_residual_norm_noalloc: x and norm must be device memory");
+    return SIM_ERR_ARG;
+  }
+  if (dh != dev || dx != dev || dn != dev) {
+    rs_set_error("sim_ls_residual_norm_noalloc: the handle (device %d), x (device %d) and norm (device %d) "
+                 "must be on the current device %d", dh, dx, dn, dev);
+    return SIM_ERR_ARG;
+  }
+  double *scratch = noalloc_scratch(ls);
   if (!scratch) return SIM_ERR_CUDA;
   // every partial the second kernel reads is written by the first one in the
   // same call, so nothing in the scratch array needs clearing between calls
-  k_resid_sq_partials<<<nblocks, 256, 0, ls->st>>>(ls->nb, ls->rp.p, ls->ci.p, ls->val.p, ls->b.p, x_dev, scratch);
-  k_partials_sqrt<<<1, 32, 0, ls->st>>>(nblocks, scratch, norm_dev);
+  k_resid_sq_partials<<<(unsigned)nblocks, 256, 0, ls->st>>>(ls->nb, ls->rp.p, ls->ci.p, ls->val.p, ls->b.p, x_dev, scratch);
+  k_partials_sqrt<<<1, 32, 0, ls->st>>>((int)nblocks, scratch, norm_dev);
   RS_LAUNCHED(2);
   e = cudaGetLastError();
   if (e != cudaSuccess) {

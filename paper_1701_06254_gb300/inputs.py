@@ -23,7 +23,7 @@ import numpy as np
 
 # well kinds / controls (Sec. "Two-phase oil-water flow model", eqs. 11-14)
 INJ, PROD = 0, 1
-BHP, WRATE, ORATE, LRATE = 0, 1, 2, 3
+BHP, WRATE, ORATE, LRATE, SHUT = 0, 1, 2, 3, 4
 
 
 @dataclass
@@ -42,6 +42,8 @@ class Fluid:
     krw_max: float = 1.0
     kro_max: float = 1.0
     g: float = 9.80665
+    pc_sw: tuple = ()          # capillary pressure table (eq. 9): s_w ascending ...
+    pc: tuple = ()             # ... and p_c in bar; empty = no capillary pressure
 
 
 @dataclass
@@ -53,6 +55,7 @@ class Well:
     r_w: float = 0.1
     skin: float = 0.0
     z_ref: float | None = None  # reference depth of p_b; None -> top perforation depth
+    bhp_limit: float = 0.0      # rate wells: injector maximum / producer minimum p_b (bar), 0 = none
 
 
 @dataclass

@@ -171,3 +171,21 @@ def test_grid_size_limit():
     c.nx, c.ny, c.nz = 400, 400, 320                    # 51.2M cells; the rock arrays are never read
     rc, msg = _create(R, c)
     assert rc == 1 and "too large" in msg, (rc, msg)
+
+
+def test_noalloc_size_rule_on_the_host(tmp_path):
+    """The allocation-free residual norm accepts 1 .. 4096 * 4096 block rows
+    (one partial sum per 4096 rows in a fixed array of 4096) and refuses
+    anything else before it touches the GPU.  The rule is a plain C header
+    of the library, compiled and run here without a GPU."""
+    import subprocess
+    hdr = os.path.join(ROOT, "paper_1701_06254_gb300", "csrc", "noalloc_limit.h")
+    src = tmp_path / "rule.c"
+    src.write_text('#include <stdio.h>\n#include "%s"\nint main(void) {\n'
+                   '  long long v[] = {0, 1, 4096, 4097, 16002, 4096LL * 4096, 4096LL * 4096 + 1, -5};\n'
+                   '  for (int i = 0; i < 8; i++) printf("%%lld\\n", rs_noalloc_blocks(v[i]));\n'
+                   '  return 0;\n}\n' % hdr)
+    exe = tmp_path / "rule"
+    subprocess.run(["gcc", "-O2", "-o", str(exe), str(src)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out == [-1, 1, 1, 2, 4, 4096, -1, -1]

@@ -35,7 +35,7 @@ MUTATIONS = [
      "int upc = P[c].pot[a] >= P[d].pot[a];", "int upc = P[c].pot[a] < P[d].pot[a];",
      "test_oracle_model", "test_buckley_leverett_front", {}),
     ("potential: gravity term with the wrong sign, eq. (5)", "or_model.c",
-     "P->pot[a] = p - P->rho[a] * gz5;", "P->pot[a] = p + P->rho[a] * gz5;",
+     "P->pot[a] = pa - P->rho[a] * gz5;", "P->pot[a] = pa + P->rho[a] * gz5;",
      "test_oracle_model", "test_hydrostatic_initial_state_is_at_rest", {}),
     ("transmissibility: arithmetic instead of harmonic mean", "or_model.c",
      "S->ft[nf++] = OR_CDARCY * (g->dy * g->dz) / (g->dx / (2.0 * kx[c]) + g->dx / (2.0 * kx[d]));",
@@ -55,11 +55,11 @@ MUTATIONS = [
      "double ro = 0.28 * sqrt(sqrt(b / a) * g->dx * g->dx", "double ro = 0.28 * sqrt(sqrt(a / b) * g->dx * g->dx",
      "test_oracle_model", "test_peaceman_anisotropic_invariances", {}),
     ("well: drawdown with the wrong sign, eq. (10)", "or_model.c",
-     "double dd = (S->pb[w] - S->p[c]) + P[c].rho[a] * dz5;",
-     "double dd = (S->p[c] - S->pb[w]) + P[c].rho[a] * dz5;",
+     "double dd = (S->pb[w] - pa) + P->rho[a] * dz5;",
+     "double dd = (pa - S->pb[w]) + P->rho[a] * dz5;",
      "test_oracle_model", "test_linear_pressure_profile", {}),
     ("viscosity: pressure term with the wrong sign, eq. (7)", "or_model.c",
-     "P->mu[a] = f->mu_ref[a] + f->c_mu[a] * dp;", "P->mu[a] = f->mu_ref[a] - f->c_mu[a] * dp;",
+     "P->mu[a] = f->mu_ref[a] + f->c_mu[a] * (pa - f->p_ref);", "P->mu[a] = f->mu_ref[a] - f->c_mu[a] * (pa - f->p_ref);",
      "test_oracle_model", "test_pressure_dependent_viscosity", {}),
     ("relative permeability: water exponent taken from oil", "or_model.c",
      "P->kr[0] = f->krw_max * pow(sh, f->nw);", "P->kr[0] = f->krw_max * pow(sh, f->no);",
@@ -105,9 +105,46 @@ MUTATIONS = [
      "R[2 * wr] = (S->pb[w] - S->wtarget[w]) / S->wtarget[w];", "R[2 * wr] = (S->pb[w] - S->wtarget[w]);",
      "test_oracle_model", "test_newton_measure_bhp_well_row", {}),
     ("water-rate row: target in reservoir instead of mass units, eq. (12)", "or_model.c",
-     "double scale = (S->wctrl[w] == OR_WRATE) ? 1.0 / (S->f.rho_ref[0] * S->wtarget[w]) : 0.0;",
-     "double scale = (S->wctrl[w] == OR_WRATE) ? 1.0 / (S->wtarget[w]) : 0.0;",
+     "*cw = sgn / (S->f.rho_ref[0] * T);", "*cw = sgn / T;",
      "test_oracle_model", "test_newton_measure_water_rate_row", {}),
+    # capillary pressure (eq. 9) and rate controls (eqs. 12-14, limits)
+    ("capillary pressure: p_w = p_o + p_c, eq. (9)", "or_model.c",
+     "double pa = a == 0 ? p - P->pc : p;", "double pa = a == 0 ? p + P->pc : p;",
+     "test_oracle_wells_capillary", "test_capillary_gravity_equilibrium_is_at_rest", {}),
+    ("capillary pressure: applied to the oil phase", "or_model.c",
+     "double pa = a == 0 ? p - P->pc : p;", "double pa = a == 1 ? p - P->pc : p;",
+     "test_oracle_wells_capillary", "test_capillary_gravity_equilibrium_is_at_rest", {}),
+    ("capillary pressure: table segment one too far", "or_model.c",
+     "  while (s >= f->pc_sw[k + 1]) k++;\n", "  while (s >= f->pc_sw[k + 1]) k++;\n  if (k + 2 < n) k++;\n",
+     "test_oracle_wells_capillary", "test_capillary_gravity_equilibrium_is_at_rest", {}),
+    ("capillary pressure: face derivative d(Pot_w)/ds_w dropped", "or_model.c",
+     "double dFdsc = T * ((upc ? P[c].dms[a] : 0.0) * dpot) - Tm * P[c].dpots[a];",
+     "double dFdsc = T * ((upc ? P[c].dms[a] : 0.0) * dpot);",
+     "test_oracle_wells_capillary", "test_jacobian_with_capillary_pressure_and_rate_controls", dict(seed=41)),
+    ("capillary pressure: water density at the oil pressure", "or_model.c",
+     "P->drhos[a] = P->drho[a] * dpa_s;", "P->drhos[a] = 0.0;",
+     "test_oracle_wells_capillary", "test_jacobian_with_capillary_pressure_and_rate_controls", dict(seed=42)),
+    ("oil rate: target taken in water surface volumes, eq. (13)", "or_model.c",
+     "*co = sgn / (S->f.rho_ref[1] * T);", "*co = sgn / (S->f.rho_ref[0] * T);",
+     "test_oracle_wells_capillary", "test_rate_producer_withdraws_its_target", dict(control=2, target=40.0)),
+    ("liquid rate: water left out, eq. (14)", "or_model.c",
+     "if (S->wctrl[w] == OR_WRATE || S->wctrl[w] == OR_LRATE) *cw", "if (S->wctrl[w] == OR_WRATE) *cw",
+     "test_oracle_wells_capillary", "test_rate_producer_withdraws_its_target", dict(control=3, target=60.0)),
+    ("rate producer: production counted negative", "or_model.c",
+     "double sgn = S->wkind[w] == OR_PROD ? -1.0 : 1.0", "double sgn = 1.0",
+     "test_oracle_wells_capillary", "test_rate_producer_withdraws_its_target", dict(control=2, target=40.0)),
+    ("BHP limit: never checked", "or_model.c",
+     "    S->n_switch += limits_rate_to_bhp(S);\n", "\n",
+     "test_oracle_wells_capillary", "test_injector_switches_to_its_bhp_limit_and_back", {}),
+    ("BHP limit: switched back whatever the rate", "or_model.c",
+     "if (r > 0.0) S->wswitched[w] = 0;", "if (1) S->wswitched[w] = 0;",
+     "test_oracle_wells_capillary", "test_held_well_stays_on_its_limit_when_the_rate_is_out_of_reach", {}),
+    ("BHP limit: never switched back", "or_model.c",
+     "if (r > 0.0) S->wswitched[w] = 0;", "if (0) S->wswitched[w] = 0;",
+     "test_oracle_wells_capillary", "test_held_producer_returns_to_its_rate_once_the_limit_delivers_it", {}),
+    ("shut well: perforations still flow", "or_model.c",
+     "    if (S->wctrl[w] == OR_SHUT) continue;\n", "\n",
+     "test_oracle_wells_capillary", "test_shut_well_carries_no_flow", {}),
     # processing, eqs. (29)-(32)
     ("reordering key: water instead of oil potential", "or_model.c",
      "for (int c = 0; c < n; c++) ls->key[c] = P[c].pot[1];", "for (int c = 0; c < n; c++) ls->key[c] = P[c].pot[0];",
