@@ -5,7 +5,8 @@
  * Yang and Chen, "A Parallel Simulator for Massive Reservoir Models
  * Utilizing Distributed-Memory Parallel Systems" (arXiv 1701.06254):
  *   model and discretisation      Sec. "Two-phase oil-water flow model",
- *                                 eqs. (3)-(18), wells eqs. (10)-(12)
+ *                                 eqs. (3)-(18), capillary pressure eq. (9),
+ *                                 wells eq. (10) with controls eqs. (11)-(14)
  *   Newton / inexact Newton       Algorithm 1, eqs. (24)-(27)
  *   decoupling                    eq. (29), ABF and Quasi-IMPES operators
  *   local potential reordering    eqs. (30)-(32)
@@ -57,7 +58,10 @@ typedef enum {
 } sim_status;
 
 enum { SIM_INJ = 0, SIM_PROD = 1 };                            /* well kind           */
-enum { SIM_BHP = 0, SIM_WRATE = 1, SIM_ORATE = 2, SIM_LRATE = 3 }; /* eqs. (11)-(14)   */
+/* well controls: BHP eq. (11), water rate eq. (12), oil rate eq. (13),
+ * liquid rate eq. (14), shut in (no flow; one of the schedule stages of the
+ * paper's Table 1) */
+enum { SIM_BHP = 0, SIM_WRATE = 1, SIM_ORATE = 2, SIM_LRATE = 3, SIM_SHUT = 4 };
 enum { SIM_DEC_NONE = 0, SIM_DEC_ABF = 1, SIM_DEC_QI = 2 };    /* eq. (29) operator   */
 enum { SIM_NEWTON_STANDARD = 0, SIM_NEWTON_INEXACT = 1 };      /* Algorithm 1         */
 /* preconditioner precision: FP64; FP32 (AMG, RAS factors, CPR vectors; FP64
@@ -71,22 +75,39 @@ typedef struct { const double *kx, *ky, *kz, *phi; } sim_rock;
 
 /* Fluid: index 0 = water, 1 = oil.  eqs. (4), (6), (7) and Corey relative
  * permeabilities kr_w = krw_max s^nw, kr_o = kro_max (1-s)^no with
- * s = (s_w - swc)/(1 - swc - sor) clipped to [0, 1]; g in m/s^2. */
+ * s = (s_w - swc)/(1 - swc - sor) clipped to [0, 1]; g in m/s^2.
+ * Capillary pressure (eq. 9, p_w = p_o - p_c(s_w)): pc_n points (0 = none,
+ * at most 16) of a table, pc_sw strictly increasing, pc_val in bar (host
+ * arrays, copied at creation), joined by straight lines and constant beyond
+ * the first and last points.  The water phase pressure sets the water
+ * density, viscosity, potential and perforation drawdown; porosity follows
+ * p_o. */
 typedef struct {
   double rho_ref[2], c_f[2], mu_ref[2], c_mu[2];
   double p_ref, c_r, swc, sor, nw, no, krw_max, kro_max, g;
+  int pc_n;
+  const double *pc_sw, *pc_val;
 } sim_fluid;
 
 /* A well (eq. 10): perforated cells (host array, n_perf entries), well
  * index per perforation (host, or NULL for Peaceman's formula with r_w and
- * skin), reference depth z_ref of p_b.  Supported controls: SIM_BHP for
- * any well, SIM_WRATE for injectors. */
+ * skin), reference depth z_ref of p_b.  Controls: SIM_BHP (target in bar)
+ * and SIM_WRATE for any well, SIM_ORATE and SIM_LRATE for producers
+ * (injectors inject water), SIM_SHUT for any well.  Rate targets are
+ * surface volumes in sm3/day (the phase mass rates of eq. 10 over each
+ * phase's reference density; a producer's production counts positive; the
+ * liquid rate is oil plus water).  bhp_limit (rate controls only; 0 = none)
+ * is an injector's maximum or a producer's minimum p_b: when a Newton update
+ * takes p_b past it the well goes on BHP control at the limit, and at the
+ * start of a later time step it returns to its rate when, at the limit, it
+ * would deliver more than the rate. */
 typedef struct {
   int kind, control;
   double target, r_w, skin, z_ref;
   int n_perf;
   const int *perf_cell;
   const double *wi;
+  double bhp_limit;
 } sim_well;
 
 typedef struct {
@@ -115,6 +136,7 @@ typedef struct {
   double ms_assemble, ms_setup, ms_solve;   /* CUDA-event time, cumulative */
   long long ws_used, ws_fallback;           /* warm starts with / without the network's term */
   double ws_r0;                             /* sum over warm-started solves of ||b - A x0|| / ||b|| */
+  long long switches;                       /* wells put on BHP control at their limit */
 } sim_stats;
 
 typedef struct sim_s *sim_t;
@@ -177,6 +199,20 @@ sim_status sim_newton_step(sim_t h, int *converged, sim_stats *st);
 sim_status sim_advance(sim_t h, int n_steps, sim_stats *st);
 
 sim_status sim_get_stats(sim_t h, sim_stats *st);
+
+/* A schedule change ("various operation constraints ... at different time
+ * stage"): from the next step on, well w has this control, target and BHP
+ * limit (as in sim_well).  A well put on BHP gets p_b = target; a well put
+ * on a rate starts 10 bar above (injector) or below (producer) the oil
+ * pressure of its first perforated cell; a shut well keeps p_b.
+ * Errors: SIM_ERR_ARG for a bad well index or a control the well's kind
+ * does not allow. */
+sim_status sim_set_well(sim_t h, int w, int control, double target, double bhp_limit);
+
+/* Current control and target of every well (n_wells entries each, host
+ * arrays; either may be NULL): after a switch to the BHP limit, SIM_BHP and
+ * the limit. */
+sim_status sim_get_well_controls(sim_t h, int *control, double *target);
 
 /* The simulator's linear system (borrowed handle, valid until sim_destroy). */
 sim_ls_t sim_linear_system(sim_t h);

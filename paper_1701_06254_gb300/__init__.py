@@ -50,13 +50,14 @@ class Fluid(C.Structure):
     _fields_ = [("rho_ref", C.c_double * 2), ("c_f", C.c_double * 2), ("mu_ref", C.c_double * 2),
                 ("c_mu", C.c_double * 2), ("p_ref", C.c_double), ("c_r", C.c_double), ("swc", C.c_double),
                 ("sor", C.c_double), ("nw", C.c_double), ("no", C.c_double), ("krw_max", C.c_double),
-                ("kro_max", C.c_double), ("g", C.c_double)]
+                ("kro_max", C.c_double), ("g", C.c_double), ("pc_n", C.c_int), ("pc_sw", C.c_void_p),
+                ("pc_val", C.c_void_p)]
 
 
 class Well(C.Structure):
     _fields_ = [("kind", C.c_int), ("control", C.c_int), ("target", C.c_double), ("r_w", C.c_double),
                 ("skin", C.c_double), ("z_ref", C.c_double), ("n_perf", C.c_int),
-                ("perf_cell", C.POINTER(C.c_int)), ("wi", C.POINTER(C.c_double))]
+                ("perf_cell", C.POINTER(C.c_int)), ("wi", C.POINTER(C.c_double)), ("bhp_limit", C.c_double)]
 
 
 class Options(C.Structure):
@@ -73,7 +74,8 @@ class Stats(C.Structure):
                 ("cuts", C.c_longlong), ("linear_solves", C.c_longlong), ("last_relres", C.c_double),
                 ("last_norm", C.c_double), ("t", C.c_double), ("last_its", C.c_int), ("last_newton", C.c_int),
                 ("ms_assemble", C.c_double), ("ms_setup", C.c_double), ("ms_solve", C.c_double),
-                ("ws_used", C.c_longlong), ("ws_fallback", C.c_longlong), ("ws_r0", C.c_double)]
+                ("ws_used", C.c_longlong), ("ws_fallback", C.c_longlong), ("ws_r0", C.c_double),
+                ("switches", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -109,6 +111,8 @@ def lib():
             "sim_newton_step": (I, [P, C.POINTER(I), C.POINTER(Stats)]),
             "sim_advance": (I, [P, I, C.POINTER(Stats)]),
             "sim_get_stats": (I, [P, C.POINTER(Stats)]),
+            "sim_set_well": (I, [P, I, I, D, D]),
+            "sim_get_well_controls": (I, [P, P, P]),
             "sim_linear_system": (P, [P]),
             "sim_ls_create": (I, [C.POINTER(P), I, I, I, I, P, P, P, C.POINTER(Options)]),
             "sim_ls_destroy": (None, [P]),
@@ -336,15 +340,19 @@ class LinearSystem:
 def _case_structs(case):
     g = Grid(case.nx, case.ny, case.nz, case.dx, case.dy, case.dz, case.top)
     f = case.fluid
-    fl = Fluid((C.c_double * 2)(*f.rho_ref), (C.c_double * 2)(*f.c_f), (C.c_double * 2)(*f.mu_ref),
-               (C.c_double * 2)(*f.c_mu), f.p_ref, f.c_r, f.swc, f.sor, f.nw, f.no, f.krw_max, f.kro_max, f.g)
     keep = []
+    pcs = np.ascontiguousarray(getattr(f, "pc_sw", ()) or [0.0], np.float64)
+    pcv = np.ascontiguousarray(getattr(f, "pc", ()) or [0.0], np.float64)
+    keep += [pcs, pcv]
+    fl = Fluid((C.c_double * 2)(*f.rho_ref), (C.c_double * 2)(*f.c_f), (C.c_double * 2)(*f.mu_ref),
+               (C.c_double * 2)(*f.c_mu), f.p_ref, f.c_r, f.swc, f.sor, f.nw, f.no, f.krw_max, f.kro_max, f.g,
+               len(getattr(f, "pc", ()) or ()), _ptr(pcs), _ptr(pcv))
     wells = (Well * max(len(case.wells), 1))()
     for k, w in enumerate(case.wells):
         pc = np.ascontiguousarray(w.perf_cells, np.int32)
         keep.append(pc)
         wells[k] = Well(w.kind, w.control, w.target, w.r_w, w.skin, case.well_z_ref(w), len(pc),
-                        pc.ctypes.data_as(C.POINTER(C.c_int)), None)
+                        pc.ctypes.data_as(C.POINTER(C.c_int)), None, getattr(w, "bhp_limit", 0.0) or 0.0)
     return g, fl, wells, keep
 
 
@@ -420,6 +428,18 @@ class Sim:
         st = Stats()
         _check(self._L.sim_get_stats(self.h, C.byref(st)))
         return st.as_dict()
+
+    def set_well(self, w, control, target, bhp_limit=0.0):
+        """A schedule change: well w's control, target and BHP limit from now on."""
+        if not 0 <= w < self.nw:
+            raise IndexError(f"well {w} of {self.nw}")
+        _check(self._L.sim_set_well(self.h, w, control, target, bhp_limit))
+
+    def well_controls(self):
+        """Current control and target of every well (after limit switching)."""
+        c = np.zeros(max(self.nw, 1), np.int32); tg = np.zeros(max(self.nw, 1))
+        _check(self._L.sim_get_well_controls(self.h, _ptr(c), _ptr(tg)))
+        return c[:self.nw], tg[:self.nw]
 
     def attach_warm_start(self, ws):
         """Use a WarmStart network for the initial guess of every solve (None detaches)."""

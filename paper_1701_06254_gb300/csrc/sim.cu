@@ -8,7 +8,10 @@
 // Euler eq. (15), two-point fluxes with the geometric transmissibility times
 // the upstream mobility (eqs. 16-18; upstream cell of face (c, d), c < d:
 // c if Phi_c >= Phi_d, else d), residual eq. (17).  Newton: Algorithm 1,
-// forcing term eq. (26) second choice, clamped to [0.01, 0.1].
+// forcing term eq. (26) second choice, clamped to [0.01, 0.1].  Also the
+// oil-rate (13) and liquid-rate (14) constraints, BHP limits with control
+// switching, schedule changes and shut wells, and a capillary pressure
+// table (eq. 9: p_w = p_o - p_c(s_w)).
 #include "common.cuh"
 #include <algorithm>
 #include <cmath>
@@ -16,9 +19,12 @@
 #include <memory>
 #include <new>
 
+#define PC_MAX 16                      // points of the capillary pressure table
 struct fluid_c {
   double rho_ref[2], c_f[2], mu_ref[2], c_mu[2];
   double p_ref, c_r, swc, sor, nw, no, krw_max, kro_max, g;
+  int pc_n;                            // 0: no capillary pressure
+  double pc_sw[PC_MAX], pc_val[PC_MAX];
 };
 
 struct sim_s {
@@ -29,6 +35,10 @@ struct sim_s {
   cudaStream_t st;
   std::vector<int> wkind, wctrl, pptr;
   std::vector<double> wtarget, wzref;
+  // requested control and target, BHP limit, held at the limit (switching)
+  std::vector<int> wctrl0, wswitched;
+  std::vector<double> wtarget0, wlimit;
+  bool any_limit = false;
   dbuf<double> kx, ky, kz, phi, tx, ty, tz;
   dbuf<int> pcell, pwell, ppos_cw, ppos_wc, cpp, cpi, wpptr, wdiag, wkind_d, wctrl_d;
   dbuf<double> pwi, wtarget_d, wzref_d;
@@ -48,7 +58,10 @@ struct sim_s {
 };
 
 // ----------------------------------------------------------- properties --
-struct cprops { double phi, dphi, rho[2], drho[2], mu[2], dmu[2], kr[2], dkr[2], m[2], dmp[2], dms[2], pot[2], dpot[2]; };
+struct cprops {
+  double phi, dphi, pc, dpc, rho[2], drho[2], drhos[2], mu[2], dmu[2], dmus[2], kr[2], dkr[2], m[2], dmp[2], dms[2],
+      pot[2], dpot[2], dpots[2];
+};
 
 __device__ __forceinline__ double corey(double x, double e) {
   if (e == 2.0) return x * x;
@@ -65,10 +78,26 @@ __device__ __forceinline__ double corey(double x, double e) {
 __device__ __forceinline__ double rho_of(const fluid_c &f, int a, double p) {
   return mul_rn(f.rho_ref[a], add_rn(1.0, mul_rn(f.c_f[a], sub_rn(p, f.p_ref))));
 }
+// capillary pressure of eq. (9) from the table: straight lines between its
+// points, constant beyond its ends; the segment is the last k with
+// sw[k] <= s, its slope the derivative (0 outside)
+__device__ __forceinline__ void capillary(const fluid_c &f, double s, double &pc, double &dpc) {
+  int n = f.pc_n;
+  if (n <= 0) { pc = 0.0; dpc = 0.0; return; }
+  if (n == 1 || s < f.pc_sw[0]) { pc = f.pc_val[0]; dpc = 0.0; return; }
+  if (s >= f.pc_sw[n - 1]) { pc = f.pc_val[n - 1]; dpc = 0.0; return; }
+  int k = 0;
+  while (s >= f.pc_sw[k + 1]) k++;
+  double slope = div_rn(sub_rn(f.pc_val[k + 1], f.pc_val[k]), sub_rn(f.pc_sw[k + 1], f.pc_sw[k]));
+  pc = add_rn(f.pc_val[k], mul_rn(sub_rn(s, f.pc_sw[k]), slope));
+  dpc = slope;
+}
+
 __device__ __forceinline__ void cell_props(const fluid_c &f, double phir, double z, double p, double sw, cprops &P) {
   double dp = p - f.p_ref;
   P.phi = phir * (1.0 + f.c_r * dp);
   P.dphi = phir * f.c_r;
+  capillary(f, sw, P.pc, P.dpc);
   double span = sub_rn(sub_rn(1.0, f.swc), f.sor);
   double sh = div_rn(sub_rn(sw, f.swc), span), dsh = 1.0 / span;
   if (sh < 0.0) { sh = 0.0; dsh = 0.0; } else if (sh > 1.0) { sh = 1.0; dsh = 0.0; }
@@ -79,22 +108,27 @@ __device__ __forceinline__ void cell_props(const fluid_c &f, double phir, double
   double gz5 = mul_rn(mul_rn(f.g, z), RS_PA2BAR);
 #pragma unroll
   for (int a = 0; a < 2; a++) {
-    P.rho[a] = rho_of(f, a, p);
+    // phase pressure, eq. (9): p_w = p_o - p_c(s_w)
+    double pa = a == 0 ? sub_rn(p, P.pc) : p, dpa_s = a == 0 ? -P.dpc : 0.0;
+    P.rho[a] = rho_of(f, a, pa);
     P.drho[a] = f.rho_ref[a] * f.c_f[a];
-    P.mu[a] = f.mu_ref[a] + f.c_mu[a] * dp;
+    P.drhos[a] = P.drho[a] * dpa_s;
+    P.mu[a] = f.mu_ref[a] + f.c_mu[a] * (pa - f.p_ref);
     P.dmu[a] = f.c_mu[a];
+    P.dmus[a] = f.c_mu[a] * dpa_s;
     double imu = 1.0 / P.mu[a];
     P.m[a] = P.rho[a] * P.kr[a] * imu;
     P.dmp[a] = P.drho[a] * P.kr[a] * imu - P.rho[a] * P.kr[a] * P.dmu[a] * imu * imu;
-    P.dms[a] = P.rho[a] * P.dkr[a] * imu;
-    P.pot[a] = sub_rn(p, mul_rn(P.rho[a], gz5));
+    P.dms[a] = P.rho[a] * P.dkr[a] * imu + P.drhos[a] * P.kr[a] * imu - P.rho[a] * P.kr[a] * P.dmus[a] * imu * imu;
+    P.pot[a] = sub_rn(pa, mul_rn(P.rho[a], gz5));
     P.dpot[a] = 1.0 - P.drho[a] * gz5;
+    P.dpots[a] = dpa_s - P.drhos[a] * gz5;
   }
 }
 
 __device__ __forceinline__ double depth(double top, double dz, int k) { return add_rn(top, mul_rn((double)k + 0.5, dz)); }
 
-// per-cell mobility / potential table for the face terms: 10 x n (SoA)
+// per-cell mobility / potential table for the face terms: 11 x n (SoA)
 __global__ void k_props(int n, int nxy, fluid_c f, double top, double dz, const double *phi, const double *p,
                         const double *s, double *pr) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -106,6 +140,7 @@ __global__ void k_props(int n, int nxy, fluid_c f, double top, double dz, const 
   pr[4 * (size_t)n + c] = P.dms[0]; pr[5 * (size_t)n + c] = P.dms[1];
   pr[6 * (size_t)n + c] = P.pot[0]; pr[7 * (size_t)n + c] = P.pot[1];
   pr[8 * (size_t)n + c] = P.dpot[0]; pr[9 * (size_t)n + c] = P.dpot[1];
+  pr[10 * (size_t)n + c] = P.dpots[0];                // the oil potential does not depend on s_w
 }
 
 // geometric two-point transmissibility of the +x, +y, +z face of each cell
@@ -131,6 +166,40 @@ __global__ void k_peaceman(int np_, double dx, double dy, double dz, const int *
   wi[q] = 2.0 * M_PI * RS_CDARCY * sqrt(a * b) * dz / (log(ro / rw[w]) + skin[w]);
 }
 
+// Mass rates of one perforation (eq. 10) for both phases (0 = water, 1 =
+// oil; + = into the cell) and their derivatives with respect to the cell's
+// p, s_w and to p_b.  Drawdown of phase a: dd = p_b - p_a + rho_a g (z -
+// z_ref).  Producer: own phase mobility, outflow only; injector (dd >= 0):
+// water only with the total cell mobility; injector crossflow (dd < 0):
+// upstream from the cell like a producer; a shut well carries nothing.
+struct pflow { double q[2], dqp[2], dqs[2], dqb[2]; };
+__device__ __forceinline__ void perf_flow(const fluid_c &f, int kind, int ctrl, double wi, const cprops &P, double pc_,
+                                          double pbw, double dz5, pflow &F) {
+#pragma unroll
+  for (int a = 0; a < 2; a++) {
+    F.q[a] = F.dqp[a] = F.dqs[a] = F.dqb[a] = 0.0;
+    if (ctrl == SIM_SHUT) continue;
+    double pa = a == 0 ? sub_rn(pc_, P.pc) : pc_;
+    double dd = add_rn(sub_rn(pbw, pa), mul_rn(P.rho[a], dz5));
+    double dd_dp = -1.0 + P.drho[a] * dz5, dd_ds = (a == 0 ? P.dpc : 0.0) + P.drhos[a] * dz5;
+    if (kind == SIM_PROD || dd < 0.0) {         // producer, or injector crossflow: upstream = cell
+      if (dd <= 0.0) {
+        F.q[a] = wi * P.m[a] * dd; F.dqp[a] = wi * (P.dmp[a] * dd + P.m[a] * dd_dp);
+        F.dqs[a] = wi * (P.dms[a] * dd + P.m[a] * dd_ds); F.dqb[a] = wi * P.m[a];
+      }
+    } else if (a == 0) {                          // injection; at dd = 0 the injecting-side derivative
+      double lt = P.kr[0] / P.mu[0] + P.kr[1] / P.mu[1];
+      double lt_p = -P.kr[0] * P.dmu[0] / (P.mu[0] * P.mu[0]) - P.kr[1] * P.dmu[1] / (P.mu[1] * P.mu[1]);
+      double lt_s = P.dkr[0] / P.mu[0] - P.kr[0] * P.dmus[0] / (P.mu[0] * P.mu[0]) + P.dkr[1] / P.mu[1] -
+                    P.kr[1] * P.dmus[1] / (P.mu[1] * P.mu[1]);
+      F.q[a] = wi * P.rho[0] * lt * dd;
+      F.dqp[a] = wi * (P.drho[0] * lt * dd + P.rho[0] * lt_p * dd + P.rho[0] * lt * dd_dp);
+      F.dqs[a] = wi * (P.drhos[0] * lt * dd + P.rho[0] * lt_s * dd + P.rho[0] * lt * dd_ds);
+      F.dqb[a] = wi * P.rho[0] * lt;
+    }
+  }
+}
+
 // --------------------------------------------------------------- assembly --
 // One thread per cell: accumulation, the six faces (evaluated from this
 // cell's side; the neighbour evaluates the same face with the same
@@ -143,7 +212,8 @@ k_assemble(int nx, int ny, int nz, fluid_c f, double top, double dz, double vol_
            const double *__restrict__ ty, const double *__restrict__ tz, const int *__restrict__ rp,
            const int *__restrict__ cpp, const int *__restrict__ cpi, const int *__restrict__ pwell,
            const double *__restrict__ pwi, const int *__restrict__ ppos_cw, const int *__restrict__ wkind,
-           const double *__restrict__ wzref, double *__restrict__ val, double *__restrict__ b) {
+           const int *__restrict__ wctrl, const double *__restrict__ wzref, double *__restrict__ val,
+           double *__restrict__ b) {
   int n = nx * ny * nz, c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   int nxy = nx * ny, i = c % nx, j = (c / nx) % ny, k = c / nxy;
@@ -158,7 +228,7 @@ k_assemble(int nx, int ny, int nz, fluid_c f, double top, double dz, double vol_
   D[0] = vol_dt * (P.dphi * P.rho[1] + P.phi * P.drho[1]) * so;
   D[1] = vol_dt * (-P.phi * P.rho[1]);
   D[2] = vol_dt * (P.dphi * P.rho[0] + P.phi * P.drho[0]) * sc;
-  D[3] = vol_dt * (P.phi * P.rho[0]);
+  D[3] = vol_dt * (P.phi * P.rho[0] + P.phi * P.drhos[0] * sc);
   // neighbours in ascending column order: -z, -y, -x, (self), +x, +y, +z
   int nb_[6] = {k > 0 ? c - nxy : -1, j > 0 ? c - nx : -1, i > 0 ? c - 1 : -1,
                 i + 1 < nx ? c + 1 : -1, j + 1 < ny ? c + nx : -1, k + 1 < nz ? c + nxy : -1};
@@ -177,14 +247,15 @@ k_assemble(int nx, int ny, int nz, fluid_c f, double top, double dz, double vol_
       double potd = pr[(size_t)(6 + a) * n + d], dpotd = pr[(size_t)(8 + a) * n + d];
       double mc = pr[(size_t)a * n + c], dmpc = pr[(size_t)(2 + a) * n + c], dmsc = pr[(size_t)(4 + a) * n + c];
       double potc = pr[(size_t)(6 + a) * n + c], dpotc = pr[(size_t)(8 + a) * n + c];
+      double dpotsc = a == 0 ? pr[(size_t)10 * n + c] : 0.0, dpotsd = a == 0 ? pr[(size_t)10 * n + d] : 0.0;
       bool upc = (c < d) ? (potc >= potd) : !(potd >= potc);
       double dpot = potd - potc;
       double Tm = T * (upc ? mc : md);
       double F = Tm * dpot;
       double dFdpc = T * ((upc ? dmpc : 0.0) * dpot) - Tm * dpotc;
-      double dFdsc = T * ((upc ? dmsc : 0.0) * dpot);
+      double dFdsc = T * ((upc ? dmsc : 0.0) * dpot) - Tm * dpotsc;
       double dFdpd = T * ((upc ? 0.0 : dmpd) * dpot) + Tm * dpotd;
-      double dFdsd = T * ((upc ? 0.0 : dmsd) * dpot);
+      double dFdsd = T * ((upc ? 0.0 : dmsd) * dpot) + Tm * dpotsd;
       if (e == 0) R0 -= F; else R1 -= F;
       D[2 * e] -= dFdpc; D[2 * e + 1] -= dFdsc;
       O[2 * e] = -dFdpd; O[2 * e + 1] = -dFdsd;
@@ -193,34 +264,19 @@ k_assemble(int nx, int ny, int nz, fluid_c f, double top, double dz, double vol_
     reinterpret_cast<double2 *>(Bo)[0] = make_double2(O[0], O[1]);
     reinterpret_cast<double2 *>(Bo)[1] = make_double2(O[2], O[3]);
   }
-  // perforations of this cell (eq. 10): producer per phase, outflow only;
-  // injector water only with the total mobility; crossflow into an
-  // injector's wellbore is upstream from the cell, like a producer
+  // perforations of this cell (eq. 10)
   for (int a2 = cpp[c]; a2 < cpp[c + 1]; a2++) {
     int q = cpi[a2], w = pwell[q];
-    double wi = pwi[q];
     double dz5 = mul_rn(mul_rn(f.g, sub_rn(z, wzref[w])), RS_PA2BAR);
+    pflow F;
+    perf_flow(f, wkind[w], wctrl[w], pwi[q], P, pc, pbh[w], dz5, F);
     double W[4] = {0, 0, 0, 0};
+#pragma unroll
     for (int a = 0; a < 2; a++) {
       int e = 1 - a;
-      double dd = add_rn(sub_rn(pbh[w], pc), mul_rn(P.rho[a], dz5)), dd_dp = -1.0 + P.drho[a] * dz5;
-      double q_ = 0, dqdp = 0, dqds = 0, dqdb = 0;
-      if (wkind[w] == SIM_PROD || dd < 0.0) {     // producer, or injector crossflow: upstream = cell
-        if (dd <= 0.0) {
-          q_ = wi * P.m[a] * dd; dqdp = wi * (P.dmp[a] * dd + P.m[a] * dd_dp);
-          dqds = wi * P.dms[a] * dd; dqdb = wi * P.m[a];
-        }
-      } else if (a == 0) {                          // injection; at dd = 0 the injecting-side derivative
-        double lt = P.kr[0] / P.mu[0] + P.kr[1] / P.mu[1];
-        double lt_p = -P.kr[0] * P.dmu[0] / (P.mu[0] * P.mu[0]) - P.kr[1] * P.dmu[1] / (P.mu[1] * P.mu[1]);
-        double lt_s = P.dkr[0] / P.mu[0] + P.dkr[1] / P.mu[1];
-        q_ = wi * P.rho[0] * lt * dd;
-        dqdp = wi * (P.drho[0] * lt * dd + P.rho[0] * lt_p * dd + P.rho[0] * lt * dd_dp);
-        dqds = wi * P.rho[0] * lt_s * dd; dqdb = wi * P.rho[0] * lt;
-      }
-      if (e == 0) R0 -= q_; else R1 -= q_;
-      D[2 * e] -= dqdp; D[2 * e + 1] -= dqds;
-      W[2 * e] = -dqdb;
+      if (e == 0) R0 -= F.q[a]; else R1 -= F.q[a];
+      D[2 * e] -= F.dqp[a]; D[2 * e + 1] -= F.dqs[a];
+      W[2 * e] = -F.dqb[a];
     }
     double *Bw = val + 4 * (size_t)ppos_cw[q];
     Bw[0] = W[0]; Bw[1] = 0.0; Bw[2] = W[2]; Bw[3] = 0.0;
@@ -231,17 +287,23 @@ k_assemble(int nx, int ny, int nz, fluid_c f, double top, double dz, double vol_
   reinterpret_cast<double2 *>(b)[c] = make_double2(-R0, -R1);
 }
 
-// well rows: eq. (11) scaled by the target, or eq. (12) scaled by the target
-// mass rate; one thread per well, perforations in order
+// well rows, one thread per well, perforations in order: BHP control
+// eq. (11) scaled by the target; a rate control sum_m (cw q_w + co q_o) - 1
+// with the weights of eq. (12) water, (13) oil or (14) liquid rate in
+// surface volumes over the target (production positive for a producer);
+// a shut well keeps p_b (1 * p_b, residual 0)
 __global__ void k_wells(int n, int nw, fluid_c f, double top, double dz, int nxy, const double *phi, const double *p,
                         const double *s, const double *pbh, const int *wpptr, const int *pcell, const double *pwi,
                         const int *ppos_wc, const int *wdiag, const int *wkind, const int *wctrl, const double *wtarget,
                         const double *wzref, double *val, double *b) {
   int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= nw) return;
+  int ctrl = wctrl[w];
+  double sgn = wkind[w] == SIM_PROD ? -1.0 : 1.0, T = wtarget[w];
+  double cw = (ctrl == SIM_WRATE || ctrl == SIM_LRATE) ? sgn / (f.rho_ref[0] * T) : 0.0;
+  double co = (ctrl == SIM_ORATE || ctrl == SIM_LRATE) ? sgn / (f.rho_ref[1] * T) : 0.0;
+  bool rate = cw != 0.0 || co != 0.0;
   double R = 0.0, Jww = 0.0;
-  bool rate = wctrl[w] == SIM_WRATE;
-  double scale = rate ? 1.0 / (f.rho_ref[0] * wtarget[w]) : 0.0;
   for (int q = wpptr[w]; q < wpptr[w + 1]; q++) {
     int c = pcell[q];
     double *B = val + 4 * (size_t)ppos_wc[q];
@@ -251,25 +313,17 @@ __global__ void k_wells(int n, int nw, fluid_c f, double top, double dz, int nxy
       double z = depth(top, dz, c / nxy);
       cell_props(f, phi[c], z, p[c], s[c], P);
       double dz5 = mul_rn(mul_rn(f.g, sub_rn(z, wzref[w])), RS_PA2BAR);
-      double dd = add_rn(sub_rn(pbh[w], p[c]), mul_rn(P.rho[0], dz5)), dd_dp = -1.0 + P.drho[0] * dz5;
-      double q_ = 0, dqdp = 0, dqds = 0, dqdb = 0;
-      if (wkind[w] == SIM_PROD || dd < 0.0) {
-        if (dd <= 0.0) { q_ = pwi[q] * P.m[0] * dd; dqdp = pwi[q] * (P.dmp[0] * dd + P.m[0] * dd_dp);
-                         dqds = pwi[q] * P.dms[0] * dd; dqdb = pwi[q] * P.m[0]; }
-      } else {
-        double lt = P.kr[0] / P.mu[0] + P.kr[1] / P.mu[1];
-        double lt_p = -P.kr[0] * P.dmu[0] / (P.mu[0] * P.mu[0]) - P.kr[1] * P.dmu[1] / (P.mu[1] * P.mu[1]);
-        double lt_s = P.dkr[0] / P.mu[0] + P.dkr[1] / P.mu[1];
-        double wi = pwi[q];
-        q_ = wi * P.rho[0] * lt * dd;
-        dqdp = wi * (P.drho[0] * lt * dd + P.rho[0] * lt_p * dd + P.rho[0] * lt * dd_dp);
-        dqds = wi * P.rho[0] * lt_s * dd; dqdb = wi * P.rho[0] * lt;
-      }
-      R += scale * q_; b0 = scale * dqdp; b1 = scale * dqds; Jww += scale * dqdb;
+      pflow F;
+      perf_flow(f, wkind[w], ctrl, pwi[q], P, p[c], pbh[w], dz5, F);
+      R += cw * F.q[0] + co * F.q[1];
+      b0 = cw * F.dqp[0] + co * F.dqp[1];
+      b1 = cw * F.dqs[0] + co * F.dqs[1];
+      Jww += cw * F.dqb[0] + co * F.dqb[1];
     }
     B[0] = b0; B[1] = b1; B[2] = 0.0; B[3] = 0.0;
   }
   if (rate) R -= 1.0;
+  else if (ctrl == SIM_SHUT) { R = 0.0; Jww = 1.0; }
   else { R = (pbh[w] - wtarget[w]) / wtarget[w]; Jww = 1.0 / wtarget[w]; }
   double *Bd = val + 4 * (size_t)wdiag[w];
   Bd[0] = Jww; Bd[1] = 0.0; Bd[2] = 0.0; Bd[3] = 1.0;
@@ -353,11 +407,15 @@ __global__ void k_hydrostatic(int n, int nxy, fluid_c f, double top, double dz, 
   p[c] = div_rn(r, a);
   s[c] = sw0;
 }
-__global__ void k_init_pb(int nw, const int *wctrl, const double *wtarget, const int *wpptr, const int *pcell,
-                          const double *p, double *pb) {
+// initial wellbore pressure: a BHP well at its target, a rate (or shut)
+// well 10 bar above (injector) or below (producer) the oil pressure of its
+// first perforated cell
+__global__ void k_init_pb(int nw, const int *wkind, const int *wctrl, const double *wtarget, const int *wpptr,
+                          const int *pcell, const double *p, double *pb) {
   int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= nw) return;
-  pb[w] = wctrl[w] == SIM_BHP ? wtarget[w] : add_rn(p[pcell[wpptr[w]]], 10.0);
+  double p0 = p[pcell[wpptr[w]]];
+  pb[w] = wctrl[w] == SIM_BHP ? wtarget[w] : (wkind[w] == SIM_PROD ? sub_rn(p0, 10.0) : add_rn(p0, 10.0));
 }
 
 // ------------------------------------------------------------- host side --
@@ -370,7 +428,8 @@ static void s_props_assemble(sim_s *h) {
   k_assemble<<<grid_for(n, 128), 128, 0, s>>>(h->nx, h->ny, h->nz, h->fl, h->top, h->dz, h->dx * h->dy * h->dz / h->dt,
                                               h->phi.p, h->p.p, h->s.p, h->pb.p, h->acc0.p, h->props.p, h->tx.p,
                                               h->ty.p, h->tz.p, ls->rp.p, h->cpp.p, h->cpi.p, h->pwell.p, h->pwi.p,
-                                              h->ppos_cw.p, h->wkind_d.p, h->wzref_d.p, ls->val.p, ls->b.p);
+                                              h->ppos_cw.p, h->wkind_d.p, h->wctrl_d.p, h->wzref_d.p, ls->val.p,
+                                              ls->b.p);
   RS_LAUNCHED(2);
   if (h->nw) {
     k_wells<<<grid_for(h->nw, 32), 32, 0, s>>>(n, h->nw, h->fl, h->top, h->dz, nxy, h->phi.p, h->p.p, h->s.p, h->pb.p,
@@ -557,6 +616,61 @@ static int s_solve(sim_s *h, double eta, double bn, int *its, double *rel) {
   return rc;
 }
 
+// ------------------------------------------------ well control switching --
+// The host keeps each well's current control and target; the device copies
+// are refreshed after every change.
+static void s_controls_upload(sim_s *h) {
+  if (!h->nw) return;
+  RS_CUDA(cudaMemcpyAsync(h->wctrl_d.p, h->wctrl.data(), h->nw * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  RS_CUDA(cudaMemcpyAsync(h->wtarget_d.p, h->wtarget.data(), h->nw * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  RS_CUDA(cudaStreamSynchronize(h->st));      // the host vectors may change right after
+}
+static void s_controls_reset(sim_s *h) {
+  for (int w = 0; w < h->nw; w++) { h->wctrl[w] = h->wctrl0[w]; h->wtarget[w] = h->wtarget0[w]; h->wswitched[w] = 0; }
+  s_controls_upload(h);
+}
+static bool is_rate(int c) { return c == SIM_WRATE || c == SIM_ORATE || c == SIM_LRATE; }
+
+// Rate to BHP, after a Newton update: a rate-controlled well with a BHP limit
+// whose p_b has passed it (injector above its maximum, producer below its
+// minimum) goes on BHP control at the limit and p_b is set to the limit.
+static int s_limits_rate_to_bhp(sim_s *h) {
+  if (!h->any_limit) return 0;
+  std::vector<double> pb = d2h(h->pb.p, h->nw, h->st);
+  int k = 0;
+  for (int w = 0; w < h->nw; w++) {
+    if (!is_rate(h->wctrl[w]) || !(h->wlimit[w] > 0.0)) continue;
+    bool past = h->wkind[w] == SIM_INJ ? pb[w] > h->wlimit[w] : pb[w] < h->wlimit[w];
+    if (!past) continue;
+    h->wctrl[w] = SIM_BHP; h->wtarget[w] = h->wlimit[w]; h->wswitched[w] = 1;
+    RS_CUDA(cudaMemcpyAsync(h->pb.p + w, &h->wlimit[w], sizeof(double), cudaMemcpyHostToDevice, h->st));
+    k++;
+  }
+  if (k) s_controls_upload(h);
+  return k;
+}
+
+static void s_props_assemble(sim_s *h);
+// BHP back to rate, at the start of a time step (after the old accumulation
+// is stored): a well held at its limit returns to its requested rate when,
+// at the limit, its rate equation's residual is positive (it would deliver
+// more than the target).
+static void s_limits_bhp_to_rate(sim_s *h) {
+  bool any = false;
+  for (int w = 0; w < h->nw; w++)
+    if (h->wswitched[w]) { h->wctrl[w] = h->wctrl0[w]; h->wtarget[w] = h->wtarget0[w]; any = true; }
+  if (!any) return;
+  s_controls_upload(h);
+  s_props_assemble(h);
+  std::vector<double> b = d2h(h->ls->b.p + 2 * (size_t)h->n, 2 * (size_t)h->nw, h->st);
+  for (int w = 0; w < h->nw; w++) {
+    if (!h->wswitched[w]) continue;
+    if (-b[2 * w] > 0.0) h->wswitched[w] = 0;
+    else { h->wctrl[w] = SIM_BHP; h->wtarget[w] = h->wlimit[w]; }
+  }
+  s_controls_upload(h);
+}
+
 static int s_newton(sim_s *h, int *iters) {
   RS_CUDA(cudaEventRecord(h->e0, h->st));
   s_props_assemble(h);
@@ -585,6 +699,7 @@ static int s_newton(sim_s *h, int *iters) {
     k_update<<<grid_for(h->n + h->nw, 256), 256, 0, h->st>>>(h->n, h->nw, h->o.sat_chop, h->ls->y.p, h->p.p, h->s.p, h->pb.p);
     RS_LAUNCHED(1);
     h->stats.newton++;
+    h->stats.switches += s_limits_rate_to_bhp(h);
     RS_CUDA(cudaEventRecord(h->e0, h->st));
     s_props_assemble(h);
     nr = s_norm(h);
@@ -612,6 +727,17 @@ static void copy_in(dbuf<double> &d, const double *src, size_t m, cudaStream_t s
   if (m) RS_CUDA(cudaMemcpyAsync(d.p, src, m * sizeof(double), cudaMemcpyDefault, s));
 }
 
+// host check of a well control (eqs. 11-14, shut): NULL when valid
+static const char *well_control_invalid(int kind, int control, double target, double limit) {
+  if (kind != SIM_INJ && kind != SIM_PROD) return "bad kind";
+  if (control < SIM_BHP || control > SIM_SHUT) return "unknown control";
+  if ((control == SIM_ORATE || control == SIM_LRATE) && kind != SIM_PROD)
+    return "oil- and liquid-rate controls need a producer (injectors inject water)";
+  if (control != SIM_SHUT && !(target > 0 && target < HUGE_VAL)) return "target must be finite and positive";
+  if (!(limit >= 0 && limit < HUGE_VAL)) return "BHP limit must be finite and >= 0 (0 = none)";
+  return nullptr;
+}
+
 extern "C" sim_status sim_create(sim_t *out, const sim_grid *g, const sim_rock *r, const sim_fluid *f,
                                  const sim_well *wells, int n_wells, const sim_options *o) {
   ABI_BEGIN
@@ -627,13 +753,20 @@ extern "C" sim_status sim_create(sim_t *out, const sim_grid *g, const sim_rock *
   if (!r->kx || !r->ky || !r->kz || !r->phi) RS_FAIL(SIM_ERR_ARG, "sim_create: NULL rock array");
   if (const char *e = rs_opts_invalid(o)) RS_FAIL(SIM_ERR_ARG, "sim_create: %s", e);
   if (!(o->dt > 0.0 && o->dt < HUGE_VAL)) RS_FAIL(SIM_ERR_ARG, "sim_create: dt must be finite and > 0");
+  if (f->pc_n < 0 || f->pc_n > PC_MAX) RS_FAIL(SIM_ERR_ARG, "sim_create: a capillary pressure table holds 0 to %d points", PC_MAX);
+  if (f->pc_n > 0) {
+    if (!f->pc_sw || !f->pc_val) RS_FAIL(SIM_ERR_ARG, "sim_create: NULL capillary pressure table");
+    for (int k = 0; k < f->pc_n; k++) {
+      if (!std::isfinite(f->pc_sw[k]) || !std::isfinite(f->pc_val[k]))
+        RS_FAIL(SIM_ERR_ARG, "sim_create: capillary pressure table entry %d is not finite", k);
+      if (k > 0 && !(f->pc_sw[k] > f->pc_sw[k - 1]))
+        RS_FAIL(SIM_ERR_ARG, "sim_create: capillary pressure table saturations must increase");
+    }
+  }
   for (int w = 0; w < n_wells; w++) {           // host-side well checks before any device work
     const sim_well &W = wells[w];
-    if (W.kind != SIM_INJ && W.kind != SIM_PROD) RS_FAIL(SIM_ERR_ARG, "well %d: bad kind", w);
-    if (W.control == SIM_WRATE && W.kind != SIM_INJ) RS_FAIL(SIM_ERR_ARG, "well %d: water-rate control needs an injector", w);
-    if (W.control != SIM_BHP && W.control != SIM_WRATE) RS_FAIL(SIM_ERR_ARG, "well %d: control not supported", w);
+    if (const char *e = well_control_invalid(W.kind, W.control, W.target, W.bhp_limit)) RS_FAIL(SIM_ERR_ARG, "well %d: %s", w, e);
     if (W.n_perf < 1 || !W.perf_cell) RS_FAIL(SIM_ERR_ARG, "well %d: no perforations", w);
-    if (!(W.target > 0)) RS_FAIL(SIM_ERR_ARG, "well %d: target must be positive", w);
     for (int q = 0; q < W.n_perf; q++)
       if (W.perf_cell[q] < 0 || W.perf_cell[q] >= g->nx * g->ny * g->nz)
         RS_FAIL(SIM_ERR_ARG, "well %d: perforation outside the grid", w);
@@ -642,7 +775,15 @@ extern "C" sim_status sim_create(sim_t *out, const sim_grid *g, const sim_rock *
   std::unique_ptr<sim_s> guard(h);
   h->nx = g->nx; h->ny = g->ny; h->nz = g->nz; h->n = g->nx * g->ny * g->nz; h->nw = n_wells;
   h->dx = g->dx; h->dy = g->dy; h->dz = g->dz; h->top = g->top_depth;
-  memcpy(&h->fl, f, sizeof(fluid_c));
+  {
+    fluid_c &F = h->fl;
+    memset(&F, 0, sizeof(F));
+    for (int a = 0; a < 2; a++) { F.rho_ref[a] = f->rho_ref[a]; F.c_f[a] = f->c_f[a]; F.mu_ref[a] = f->mu_ref[a]; F.c_mu[a] = f->c_mu[a]; }
+    F.p_ref = f->p_ref; F.c_r = f->c_r; F.swc = f->swc; F.sor = f->sor; F.nw = f->nw; F.no = f->no;
+    F.krw_max = f->krw_max; F.kro_max = f->kro_max; F.g = f->g;
+    F.pc_n = f->pc_n;
+    for (int k = 0; k < f->pc_n; k++) { F.pc_sw[k] = f->pc_sw[k]; F.pc_val[k] = f->pc_val[k]; }
+  }
   h->o = rs_opts_from(o);
   h->st = (cudaStream_t)o->cuda_stream;
   h->dt = h->o.dt;
@@ -657,13 +798,13 @@ extern "C" sim_status sim_create(sim_t *out, const sim_grid *g, const sim_rock *
   std::vector<std::vector<int>> cellwells(n);
   for (int w = 0; w < nw; w++) {
     const sim_well &W = wells[w];
-    if (W.kind != SIM_INJ && W.kind != SIM_PROD) RS_FAIL(SIM_ERR_ARG, "well %d: bad kind", w);
-    if (W.control == SIM_WRATE && W.kind != SIM_INJ) RS_FAIL(SIM_ERR_ARG, "well %d: water-rate control needs an injector", w);
-    if (W.control != SIM_BHP && W.control != SIM_WRATE) RS_FAIL(SIM_ERR_ARG, "well %d: control not supported", w);
+    if (const char *e = well_control_invalid(W.kind, W.control, W.target, W.bhp_limit)) RS_FAIL(SIM_ERR_ARG, "well %d: %s", w, e);
     if (W.n_perf < 1 || !W.perf_cell) RS_FAIL(SIM_ERR_ARG, "well %d: no perforations", w);
-    if (!(W.target > 0)) RS_FAIL(SIM_ERR_ARG, "well %d: target must be positive", w);
     h->wkind.push_back(W.kind); h->wctrl.push_back(W.control);
     h->wtarget.push_back(W.target); h->wzref.push_back(W.z_ref);
+    h->wctrl0.push_back(W.control); h->wtarget0.push_back(W.target); h->wlimit.push_back(W.bhp_limit);
+    h->wswitched.push_back(0);
+    if (W.bhp_limit > 0.0) h->any_limit = true;
     rw[w] = W.r_w; skin[w] = W.skin;
     for (int q = 0; q < W.n_perf; q++) {
       int c = W.perf_cell[q];
@@ -731,7 +872,7 @@ extern "C" sim_status sim_create(sim_t *out, const sim_grid *g, const sim_rock *
     RS_LAUNCHED(1);
   }
   h->p.alloc(n); h->s.alloc(n); h->pb.alloc(nw ? nw : 1); h->acc0.alloc(2 * (size_t)n);
-  h->props.alloc(10 * (size_t)n); h->p0.alloc(n); h->s0.alloc(n); h->pb0.alloc(nw ? nw : 1);
+  h->props.alloc(11 * (size_t)n); h->p0.alloc(n); h->s0.alloc(n); h->pb0.alloc(nw ? nw : 1);
   rs_fill_d(h->p.p, h->fl.p_ref, n, s); rs_fill_d(h->s.p, h->fl.swc, n, s); rs_fill_d(h->pb.p, 0.0, nw ? nw : 1, s);
   h->ls = new sim_ls_s();
   ls_init(h->ls, nx, ny, nz, nw, rp.data(), ci.data(), wc0.data(), h->o, s);
@@ -751,7 +892,9 @@ extern "C" sim_status sim_init_hydrostatic(sim_t h, double p_datum, double sw0) 
   k_hydrostatic<<<grid_for(h->n, 256), 256, 0, h->st>>>(h->n, nxy, h->fl, h->top, h->dz, p_datum, sw0, h->p.p, h->s.p);
   RS_LAUNCHED(1);
   if (h->nw) {
-    k_init_pb<<<grid_for(h->nw, 32), 32, 0, h->st>>>(h->nw, h->wctrl_d.p, h->wtarget_d.p, h->wpptr.p, h->pcell.p, h->p.p, h->pb.p);
+    s_controls_reset(h);
+    k_init_pb<<<grid_for(h->nw, 32), 32, 0, h->st>>>(h->nw, h->wkind_d.p, h->wctrl_d.p, h->wtarget_d.p, h->wpptr.p,
+                                                     h->pcell.p, h->p.p, h->pb.p);
     RS_LAUNCHED(1);
   }
   h->t = 0.0;
@@ -835,6 +978,7 @@ extern "C" sim_status sim_newton_step(sim_t h, int *converged, sim_stats *st) {
     k_update<<<grid_for(h->n + h->nw, 256), 256, 0, h->st>>>(h->n, h->nw, h->o.sat_chop, h->ls->y.p, h->p.p, h->s.p, h->pb.p);
     RS_LAUNCHED(1);
     h->stats.newton++;
+    h->stats.switches += s_limits_rate_to_bhp(h);
   }
   if (st) *st = h->stats;
   ABI_END
@@ -846,6 +990,8 @@ extern "C" sim_status sim_advance(sim_t h, int n_steps, sim_stats *st) {
   cudaStream_t s = h->st;
   int n = h->n, nw = h->nw;
   sim_status bad = SIM_OK;
+  std::vector<int> c0(nw), w0(nw);
+  std::vector<double> t0(nw);
   for (int stp = 0; stp < n_steps && bad == SIM_OK; stp++) {
     double rem = h->o.dt, hh = h->o.dt;
     int cuts = 0;
@@ -857,6 +1003,8 @@ extern "C" sim_status sim_advance(sim_t h, int n_steps, sim_stats *st) {
       s_store_old(h);
       h->dt = dt;
       h->first_pending = true;
+      s_limits_bhp_to_rate(h);
+      c0 = h->wctrl; t0 = h->wtarget; w0 = h->wswitched;
       int its;
       int r = s_newton(h, &its);
       h->stats.last_newton = its;
@@ -864,6 +1012,10 @@ extern "C" sim_status sim_advance(sim_t h, int n_steps, sim_stats *st) {
       RS_CUDA(cudaMemcpyAsync(h->p.p, h->p0.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
       RS_CUDA(cudaMemcpyAsync(h->s.p, h->s0.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
       if (nw) RS_CUDA(cudaMemcpyAsync(h->pb.p, h->pb0.p, nw * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      if (h->wctrl != c0 || h->wtarget != t0 || h->wswitched != w0) {
+        h->wctrl = c0; h->wtarget = t0; h->wswitched = w0;
+        s_controls_upload(h);
+      }
       h->stats.cuts++; cuts++;
       if (cuts > h->o.max_cuts) { bad = r == 2 ? SIM_ERR_NAN : SIM_ERR_NOT_CONVERGED; break; }
       hh = 0.5 * hh;
@@ -881,6 +1033,39 @@ extern "C" sim_status sim_get_stats(sim_t h, sim_stats *st) {
   if (!h || !st) RS_FAIL(SIM_ERR_ARG, "NULL argument");
   h->stats.t = h->t;
   *st = h->stats;
+  ABI_END
+}
+
+extern "C" sim_status sim_set_well(sim_t h, int w, int control, double target, double bhp_limit) {
+  ABI_BEGIN
+  if (!h) RS_FAIL(SIM_ERR_ARG, "NULL handle");
+  if (w < 0 || w >= h->nw) RS_FAIL(SIM_ERR_ARG, "sim_set_well: no well %d", w);
+  if (const char *e = well_control_invalid(h->wkind[w], control, target, bhp_limit))
+    RS_FAIL(SIM_ERR_ARG, "sim_set_well: well %d: %s", w, e);
+  h->wctrl[w] = h->wctrl0[w] = control;
+  h->wtarget[w] = h->wtarget0[w] = target;
+  h->wlimit[w] = bhp_limit; h->wswitched[w] = 0;
+  h->any_limit = false;
+  for (int k = 0; k < h->nw; k++) if (h->wlimit[k] > 0.0) h->any_limit = true;
+  s_controls_upload(h);
+  double pbw = 0.0;
+  if (control == SIM_BHP) pbw = target;
+  else if (control != SIM_SHUT) {
+    double p0 = d2h(h->p.p + d2h(h->pcell.p + h->pptr[w], 1, h->st)[0], 1, h->st)[0];
+    pbw = h->wkind[w] == SIM_PROD ? p0 - 10.0 : p0 + 10.0;
+  }
+  if (control != SIM_SHUT) RS_CUDA(cudaMemcpyAsync(h->pb.p + w, &pbw, sizeof(double), cudaMemcpyHostToDevice, h->st));
+  RS_CUDA(cudaStreamSynchronize(h->st));
+  ABI_END
+}
+
+extern "C" sim_status sim_get_well_controls(sim_t h, int *control, double *target) {
+  ABI_BEGIN
+  if (!h) RS_FAIL(SIM_ERR_ARG, "NULL handle");
+  for (int w = 0; w < h->nw; w++) {
+    if (control) control[w] = h->wctrl[w];
+    if (target) target[w] = h->wtarget[w];
+  }
   ABI_END
 }
 

@@ -90,18 +90,34 @@ def test_bad_wells_are_rejected_before_device_work():
     from paper_1701_06254_gb300 import inputs as I
     base = I.case0()
     bad = [
-        (dict(kind=5), "bad kind"),
-        (dict(kind=I.PROD, control=I.WRATE), "needs an injector"),
-        (dict(control=7), "not supported"),
-        (dict(target=0.0), "positive"),
-        (dict(perf_cells=np.array([base.n], np.int32)), "outside the grid"),
-        (dict(perf_cells=np.array([-1], np.int32)), "outside the grid"),
+        (0, dict(kind=5), "bad kind"),
+        (0, dict(control=I.ORATE), "need a producer"),          # an injector injects water only
+        (0, dict(control=I.LRATE), "need a producer"),
+        (0, dict(control=7), "unknown control"),
+        (0, dict(target=0.0), "positive"),
+        (0, dict(target=float("inf")), "positive"),
+        (1, dict(bhp_limit=-1.0), "BHP limit"),
+        (1, dict(bhp_limit=float("nan")), "BHP limit"),
+        (0, dict(perf_cells=np.array([base.n], np.int32)), "outside the grid"),
+        (0, dict(perf_cells=np.array([-1], np.int32)), "outside the grid"),
     ]
-    for change, text in bad:
+    for w, change, text in bad:
         c = copy.deepcopy(base)
-        c.wells[0] = dataclasses.replace(c.wells[0], **change)
+        c.wells[w] = dataclasses.replace(c.wells[w], **change)
         rc, msg = _create(R, c)
         assert rc == 1 and text in msg, (change, rc, msg)
+
+
+def test_bad_capillary_tables_are_rejected_before_device_work():
+    import paper_1701_06254_gb300 as R
+    from paper_1701_06254_gb300 import inputs as I
+    for sw, pc, text in (((0.3, 0.2), (1.0, 0.5), "must increase"),
+                         ((0.2, 0.3), (1.0, float("nan")), "not finite"),
+                         (tuple(np.linspace(0.2, 0.8, 17)), tuple(np.linspace(2.0, 0.0, 17)), "0 to 16 points")):
+        c = I.case0()
+        c.fluid = dataclasses.replace(c.fluid, pc_sw=sw, pc=pc)
+        rc, msg = _create(R, c)
+        assert rc == 1 and text in msg, (sw, rc, msg)
 
 
 def test_ls_create_checks_options():
