@@ -23,7 +23,7 @@ _lib = None
 DEFAULT_OPTS = dict(decoupling=1, reorder=1, newton=0, newton_tol=1e-8, lin_tol=1e-8,
                     max_newton=20, restart=50, max_lin=100, tile_x=4, tile_y=4,
                     amg_theta=0.25, amg_max_levels=25, amg_coarse_max=128,
-                    seed=0x5EED, max_cuts=6, dt=1.0, sat_chop=0.0)
+                    seed=0x5EED, max_cuts=6, dt=1.0, sat_chop=0.0, krylov=0, overlap=1, interp=0)
 
 
 def build(force: bool = False) -> str:
@@ -75,7 +75,8 @@ class Opts(C.Structure):
                 ("max_newton", C.c_int), ("restart", C.c_int), ("max_lin", C.c_int),
                 ("tile_x", C.c_int), ("tile_y", C.c_int), ("amg_theta", C.c_double),
                 ("amg_max_levels", C.c_int), ("amg_coarse_max", C.c_int),
-                ("seed", C.c_uint64), ("max_cuts", C.c_int), ("dt", C.c_double), ("sat_chop", C.c_double)]
+                ("seed", C.c_uint64), ("max_cuts", C.c_int), ("dt", C.c_double), ("sat_chop", C.c_double),
+                ("krylov", C.c_int), ("overlap", C.c_int), ("interp", C.c_int)]
 
 
 def make_opts(**kw) -> Opts:

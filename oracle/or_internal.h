@@ -21,6 +21,7 @@ enum { OR_INJ = 0, OR_PROD = 1 };
 enum { OR_BHP = 0, OR_WRATE = 1, OR_ORATE = 2, OR_LRATE = 3, OR_SHUT = 4 };
 enum { OR_DEC_NONE = 0, OR_DEC_ABF = 1, OR_DEC_QI = 2 };
 enum { OR_STANDARD = 0, OR_INEXACT = 1 };
+enum { OR_FGMRES = 0, OR_BICGSTAB = 1 };
 
 typedef struct {
   int nx, ny, nz;
@@ -54,6 +55,9 @@ typedef struct {
   int max_cuts;
   double dt;
   double sat_chop;       /* max |ds_w| per Newton update, 0 = full step */
+  int krylov;            /* OR_FGMRES or OR_BICGSTAB */
+  int overlap;           /* RAS overlap (graph distance), 1 or 2 */
+  int interp;            /* AMG interpolation: 0 direct, 1 extended+i */
 } or_opts;
 
 /* ---- compressed sparse rows (scalar) ---- */

@@ -373,8 +373,85 @@ long or_reorth_count(void) { return S_reorth; }
    with classical Gram-Schmidt and a conditional second pass; Givens
    rotations on the Hessenberg matrix.  Returns 0 (converged), 1 (iteration limit) or
    2 (non-finite value). */
+/* BiCGSTAB (van der Vorst), right preconditioned by CPR-FPF: the paper's
+   other Krylov method (Examples 3, 6 and 7; each iteration applies the
+   preconditioner twice).  Solves A M^-1 u = b with x = M^-1 u from x = 0.
+   One iteration:
+     rho = (rh, r);  beta = (rho / rho_prev) (alpha / omega)
+     p = r + beta (p - omega v);  ph = M^-1 p;  v = A ph
+     alpha = rho / (rh, v);  s = r - alpha v
+     (stop with x += alpha ph when ||s|| <= tol ||b||)
+     sh = M^-1 s;  t = A sh;  omega = (t, s) / (t, t)
+     x += alpha ph + omega sh;  r = s - omega t
+   The iteration stops when the recursive residual meets tol ||b||; the true
+   residual b - A x is then checked, and when it does not meet the tolerance
+   (or on a breakdown: rho, (rh, v) or omega zero) the method restarts from
+   the true residual with rh = r.  At most max_lin iterations. */
+static int or_lsys_solve_bicgstab(or_lsys *ls, double tol, double *x, int *its_out, double *relres)
+{
+  int nu = 2 * ls->nb, maxit = ls->o.max_lin, its = 0, rc = 1;
+  double *r = xc(nu, 8), *rh = xc(nu, 8), *p = xc(nu, 8), *v = xc(nu, 8), *s = xc(nu, 8);
+  double *t = xc(nu, 8), *ph = xc(nu, 8), *sh = xc(nu, 8);
+  for (int i = 0; i < nu; i++) x[i] = 0.0;
+  double bn = sqrt(dot(ls->b, ls->b, nu)), rn = bn;
+  if (bn == 0.0) { *its_out = 0; *relres = 0.0; rc = 0; goto out; }
+  if (bn != bn) { *its_out = 0; *relres = bn; rc = 2; goto out; }
+  memcpy(r, ls->b, 8 * (size_t)nu);
+  for (;;) {                                   /* (re)start from the residual in r */
+    memcpy(rh, r, 8 * (size_t)nu);
+    memset(p, 0, 8 * (size_t)nu); memset(v, 0, 8 * (size_t)nu);
+    double rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+    int broke = 0, done = 0;
+    while (its < maxit) {
+      double rho = dot(rh, r, nu);
+      if (rho == 0.0) { broke = 1; break; }
+      double beta = (rho / rho_prev) * (alpha / omega);
+      for (int i = 0; i < nu; i++) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+      or_cpr_apply(ls, p, ph);
+      or_bsr_mv(ls, ph, v);
+      double rv = dot(rh, v, nu);
+      if (rv == 0.0) { broke = 1; break; }
+      alpha = rho / rv;
+      for (int i = 0; i < nu; i++) s[i] = r[i] - alpha * v[i];
+      its++;
+      double sn = sqrt(dot(s, s, nu));
+      if (sn != sn) { rc = 2; rn = sn; goto out; }
+      if (sn <= tol * bn) {
+        for (int i = 0; i < nu; i++) x[i] += alpha * ph[i];
+        done = 1; break;
+      }
+      or_cpr_apply(ls, s, sh);
+      or_bsr_mv(ls, sh, t);
+      double tt = dot(t, t, nu), ts = dot(t, s, nu);
+      omega = tt > 0.0 ? ts / tt : 0.0;
+      for (int i = 0; i < nu; i++) x[i] += alpha * ph[i] + omega * sh[i];
+      for (int i = 0; i < nu; i++) r[i] = s[i] - omega * t[i];
+      rn = sqrt(dot(r, r, nu));
+      if (rn != rn) { rc = 2; goto out; }
+      if (rn <= tol * bn) { done = 1; break; }
+      if (omega == 0.0) { broke = 1; break; }
+      rho_prev = rho;
+    }
+    /* true residual */
+    or_bsr_mv(ls, x, t);
+    for (int i = 0; i < nu; i++) r[i] = ls->b[i] - t[i];
+    rn = sqrt(dot(r, r, nu));
+    if (rn != rn) { rc = 2; goto out; }
+    if (rn <= tol * bn) { rc = 0; break; }
+    if (its >= maxit) { rc = 1; break; }
+    if (!done && !broke) { rc = 1; break; }
+  }
+out:
+  if (bn > 0.0 && rc != 2) *relres = rn / bn;
+  else if (rc == 2) *relres = NAN;
+  *its_out = its;
+  free(r); free(rh); free(p); free(v); free(s); free(t); free(ph); free(sh);
+  return rc;
+}
+
 int or_lsys_solve(or_lsys *ls, double tol, double *y, int *its_out, double *relres)
 {
+  if (ls->o.krylov == OR_BICGSTAB) return or_lsys_solve_bicgstab(ls, tol, y, its_out, relres);
   int nu = 2 * ls->nb, m = ls->o.restart > 0 ? ls->o.restart : 50, maxit = ls->o.max_lin;
   double *V = xc((size_t)(m + 1) * nu, 8), *Z = xc((size_t)m * nu, 8);
   double *H = xc((size_t)(m + 1) * m, 8), *cs = xc(m, 8), *sn = xc(m, 8), *g = xc(m + 1, 8);

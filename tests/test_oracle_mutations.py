@@ -177,6 +177,18 @@ MUTATIONS = [
     ("FGMRES restart: the cycle's correction replaces the iterate", "or_solve.c",
      "s += yy[k] * Z[(size_t)k * nu + i]; y[i] += s; }", "s += yy[k] * Z[(size_t)k * nu + i]; y[i] = s; }",
      "test_oracle_solver", "test_restarted_fgmres_matches_dense_solve", {}),
+    ("BiCGSTAB: search direction without the omega v term", "or_solve.c",
+     "p[i] = r[i] + beta * (p[i] - omega * v[i]);", "p[i] = r[i] + beta * p[i];",
+     "test_oracle_solver", "test_bicgstab_cpr_matches_dense_solve", dict(tile=(2, 2), coarse=8)),
+    ("BiCGSTAB: update without the second preconditioned direction", "or_solve.c",
+     "x[i] += alpha * ph[i] + omega * sh[i];", "x[i] += alpha * ph[i];",
+     "test_oracle_solver", "test_bicgstab_cpr_matches_dense_solve", dict(tile=(2, 2), coarse=8)),
+    ("BiCGSTAB: residual update with the wrong sign", "or_solve.c",
+     "r[i] = s[i] - omega * t[i];", "r[i] = s[i] + omega * t[i];",
+     "test_oracle_solver", "test_bicgstab_cpr_matches_dense_solve", dict(tile=(2, 2), coarse=8)),
+    ("BiCGSTAB: beta without the alpha / omega factor", "or_solve.c",
+     "double beta = (rho / rho_prev) * (alpha / omega);", "double beta = (rho / rho_prev);",
+     "test_oracle_solver", "test_bicgstab_cpr_matches_dense_solve", dict(tile=(2, 2), coarse=8)),
     # AMG (Algorithm 2, pressure stage)
     ("strength: comparison reversed", "or_amg.c",
      "-A->v[q] >= thr", "-A->v[q] <= thr",
