@@ -67,6 +67,13 @@ enum { SIM_NEWTON_STANDARD = 0, SIM_NEWTON_INEXACT = 1 };      /* Algorithm 1   
 /* preconditioner precision: FP64; FP32 (AMG, RAS factors, CPR vectors; FP64
  * coarsest solve); FP32 with the RAS factor values stored in BF16 */
 enum { SIM_PREC_FP64 = 0, SIM_PREC_MIXED = 1, SIM_PREC_MIXED_BF16 = 2 };
+/* Krylov method of the linear solve: flexible GMRES(restart) (the paper's
+ * GMRES(50), Examples 4-5) or BiCGSTAB (Examples 3, 6, 7), both right
+ * preconditioned by CPR-FPF (Algorithm 2) */
+enum { SIM_KRYLOV_FGMRES = 0, SIM_KRYLOV_BICGSTAB = 1 };
+/* AMG interpolation on the pressure block: direct, or extended+i (distance-
+ * two interpolation through the strong F neighbours' strong C points) */
+enum { SIM_INTERP_DIRECT = 0, SIM_INTERP_EXTI = 1 };
 
 typedef struct { int nx, ny, nz; double dx, dy, dz, top_depth; } sim_grid;
 
@@ -126,6 +133,9 @@ typedef struct {
   double dt;           /* time step, days                                          */
   void *cuda_stream;   /* cudaStream_t or NULL                                     */
   double sat_chop;     /* max |ds_w| applied per Newton update, 0 = full step      */
+  int krylov;          /* SIM_KRYLOV_FGMRES or SIM_KRYLOV_BICGSTAB                 */
+  int overlap;         /* RAS overlap in the matrix graph: 1 or 2 (Table 9)        */
+  int interp;          /* SIM_INTERP_DIRECT or SIM_INTERP_EXTI                     */
 } sim_options;
 
 /* Statistics, cumulative since creation. */
@@ -145,7 +155,7 @@ typedef struct sim_ls_s *sim_ls_t;
 /* Fill *o with the defaults: FP64, ABF, reordering on, standard Newton,
  * newton_tol 1e-8, lin_tol 1e-8, max_newton 20, restart 50, max_lin 100,
  * 4x4 tiles, theta 0.25, 25 levels, coarsest <= 128 rows, 6 cuts, dt 1,
- * no saturation chop. */
+ * no saturation chop, FGMRES, overlap 1, direct interpolation. */
 void sim_default_options(sim_options *o);
 
 /* Create a simulator (copies everything).  Builds transmissibilities,

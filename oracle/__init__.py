@@ -128,7 +128,8 @@ def _sig(lib):
         "or_ls_amg": (P, [P]),
         "or_ls_sub_sizes": (None, [P, C.c_int, _ip]),
         "or_ls_sub_get": (None, [P, C.c_int, _ip, _ip, _ip, _ip, _dp, _dp]),
-        "or_amg_new": (P, [C.c_int, _ip, _ip, _dp, C.c_double, C.c_uint64, C.c_int, C.c_int]),
+        "or_amg_new": (P, [C.c_int, _ip, _ip, _dp, C.c_double, C.c_uint64, C.c_int, C.c_int, C.c_int]),
+        "or_interp_given": (None, [C.c_int, _ip, _ip, _dp, C.c_double, C.c_void_p, C.c_int, _ip, _ip, _ip, _dp]),
         "or_amg_delete": (None, [P]),
         "or_amg_nlev": (C.c_int, [P]),
         "or_amg_level_sizes": (None, [P, C.c_int, _ip]),
@@ -180,6 +181,20 @@ def pm_mapping(key):
     return pm
 
 
+def interpolation(rp, ci, v, cf, theta=0.25, interp=0):
+    """P of a scalar CSR matrix for a given C/F split (cf: 1 = C, -1 = F):
+    direct (interp=0) or extended+i (interp=1).  Returns (prp, pci, pv)."""
+    rp = np.ascontiguousarray(rp, np.int32); ci = np.ascontiguousarray(ci, np.int32)
+    v = np.ascontiguousarray(v, np.float64); cf = np.ascontiguousarray(cf, np.int8)
+    n = len(rp) - 1
+    nnz = C.c_int()
+    lib().or_interp_given(n, _i(rp), _i(ci), _d(v), theta, cf.ctypes.data, interp, C.byref(nnz), None, None, None)
+    prp = np.zeros(n + 1, np.int32); pci = np.zeros(max(nnz.value, 1), np.int32); pv = np.zeros(max(nnz.value, 1))
+    lib().or_interp_given(n, _i(rp), _i(ci), _d(v), theta, cf.ctypes.data, interp, C.byref(nnz), _i(prp), _i(pci),
+                          _d(pv))
+    return prp, pci[:nnz.value], pv[:nnz.value]
+
+
 def forcing(l, bn, rprev, bprev):
     """eta_l of eq. (26), second choice, clamped to [0.01, 0.1]."""
     return lib().or_forcing(l, bn, rprev, bprev)
@@ -196,7 +211,8 @@ def splitmix64(x):
 class AMG:
     """Standalone AMG hierarchy on a scalar CSR matrix."""
 
-    def __init__(self, rp, ci, v, theta=0.25, seed=0x5EED, coarse_max=128, max_levels=25, _handle=None, _owner=None):
+    def __init__(self, rp, ci, v, theta=0.25, seed=0x5EED, coarse_max=128, max_levels=25, interp=0, _handle=None,
+                 _owner=None):
         self._lib = lib()
         if _handle is not None:
             self.h, self._own, self._owner = _handle, False, _owner
@@ -205,7 +221,8 @@ class AMG:
         self._ci = np.ascontiguousarray(ci, dtype=np.int32)
         self._v = np.ascontiguousarray(v, dtype=np.float64)
         n = len(self._rp) - 1
-        self.h = self._lib.or_amg_new(n, _i(self._rp), _i(self._ci), _d(self._v), theta, seed, coarse_max, max_levels)
+        self.h = self._lib.or_amg_new(n, _i(self._rp), _i(self._ci), _d(self._v), theta, seed, coarse_max, max_levels,
+                                      interp)
         self._own = True
 
     def __del__(self):

@@ -10,7 +10,8 @@
  *   coarsening   PMIS (parallel modified independent set) with weights
  *                w_i = |S^T_i| + h(i), h a splitmix64 hash in [0, 1)
  *   interpolation direct (Stueben), positive off-diagonals lumped into the
- *                diagonal, R = P^T, Galerkin A_c = R (A P)
+ *                diagonal; or extended+i (De Sterck, Falgout, Nolting and
+ *                Yang); R = P^T, Galerkin A_c = R (A P)
  *   cycle        one V(1,1) with l1-Jacobi smoothing, zero initial guess
  *   coarsest     dense LU with partial pivoting
  * Every sum is accumulated left to right in the order of the loops below.
@@ -161,6 +162,130 @@ static void interp(const or_csr *A, const unsigned char *S, const signed char *c
   free(cidx);
 }
 
+/* value of row k's entry in column col (binary search; rows are sorted),
+   found = 0 when the row has no such entry */
+static double row_value(const or_csr *A, int k, int col, int *found)
+{
+  int a = A->rp[k], b = A->rp[k + 1];
+  while (a < b) {
+    int m = (a + b) / 2;
+    if (A->ci[m] == col) { *found = 1; return A->v[m]; }
+    if (A->ci[m] < col) a = m + 1; else b = m;
+  }
+  *found = 0;
+  return 0.0;
+}
+
+/* the couplings of row k that extended+i distributes: a_kl when it differs
+   in sign from the diagonal a_kk, else 0 */
+static double hat(double akk, double akl)
+{
+  if (akk < 0.0) return akl > 0.0 ? akl : 0.0;
+  return akl < 0.0 ? akl : 0.0;
+}
+
+static int in_sorted(const int *a, int m, int x)
+{
+  int lo = 0, hi = m;
+  while (lo < hi) { int md = (lo + hi) / 2; if (a[md] == x) return 1; if (a[md] < x) lo = md + 1; else hi = md; }
+  return 0;
+}
+
+/* extended+i interpolation (De Sterck, Falgout, Nolting and Yang, "Distance-
+   two interpolation for parallel algebraic multigrid", 2008).  C point: P_i =
+   e_{c(i)}.  F point i: the interpolatory set is C^_i = C^s_i united with the
+   strong C neighbours C^s_k of every strong F neighbour k in F^s_i.  With
+   a^_kl the couplings of row k of the opposite sign to a_kk and, for each k
+   in F^s_i, D_k = sum over l in C^_i + {i} of a^_kl (row k's column order):
+     at_ii = a_ii + sum_{n weak, n not in C^_i} a_in
+                  + sum_{k in F^s_i} a_ik a^_ki / D_k      (a_ik itself when D_k = 0)
+     w_ij  = -(a_ij + sum_{k in F^s_i, D_k != 0, j in row k} a_ik a^_kj / D_k) / at_ii
+   for j in C^_i ascending (a_ij = 0 when j is no neighbour of i); both sums
+   run in row i's column order.  An F point without strong connections has
+   an empty row. */
+static void interp_exti(const or_csr *A, const unsigned char *S, const signed char *cf, or_csr *P)
+{
+  int n = A->n;
+  int *cidx = xc(n, 4), nc = 0;
+  for (int i = 0; i < n; i++) cidx[i] = (cf[i] == 1) ? nc++ : -1;
+  int *stamp = xc(n, 4);
+  for (int i = 0; i < n; i++) stamp[i] = -1;
+  int maxrow = 0;
+  for (int i = 0; i < n; i++) if (A->rp[i + 1] - A->rp[i] > maxrow) maxrow = A->rp[i + 1] - A->rp[i];
+  /* C^_i of every F row, sorted ascending */
+  int **set = xc(n, sizeof(int *)), *len = xc(n, 4), *buf = xc(n, 4);
+  for (int i = 0; i < n; i++) {
+    if (cf[i] == 1) continue;
+    int m = 0;
+    for (int q = A->rp[i]; q < A->rp[i + 1]; q++) {
+      int j = A->ci[q];
+      if (!S[q] || j == i) continue;
+      if (cf[j] == 1) { if (stamp[j] != i) { stamp[j] = i; buf[m++] = j; } }
+      else for (int r = A->rp[j]; r < A->rp[j + 1]; r++) {
+        int l = A->ci[r];
+        if (S[r] && cf[l] == 1 && stamp[l] != i) { stamp[l] = i; buf[m++] = l; }
+      }
+    }
+    for (int a = 1; a < m; a++) { int v = buf[a], b = a - 1; while (b >= 0 && buf[b] > v) { buf[b + 1] = buf[b]; b--; } buf[b + 1] = v; }
+    set[i] = xc(m, 4); memcpy(set[i], buf, 4 * (size_t)m); len[i] = m;
+  }
+  P->n = n; P->m = nc;
+  P->rp = xc(n + 1, 4);
+  for (int i = 0; i < n; i++) P->rp[i + 1] = P->rp[i] + (cf[i] == 1 ? 1 : len[i]);
+  P->nnz = P->rp[n];
+  P->ci = xc(P->nnz, 4); P->v = xc(P->nnz, 8);
+  double *D = xc(maxrow, 8);
+  for (int i = 0; i < n; i++) {
+    int o = P->rp[i];
+    if (cf[i] == 1) { P->ci[o] = cidx[i]; P->v[o] = 1.0; continue; }
+    int m = len[i];
+    if (m == 0) continue;
+    const int *cs = set[i];
+    int q0 = A->rp[i], f;
+    /* D_k of each strong F neighbour, by its position in row i */
+    for (int q = q0; q < A->rp[i + 1]; q++) {
+      int k = A->ci[q];
+      D[q - q0] = 0.0;
+      if (!S[q] || k == i || cf[k] != -1) continue;
+      double akk = row_value(A, k, k, &f), d = 0.0;
+      for (int r = A->rp[k]; r < A->rp[k + 1]; r++) {
+        int l = A->ci[r];
+        if (l == i || in_sorted(cs, m, l)) d = d + hat(akk, A->v[r]);
+      }
+      D[q - q0] = d;
+    }
+    double at = 0.0;
+    at = row_value(A, i, i, &f);
+    for (int q = q0; q < A->rp[i + 1]; q++) {
+      int j = A->ci[q];
+      if (j == i) continue;
+      if (S[q]) {
+        if (cf[j] == 1) continue;
+        if (D[q - q0] == 0.0) at = at + A->v[q];
+        else {
+          double akk = row_value(A, j, j, &f), aki = row_value(A, j, i, &f);
+          at = at + (A->v[q] * hat(akk, aki)) / D[q - q0];
+        }
+      } else if (!in_sorted(cs, m, j)) at = at + A->v[q];
+    }
+    for (int a = 0; a < m; a++) {
+      int j = cs[a];
+      double num = row_value(A, i, j, &f);
+      for (int q = q0; q < A->rp[i + 1]; q++) {
+        int k = A->ci[q];
+        if (!S[q] || k == i || cf[k] != -1 || D[q - q0] == 0.0) continue;
+        double akj = row_value(A, k, j, &f);
+        if (!f) continue;
+        double akk = row_value(A, k, k, &f);
+        num = num + (A->v[q] * hat(akk, akj)) / D[q - q0];
+      }
+      P->ci[o] = cidx[j]; P->v[o++] = -num / at;
+    }
+  }
+  for (int i = 0; i < n; i++) if (cf[i] != 1) free(set[i]);
+  free(set); free(len); free(buf); free(stamp); free(cidx); free(D);
+}
+
 /* T = A^T; rows of T list their columns in ascending order */
 void or_transpose(const or_csr *A, or_csr *T)
 {
@@ -265,7 +390,8 @@ static void dense_solve(int n, const double *a, const int *piv, const double *f,
    has at most coarse_max rows or l = max_levels - 1 (dense LU), or when
    PMIS finds no coarse point (then the coarsest solve is 10 l1-Jacobi
    sweeps unless the level is small enough for the dense LU). */
-int or_amg_setup(or_amg *h, const or_csr *A0, double theta, uint64_t seed, int coarse_max, int max_levels)
+int or_amg_setup(or_amg *h, const or_csr *A0, double theta, uint64_t seed, int coarse_max, int max_levels,
+                 int interpolation)
 {
   memset(h, 0, sizeof(*h));
   if (max_levels > 32) max_levels = 32;
@@ -282,7 +408,8 @@ int or_amg_setup(or_amg *h, const or_csr *A0, double theta, uint64_t seed, int c
     L->pmis_rounds = pmis(&L->A, L->strong, seed, l, L->cf);
     int nc = 0; for (int i = 0; i < n; i++) nc += (L->cf[i] == 1);
     if (nc == 0) { h->coarse_dense = 0; break; }
-    interp(&L->A, L->strong, L->cf, &L->P);
+    if (interpolation == 1) interp_exti(&L->A, L->strong, L->cf, &L->P);
+    else interp(&L->A, L->strong, L->cf, &L->P);
     or_transpose(&L->P, &L->R);
     or_csr AP; or_spgemm(&L->A, &L->P, &AP);
     or_spgemm(&L->R, &AP, &h->lev[l + 1].A);
@@ -331,13 +458,34 @@ void or_amg_vcycle(const or_amg *h, int l, const double *f, double *x)
 
 /* ---- standalone AMG for tests ---- */
 or_amg *or_amg_new(int n, const int *rp, const int *ci, const double *v, double theta,
-                   uint64_t seed, int coarse_max, int max_levels)
+                   uint64_t seed, int coarse_max, int max_levels, int interpolation)
 {
   or_csr A; A.n = A.m = n; A.nnz = rp[n];
   A.rp = (int *)rp; A.ci = (int *)ci; A.v = (double *)v;
   or_amg *h = xc(1, sizeof(or_amg));
-  or_amg_setup(h, &A, theta, seed, coarse_max, max_levels);
+  or_amg_setup(h, &A, theta, seed, coarse_max, max_levels, interpolation);
   return h;
+}
+
+/* test hook: strength and interpolation (0 direct, 1 extended+i) of a
+   scalar matrix for a given C/F split; *nnz receives the size of P, and
+   prp / pci / pv (when not NULL) its rows */
+void or_interp_given(int n, const int *rp, const int *ci, const double *v, double theta, const signed char *cf,
+                     int interpolation, int *nnz, int *prp, int *pci, double *pv)
+{
+  or_csr A; A.n = A.m = n; A.nnz = rp[n];
+  A.rp = (int *)rp; A.ci = (int *)ci; A.v = (double *)v;
+  unsigned char *S = xc(A.nnz, 1);
+  strength(&A, theta, S);
+  or_csr P;
+  memset(&P, 0, sizeof(P));
+  if (interpolation == 1) interp_exti(&A, S, cf, &P); else interp(&A, S, cf, &P);
+  *nnz = P.nnz;
+  if (prp) memcpy(prp, P.rp, 4 * (size_t)(n + 1));
+  if (pci) memcpy(pci, P.ci, 4 * (size_t)P.nnz);
+  if (pv) memcpy(pv, P.v, 8 * (size_t)P.nnz);
+  or_csr_free(&P);
+  free(S);
 }
 void or_amg_delete(or_amg *h) { if (h) { or_amg_free(h); free(h); } }
 int or_amg_nlev(const or_amg *h) { return h->nlev; }

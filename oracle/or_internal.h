@@ -133,7 +133,7 @@ typedef struct {
 void or_csr_free(or_csr *a);
 void or_amg_free(or_amg *h);
 int  or_amg_setup(or_amg *h, const or_csr *A0, double theta, uint64_t seed,
-                  int coarse_max, int max_levels);
+                  int coarse_max, int max_levels, int interpolation);
 void or_amg_vcycle(const or_amg *h, int l, const double *f, double *x);
 uint64_t or_splitmix64(uint64_t x);
 double or_pmis_hash(uint64_t seed, int level, int i);

@@ -153,8 +153,9 @@ void or_potential_rank(int m, const double *key, const int *idx, int *order)
 
 /* Subdomain = column tile of tile_x x tile_y cells over all layers; a well
    belongs to the tile of its first perforated cell.  The local system is
-   the rows of (owned unknowns + their neighbours in the matrix graph),
-   restricted to those rows and columns, with cells ordered by descending
+   the rows of the owned unknowns and of every unknown within graph
+   distance `overlap` of them in the matrix graph (overlap 1, or 2 as in the
+   paper's Table 9), restricted to those rows and columns, with cells ordered by descending
    oil potential (eq. 30, applied per subdomain) and wells last (eq. 32). */
 static void build_subs(or_lsys *ls)
 {
@@ -177,15 +178,20 @@ static void build_subs(or_lsys *ls)
   for (int r = 0; r < nb; r++) { mark[r] = 0; loc[r] = -1; }
   for (int s = 0; s < ls->nsub; s++) {
     or_sub *S = &ls->sub[s];
-    int m = 0;
+    int m = 0, ov = ls->o.overlap == 2 ? 2 : 1;
     for (int a = 0; a < S->nown; a++) {
       int g = S->own[a];
       if (!mark[g]) { mark[g] = 1; list[m++] = g; }
-      for (int q = ls->rp[g]; q < ls->rp[g + 1]; q++) {
-        int c = ls->ci[q];
-        if (!mark[c]) { mark[c] = 1; list[m++] = c; }
-      }
     }
+    /* rings of graph neighbours, one per level of overlap */
+    for (int lev = 0, r0 = 0, r1 = m; lev < ov; lev++, r0 = r1, r1 = m)
+      for (int a = r0; a < r1; a++) {
+        int g = list[a];
+        for (int q = ls->rp[g]; q < ls->rp[g + 1]; q++) {
+          int c = ls->ci[q];
+          if (!mark[c]) { mark[c] = 1; list[m++] = c; }
+        }
+      }
     /* split into cells and wells, each in ascending global order */
     int mc = 0, mw = 0;
     int *cells = xc(m, 4), *wl = xc(m, 4);
@@ -337,7 +343,8 @@ int or_lsys_setup(or_lsys *ls)
     for (int q = ls->rp[i]; q < ls->rp[i + 1]; q++)
       if (ls->ci[q] < ls->n) { A.ci[nnz] = ls->ci[q]; A.v[nnz++] = ls->val[4 * (size_t)q]; }
   or_amg_free(&ls->amg);
-  int rc = or_amg_setup(&ls->amg, &A, ls->o.amg_theta, ls->o.seed, ls->o.amg_coarse_max, ls->o.amg_max_levels);
+  int rc = or_amg_setup(&ls->amg, &A, ls->o.amg_theta, ls->o.seed, ls->o.amg_coarse_max, ls->o.amg_max_levels,
+                        ls->o.interp);
   or_csr_free(&A);
   ls->have_setup = 1;
   return rc;

@@ -18,6 +18,8 @@ from . import inputs  # noqa: F401  (synthetic workloads)
 _lib = None
 
 PREC_FP64, PREC_MIXED, PREC_MIXED_BF16 = 0, 1, 2
+KRYLOV_FGMRES, KRYLOV_BICGSTAB = 0, 1
+INTERP_DIRECT, INTERP_EXTI = 0, 1
 DEC_NONE, DEC_ABF, DEC_QI = 0, 1, 2
 OP_SPMV, OP_RAS, OP_VCYCLE, OP_CPR = 0, 1, 2, 3
 T_NONE, T_SPMV64, T_SPMV_PREC, T_RAS, T_VCYCLE, T_ORTHO, T_ASSEMBLE = 0, 1, 2, 3, 4, 5, 6
@@ -66,7 +68,7 @@ class Options(C.Structure):
                 ("restart", C.c_int), ("max_lin", C.c_int), ("tile_x", C.c_int), ("tile_y", C.c_int),
                 ("amg_theta", C.c_double), ("amg_max_levels", C.c_int), ("amg_coarse_max", C.c_int),
                 ("seed", C.c_uint64), ("max_cuts", C.c_int), ("dt", C.c_double), ("cuda_stream", C.c_void_p),
-                ("sat_chop", C.c_double)]
+                ("sat_chop", C.c_double), ("krylov", C.c_int), ("overlap", C.c_int), ("interp", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -204,7 +206,7 @@ def launch_count():
 
 OPT_KEYS = ("precision", "decoupling", "reorder", "newton", "newton_tol", "lin_tol", "max_newton", "restart",
             "max_lin", "tile_x", "tile_y", "amg_theta", "amg_max_levels", "amg_coarse_max", "seed", "max_cuts", "dt",
-            "sat_chop")
+            "sat_chop", "krylov", "overlap", "interp")
 
 
 def make_options(stream=None, **kw):

@@ -97,6 +97,7 @@ struct rs_opts {
   uint64_t seed;
   int max_cuts;
   double dt, sat_chop;
+  int krylov, overlap, interp;
 };
 const char *rs_opts_invalid(const sim_options *o);
 rs_opts rs_opts_from(const sim_options *o);
@@ -211,6 +212,8 @@ struct sim_ls_s {
   dbuf<float> w2, isp;          // double-float w planes; split 1 / h_{j+1,j}
   dbuf<int> ticket;             // last-block ticket of the Gram-Schmidt sweeps (zero between launches)
   dbuf<float> vallo;            // lo plane of the decoupled matrix (hi: val32)
+  dbuf<double> bcg;             // BiCGSTAB vectors: rh, p, v, s, t, ph, sh, x (2 nb each)
+  dbuf<float> bcg32;            // mixed precision: the FP32 preconditioned vector
   // timer brackets recorded inside the graph (event nodes): pairs of events
   // and the family of each pair, read back after every replay
   std::vector<cudaEvent_t> gev;

@@ -976,7 +976,137 @@ __global__ void k_xupdate(int nu, int jend, const double *yk, const Tz *Z, doubl
   x[i] += s;
 }
 
+// ------------------------------------------------------------ BiCGSTAB ---
+// Right-preconditioned BiCGSTAB (van der Vorst), the paper's other Krylov
+// method (its Examples 3, 6 and 7): two CPR applications per iteration.
+// FP64 vectors throughout; in mixed precision the preconditioner returns an
+// FP32 vector, widened to FP64 before its product with A.
+__global__ void k_bcg_p(int nu, const double *r, const double *v, double beta, double omega, double *p) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nu) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+}
+__global__ void k_bcg_s(int nu, const double *r, const double *v, double alpha, double *s) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nu) s[i] = r[i] - alpha * v[i];
+}
+__global__ void k_bcg_xr(int nu, double alpha, const double *ph, double omega, const double *sh, const double *s,
+                         const double *t, double *x, double *r) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nu) { x[i] += alpha * ph[i] + omega * sh[i]; r[i] = s[i] - omega * t[i]; }
+}
+__global__ void k_bcg_xa(int nu, double alpha, const double *ph, double *x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nu) x[i] += alpha * ph[i];
+}
+__global__ void k_widen(int nu, const float *a, double *b) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nu) b[i] = (double)a[i];
+}
+
+// z = M^-1 v (CPR-FPF) in FP64
+static void bcg_precond(sim_ls_s *ls, const double *v, double *z) {
+  int nu = 2 * ls->nb;
+  if (ls->o.precision != SIM_PREC_FP64) {
+    ls_cpr(ls, v, nullptr, ls->bcg32.p);
+    k_widen<<<grid_for(nu, 256), 256, 0, ls->st>>>(nu, ls->bcg32.p, z);
+    RS_LAUNCHED(1);
+  } else {
+    ls_cpr(ls, v, z, nullptr);
+  }
+}
+
+// Solves A M^-1 u = b, x = M^-1 u, from x = 0 or from the initial guess in
+// ls->y (x0; the solution is left in ls->y).  Stops
+// when the recursive residual meets tol ||b||, then checks the true residual
+// b - A x; when that misses the tolerance, or on a breakdown (rho, (rh, v)
+// or omega zero), it restarts from the true residual with rh = r.  At most
+// max_lin iterations.  0 = converged, 1 = iteration cap, 2 = non-finite.
+static int ls_solve_bicgstab(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
+  cudaStream_t st = ls->st;
+  int nu = 2 * ls->nb, maxit = ls->o.max_lin, its = 0, rc = 1;
+  ls->bcg.ensure(8 * (size_t)nu);
+  if (ls->o.precision != SIM_PREC_FP64) ls->bcg32.ensure(nu);
+  double *rh = ls->bcg.p, *p = rh + nu, *v = p + nu, *sv = v + nu, *t = sv + nu, *ph = t + nu, *sh = ph + nu;
+  double *x = ls->y.p, *r = ls->r.p;
+  unsigned g = grid_for(nu, 256);
+  double bn = rs_norm2(ls->b.p, nu, st), rn = bn;
+  if (bn == 0.0) { rs_fill_d(x, 0.0, nu, st); *its_out = 0; *relres = 0.0; return 0; }
+  if (!std::isfinite(bn)) { rs_fill_d(x, 0.0, nu, st); *its_out = 0; *relres = NAN; return 2; }
+  if (x0) {                                   // r = b - A x0
+    spmv<double, double, double, double>(ls, ls->val.p, x, ls->b.p, r, st);
+    rn = rs_norm2(r, nu, st);
+  }
+  if (!x0 || !std::isfinite(rn)) {
+    rs_fill_d(x, 0.0, nu, st);
+    RS_CUDA(cudaMemcpyAsync(r, ls->b.p, nu * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    rn = bn;
+  }
+  if (rn <= tol * bn) { *its_out = 0; *relres = rn / bn; return 0; }
+  auto check = [&]() {
+    if (ls->errw[0]) RS_FAIL(SIM_ERR_TIMEOUT, "RAS apply: bulk copy wait gave up (code %d)", ls->errw[0]);
+  };
+  for (;;) {
+    RS_CUDA(cudaMemcpyAsync(rh, r, nu * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    rs_fill_d(p, 0.0, nu, st); rs_fill_d(v, 0.0, nu, st);
+    double rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+    bool broke = false, done = false;
+    while (its < maxit) {
+      double rho;
+      { const double *xs[1] = {rh}, *ys[1] = {r}; rs_dots(xs, ys, 1, nu, &rho, st); }
+      if (!std::isfinite(rho)) { *its_out = its; *relres = NAN; return 2; }
+      if (rho == 0.0) { broke = true; break; }
+      double beta = (rho / rho_prev) * (alpha / omega);
+      k_bcg_p<<<g, 256, 0, st>>>(nu, r, v, beta, omega, p);
+      RS_LAUNCHED(1);
+      bcg_precond(ls, p, ph);
+      ls_spmv64(ls, ph, v);
+      double rv;
+      { const double *xs[1] = {rh}, *ys[1] = {v}; rs_dots(xs, ys, 1, nu, &rv, st); }
+      check();
+      if (!std::isfinite(rv)) { *its_out = its; *relres = NAN; return 2; }
+      if (rv == 0.0) { broke = true; break; }
+      alpha = rho / rv;
+      k_bcg_s<<<g, 256, 0, st>>>(nu, r, v, alpha, sv);
+      RS_LAUNCHED(1);
+      its++;
+      double sn = rs_norm2(sv, nu, st);
+      if (!std::isfinite(sn)) { *its_out = its; *relres = NAN; return 2; }
+      if (sn <= tol * bn) {
+        k_bcg_xa<<<g, 256, 0, st>>>(nu, alpha, ph, x);
+        RS_LAUNCHED(1);
+        done = true;
+        break;
+      }
+      bcg_precond(ls, sv, sh);
+      ls_spmv64(ls, sh, t);
+      double tt_ts[2];
+      { const double *xs[2] = {t, t}, *ys[2] = {t, sv}; rs_dots(xs, ys, 2, nu, tt_ts, st); }
+      check();
+      omega = tt_ts[0] > 0.0 ? tt_ts[1] / tt_ts[0] : 0.0;
+      k_bcg_xr<<<g, 256, 0, st>>>(nu, alpha, ph, omega, sh, sv, t, x, r);
+      RS_LAUNCHED(1);
+      rn = rs_norm2(r, nu, st);
+      if (!std::isfinite(rn)) { *its_out = its; *relres = NAN; return 2; }
+      if (rn <= tol * bn) { done = true; break; }
+      if (omega == 0.0) { broke = true; break; }
+      rho_prev = rho;
+    }
+    // true residual r = b - A x
+    spmv<double, double, double, double>(ls, ls->val.p, x, ls->b.p, r, st);
+    rn = rs_norm2(r, nu, st);
+    ls->timer_flush();
+    if (!std::isfinite(rn)) { rc = 2; break; }
+    if (rn <= tol * bn) { rc = 0; break; }
+    if (its >= maxit) { rc = 1; break; }
+    if (!done && !broke) { rc = 1; break; }
+  }
+  *its_out = its;
+  *relres = rc == 2 ? NAN : rn / bn;
+  return rc;
+}
+
 int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
+  if (ls->o.krylov == SIM_KRYLOV_BICGSTAB) return ls_solve_bicgstab(ls, tol, its_out, relres, x0);
   cudaStream_t s = ls->st;
   int nu = 2 * ls->nb, m = std::min(ls->o.restart, ORTHO_MAXV - 1), maxit = ls->o.max_lin;
   // df: double-float Arnoldi basis (its kernels use 32-bit offsets into the

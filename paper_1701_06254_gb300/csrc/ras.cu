@@ -4,7 +4,7 @@
 // eqs. (30)-(32) applied inside each subdomain.  A subdomain is a column
 // tile of tile_x x tile_y cells over all layers (a well goes with the tile
 // of its first perforated cell); its local system is the owned rows plus
-// their graph neighbours (overlap 1).  Each subdomain maps to one thread
+// every row within graph distance 1 or 2 of them (the overlap, Table 9).  Each subdomain maps to one thread
 // block: the potential sort, the level sets of the reordered factors, the
 // factorisation and both triangular solves run level by level inside that
 // block.
@@ -76,13 +76,18 @@ void ras_build_static(sim_ls_s *ls) {
   int maxcells = 0;
   for (int s = 0; s < nsub; s++) {
     std::vector<int> list;
-    for (int g : own[s]) {
+    for (int g : own[s])
       if (!mark[g]) { mark[g] = 1; list.push_back(g); }
-      for (int q = ls->h_rp[g]; q < ls->h_rp[g + 1]; q++) {
-        int c = ls->h_ci[q];
-        if (!mark[c]) { mark[c] = 1; list.push_back(c); }
+    // rings of graph neighbours, one per level of overlap (1, or 2: Table 9)
+    int ov = ls->o.overlap == 2 ? 2 : 1;
+    for (int lev = 0, r0 = 0, r1 = (int)list.size(); lev < ov; lev++, r0 = r1, r1 = (int)list.size())
+      for (int a = r0; a < r1; a++) {
+        int g = list[a];
+        for (int q = ls->h_rp[g]; q < ls->h_rp[g + 1]; q++) {
+          int c = ls->h_ci[q];
+          if (!mark[c]) { mark[c] = 1; list.push_back(c); }
+        }
       }
-    }
     std::sort(list.begin(), list.end());      // cells ascending, then wells ascending
     int m = (int)list.size(), base = (int)ext.size(), nc = 0;
     for (int a = 0; a < m; a++) {

@@ -178,6 +178,9 @@ const char *rs_opts_invalid(const sim_options *o) {
   if (!(o->lin_tol >= 0.0 && o->lin_tol < HUGE_VAL)) return "lin_tol must be finite and >= 0";
   if (!(o->amg_theta >= 0.0 && o->amg_theta <= 1.0)) return "amg_theta must lie in [0, 1]";
   if (o->max_newton < 0 || o->max_cuts < 0 || o->amg_coarse_max < 0) return "negative iteration or size limit";
+  if (o->krylov != SIM_KRYLOV_FGMRES && o->krylov != SIM_KRYLOV_BICGSTAB) return "unknown Krylov method";
+  if (o->overlap != 1 && o->overlap != 2) return "RAS overlap must be 1 or 2";
+  if (o->interp != SIM_INTERP_DIRECT && o->interp != SIM_INTERP_EXTI) return "unknown AMG interpolation";
   return nullptr;
 }
 
@@ -190,6 +193,7 @@ rs_opts rs_opts_from(const sim_options *o) {
   r.theta = o->amg_theta; r.max_levels = o->amg_max_levels < 1 ? 1 : (o->amg_max_levels > 32 ? 32 : o->amg_max_levels);
   r.coarse_max = o->amg_coarse_max; r.seed = o->seed; r.max_cuts = o->max_cuts; r.dt = o->dt;
   r.sat_chop = o->sat_chop > 0.0 ? o->sat_chop : 0.0;
+  r.krylov = o->krylov; r.overlap = o->overlap; r.interp = o->interp;
   return r;
 }
 
@@ -198,4 +202,5 @@ extern "C" void sim_default_options(sim_options *o) {
   o->newton_tol = 1e-8; o->lin_tol = 1e-8; o->max_newton = 20; o->restart = 50; o->max_lin = 100;
   o->tile_x = 4; o->tile_y = 4; o->amg_theta = 0.25; o->amg_max_levels = 25; o->amg_coarse_max = 128;
   o->seed = 0x5EED; o->max_cuts = 6; o->dt = 1.0; o->cuda_stream = nullptr; o->sat_chop = 0.0;
+  o->krylov = SIM_KRYLOV_FGMRES; o->overlap = 1; o->interp = SIM_INTERP_DIRECT;
 }

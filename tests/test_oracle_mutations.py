@@ -164,7 +164,10 @@ MUTATIONS = [
     ("RAS: overlap rows written back (not restricted)", "or_solve.c",
      "    for (int b = 0; b < S->nown; b++) {\n      int g = S->own[b], a = S->opos[b];\n",
      "    for (int a = 0; a < m; a++) {\n      int g = S->ext[a];\n",
-     "test_oracle_solver", "test_ras_is_restricted_schwarz_with_exact_local_solves", {}),
+     "test_oracle_solver", "test_ras_is_restricted_schwarz_with_exact_local_solves", dict(overlap=1)),
+    ("RAS: overlap 2 builds a single ring", "or_solve.c",
+     "int m = 0, ov = ls->o.overlap == 2 ? 2 : 1;", "int m = 0, ov = 1;",
+     "test_oracle_solver", "test_subdomains_partition_and_overlap", dict(overlap=2)),
     ("GMRES: Givens rotation with the wrong sign", "or_solve.c",
      "h[k + 1] = -sn[k] * h[k] + cs[k] * h[k + 1];", "h[k + 1] = sn[k] * h[k] + cs[k] * h[k + 1];",
      "test_oracle_solver", "test_fgmres_iterations_equal_minimal_residual_gmres", dict(tile=(2, 2), coarse=8)),
@@ -208,6 +211,19 @@ MUTATIONS = [
     ("interpolation: weights with the wrong sign", "or_amg.c",
      "P->v[o++] = -(alpha * A->v[q]) / dg;", "P->v[o++] = (alpha * A->v[q]) / dg;",
      "test_oracle_solver", "test_interpolation_and_galerkin_product", dict(positive=False)),
+    ("extended+i: no distance-two points", "or_amg.c",
+     "      else for (int r = A->rp[j]; r < A->rp[j + 1]; r++) {\n        int l = A->ci[r];\n        if (S[r] && cf[l] == 1 && stamp[l] != i)",
+     "      else for (int r = A->rp[j]; r < A->rp[j]; r++) {\n        int l = A->ci[r];\n        if (S[r] && cf[l] == 1 && stamp[l] != i)",
+     "test_oracle_solver", "test_exti_reproduces_linear_interpolation_in_1d", {}),
+    ("extended+i: D_k without the coupling back to i", "or_amg.c",
+     "if (l == i || in_sorted(cs, m, l)) d = d + hat(akk, A->v[r]);", "if (in_sorted(cs, m, l)) d = d + hat(akk, A->v[r]);",
+     "test_oracle_solver", "test_exti_reproduces_linear_interpolation_in_1d", {}),
+    ("extended+i: distributes couplings of the diagonal's sign", "or_amg.c",
+     "  return akl < 0.0 ? akl : 0.0;\n}", "  return akl > 0.0 ? akl : 0.0;\n}",
+     "test_oracle_solver", "test_exti_reproduces_linear_interpolation_in_1d", {}),
+    ("extended+i: weak couplings not lumped into the diagonal", "or_amg.c",
+     "      } else if (!in_sorted(cs, m, j)) at = at + A->v[q];", "      }",
+     "test_oracle_solver", "test_exti_pattern_and_row_sums", dict(seed=1)),
     ("coarsest solve: LU without row exchanges", "or_amg.c",
      "if (fabs(a[(size_t)i * n + k]) > mx) {", "if (0) {",
      "test_oracle_solver", "test_coarsest_only_hierarchy_is_a_dense_solve", dict(permuted=True)),

@@ -218,12 +218,14 @@ def test_reordering_key_is_the_oil_potential(oracle_lib):
     assert np.abs(key - (p - rho_w * f.g * z * 1e-5)).max() > 1.0    # the phases differ by bars here
 
 
-def test_subdomains_partition_and_overlap(oracle_lib):
+@pytest.mark.parametrize("overlap", [1, 2])
+def test_subdomains_partition_and_overlap(oracle_lib, overlap):
     """Owned sets partition the unknowns; the extended set of each
-    subdomain is its owned rows plus their graph neighbours (overlap 1);
-    cells come in descending potential order and wells last (eq. 32)."""
+    subdomain is every row within graph distance `overlap` of its owned
+    rows (1, or 2 as in the paper's Table 9); cells come in descending
+    potential order and wells last (eq. 32)."""
     c = I.small_case(7, 5, 2, seed=13)
-    s = _system(oracle_lib, c, 70, tile_x=3, tile_y=2)
+    s = _system(oracle_lib, c, 70, tile_x=3, tile_y=2, overlap=overlap)
     s.ls.setup()
     rp, ci, val, b, key = s.ls.get()
     nb = c.n + 2
@@ -232,8 +234,8 @@ def test_subdomains_partition_and_overlap(oracle_lib):
         d = s.ls.sub(k)
         owned.extend(d["own"].tolist())
         nbrs = set(d["own"].tolist())
-        for g in d["own"]:
-            nbrs.update(ci[rp[g]:rp[g + 1]].tolist())
+        for _ in range(overlap):                       # breadth-first rings
+            nbrs = nbrs | {int(x) for g in nbrs for x in ci[rp[g]:rp[g + 1]]}
         assert set(d["ext"].tolist()) == nbrs
         cells = [g for g in d["ext"] if g < c.n]
         wells = [g for g in d["ext"] if g >= c.n]
@@ -244,17 +246,19 @@ def test_subdomains_partition_and_overlap(oracle_lib):
     assert s.ls.nsub == 3 * 3
 
 
-def test_ras_is_restricted_schwarz_with_exact_local_solves(oracle_lib):
+@pytest.mark.parametrize("overlap", [1, 2])
+def test_ras_is_restricted_schwarz_with_exact_local_solves(oracle_lib, overlap):
     """The RAS stage of Algorithm 2 is sum_s R~_s^T A_s^{-1} R_s: each
     subdomain solves on its extended rows and keeps only the rows it owns.
     On a heterogeneous 1D line in natural order every extended matrix is
     block tridiagonal, so BILU(0) is its exact LU, and the output at a
-    subdomain's owned unknowns equals a dense solve of its extended system."""
+    subdomain's owned unknowns equals a dense solve of its extended system
+    (overlap rows: `overlap` cells on each inner side)."""
     n = 40
     kk = np.exp(np.random.default_rng(3).normal(np.log(100.0), 1.0, n))
     c = I.Case("line", n, 1, 1, 10.0, 10.0, 10.0, 1000.0, kk, kk.copy(), kk.copy(),
                np.full(n, 0.2), I.Fluid(g=0.0), [], dt=1.0, n_steps=1)
-    s = _system(oracle_lib, c, 80, tile_x=4, tile_y=1, reorder=0)
+    s = _system(oracle_lib, c, 80, tile_x=4, tile_y=1, reorder=0, overlap=overlap)
     s.ls.setup()
     assert s.ls.nsub == 10
     rp, ci, val, b, key = s.ls.get()
@@ -265,7 +269,7 @@ def test_ras_is_restricted_schwarz_with_exact_local_solves(oracle_lib):
     for k in range(s.ls.nsub):
         d = s.ls.sub(k)
         ext = list(d["ext"])
-        assert len(ext) == len(d["own"]) + (k > 0) + (k < s.ls.nsub - 1)     # overlap 1
+        assert len(ext) == len(d["own"]) + overlap * ((k > 0) + (k < s.ls.nsub - 1))
         idx = np.array([2 * g + e for g in ext for e in (0, 1)])
         y = np.linalg.solve(J[np.ix_(idx, idx)], f[idx])
         for g in d["own"]:
@@ -559,3 +563,95 @@ def test_bicgstab_newton_run_matches_fgmres_run(oracle_lib):
         out.append(s.get_state())
     assert np.max(np.abs(out[1][0] - out[0][0]) / out[0][0]) < 1e-8
     assert np.max(np.abs(out[1][1] - out[0][1])) < 1e-8
+
+
+# ---- extended+i interpolation (the survey's stronger AMG option) ----
+def _lap1d(n):
+    """[-1 2 -1] with zero-row-sum (Neumann) ends, CSR."""
+    M = np.zeros((n, n))
+    for i in range(n):
+        if i > 0: M[i, i - 1] = -1.0
+        if i + 1 < n: M[i, i + 1] = -1.0
+        M[i, i] = -M[i].sum()
+    return M
+
+
+def test_exti_reproduces_linear_interpolation_in_1d(oracle_lib):
+    """On the 1D Laplacian with two F points between C points (C F F C F F C),
+    direct interpolation can only copy the one strong C neighbour, while
+    extended+i reaches the C point behind the strong F neighbour: the first
+    F point gets 2/3 and 1/3, the second 1/3 and 2/3 -- linear
+    interpolation, exact for the discrete harmonic functions of this
+    operator."""
+    M = _lap1d(7)
+    rp, ci, v = _csr(M)
+    cf = np.array([1, -1, -1, 1, -1, -1, 1], np.int8)
+    prp, pci, pv = oracle_lib.interpolation(rp, ci, v, cf, interp=1)
+    rows = {i: dict(zip(pci[prp[i]:prp[i + 1]].tolist(), pv[prp[i]:prp[i + 1]].tolist())) for i in range(7)}
+    assert rows[0] == {0: 1.0} and rows[3] == {1: 1.0} and rows[6] == {2: 1.0}
+    for i, (a, b) in ((1, (0, 1)), (2, (0, 1)), (4, (1, 2)), (5, (1, 2))):
+        near, far = (2 / 3, 1 / 3) if i in (1, 4) else (1 / 3, 2 / 3)
+        assert rows[i].keys() == {a, b}
+        assert rows[i][a] == pytest.approx(near, rel=1e-14) and rows[i][b] == pytest.approx(far, rel=1e-14)
+    # direct interpolation for comparison: one C point per F row
+    prp, pci, pv = oracle_lib.interpolation(rp, ci, v, cf, interp=0)
+    assert np.all(np.diff(prp)[[1, 2, 4, 5]] == 1)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_exti_pattern_and_row_sums(oracle_lib, seed):
+    """For the C/F split PMIS gives on a zero-row-sum M-matrix with weak and
+    strong couplings: the pattern of each F row of P is exactly its strong C
+    neighbours plus the strong C neighbours of its strong F neighbours, and
+    every such row sums to 1 (the interpolation preserves constants, the
+    near null space of the operator)."""
+    M = _random_mmatrix(60, seed)
+    M[np.diag_indices(60)] = 0.0
+    M[np.diag_indices(60)] = -M.sum(axis=1)
+    rp, ci, v = _csr(M)
+    amg = oracle_lib.AMG(rp, ci, v, coarse_max=4, interp=1)
+    lv = amg.level(0)
+    cf, S = lv["cf"], lv["strong"]
+    prp, pci, pv = oracle_lib.interpolation(rp, ci, v, cf, interp=1)
+    np.testing.assert_array_equal(prp, lv["prp"])
+    np.testing.assert_array_equal(pci, lv["pci"])
+    cidx = np.cumsum(cf == 1) - 1
+    n = 60
+    strong = [set() for _ in range(n)]
+    for i in range(n):
+        for q in range(rp[i], rp[i + 1]):
+            if S[q]:
+                strong[i].add(int(ci[q]))
+    for i in range(n):
+        got = set(pci[prp[i]:prp[i + 1]].tolist())
+        if cf[i] == 1:
+            assert got == {int(cidx[i])}
+            continue
+        want = {j for j in strong[i] if cf[j] == 1}
+        for k in strong[i]:
+            if cf[k] == -1:
+                want |= {j for j in strong[k] if cf[j] == 1}
+        assert got == {int(cidx[j]) for j in want}, i
+        if want:
+            assert pv[prp[i]:prp[i + 1]].sum() == pytest.approx(1.0, rel=1e-12)
+    assert any(len(set(pci[prp[i]:prp[i + 1]])) > sum(cf[j] == 1 for j in strong[i]) for i in range(n) if cf[i] == -1)
+
+
+def test_exti_vcycle_converges_faster_than_direct(oracle_lib):
+    """On the 3D Poisson problem the extended+i hierarchy's V-cycle reduces
+    the error faster than direct interpolation's (the reason the survey
+    lists it as the stronger option)."""
+    rates = {}
+    for interp in (0, 1):
+        M = _poisson3d(12)
+        rp, ci, v = _csr(M)
+        amg = oracle_lib.AMG(rp, ci, v, coarse_max=32, interp=interp)
+        n = M.shape[0]
+        x = np.random.default_rng(5).standard_normal(n)
+        e = x.copy()
+        for _ in range(8):
+            e_new = e - amg.apply(M @ e)
+            rate = np.linalg.norm(e_new) / np.linalg.norm(e)
+            e = e_new
+        rates[interp] = rate
+    assert rates[1] < rates[0] < 0.7, rates
