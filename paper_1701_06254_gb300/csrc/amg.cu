@@ -3,7 +3,8 @@
 // component; this library uses
 //   strength   S_i = { j != i : -a_ij >= theta * max_{k != i}(-a_ik) }
 //   coarsening PMIS with weights |S^T_i| + h(i), h = splitmix64 hash in [0,1)
-//   interpolation direct (positive off-diagonals lumped into the diagonal),
+//   interpolation direct (positive off-diagonals lumped into the diagonal)
+//                 or extended+i (distance two, option interp),
 //              R = P^T, Galerkin A_c = R (A P)
 //   cycle      V(1,1), l1-Jacobi smoothing, zero initial guess
 //   coarsest   dense inverse (FP64) from an LU with partial pivoting
@@ -200,6 +201,129 @@ __global__ void k_interp_fill(int n, const int *rp, const int *ci, const double 
   double dg = add_rn(aii, spos), alpha = div_rn(sneg, snegc);
   for (int q = rp[i]; q < rp[i + 1]; q++)
     if (S[q] && cf[ci[q]] == 1) { pci[o] = cidx[ci[q]]; pv[o++] = div_rn(-mul_rn(alpha, v[q]), dg); }
+}
+
+// --------------------------------------------- extended+i interpolation ---
+// De Sterck, Falgout, Nolting and Yang (2008).  For an F point i the
+// interpolatory set C^_i is its strong C neighbours plus the strong C
+// neighbours of its strong F neighbours k; with a^_kl the couplings of row k
+// of the sign opposite to a_kk and D_k = sum over l in C^_i + {i} of a^_kl,
+//   at_ii = a_ii + sum_{weak n not in C^_i} a_in + sum_k a_ik a^_ki / D_k
+//           (a_ik itself when D_k = 0),
+//   w_ij  = -(a_ij + sum_{k: D_k != 0, j in row k} a_ik a^_kj / D_k) / at_ii,
+// sums in row i's (and row k's) column order with round-to-nearest
+// operations, so the result equals a plain IEEE evaluation in that order.
+// One thread per row; rows of A have ascending columns.
+__device__ __forceinline__ double exti_hat(double akk, double akl) {
+  if (akk < 0.0) return akl > 0.0 ? akl : 0.0;
+  return akl < 0.0 ? akl : 0.0;
+}
+__device__ __forceinline__ int row_find(const int *ci, int a, int b, int col) {
+  while (a < b) {
+    int m = (a + b) >> 1, c = ci[m];
+    if (c == col) return m;
+    if (c < col) a = m + 1; else b = m;
+  }
+  return -1;
+}
+__device__ __forceinline__ bool in_list(const int *s, int m, int x) {
+  int lo = 0, hi = m;
+  while (lo < hi) { int md = (lo + hi) >> 1, v = s[md]; if (v == x) return true; if (v < x) lo = md + 1; else hi = md; }
+  return false;
+}
+// upper bound on |C^_i| (candidates before duplicates are removed)
+__global__ void k_exti_bound(int n, const int *rp, const int *ci, const uint8_t *S, const int8_t *cf, int *ub) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = 0;
+  if (cf[i] != 1)
+    for (int q = rp[i]; q < rp[i + 1]; q++) {
+      int j = ci[q];
+      if (!S[q] || j == i) continue;
+      if (cf[j] == 1) c++;
+      else for (int r = rp[j]; r < rp[j + 1]; r++) if (S[r] && cf[ci[r]] == 1) c++;
+    }
+  ub[i] = c;
+}
+// C^_i of each F row, sorted and without duplicates, in its segment of
+// cand (offsets uoff); len[i] = |C^_i| (1 for a C point)
+__global__ void k_exti_cands(int n, const int *rp, const int *ci, const uint8_t *S, const int8_t *cf, const int *uoff,
+                             int *cand, int *len) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (cf[i] == 1) { len[i] = 1; return; }
+  int *c = cand + uoff[i], m = 0;
+  for (int q = rp[i]; q < rp[i + 1]; q++) {
+    int j = ci[q];
+    if (!S[q] || j == i) continue;
+    if (cf[j] == 1) c[m++] = j;
+    else for (int r = rp[j]; r < rp[j + 1]; r++) if (S[r] && cf[ci[r]] == 1) c[m++] = ci[r];
+  }
+  for (int a = 1; a < m; a++) { int v = c[a], b = a - 1; while (b >= 0 && c[b] > v) { c[b + 1] = c[b]; b--; } c[b + 1] = v; }
+  int u = 0;
+  for (int a = 0; a < m; a++) if (u == 0 || c[a] != c[u - 1]) c[u++] = c[a];
+  len[i] = u;
+}
+// D_k for each strong F neighbour k of an F row, stored at k's position q in row i
+__global__ void k_exti_dk(int n, const int *rp, const int *ci, const double *v, const uint8_t *S, const int8_t *cf,
+                          const int *uoff, const int *cand, const int *prp, double *D) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || cf[i] == 1) return;
+  const int *cs = cand + uoff[i];
+  int m = prp[i + 1] - prp[i];
+  for (int q = rp[i]; q < rp[i + 1]; q++) {
+    int k = ci[q];
+    D[q] = 0.0;
+    if (!S[q] || k == i || cf[k] != -1) continue;
+    int dk = row_find(ci, rp[k], rp[k + 1], k);
+    double akk = dk >= 0 ? v[dk] : 0.0, d = 0.0;
+    for (int r = rp[k]; r < rp[k + 1]; r++) {
+      int l = ci[r];
+      if (l == i || in_list(cs, m, l)) d = add_rn(d, exti_hat(akk, v[r]));
+    }
+    D[q] = d;
+  }
+}
+__global__ void k_exti_fill(int n, const int *rp, const int *ci, const double *v, const uint8_t *S, const int8_t *cf,
+                            const int *cidx, const int *uoff, const int *cand, const double *D, const int *prp, int *pci,
+                            double *pv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int o = prp[i], m = prp[i + 1] - o;
+  if (cf[i] == 1) { pci[o] = cidx[i]; pv[o] = 1.0; return; }
+  if (m == 0) return;
+  const int *cs = cand + uoff[i];
+  int di = row_find(ci, rp[i], rp[i + 1], i);
+  double at = di >= 0 ? v[di] : 0.0;
+  for (int q = rp[i]; q < rp[i + 1]; q++) {
+    int j = ci[q];
+    if (j == i) continue;
+    if (S[q]) {
+      if (cf[j] == 1) continue;
+      if (D[q] == 0.0) at = add_rn(at, v[q]);
+      else {
+        int dk = row_find(ci, rp[j], rp[j + 1], j), ki = row_find(ci, rp[j], rp[j + 1], i);
+        double akk = dk >= 0 ? v[dk] : 0.0, aki = ki >= 0 ? v[ki] : 0.0;
+        at = add_rn(at, div_rn(mul_rn(v[q], exti_hat(akk, aki)), D[q]));
+      }
+    } else if (!in_list(cs, m, j)) at = add_rn(at, v[q]);
+  }
+  for (int a = 0; a < m; a++) {
+    int j = cs[a];
+    int qj = row_find(ci, rp[i], rp[i + 1], j);
+    double num = qj >= 0 ? v[qj] : 0.0;
+    for (int q = rp[i]; q < rp[i + 1]; q++) {
+      int k = ci[q];
+      if (!S[q] || k == i || cf[k] != -1 || D[q] == 0.0) continue;
+      int kj = row_find(ci, rp[k], rp[k + 1], j);
+      if (kj < 0) continue;
+      int dk = row_find(ci, rp[k], rp[k + 1], k);
+      double akk = dk >= 0 ? v[dk] : 0.0;
+      num = add_rn(num, div_rn(mul_rn(v[q], exti_hat(akk, v[kj])), D[q]));
+    }
+    pci[o + a] = cidx[j];
+    pv[o + a] = div_rn(-num, at);
+  }
 }
 
 // ------------------------------------------------------------ transpose ---
@@ -558,7 +682,11 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
     if (mixed) { L.f32.ensure(n); L.x32.ensure(n); L.r32.ensure(n); L.t32.ensure(n); }
     L.cf.ensure(n); L.strong.ensure(L.A.nnz); L.tpos.ensure(L.A.nnz);
     L.nc = 0; L.rounds = 0;
-    if (n <= o.coarse_max || l == o.max_levels - 1) { h.coarse_dense = 1; break; }
+    if (n <= o.coarse_max || l == o.max_levels - 1) {      // coarsest: no split (all marks 0)
+      RS_CUDA(cudaMemsetAsync(L.cf.p, 0, (size_t)n, s));
+      h.coarse_dense = 1;
+      break;
+    }
     rs_fill_i(h.flag.p, 0, 4 + 1025, s);
     if (L.A.nnz > 8LL * n) k_tpos_warp<<<grid_for((size_t)n * 32, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.tpos.p, h.flag.p + 1);
     else k_tpos<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.tpos.p, h.flag.p + 1);
@@ -614,14 +742,36 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
     // P
     L.P.n = n; L.P.m = nc;
     L.P.rp.ensure(n + 1);
-    k_interp_count<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, L.P.rp.p);
-    RS_LAUNCHED(1);
-    L.P.nnz = rs_scan(L.P.rp.p, L.P.rp.p, n, s);
-    RS_CUDA(cudaMemcpyAsync(L.P.rp.p + n, &L.P.nnz, sizeof(int), cudaMemcpyHostToDevice, s));
-    L.P.ci.ensure(L.P.nnz); L.P.v.ensure(L.P.nnz);
-    k_interp_fill<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, L.strong.p, L.cf.p, scratch.p,
-                                                   L.P.rp.p, L.P.ci.p, L.P.v.p);
-    RS_LAUNCHED(1);
+    if (o.interp == SIM_INTERP_EXTI) {
+      static thread_local dbuf<int> uoff, cand;
+      static thread_local dbuf<double> dk;
+      uoff.ensure(n + 1);
+      k_exti_bound<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, uoff.p);
+      RS_LAUNCHED(1);
+      int ncand = rs_scan(uoff.p, uoff.p, n, s);
+      cand.ensure(ncand > 0 ? ncand : 1);
+      k_exti_cands<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, uoff.p, cand.p,
+                                                    L.P.rp.p);
+      RS_LAUNCHED(1);
+      L.P.nnz = rs_scan(L.P.rp.p, L.P.rp.p, n, s);
+      RS_CUDA(cudaMemcpyAsync(L.P.rp.p + n, &L.P.nnz, sizeof(int), cudaMemcpyHostToDevice, s));
+      L.P.ci.ensure(L.P.nnz); L.P.v.ensure(L.P.nnz);
+      dk.ensure(L.A.nnz > 0 ? L.A.nnz : 1);
+      k_exti_dk<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, L.strong.p, L.cf.p, uoff.p, cand.p,
+                                                 L.P.rp.p, dk.p);
+      k_exti_fill<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, L.strong.p, L.cf.p, scratch.p,
+                                                   uoff.p, cand.p, dk.p, L.P.rp.p, L.P.ci.p, L.P.v.p);
+      RS_LAUNCHED(2);
+    } else {
+      k_interp_count<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, L.P.rp.p);
+      RS_LAUNCHED(1);
+      L.P.nnz = rs_scan(L.P.rp.p, L.P.rp.p, n, s);
+      RS_CUDA(cudaMemcpyAsync(L.P.rp.p + n, &L.P.nnz, sizeof(int), cudaMemcpyHostToDevice, s));
+      L.P.ci.ensure(L.P.nnz); L.P.v.ensure(L.P.nnz);
+      k_interp_fill<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, L.strong.p, L.cf.p, scratch.p,
+                                                     L.P.rp.p, L.P.ci.p, L.P.v.p);
+      RS_LAUNCHED(1);
+    }
     // R = P^T
     L.R.n = nc; L.R.m = n; L.R.nnz = L.P.nnz;
     L.R.rp.ensure(nc + 1); L.R.ci.ensure(L.P.nnz); L.R.v.ensure(L.P.nnz);

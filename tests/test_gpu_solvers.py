@@ -83,3 +83,59 @@ def test_whole_run_inexact_newton_bicgstab():
     c.newton = "inexact"
     _run_compare(c, 3, krylov=R.KRYLOV_BICGSTAB, max_lin=300, newton=1, precision=R.PREC_MIXED_BF16,
                  decoupling=R.DEC_QI)
+
+
+@pytest.mark.parametrize("mk", [lambda: I.small_case(6, 5, 3, seed=21), lambda: I.small_case(11, 7, 4, seed=22)])
+def test_overlap_two_matches_oracle(mk):
+    """RAS with overlap 2 (the paper's Table 9): each subdomain's rows in
+    reordered order and its ILU level sets bit for bit, RAS and CPR
+    applications to 1e-10 (FP64), FGMRES iterations within one."""
+    c = mk()
+    o, gl = _shared(c, 320, overlap=2, tile_x=3, tile_y=2)
+    o.ls.setup(); gl.setup()
+    assert gl.ras_count() == o.ls.nsub
+    for s in range(o.ls.nsub):
+        np.testing.assert_array_equal(gl.ras_ext(s), o.ls.sub(s)["ext"])
+    x = np.random.default_rng(32).standard_normal(2 * (c.n + len(c.wells)))
+    for op, fo in ((R.OP_RAS, o.ls.ras), (R.OP_CPR, o.ls.cpr)):
+        yg, yo = gl.apply(op, x), fo(x)
+        assert np.abs(yg - yo).max() <= 1e-10 * np.abs(yo).max(), op
+    rco, yo, itso, _ = o.ls.solve(1e-10)
+    yg, itsg, relg = gl.solve(1e-10)
+    assert rco == 0 and relg <= 1e-10 and abs(itsg - itso) <= 1
+
+
+@pytest.mark.parametrize("mk", [lambda: I.small_case(11, 7, 4, seed=22), lambda: I.case2(nx=30, ny=26, nz=6)])
+def test_extended_i_hierarchy_is_bit_exact(mk):
+    """Extended+i interpolation on shared FP64 input: every AMG level's
+    operator, C/F split and interpolation (pattern and values) bit for bit,
+    the V-cycle to 1e-10, and FGMRES iterations within one."""
+    c = mk()
+    o, gl = _shared(c, 330, interp=R.INTERP_EXTI, decoupling=R.DEC_QI, amg_coarse_max=16)
+    o.ls.setup(); gl.setup()
+    oa = o.ls.amg()
+    assert gl.amg_nlev() == oa.nlev and oa.nlev >= 3
+    for l in range(oa.nlev):
+        gd, od = gl.amg_level(l), oa.level(l)
+        np.testing.assert_array_equal(gd["rp"], od["rp"])
+        np.testing.assert_array_equal(gd["ci"], od["ci"])
+        np.testing.assert_array_equal(gd["v"], od["v"])
+        np.testing.assert_array_equal(gd["cf"], od["cf"])
+        if l < oa.nlev - 1:
+            np.testing.assert_array_equal(gd["prp"], od["prp"])
+            np.testing.assert_array_equal(gd["pci"], od["pci"])
+            np.testing.assert_array_equal(gd["pv"], od["pv"])
+    f = np.random.default_rng(33).standard_normal(c.n)
+    yg, yo = gl.apply(R.OP_VCYCLE, f), oa.apply(f)
+    assert np.abs(yg - yo).max() <= 1e-10 * np.abs(yo).max()
+    rco, yo, itso, _ = o.ls.solve(1e-10)
+    yg, itsg, relg = gl.solve(1e-10)
+    assert rco == 0 and relg <= 1e-10 and abs(itsg - itso) <= 1
+
+
+@pytest.mark.parametrize("prec", [R.PREC_FP64, R.PREC_MIXED_BF16], ids=["fp64", "bf16"])
+def test_whole_run_overlap_two_extended_i(prec):
+    """The channelised physics at 42x38x8 with overlap-2 RAS and extended+i
+    AMG together, QI decoupling: three 10-day steps against the oracle."""
+    c = I.case2(nx=42, ny=38, nz=8)
+    _run_compare(c, 3, overlap=2, interp=R.INTERP_EXTI, decoupling=R.DEC_QI, precision=prec)
