@@ -33,11 +33,19 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-timesteps/s at 1M cells, relres 1e-6: mixed+learned vs plain FP64; %HBM peak"
 # decoupling codes, the same in the CUDA library (SIM_DEC_*) and the oracle
 DECOUPLING = {"none": 0, "abf": 1, "qi": 2}
+KRYLOV = {"fgmres": 0, "bicgstab": 1}
+INTERP = {"direct": 0, "exti": 1}
+NEWTON = {"standard": 0, "inexact": 1}
 
 
 def oracle_opts(args):
     """The oracle's options for the configuration the GPU arm runs."""
-    return dict(max_lin=args.max_lin, decoupling=DECOUPLING[args.decoupling], reorder=0 if args.no_reorder else 1)
+    tx, ty = (int(v) for v in args.tile.split("x"))
+    o = dict(max_lin=args.max_lin, decoupling=DECOUPLING[args.decoupling], reorder=0 if args.no_reorder else 1,
+             tile_x=tx, tile_y=ty, krylov=KRYLOV[args.krylov], overlap=args.overlap, interp=INTERP[args.interp])
+    if args.newton:
+        o["newton"] = NEWTON[args.newton]
+    return o
 
 
 UNIT = "cell-timesteps/s"
@@ -126,9 +134,15 @@ def ras_bytes(ls, precision):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
-# ncu capture summarised in profiles/ (null once the kernel changes)
-NCU_TRAFFIC = {("ras", "mixed_bf16"): 167.8e6, ("spmv_prec", "mixed_bf16"): 164.3e6,
-               ("spmv64", "mixed_bf16"): 273.4e6}
+# ncu captures summarised in profiles/, keyed by (kernel family, precision,
+# decoupling): a capture is quoted only for the configuration it was taken in
+# (null otherwise, and null once the kernel changes)
+NCU_TRAFFIC = {("ras", "mixed_bf16", "abf"): 167.8e6, ("spmv_prec", "mixed_bf16", "abf"): 164.3e6,
+               ("spmv64", "mixed_bf16", "abf"): 273.4e6}
+
+
+def ncu_traffic(kernel, args):
+    return NCU_TRAFFIC.get((kernel, args.precision, args.decoupling))
 
 
 def spmv_bytes(nb, nnzb, val_b, x_b, f_b, y_b):
@@ -176,6 +190,22 @@ def _host_state(sim):
         return np.array(p), np.array(sw)
     except Exception:
         return None
+
+
+def oracle_timed_step(case, opts, state, omp):
+    """One time step of the CPU oracle from a given state (p, s_w, p_b, t):
+    the same step the GPU arm times first, on one core (omp=False) or with
+    the OpenMP build on all host cores (bit-identical results).  Returns
+    (seconds, Newton iterations, FGMRES iterations, return code)."""
+    import oracle
+    s = oracle.Sim(case, omp=omp, **opts)
+    p, sw, pb, t = state
+    s.set_state(np.asarray(p, np.float64), np.asarray(sw, np.float64), np.asarray(pb, np.float64), t)
+    t0 = time.perf_counter()
+    rc = s.advance(1)
+    t1 = time.perf_counter()
+    st = s.stats()
+    return t1 - t0, st["newton"], st["lin"], rc
 
 
 def oracle_newton_iteration(case, opts):
@@ -441,6 +471,16 @@ def main():
                     help="decoupling of the Newton system (eq. 29): Quasi-IMPES (default, with the potential "
                          "reordering the paper's configuration for its SPE10 runs), ABF or none")
     ap.add_argument("--no-reorder", action="store_true", help="switch off the local potential reordering")
+    ap.add_argument("--krylov", default="fgmres", choices=["fgmres", "bicgstab"],
+                    help="Krylov method: FGMRES(50) (default) or BiCGSTAB, both right-preconditioned by CPR")
+    ap.add_argument("--newton", default=None, choices=["standard", "inexact"],
+                    help="Newton variant (default: the workload's own; the 1M-cell case runs standard Newton "
+                         "at relres 1e-6)")
+    ap.add_argument("--overlap", type=int, default=1, choices=[1, 2], help="RAS overlap")
+    ap.add_argument("--interp", default="direct", choices=["direct", "exti"], help="AMG interpolation")
+    ap.add_argument("--fp64-basis", action="store_true",
+                    help="mixed precision with the FGMRES basis, w = A z and Gram-Schmidt in FP64 instead of "
+                         "double-float")
     ap.add_argument("--roofline", default="ras", choices=["ras", "spmv64", "spmv_prec"])
     ap.add_argument("--workload", default="single", choices=["single", "ensemble"],
                     help="single: the 1M-cell case; ensemble: --members independent models advanced together")
@@ -485,7 +525,10 @@ def main():
     tx, ty = (int(v) for v in args.tile.split("x"))
     opts = dict(precision=prec, max_lin=args.max_lin, tile_x=tx, tile_y=ty,
                 decoupling=DECOUPLING[args.decoupling],
-                reorder=0 if args.no_reorder else 1)
+                reorder=0 if args.no_reorder else 1, krylov=KRYLOV[args.krylov], overlap=args.overlap,
+                interp=INTERP[args.interp], fp64_basis=1 if args.fp64_basis else 0)
+    if args.newton:
+        opts["newton"] = NEWTON[args.newton]
     ws_info = False
     ws = None
     if args.learned:
@@ -504,7 +547,7 @@ def main():
     # the state the timed steps start from, so that the end-to-end pass below
     # replays exactly the same steps
     saved = None
-    if not args.no_e2e:
+    if not (args.no_e2e and args.no_cpu_baseline):
         nw = len(case.wells)
         saved = (torch.empty(case.n, dtype=torch.float64, pin_memory=True),
                  torch.empty(case.n, dtype=torch.float64, pin_memory=True),
@@ -562,7 +605,7 @@ def main():
     peak, src = peaks()
     achieved = bpl / (kms / nk * 1e-3) / 1e9 if nk else 0.0
     roof = {"kernel": args.roofline, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": src, "traffic": NCU_TRAFFIC.get((args.roofline, args.precision)),
+            "frac": achieved / peak, "peak_source": src, "traffic": ncu_traffic(args.roofline, args),
             "launches": nk,
             "ms_per_launch": kms / nk if nk else None, "algorithmic_bytes_per_launch": bpl}
 
@@ -580,10 +623,10 @@ def main():
         for name, f, b in others:
             n_, t_ = sim.ls.kernel_time(f)
             ach = b / (t_ / n_ * 1e-3) / 1e9 if n_ else 0.0
-            key = {"spmv_prec": "spmv_prec", "spmv_w": "spmv64"}.get(name)
+            key = {"spmv_prec": "spmv_prec", "spmv_w": "spmv64", "vcycle": "vcycle"}.get(name)
             rooflines[name] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                                "ms_per_launch": t_ / n_ if n_ else None, "algorithmic_bytes_per_launch": b,
-                               "launches": n_, "traffic": NCU_TRAFFIC.get((key, args.precision))}
+                               "launches": n_, "traffic": ncu_traffic(key, args)}
         sim.ls.kernel_timer(fams)
 
     # end to end through the public API with host buffers
@@ -618,28 +661,49 @@ def main():
         lv = measure_variant(R, torch, case, opts, args, ws)
         lv["training"] = info
         variants[args.precision + "_learned"] = lv
+        if prec != R.PREC_FP64:
+            # the precision split as first specified: FP32/BF16 preconditioner,
+            # FGMRES basis, w = A z and Gram-Schmidt in FP64
+            variants[args.precision + "_fp64_basis"] = measure_variant(R, torch, case, dict(opts, fp64_basis=1), args)
+        # the paper's other solver settings on the same workload: inexact Newton
+        # (eq. 26, Eisenstat-Walker forcing) and BiCGSTAB (Tables 2, 3, 6);
+        # RAS overlap 2 (Table 9) with extended+i AMG
+        variants["inexact_newton"] = measure_variant(R, torch, case, dict(opts, newton=1), args)
+        variants["bicgstab"] = measure_variant(R, torch, case, dict(opts, krylov=1, max_lin=300), args)
+        variants["overlap2_exti"] = measure_variant(R, torch, case, dict(opts, overlap=2, interp=1), args)
     precision_error = None
     if variants is not None:
-        ref = variants["plain_fp64"].pop("_state", None)
-        learned = variants[args.precision + "_learned"].pop("_state", None)
+        states = {k: v.pop("_state", None) for k, v in variants.items()}
+        ref = states.pop("plain_fp64", None)
         try:
             if ref is not None and end_state is not None:
                 precision_error = {
                     "reference": "the plain FP64 GPU method over the same warm-up and timed steps "
                                  "(it matches the FP64 oracle to 1e-6 in the parity tests)",
                     args.precision: state_difference(end_state, ref)}
-                if learned is not None:
-                    precision_error[args.precision + "_learned"] = state_difference(learned, ref)
+                for k, st_ in states.items():
+                    if st_ is not None:
+                        precision_error[k] = state_difference(st_, ref)
         except Exception as e:                # reported, never fatal
             precision_error = {"error": str(e)[:200]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_it, its = oracle_newton_iteration(case, oracle_opts(args))
-        cpu = {"value": case.n / (t_it * max(newton_per_step, 1.0)), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one Newton iteration of the first time step of {case.name} by the FP64 CPU oracle "
-                         f"(assembly + setup + {its} FGMRES iterations, {t_it:.1f} s), scaled by the GPU run's "
-                         f"{newton_per_step:.2f} Newton iterations per step"}
+        # the first timed step, re-seeded: the oracle starts from the GPU's
+        # state at the start of the timed region and advances the same step,
+        # once on one core and once with its OpenMP build on all host cores
+        import oracle
+        state = (saved[0].numpy(), saved[1].numpy(), saved[2].numpy()[:len(case.wells)], t_saved)
+        t1c, nn1, li1, rc1 = oracle_timed_step(case, oracle_opts(args), state, omp=False)
+        tac, nna, lia, rca = oracle_timed_step(case, oracle_opts(args), state, omp=True)
+        thr = oracle.omp_threads()
+        cpu = {"value": case.n / t1c, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the first timed step of {case.name} (t = {t_saved:g} d, dt = {case.dt:g} d) re-seeded from "
+                         f"the GPU state at the start of the timed region: {nn1} Newton and {li1} FGMRES iterations, "
+                         f"{t1c:.1f} s on one core (rc {rc1})",
+               "all_cores": {"value": case.n / tac, "cores": thr, "nproc": os.cpu_count(), "seconds": tac,
+                             "newton": nna, "linear_its": lia, "rc": rca,
+                             "build": "OpenMP on the oracle's element-wise loops (bit-identical results)"}}
 
     if rank == 0:
         line = {
@@ -648,6 +712,9 @@ def main():
             "vs_baseline": None, "dtype": {"mixed": "f64+f32", "mixed_bf16": "f64+f32+bf16", "fp64": "f64"}[args.precision], "data": "synthetic",
             "config": {"workload": case.name, "cells": case.n, "wells": len(case.wells), "dt_days": case.dt,
                        "relres": case.lin_tol, "precision": args.precision, "learned_warm_start": ws_info,
+                       "krylov": {"method": args.krylov,
+                                  "basis": "fp64" if (args.precision == "fp64" or args.fp64_basis) else "double-float"},
+                       "newton": args.newton or case.newton, "ras_overlap": args.overlap, "amg_interp": args.interp,
                        "ras_tile": args.tile, "decoupling": args.decoupling, "reorder": not args.no_reorder,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "working set larger than L2 (no flush needed)",

@@ -136,6 +136,9 @@ typedef struct {
   int krylov;          /* SIM_KRYLOV_FGMRES or SIM_KRYLOV_BICGSTAB                 */
   int overlap;         /* RAS overlap in the matrix graph: 1 or 2 (Table 9)        */
   int interp;          /* SIM_INTERP_DIRECT or SIM_INTERP_EXTI                     */
+  int fp64_basis;      /* mixed precision only: 1 keeps the FGMRES basis, w = A z
+                          and Gram-Schmidt in FP64; 0 (default) holds them in
+                          double-float (hi + lo FP32, ~48-bit significand)     */
 } sim_options;
 
 /* Statistics, cumulative since creation. */
@@ -155,7 +158,8 @@ typedef struct sim_ls_s *sim_ls_t;
 /* Fill *o with the defaults: FP64, ABF, reordering on, standard Newton,
  * newton_tol 1e-8, lin_tol 1e-8, max_newton 20, restart 50, max_lin 100,
  * 4x4 tiles, theta 0.25, 25 levels, coarsest <= 128 rows, 6 cuts, dt 1,
- * no saturation chop, FGMRES, overlap 1, direct interpolation. */
+ * no saturation chop, FGMRES, overlap 1, direct interpolation, double-float
+ * basis in mixed precision. */
 void sim_default_options(sim_options *o);
 
 /* Create a simulator (copies everything).  Builds transmissibilities,

@@ -18,7 +18,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = ["or_model.c", "or_solve.c", "or_amg.c"]
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
+_LIB_OMP = os.path.join(_LIBDIR, "liboracle_omp.so")
 _lib = None
+_lib_omp = None
 
 DEFAULT_OPTS = dict(decoupling=1, reorder=1, newton=0, newton_tol=1e-8, lin_tol=1e-8,
                     max_newton=20, restart=50, max_lin=100, tile_x=4, tile_y=4,
@@ -26,26 +28,30 @@ DEFAULT_OPTS = dict(decoupling=1, reorder=1, newton=0, newton_tol=1e-8, lin_tol=
                     seed=0x5EED, max_cuts=6, dt=1.0, sat_chop=0.0, krylov=0, overlap=1, interp=0)
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, omp: bool = False) -> str:
     """Compile the oracle into oracle/_lib/liboracle.so (gcc, -O2,
-    -ffp-contract=off so that no multiply-add is fused)."""
+    -ffp-contract=off so that no multiply-add is fused); omp=True builds
+    liboracle_omp.so, the same sources with OpenMP on the loops that write
+    disjoint outputs (bit-identical results, for timing on all cores)."""
+    out = _LIB_OMP if omp else _LIB
     srcs = [os.path.join(_HERE, s) for s in _SRC] + [os.path.join(_HERE, "or_internal.h")]
-    if not force and os.path.exists(_LIB):
-        t = os.path.getmtime(_LIB)
+    if not force and os.path.exists(out):
+        t = os.path.getmtime(out)
         if all(os.path.getmtime(s) <= t for s in srcs):
-            return _LIB
+            return out
     os.makedirs(_LIBDIR, exist_ok=True)
-    tmp = _LIB + f".tmp{os.getpid()}"
-    compile_sources(_HERE, tmp)
-    os.replace(tmp, _LIB)
-    return _LIB
+    tmp = out + f".tmp{os.getpid()}"
+    compile_sources(_HERE, tmp, omp=omp)
+    os.replace(tmp, out)
+    return out
 
 
-def compile_sources(src_dir: str, out: str) -> None:
+def compile_sources(src_dir: str, out: str, omp: bool = False) -> None:
     """gcc the oracle's C files found in src_dir into the shared library out
     (also used by the tests that build a copy with a planted mistake)."""
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=gnu11", "-fPIC", "-shared",
-           "-o", out] + [os.path.join(src_dir, s) for s in _SRC] + ["-lm"]
+           "-Wno-unknown-pragmas"] + (["-fopenmp"] if omp else []) + \
+        ["-o", out] + [os.path.join(src_dir, s) for s in _SRC] + ["-lm"]
     subprocess.run(cmd, check=True)
 
 
@@ -147,8 +153,15 @@ def _sig(lib):
         f.argtypes = args
 
 
-def lib():
-    global _lib
+def lib(omp: bool = False):
+    """The oracle library; omp=True the OpenMP build (same results)."""
+    global _lib, _lib_omp
+    if omp:
+        if _lib_omp is None:
+            build(omp=True)
+            _lib_omp = C.CDLL(_LIB_OMP)
+            _sig(_lib_omp)
+        return _lib_omp
     if _lib is None:
         build()
         _lib = C.CDLL(_LIB)
@@ -162,6 +175,15 @@ def _d(a):
 
 def _i(a):
     return a.ctypes.data_as(_ip)
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP build of the oracle runs its parallel loops on."""
+    lib(omp=True)
+    try:
+        return int(C.CDLL("libgomp.so.1").omp_get_max_threads())
+    except OSError:
+        return os.cpu_count() or 1
 
 
 def potential_order(key, idx=None):
@@ -277,9 +299,9 @@ class LinearSystem:
         self._fill_sizes()
 
     @classmethod
-    def _wrap(cls, handle, owner):
+    def _wrap(cls, handle, owner, library=None):
         self = cls.__new__(cls)
-        self._lib = lib(); self.h = handle; self._own = False; self._owner = owner
+        self._lib = library or lib(); self.h = handle; self._own = False; self._owner = owner
         self._fill_sizes()
         return self
 
@@ -368,8 +390,8 @@ def _case_structs(case):
 class Sim:
     """The oracle simulator for one Case."""
 
-    def __init__(self, case, **opts):
-        self._lib = lib()
+    def __init__(self, case, omp=False, **opts):
+        self._lib = lib(omp)
         self.case = case
         o = dict(newton=0 if case.newton == "standard" else 1, newton_tol=case.newton_tol,
                  lin_tol=case.lin_tol, dt=case.dt, sat_chop=case.sat_chop)
@@ -381,7 +403,7 @@ class Sim:
         self.h = self._lib.or_sim_create(C.byref(g), *(_d(a) for a in self._k), C.byref(fl), wells,
                                          len(case.wells), C.byref(self.opts))
         self.n, self.nw = case.n, len(case.wells)
-        self.ls = LinearSystem._wrap(self._lib.or_sim_lsys(self.h), self)
+        self.ls = LinearSystem._wrap(self._lib.or_sim_lsys(self.h), self, self._lib)
 
     def __del__(self):
         if getattr(self, "h", None):

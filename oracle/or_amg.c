@@ -423,6 +423,7 @@ int or_amg_setup(or_amg *h, const or_csr *A0, double theta, uint64_t seed, int c
 
 static void csr_mv(const or_csr *A, const double *x, double *y)
 {
+  #pragma omp parallel for schedule(static)
   for (int i = 0; i < A->n; i++) { double s = 0.0; for (int q = A->rp[i]; q < A->rp[i + 1]; q++) s += A->v[q] * x[A->ci[q]]; y[i] = s; }
 }
 

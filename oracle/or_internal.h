@@ -6,6 +6,10 @@
  * (arXiv 1701.06254).  Only the test suite, __graft_entry__.smoke() and the
  * CPU-baseline leg of bench.py load it.  It shares no code with the CUDA
  * library.  Built with -O2 -ffp-contract=off: every a*b+c rounds twice.
+ * A second build with -fopenmp (liboracle_omp.so, for timing the oracle on
+ * all host cores) runs the loops marked "omp parallel for" on several
+ * threads: each of those writes disjoint outputs and sums nothing across
+ * iterations, so both builds give bit-identical results.
  */
 #ifndef OR_INTERNAL_H
 #define OR_INTERNAL_H

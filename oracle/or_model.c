@@ -369,8 +369,10 @@ void or_sim_assemble(or_sim *S)
   double *R = xc(2 * (size_t)ls->nb, 8);
   memset(ls->val, 0, 32 * (size_t)ls->nnzb);
   props_t *P = xc(n, sizeof(props_t));
+  #pragma omp parallel for schedule(static)
   for (int c = 0; c < n; c++) cell_props(S, c, S->p[c], S->s[c], &P[c]);
   /* accumulation: (V/dt)[(phi rho s)^{n+1} - (phi rho s)^n] */
+  #pragma omp parallel for schedule(static)
   for (int c = 0; c < n; c++) {
     double vt = S->vol[c] / S->dt, sw = S->s[c], so = 1.0 - sw;
     double *J = &ls->val[4 * (size_t)bpos(ls, c, c)];

@@ -60,6 +60,7 @@ void or_lsys_free(or_lsys *ls)
 /* y = A x over the 2x2 block system */
 void or_bsr_mv(const or_lsys *ls, const double *x, double *y)
 {
+  #pragma omp parallel for schedule(static)
   for (int i = 0; i < ls->nb; i++) {
     double y0 = 0, y1 = 0;
     for (int q = ls->rp[i]; q < ls->rp[i + 1]; q++) {
@@ -291,6 +292,7 @@ static void bilu0(or_sub *S)
    factors and writes back only the unknowns it owns (restricted). */
 void or_ras_apply(const or_lsys *ls, const double *f, double *x)
 {
+  #pragma omp parallel for schedule(dynamic, 4)
   for (int s = 0; s < ls->nsub; s++) {
     const or_sub *S = &ls->sub[s];
     int m = S->next;
@@ -328,6 +330,7 @@ int or_lsys_setup(or_lsys *ls)
   else if (ls->o.decoupling == OR_DEC_QI) quasi_impes(ls);
   else for (int i = 0; i < ls->nb; i++) { double *D = &ls->dmat[4 * (size_t)i]; D[0] = 1; D[1] = 0; D[2] = 0; D[3] = 1; }
   build_subs(ls);
+  #pragma omp parallel for schedule(dynamic, 4)
   for (int s = 0; s < ls->nsub; s++) bilu0(&ls->sub[s]);
   /* pressure block A_pp: entry [0][0] of every cell-cell block (eq. 34 restricts to cell pressures) */
   or_csr A; A.n = A.m = ls->n;

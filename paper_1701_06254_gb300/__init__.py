@@ -68,7 +68,8 @@ class Options(C.Structure):
                 ("restart", C.c_int), ("max_lin", C.c_int), ("tile_x", C.c_int), ("tile_y", C.c_int),
                 ("amg_theta", C.c_double), ("amg_max_levels", C.c_int), ("amg_coarse_max", C.c_int),
                 ("seed", C.c_uint64), ("max_cuts", C.c_int), ("dt", C.c_double), ("cuda_stream", C.c_void_p),
-                ("sat_chop", C.c_double), ("krylov", C.c_int), ("overlap", C.c_int), ("interp", C.c_int)]
+                ("sat_chop", C.c_double), ("krylov", C.c_int), ("overlap", C.c_int), ("interp", C.c_int),
+                ("fp64_basis", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -206,7 +207,7 @@ def launch_count():
 
 OPT_KEYS = ("precision", "decoupling", "reorder", "newton", "newton_tol", "lin_tol", "max_newton", "restart",
             "max_lin", "tile_x", "tile_y", "amg_theta", "amg_max_levels", "amg_coarse_max", "seed", "max_cuts", "dt",
-            "sat_chop", "krylov", "overlap", "interp")
+            "sat_chop", "krylov", "overlap", "interp", "fp64_basis")
 
 
 def make_options(stream=None, **kw):

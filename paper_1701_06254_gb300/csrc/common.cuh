@@ -97,7 +97,7 @@ struct rs_opts {
   uint64_t seed;
   int max_cuts;
   double dt, sat_chop;
-  int krylov, overlap, interp;
+  int krylov, overlap, interp, fp64_basis;
 };
 const char *rs_opts_invalid(const sim_options *o);
 rs_opts rs_opts_from(const sim_options *o);

@@ -1112,7 +1112,7 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
   // df: double-float Arnoldi basis (its kernels use 32-bit offsets into the
   // 2 (m + 1) nu floats of the basis; larger systems keep the FP64 basis)
   bool mixed = ls->o.precision != SIM_PREC_FP64;
-  bool df = mixed && 2.0 * (m + 1) * (double)nu < 2147483647.0;
+  bool df = mixed && !ls->o.fp64_basis && 2.0 * (m + 1) * (double)nu < 2147483647.0;
   ls->V.ensure((size_t)(m + 1) * nu);
   if (mixed) ls->Z32.ensure((size_t)m * nu); else ls->Z.ensure((size_t)m * nu);
   int chd = 0, nblk = df ? ortho_blocks_df(nu, &chd) : ortho_blocks(nu);

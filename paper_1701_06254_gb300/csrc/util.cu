@@ -193,7 +193,7 @@ rs_opts rs_opts_from(const sim_options *o) {
   r.theta = o->amg_theta; r.max_levels = o->amg_max_levels < 1 ? 1 : (o->amg_max_levels > 32 ? 32 : o->amg_max_levels);
   r.coarse_max = o->amg_coarse_max; r.seed = o->seed; r.max_cuts = o->max_cuts; r.dt = o->dt;
   r.sat_chop = o->sat_chop > 0.0 ? o->sat_chop : 0.0;
-  r.krylov = o->krylov; r.overlap = o->overlap; r.interp = o->interp;
+  r.krylov = o->krylov; r.overlap = o->overlap; r.interp = o->interp; r.fp64_basis = o->fp64_basis != 0;
   return r;
 }
 
@@ -202,5 +202,5 @@ extern "C" void sim_default_options(sim_options *o) {
   o->newton_tol = 1e-8; o->lin_tol = 1e-8; o->max_newton = 20; o->restart = 50; o->max_lin = 100;
   o->tile_x = 4; o->tile_y = 4; o->amg_theta = 0.25; o->amg_max_levels = 25; o->amg_coarse_max = 128;
   o->seed = 0x5EED; o->max_cuts = 6; o->dt = 1.0; o->cuda_stream = nullptr; o->sat_chop = 0.0;
-  o->krylov = SIM_KRYLOV_FGMRES; o->overlap = 1; o->interp = SIM_INTERP_DIRECT;
+  o->krylov = SIM_KRYLOV_FGMRES; o->overlap = 1; o->interp = SIM_INTERP_DIRECT; o->fp64_basis = 0;
 }

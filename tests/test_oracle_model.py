@@ -526,3 +526,18 @@ def test_newton_measure_water_rate_row(oracle_lib):
     cell = qw * 1.0 / (fl.rho_ref[0] * dx * dx * dz * 0.23)
     assert cell < 1e-6                                  # ... the cell row does not
     assert s.residual_norm() == pytest.approx(expect, rel=1e-12)
+
+
+def test_openmp_build_gives_identical_results(oracle_lib):
+    """The OpenMP build of the oracle (used only to time it on all host
+    cores) parallelises loops that write disjoint outputs and sum nothing
+    across iterations, so two time steps give bit-identical states."""
+    c = I.small_case(9, 8, 3, seed=17)
+    out = []
+    for omp in (False, True):
+        s = oracle_lib.Sim(c, omp=omp)
+        s.init_hydrostatic()
+        assert s.advance(2) == 0
+        out.append(s.get_state())
+    for a, b in zip(out[0][:3], out[1][:3]):
+        np.testing.assert_array_equal(a, b)
