@@ -173,12 +173,15 @@ struct ras_data {
   dbuf<int> nlev;               // per subdomain: #L levels, #U levels
   dbuf<int> lvl_ptr;            // per subdomain: offsets of the L and U level groups
   int max_lvl_ptr = 0;
-  // shared-memory apply: one packed blob per subdomain (see ras.cu)
+  // shared-memory apply: one factor stream per subdomain (see ras.cu)
   bool smem_path = false;
   bool built = false;           // a setup has run (level sets exportable)
-  size_t smem_bytes = 0;        // largest blob + local vector
-  dbuf<long long> blob_off;     // nsub + 1 byte offsets
-  dbuf<unsigned char> blob;
+  size_t smem_bytes = 0;        // ring + largest local vector
+  int m_max = 0;                // most extended rows in a subdomain
+  dbuf<long long> blob_off;     // nsub + 1 byte offsets (stream bounds)
+  dbuf<unsigned char> blob;     // the streams
+  dbuf<int> gidx;               // per subdomain and position: 2 * global row + owned flag
+  dbuf<int4> gdesc;             // group descriptors (packing scratch)
 };
 
 // ---------------------------------------------------------- linear system --

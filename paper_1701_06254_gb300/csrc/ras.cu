@@ -14,46 +14,39 @@
 #include <cfloat>
 #include <climits>
 
-// Packed per-subdomain factors for the shared-memory apply.  Rows are in
-// position (reordered) order; the diagonal blocks are dropped from the
-// entry arrays (their inverses are stored instead), so row i's L entries
-// are [rp[i], dg[i]) and its U entries [dg[i], rp[i+1]).  Lrow lists the rows
-// of L levels >= 1 level by level (Llev gives the level boundaries), Urow
-// all rows by U level.  gidx holds 2 * global row + owned flag.
-//   16 B header {m, L rows, L levels with rows, U levels}
-//   gidx int32[m] | rp u16[m+1] | dg u16[m] | Lrow u16[m] | Llev u16[m+1]
-//   | Urow u16[m] | Ulev u16[m+1] | cols u16[e] | vals VB[e] | dinv VB[m]
-// every section starts on a 16-byte boundary.
+// Streamed per-subdomain factors for the shared-memory apply.  One warp
+// solves one subdomain: its local vector y lives in shared memory, and the
+// factors, which each application reads exactly once and in a fixed order,
+// flow through a small shared-memory ring filled by bulk copies
+// (cp.async.bulk + mbarrier) a few chunks ahead of the sweep.  The stream of
+// a subdomain (16-byte aligned pieces):
+//   header  {m, L groups, U groups, stream bytes}
+//   groups  the rows of the L sweep (L levels 1.., level 0 has no entries),
+//           then the rows of the U sweep (U levels 0..), level by level;
+//           a level is split into groups of at most 32 rows (one per lane)
+//           and at most a group-byte cap, so a group always fits the ring
+// A group:
+//   {nrows, nent, bytes}                          16 B
+//   row records: local row, first and end entry   8 B (L) or RREC_U (U, with
+//               (group-relative), U: the inverse  the 2x2 block, 4 values)
+//               diagonal block
+//   cols  u16[nent] | vals [nent][4]   (the row records, the columns and
+//   the values each start on a 16-byte boundary)
+// The global row of each local row (bit 0: owned) is a separate array
+// (gidx), read by the gather and the scatter.
 #define RAS_SMEM_BUDGET (200 * 1024)
-// Packed per-subdomain factors (one "blob", 16-byte aligned sections):
-//   header: m, rows walked by the L sweep, L levels walked, U levels, e, eL
-//   gidx[m]   global row of each local row (bit 0: owned)
-//   llev, ulev  level boundaries (uint16) into lrec / urec
-//   lrec, urec  one uint32 per row of a level: local row (low 16 bits) and
-//               the offset of its first off-diagonal entry (high 16 bits);
-//               a row's entries end where the next record's begin (a
-//               sentinel record closes each list)
-//   cols[e], vals[e]  off-diagonal blocks in the order of the records: the L
-//               sweep's rows first (level by level), then the U sweep's
-//   dinv[m]   inverse diagonal blocks, by local row
-// Sizes use m for every level count, so the layout depends only on (m, e).
-struct blob_layout { int gidx, llev, ulev, lrec, urec, cols, vals, dinv, total; };
-#define BLOB_HDR 32
+#define RAS_GROUP_ROWS 32
+template <class TB> struct ring_cfg;                       // ring bytes, chunk bytes per stored type
+template <> struct ring_cfg<__nv_bfloat16> { static const int R = 8192, C = 2048; };
+template <> struct ring_cfg<float> { static const int R = 16384, C = 4096; };
+template <> struct ring_cfg<double> { static const int R = 32768, C = 8192; };
+// U row record: 8 bytes of indices, then the inverse diagonal block at DOFF
+template <class TB> __host__ __device__ constexpr int rrec_doff() { return 4 * (int)sizeof(TB) <= 8 ? 8 : 16; }
+template <class TB> __host__ __device__ constexpr int rrec_u() { return (rrec_doff<TB>() + 4 * (int)sizeof(TB) + 15) & ~15; }
+// a group's byte cap: one chunk short of the ring, so that a group starting
+// anywhere in a chunk has landed once the chunks it touches have
+template <class TB> __host__ __device__ constexpr int group_cap() { return ring_cfg<TB>::R - ring_cfg<TB>::C; }
 __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
-__host__ __device__ inline blob_layout blob_lay(int m, int e, int vb) {
-  blob_layout L;
-  int o = BLOB_HDR;
-  L.gidx = o; o = al16(o + 4 * m);
-  L.llev = o; o = al16(o + 2 * (m + 1));
-  L.ulev = o; o = al16(o + 2 * (m + 1));
-  L.lrec = o; o = al16(o + 4 * (m + 1));
-  L.urec = o; o = al16(o + 4 * (m + 1));
-  L.cols = o; o = al16(o + 2 * e);
-  L.vals = o; o = al16(o + vb * e);
-  L.dinv = o; o = al16(o + vb * m);
-  L.total = o;
-  return L;
-}
 
 // ------------------------------------------------- static partition (host)
 void ras_build_static(sim_ls_s *ls) {
@@ -132,24 +125,35 @@ void ras_build_static(sim_ls_s *ls) {
   int m = 1;
   while (m < maxcells) m <<= 1;
   R.max_lvl_ptr = m;   // sort width (power of two >= most cells in a subdomain)
-  // shared-memory apply: blob sizes are static (rows and entries per
-  // subdomain do not change with the ordering)
+  // shared-memory apply: a bound on each subdomain's stream (the grouping
+  // follows the level sets of each setup, the bound only rows and entries:
+  // at most one group per walked row, each with its header and padding)
   {
     int vb = ls->o.precision == SIM_PREC_FP64 ? 32 : (ls->o.precision == SIM_PREC_MIXED_BF16 ? 8 : 16);
+    int ru = ls->o.precision == SIM_PREC_FP64 ? rrec_u<double>()
+                                              : (ls->o.precision == SIM_PREC_MIXED_BF16 ? rrec_u<__nv_bfloat16>()
+                                                                                        : rrec_u<float>());
+    int ring = ls->o.precision == SIM_PREC_FP64 ? ring_cfg<double>::R
+                                                : (ls->o.precision == SIM_PREC_MIXED_BF16 ? ring_cfg<__nv_bfloat16>::R
+                                                                                          : ring_cfg<float>::R);
     int yb = ls->o.precision == SIM_PREC_FP64 ? 16 : 8;   // local vector: double2 or float2 per row
     std::vector<long long> boff(nsub + 1, 0);
-    size_t mx = 0;
+    int mmax = 0;
     bool fits16 = true;
     for (int s2 = 0; s2 < nsub; s2++) {
-      int ms = sub_ptr[s2 + 1] - sub_ptr[s2], nz = lrp_ptr[s2 + 1] - lrp_ptr[s2];
-      if (ms >= 65535 || nz >= 65535) fits16 = false;
-      blob_layout L = blob_lay(ms, nz - ms, vb);
-      boff[s2 + 1] = boff[s2] + L.total;
-      mx = std::max(mx, (size_t)L.total + (size_t)ms * yb);
+      long long ms = sub_ptr[s2 + 1] - sub_ptr[s2], nz = lrp_ptr[s2 + 1] - lrp_ptr[s2], e = nz - ms;
+      if (ms >= 65535) fits16 = false;
+      long long bound = 16 + 2 * ms * (16 + 48) + ms * (8 + ru) + e * (2 + vb);   // header + 3 paddings per group
+      boff[s2 + 1] = boff[s2] + ((bound + 15) & ~15LL);
+      mmax = std::max(mmax, (int)ms);
     }
-    R.smem_bytes = mx;
-    R.smem_path = fits16 && mx <= RAS_SMEM_BUDGET;
-    if (R.smem_path) { h2d(R.blob_off, boff, st); R.blob.alloc(boff[nsub]); }
+    R.m_max = mmax;
+    R.smem_bytes = (size_t)mmax * yb + ring;
+    R.smem_path = fits16 && R.smem_bytes <= RAS_SMEM_BUDGET;
+    if (R.smem_path) {
+      h2d(R.blob_off, boff, st); R.blob.alloc(boff[nsub]);
+      R.gidx.alloc(ext.size()); R.gdesc.alloc(2 * ext.size() + 2 * (size_t)nsub);
+    }
   }
   if ((size_t)m * 12 > 200 * 1024) RS_FAIL(SIM_ERR_ARG, "RAS: %d cells per subdomain is too many (reduce tile_x/tile_y)", maxcells);
   if ((size_t)R.max_ext * 16 > 200 * 1024) RS_FAIL(SIM_ERR_ARG, "RAS: subdomain too large");
@@ -486,87 +490,118 @@ __device__ __forceinline__ void row_sub(T2 &a, int q0, int q1, const uint16_t *c
   }
 }
 
-// T: factor type (FP32 or FP64), TB: stored value type (T, or BF16)
+// T: factor type (FP32 or FP64), TB: stored value type (T, or BF16).
+// One block per subdomain.  Thread 0 splits the levels into groups (at most
+// 32 rows and group_cap bytes each) and lays them out; then each warp fills
+// whole groups: row records (with the inverse diagonal block for U rows),
+// columns and values in the row's entry order.
 template <class T, class TB>
 __global__ void k_ras_pack(const int *sub_ptr, const int *lrp_ptr, const int *ext, const uint8_t *owned,
                            const int *perm, const int *frp, const int *fci, const int *fdiag, const T *fv,
                            const T *dinv, const int *lvl_rows, const int *nlev, const int *lvl_ptr,
-                           const long long *blob_off, unsigned char *blobs, const int *order) {
-  __shared__ int part[129];
+                           const long long *blob_off, unsigned char *blobs, int *gidx, int4 *gdesc,
+                           const int *order, int *err) {
   int s = order[blockIdx.x], base = sub_ptr[s], m = sub_ptr[s + 1] - base, pbase = lrp_ptr[s], fbase = base + s;
-  int e = (lrp_ptr[s + 1] - pbase) - m;
-  blob_layout Lb = blob_lay(m, e, 4 * (int)sizeof(TB));
-  unsigned char *b = blobs + blob_off[s];
-  int *gidx = (int *)(b + Lb.gidx);
-  uint16_t *llev = (uint16_t *)(b + Lb.llev), *ulev = (uint16_t *)(b + Lb.ulev);
-  uint32_t *lrec = (uint32_t *)(b + Lb.lrec), *urec = (uint32_t *)(b + Lb.urec);
-  uint16_t *cols = (uint16_t *)(b + Lb.cols);
-  TB *vals = (TB *)(b + Lb.vals), *dv = (TB *)(b + Lb.dinv);
   const int *pL = lvl_ptr + 2 * (base + s), *pU = pL + (m + 1);
   const int *rL = lvl_rows + 2 * base, *rU = rL + m;
   int nL = nlev[2 * s], nU = nlev[2 * s + 1];
-  int l0 = 1 < nL ? pL[1] : 0;                      // level 0 of L has no entries: not walked
-  int nLl = nL > 1 ? nL - 1 : 0, nLrows = nL > 1 ? pL[nL] - l0 : 0;
+  unsigned char *b = blobs + blob_off[s];
+  int4 *gd = gdesc + 2 * (base + s);                 // room for 2 (m + 1) groups
+  const int VB = 4 * (int)sizeof(TB), RU = rrec_u<TB>(), CAP = group_cap<TB>();
+  __shared__ int ngr[3];
   // row i's entries in the factor: [frp, diag) lower, (diag, frp next) upper
-  auto lo0 = [&](int i) { return frp[fbase + i]; };
-  auto dgl = [&](int i) { return fdiag[base + i] - pbase; };
-  auto hi1 = [&](int i) { return frp[fbase + i + 1]; };
-  const int nt = blockDim.x, t = threadIdx.x;
-  // records of the L sweep's rows (level order), entries placed in that order
-  int eL = 0;
-  {
-    int per = (nLrows + nt - 1) / nt, r0 = t * per, r1 = min(nLrows, r0 + per), sum = 0;
-    for (int r = r0; r < r1; r++) { int i = rL[l0 + r]; sum += dgl(i) - lo0(i); }
-    part[t] = sum;
-    __syncthreads();
-    if (t == 0) { int acc = 0; for (int k = 0; k < nt; k++) { int v = part[k]; part[k] = acc; acc += v; } part[nt] = acc; }
-    __syncthreads();
-    int off = part[t];
-    for (int r = r0; r < r1; r++) {
-      int i = rL[l0 + r], q0 = lo0(i), qd = dgl(i);
-      lrec[r] = (uint32_t)i | ((uint32_t)off << 16);
-      for (int q = q0; q < qd; q++, off++) {
-        cols[off] = (uint16_t)fci[pbase + q];
-        const T *src = fv + 4 * (size_t)(pbase + q);
-        for (int u = 0; u < 4; u++) vals[4 * off + u] = to_blob_d<TB>(src[u]);
+  auto nlo = [&](int i) { return fdiag[base + i] - pbase - frp[fbase + i]; };
+  auto nup = [&](int i) { return frp[fbase + i + 1] - (fdiag[base + i] - pbase) - 1; };
+  if (threadIdx.x == 0) {
+    // groups: {first row (index into the sweep's row list), rows, entries, byte offset | U flag in bit 0}
+    int off = 16, ng = 0, ngL = 0;
+    for (int sweep = 0; sweep < 2; sweep++) {
+      const int *pp = sweep ? pU : pL, *rr = sweep ? rU : rL;
+      int nl = sweep ? nU : nL, rrec = sweep ? RU : 8;
+      for (int l = sweep ? 0 : 1; l < nl; l++) {
+        int a = pp[l], a1 = pp[l + 1];
+        while (a < a1) {
+          int rows = 0, ent = 0;
+          for (;;) {
+            if (a + rows >= a1 || rows == RAS_GROUP_ROWS) break;
+            int i = rr[a + rows], ne = sweep ? nup(i) : nlo(i);
+            int nb = 16 + al16((rows + 1) * rrec) + al16(2 * (ent + ne)) + (ent + ne) * VB;
+            if (rows > 0 && nb > CAP) break;
+            rows++; ent += ne;
+          }
+          gd[ng] = make_int4(a, rows, ent, (off << 1) | sweep);
+          off += al16(16 + al16(rows * rrec) + al16(2 * ent) + ent * VB);
+          ng++;
+          a += rows;
+        }
       }
+      if (!sweep) ngL = ng;
     }
-    eL = part[nt];
-    __syncthreads();
-  }
-  // records of the U sweep's rows (level order), after the L entries
-  {
-    int per = (m + nt - 1) / nt, r0 = t * per, r1 = min(m, r0 + per), sum = 0;
-    for (int r = r0; r < r1; r++) { int i = rU[r]; sum += hi1(i) - dgl(i) - 1; }
-    part[t] = sum;
-    __syncthreads();
-    if (t == 0) { int acc = 0; for (int k = 0; k < nt; k++) { int v = part[k]; part[k] = acc; acc += v; } part[nt] = acc; }
-    __syncthreads();
-    int off = eL + part[t];
-    for (int r = r0; r < r1; r++) {
-      int i = rU[r], qd = dgl(i), q1 = hi1(i);
-      urec[r] = (uint32_t)i | ((uint32_t)off << 16);
-      for (int q = qd + 1; q < q1; q++, off++) {
-        cols[off] = (uint16_t)fci[pbase + q];
-        const T *src = fv + 4 * (size_t)(pbase + q);
-        for (int u = 0; u < 4; u++) vals[4 * off + u] = to_blob_d<TB>(src[u]);
-      }
-    }
-  }
-  if (t == 0) {
+    // the stream must fit its bound (rows and entries only); never true by
+    // construction, checked so that a violation is an error, not an overrun
+    if ((long long)off > blob_off[s + 1] - blob_off[s]) { atomicExch(err, 4); ngL = 0; ng = 0; off = 16; }
+    ngr[0] = ngL; ngr[1] = ng - ngL; ngr[2] = off;
     int *hdr = (int *)b;
-    hdr[0] = m; hdr[1] = nLrows; hdr[2] = nLl; hdr[3] = nU; hdr[4] = e; hdr[5] = eL; hdr[6] = 0; hdr[7] = 0;
-    lrec[nLrows] = (uint32_t)eL << 16;               // sentinels: where the last row's entries end
-    urec[m] = (uint32_t)e << 16;
+    hdr[0] = m; hdr[1] = ngL; hdr[2] = ng - ngL; hdr[3] = off;
   }
-  for (int pos = t; pos < m; pos += nt) {
+  __syncthreads();
+  int ng = ngr[0] + ngr[1];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int g = wid; g < ng; g += nwarps) {
+    int4 d = gd[g];
+    int sweep = d.w & 1, goff = d.w >> 1, rows = d.y, ent = d.z, rrec = sweep ? RU : 8;
+    const int *rr = sweep ? rU : rL;
+    unsigned char *G = b + goff;
+    uint16_t *cols = (uint16_t *)(G + 16 + al16(rows * rrec));
+    TB *vals = (TB *)(G + 16 + al16(rows * rrec) + al16(2 * ent));
+    int i = lane < rows ? rr[d.x + lane] : 0;
+    int ne = lane < rows ? (sweep ? nup(i) : nlo(i)) : 0;
+    int e0 = ne;                                      // exclusive prefix of the entry counts
+    for (int o = 1; o < 32; o <<= 1) { int y = __shfl_up_sync(0xffffffffu, e0, o); if (lane >= o) e0 += y; }
+    e0 -= ne;
+    if (lane == 0) {
+      int *h = (int *)G;
+      h[0] = rows | (ent << 16); h[1] = al16(16 + al16(rows * rrec) + al16(2 * ent) + ent * VB); h[2] = 0; h[3] = 0;
+    }
+    if (lane < rows) {
+      uint16_t *rec = (uint16_t *)(G + 16 + lane * rrec);
+      rec[0] = (uint16_t)i; rec[1] = (uint16_t)e0; rec[2] = (uint16_t)(e0 + ne); rec[3] = 0;
+      if (sweep) {
+        TB *dv = (TB *)((unsigned char *)rec + rrec_doff<TB>());
+        const T *dsrc = dinv + 4 * (size_t)(base + i);
+        for (int u = 0; u < 4; u++) dv[u] = to_blob_d<TB>(dsrc[u]);
+      }
+      int q0 = sweep ? fdiag[base + i] - pbase + 1 : frp[fbase + i];
+      for (int k = 0; k < ne; k++) {
+        int q = q0 + k;
+        cols[e0 + k] = (uint16_t)fci[pbase + q];
+        const T *src = fv + 4 * (size_t)(pbase + q);
+        for (int u = 0; u < 4; u++) vals[4 * (e0 + k) + u] = to_blob_d<TB>(src[u]);
+      }
+    }
+  }
+  for (int pos = threadIdx.x; pos < m; pos += blockDim.x) {
     int x = perm[base + pos];
-    gidx[pos] = (ext[base + x] << 1) | (owned[base + x] ? 1 : 0);
-    const T *d = dinv + 4 * (size_t)(base + pos);
-    for (int u = 0; u < 4; u++) dv[4 * pos + u] = to_blob_d<TB>(d[u]);
+    gidx[base + pos] = (ext[base + x] << 1) | (owned[base + x] ? 1 : 0);
   }
-  for (int k = t; k <= nLl; k += nt) llev[k] = (uint16_t)(pL[k + 1] - l0);
-  for (int k = t; k <= nU; k += nt) ulev[k] = (uint16_t)pU[k];
+}
+
+// one 2x2 block from the ring at stream offset off: a 32-byte FP64 block
+// may wrap around the ring's end, so its two 16-byte halves are addressed
+// separately (16-byte alignment keeps every other element whole)
+template <int RB> __device__ __forceinline__ void ring_blk4(const unsigned char *ring, int off, const __nv_bfloat16 *,
+                                                           float &b0, float &b1, float &b2, float &b3) {
+  blk4(reinterpret_cast<const __nv_bfloat16 *>(ring + (off & (RB - 1))), b0, b1, b2, b3);
+}
+template <int RB> __device__ __forceinline__ void ring_blk4(const unsigned char *ring, int off, const float *,
+                                                           float &b0, float &b1, float &b2, float &b3) {
+  blk4(reinterpret_cast<const float *>(ring + (off & (RB - 1))), b0, b1, b2, b3);
+}
+template <int RB> __device__ __forceinline__ void ring_blk4(const unsigned char *ring, int off, const double *,
+                                                           double &b0, double &b1, double &b2, double &b3) {
+  double2 u = *reinterpret_cast<const double2 *>(ring + (off & (RB - 1)));
+  double2 v = *reinterpret_cast<const double2 *>(ring + ((off + 16) & (RB - 1)));
+  b0 = u.x; b1 = u.y; b2 = v.x; b3 = v.y;
 }
 
 template <class T> struct v2_t;
@@ -610,101 +645,120 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity
   return false;
 }
 
-// x = R(A)^{-1} f with the subdomain's packed factors held in shared
-// memory.  One block per subdomain: thread 0 starts two bulk copies of the
-// blob (header + gather indices first, the factors second); the block
-// gathers the extended right-hand side as soon as the first part lands,
-// then runs the level-scheduled L and U solves on chip and writes (or adds)
-// the owned rows.
-#define RAS_BS 64
+// x = R(A)^{-1} f, one warp per subdomain (one warp per block).  Lane 0
+// keeps the ring NSLOT chunks ahead of the sweep with bulk copies; every
+// lane waits on a chunk's mbarrier before reading it (bounded waits).  The
+// sweep takes one group at a time: lane r solves row r of the group (its
+// entries in stored order), then the warp synchronises; at the end the
+// owned rows are written (or added).
 template <class T, class Tin, bool ACC, class TB>
-__global__ void __launch_bounds__(RAS_BS) k_ras_apply_smem(const long long *blob_off, const unsigned char *blobs, const int *order,
-                                                           const Tin *__restrict__ f, T *__restrict__ x, int *err) {
+__global__ void __launch_bounds__(32) k_ras_apply_stream(const long long *blob_off, const unsigned char *blobs,
+                                                        const int *gidx_all, const int *sub_ptr, const int *order,
+                                                        const Tin *__restrict__ f, T *__restrict__ x, int *err) {
+  constexpr int RB = ring_cfg<TB>::R, CB = ring_cfg<TB>::C, NSLOT = RB / CB, RU = rrec_u<TB>();
   extern __shared__ uint4 sm4[];
-  __shared__ uint64_t bar[2];
+  __shared__ uint64_t bar[NSLOT];
   typedef typename v2_t<T>::type T2;
-  int s = order[blockIdx.x];                 // longest subdomains first
-  const unsigned char *b = blobs + blob_off[s];
-  int total = (int)(blob_off[s + 1] - blob_off[s]);
-  unsigned char *sb = reinterpret_cast<unsigned char *>(sm4);
-  // the first section (header + gidx) ends where llev starts; its size depends only on m
-  int m0 = ((const int *)b)[0];
-  int head = blob_lay(m0, 0, 4 * (int)sizeof(TB)).llev;
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+  typedef typename v2_t<Tin>::type Tin2;
+  const int lane = threadIdx.x;
+  const int s = order[blockIdx.x];
+  const unsigned char *st = blobs + blob_off[s];
+  const int *gidx = gidx_all + sub_ptr[s];
+  unsigned char *ring = reinterpret_cast<unsigned char *>(sm4);
+  const int m = sub_ptr[s + 1] - sub_ptr[s];
+  T2 *y = reinterpret_cast<T2 *>(ring + RB);
+  // header: m, L groups, U groups, stream bytes (read once from global memory)
+  int4 hd = *reinterpret_cast<const int4 *>(st);
+  const int ngL = hd.y, ngU = hd.z, total = hd.w;
+  const int nchunk = (total + CB - 1) / CB;
+  if (lane == 0) {
+    for (int k = 0; k < NSLOT; k++) mbar_init(&bar[k], 1);
     mbar_fence_init();
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(&bar[0], (unsigned)head);
-    bulk_g2s(sb, b, (unsigned)head, &bar[0]);
-    mbar_arrive_expect_tx(&bar[1], (unsigned)(total - head));
-    for (int off = head; off < total; off += 32768) {
-      int len = total - off < 32768 ? total - off : 32768;
-      bulk_g2s(sb + off, b + off, (unsigned)len, &bar[1]);
+  __syncwarp();
+  int issued = 0;
+  auto issue_upto = [&](int lim) {                  // lane 0: chunks [issued, lim)
+    for (; issued < lim && issued < nchunk; issued++) {
+      int len = total - issued * CB < CB ? total - issued * CB : CB;
+      uint64_t *bk = &bar[issued % NSLOT];
+      mbar_arrive_expect_tx(bk, (unsigned)len);
+      bulk_g2s(ring + (issued % NSLOT) * CB, st + (size_t)issued * CB, (unsigned)len, bk);
+    }
+  };
+  if (lane == 0) issue_upto(NSLOT);
+  issued = __shfl_sync(0xffffffffu, issued, 0);
+  // gather the extended right-hand side (overlaps the first bulk copies)
+  const Tin2 *f2 = reinterpret_cast<const Tin2 *>(f);
+  for (int p0 = lane; p0 < m; p0 += 8 * 32) {
+    Tin2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) { int pos = p0 + u * 32; if (pos < m) v[u] = f2[gidx[pos] >> 1]; }
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      int pos = p0 + u * 32;
+      if (pos < m) { T2 t; t.x = (T)v[u].x; t.y = (T)v[u].y; y[pos] = t; }
     }
   }
-  bool ok0 = mbar_wait_bounded(&bar[0], 0, err, 1);
-  const int *hdr = (const int *)sb;
-  int m = m0, nLl = hdr[2], nU = hdr[3], e = hdr[4];
-  const int *gidx = (const int *)(sb + BLOB_HDR);
-  T2 *y = reinterpret_cast<T2 *>(sm4 + total / 16);
-  typedef typename v2_t<Tin>::type Tin2;
-  const Tin2 *f2 = reinterpret_cast<const Tin2 *>(f);
-  if (ok0)   // gather, 8 independent loads in flight per thread
-    for (int p0 = threadIdx.x; p0 < m; p0 += 8 * blockDim.x) {
-      Tin2 v[8];
-#pragma unroll
-      for (int u = 0; u < 8; u++) { int pos = p0 + u * blockDim.x; if (pos < m) v[u] = f2[gidx[pos] >> 1]; }
-#pragma unroll
-      for (int u = 0; u < 8; u++) {
-        int pos = p0 + u * blockDim.x;
-        if (pos < m) { T2 t; t.x = (T)v[u].x; t.y = (T)v[u].y; y[pos] = t; }
+  __syncwarp();
+  int landed = 0;                                    // chunks waited for
+  bool ok = true;
+  // wait until stream bytes [.., end) are in the ring
+  auto ensure = [&](int end) {
+    int need = (end + CB - 1) / CB;
+    for (; landed < need && ok; landed++)
+      ok = mbar_wait_bounded(&bar[landed % NSLOT], (landed / NSLOT) & 1, err, 3);
+  };
+  int cons = 16;                                     // stream position of the current group
+  const int ng = ngL + ngU;
+  for (int g = 0; g < ng; g++) {
+    ensure(cons + 16);
+    if (!__all_sync(0xffffffffu, ok)) return;
+    const int *gh = reinterpret_cast<const int *>(ring + (cons & (RB - 1)));
+    int rows = gh[0] & 0xffff, ent = gh[0] >> 16, gbytes = gh[1];
+    ensure(cons + gbytes);
+    if (!__all_sync(0xffffffffu, ok)) return;
+    const bool up = g >= ngL;
+    const int rrec = up ? RU : 8;
+    if (lane < rows) {
+      int ro = cons + 16 + lane * rrec;
+      const uint16_t *rec = reinterpret_cast<const uint16_t *>(ring + (ro & (RB - 1)));
+      int i = rec[0], e0 = rec[1], e1 = rec[2];
+      int co = cons + 16 + al16(rows * rrec), vo = co + al16(2 * ent);   // both 16-byte aligned
+      T2 a = y[i];
+      for (int e = e0; e < e1; e++) {
+        int c = *reinterpret_cast<const uint16_t *>(ring + ((co + 2 * e) & (RB - 1)));
+        T b0, b1, b2, b3;
+        ring_blk4<RB>(ring, vo + e * 4 * (int)sizeof(TB), (const TB *)nullptr, b0, b1, b2, b3);
+        T2 yc = y[c];
+        a.x -= b0 * yc.x + b1 * yc.y;
+        a.y -= b2 * yc.x + b3 * yc.y;
+      }
+      if (up) {
+        T d0, d1, d2, d3;
+        ring_blk4<RB>(ring, ro + rrec_doff<TB>(), (const TB *)nullptr, d0, d1, d2, d3);
+        T2 o;
+        o.x = d0 * a.x + d1 * a.y; o.y = d2 * a.x + d3 * a.y;
+        y[i] = o;
+      } else {
+        y[i] = a;
       }
     }
-  bool ok1 = mbar_wait_bounded(&bar[1], 0, err, 2);
-  // uniform decision (and the barrier after the gather): on a timeout the
-  // error is recorded and nothing is written
-  if (!__syncthreads_and(ok0 && ok1)) return;
-  blob_layout Lb = blob_lay(m, e, 4 * (int)sizeof(TB));
-  const uint16_t *llev = (const uint16_t *)(sb + Lb.llev), *ulev = (const uint16_t *)(sb + Lb.ulev);
-  const uint32_t *lrec = (const uint32_t *)(sb + Lb.lrec), *urec = (const uint32_t *)(sb + Lb.urec);
-  const uint16_t *cols = (const uint16_t *)(sb + Lb.cols);
-  const TB *vals = (const TB *)(sb + Lb.vals), *dv = (const TB *)(sb + Lb.dinv);
-  // a level's rows are consecutive records; each record gives the row and
-  // where its entries start, the next record where they end
-  for (int k = 0; k < nLl; k++) {
-    for (int r = llev[k] + threadIdx.x; r < llev[k + 1]; r += blockDim.x) {
-      uint32_t rec = lrec[r], nxt = lrec[r + 1];
-      int i = rec & 0xffffu;
-      T2 a = y[i];
-      row_sub<T, T2, TB>(a, (int)(rec >> 16), (int)(nxt >> 16), cols, vals, y);
-      y[i] = a;
+    cons += gbytes;
+    __syncwarp();
+    // chunks wholly behind the sweep are free: refill them
+    if (lane == 0 && issued < nchunk && issued < cons / CB + NSLOT) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_upto(cons / CB + NSLOT);
     }
-    __syncthreads();
+    issued = __shfl_sync(0xffffffffu, issued, 0);
   }
-  for (int k = 0; k < nU; k++) {
-    for (int r = ulev[k] + threadIdx.x; r < ulev[k + 1]; r += blockDim.x) {
-      uint32_t rec = urec[r], nxt = urec[r + 1];
-      int i = rec & 0xffffu;
-      T2 a = y[i];
-      T d0, d1, d2, d3;
-      blk4(dv + 4 * i, d0, d1, d2, d3);
-      row_sub<T, T2, TB>(a, (int)(rec >> 16), (int)(nxt >> 16), cols, vals, y);
-      T2 o;
-      o.x = d0 * a.x + d1 * a.y; o.y = d2 * a.x + d3 * a.y;
-      y[i] = o;
-    }
-    __syncthreads();
-  }
-  for (int pos = threadIdx.x; pos < m; pos += blockDim.x) {
+  for (int pos = lane; pos < m; pos += 32) {
     int gi = gidx[pos];
     if (gi & 1) {
-      size_t g = (size_t)(gi >> 1);
+      size_t gg = (size_t)(gi >> 1);
       T2 v = y[pos];
-      if (ACC) { x[2 * g] += v.x; x[2 * g + 1] += v.y; }
-      else { x[2 * g] = v.x; x[2 * g + 1] = v.y; }
+      if (ACC) { x[2 * gg] += v.x; x[2 * gg + 1] += v.y; }
+      else { x[2 * gg] = v.x; x[2 * gg + 1] = v.y; }
     }
   }
 }
@@ -712,18 +766,20 @@ __global__ void __launch_bounds__(RAS_BS) k_ras_apply_smem(const long long *blob
 void ras_pack(sim_ls_s *ls) {
   ras_data &R = ls->ras;
   if (!R.smem_path) return;
+#define RAS_PACK_ARGS R.sub_ptr.p, R.lrp_ptr.p, R.ext.p, R.owned.p, R.perm.p, R.frp.p, R.fci.p, R.fdiag.p
   if (ls->o.precision == SIM_PREC_MIXED_BF16)
-    k_ras_pack<float, __nv_bfloat16><<<R.nsub, 128, 0, ls->st>>>(R.sub_ptr.p, R.lrp_ptr.p, R.ext.p, R.owned.p, R.perm.p,
-                                                  R.frp.p, R.fci.p, R.fdiag.p, R.fval32.p, R.dinv32.p, R.lvl_rows.p,
-                                                  R.nlev.p, R.lvl_ptr.p, R.blob_off.p, R.blob.p, R.order.p);
+    k_ras_pack<float, __nv_bfloat16><<<R.nsub, 128, 0, ls->st>>>(RAS_PACK_ARGS, R.fval32.p, R.dinv32.p, R.lvl_rows.p,
+                                                                R.nlev.p, R.lvl_ptr.p, R.blob_off.p, R.blob.p,
+                                                                R.gidx.p, R.gdesc.p, R.order.p, ls->errw_dev);
   else if (ls->o.precision != SIM_PREC_FP64)
-    k_ras_pack<float, float><<<R.nsub, 128, 0, ls->st>>>(R.sub_ptr.p, R.lrp_ptr.p, R.ext.p, R.owned.p, R.perm.p, R.frp.p,
-                                                  R.fci.p, R.fdiag.p, R.fval32.p, R.dinv32.p, R.lvl_rows.p,
-                                                  R.nlev.p, R.lvl_ptr.p, R.blob_off.p, R.blob.p, R.order.p);
+    k_ras_pack<float, float><<<R.nsub, 128, 0, ls->st>>>(RAS_PACK_ARGS, R.fval32.p, R.dinv32.p, R.lvl_rows.p, R.nlev.p,
+                                                        R.lvl_ptr.p, R.blob_off.p, R.blob.p, R.gidx.p, R.gdesc.p,
+                                                        R.order.p, ls->errw_dev);
   else
-    k_ras_pack<double, double><<<R.nsub, 128, 0, ls->st>>>(R.sub_ptr.p, R.lrp_ptr.p, R.ext.p, R.owned.p, R.perm.p, R.frp.p,
-                                                   R.fci.p, R.fdiag.p, R.fval.p, R.dinv.p, R.lvl_rows.p,
-                                                   R.nlev.p, R.lvl_ptr.p, R.blob_off.p, R.blob.p, R.order.p);
+    k_ras_pack<double, double><<<R.nsub, 128, 0, ls->st>>>(RAS_PACK_ARGS, R.fval.p, R.dinv.p, R.lvl_rows.p, R.nlev.p,
+                                                          R.lvl_ptr.p, R.blob_off.p, R.blob.p, R.gidx.p, R.gdesc.p,
+                                                          R.order.p, ls->errw_dev);
+#undef RAS_PACK_ARGS
   RS_LAUNCHED(1);
 }
 
@@ -736,8 +792,12 @@ __global__ void k_cast_acc(size_t m, const Tin *a, T *b, bool acc) {
 template <class T, class Tin, class TB>
 static void ras_apply_go(sim_ls_s *ls, const Tin *f, T *x, bool acc) {
   ras_data &R = ls->ras;
-  if (acc) k_ras_apply_smem<T, Tin, true, TB><<<R.nsub, RAS_BS, R.smem_bytes, ls->st>>>(R.blob_off.p, R.blob.p, R.order.p, f, x, ls->errw_dev);
-  else k_ras_apply_smem<T, Tin, false, TB><<<R.nsub, RAS_BS, R.smem_bytes, ls->st>>>(R.blob_off.p, R.blob.p, R.order.p, f, x, ls->errw_dev);
+  if (acc)
+    k_ras_apply_stream<T, Tin, true, TB><<<R.nsub, 32, R.smem_bytes, ls->st>>>(R.blob_off.p, R.blob.p, R.gidx.p,
+                                                                              R.sub_ptr.p, R.order.p, f, x, ls->errw_dev);
+  else
+    k_ras_apply_stream<T, Tin, false, TB><<<R.nsub, 32, R.smem_bytes, ls->st>>>(R.blob_off.p, R.blob.p, R.gidx.p,
+                                                                               R.sub_ptr.p, R.order.p, f, x, ls->errw_dev);
 }
 template <class T, class Tin> static void ras_apply_launch(sim_ls_s *ls, const Tin *f, T *x, bool acc);
 template <> void ras_apply_launch<double, double>(sim_ls_s *ls, const double *f, double *x, bool acc) {
@@ -758,7 +818,7 @@ template <class T, class Tin> void ls_ras_apply(sim_ls_s *ls, const Tin *f, T *x
   if (R.smem_path) {
     static bool attr = false;
     if (!attr) {
-#define RAS_ATTR(...) RS_CUDA(cudaFuncSetAttribute(k_ras_apply_smem<__VA_ARGS__>, cudaFuncAttributeMaxDynamicSharedMemorySize, RAS_SMEM_BUDGET))
+#define RAS_ATTR(...) RS_CUDA(cudaFuncSetAttribute(k_ras_apply_stream<__VA_ARGS__>, cudaFuncAttributeMaxDynamicSharedMemorySize, RAS_SMEM_BUDGET))
       RAS_ATTR(float, float, false, float); RAS_ATTR(float, float, true, float);
       RAS_ATTR(float, double, false, float); RAS_ATTR(float, double, true, float);
       RAS_ATTR(float, float, false, __nv_bfloat16); RAS_ATTR(float, float, true, __nv_bfloat16);
