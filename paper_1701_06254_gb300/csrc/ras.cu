@@ -15,18 +15,20 @@
 #include <climits>
 
 // Streamed per-subdomain factors for the shared-memory apply.  One warp
-// solves one subdomain: its local vector y lives in shared memory, and the
-// factors, which each application reads exactly once and in a fixed order,
-// flow through a small shared-memory ring filled by bulk copies
-// (cp.async.bulk + mbarrier) a few chunks ahead of the sweep.  The stream of
-// a subdomain (16-byte aligned pieces):
-//   header  {m, L groups, U groups, stream bytes}
+// solves one subdomain: its local vector y lives in shared
+// memory, and the factors, which each application reads exactly once and in
+// a fixed order, flow through a small shared-memory ring filled by bulk
+// copies (cp.async.bulk + mbarrier) a few chunks ahead of the sweep.  The
+// stream of a subdomain (16-byte aligned pieces):
+//   header  {m, L groups, U groups, stream bytes, first group's start} 32 B
 //   groups  the rows of the L sweep (L levels 1.., level 0 has no entries),
 //           then the rows of the U sweep (U levels 0..), level by level;
 //           a level is split into groups of at most 32 rows (one per lane)
-//           and at most a group-byte cap, so a group always fits the ring
+//           and at most one chunk of bytes; a group never straddles the
+//           end of the ring (the stream is padded to the next ring period
+//           instead), so its pieces are contiguous in shared memory
 // A group:
-//   {nrows, nent, bytes}                          16 B
+//   {nrows | nent << 16, bytes, next group's start}   16 B
 //   row records: local row, first and end entry   8 B (L) or RREC_U (U, with
 //               (group-relative), U: the inverse  the 2x2 block, 4 values)
 //               diagonal block
@@ -43,9 +45,9 @@ template <> struct ring_cfg<double> { static const int R = 32768, C = 8192; };
 // U row record: 8 bytes of indices, then the inverse diagonal block at DOFF
 template <class TB> __host__ __device__ constexpr int rrec_doff() { return 4 * (int)sizeof(TB) <= 8 ? 8 : 16; }
 template <class TB> __host__ __device__ constexpr int rrec_u() { return (rrec_doff<TB>() + 4 * (int)sizeof(TB) + 15) & ~15; }
-// a group's byte cap: one chunk short of the ring, so that a group starting
-// anywhere in a chunk has landed once the chunks it touches have
-template <class TB> __host__ __device__ constexpr int group_cap() { return ring_cfg<TB>::R - ring_cfg<TB>::C; }
+// a group's byte cap: one chunk (a group then touches at most two chunks,
+// and padding to the next ring period wastes at most a quarter of it)
+template <class TB> __host__ __device__ constexpr int group_cap() { return ring_cfg<TB>::C; }
 __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
 
 // ------------------------------------------------- static partition (host)
@@ -144,11 +146,12 @@ void ras_build_static(sim_ls_s *ls) {
       long long ms = sub_ptr[s2 + 1] - sub_ptr[s2], nz = lrp_ptr[s2 + 1] - lrp_ptr[s2], e = nz - ms;
       if (ms >= 65535) fits16 = false;
       long long bound = 16 + 2 * ms * (16 + 48) + ms * (8 + ru) + e * (2 + vb);   // header + 3 paddings per group
+      bound = bound + bound / 3 + ring;                     // ring-period padding: <= one chunk per ring
       boff[s2 + 1] = boff[s2] + ((bound + 15) & ~15LL);
       mmax = std::max(mmax, (int)ms);
     }
     R.m_max = mmax;
-    R.smem_bytes = (size_t)mmax * yb + ring;
+    R.smem_bytes = ((size_t)mmax * yb + 15) / 16 * 16 + ring;    // the ring, then the local vector
     R.smem_path = fits16 && R.smem_bytes <= RAS_SMEM_BUDGET;
     if (R.smem_path) {
       h2d(R.blob_off, boff, st); R.blob.alloc(boff[nsub]);
@@ -507,14 +510,14 @@ __global__ void k_ras_pack(const int *sub_ptr, const int *lrp_ptr, const int *ex
   int nL = nlev[2 * s], nU = nlev[2 * s + 1];
   unsigned char *b = blobs + blob_off[s];
   int4 *gd = gdesc + 2 * (base + s);                 // room for 2 (m + 1) groups
-  const int VB = 4 * (int)sizeof(TB), RU = rrec_u<TB>(), CAP = group_cap<TB>();
+  const int VB = 4 * (int)sizeof(TB), RU = rrec_u<TB>(), CAP = group_cap<TB>(), RB = ring_cfg<TB>::R;
   __shared__ int ngr[3];
   // row i's entries in the factor: [frp, diag) lower, (diag, frp next) upper
   auto nlo = [&](int i) { return fdiag[base + i] - pbase - frp[fbase + i]; };
   auto nup = [&](int i) { return frp[fbase + i + 1] - (fdiag[base + i] - pbase) - 1; };
   if (threadIdx.x == 0) {
     // groups: {first row (index into the sweep's row list), rows, entries, byte offset | U flag in bit 0}
-    int off = 16, ng = 0, ngL = 0;
+    int off = 32, ng = 0, ngL = 0;                   // a 32-byte stream header
     for (int sweep = 0; sweep < 2; sweep++) {
       const int *pp = sweep ? pU : pL, *rr = sweep ? rU : rL;
       int nl = sweep ? nU : nL, rrec = sweep ? RU : 8;
@@ -529,8 +532,10 @@ __global__ void k_ras_pack(const int *sub_ptr, const int *lrp_ptr, const int *ex
             if (rows > 0 && nb > CAP) break;
             rows++; ent += ne;
           }
+          int gb = al16(16 + al16(rows * rrec) + al16(2 * ent) + ent * VB);
+          if ((off & (RB - 1)) + gb > RB) off = (off + RB - 1) & ~(RB - 1);    // no group across the ring's end
           gd[ng] = make_int4(a, rows, ent, (off << 1) | sweep);
-          off += al16(16 + al16(rows * rrec) + al16(2 * ent) + ent * VB);
+          off += gb;
           ng++;
           a += rows;
         }
@@ -539,10 +544,12 @@ __global__ void k_ras_pack(const int *sub_ptr, const int *lrp_ptr, const int *ex
     }
     // the stream must fit its bound (rows and entries only); never true by
     // construction, checked so that a violation is an error, not an overrun
-    if ((long long)off > blob_off[s + 1] - blob_off[s]) { atomicExch(err, 4); ngL = 0; ng = 0; off = 16; }
+    if ((long long)off > blob_off[s + 1] - blob_off[s]) { atomicExch(err, 4); ngL = 0; ng = 0; off = 32; }
     ngr[0] = ngL; ngr[1] = ng - ngL; ngr[2] = off;
     int *hdr = (int *)b;
     hdr[0] = m; hdr[1] = ngL; hdr[2] = ng - ngL; hdr[3] = off;
+    // each group records the next one's start: the stream header the first
+    ((int *)b)[4] = ng ? (gd[0].w >> 1) : 0;
   }
   __syncthreads();
   int ng = ngr[0] + ngr[1];
@@ -561,7 +568,8 @@ __global__ void k_ras_pack(const int *sub_ptr, const int *lrp_ptr, const int *ex
     e0 -= ne;
     if (lane == 0) {
       int *h = (int *)G;
-      h[0] = rows | (ent << 16); h[1] = al16(16 + al16(rows * rrec) + al16(2 * ent) + ent * VB); h[2] = 0; h[3] = 0;
+      h[0] = rows | (ent << 16); h[1] = al16(16 + al16(rows * rrec) + al16(2 * ent) + ent * VB);
+      h[2] = g + 1 < ng ? (gd[g + 1].w >> 1) : 0; h[3] = 0;          // where the next group starts
     }
     if (lane < rows) {
       uint16_t *rec = (uint16_t *)(G + 16 + lane * rrec);
@@ -646,11 +654,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity
 }
 
 // x = R(A)^{-1} f, one warp per subdomain (one warp per block).  Lane 0
-// keeps the ring NSLOT chunks ahead of the sweep with bulk copies; every
-// lane waits on a chunk's mbarrier before reading it (bounded waits).  The
-// sweep takes one group at a time: lane r solves row r of the group (its
-// entries in stored order), then the warp synchronises; at the end the
-// owned rows are written (or added).
+// keeps the ring NSLOT chunks ahead of the sweep with bulk copies; every lane
+// waits on a chunk's mbarrier before reading it (bounded waits).  The sweep
+// takes one group at a time: lane r solves row r of the group (its entries
+// in stored order), then the warp synchronises; at the end the owned rows
+// are written (or added).
 template <class T, class Tin, bool ACC, class TB>
 __global__ void __launch_bounds__(32) k_ras_apply_stream(const long long *blob_off, const unsigned char *blobs,
                                                         const int *gidx_all, const int *sub_ptr, const int *order,
@@ -665,19 +673,20 @@ __global__ void __launch_bounds__(32) k_ras_apply_stream(const long long *blob_o
   const unsigned char *st = blobs + blob_off[s];
   const int *gidx = gidx_all + sub_ptr[s];
   unsigned char *ring = reinterpret_cast<unsigned char *>(sm4);
-  const int m = sub_ptr[s + 1] - sub_ptr[s];
   T2 *y = reinterpret_cast<T2 *>(ring + RB);
-  // header: m, L groups, U groups, stream bytes (read once from global memory)
-  int4 hd = *reinterpret_cast<const int4 *>(st);
-  const int ngL = hd.y, ngU = hd.z, total = hd.w;
+  const int m = sub_ptr[s + 1] - sub_ptr[s];
+  // header: m, L groups, U groups, stream bytes, first group's start
+  const int4 hd = *reinterpret_cast<const int4 *>(st);
+  const int ngL = hd.y, ng = hd.y + hd.z, total = hd.w;
+  int cons = reinterpret_cast<const int *>(st)[4];
   const int nchunk = (total + CB - 1) / CB;
   if (lane == 0) {
     for (int k = 0; k < NSLOT; k++) mbar_init(&bar[k], 1);
     mbar_fence_init();
   }
   __syncwarp();
-  int issued = 0;
-  auto issue_upto = [&](int lim) {                  // lane 0: chunks [issued, lim)
+  int issued = 0;                                    // lane 0: chunks issued
+  auto issue_upto = [&](int lim) {
     for (; issued < lim && issued < nchunk; issued++) {
       int len = total - issued * CB < CB ? total - issued * CB : CB;
       uint64_t *bk = &bar[issued % NSLOT];
@@ -686,7 +695,6 @@ __global__ void __launch_bounds__(32) k_ras_apply_stream(const long long *blob_o
     }
   };
   if (lane == 0) issue_upto(NSLOT);
-  issued = __shfl_sync(0xffffffffu, issued, 0);
   // gather the extended right-hand side (overlaps the first bulk copies)
   const Tin2 *f2 = reinterpret_cast<const Tin2 *>(f);
   for (int p0 = lane; p0 < m; p0 += 8 * 32) {
@@ -700,42 +708,38 @@ __global__ void __launch_bounds__(32) k_ras_apply_stream(const long long *blob_o
     }
   }
   __syncwarp();
-  int landed = 0;                                    // chunks waited for
+  int landed = 0, freed = 0;                         // chunks waited for; chunks behind the sweep
   bool ok = true;
-  // wait until stream bytes [.., end) are in the ring
-  auto ensure = [&](int end) {
-    int need = (end + CB - 1) / CB;
-    for (; landed < need && ok; landed++)
-      ok = mbar_wait_bounded(&bar[landed % NSLOT], (landed / NSLOT) & 1, err, 3);
-  };
-  int cons = 16;                                     // stream position of the current group
-  const int ng = ngL + ngU;
   for (int g = 0; g < ng; g++) {
-    ensure(cons + 16);
-    if (!__all_sync(0xffffffffu, ok)) return;
-    const int *gh = reinterpret_cast<const int *>(ring + (cons & (RB - 1)));
-    int rows = gh[0] & 0xffff, ent = gh[0] >> 16, gbytes = gh[1];
-    ensure(cons + gbytes);
+    // the group's header first, then the rest of its bytes
+    int need = (cons + 16 + CB - 1) / CB;
+    for (; landed < need && ok; landed++) ok = mbar_wait_bounded(&bar[landed % NSLOT], (landed / NSLOT) & 1, err, 3);
+    const unsigned char *G = ring + (cons & (RB - 1));         // the group is contiguous in the ring
+    const int4 h4 = *reinterpret_cast<const int4 *>(G);
+    const int rows = h4.x & 0xffff, ent = h4.x >> 16;
+    need = (cons + h4.y + CB - 1) / CB;
+    for (; landed < need && ok; landed++) ok = mbar_wait_bounded(&bar[landed % NSLOT], (landed / NSLOT) & 1, err, 3);
     if (!__all_sync(0xffffffffu, ok)) return;
     const bool up = g >= ngL;
     const int rrec = up ? RU : 8;
     if (lane < rows) {
-      int ro = cons + 16 + lane * rrec;
-      const uint16_t *rec = reinterpret_cast<const uint16_t *>(ring + (ro & (RB - 1)));
-      int i = rec[0], e0 = rec[1], e1 = rec[2];
-      int co = cons + 16 + al16(rows * rrec), vo = co + al16(2 * ent);   // both 16-byte aligned
+      const unsigned char *rec = G + 16 + lane * rrec;
+      const uint2 ri = *reinterpret_cast<const uint2 *>(rec);
+      const int i = ri.x & 0xffff, e0 = ri.x >> 16, e1 = ri.y & 0xffff;
+      const uint16_t *cols = reinterpret_cast<const uint16_t *>(G + 16 + al16(rows * rrec));
+      const TB *vals = reinterpret_cast<const TB *>(G + 16 + al16(rows * rrec) + al16(2 * ent));
       T2 a = y[i];
       for (int e = e0; e < e1; e++) {
-        int c = *reinterpret_cast<const uint16_t *>(ring + ((co + 2 * e) & (RB - 1)));
+        int c = cols[e];
         T b0, b1, b2, b3;
-        ring_blk4<RB>(ring, vo + e * 4 * (int)sizeof(TB), (const TB *)nullptr, b0, b1, b2, b3);
+        blk4(vals + 4 * e, b0, b1, b2, b3);
         T2 yc = y[c];
         a.x -= b0 * yc.x + b1 * yc.y;
         a.y -= b2 * yc.x + b3 * yc.y;
       }
       if (up) {
         T d0, d1, d2, d3;
-        ring_blk4<RB>(ring, ro + rrec_doff<TB>(), (const TB *)nullptr, d0, d1, d2, d3);
+        blk4(reinterpret_cast<const TB *>(rec + rrec_doff<TB>()), d0, d1, d2, d3);
         T2 o;
         o.x = d0 * a.x + d1 * a.y; o.y = d2 * a.x + d3 * a.y;
         y[i] = o;
@@ -743,14 +747,14 @@ __global__ void __launch_bounds__(32) k_ras_apply_stream(const long long *blob_o
         y[i] = a;
       }
     }
-    cons += gbytes;
+    cons = h4.z;                                     // the next group's start
     __syncwarp();
     // chunks wholly behind the sweep are free: refill them
-    if (lane == 0 && issued < nchunk && issued < cons / CB + NSLOT) {
+    if (lane == 0 && cons / CB > freed) {
+      freed = cons / CB;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_upto(cons / CB + NSLOT);
+      issue_upto(freed + NSLOT);
     }
-    issued = __shfl_sync(0xffffffffu, issued, 0);
   }
   for (int pos = lane; pos < m; pos += 32) {
     int gi = gidx[pos];
