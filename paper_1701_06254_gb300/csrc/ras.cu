@@ -39,7 +39,7 @@
 #define RAS_SMEM_BUDGET (200 * 1024)
 #define RAS_GROUP_ROWS 32
 template <class TB> struct ring_cfg;                       // ring bytes, chunk bytes per stored type
-template <> struct ring_cfg<__nv_bfloat16> { static const int R = 8192, C = 2048; };
+template <> struct ring_cfg<__nv_bfloat16> { static const int R = 4096, C = 1024; };
 template <> struct ring_cfg<float> { static const int R = 16384, C = 4096; };
 template <> struct ring_cfg<double> { static const int R = 32768, C = 8192; };
 // U row record: 8 bytes of indices, then the inverse diagonal block at DOFF
