@@ -617,7 +617,7 @@ __global__ void k_dense_lu_inv(int n, double *a, int *piv, double *inv) {
 
 // k_dense_lu_inv with the matrix in shared memory (n <= 128: at most
 // 128 KB); the same operations in the same order
-__global__ void k_dense_lu_inv_smem(int n, const double *ag, int *piv, double *inv) {
+__global__ void k_dense_lu_inv_smem(int n, const double *ag, int *piv, double *inv, int xs_smem) {
   extern __shared__ double sa[];
   __shared__ double smx[512]; __shared__ int sid[512]; __shared__ int spiv[128];
   int t = threadIdx.x, nt = blockDim.x;
@@ -648,12 +648,20 @@ __global__ void k_dense_lu_inv_smem(int n, const double *ag, int *piv, double *i
     }
     __syncthreads();
   }
+  // column c of the inverse by the two triangular solves, one thread per
+  // column; the column is worked on in shared memory when it fits beside the
+  // factors (xs), else in place in the output
+  bool xs = xs_smem != 0;
   for (int c = t; c < n; c += nt) {
-    double *x = inv + (size_t)c * n;            // stored transposed: inv[c][i] = (A^{-1})_{ic}
+    double *x = xs ? sa + (size_t)n * n + (size_t)c * n : inv + (size_t)c * n;
     for (int i = 0; i < n; i++) x[i] = (i == c) ? 1.0 : 0.0;
     for (int k = 0; k < n; k++) if (spiv[k] != k) { double y = x[k]; x[k] = x[spiv[k]]; x[spiv[k]] = y; }
     for (int i = 0; i < n; i++) { double s = x[i]; for (int j = 0; j < i; j++) s -= sa[i * n + j] * x[j]; x[i] = s; }
     for (int i = n - 1; i >= 0; i--) { double s = x[i]; for (int j = i + 1; j < n; j++) s -= sa[i * n + j] * x[j]; x[i] = s / sa[i * n + i]; }
+  }
+  if (xs) {                                     // stored transposed: inv[c][i] = (A^{-1})_{ic}
+    __syncthreads();
+    for (int e = t; e < n * n; e += nt) inv[e] = sa[(size_t)n * n + e];
   }
 }
 
@@ -806,10 +814,11 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
     if (n <= 128) {
       static bool attr = false;
       if (!attr) {
-        RS_CUDA(cudaFuncSetAttribute(k_dense_lu_inv_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 8));
+        RS_CUDA(cudaFuncSetAttribute(k_dense_lu_inv_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr = true;
       }
-      k_dense_lu_inv_smem<<<1, 512, (size_t)n * n * 8, s>>>(n, a.p, h.piv.p, h.lu.p);
+      int xs = (size_t)2 * n * n * 8 <= 200 * 1024;      // the inverse's columns beside the factors
+      k_dense_lu_inv_smem<<<1, 512, (size_t)(xs ? 2 : 1) * n * n * 8, s>>>(n, a.p, h.piv.p, h.lu.p, xs);
     } else {
       k_dense_lu_inv<<<1, 512, 0, s>>>(n, a.p, h.piv.p, h.lu.p);
     }
@@ -822,6 +831,8 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
 template <class T>
 __global__ void k_vc_pre(int n, const int *rp, const int *ci, const T *v, const T *dinv, const T *f, T *x, T *r) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_trigger();
+  pdl_wait();
   if (i >= n) return;
   T s = f[i];
   for (int q = rp[i]; q < rp[i + 1]; q++) { int j = ci[q]; s -= v[q] * (f[j] * dinv[j]); }
@@ -831,6 +842,8 @@ __global__ void k_vc_pre(int n, const int *rp, const int *ci, const T *v, const 
 template <class T>
 __global__ void k_prolong_add(int n, const int *rp, const int *ci, const T *v, const T *e, const T *x, T *t) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_trigger();
+  pdl_wait();
   if (i >= n) return;
   T s = x[i];
   for (int q = rp[i]; q < rp[i + 1]; q++) s += v[q] * e[ci[q]];
@@ -839,6 +852,8 @@ __global__ void k_prolong_add(int n, const int *rp, const int *ci, const T *v, c
 template <class T>
 __global__ void k_vc_post(int n, const int *rp, const int *ci, const T *v, const T *dinv, const T *f, const T *t, T *x) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_trigger();
+  pdl_wait();
   if (i >= n) return;
   T s = f[i];
   for (int q = rp[i]; q < rp[i + 1]; q++) s -= v[q] * t[ci[q]];
@@ -847,6 +862,8 @@ __global__ void k_vc_post(int n, const int *rp, const int *ci, const T *v, const
 template <class T>
 __global__ void k_restrict_x(int n, const int *rp, const int *ci, const T *v, const T *u, const T *dinv, T *y, T *x) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_trigger();
+  pdl_wait();
   if (i >= n) return;
   T s = 0;
   for (int q = rp[i]; q < rp[i + 1]; q++) s += v[q] * u[ci[q]];
@@ -856,6 +873,8 @@ __global__ void k_restrict_x(int n, const int *rp, const int *ci, const T *v, co
 template <class T>
 __global__ void k_jacobi(int n, const int *rp, const int *ci, const T *v, const T *dinv, const T *f, const T *x, T *y) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_trigger();
+  pdl_wait();
   if (i >= n) return;
   T s = f[i];
   for (int q = rp[i]; q < rp[i + 1]; q++) s -= v[q] * x[ci[q]];
@@ -864,6 +883,8 @@ __global__ void k_jacobi(int n, const int *rp, const int *ci, const T *v, const 
 template <class T>
 __global__ void k_dense_apply(int n, const double *invT, const T *f, T *x) {
   // x_i = sum_c (A^{-1})_{ic} f_c, invT[c][i]; one warp per row
+  pdl_trigger();
+  pdl_wait();
   int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (i >= n) return;
   double s = 0.0;
@@ -882,6 +903,8 @@ __global__ void k_dense_apply(int n, const double *invT, const T *f, T *x) {
 template <class T, int L, int MODE>
 __global__ void k_vc_lanes(int n, const int *__restrict__ rp, const int *__restrict__ ci, const T *__restrict__ v,
                            const T *__restrict__ dinv, const T *__restrict__ f, const T *__restrict__ u, T *o1, T *o2) {
+  pdl_trigger();
+  pdl_wait();
   int g = (blockIdx.x * blockDim.x + threadIdx.x) / L, k = threadIdx.x % L;
   int i = g < n ? g : n - 1;                       // whole groups stay in the shuffles
   int q0 = rp[i], q1 = rp[i + 1];
@@ -926,19 +949,19 @@ static void vc_sweep(int L, int n, const int *rp, const int *ci, const T *v, con
   if (n <= 0) return;
   if (L == 1) {
     unsigned g = grid_for(n, 256);
-    if (MODE == 0) k_vc_pre<T><<<g, 256, 0, s>>>(n, rp, ci, v, dinv, f, o1, o2);
-    else if (MODE == 1 && o2) k_restrict_x<T><<<g, 256, 0, s>>>(n, rp, ci, v, u, dinv, o1, o2);
-    else if (MODE == 1) k_csr_spmv<T><<<g, 256, 0, s>>>(n, rp, ci, v, u, o1);
-    else if (MODE == 2) k_prolong_add<T><<<g, 256, 0, s>>>(n, rp, ci, v, u, f, o1);
-    else k_vc_post<T><<<g, 256, 0, s>>>(n, rp, ci, v, dinv, f, u, o1);
+    if (MODE == 0) launch_pdl(k_vc_pre<T>, g, 256, 0, s, n, rp, ci, v, dinv, f, o1, o2);
+    else if (MODE == 1 && o2) launch_pdl(k_restrict_x<T>, g, 256, 0, s, n, rp, ci, v, u, dinv, o1, o2);
+    else if (MODE == 1) launch_pdl(k_csr_spmv<T>, g, 256, 0, s, n, rp, ci, v, u, o1);
+    else if (MODE == 2) launch_pdl(k_prolong_add<T>, g, 256, 0, s, n, rp, ci, v, u, f, o1);
+    else launch_pdl(k_vc_post<T>, g, 256, 0, s, n, rp, ci, v, dinv, f, u, o1);
     RS_LAUNCHED(1);
     return;
   }
   unsigned g = grid_for((size_t)n * L, 256);
-  if (L == 4) k_vc_lanes<T, 4, MODE><<<g, 256, 0, s>>>(n, rp, ci, v, dinv, f, u, o1, o2);
-  else if (L == 8) k_vc_lanes<T, 8, MODE><<<g, 256, 0, s>>>(n, rp, ci, v, dinv, f, u, o1, o2);
-  else if (L == 16) k_vc_lanes<T, 16, MODE><<<g, 256, 0, s>>>(n, rp, ci, v, dinv, f, u, o1, o2);
-  else k_vc_lanes<T, 32, MODE><<<g, 256, 0, s>>>(n, rp, ci, v, dinv, f, u, o1, o2);
+  if (L == 4) launch_pdl(k_vc_lanes<T, 4, MODE>, g, 256, 0, s, n, rp, ci, v, dinv, f, u, o1, o2);
+  else if (L == 8) launch_pdl(k_vc_lanes<T, 8, MODE>, g, 256, 0, s, n, rp, ci, v, dinv, f, u, o1, o2);
+  else if (L == 16) launch_pdl(k_vc_lanes<T, 16, MODE>, g, 256, 0, s, n, rp, ci, v, dinv, f, u, o1, o2);
+  else launch_pdl(k_vc_lanes<T, 32, MODE>, g, 256, 0, s, n, rp, ci, v, dinv, f, u, o1, o2);
   RS_LAUNCHED(1);
 }
 
@@ -968,7 +991,7 @@ int amg_vcycle(amg_hier &h, int l, cudaStream_t s) {
   int n = A.n;
   if (l == h.nlev - 1) {
     if (h.coarse_dense) {
-      k_dense_apply<T><<<grid_for(n, 8), 256, 0, s>>>(n, h.lu.p, LP::f(L), LP::x(L));
+      launch_pdl(k_dense_apply<T>, grid_for(n, 8), 256, 0, s, n, (const double *)h.lu.p, (const T *)LP::f(L), LP::x(L));
       RS_LAUNCHED(1);
       return 1;
     }
@@ -1037,6 +1060,8 @@ template void amg_vcycle_graph<float>(amg_hier &, cudaStream_t);
 template <class T>
 __global__ void k_csr_spmv(int n, const int *rp, const int *ci, const T *v, const T *x, T *y) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_trigger();
+  pdl_wait();
   if (i >= n) return;
   T s = 0;
   for (int q = rp[i]; q < rp[i + 1]; q++) s += v[q] * x[ci[q]];

@@ -64,6 +64,26 @@ template <class T> std::vector<T> d2h(const T *d, size_t m, cudaStream_t s) {
 }
 inline unsigned grid_for(size_t n, int bs) { size_t g = (n + bs - 1) / bs; return (unsigned)(g ? g : 1); }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may be
+// scheduled while the kernel before it in the stream is still running, so
+// its launch latency overlaps that kernel's last wave.  Such a kernel calls
+// pdl_wait() before it touches memory: the wait returns once the previous
+// kernel has completed and its writes are visible (at once when there is no
+// such kernel).  pdl_trigger() lets the next kernel be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid); cfg.blockDim = dim3(block); cfg.dynamicSmemBytes = smem; cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at; cfg.numAttrs = 1;
+  RS_CUDA(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
+}
+
 // ------------------------------------------------------- device helpers --
 // Arithmetic used where a floating-point value decides an integer (the
 // decoupled matrix, the reordering key, AMG strength / PMIS / P / RAP):

@@ -248,21 +248,35 @@ __global__ void k_ras_pattern(const int *sub_ptr, const int *lrp_ptr, const int 
 
 // level sets of the L and U factors; rows of a level in ascending position
 __global__ void k_ras_levels(const int *sub_ptr, const int *lrp_ptr, const int *frp, const int *fci, int *lvl,
-                             int *lvl_rows, int *nlev, int *lvl_ptr) {
+                             int *lvl_rows, int *nlev, int *lvl_ptr, int staged) {
   // the L levels (forward over the rows) and the U levels (backward) are
-  // independent: thread 0 walks one, thread 32 (another warp) the other
+  // independent: thread 0 walks one, thread 32 (another warp) the other.
+  // With `staged`, the block first copies the subdomain's pattern into shared
+  // memory, so the two serial walks read it (and their levels) from there.
+  extern __shared__ int lsm[];
   int s = blockIdx.x, base = sub_ptr[s], m = sub_ptr[s + 1] - base, pbase = lrp_ptr[s], fbase = base + s;
+  int nnz = frp[fbase + m];
+  const int *rp_ = frp + fbase, *ci_ = fci + pbase;
+  int *lvL = lvl + 2 * base, *lvU = lvL + m;
+  if (staged) {
+    int *srp = lsm, *sci = lsm + (m + 1);
+    for (int k = threadIdx.x; k <= m; k += blockDim.x) srp[k] = rp_[k];
+    for (int k = threadIdx.x; k < nnz; k += blockDim.x) sci[k] = ci_[k];
+    rp_ = srp; ci_ = sci;
+    lvL = sci + nnz; lvU = lvL + m;
+    __syncthreads();
+  }
   bool upper;
   if (threadIdx.x == 0) upper = false;
   else if (threadIdx.x == 32) upper = true;
   else return;
-  int *Lv = lvl + 2 * base + (upper ? m : 0);
+  int *Lv = upper ? lvU : lvL;
   int nl = 0;
   for (int t = 0; t < m; t++) {
     int i = upper ? m - 1 - t : t;
     int lv = 0;
-    for (int q = pbase + frp[fbase + i]; q < pbase + frp[fbase + i + 1]; q++) {
-      int c = fci[q];
+    for (int q = rp_[i]; q < rp_[i + 1]; q++) {
+      int c = ci_[q];
       if ((upper ? c > i : c < i) && Lv[c] + 1 > lv) lv = Lv[c] + 1;
     }
     Lv[i] = lv; if (lv + 1 > nl) nl = lv + 1;
@@ -270,8 +284,9 @@ __global__ void k_ras_levels(const int *sub_ptr, const int *lrp_ptr, const int *
   nlev[2 * s + (upper ? 1 : 0)] = nl;
   int *pp = lvl_ptr + 2 * (base + s) + (upper ? m + 1 : 0);
   int *rr = lvl_rows + 2 * base + (upper ? m : 0);
+  int *Lg = lvl + 2 * base + (upper ? m : 0);
   for (int l = 0; l <= nl; l++) pp[l] = 0;
-  for (int i = 0; i < m; i++) pp[Lv[i] + 1]++;
+  for (int i = 0; i < m; i++) { int v = Lv[i]; pp[v + 1]++; if (staged) Lg[i] = v; }
   for (int l = 0; l < nl; l++) pp[l + 1] += pp[l];
   // fill: rows in ascending position within a level (counts reused as cursors)
   for (int i = 0; i < m; i++) rr[pp[Lv[i]]++] = i;
@@ -374,8 +389,16 @@ void ras_setup(sim_ls_s *ls) {
   fsrc.ensure(R.lci.n);
   k_ras_pattern<<<R.nsub, 256, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.lrp.p, R.lrlen.p, R.lci.p, R.lsrc.p, R.perm.p,
                                        R.ipos.p, R.frp.p, R.fci.p, R.fdiag.p, fsrc.p);
-  k_ras_levels<<<R.nsub, 64, 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.frp.p, R.fci.p, R.lvl.p, R.lvl_rows.p, R.nlev.p,
-                                     R.lvl_ptr.p);
+  // level walks from shared memory when the largest pattern fits
+  size_t lsmem = (3 * (size_t)R.max_ext + 1 + (size_t)R.max_nnz) * sizeof(int);
+  int staged = lsmem <= 200 * 1024;
+  static bool lattr = false;
+  if (!lattr) {
+    RS_CUDA(cudaFuncSetAttribute(k_ras_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    lattr = true;
+  }
+  k_ras_levels<<<R.nsub, 64, staged ? lsmem : 0, s>>>(R.sub_ptr.p, R.lrp_ptr.p, R.frp.p, R.fci.p, R.lvl.p,
+                                                      R.lvl_rows.p, R.nlev.p, R.lvl_ptr.p, staged);
   // longest subdomains first for the factorisation and the applies (their
   // CTAs' times grow with the level counts)
   R.order.ensure(R.nsub);
@@ -512,44 +535,83 @@ __global__ void k_ras_pack(const int *sub_ptr, const int *lrp_ptr, const int *ex
   int4 *gd = gdesc + 2 * (base + s);                 // room for 2 (m + 1) groups
   const int VB = 4 * (int)sizeof(TB), RU = rrec_u<TB>(), CAP = group_cap<TB>(), RB = ring_cfg<TB>::R;
   __shared__ int ngr[3];
+  // dynamic shared memory: per level its group count (then the first group's
+  // index), per group its bytes
+  extern __shared__ int psm[];
+  const int nlevels = (nL > 1 ? nL - 1 : 0) + nU;
+  int *lgc = psm, *gby = psm + nlevels + 1;
   // row i's entries in the factor: [frp, diag) lower, (diag, frp next) upper
   auto nlo = [&](int i) { return fdiag[base + i] - pbase - frp[fbase + i]; };
   auto nup = [&](int i) { return frp[fbase + i + 1] - (fdiag[base + i] - pbase) - 1; };
-  if (threadIdx.x == 0) {
-    // groups: {first row (index into the sweep's row list), rows, entries, byte offset | U flag in bit 0}
-    int off = 32, ng = 0, ngL = 0;                   // a 32-byte stream header
-    for (int sweep = 0; sweep < 2; sweep++) {
-      const int *pp = sweep ? pU : pL, *rr = sweep ? rU : rL;
-      int nl = sweep ? nU : nL, rrec = sweep ? RU : 8;
-      for (int l = sweep ? 0 : 1; l < nl; l++) {
-        int a = pp[l], a1 = pp[l + 1];
-        while (a < a1) {
-          int rows = 0, ent = 0;
-          for (;;) {
-            if (a + rows >= a1 || rows == RAS_GROUP_ROWS) break;
-            int i = rr[a + rows], ne = sweep ? nup(i) : nlo(i);
-            int nb = 16 + al16((rows + 1) * rrec) + al16(2 * (ent + ne)) + (ent + ne) * VB;
-            if (rows > 0 && nb > CAP) break;
-            rows++; ent += ne;
-          }
-          int gb = al16(16 + al16(rows * rrec) + al16(2 * ent) + ent * VB);
-          if ((off & (RB - 1)) + gb > RB) off = (off + RB - 1) & ~(RB - 1);    // no group across the ring's end
-          gd[ng] = make_int4(a, rows, ent, (off << 1) | sweep);
-          off += gb;
-          ng++;
-          a += rows;
-        }
+  // level lv of the sweep order: L levels 1..nL-1, then U levels 0..nU-1
+  auto level_of = [&](int lv, int &sweep, int &a, int &a1) {
+    int nLw = nL > 1 ? nL - 1 : 0;
+    sweep = lv >= nLw;
+    int l = sweep ? lv - nLw : lv + 1;
+    const int *pp = sweep ? pU : pL;
+    a = pp[l]; a1 = pp[l + 1];
+  };
+  // split one level into groups of at most RAS_GROUP_ROWS rows and CAP bytes;
+  // emit(first, rows, entries) for each group in order
+  auto split = [&](int lv, auto emit) {
+    int sweep, a, a1;
+    level_of(lv, sweep, a, a1);
+    const int *rr = sweep ? rU : rL;
+    int rrec = sweep ? RU : 8;
+    while (a < a1) {
+      int rows = 0, ent = 0;
+      for (;;) {
+        if (a + rows >= a1 || rows == RAS_GROUP_ROWS) break;
+        int i = rr[a + rows], ne = sweep ? nup(i) : nlo(i);
+        int nb = 16 + al16((rows + 1) * rrec) + al16(2 * (ent + ne)) + (ent + ne) * VB;
+        if (rows > 0 && nb > CAP) break;
+        rows++; ent += ne;
       }
-      if (!sweep) ngL = ng;
+      emit(a, rows, ent, sweep);
+      a += rows;
+    }
+  };
+  for (int lv = threadIdx.x; lv < nlevels; lv += blockDim.x) {       // groups per level
+    int c = 0;
+    split(lv, [&](int, int, int, int) { c++; });
+    lgc[lv] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {                                            // first group of each level
+    int acc = 0, nLw = nL > 1 ? nL - 1 : 0, ngL = 0;
+    for (int lv = 0; lv < nlevels; lv++) { int c = lgc[lv]; lgc[lv] = acc; acc += c; if (lv == nLw - 1) ngL = acc; }
+    lgc[nlevels] = acc;
+    ngr[0] = nLw > 0 ? ngL : 0; ngr[1] = acc - ngr[0];
+  }
+  __syncthreads();
+  for (int lv = threadIdx.x; lv < nlevels; lv += blockDim.x) {       // descriptors and bytes
+    int g = lgc[lv];
+    split(lv, [&](int a, int rows, int ent, int sweep) {
+      int rrec = sweep ? RU : 8;
+      gd[g] = make_int4(a, rows, ent, sweep);
+      gby[g] = al16(16 + al16(rows * rrec) + al16(2 * ent) + ent * VB);
+      g++;
+    });
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // offsets: groups in order after a 32-byte stream header, none across the
+    // end of a ring period (moved to the next period instead)
+    int ng = ngr[0] + ngr[1], off = 32;
+    for (int g = 0; g < ng; g++) {
+      int gb = gby[g];
+      if ((off & (RB - 1)) + gb > RB) off = (off + RB - 1) & ~(RB - 1);
+      gd[g].w = (off << 1) | gd[g].w;
+      off += gb;
     }
     // the stream must fit its bound (rows and entries only); never true by
     // construction, checked so that a violation is an error, not an overrun
-    if ((long long)off > blob_off[s + 1] - blob_off[s]) { atomicExch(err, 4); ngL = 0; ng = 0; off = 32; }
-    ngr[0] = ngL; ngr[1] = ng - ngL; ngr[2] = off;
+    if ((long long)off > blob_off[s + 1] - blob_off[s]) { atomicExch(err, 4); ngr[0] = 0; ngr[1] = 0; off = 32; ng = 0; }
+    ngr[2] = off;
     int *hdr = (int *)b;
-    hdr[0] = m; hdr[1] = ngL; hdr[2] = ng - ngL; hdr[3] = off;
+    hdr[0] = m; hdr[1] = ngr[0]; hdr[2] = ngr[1]; hdr[3] = off;
     // each group records the next one's start: the stream header the first
-    ((int *)b)[4] = ng ? (gd[0].w >> 1) : 0;
+    hdr[4] = ng ? (gd[0].w >> 1) : 0;
   }
   __syncthreads();
   int ng = ngr[0] + ngr[1];
@@ -770,17 +832,25 @@ __global__ void __launch_bounds__(32) k_ras_apply_stream(const long long *blob_o
 void ras_pack(sim_ls_s *ls) {
   ras_data &R = ls->ras;
   if (!R.smem_path) return;
+  size_t psmem = (4 * (size_t)R.m_max + 8) * sizeof(int);      // level group counts and group bytes
+  static bool pattr = false;
+  if (!pattr) {
+    RS_CUDA(cudaFuncSetAttribute(k_ras_pack<float, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    RS_CUDA(cudaFuncSetAttribute(k_ras_pack<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    RS_CUDA(cudaFuncSetAttribute(k_ras_pack<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    pattr = true;
+  }
 #define RAS_PACK_ARGS R.sub_ptr.p, R.lrp_ptr.p, R.ext.p, R.owned.p, R.perm.p, R.frp.p, R.fci.p, R.fdiag.p
   if (ls->o.precision == SIM_PREC_MIXED_BF16)
-    k_ras_pack<float, __nv_bfloat16><<<R.nsub, 128, 0, ls->st>>>(RAS_PACK_ARGS, R.fval32.p, R.dinv32.p, R.lvl_rows.p,
+    k_ras_pack<float, __nv_bfloat16><<<R.nsub, 128, psmem, ls->st>>>(RAS_PACK_ARGS, R.fval32.p, R.dinv32.p, R.lvl_rows.p,
                                                                 R.nlev.p, R.lvl_ptr.p, R.blob_off.p, R.blob.p,
                                                                 R.gidx.p, R.gdesc.p, R.order.p, ls->errw_dev);
   else if (ls->o.precision != SIM_PREC_FP64)
-    k_ras_pack<float, float><<<R.nsub, 128, 0, ls->st>>>(RAS_PACK_ARGS, R.fval32.p, R.dinv32.p, R.lvl_rows.p, R.nlev.p,
+    k_ras_pack<float, float><<<R.nsub, 128, psmem, ls->st>>>(RAS_PACK_ARGS, R.fval32.p, R.dinv32.p, R.lvl_rows.p, R.nlev.p,
                                                         R.lvl_ptr.p, R.blob_off.p, R.blob.p, R.gidx.p, R.gdesc.p,
                                                         R.order.p, ls->errw_dev);
   else
-    k_ras_pack<double, double><<<R.nsub, 128, 0, ls->st>>>(RAS_PACK_ARGS, R.fval.p, R.dinv.p, R.lvl_rows.p, R.nlev.p,
+    k_ras_pack<double, double><<<R.nsub, 128, psmem, ls->st>>>(RAS_PACK_ARGS, R.fval.p, R.dinv.p, R.lvl_rows.p, R.nlev.p,
                                                           R.lvl_ptr.p, R.blob_off.p, R.blob.p, R.gidx.p, R.gdesc.p,
                                                           R.order.p, ls->errw_dev);
 #undef RAS_PACK_ARGS
