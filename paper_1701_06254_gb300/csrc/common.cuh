@@ -229,6 +229,10 @@ struct sim_ls_s {
   const void *it_sig[10] = {};   // buffers, restart length and precision it was recorded with
   cudaStream_t cap = nullptr;
   bool capturing = false;
+  // the RAS setup runs on a stream of its own beside the AMG setup (both
+  // need only the decoupled matrix): fork after the decoupling, join after both
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   dbuf<int> jd;                 // the step index the graph's kernels read
   dbuf<double> vcur, zcur64;
   dbuf<float> zcur32, vcur32;

@@ -64,6 +64,9 @@ void sim_ls_s::graph_timers() {
 sim_ls_s::~sim_ls_s() {
   drop_graph();
   if (cap) cudaStreamDestroy(cap);
+  if (st2) cudaStreamDestroy(st2);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
   for (auto e : ev) cudaEventDestroy(e);
   if (hpin) cudaFreeHost(hpin);
   if (errw) cudaFreeHost(errw);
@@ -442,8 +445,29 @@ void ls_setup(sim_ls_s *ls) {
   RS_LAUNCHED(1);
   }
   RS_CHECK_LAUNCH();
-  { rs_timed tm(ls, SIM_T_RAS_SETUP); ras_setup(ls); }
+  // RAS setup (reordering, level sets, factors, streams) on the second
+  // stream, concurrently with the AMG setup on the first: independent work
+  // on the same decoupled matrix, whose kernels are latency-bound and fill
+  // each other's idle SMs
+  if (!ls->st2) {
+    RS_CUDA(cudaStreamCreateWithFlags(&ls->st2, cudaStreamNonBlocking));
+    RS_CUDA(cudaEventCreateWithFlags(&ls->ev_fork, cudaEventDisableTiming));
+    RS_CUDA(cudaEventCreateWithFlags(&ls->ev_join, cudaEventDisableTiming));
+  }
+  RS_CUDA(cudaEventRecord(ls->ev_fork, s));
+  RS_CUDA(cudaStreamWaitEvent(ls->st2, ls->ev_fork, 0));
+  {
+    struct swap_stream {                     // ls->st names the second stream inside the RAS setup
+      sim_ls_s *l; cudaStream_t keep;
+      swap_stream(sim_ls_s *l_) : l(l_), keep(l_->st) { l->st = l->st2; }
+      ~swap_stream() { l->st = keep; }
+    } sw(ls);
+    rs_timed tm(ls, SIM_T_RAS_SETUP);
+    ras_setup(ls);
+  }
   { rs_timed tm(ls, SIM_T_AMG_SETUP); amg_setup(ls->amg, ls->o, s); }
+  RS_CUDA(cudaEventRecord(ls->ev_join, ls->st2));
+  RS_CUDA(cudaStreamWaitEvent(s, ls->ev_join, 0));
   ls->have_setup = true;
 }
 

@@ -391,7 +391,9 @@ void ras_setup(sim_ls_s *ls) {
                                        R.ipos.p, R.frp.p, R.fci.p, R.fdiag.p, fsrc.p);
   // level walks from shared memory when the largest pattern fits
   size_t lsmem = (3 * (size_t)R.max_ext + 1 + (size_t)R.max_nnz) * sizeof(int);
-  int staged = lsmem <= 200 * 1024;
+  // (measured: staging the pattern cut the walks' latency but limited the
+  // blocks per SM, and the launch took longer; the walks read global memory)
+  int staged = 0 * (lsmem <= 200 * 1024);
   static bool lattr = false;
   if (!lattr) {
     RS_CUDA(cudaFuncSetAttribute(k_ras_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
