@@ -253,10 +253,20 @@ def run_reference(args, case, rank):
 
 
 def train_warm_start(R, args, opts):
-    """Record the solves of --ws-members 64x64x16 models with the 1M-cell
-    case's physics (seeds 3000 + k, --ws-steps steps each), train the
-    network on them for --ws-epochs epochs (outside the timed region)."""
+    """The learned warm start's network: the weights trained offline by
+    paper_1701_06254_gb300/train_warm_start.py on the solves of 200
+    64x64x16 realisations of the 1M-cell case's physics when that file is
+    present (--ws-file), else a quick stand-in: record the solves of
+    --ws-members 64x64x16 models (seeds 3000 + k, --ws-steps steps each) and
+    train on them for --ws-epochs epochs (outside the timed region)."""
     from paper_1701_06254_gb300 import inputs as I
+    if args.ws_file and os.path.exists(args.ws_file):
+        from paper_1701_06254_gb300 import train_warm_start as T
+        params, info = T.load(args.ws_file)
+        ws = R.WarmStart(seed=7)
+        ws.set_params(params)
+        info = dict(info, source=os.path.basename(args.ws_file) + " (trained offline by train_warm_start.py)")
+        return ws, info
     t0 = time.perf_counter()
     ws = R.WarmStart(seed=7)
     for k in range(args.ws_members):
@@ -488,6 +498,8 @@ def main():
     ap.add_argument("--workers", default="auto", help="ensemble host workers, or 'auto' for the autotuner")
     ap.add_argument("--learned", action="store_true",
                     help="train the warm-start network on recorded 64x64x16 solves first and attach it")
+    ap.add_argument("--ws-file", default=os.path.join(ROOT, "paper_1701_06254_gb300", "warm_start_64x64x16.npz"),
+                    help="trained warm-start weights (train_warm_start.py); when missing, a short stand-in training")
     ap.add_argument("--ws-members", type=int, default=8)
     ap.add_argument("--ws-steps", type=int, default=5)
     ap.add_argument("--ws-epochs", type=int, default=10)

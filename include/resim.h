@@ -393,15 +393,16 @@ sim_status sim_batch_autotune(sim_batch_t b, const int *candidates, int n_candid
  * with TMEM accumulators for the forward and data-gradient convolutions, see
  * sim_ws_use_tcgen05), for inference and for training (Adam with FP32 master
  * weights).  It is grid-size agnostic: weights trained on one grid apply to
- * any other.  Inputs per cell (8 channels): the decoupled right-hand side
- * b (pressure and saturation rows, each over its rms over the cells),
- * (ln k - 4) / 2, 4 (s_w - 0.5), one application of the CPR preconditioner
- * z1 = M^-1 b (each component over its rms), and the previous solve's update
- * (each component over its rms; zero before the first solve).  Output: a
- * correction to z1, each component in units of the rms of z1's, so the
- * predicted update is z1 + rms(z1) * output (well rows: z1).  The head layer
- * starts at zero: an untrained network predicts z1.  A handle is used by one
- * caller at a time (calls on it are serialised internally). */
+ * any other.  Inputs per cell (8 channels): the Newton residual, i.e. the
+ * decoupled right-hand side b (pressure and saturation rows, each over its
+ * rms over the cells), (ln k - 4) / 2, 4 (s_w - 0.5), the previous solve's
+ * update (each component over its rms; zero before the first solve) and two
+ * zero channels.  Output: the shape of the update, each component (pressure,
+ * saturation) with unit rms over the cells; well rows are not predicted (0).
+ * The two components enter the initial guess as separate candidates whose
+ * scales a least-squares fit sets (sim_ws_attach).  The head layer starts at
+ * zero: an untrained network predicts nothing.  A handle is used by one caller at a time (calls
+ * on it are serialised internally). */
 typedef struct sim_ws_s *sim_ws_t;
 sim_status sim_ws_create(sim_ws_t *out, unsigned long long seed);   /* He-normal weights from seed, zero head */
 void sim_ws_destroy(sim_ws_t ws);
@@ -435,8 +436,8 @@ sim_status sim_ws_zero_grad(sim_ws_t ws);
 sim_status sim_ws_adam(sim_ws_t ws, double lr);
 
 /* Record: every linear solve of h appends its (features, target) pair, the
- * target being (update - z1) / rms(z1), to ws's dataset (device memory).
- * NULL stops recording. */
+ * target being the solved update with each component over its rms, to ws's
+ * dataset (device memory).  NULL stops recording. */
 sim_status sim_ws_record(sim_t h, sim_ws_t ws);
 sim_status sim_ws_dataset(sim_ws_t ws, int *n_samples);
 /* Train on the dataset: `epochs` passes in a seeded random order, an Adam
@@ -447,11 +448,13 @@ sim_status sim_ws_eval(sim_ws_t ws, double *mean_loss);
 
 /* Attach a network to a simulator (NULL detaches).  Every linear solve then
  * starts from the least-squares combination, on the decoupled system, of
- * z1 = M^-1 b, the network's correction and (at the first Newton iteration
- * of a time step) the previous step's first update: the x0 in their span
- * with the smallest ||b - J x0||.  The network's term is kept only when it
- * lowers that residual (ws_used), else it is dropped (ws_fallback); the
- * guess is never worse than zero.  The stopping test stays
+ * the network's predicted update (its pressure and saturation parts as two
+ * candidates) and (at the first Newton iteration of a time step) the
+ * previous step's first update: the x0 in their span with the
+ * smallest ||b - J x0||.  The network's term is kept only when it lowers that
+ * residual (ws_used), else it is dropped (ws_fallback: the previous step's
+ * first update alone where there is one, else zero); the guess is never
+ * worse than zero.  The stopping test stays
  * ||b - J y|| <= tol ||b||, so the converged update meets the same
  * tolerance either way.  sim_init_hydrostatic clears the history. */
 sim_status sim_ws_attach(sim_t h, sim_ws_t ws);

@@ -301,7 +301,7 @@ int sim_history(sim_t h, double *y, double *sc, int have, bool save);   // y: 2 
 // learned warm start (nn.cu)
 struct sim_ws_s;
 void ws_rms2(int n, const double *v, double *out, cudaStream_t s);
-void ws_predict(sim_ws_s *w, int nx, int ny, int nz, int nb, const double *b, const double *z1, const double *kx,
-                const double *sw, const double *yp, const double *sc, double *y, cudaStream_t s);
-void ws_record(sim_ws_s *w, int nx, int ny, int nz, const double *b, const double *z1, const double *kx,
-               const double *sw, const double *yp, const double *sc, const double *y, cudaStream_t s);
+void ws_predict(sim_ws_s *w, int nx, int ny, int nz, int nb, const double *b, const double *kx, const double *sw,
+                const double *yp, const double *sc, double *y, cudaStream_t s);
+void ws_record(sim_ws_s *w, int nx, int ny, int nz, const double *b, const double *kx, const double *sw,
+               const double *yp, const double *sc, const double *y, cudaStream_t s);

@@ -1378,14 +1378,14 @@ extern "C" sim_status sim_ws_eval(sim_ws_t w, double *mean_loss) {
 
 // ------------------------------------------------ simulator integration ---
 // Features of the current system, on the simulator's stream: X [n][16] BF16,
-// from the decoupled right-hand side b, one application of the CPR
-// preconditioner z1 = M^-1 b, ln k, s_w and the previous solve's update yp
-// (cell rows; each vector component over its rms over the cells):
+// from the decoupled right-hand side b (the Newton residual), ln k, s_w and
+// the previous solve's update yp (cell rows; each vector component over its
+// rms over the cells; channels 6-7 are zero):
 //   sc[0], sc[1] = rms of b (pressure / saturation rows),
-//   sc[2], sc[3] = rms of z1 (also the output scales),
+//   sc[2], sc[3] = rms of the solved update (recording only: the target's scales),
 //   sc[4], sc[5] = rms of yp (0 when there is no previous update).
-__global__ void k_ws_features(int n, const double *b, const double *z1, const double *kx, const double *sw,
-                              const double *yp, const double *sc, bf16 *X) {
+__global__ void k_ws_features(int n, const double *b, const double *kx, const double *sw, const double *yp,
+                              const double *sc, bf16 *X) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   auto q = [](double a, double s) { return s > 0.0 ? (float)(a / s) : 0.f; };
@@ -1394,10 +1394,10 @@ __global__ void k_ws_features(int n, const double *b, const double *z1, const do
   f[1] = q(b[2 * (size_t)c + 1], sc[1]);
   f[2] = (float)((log(kx[c]) - 4.0) * 0.5);
   f[3] = (float)((sw[c] - 0.5) * 4.0);
-  f[4] = q(z1[2 * (size_t)c], sc[2]);
-  f[5] = q(z1[2 * (size_t)c + 1], sc[3]);
-  f[6] = q(yp[2 * (size_t)c], sc[4]);
-  f[7] = q(yp[2 * (size_t)c + 1], sc[5]);
+  f[4] = q(yp[2 * (size_t)c], sc[4]);
+  f[5] = q(yp[2 * (size_t)c + 1], sc[5]);
+  f[6] = 0.f;
+  f[7] = 0.f;
   bf16 *o = X + (size_t)c * CIN_GPU;
 #pragma unroll
   for (int a = 0; a < 8; a++) o[a] = __float2bfloat16_rn(f[a]);
@@ -1405,21 +1405,25 @@ __global__ void k_ws_features(int n, const double *b, const double *z1, const do
   for (int a = 8; a < CIN_GPU; a++) o[a] = __float2bfloat16_rn(0.f);
 }
 
-// The network predicts a correction to z1: d = rms(z1_a) Y[c][a] for
-// cells, 0 for well rows
-__global__ void k_ws_predict(int n, int nb, const float *Y, const double *sc, double *d) {
+// The network predicts the update's shape, each component with unit rms:
+// two candidate vectors, its pressure part dp = (Y[c][0], 0) and its
+// saturation part ds = (0, Y[c][1]) for cells, 0 for well rows (the least-
+// squares fit of the initial guess sets both scales)
+__global__ void k_ws_predict(int n, int nb, const float *Y, double *dp, double *ds) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * nb) return;
   int c = i >> 1, a = i & 1;
-  d[i] = c < n ? (double)Y[(size_t)c * COUT_HEAD + a] * sc[2 + a] : 0.0;
+  double v = c < n ? (double)Y[(size_t)c * COUT_HEAD + a] : 0.0;
+  dp[i] = a == 0 ? v : 0.0;
+  ds[i] = a == 1 ? v : 0.0;
 }
 
-// T[c][a] = (y - z1)[2c + a] / rms(z1_a) (the training target of this system)
-__global__ void k_ws_target(int n, const double *y, const double *z1, const double *sc, float *T) {
+// T[c][a] = y[2c + a] / rms(y_a) (the training target of this system)
+__global__ void k_ws_target(int n, const double *y, const double *sc, float *T) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * n) return;
   double s = sc[2 + (i & 1)];
-  T[i] = s > 0.0 ? (float)((y[i] - z1[i]) / s) : 0.f;
+  T[i] = s > 0.0 ? (float)(y[i] / s) : 0.f;
 }
 
 // rms over the n cells of the two interleaved components of v -> out[0], out[1]
@@ -1444,10 +1448,11 @@ void ws_rms2(int n, const double *v, double *out, cudaStream_t s) {
   RS_LAUNCHED(1);
 }
 
-// predicted correction d to z1 (2 nb, FP64, device) for the system whose
-// decoupled right-hand side is b; z1, yp, sc as above (device)
-void ws_predict(sim_ws_s *w, int nx, int ny, int nz, int nb, const double *b, const double *z1, const double *kx,
-                const double *sw, const double *yp, const double *sc, double *y, cudaStream_t s) {
+// predicted update as two candidates in y (2 x 2 nb, FP64, device: pressure
+// part, then saturation part) for the system whose decoupled right-hand side
+// is b; yp, sc as above (device)
+void ws_predict(sim_ws_s *w, int nx, int ny, int nz, int nb, const double *b, const double *kx, const double *sw,
+                const double *yp, const double *sc, double *y, cudaStream_t s) {
   std::lock_guard<std::mutex> guard(w->use);
   dims d = {nx, ny, nz};
   ensure_dims(w, d);
@@ -1455,7 +1460,7 @@ void ws_predict(sim_ws_s *w, int nx, int ny, int nz, int nb, const double *b, co
   // the network runs on its own stream, ordered after the simulator's work
   cudaEvent_t ev;
   RS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-  k_ws_features<<<grid_for(n, 256), 256, 0, s>>>(n, b, z1, kx, sw, yp, sc, w->X0.p);
+  k_ws_features<<<grid_for(n, 256), 256, 0, s>>>(n, b, kx, sw, yp, sc, w->X0.p);
   RS_LAUNCHED(1);
   RS_CUDA(cudaEventRecord(ev, s));
   RS_CUDA(cudaStreamWaitEvent(w->st, ev, 0));
@@ -1463,13 +1468,13 @@ void ws_predict(sim_ws_s *w, int nx, int ny, int nz, int nb, const double *b, co
   RS_CUDA(cudaEventRecord(ev, w->st));
   RS_CUDA(cudaStreamWaitEvent(s, ev, 0));
   RS_CUDA(cudaEventDestroy(ev));
-  k_ws_predict<<<grid_for(2 * nb, 256), 256, 0, s>>>(n, nb, w->Y.p, sc, y);
+  k_ws_predict<<<grid_for(2 * nb, 256), 256, 0, s>>>(n, nb, w->Y.p, y, y + 2 * (size_t)nb);
   RS_LAUNCHED(1);
 }
 
 // append (features, target) of a solved system to the dataset
-void ws_record(sim_ws_s *w, int nx, int ny, int nz, const double *b, const double *z1, const double *kx,
-               const double *sw, const double *yp, const double *sc, const double *y, cudaStream_t s) {
+void ws_record(sim_ws_s *w, int nx, int ny, int nz, const double *b, const double *kx, const double *sw,
+               const double *yp, const double *sc, const double *y, cudaStream_t s) {
   std::lock_guard<std::mutex> guard(w->use);
   if (w->data.size() >= w->max_samples) return;
   dims d = {nx, ny, nz};
@@ -1478,8 +1483,8 @@ void ws_record(sim_ws_s *w, int nx, int ny, int nz, const double *b, const doubl
   S->d = d;
   S->X.alloc((size_t)n * CIN_GPU);
   S->T.alloc((size_t)n * NPRED);
-  k_ws_features<<<grid_for(n, 256), 256, 0, s>>>(n, b, z1, kx, sw, yp, sc, S->X.p);
-  k_ws_target<<<grid_for(2 * n, 256), 256, 0, s>>>(n, y, z1, sc, S->T.p);
+  k_ws_features<<<grid_for(n, 256), 256, 0, s>>>(n, b, kx, sw, yp, sc, S->X.p);
+  k_ws_target<<<grid_for(2 * n, 256), 256, 0, s>>>(n, y, sc, S->T.p);
   RS_LAUNCHED(2);
   RS_CUDA(cudaStreamSynchronize(s));       // the sample is complete before another stream reads it
   w->data.push_back(std::move(S));

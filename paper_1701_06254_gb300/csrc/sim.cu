@@ -47,11 +47,10 @@ struct sim_s {
   sim_ls_s *ls = nullptr;
   sim_stats stats;
   // learned warm start: the network used for initial guesses, the one that
-  // records (features, target) pairs, the previous solve's update, z1 = M^-1 b
-  // and the scales [rms b_p, rms b_s, rms z1_p, rms z1_s, rms y_prev_p, rms y_prev_s]
+  // records (features, target) pairs, the previous solve's update and the
+  // scales [rms b_p, rms b_s, rms y_p, rms y_s (of the solved update), rms y_prev_p, rms y_prev_s]
   sim_ws_s *ws = nullptr, *rec = nullptr;
-  dbuf<double> yprev, wsc, z1, dws, u, yfirst;
-  dbuf<float> z1f;
+  dbuf<double> yprev, wsc, dws, u, yfirst;
   bool have_prev = false, have_first = false, first_pending = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   ~sim_s() { delete ls; if (e0) cudaEventDestroy(e0); if (e1) cudaEventDestroy(e1); }
@@ -525,13 +524,15 @@ static double ls_fit(int m, const double G[3][3], const double r[3], double bb, 
 
 // One linear solve of the Newton system on the device (after ls_setup).
 // With a network attached, the initial guess is the least-squares
-// combination, on the decoupled system, of z1 = M^-1 b (one application of
-// the CPR preconditioner), the network's correction d and, at the first
+// combination, on the decoupled system, of the network's predicted update,
+// taken as two candidates (its pressure part and its saturation part, each
+// predicted with unit rms, so the fit sets both scales) and, at the first
 // Newton iteration of a step, the previous step's first update.  The
-// network's term is kept only when it lowers ||b - A x0|| below what the
-// other candidates reach without it (otherwise the plain combination is the
-// fallback); any such combination has ||b - A x0|| <= ||b||, the zero guess's.
-// Recording needs z1 and the rms scales of b, z1 and the previous update.
+// network's terms are kept only when they lower ||b - A x0|| below what the
+// other candidate reaches without them (otherwise that plain guess, or zero,
+// is the fallback); any such combination has ||b - A x0|| <= ||b||, the
+// zero guess's.  Recording needs the rms of b, of the previous update and of
+// the solved update (the target is the solved update over its rms).
 static int s_solve(sim_s *h, double eta, double bn, int *its, double *rel) {
   sim_ls_s *ls = h->ls;
   cudaStream_t st = h->st;
@@ -542,32 +543,23 @@ static int s_solve(sim_s *h, double eta, double bn, int *its, double *rel) {
   h->first_pending = false;
   rs_timed tm_ws(ls, h->ws ? SIM_T_WARMSTART : 0);
   if (learn) {
-    h->z1.ensure(nu);
-    if (ls->o.precision != SIM_PREC_FP64) {
-      h->z1f.ensure(nu);
-      ls_cpr(ls, ls->b.p, nullptr, h->z1f.p);
-      k_f2d<<<grid_for(nu, 256), 256, 0, st>>>((size_t)nu, h->z1f.p, h->z1.p);
-      RS_LAUNCHED(1);
-    } else {
-      ls_cpr(ls, ls->b.p, h->z1.p, nullptr);
-    }
     ws_rms2(h->n, ls->b.p, h->wsc.p, st);
-    ws_rms2(h->n, h->z1.p, h->wsc.p + 2, st);
     if (!h->have_prev) RS_CUDA(cudaMemsetAsync(h->wsc.p + 4, 0, 2 * sizeof(double), st));
   }
   if (h->ws) {
-    h->dws.ensure(nu); h->u.ensure(3 * (size_t)nu);
+    h->dws.ensure(2 * (size_t)nu); h->u.ensure(3 * (size_t)nu);
     {
       rs_timed tm_net(ls, SIM_T_NETWORK);
-      ws_predict(h->ws, h->nx, h->ny, h->nz, nb, ls->b.p, h->z1.p, h->kx.p, h->s.p, h->yprev.p, h->wsc.p, h->dws.p, st);
+      ws_predict(h->ws, h->nx, h->ny, h->nz, nb, ls->b.p, h->kx.p, h->s.p, h->yprev.p, h->wsc.p, h->dws.p, st);
     }
-    // candidates: 0 = z1, 1 = previous step's first update (if any), then d
+    // candidates: the previous step's first update (if any), then the
+    // network's pressure and saturation parts
     const double *c[3];
     int m = 0;
-    c[m++] = h->z1.p;
     if (first && h->have_first) c[m++] = h->yfirst.p;
     int id = m;
     c[m++] = h->dws.p;
+    c[m++] = h->dws.p + nu;
     double *u[3];
     for (int k = 0; k < m; k++) { u[k] = h->u.p + (size_t)k * nu; ls_spmv64_untimed(ls, c[k], u[k]); }
     const double *xs[9], *ys[9];
@@ -581,7 +573,7 @@ static int s_solve(sim_s *h, double eta, double bn, int *its, double *rel) {
     for (int i = 0; i < m; i++) for (int j = 0; j <= i; j++) { G[i][j] = G[j][i] = dv[q]; q++; }
     for (int i = 0; i < m; i++) r[i] = dv[q++];
     double bb = bn * bn, beta_p[3] = {0, 0, 0}, beta_d[3] = {0, 0, 0};
-    double res_p = ls_fit(id, G, r, bb, beta_p);       // without the network's term
+    double res_p = id ? ls_fit(id, G, r, bb, beta_p) : bb;   // without the network's term
     double res_d = ls_fit(m, G, r, bb, beta_d);        // with it
     const double *beta = beta_p;
     double res = res_p;
@@ -601,11 +593,12 @@ static int s_solve(sim_s *h, double eta, double bn, int *its, double *rel) {
   tm_ws.stop();
   int rc = ls_solve(ls, eta, its, rel, x0);
   if (rc == 2) return rc;
+  if (learn) ws_rms2(h->n, ls->y.p, h->wsc.p + 2, st);        // the solved update's scales
   if (h->rec)
-    ws_record(h->rec, h->nx, h->ny, h->nz, ls->b.p, h->z1.p, h->kx.p, h->s.p, h->yprev.p, h->wsc.p, ls->y.p, st);
+    ws_record(h->rec, h->nx, h->ny, h->nz, ls->b.p, h->kx.p, h->s.p, h->yprev.p, h->wsc.p, ls->y.p, st);
   if (learn) {
     RS_CUDA(cudaMemcpyAsync(h->yprev.p, ls->y.p, nu * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    ws_rms2(h->n, ls->y.p, h->wsc.p + 4, st);
+    RS_CUDA(cudaMemcpyAsync(h->wsc.p + 4, h->wsc.p + 2, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     h->have_prev = true;
     if (first) {
       h->yfirst.ensure(nu);

@@ -176,14 +176,15 @@ def test_warm_start_keeps_the_converged_solution():
 
 
 def test_untrained_network_falls_back_to_the_plain_guess():
-    """A fresh network's head is zero, so its correction adds nothing: every
-    solve falls back to the combination of M^-1 b and the previous step's
-    first update, whose residual is below the zero guess's."""
+    """A fresh network's head is zero, so its prediction adds nothing: every
+    solve falls back to the previous step's first update where there is one
+    (the first Newton iteration of every step after the first), whose
+    residual is below the zero guess's, and to zero elsewhere."""
     c = I.ensemble_member(4, seed0=5300, size_lo=(10, 10, 4), size_hi=(12, 12, 5))
-    g = _run(c, 2, ws=R.WarmStart(seed=14), precision=R.PREC_MIXED)
+    g = _run(c, 3, ws=R.WarmStart(seed=14), precision=R.PREC_MIXED)
     st = g.stats()
     assert st["ws_used"] == 0 and st["ws_fallback"] == st["linear_solves"] > 0
-    assert st["ws_r0"] / st["linear_solves"] < 1.0
+    assert st["ws_r0"] < st["linear_solves"]          # some solves started below ||b||, none above
 
 
 def test_warm_start_iteration_savings():
