@@ -448,17 +448,30 @@ __global__ void __launch_bounds__(128) k_spgemm_merge(int n, const int *arp, con
   clen[row] = cnt;
 }
 
+// Rows of A longer than SPG_KMAX, one warp per row.  The products of a row
+// (at most `cap` of them: rows with more are left to the launch with the
+// larger capacity) are expanded with (column, sequence) keys, sorted, and
+// each column's products summed in sequence order.  The keys and values sit
+// in shared memory, or (gscratch, for the rare rows beyond what shared
+// memory holds) in a global scratch area of cap entries per warp.  lo_cap:
+// rows with at most lo_cap products belong to the other launch.
 template <bool NUMERIC>
 __global__ void k_spgemm(int n, const int *arp, const int *aci, const double *av, const int *brp, const int *bci,
-                         const double *bv, const int *crp, int *clen, int *cci, double *cv, int cap) {
+                         const double *bv, const int *crp, int *clen, int *cci, double *cv, int cap, int lo_cap,
+                         unsigned long long *gscratch) {
   extern __shared__ unsigned long long sm_keys[];
   const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned long long *keys = sm_keys + (size_t)wid * cap;
-  double *vals = reinterpret_cast<double *>(sm_keys + (size_t)warps * cap) + (size_t)wid * cap;
+  unsigned long long *kbase = gscratch ? gscratch + (size_t)blockIdx.x * warps * 2 * cap : sm_keys;
+  unsigned long long *keys = kbase + (size_t)wid * cap;
+  double *vals = reinterpret_cast<double *>(kbase + (size_t)warps * cap) + (size_t)wid * cap;
   const unsigned FULL = 0xffffffffu;
   for (int row = blockIdx.x * warps + wid; row < n; row += gridDim.x * warps) {
     int a0 = arp[row], a1 = arp[row + 1], base = 0;
     if (a1 - a0 <= SPG_KMAX) continue;               // the merge kernel's row
+    {
+      int np_ = crp[row + 1] - crp[row];             // this row's products (scratch offsets)
+      if (np_ > cap || np_ <= lo_cap) continue;      // the other launch's row
+    }
     for (int q0 = a0; q0 < a1; q0 += 32) {
       int q = q0 + lane, len = 0, k = 0;
       if (q < a1) { k = aci[q]; len = brp[k + 1] - brp[k]; }
@@ -522,10 +535,12 @@ static void spgemm(const csr_dev<double> &A, const csr_dev<double> &B, csr_dev<d
   k_row_products<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, B.rp.p, toff.p, flag.p);
   RS_LAUNCHED(1);
   int mx1 = d2h(flag.p, 1, s)[0], mx = std::max(mx1 - 1, 0);
-  int cap = 32;
-  while (cap < mx) cap <<= 1;
+  int cap_all = 32;
+  while (cap_all < mx) cap_all <<= 1;
+  // shared-memory capacity at most 8192 products per warp (128 KB); rows with
+  // more go to a second launch with a global scratch area
+  int cap = std::min(cap_all, 8192);
   size_t per_warp = (size_t)cap * 16;
-  if (per_warp > 200 * 1024) RS_FAIL(SIM_ERR_ARG, "AMG: Galerkin row needs %d products (limit 12800)", mx);
   int warps = (int)std::min<size_t>(8, std::max<size_t>(1, (96 * 1024) / per_warp));
   size_t smem = per_warp * warps;
   static bool attr = false;
@@ -534,6 +549,7 @@ static void spgemm(const csr_dev<double> &A, const csr_dev<double> &B, csr_dev<d
     attr = true;
   }
   int total = rs_scan(toff.p, toff.p, n, s);          // row offsets into the scratch arrays
+  RS_CUDA(cudaMemcpyAsync(toff.p + n, &total, sizeof(int), cudaMemcpyHostToDevice, s));   // (pageable: copied at once)
   tci.ensure(std::max(total, 1)); tv.ensure(std::max(total, 1));
   C.n = n; C.m = B.m;
   C.rp.ensure(n + 1);
@@ -544,8 +560,16 @@ static void spgemm(const csr_dev<double> &A, const csr_dev<double> &B, csr_dev<d
   if (mx1 > 0) {                                       // rows of A longer than SPG_KMAX
     unsigned grid = (unsigned)std::min<size_t>((n + warps - 1) / warps, 152 * 64);
     k_spgemm<true><<<grid, warps * 32, smem, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, toff.p, clen.p,
-                                                  tci.p, tv.p, cap);
+                                                  tci.p, tv.p, cap, -1, nullptr);
     RS_LAUNCHED(1);
+    if (cap_all > cap) {                               // rows beyond the shared-memory capacity
+      static thread_local dbuf<unsigned long long> gs;
+      const int gw = 4, gblocks = 64;
+      gs.ensure((size_t)gblocks * gw * 2 * cap_all);
+      k_spgemm<true><<<gblocks, gw * 32, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, toff.p, clen.p,
+                                                 tci.p, tv.p, cap_all, cap, gs.p);
+      RS_LAUNCHED(1);
+    }
   }
   RS_CHECK_LAUNCH();
   C.nnz = rs_scan(clen.p, C.rp.p, n, s);
