@@ -337,15 +337,29 @@ sim_status sim_kernel_time(sim_ls_t ls, int which, long long *launches, double *
 
 /* Launch mode of the FGMRES Arnoldi step (Algorithm 1's inner loop: CPR
  * application, SpMV, Gram-Schmidt, Givens update).  The paper has no
- * counterpart: it concerns only how the kernels are issued.  on = 1 (the
- * default): each step is one replay of a CUDA graph recorded at the first
- * solve after a setup, whose kernels read the step index from device memory;
- * on = 0: every kernel is launched on its own.  Both issue the same kernels
- * on the same data, so results are bit-identical; kernel timers work in both
- * (graph brackets are event nodes).  Subdomains too large for the shared-
- * memory RAS kernel always use separate launches.  Errors: SIM_ERR_ARG for a
- * NULL handle. */
-sim_status sim_ls_step_graph(sim_ls_t ls, int on);
+ * counterpart: it concerns only how the kernels are issued.
+ *   mode = 2: a whole restart cycle runs from one launch of a CUDA graph
+ *     whose WHILE node replays the recorded step and, after each step,
+ *     decides on the device whether to go on (residual estimate above
+ *     tol * ||b||, h_{j+1,j} nonzero and finite, steps left in the cycle and
+ *     in max_lin); the host waits once per cycle.
+ *   mode = 1 (the default): each step is one replay of a CUDA graph
+ *     recorded at the first solve after a setup, whose kernels read the step
+ *     index from device memory; the host waits after every step and takes
+ *     the same decision.
+ *   mode = 0: every kernel is launched on its own.
+ * All modes issue the same kernels on the same data, so results are
+ * bit-identical.  Kernel timers work in modes 0 and 1 (graph brackets are
+ * event nodes); with timers on, mode 2 runs as mode 1.  Subdomains too large
+ * for the shared-memory RAS kernel always use separate launches; a driver
+ * that cannot record the WHILE node leaves mode 1 in use.  The mode the last
+ * FGMRES solve actually used is returned by sim_ls_graph_mode (-1 before the
+ * first solve).  On the 1M-cell channelised case mode 2 measured about 1%
+ * slower per time step than mode 1 (the body relaunch inside the WHILE node
+ * costs more than the host's wait and relaunch), hence the default.
+ * Errors: SIM_ERR_ARG for a NULL handle or a mode outside 0..2. */
+sim_status sim_ls_step_graph(sim_ls_t ls, int mode);
+sim_status sim_ls_graph_mode(sim_ls_t ls, int *mode);
 
 /* ---- ensembles: many independent models advanced together ----
  *

@@ -128,6 +128,7 @@ def lib():
             "sim_ls_residual_norm_noalloc": (I, [P, P, P]),
             "sim_kernel_timer": (I, [P, C.c_uint]),
             "sim_ls_step_graph": (I, [P, C.c_int]),
+            "sim_ls_graph_mode": (I, [P, C.POINTER(C.c_int)]),
             "sim_kernel_time": (I, [P, I, C.POINTER(C.c_longlong), C.POINTER(D)]),
             "sim_batch_create": (I, [C.POINTER(P), I, C.POINTER(Grid), C.POINTER(Rock), C.POINTER(Fluid),
                                      C.POINTER(C.POINTER(Well)), C.POINTER(I), C.POINTER(Options), I]),
@@ -329,10 +330,19 @@ class LinearSystem:
             mask |= 1 << f
         _check(self._L.sim_kernel_timer(self.h, mask))
 
-    def step_graph(self, on):
-        """Issue each Arnoldi step as one CUDA graph replay (True, the
-        default) or as separate kernel launches (False); same results."""
-        _check(self._L.sim_ls_step_graph(self.h, 1 if on else 0))
+    def step_graph(self, mode):
+        """Launch mode of the Arnoldi steps: 2 a whole restart cycle from
+        one graph launch with a device-side WHILE node, 1 (or True, the
+        default) one graph replay per step, 0 (or False) separate kernel
+        launches; same results in all three."""
+        mode = 1 if mode is True else 0 if mode is False else int(mode)
+        _check(self._L.sim_ls_step_graph(self.h, mode))
+
+    def graph_mode(self):
+        """The launch mode the last FGMRES solve used (-1 before any)."""
+        m = C.c_int()
+        _check(self._L.sim_ls_graph_mode(self.h, C.byref(m)))
+        return m.value
 
     def kernel_time(self, which):
         n, ms = C.c_longlong(), C.c_double()

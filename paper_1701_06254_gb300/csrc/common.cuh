@@ -70,6 +70,9 @@ inline unsigned grid_for(size_t n, int bs) { size_t g = (n + bs - 1) / bs; retur
 // pdl_wait() before it touches memory: the wait returns once the previous
 // kernel has completed and its writes are visible (at once when there is no
 // such kernel).  pdl_trigger() lets the next kernel be scheduled early.
+// rs_pdl_off (per host thread) makes launch_pdl an ordinary launch: used
+// while recording a graph body that cannot hold programmatic edges.
+inline thread_local bool rs_pdl_off = false;
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 template <typename... KArgs, typename... Args>
@@ -80,7 +83,7 @@ inline void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, si
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at; cfg.numAttrs = 1;
+  cfg.attrs = at; cfg.numAttrs = rs_pdl_off ? 0 : 1;
   RS_CUDA(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
 }
 
@@ -223,8 +226,12 @@ struct sim_ls_s {
   dbuf<float> x32a, x32b, x32c; // CPR work (FP32)
   double *hpin = nullptr;       // pinned host scalars: 4 per Arnoldi step (estimate, h_{j+1,j}, second pass)
   // one Arnoldi step as a CUDA graph (recorded after each setup)
-  bool graph_on = true;
+  int graph_mode = 1;           // 0 separate launches, 1 a graph per Arnoldi step, 2 a device-side loop
   cudaGraphExec_t it_exec = nullptr;
+  cudaGraphExec_t loop_exec = nullptr;   // the Arnoldi steps of a cycle in a graph WHILE node
+  dbuf<double> loopd;           // loop parameters and results: threshold, step cap, steps done, non-finite flag
+  int loop_state = 0;           // device-side loop: 0 not built, 1 built with programmatic edges, 2 without, -1 unavailable
+  int last_mode = -1;           // launch mode the last FGMRES solve used (0, 1, 2)
   long long it_launches = 0;
   const void *it_sig[10] = {};   // buffers, restart length and precision it was recorded with
   cudaStream_t cap = nullptr;
@@ -247,6 +254,8 @@ struct sim_ls_s {
   std::vector<int> gev_fam;
   void drop_graph() {
     if (it_exec) { cudaGraphExecDestroy(it_exec); it_exec = nullptr; }
+    if (loop_exec) { cudaGraphExecDestroy(loop_exec); loop_exec = nullptr; }
+    if (loop_state > 0) loop_state = 0;
     for (auto e : gev) cudaEventDestroy(e);
     gev.clear(); gev_fam.clear();
   }

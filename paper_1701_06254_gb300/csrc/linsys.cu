@@ -1129,6 +1129,22 @@ static int ls_solve_bicgstab(sim_ls_s *ls, double tol, int *its_out, double *rel
   return rc;
 }
 
+// End of one Arnoldi step inside the device-side loop: continue the cycle
+// while the step's residual estimate is finite and above the threshold, its
+// h_{j+1,j} is not zero and the cycle has steps left (at most the restart
+// length, so the loop always ends); record the steps done and whether a
+// non-finite value appeared.  lp = {threshold, step cap, steps done, flag}.
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const int *jd, const double *hp, double *lp) {
+  int j = *jd - 1;                                   // the step just done (jd already advanced)
+  double est = hp[4 * j], hn = hp[4 * j + 1];
+  bool bad = !isfinite(est) || !isfinite(hn);
+  bool more = !bad && est > lp[0] && (double)(j + 1) < lp[1] && hn != 0.0;
+  lp[2] = (double)(j + 1);
+  lp[3] = bad ? 1.0 : 0.0;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+__global__ void k_loop_params(double *lp, double thr, double cap) { lp[0] = thr; lp[1] = cap; lp[2] = 0.0; lp[3] = 0.0; }
+
 int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
   if (ls->o.krylov == SIM_KRYLOV_BICGSTAB) return ls_solve_bicgstab(ls, tol, its_out, relres, x0);
   cudaStream_t s = ls->st;
@@ -1237,25 +1253,15 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
   // graph, read after each replay.
   // The recording holds raw pointers: record again whenever one of the
   // solver's own buffers, the restart length or the precision has changed.
-  bool use_graph = ls->graph_on && ls->ras.smem_path;
+  bool use_graph = ls->graph_mode > 0 && ls->ras.smem_path;
+  // the device-side loop needs a body without timer event nodes
+  bool use_loop = use_graph && ls->graph_mode == 2 && ls->timer_mask == 0;
   const void *sig[10] = {ls->V.p, ls->Z.p, ls->Z32.p, ls->w.p, ls->partial.p, ls->hbuf.p,
                          (const void *)(size_t)m, (const void *)(size_t)ls->o.precision,
                          (const void *)(size_t)ls->timer_mask, ls->w2.p};
   if (use_graph && ls->it_exec && memcmp(sig, ls->it_sig, sizeof(sig)) != 0) ls->drop_graph();
-  if (use_graph && !ls->it_exec) {
-    ls->drop_graph();
-    ortho_attr();
-    ls->jd.ensure(1);
-    if (df) ls->vcur32.ensure(nu); else ls->vcur.ensure(nu);
-    if (mixed) ls->zcur32.ensure(nu); else ls->zcur64.ensure(nu);
-    if (!ls->cap) RS_CUDA(cudaStreamCreateWithFlags(&ls->cap, cudaStreamNonBlocking));
-    cudaStream_t keep = ls->st;
-    cudaGraph_t g = nullptr;
-    RS_CUDA(cudaStreamBeginCapture(ls->cap, cudaStreamCaptureModeRelaxed));
-    ls->st = ls->cap;
-    ls->capturing = true;
-    try {
-      cudaStream_t c = ls->cap;
+  // one Arnoldi step recorded on stream c (the capture stream)
+  auto record_step = [&](cudaStream_t c) {
       const int *jd = ls->jd.p;
       if (df) {
         k_basis_get_df<<<grid_for(nu, 256), 256, 0, c>>>(nu, V32, jd, ls->vcur32.p);
@@ -1285,6 +1291,21 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
       k_step_inc<<<1, 1, 0, c>>>(ls->jd.p);
       RS_LAUNCHED(3);
       RS_CHECK_LAUNCH();
+  };
+  if (use_graph && !ls->it_exec) {
+    ls->drop_graph();
+    ortho_attr();
+    ls->jd.ensure(1);
+    if (df) ls->vcur32.ensure(nu); else ls->vcur.ensure(nu);
+    if (mixed) ls->zcur32.ensure(nu); else ls->zcur64.ensure(nu);
+    if (!ls->cap) RS_CUDA(cudaStreamCreateWithFlags(&ls->cap, cudaStreamNonBlocking));
+    cudaStream_t keep = ls->st;
+    cudaGraph_t g = nullptr;
+    RS_CUDA(cudaStreamBeginCapture(ls->cap, cudaStreamCaptureModeRelaxed));
+    ls->st = ls->cap;
+    ls->capturing = true;
+    try {
+      record_step(ls->cap);
     } catch (...) {
       ls->st = keep; ls->capturing = false;
       cudaStreamEndCapture(ls->cap, &g);
@@ -1314,13 +1335,83 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
     ls->it_launches = nk;
     rs_launches -= (unsigned long long)nk;             // recorded, not launched
   }
+  // The same step as the body of a graph WHILE node, ended by k_loop_cond:
+  // a whole cycle of Arnoldi steps runs from one launch, and the host waits
+  // once per cycle instead of once per step.
+  if (use_loop && !ls->loop_exec && ls->loop_state == 0) {
+    // first with the kernels' programmatic-launch edges, else with plain
+    // edges; a driver that records neither leaves the per-step graph in use
+    ls->loopd.ensure(4);
+    cudaStream_t keep = ls->st;
+    for (int attempt = 0; attempt < 2 && !ls->loop_exec; attempt++) {
+      cudaGraph_t g = nullptr;
+      bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+      rs_pdl_off = attempt == 1;
+      try {
+        cudaGraphConditionalHandle hc;
+        cudaGraphNodeParams np = {};
+        cudaGraphNode_t node;
+        ok = ok && cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+        if (ok) {
+          np.type = cudaGraphNodeTypeConditional;
+          np.conditional.handle = hc;
+          np.conditional.type = cudaGraphCondTypeWhile;
+          np.conditional.size = 1;
+          ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess;
+        }
+        ok = ok && cudaStreamBeginCaptureToGraph(ls->cap, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                 cudaStreamCaptureModeRelaxed) == cudaSuccess;
+        if (ok) {
+          ls->st = ls->cap;
+          ls->capturing = true;
+          try {
+            record_step(ls->cap);
+            k_loop_cond<<<1, 1, 0, ls->cap>>>(hc, ls->jd.p, hp_dev, ls->loopd.p);
+            ok = cudaGetLastError() == cudaSuccess;
+          } catch (...) {
+            ok = false;
+          }
+          ls->st = keep;
+          ls->capturing = false;
+          cudaGraph_t gb = nullptr;
+          ok = cudaStreamEndCapture(ls->cap, &gb) == cudaSuccess && ok;
+        }
+        ok = ok && cudaGraphInstantiate(&ls->loop_exec, g, 0) == cudaSuccess;
+      } catch (...) {
+        ok = false;
+      }
+      rs_pdl_off = false;
+      ls->st = keep; ls->capturing = false;
+      if (g) cudaGraphDestroy(g);
+      if (!ok) {
+        if (ls->loop_exec) cudaGraphExecDestroy(ls->loop_exec);
+        ls->loop_exec = nullptr;
+        (void)cudaGetLastError();                     // the failed recording's error is not sticky
+      }
+      rs_launches -= (unsigned long long)ls->it_launches;   // recorded, not launched
+      ls->loop_state = ok ? attempt + 1 : -1;
+    }
+  }
+  if (use_loop && !ls->loop_exec) use_loop = false;
+  ls->last_mode = use_loop ? 2 : use_graph ? 1 : 0;
   for (;;) {
     if (df) k_start_df<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->r.p, beta, V32, G, m);
     else k_start<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->r.p, beta, ls->V.p, G, m);
     RS_LAUNCHED(1);
     int jend = 0;
     if (use_graph) RS_CUDA(cudaMemsetAsync(ls->jd.p, 0, sizeof(int), s));
-    for (int j = 0; j < m; j++) {
+    if (use_loop) {
+      // the cycle on the device: at most min(m, max_lin - its) steps
+      k_loop_params<<<1, 1, 0, s>>>(ls->loopd.p, tol * bn, (double)std::min(m, maxit - its));
+      RS_CUDA(cudaGraphLaunch(ls->loop_exec, s));
+      std::vector<double> lo = d2h(ls->loopd.p + 2, 2, s);
+      if (ls->errw[0]) RS_FAIL(SIM_ERR_TIMEOUT, "RAS apply: bulk copy wait gave up (code %d)", ls->errw[0]);
+      jend = (int)lo[0];
+      its += jend;
+      RS_LAUNCHED(1 + (long long)jend * (ls->it_launches + 1));
+      if (lo[1] != 0.0) { *its_out = its; *relres = NAN; return 2; }
+    }
+    for (int j = 0; j < m && !use_loop; j++) {
       if (use_graph) {
         RS_CUDA(cudaGraphLaunch(ls->it_exec, s));
         RS_LAUNCHED(ls->it_launches);

@@ -1323,11 +1323,18 @@ extern "C" sim_status sim_kernel_timer(sim_ls_t ls, unsigned mask) {
   for (int k = 0; k < SIM_T_NFAMILIES; k++) { ls->timer_launches[k] = 0; ls->timer_ms[k] = 0; }
   ABI_END
 }
+extern "C" sim_status sim_ls_graph_mode(sim_ls_t ls, int *mode) {
+  ABI_BEGIN
+  if (!ls || !mode) RS_FAIL(SIM_ERR_ARG, "NULL argument");
+  *mode = ls->last_mode;
+  ABI_END
+}
 extern "C" sim_status sim_ls_step_graph(sim_ls_t ls, int on) {
   ABI_BEGIN
   if (!ls) RS_FAIL(SIM_ERR_ARG, "NULL handle");
-  ls->graph_on = on != 0;
-  if (!ls->graph_on) ls->drop_graph();
+  if (on < 0 || on > 2) RS_FAIL(SIM_ERR_ARG, "sim_ls_step_graph: mode %d (0, 1 or 2)", on);
+  ls->graph_mode = on;
+  ls->drop_graph();
   ABI_END
 }
 extern "C" sim_status sim_kernel_time(sim_ls_t ls, int which, long long *launches, double *ms) {
