@@ -7,7 +7,8 @@
 //                 or extended+i (distance two, option interp),
 //              R = P^T, Galerkin A_c = R (A P)
 //   cycle      V(1,1), l1-Jacobi smoothing, zero initial guess
-//   coarsest   dense inverse (FP64) from an LU with partial pivoting
+//   coarsest   dense inverse (FP64): Gauss-Jordan with partial pivoting in
+//              shared memory (n <= 128), else an LU with partial pivoting
 // Setup runs in FP64 with explicit round-to-nearest operations in a fixed
 // order, so the C/F split, P and every coarse operator are bit-identical to
 // a plain sequential evaluation of the same formulas on the same input.
@@ -48,18 +49,28 @@ __global__ void k_tpos_warp(int n, const int *rp, const int *ci, int *tpos, int 
   }
 }
 
+// Comparisons of doubles taken on integers: dkey orders finite doubles as
+// IEEE comparison does (both zeros map to 0; dkey(-x) = -dkey(x)), so a
+// comparison decides the same as on the doubles while keeping the FP64
+// pipe (a small fraction of the FP32 rate on this GPU) for arithmetic.
+__device__ __forceinline__ long long dkey(double x) {
+  long long b = __double_as_longlong(x), m = b & 0x7fffffffffffffffLL;
+  return b < 0 ? -m : m;
+}
+
 __global__ void k_strength(int n, const int *rp, const int *ci, const double *v, double theta, uint8_t *S) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  bool have = false; double mx = 0.0;
+  bool have = false; double mx = 0.0; long long mxk = 0;
   for (int q = rp[i]; q < rp[i + 1]; q++) {
     if (ci[q] == i) continue;
-    double t = -v[q];
-    if (!have || t > mx) { mx = t; have = true; }
+    long long tk = -dkey(v[q]);                     // key of t = -a_iq
+    if (!have || tk > mxk) { mx = -v[q]; mxk = tk; have = true; }
   }
-  double thr = mul_rn(theta, mx);
+  long long thrk = dkey(mul_rn(theta, mx));
+  bool any = have && mxk > 0;                       // max_k (-a_ik) > 0
   for (int q = rp[i]; q < rp[i + 1]; q++)
-    S[q] = (uint8_t)(have && mx > 0.0 && ci[q] != i && -v[q] >= thr);
+    S[q] = (uint8_t)(any && ci[q] != i && -dkey(v[q]) >= thrk);
 }
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
@@ -92,11 +103,11 @@ __global__ void k_pmis_select(int n, const int *rp, const int *ci, const uint8_t
   int8_t best = 0;
   if (cf[i] == 0) {
     best = 1;
-    double wi = w[i];
+    long long wi = __double_as_longlong(w[i]);      // weights are >= +0: their bits order them
     for (int q = rp[i]; q < rp[i + 1] && best; q++) {
       int j = ci[q];
       if (j == i || !(S[q] || S[tpos[q]]) || cf[j] != 0) continue;
-      double wj = w[j];
+      long long wj = __double_as_longlong(w[j]);
       if (wj > wi || (wj == wi && j < i)) best = 0;
     }
   }
@@ -129,11 +140,11 @@ __global__ void k_pmis_select_lanes(int n, const int *rp, const int *ci, const u
   int i = g < n ? g : n - 1;
   bool cand = cf[i] == 0, beaten = false;
   if (cand) {
-    double wi = w[i];
+    long long wi = __double_as_longlong(w[i]);      // weights are >= +0: their bits order them
     for (int q = rp[i] + k; q < rp[i + 1]; q += L) {
       int j = ci[q];
       if (j == i || !(S[q] || S[tpos[q]]) || cf[j] != 0) continue;
-      double wj = w[j];
+      long long wj = __double_as_longlong(w[j]);
       if (wj > wi || (wj == wi && j < i)) { beaten = true; break; }
     }
   }
@@ -184,23 +195,47 @@ __global__ void k_interp_count(int n, const int *rp, const int *ci, const uint8_
   len[i] = c;
 }
 
+// pcap: capacity of pci / pv (a row that would pass it sets *err and is
+// skipped; nnz(P) <= nnz(A) makes that impossible for direct interpolation)
 __global__ void k_interp_fill(int n, const int *rp, const int *ci, const double *v, const uint8_t *S,
-                              const int8_t *cf, const int *cidx, const int *prp, int *pci, double *pv) {
+                              const int8_t *cf, const int *cidx, const int *prp, int *pci, double *pv, int pcap,
+                              int *err) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int o = prp[i];
+  if (prp[i + 1] > pcap) { atomicExch(err, 1); return; }
   if (cf[i] == 1) { pci[o] = cidx[i]; pv[o] = 1.0; return; }
   if (prp[i + 1] == o) return;
+  // sums in the row's column order: sneg / spos (one FP64 add per entry,
+  // its target chosen by the sign) while the strong C entries are listed;
+  // then snegc and the weights over that list only
+  const int MAXC = 32;
+  int m = prp[i + 1] - o, qs[MAXC], nq = 0;
   double sneg = 0.0, spos = 0.0, snegc = 0.0, aii = 0.0;
   for (int q = rp[i]; q < rp[i + 1]; q++) {
     double a = v[q];
-    if (ci[q] == i) { aii = a; continue; }
-    if (a < 0.0) sneg = add_rn(sneg, a); else spos = add_rn(spos, a);
+    int j = ci[q];
+    if (S[q] && cf[j] == 1 && nq < MAXC) qs[nq++] = q;
+    if (j == i) { aii = a; continue; }
+    bool neg = dkey(a) < 0;
+    double acc = add_rn(neg ? sneg : spos, a);
+    if (neg) sneg = acc; else spos = acc;
   }
-  for (int q = rp[i]; q < rp[i + 1]; q++) if (S[q] && cf[ci[q]] == 1) snegc = add_rn(snegc, v[q]);
+  if (m <= MAXC) {
+    for (int t = 0; t < m; t++) snegc = add_rn(snegc, v[qs[t]]);
+  } else {
+    for (int q = rp[i]; q < rp[i + 1]; q++) if (S[q] && cf[ci[q]] == 1) snegc = add_rn(snegc, v[q]);
+  }
   double dg = add_rn(aii, spos), alpha = div_rn(sneg, snegc);
-  for (int q = rp[i]; q < rp[i + 1]; q++)
-    if (S[q] && cf[ci[q]] == 1) { pci[o] = cidx[ci[q]]; pv[o++] = div_rn(-mul_rn(alpha, v[q]), dg); }
+  if (m <= MAXC) {
+    for (int t = 0; t < m; t++) {
+      int q = qs[t];
+      pci[o + t] = cidx[ci[q]]; pv[o + t] = div_rn(-mul_rn(alpha, v[q]), dg);
+    }
+  } else {
+    for (int q = rp[i]; q < rp[i + 1]; q++)
+      if (S[q] && cf[ci[q]] == 1) { pci[o] = cidx[ci[q]]; pv[o++] = div_rn(-mul_rn(alpha, v[q]), dg); }
+  }
 }
 
 // --------------------------------------------- extended+i interpolation ---
@@ -372,24 +407,24 @@ __global__ void k_sort_rows_warp(int n, const int *rp, int *ci, double *v) {
 }
 
 // -------------------------------------------------------------- SpGEMM ----
-// C = A B.  Rows of A with at most SPG_KMAX entries: k_spgemm_merge.  Longer
-// rows, one warp per row of C: expand every product A_ik B_kj with its
-// sequence number (row of A ascending, then row of B ascending), sort the
-// (column, sequence) keys in shared memory, and sum each column's products
-// in sequence order starting from 0.  One pass: each row is written at the
-// offset of its product count (an upper bound of its length) into a scratch
-// array, then the rows are packed.
+// C = A B, each column of a row of C the sum of its products A_ik B_kj in
+// the order of k (the row of A's column order), starting from 0.  Rows of A
+// with at most SPG_KMAX entries and at most SPG_MERGE_P products:
+// k_spgemm_merge (one thread per row); the others: k_spgemm_hash (one warp
+// per row).  One pass: each row is written at the offset of its product
+// count (an upper bound of its length) into a scratch array, then the rows
+// are packed.
 // products per row of C; mx = 1 + the most products of a row that the
-// sorting kernel handles (rows with more than SPG_KMAX entries in A), 0 if
-// there is none
+// hash kernel handles, 0 if there is none
 #define SPG_KMAX 8
+#define SPG_MERGE_P 96
 __global__ void k_row_products(int n, const int *arp, const int *aci, const int *brp, int *prod, int *mx) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int s = 0;
   for (int q = arp[i]; q < arp[i + 1]; q++) { int k = aci[q]; s += brp[k + 1] - brp[k]; }
   prod[i] = s;
-  if (arp[i + 1] - arp[i] > SPG_KMAX) atomicMax(mx, s + 1);   // + 1: "a long row exists" even with 0 products
+  if (arp[i + 1] - arp[i] > SPG_KMAX || s > SPG_MERGE_P) atomicMax(mx, s + 1);   // + 1: "a hash row exists" even with 0 products
 }
 // C row i = scratch[toff[i] .. toff[i] + clen[i]), eight lanes per row
 __global__ void k_pack_rows(int n, const int *toff, const int *clen, const int *crp, const int *tci, const double *tv,
@@ -400,15 +435,15 @@ __global__ void k_pack_rows(int n, const int *toff, const int *clen, const int *
   for (int t = lane; t < len; t += 8) { cci[b + t] = tci[a + t]; cv[b + t] = tv[a + t]; }
 }
 
-// C = A B for the rows of A with at most K entries, one thread per row: a
-// k-way merge of the k rows of B that the row of A selects (each sorted by
-// column, its head kept in registers).  The smallest head column is the next
-// column of C; its products are summed in the order of the row of A,
-// starting from 0, which is the order of the sorted expansion below, so both
-// kernels give the same bits.  Only short rows of A take this path (the
-// finest level's stencil rows and its restriction): a thread walks its row
-// of C serially, which loses to the warp-per-row sort once rows of A and C
-// grow (measured on the coarser levels of the 1M-cell hierarchy).
+// C = A B for the rows of A with at most K entries and at most SPG_MERGE_P
+// products, one thread per row: a k-way merge of the k rows of B that the
+// row of A selects (each sorted by column, its head kept in registers).  The
+// smallest head column is the next column of C; its products are summed in
+// the order of the row of A, starting from 0, as in the hash kernel below,
+// so both kernels give the same bits.  Only short rows take this path (the
+// finest level's stencil rows and most of its restriction): a thread walks
+// its row of C serially, which loses to a warp per row once rows grow
+// (measured on the coarser levels of the 1M-cell hierarchy).
 template <int K>
 __global__ void __launch_bounds__(128) k_spgemm_merge(int n, const int *arp, const int *aci, const double *av,
                                                       const int *brp, const int *bci, const double *bv,
@@ -416,7 +451,7 @@ __global__ void __launch_bounds__(128) k_spgemm_merge(int n, const int *arp, con
   int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
   int a0 = arp[row], k = arp[row + 1] - a0;
-  if (k > K) return;
+  if (k > K || toff[row + 1] - toff[row] > SPG_MERGE_P) return;
   int pos[K], end[K], col[K];
   double a[K];
 #pragma unroll
@@ -448,137 +483,188 @@ __global__ void __launch_bounds__(128) k_spgemm_merge(int n, const int *arp, con
   clen[row] = cnt;
 }
 
-// Rows of A longer than SPG_KMAX, one warp per row.  The products of a row
-// (at most `cap` of them: rows with more are left to the launch with the
-// larger capacity) are expanded with (column, sequence) keys, sorted, and
-// each column's products summed in sequence order.  The keys and values sit
-// in shared memory, or (gscratch, for the rare rows beyond what shared
-// memory holds) in a global scratch area of cap entries per warp.  lo_cap:
-// rows with at most lo_cap products belong to the other launch.
-template <bool NUMERIC>
-__global__ void k_spgemm(int n, const int *arp, const int *aci, const double *av, const int *brp, const int *bci,
-                         const double *bv, const int *crp, int *clen, int *cci, double *cv, int cap, int lo_cap,
-                         unsigned long long *gscratch) {
-  extern __shared__ unsigned long long sm_keys[];
+// Rows that the merge kernel leaves (more than SPG_KMAX entries in A, or
+// more than SPG_MERGE_P products), one warp per row of C.  The products are
+// taken in sequence order (row of A ascending, then row of B ascending), 32
+// at a time; each lane claims its column's slot in an open-addressing hash
+// table (compare-and-swap on the key, linear probing; the table has at
+// least as many slots as the row has products, so a probe always ends), and
+// the lanes of one chunk that hit the same slot are summed by the lowest of
+// them in lane order.  So each column's products are summed in sequence
+// order starting from 0, as in the merge kernel.  The occupied slots are
+// then compacted, sorted by column (bitonic; the columns are distinct) and
+// written at the row's scratch offset.  The table sits in shared memory, or
+// (gscratch, for the rare rows beyond what shared memory holds) in a global
+// scratch area; tcap slots per warp.  Rows with at most lo_p products
+// belong to the other launch.
+__host__ __device__ constexpr size_t spg_warp_doubles(int tcap) {
+  // vals[tcap], seg_a[32], prodbuf[32] (doubles), keys[tcap], seg_off[33], seg_k[32] (ints)
+  return (size_t)tcap + 64 + ((size_t)tcap + 65 + 1) / 2;
+}
+__global__ void __launch_bounds__(256) k_spgemm_hash(int n, const int *arp, const int *aci, const double *av,
+                                                     const int *brp, const int *bci, const double *bv,
+                                                     const int *toff, int *clen, int *cci, double *cv, int tcap,
+                                                     int lo_p, double *gscratch) {
+  extern __shared__ double sm_hash[];
   const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned long long *kbase = gscratch ? gscratch + (size_t)blockIdx.x * warps * 2 * cap : sm_keys;
-  unsigned long long *keys = kbase + (size_t)wid * cap;
-  double *vals = reinterpret_cast<double *>(kbase + (size_t)warps * cap) + (size_t)wid * cap;
   const unsigned FULL = 0xffffffffu;
+  const size_t wd = spg_warp_doubles(tcap);
+  double *base = gscratch ? gscratch + ((size_t)blockIdx.x * warps + wid) * wd : sm_hash + (size_t)wid * wd;
+  double *vals = base, *seg_a = base + tcap, *prodbuf = seg_a + 32;
+  int *keys = reinterpret_cast<int *>(prodbuf + 32), *seg_off = keys + tcap, *seg_k = seg_off + 33;
+  volatile int *vkeys = keys;
   for (int row = blockIdx.x * warps + wid; row < n; row += gridDim.x * warps) {
-    int a0 = arp[row], a1 = arp[row + 1], base = 0;
-    if (a1 - a0 <= SPG_KMAX) continue;               // the merge kernel's row
-    {
-      int np_ = crp[row + 1] - crp[row];             // this row's products (scratch offsets)
-      if (np_ > cap || np_ <= lo_cap) continue;      // the other launch's row
-    }
+    int a0 = arp[row], a1 = arp[row + 1], out = toff[row], p = toff[row + 1] - out;
+    if (a1 - a0 <= SPG_KMAX && p <= SPG_MERGE_P) continue;    // the merge kernel's row
+    if (p > tcap || p <= lo_p) continue;                      // the other launch's row
+    int T = 32;
+    while (T < p) T <<= 1;
+    for (int i = lane; i < T; i += 32) { keys[i] = -1; vals[i] = 0.0; }
+    __syncwarp();
     for (int q0 = a0; q0 < a1; q0 += 32) {
       int q = q0 + lane, len = 0, k = 0;
-      if (q < a1) { k = aci[q]; len = brp[k + 1] - brp[k]; }
+      double a = 0.0;
+      if (q < a1) { k = aci[q]; len = brp[k + 1] - brp[k]; a = av[q]; }
       int incl = len;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) { int y = __shfl_up_sync(FULL, incl, o); if (lane >= o) incl += y; }
-      int tot = __shfl_sync(FULL, incl, 31), off = base + incl - len;
-      if (q < a1) {
-        double a = NUMERIC ? av[q] : 0.0;
-        int b0 = brp[k];
-        for (int r = 0; r < len; r++) {
-          int seq = off + r;
-          keys[seq] = ((unsigned long long)(unsigned)bci[b0 + r] << 32) | (unsigned)seq;
-          if (NUMERIC) vals[seq] = mul_rn(a, bv[b0 + r]);
+      int tot = __shfl_sync(FULL, incl, 31);
+      seg_off[lane] = incl - len; seg_k[lane] = k; seg_a[lane] = a;
+      __syncwarp();
+      int nseg = min(32, a1 - q0);
+      for (int t0 = 0; t0 < tot; t0 += 32) {
+        int t = t0 + lane, slot = -1 - lane;
+        double prod = 0.0;
+        if (t < tot) {
+          int lo = 0, hi = nseg - 1;                          // last segment starting at or before t
+          while (lo < hi) { int md = (lo + hi + 1) >> 1; if (seg_off[md] <= t) lo = md; else hi = md - 1; }
+          int b = brp[seg_k[lo]] + (t - seg_off[lo]), c = bci[b];
+          prod = mul_rn(seg_a[lo], bv[b]);
+          int h = (int)(((unsigned)c * 0x9E3779B1u) & (unsigned)(T - 1));
+          for (int it = 0; it < T; it++) {
+            int key = vkeys[h];
+            if (key == c) break;
+            if (key == -1) {
+              int old = atomicCAS(&keys[h], -1, c);
+              if (old == -1 || old == c) break;
+            }
+            h = (h + 1) & (T - 1);
+          }
+          slot = h;
         }
+        unsigned grp = __match_any_sync(FULL, slot);
+        prodbuf[lane] = prod;
+        __syncwarp();
+        if (t < tot && lane == __ffs(grp) - 1) {
+          double s = vals[slot];
+          for (unsigned m = grp; m; m &= m - 1) s = add_rn(s, prodbuf[__ffs(m) - 1]);
+          vals[slot] = s;
+        }
+        __syncwarp();
       }
-      base += tot;
     }
-    int m = 1;
-    while (m < base) m <<= 1;
-    for (int i = base + lane; i < m; i += 32) keys[i] = ~0ull;
+    // compact the occupied slots to the front of the table
+    int u = 0;
+    for (int i0 = 0; i0 < T; i0 += 32) {
+      int key = keys[i0 + lane];
+      double v = vals[i0 + lane];
+      unsigned mask = __ballot_sync(FULL, key >= 0);
+      int pre = __popc(mask & ((1u << lane) - 1u));
+      __syncwarp();
+      if (key >= 0) { keys[u + pre] = key; vals[u + pre] = v; }
+      u += __popc(mask);
+      __syncwarp();
+    }
+    int M = 1;
+    while (M < u) M <<= 1;
+    for (int i = u + lane; i < M; i += 32) keys[i] = INT_MAX;
     __syncwarp();
-    for (int k = 2; k <= m; k <<= 1)
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int i = lane; i < m; i += 32) {
+    for (int kk = 2; kk <= M; kk <<= 1)
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        for (int i = lane; i < M; i += 32) {
           int ixj = i ^ j;
           if (ixj > i) {
-            unsigned long long x = keys[i], y = keys[ixj];
-            bool up = (i & k) == 0;
-            if ((x > y) == up) { keys[i] = y; keys[ixj] = x; }
+            int x = keys[i], y = keys[ixj];
+            bool up = (i & kk) == 0;
+            if ((x > y) == up) {
+              keys[i] = y; keys[ixj] = x;
+              double w = vals[i]; vals[i] = vals[ixj]; vals[ixj] = w;
+            }
           }
         }
         __syncwarp();
       }
-    int running = 0, out = NUMERIC ? crp[row] : 0;
-    for (int c0 = 0; c0 < base; c0 += 32) {
-      int i = c0 + lane;
-      unsigned col = i < base ? (unsigned)(keys[i] >> 32) : 0u;
-      bool head = i < base && (i == 0 || (unsigned)(keys[i - 1] >> 32) != col);
-      unsigned mask = __ballot_sync(FULL, head);
-      if (NUMERIC && head) {
-        int pre = __popc(mask & ((1u << lane) - 1u));
-        double s = 0.0;
-        for (int t = i; t < base && (unsigned)(keys[t] >> 32) == col; t++) s = add_rn(s, vals[(unsigned)keys[t]]);
-        cci[out + running + pre] = (int)col; cv[out + running + pre] = s;
-      }
-      running += __popc(mask);
-    }
-    if (clen && lane == 0) clen[row] = running;
+    for (int i = lane; i < u; i += 32) { cci[out + i] = keys[i]; cv[out + i] = vals[i]; }
+    if (lane == 0) clen[row] = u;
     __syncwarp();
   }
 }
 
-static void spgemm(const csr_dev<double> &A, const csr_dev<double> &B, csr_dev<double> &C, dbuf<int> &flag,
-                   cudaStream_t s) {
-  static thread_local dbuf<int> toff, clen, tci;
-  static thread_local dbuf<double> tv;
+// SpGEMM C = A B in two phases with one host wait between them.
+// spgemm_count: products per row of C (scratch offsets, toff) and their
+// total in *tot, the long-row marker (1 + the most products of a row that
+// the sorting kernel handles, 0 if none) in *mx (which must be 0 before);
+// no host wait.  spgemm_fill: given those two values on the host, the
+// numeric product into scratch, the row pointers of C (C.rp[n] and *nnz =
+// nnz(C) on the device) and the packed rows; C's arrays are sized by the
+// product total, an upper bound of nnz(C), so no further wait is needed.
+struct spg_scratch { dbuf<int> toff, clen, tci; dbuf<double> tv, gs; };
+static spg_scratch &spg() { static thread_local spg_scratch z; return z; }
+
+static void spgemm_count(const csr_dev<double> &A, const csr_dev<double> &B, int *tot, int *mx, cudaStream_t s) {
+  spg_scratch &z = spg();
   int n = A.n;
-  toff.ensure(n + 1); clen.ensure(n + 1);
-  rs_fill_i(flag.p, 0, 1, s);
-  k_row_products<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, B.rp.p, toff.p, flag.p);
+  z.toff.ensure(n + 1); z.clen.ensure(n + 1);
+  k_row_products<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, B.rp.p, z.toff.p, mx);
   RS_LAUNCHED(1);
-  int mx1 = d2h(flag.p, 1, s)[0], mx = std::max(mx1 - 1, 0);
-  int cap_all = 32;
-  while (cap_all < mx) cap_all <<= 1;
-  // shared-memory capacity at most 8192 products per warp (128 KB); rows with
-  // more go to a second launch with a global scratch area
-  int cap = std::min(cap_all, 8192);
-  size_t per_warp = (size_t)cap * 16;
-  int warps = (int)std::min<size_t>(8, std::max<size_t>(1, (96 * 1024) / per_warp));
-  size_t smem = per_warp * warps;
+  rs_scan_dev(z.toff.p, z.toff.p, n, z.toff.p + n, tot, s);      // row offsets into the scratch arrays
+}
+
+static void spgemm_fill(const csr_dev<double> &A, const csr_dev<double> &B, csr_dev<double> &C, int total, int mx1,
+                        int *nnz, cudaStream_t s) {
+  spg_scratch &z = spg();
+  int n = A.n, mx = std::max(mx1 - 1, 0);
+  // hash-table slots per warp: at least the products of the largest row in
+  // the launch; rows beyond 1024 products (above the 99.9th percentile on
+  // the channelised cases) go to a second launch with a global scratch area
+  int tall = 64;
+  while (tall < mx) tall <<= 1;
+  int tcap = std::min(tall, 1024);
+  size_t wbytes = spg_warp_doubles(tcap) * sizeof(double);
+  int warps = (int)std::min<size_t>(8, std::max<size_t>(1, (100 * 1024) / wbytes));
+  size_t smem = wbytes * warps;
   static bool attr = false;
   if (!attr) {
-    RS_CUDA(cudaFuncSetAttribute(k_spgemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    RS_CUDA(cudaFuncSetAttribute(k_spgemm_hash, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr = true;
   }
-  int total = rs_scan(toff.p, toff.p, n, s);          // row offsets into the scratch arrays
-  RS_CUDA(cudaMemcpyAsync(toff.p + n, &total, sizeof(int), cudaMemcpyHostToDevice, s));   // (pageable: copied at once)
-  tci.ensure(std::max(total, 1)); tv.ensure(std::max(total, 1));
-  C.n = n; C.m = B.m;
+  z.tci.ensure(std::max(total, 1)); z.tv.ensure(std::max(total, 1));
+  C.n = n; C.m = B.m; C.nnz = -1;                      // known on the host at the next wait
   C.rp.ensure(n + 1);
   unsigned gm = grid_for(n, 128);
-  k_spgemm_merge<SPG_KMAX><<<gm, 128, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, toff.p, clen.p, tci.p,
-                                              tv.p);
+  k_spgemm_merge<SPG_KMAX><<<gm, 128, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, z.toff.p, z.clen.p,
+                                              z.tci.p, z.tv.p);
   RS_LAUNCHED(1);
-  if (mx1 > 0) {                                       // rows of A longer than SPG_KMAX
-    unsigned grid = (unsigned)std::min<size_t>((n + warps - 1) / warps, 152 * 64);
-    k_spgemm<true><<<grid, warps * 32, smem, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, toff.p, clen.p,
-                                                  tci.p, tv.p, cap, -1, nullptr);
+  if (mx1 > 0) {                                       // rows for the hash kernel
+    unsigned grid = (unsigned)std::min<size_t>((n + warps - 1) / warps, 152 * 32);
+    k_spgemm_hash<<<grid, warps * 32, smem, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, z.toff.p,
+                                                 z.clen.p, z.tci.p, z.tv.p, tcap, -1, nullptr);
     RS_LAUNCHED(1);
-    if (cap_all > cap) {                               // rows beyond the shared-memory capacity
-      static thread_local dbuf<unsigned long long> gs;
+    if (tall > tcap) {                                 // rows beyond the shared-memory capacity
       const int gw = 4, gblocks = 64;
-      gs.ensure((size_t)gblocks * gw * 2 * cap_all);
-      k_spgemm<true><<<gblocks, gw * 32, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, toff.p, clen.p,
-                                                 tci.p, tv.p, cap_all, cap, gs.p);
+      z.gs.ensure((size_t)gblocks * gw * spg_warp_doubles(tall));
+      k_spgemm_hash<<<gblocks, gw * 32, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, z.toff.p, z.clen.p,
+                                                z.tci.p, z.tv.p, tall, tcap, z.gs.p);
       RS_LAUNCHED(1);
     }
   }
   RS_CHECK_LAUNCH();
-  C.nnz = rs_scan(clen.p, C.rp.p, n, s);
-  RS_CUDA(cudaMemcpyAsync(C.rp.p + n, &C.nnz, sizeof(int), cudaMemcpyHostToDevice, s));
-  C.ci.ensure(C.nnz); C.v.ensure(C.nnz);
-  k_pack_rows<<<grid_for((size_t)n * 8, 256), 256, 0, s>>>(n, toff.p, clen.p, C.rp.p, tci.p, tv.p, C.ci.p, C.v.p);
+  rs_scan_dev(z.clen.p, C.rp.p, n, C.rp.p + n, nnz, s);
+  C.ci.ensure(std::max(total, 1)); C.v.ensure(std::max(total, 1));
+  k_pack_rows<<<grid_for((size_t)n * 8, 256), 256, 0, s>>>(n, z.toff.p, z.clen.p, C.rp.p, z.tci.p, z.tv.p, C.ci.p,
+                                                          C.v.p);
   RS_LAUNCHED(1);
   RS_CHECK_LAUNCH();
-  RS_CUDA(cudaStreamSynchronize(s));   // C.nnz host value lives on this stack frame's caller
 }
 
 // ------------------------------------------------------------ smoother ----
@@ -639,53 +725,61 @@ __global__ void k_dense_lu_inv(int n, double *a, int *piv, double *inv) {
   }
 }
 
-// k_dense_lu_inv with the matrix in shared memory (n <= 128: at most
-// 128 KB); the same operations in the same order
-__global__ void k_dense_lu_inv_smem(int n, const double *ag, int *piv, double *inv, int xs_smem) {
+// The inverse of the coarsest operator (n <= 128) by Gauss-Jordan
+// elimination with partial (row) pivoting, in place in shared memory (at
+// most 128 KB).  Step k: warp 0 finds the pivot row (largest |a_ik|, the
+// lowest index on ties), swaps it with row k, saves column k and scales row
+// k by 1/a_kk (a_kk itself becomes 1/a_kk); then every thread eliminates
+// column k from its elements of the other rows (a_ik itself becomes
+// -a_ik/a_kk).  Two block barriers per step.  At the end the row swaps are
+// undone on the columns, in reverse order, while the result is written.
+// Stored transposed: inv[c][i] = (A^{-1})_{ic}.  Equal to the LU solve of
+// the same system up to rounding.
+__global__ void __launch_bounds__(512) k_dense_gj_inv_smem(int n, const double *ag, int *piv, double *inv) {
   extern __shared__ double sa[];
-  __shared__ double smx[512]; __shared__ int sid[512]; __shared__ int spiv[128];
-  int t = threadIdx.x, nt = blockDim.x;
+  __shared__ double fcol[128];
+  __shared__ int sperm[128], scol[128];
+  int t = threadIdx.x, nt = blockDim.x, lane = t & 31;
   for (int e = t; e < n * n; e += nt) sa[e] = ag[e];
   __syncthreads();
   for (int k = 0; k < n; k++) {
-    double best = -1.0; int bi = n;
-    for (int i = k + t; i < n; i += nt) { double x = fabs(sa[i * n + k]); if (x > best) { best = x; bi = i; } }
-    smx[t] = best; sid[t] = bi;
-    __syncthreads();
-    for (int o = nt >> 1; o > 0; o >>= 1) {
-      if (t < o) {
-        double x = smx[t + o]; int xi = sid[t + o];
-        if (x > smx[t] || (x == smx[t] && xi < sid[t])) { smx[t] = x; sid[t] = xi; }
+    if (t < 32) {
+      double best = -1.0; int bi = n;
+      for (int i = k + lane; i < n; i += 32) { double x = fabs(sa[i * n + k]); if (x > best) { best = x; bi = i; } }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        double x = __shfl_xor_sync(0xffffffffu, best, o); int xi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (x > best || (x == best && xi < bi)) { best = x; bi = xi; }
       }
-      __syncthreads();
+      int p = bi < n ? bi : k;
+      if (p != k)
+        for (int j = lane; j < n; j += 32) { double x = sa[k * n + j]; sa[k * n + j] = sa[p * n + j]; sa[p * n + j] = x; }
+      __syncwarp();
+      double d = sa[k * n + k];
+      for (int i = lane; i < n; i += 32) fcol[i] = sa[i * n + k];
+      __syncwarp();
+      double r = 1.0 / d;
+      for (int j = lane; j < n; j += 32) sa[k * n + j] = j == k ? r : sa[k * n + j] * r;
+      if (lane == 0) { sperm[k] = p; piv[k] = p; }
     }
-    int p = sid[0];
-    if (t == 0) { piv[k] = p; spiv[k] = p; }
-    if (p != k)
-      for (int j = t; j < n; j += nt) { double x = sa[k * n + j]; sa[k * n + j] = sa[p * n + j]; sa[p * n + j] = x; }
     __syncthreads();
-    for (int i = k + 1 + t; i < n; i += nt) sa[i * n + k] = div_rn(sa[i * n + k], sa[k * n + k]);
-    __syncthreads();
-    for (int e = t; e < (n - k - 1) * (n - k - 1); e += nt) {
-      int i = k + 1 + e / (n - k - 1), j = k + 1 + e % (n - k - 1);
-      sa[i * n + j] = sub_rn(sa[i * n + j], mul_rn(sa[i * n + k], sa[k * n + j]));
+    for (int e = t; e < n * n; e += nt) {
+      int i = e / n, j = e - i * n;
+      if (i == k) continue;
+      double f = fcol[i];
+      sa[e] = j == k ? -f * sa[k * n + k] : sa[e] - f * sa[k * n + j];
     }
     __syncthreads();
   }
-  // column c of the inverse by the two triangular solves, one thread per
-  // column; the column is worked on in shared memory when it fits beside the
-  // factors (xs), else in place in the output
-  bool xs = xs_smem != 0;
-  for (int c = t; c < n; c += nt) {
-    double *x = xs ? sa + (size_t)n * n + (size_t)c * n : inv + (size_t)c * n;
-    for (int i = 0; i < n; i++) x[i] = (i == c) ? 1.0 : 0.0;
-    for (int k = 0; k < n; k++) if (spiv[k] != k) { double y = x[k]; x[k] = x[spiv[k]]; x[spiv[k]] = y; }
-    for (int i = 0; i < n; i++) { double s = x[i]; for (int j = 0; j < i; j++) s -= sa[i * n + j] * x[j]; x[i] = s; }
-    for (int i = n - 1; i >= 0; i--) { double s = x[i]; for (int j = i + 1; j < n; j++) s -= sa[i * n + j] * x[j]; x[i] = s / sa[i * n + i]; }
+  // undo the row swaps on the columns: the final column c comes from scol[c]
+  if (t == 0) {
+    for (int c = 0; c < n; c++) scol[c] = c;
+    for (int k = n - 1; k >= 0; k--) { int p = sperm[k]; int x = scol[k]; scol[k] = scol[p]; scol[p] = x; }
   }
-  if (xs) {                                     // stored transposed: inv[c][i] = (A^{-1})_{ic}
-    __syncthreads();
-    for (int e = t; e < n * n; e += nt) inv[e] = sa[(size_t)n * n + e];
+  __syncthreads();
+  for (int e = t; e < n * n; e += nt) {
+    int c = e / n, i = e - c * n;
+    inv[e] = sa[i * n + scol[c]];
   }
 }
 
@@ -698,151 +792,220 @@ static void csr_cast(const csr_dev<double> &a, csr_dev<float> &b, cudaStream_t s
   rs_cast_d2f(a.v.p, b.v.p, a.nnz, s);
 }
 
+// Words of h.flag, the setup's device counters, read back into the pinned
+// h.hflag at the few points where the host needs a size: per level once
+// after the split, P and the products of A P are known (wait 1), and once
+// after the products of R (A P) are known (wait 2); nnz of the coarse
+// operators at the next wait 1 or at the end.
+enum {
+  AF_SYM = 0,        // pattern of A not structurally symmetric
+  AF_PCAP = 1,       // a row of P beyond its capacity
+  AF_NC = 2,         // C points (coarse size)
+  AF_PNNZ = 3,       // nnz(P)
+  AF_APTOT = 4, AF_APMX = 5, AF_APNNZ = 6,     // products, long-row marker and nnz of A P
+  AF_RAPTOT = 7, AF_RAPMX = 8,                 // the same for R (A P)
+  AF_SLOTS = 16,
+  AF_LNNZ = 16,      // [16 + l]: nnz of level l's operator (l >= 1)
+  AF_CNT = 48,       // [48 + r]: undecided points after PMIS round r - 1 (r = 0: after the initialisation)
+  AF_ROUNDS_MAX = 1020,
+  AF_WORDS = AF_CNT + AF_ROUNDS_MAX + 8
+};
+
+static const int *amg_read(amg_hier &h, int lo, int count, cudaStream_t s) {
+  RS_CUDA(cudaMemcpyAsync(h.hflag + lo, h.flag.p + lo, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, s));
+  RS_CUDA(cudaStreamSynchronize(s));
+  return h.hflag;
+}
+
+// PMIS rounds [r0, r1): round r runs only while cnt[r] > 0, so the rounds
+// past the last one do nothing
+static void pmis_rounds(amg_level &L, amg_hier &h, int n, int lanes, int r0, int r1, cudaStream_t s) {
+  int *cnt = h.flag.p + AF_CNT;
+  for (int r = r0; r < r1; r++) {
+    if (lanes == 1) {
+      k_pmis_select<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, h.hashw.p,
+                                                     L.cf.p, h.newc.p, cnt + r);
+      k_pmis_update<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, h.newc.p,
+                                                     cnt + r + 1, cnt + r);
+    } else {
+      unsigned gl = grid_for((size_t)n * lanes, 128);
+#define PMIS_LANES(LL)                                                                                          \
+      if (lanes == LL) {                                                                                        \
+        k_pmis_select_lanes<LL><<<gl, 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, h.hashw.p,      \
+                                                   L.cf.p, h.newc.p, cnt + r);                                  \
+        k_pmis_update_lanes<LL><<<gl, 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, h.newc.p,         \
+                                                   cnt + r + 1, cnt + r);                                       \
+      }
+      PMIS_LANES(4) PMIS_LANES(16)
+#undef PMIS_LANES
+    }
+  }
+  RS_LAUNCHED(2 * (r1 - r0));
+  RS_CHECK_LAUNCH();
+}
+
+// P (and the C-point numbering in cidx) of level L from its C/F split, and
+// the products of A P; no host wait for direct interpolation (nnz(P) <=
+// nnz(A) sizes P), two for extended+i.  Returns nnz(P) when it is known on
+// the host, else -1.
+static int build_p(amg_level &L, amg_hier &h, const rs_opts &o, int n, size_t acap, dbuf<int> &cidx,
+                   cudaStream_t s) {
+  int *F = h.flag.p;
+  k_cflag<<<grid_for(n, 256), 256, 0, s>>>(n, L.cf.p, cidx.p);
+  RS_LAUNCHED(1);
+  rs_scan_dev(cidx.p, cidx.p, n, cidx.p + n, F + AF_NC, s);
+  L.P.n = n;
+  L.P.rp.ensure(n + 1);
+  int pnnz = -1;
+  if (o.interp == SIM_INTERP_EXTI) {
+    static thread_local dbuf<int> uoff, cand;
+    static thread_local dbuf<double> dk;
+    uoff.ensure(n + 1);
+    k_exti_bound<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, uoff.p);
+    RS_LAUNCHED(1);
+    int ncand = rs_scan(uoff.p, uoff.p, n, s);
+    cand.ensure(ncand > 0 ? ncand : 1);
+    k_exti_cands<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, uoff.p, cand.p,
+                                                  L.P.rp.p);
+    RS_LAUNCHED(1);
+    pnnz = rs_scan(L.P.rp.p, L.P.rp.p, n, s);
+    RS_CUDA(cudaMemcpyAsync(L.P.rp.p + n, &pnnz, sizeof(int), cudaMemcpyHostToDevice, s));
+    RS_CUDA(cudaStreamSynchronize(s));                 // pnnz is a local
+    L.P.ci.ensure(pnnz > 0 ? pnnz : 1); L.P.v.ensure(pnnz > 0 ? pnnz : 1);
+    dk.ensure(acap > 0 ? acap : 1);
+    k_exti_dk<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, L.strong.p, L.cf.p, uoff.p, cand.p,
+                                               L.P.rp.p, dk.p);
+    k_exti_fill<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, L.strong.p, L.cf.p, cidx.p,
+                                                 uoff.p, cand.p, dk.p, L.P.rp.p, L.P.ci.p, L.P.v.p);
+    RS_LAUNCHED(2);
+  } else {
+    k_interp_count<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, L.P.rp.p);
+    RS_LAUNCHED(1);
+    rs_scan_dev(L.P.rp.p, L.P.rp.p, n, L.P.rp.p + n, F + AF_PNNZ, s);
+    L.P.ci.ensure(acap > 0 ? acap : 1); L.P.v.ensure(acap > 0 ? acap : 1);
+    k_interp_fill<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, L.strong.p, L.cf.p, cidx.p,
+                                                   L.P.rp.p, L.P.ci.p, L.P.v.p, (int)L.P.ci.n, F + AF_PCAP);
+    RS_LAUNCHED(1);
+  }
+  RS_CHECK_LAUNCH();
+  spgemm_count(L.A, L.P, F + AF_APTOT, F + AF_APMX, s);
+  return pnnz;
+}
+
 void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
   h.drop_graphs();                                  // buffers below may move
-  h.flag.ensure(4 + 1025);
+  h.flag.ensure(AF_WORDS);
+  if (!h.hflag) RS_CUDA(cudaMallocHost((void **)&h.hflag, AF_WORDS * sizeof(int)));
+  int *F = h.flag.p;
   bool mixed = o.precision != SIM_PREC_FP64;
   int l = 0;
   for (;;) {
     amg_level &L = h.lev[l];
     int n = L.A.n;
+    // nnz(A) of a coarse level is known on the host only at this level's
+    // first wait: until then its capacity bounds it, and the previous
+    // setup's count picks the launch shapes (which do not change results)
+    size_t acap = l == 0 ? (size_t)L.A.nnz : L.A.ci.n;
+    long long nnz_hint = L.A.nnz >= 0 ? L.A.nnz : (L.nnz_prev > 0 ? L.nnz_prev : (long long)acap);
     L.dinv.ensure(n);
     if (mixed) L.dinv32.ensure(n);
     k_l1<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, L.dinv.p, mixed ? L.dinv32.p : nullptr);
     RS_LAUNCHED(1);
     L.f.ensure(n); L.x.ensure(n); L.r.ensure(n); L.t.ensure(n);
     if (mixed) { L.f32.ensure(n); L.x32.ensure(n); L.r32.ensure(n); L.t32.ensure(n); }
-    L.cf.ensure(n); L.strong.ensure(L.A.nnz); L.tpos.ensure(L.A.nnz);
+    L.cf.ensure(n); L.strong.ensure(acap); L.tpos.ensure(acap);
+    int rounds_hint = L.rounds;
     L.nc = 0; L.rounds = 0;
     if (n <= o.coarse_max || l == o.max_levels - 1) {      // coarsest: no split (all marks 0)
       RS_CUDA(cudaMemsetAsync(L.cf.p, 0, (size_t)n, s));
       h.coarse_dense = 1;
       break;
     }
-    rs_fill_i(h.flag.p, 0, 4 + 1025, s);
-    if (L.A.nnz > 8LL * n) k_tpos_warp<<<grid_for((size_t)n * 32, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.tpos.p, h.flag.p + 1);
-    else k_tpos<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.tpos.p, h.flag.p + 1);
+    rs_fill_i(F, 0, AF_SLOTS, s);
+    rs_fill_i(F + AF_CNT, 0, AF_WORDS - AF_CNT, s);
+    if (nnz_hint > 8LL * n) k_tpos_warp<<<grid_for((size_t)n * 32, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.tpos.p, F + AF_SYM);
+    else k_tpos<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.tpos.p, F + AF_SYM);
     k_strength<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, o.theta, L.strong.p);
     h.hashw.ensure(n); h.newc.ensure(n);
     k_pmis_init<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, o.seed, l,
-                                                 h.hashw.p, L.cf.p, h.flag.p + 4);
+                                                 h.hashw.p, L.cf.p, F + AF_CNT);
     RS_LAUNCHED(3);
     RS_CHECK_LAUNCH();
-    if (d2h(h.flag.p + 1, 1, s)[0]) RS_FAIL(SIM_ERR_ARG, "AMG: level %d pattern is not structurally symmetric", l);
-    // rounds in batches of PMIS_BATCH: cnt[0] = undecided points after the
-    // initialisation, cnt[r + 1] = after round r; round r runs only while
-    // cnt[r] > 0, so the rounds past the last one do nothing
-    const int PMIS_BATCH = 4;
-    int *cnt = h.flag.p + 4;
-    const int lanes = pmis_lanes(L.A.nnz, n);
-    for (int done = 0;;) {
-      for (int r = done; r < done + PMIS_BATCH; r++) {
-        if (lanes == 1) {
-          k_pmis_select<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, h.hashw.p,
-                                                         L.cf.p, h.newc.p, cnt + r);
-          k_pmis_update<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, h.newc.p,
-                                                         cnt + r + 1, cnt + r);
-        } else {
-          unsigned gl = grid_for((size_t)n * lanes, 128);
-#define PMIS_LANES(LL)                                                                                          \
-          if (lanes == LL) {                                                                                    \
-            k_pmis_select_lanes<LL><<<gl, 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, h.hashw.p,  \
-                                                       L.cf.p, h.newc.p, cnt + r);                              \
-            k_pmis_update_lanes<LL><<<gl, 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, h.newc.p,     \
-                                                       cnt + r + 1, cnt + r);                                   \
-          }
-          PMIS_LANES(4) PMIS_LANES(16)
-#undef PMIS_LANES
-        }
-      }
-      RS_LAUNCHED(2 * PMIS_BATCH);
-      RS_CHECK_LAUNCH();
-      std::vector<int> und = d2h(cnt + done, PMIS_BATCH + 1, s);
+    // as many rounds as the previous setup took here, plus two (spare
+    // rounds return at once); more in batches of four when they were not enough
+    const int lanes = pmis_lanes(nnz_hint, n);
+    int done = std::min(rounds_hint > 0 ? rounds_hint + 2 : 10, (int)AF_ROUNDS_MAX);
+    pmis_rounds(L, h, n, lanes, 0, done, s);
+    static thread_local dbuf<int> cidx;      // C flags, then coarse index of each C point
+    cidx.ensure(n + 1);
+    const int *hf = nullptr;
+    for (;;) {
+      int pnnz = build_p(L, h, o, n, acap, cidx, s);
+      hf = amg_read(h, 0, AF_CNT + done + 1, s);        // wait 1
+      if (hf[AF_SYM]) RS_FAIL(SIM_ERR_ARG, "AMG: level %d pattern is not structurally symmetric", l);
+      if (hf[AF_PCAP]) RS_FAIL(SIM_ERR_ARG, "AMG: level %d interpolation beyond its capacity", l);
+      if (pnnz >= 0) L.P.nnz = pnnz; else L.P.nnz = hf[AF_PNNZ];
       int z = -1;
-      for (int r = 0; r <= PMIS_BATCH; r++) if (und[r] == 0) { z = r; break; }
-      if (z >= 0) { L.rounds = done + z; break; }
-      done += PMIS_BATCH;
-      if (done + PMIS_BATCH >= 1024) RS_FAIL(SIM_ERR_TIMEOUT, "AMG: PMIS did not finish in 1024 rounds");
+      for (int r = 0; r <= done; r++) if (hf[AF_CNT + r] == 0) { z = r; break; }
+      if (z >= 0) { L.rounds = z; break; }
+      if (done + 4 > AF_ROUNDS_MAX) RS_FAIL(SIM_ERR_TIMEOUT, "AMG: PMIS did not finish in %d rounds", done);
+      pmis_rounds(L, h, n, lanes, done, done + 4, s);
+      done += 4;
+      rs_fill_i(F, 0, AF_SLOTS, s);                       // P and A P again from the finished split
     }
-    static thread_local dbuf<int> scratch;   // C flags, then coarse index of each C point
-    scratch.ensure(n + 1);
-    k_cflag<<<grid_for(n, 256), 256, 0, s>>>(n, L.cf.p, scratch.p);
-    RS_LAUNCHED(1);
-    int nc = rs_scan(scratch.p, scratch.p, n, s);
+    if (l > 0) L.A.nnz = hf[AF_LNNZ + l];
+    int nc = hf[AF_NC], ap_tot = hf[AF_APTOT], ap_mx = hf[AF_APMX];
     L.nc = nc;
     if (nc == 0) { h.coarse_dense = 0; break; }
-    // P
-    L.P.n = n; L.P.m = nc;
-    L.P.rp.ensure(n + 1);
-    if (o.interp == SIM_INTERP_EXTI) {
-      static thread_local dbuf<int> uoff, cand;
-      static thread_local dbuf<double> dk;
-      uoff.ensure(n + 1);
-      k_exti_bound<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, uoff.p);
-      RS_LAUNCHED(1);
-      int ncand = rs_scan(uoff.p, uoff.p, n, s);
-      cand.ensure(ncand > 0 ? ncand : 1);
-      k_exti_cands<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, uoff.p, cand.p,
-                                                    L.P.rp.p);
-      RS_LAUNCHED(1);
-      L.P.nnz = rs_scan(L.P.rp.p, L.P.rp.p, n, s);
-      RS_CUDA(cudaMemcpyAsync(L.P.rp.p + n, &L.P.nnz, sizeof(int), cudaMemcpyHostToDevice, s));
-      L.P.ci.ensure(L.P.nnz); L.P.v.ensure(L.P.nnz);
-      dk.ensure(L.A.nnz > 0 ? L.A.nnz : 1);
-      k_exti_dk<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, L.strong.p, L.cf.p, uoff.p, cand.p,
-                                                 L.P.rp.p, dk.p);
-      k_exti_fill<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, L.strong.p, L.cf.p, scratch.p,
-                                                   uoff.p, cand.p, dk.p, L.P.rp.p, L.P.ci.p, L.P.v.p);
-      RS_LAUNCHED(2);
-    } else {
-      k_interp_count<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, L.P.rp.p);
-      RS_LAUNCHED(1);
-      L.P.nnz = rs_scan(L.P.rp.p, L.P.rp.p, n, s);
-      RS_CUDA(cudaMemcpyAsync(L.P.rp.p + n, &L.P.nnz, sizeof(int), cudaMemcpyHostToDevice, s));
-      L.P.ci.ensure(L.P.nnz); L.P.v.ensure(L.P.nnz);
-      k_interp_fill<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, L.strong.p, L.cf.p, scratch.p,
-                                                     L.P.rp.p, L.P.ci.p, L.P.v.p);
-      RS_LAUNCHED(1);
-    }
+    L.P.m = nc;
+    static thread_local csr_dev<double> AP;
+    spgemm_fill(L.A, L.P, AP, ap_tot, ap_mx, F + AF_APNNZ, s);
     // R = P^T
     L.R.n = nc; L.R.m = n; L.R.nnz = L.P.nnz;
-    L.R.rp.ensure(nc + 1); L.R.ci.ensure(L.P.nnz); L.R.v.ensure(L.P.nnz);
+    L.R.rp.ensure(nc + 1); L.R.ci.ensure(L.P.nnz > 0 ? L.P.nnz : 1); L.R.v.ensure(L.P.nnz > 0 ? L.P.nnz : 1);
     static thread_local dbuf<int> fill;
     fill.ensure(nc + 1);
     rs_fill_i(L.R.rp.p, 0, nc + 1, s);
     rs_fill_i(fill.p, 0, nc + 1, s);
     k_col_count<<<grid_for(L.P.nnz, 256), 256, 0, s>>>(L.P.nnz, L.P.ci.p, L.R.rp.p);
     RS_LAUNCHED(1);
-    rs_scan(L.R.rp.p, L.R.rp.p, nc, s);
-    RS_CUDA(cudaMemcpyAsync(L.R.rp.p + nc, &L.R.nnz, sizeof(int), cudaMemcpyHostToDevice, s));
+    rs_scan_dev(L.R.rp.p, L.R.rp.p, nc, L.R.rp.p + nc, nullptr, s);
     k_transpose_fill<<<grid_for(n, 256), 256, 0, s>>>(n, L.P.rp.p, L.P.ci.p, L.P.v.p, L.R.rp.p, fill.p, L.R.ci.p,
                                                       L.R.v.p);
     k_sort_rows_warp<<<grid_for((size_t)nc * 32, 128), 128, 0, s>>>(nc, L.R.rp.p, L.R.ci.p, L.R.v.p);
     RS_LAUNCHED(2);
     // A_{l+1} = R (A P)
-    static thread_local csr_dev<double> AP;
-    spgemm(L.A, L.P, AP, h.flag, s);
-    spgemm(L.R, AP, h.lev[l + 1].A, h.flag, s);
+    spgemm_count(L.R, AP, F + AF_RAPTOT, F + AF_RAPMX, s);
+    hf = amg_read(h, 0, AF_SLOTS, s);                   // wait 2
+    AP.nnz = hf[AF_APNNZ];
+    spgemm_fill(L.R, AP, h.lev[l + 1].A, hf[AF_RAPTOT], hf[AF_RAPMX], F + AF_LNNZ + l + 1, s);
     if (mixed) { csr_cast(L.P, L.P32, s); csr_cast(L.R, L.R32, s); }
     l++;
   }
   h.nlev = l + 1;
+  // nnz of the coarse operators not yet read (the coarsest one's at least)
+  bool unknown = false;
+  for (int k = 1; k < h.nlev; k++) unknown |= h.lev[k].A.nnz < 0;
+  if (unknown) {
+    const int *hf = amg_read(h, AF_LNNZ, h.nlev, s);
+    for (int k = 1; k < h.nlev; k++) if (h.lev[k].A.nnz < 0) h.lev[k].A.nnz = hf[AF_LNNZ + k];
+  }
+  for (int k = 0; k < h.nlev; k++) h.lev[k].nnz_prev = h.lev[k].A.nnz;
   for (int k = 0; k < h.nlev && mixed; k++) csr_cast(h.lev[k].A, h.lev[k].A32, s);
   amg_level &C = h.lev[l];
   if (h.coarse_dense) {
     int n = C.A.n;
     if (n > 2048) RS_FAIL(SIM_ERR_ARG, "AMG: coarsest level of %d rows is too large for the dense solve", n);
-    static thread_local dbuf<double> a;
+    dbuf<double> &a = h.dense_a;
     a.ensure((size_t)n * n); h.lu.ensure((size_t)n * n); h.piv.ensure(n);
     k_dense_build<<<grid_for(n, 128), 128, 0, s>>>(n, C.A.rp.p, C.A.ci.p, C.A.v.p, a.p);
     if (n <= 128) {
       static bool attr = false;
       if (!attr) {
-        RS_CUDA(cudaFuncSetAttribute(k_dense_lu_inv_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        RS_CUDA(cudaFuncSetAttribute(k_dense_gj_inv_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr = true;
       }
-      int xs = (size_t)2 * n * n * 8 <= 200 * 1024;      // the inverse's columns beside the factors
-      k_dense_lu_inv_smem<<<1, 512, (size_t)(xs ? 2 : 1) * n * n * 8, s>>>(n, a.p, h.piv.p, h.lu.p, xs);
+      k_dense_gj_inv_smem<<<1, 512, (size_t)n * n * 8, s>>>(n, a.p, h.piv.p, h.lu.p);
     } else {
       k_dense_lu_inv<<<1, 512, 0, s>>>(n, a.p, h.piv.p, h.lu.p);
     }

@@ -101,6 +101,10 @@ __device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(
 // ------------------------------------------------------------ utilities --
 // exclusive scan of n int32 values (in may alias out); returns the total
 int rs_scan(const int *in, int *out, int n, cudaStream_t s);
+// the same without a host wait: the total goes to device memory, at tail
+// (e.g. out + n) and tot2 (either may be nullptr); in may alias out when
+// tail is not in[n] of a later use.  Stream-ordered, no synchronisation.
+void rs_scan_dev(const int *in, int *out, int n, int *tail, int *tot2, cudaStream_t s);
 // deterministic reductions (fixed association order for a given n)
 void rs_dot_partials(const double *x, const double *y, int n, double *partials, int nblk, cudaStream_t s);
 double rs_norm2(const double *x, int n, cudaStream_t s);   // syncs
@@ -138,6 +142,7 @@ struct amg_level {
   dbuf<uint8_t> strong;
   dbuf<int> tpos;               // position of (j,i) in row j for each (i,j)
   int nc = 0, rounds = 0;
+  int nnz_prev = 0;             // nnz(A) of this level at the previous setup (a launch-shape hint)
   dbuf<double> f, x, r, t;      // cycle work vectors (FP64)
   dbuf<float> f32, x32, r32, t32;
 };
@@ -149,6 +154,8 @@ struct amg_hier {
   dbuf<double> lu;              // dense LU of the coarsest level
   dbuf<int> piv;
   dbuf<int> flag;               // device counters / error words
+  int *hflag = nullptr;         // pinned host copy of flag, read at the setup's few waits
+  dbuf<double> dense_a;         // the coarsest operator as a dense matrix (setup scratch)
   dbuf<double> hashw;           // PMIS weights
   dbuf<int8_t> newc;
   // the V-cycle of the current hierarchy as a CUDA graph ([0] FP64, [1] FP32),
@@ -159,7 +166,7 @@ struct amg_hier {
   void drop_graphs() {
     for (auto &e : vc_exec) if (e) { cudaGraphExecDestroy(e); e = nullptr; }
   }
-  ~amg_hier() { drop_graphs(); if (cap) cudaStreamDestroy(cap); }
+  ~amg_hier() { drop_graphs(); if (cap) cudaStreamDestroy(cap); if (hflag) cudaFreeHost(hflag); }
 };
 
 void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s);   // level 0 A must be filled

@@ -60,8 +60,14 @@ __global__ void k_scan_single(int *part, int m) {   // exclusive, in place; part
   }
   if (threadIdx.x == 0) part[m] = carry;
 }
-__global__ void k_scan_final(const int *in, int *out, int n, const int *part) {
+// tail: where the total goes besides part[nblk] (out + n for a row-pointer
+// array, a device counter, or nullptr); tot2 a second copy (or nullptr)
+__global__ void k_scan_final(const int *in, int *out, int n, const int *part, int nblk, int *tail, int *tot2) {
   __shared__ int sh[SCAN_BS / 32]; __shared__ int tot;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (tail) *tail = part[nblk];
+    if (tot2) *tot2 = part[nblk];
+  }
   int base = blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_IT;
   int v[SCAN_IT], s = 0;
   for (int k = 0; k < SCAN_IT; k++) { v[k] = (base + k < n) ? in[base + k] : 0; s += v[k]; }
@@ -76,13 +82,58 @@ int rs_scan(const int *in, int *out, int n, cudaStream_t s) {
   part.ensure(nblk + 1);
   k_scan_partials<<<nblk, SCAN_BS, 0, s>>>(in, n, part.p);
   k_scan_single<<<1, SCAN_BS, 0, s>>>(part.p, nblk);
-  k_scan_final<<<nblk, SCAN_BS, 0, s>>>(in, out, n, part.p);
+  k_scan_final<<<nblk, SCAN_BS, 0, s>>>(in, out, n, part.p, nblk, nullptr, nullptr);
   RS_LAUNCHED(3);
   RS_CHECK_LAUNCH();
   int tot = 0;
   RS_CUDA(cudaMemcpyAsync(&tot, part.p + nblk, sizeof(int), cudaMemcpyDeviceToHost, s));
   RS_CUDA(cudaStreamSynchronize(s));
   return tot;
+}
+
+__global__ void k_scan_empty(int *tail, int *tot2) {
+  if (tail) *tail = 0;
+  if (tot2) *tot2 = 0;
+}
+// one block over the whole array, chunk after chunk (short arrays: one
+// launch instead of three)
+__global__ void k_scan_one(const int *in, int *out, int n, int *tail, int *tot2) {
+  __shared__ int sh[SCAN_BS / 32]; __shared__ int tot;
+  int carry = 0;
+  for (int c0 = 0; c0 < n; c0 += SCAN_CHUNK) {
+    int base = c0 + threadIdx.x * SCAN_IT;
+    int v[SCAN_IT], s = 0;
+    for (int k = 0; k < SCAN_IT; k++) { v[k] = (base + k < n) ? in[base + k] : 0; s += v[k]; }
+    int e = block_excl_scan(s, sh, &tot) + carry;
+    for (int k = 0; k < SCAN_IT; k++) if (base + k < n) { out[base + k] = e; e += v[k]; }
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (tail) *tail = carry;
+    if (tot2) *tot2 = carry;
+  }
+}
+void rs_scan_dev(const int *in, int *out, int n, int *tail, int *tot2, cudaStream_t s) {
+  if (n <= 0) {
+    k_scan_empty<<<1, 1, 0, s>>>(tail, tot2);
+    RS_LAUNCHED(1);
+    return;
+  }
+  if (n <= 8 * SCAN_CHUNK) {
+    k_scan_one<<<1, SCAN_BS, 0, s>>>(in, out, n, tail, tot2);
+    RS_LAUNCHED(1);
+    RS_CHECK_LAUNCH();
+    return;
+  }
+  int nblk = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+  static thread_local dbuf<int> part;
+  part.ensure(nblk + 1);
+  k_scan_partials<<<nblk, SCAN_BS, 0, s>>>(in, n, part.p);
+  k_scan_single<<<1, SCAN_BS, 0, s>>>(part.p, nblk);
+  k_scan_final<<<nblk, SCAN_BS, 0, s>>>(in, out, n, part.p, nblk, tail, tot2);
+  RS_LAUNCHED(3);
+  RS_CHECK_LAUNCH();
 }
 
 // ------------------------------------------------------------ reductions --
