@@ -49,15 +49,6 @@ __global__ void k_tpos_warp(int n, const int *rp, const int *ci, int *tpos, int 
   }
 }
 
-// Comparisons of doubles taken on integers: dkey orders finite doubles as
-// IEEE comparison does (both zeros map to 0; dkey(-x) = -dkey(x)), so a
-// comparison decides the same as on the doubles while keeping the FP64
-// pipe (a small fraction of the FP32 rate on this GPU) for arithmetic.
-__device__ __forceinline__ long long dkey(double x) {
-  long long b = __double_as_longlong(x), m = b & 0x7fffffffffffffffLL;
-  return b < 0 ? -m : m;
-}
-
 __global__ void k_strength(int n, const int *rp, const int *ci, const double *v, double theta, uint8_t *S) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;

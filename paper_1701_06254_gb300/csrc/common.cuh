@@ -97,6 +97,15 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+// Comparisons of doubles taken on integers: dkey orders finite doubles and
+// the infinities as IEEE comparison does (both zeros map to 0; dkey(-x) =
+// -dkey(x)), so a comparison decides the same as on the doubles while the
+// FP64 pipe (a small fraction of the FP32 rate on this GPU) is kept for
+// arithmetic.
+__device__ __forceinline__ long long dkey(double x) {
+  long long b = __double_as_longlong(x), m = b & 0x7fffffffffffffffLL;
+  return b < 0 ? -m : m;
+}
 
 // ------------------------------------------------------------ utilities --
 // exclusive scan of n int32 values (in may alias out); returns the total
