@@ -137,8 +137,12 @@ def ras_bytes(ls, precision):
 # ncu captures summarised in profiles/, keyed by (kernel family, precision,
 # decoupling): a capture is quoted only for the configuration it was taken in
 # (null otherwise, and null once the kernel changes)
-NCU_TRAFFIC = {("ras", "mixed_bf16", "abf"): 167.8e6, ("spmv_prec", "mixed_bf16", "abf"): 164.3e6,
-               ("spmv64", "mixed_bf16", "abf"): 273.4e6}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# ncu captures of the benchmark's own command (profiles/dram_traffic_channelised_1m.md),
+# keyed on (kernel family, precision, decoupling); a configuration without a
+# capture of the current kernels reports null
+NCU_TRAFFIC = {("ras", "mixed_bf16", "qi"): 202.2e6, ("spmv_prec", "mixed_bf16", "qi"): 162.5e6,
+               ("spmv64", "mixed_bf16", "qi"): 271.3e6, ("vcycle", "mixed_bf16", "qi"): 351.8e6}
 
 
 def ncu_traffic(kernel, args):
@@ -349,6 +353,45 @@ def ensemble_seed0(rank, members):
     return 2000 + rank * members
 
 
+def time_ensemble(R, torch, args, cases, prec, dec, dist, local, steps, warmup):
+    """Advance the members together through the ensemble driver (host
+    workers chosen by the autotuner unless --workers is a number): `warmup`
+    untimed steps, then `steps` timed ones between device-wide
+    synchronisations (members run on streams of their own), on the host
+    clock, max over ranks."""
+    auto = args.workers == "auto"
+    batch = R.Batch(cases, workers=0 if auto else int(args.workers), precision=prec, max_lin=args.max_lin,
+                    decoupling=dec)
+    batch.init_hydrostatic()
+    tuned = None
+    if auto:
+        chosen, secs = batch.autotune(candidates=(4, 8, 16, 32))
+        tuned = {"chosen": chosen, "seconds_per_candidate": secs}
+    for _ in range(warmup):
+        batch.advance(1)
+    st0 = [m.stats() for m in batch.members]
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    l0 = R.launch_count()
+    clocks.start()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        batch.advance(1)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    ck = clocks.stop()
+    launches = R.launch_count() - l0
+    sec = rank_max(sec, dist, "cuda")
+    st1 = [m.stats() for m in batch.members]
+    out = {"seconds": sec, "launches": launches, "clocks": ck, "autotune": tuned, "workers": batch.workers,
+           "newton": sum(b["newton"] - a["newton"] for a, b in zip(st0, st1)),
+           "linear_its": sum(b["linear_its"] - a["linear_its"] for a, b in zip(st0, st1))}
+    del batch
+    return out
+
+
 def run_ensemble(args, rank, world, local):
     """--members independent models (grids drawn from U{32..128}^2 x U{8..32},
     seeds 2000 + k) advanced together by the ensemble driver.  Each rank of a
@@ -372,44 +415,17 @@ def run_ensemble(args, rank, world, local):
     prec = {"mixed": R.PREC_MIXED, "mixed_bf16": R.PREC_MIXED_BF16, "fp64": R.PREC_FP64}[args.precision]
     cases = I.ensemble(args.members, seed0=ensemble_seed0(rank, args.members))
     cells = sum(c.n for c in cases)
-    auto = args.workers == "auto"
     dec = DECOUPLING[args.decoupling]
-    batch = R.Batch(cases, workers=0 if auto else int(args.workers), precision=prec, max_lin=args.max_lin,
-                    decoupling=dec)
-    batch.init_hydrostatic()
-    tuned = None
-    if auto:
-        chosen, secs = batch.autotune(candidates=(4, 8, 16, 32))
-        tuned = {"chosen": chosen, "seconds_per_candidate": secs}
-    for _ in range(args.warmup):
-        batch.advance(1)
-    st0 = [m.stats() for m in batch.members]
-    clocks = Clocks(local)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    l0 = R.launch_count()
-    clocks.start()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        batch.advance(1)
-    torch.cuda.synchronize()
-    sec = time.perf_counter() - t0
-    ck = clocks.stop()
-    launches = R.launch_count() - l0
-    sec = rank_max(sec, dist, "cuda")
+    e = time_ensemble(R, torch, args, cases, prec, dec, dist, local, args.steps, args.warmup)
+    sec, launches, ck, tuned, workers_used = e["seconds"], e["launches"], e["clocks"], e["autotune"], e["workers"]
     cells_all = rank_sum(cells, dist, "cuda")           # each rank's members differ in size
-    workers_used = batch.workers
-    st1 = [m.stats() for m in batch.members]
-    newton = sum(b["newton"] - a["newton"] for a, b in zip(st0, st1))
-    lin = sum(b["linear_its"] - a["linear_its"] for a, b in zip(st0, st1))
+    newton, lin = e["newton"], e["linear_its"]
     # the same ensemble with the learned warm start: the network is trained
     # first (outside the timing) and every member gets its own copy of it
     # (same parameters; a network serves one caller at a time, so members
     # sharing one would queue on it)
     variants = None
     if not args.no_variants:
-        del batch
         ws, info = train_warm_start(R, args, dict(precision=prec, max_lin=args.max_lin, decoupling=dec))
         params = ws.params()
         b2 = R.Batch(cases, workers=workers_used, precision=prec, max_lin=args.max_lin, decoupling=dec)
@@ -495,6 +511,9 @@ def main():
     ap.add_argument("--workload", default="single", choices=["single", "ensemble"],
                     help="single: the 1M-cell case; ensemble: --members independent models advanced together")
     ap.add_argument("--members", type=int, default=128)
+    ap.add_argument("--ens-members", type=int, default=32,
+                    help="members of the ensemble variant of the single-model run (0: none)")
+    ap.add_argument("--ens-steps", type=int, default=2)
     ap.add_argument("--workers", default="auto", help="ensemble host workers, or 'auto' for the autotuner")
     ap.add_argument("--learned", action="store_true",
                     help="train the warm-start network on recorded 64x64x16 solves first and attach it")
@@ -687,6 +706,21 @@ def main():
         variants["ras_overlap2"] = measure_variant(R, torch, case, dict(opts, overlap=2), args)
         if args.exti_variant:
             variants["amg_exti"] = measure_variant(R, torch, case, dict(opts, interp=1), args)
+        if args.ens_members > 0:
+            # the batched ensemble: --ens-members independent models (grids
+            # drawn from U{32..128}^2 x U{8..32}) advanced together
+            cases_e = I.ensemble(args.ens_members, seed0=ensemble_seed0(rank, args.ens_members))
+            e = time_ensemble(R, torch, args, cases_e, prec, DECOUPLING[args.decoupling], dist, local,
+                              args.ens_steps, 3)
+            cells_e = rank_sum(sum(c.n for c in cases_e), dist, "cuda")
+            variants["ensemble"] = {
+                "workload": f"ensemble_{args.ens_members}", "members": args.ens_members, "cells_all_ranks": int(cells_e),
+                "value": cells_e * args.ens_steps / e["seconds"], "unit": UNIT,
+                "ms_per_step": e["seconds"] * 1e3 / args.ens_steps, "steps": args.ens_steps, "warmup": 3,
+                "workers": e["workers"], "autotune": e["autotune"], "gpu_launches": e["launches"],
+                "newton_per_member_step": e["newton"] / (args.ens_members * args.ens_steps),
+                "fgmres_its_per_newton": e["linear_its"] / max(e["newton"], 1), "clocks": e["clocks"],
+                "timer": "host clock between device-wide synchronisations (members on their own streams)"}
     precision_error = None
     if variants is not None:
         states = {k: v.pop("_state", None) for k, v in variants.items()}
