@@ -400,22 +400,22 @@ __global__ void k_sort_rows_warp(int n, const int *rp, int *ci, double *v) {
 // -------------------------------------------------------------- SpGEMM ----
 // C = A B, each column of a row of C the sum of its products A_ik B_kj in
 // the order of k (the row of A's column order), starting from 0.  Rows of A
-// with at most SPG_KMAX entries and at most SPG_MERGE_P products:
-// k_spgemm_merge (one thread per row); the others: k_spgemm_hash (one warp
-// per row).  One pass: each row is written at the offset of its product
+// with at most SPG_KMAX entries and at most SPG_MERGE_P products, on products
+// of many rows (spg_merge_p): k_spgemm_merge (one thread per row); the
+// others: k_spgemm_hash (one warp per row).  One pass: each row is written at the offset of its product
 // count (an upper bound of its length) into a scratch array, then the rows
 // are packed.
 // products per row of C; mx = 1 + the most products of a row that the
 // hash kernel handles, 0 if there is none
 #define SPG_KMAX 8
 #define SPG_MERGE_P 96
-__global__ void k_row_products(int n, const int *arp, const int *aci, const int *brp, int *prod, int *mx) {
+__global__ void k_row_products(int n, const int *arp, const int *aci, const int *brp, int *prod, int *mx, int merge_p) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int s = 0;
   for (int q = arp[i]; q < arp[i + 1]; q++) { int k = aci[q]; s += brp[k + 1] - brp[k]; }
   prod[i] = s;
-  if (arp[i + 1] - arp[i] > SPG_KMAX || s > SPG_MERGE_P) atomicMax(mx, s + 1);   // + 1: "a hash row exists" even with 0 products
+  if (arp[i + 1] - arp[i] > SPG_KMAX || s > merge_p) atomicMax(mx, s + 1);   // + 1: "a hash row exists" even with 0 products
 }
 // C row i = scratch[toff[i] .. toff[i] + clen[i]), eight lanes per row
 __global__ void k_pack_rows(int n, const int *toff, const int *clen, const int *crp, const int *tci, const double *tv,
@@ -426,7 +426,7 @@ __global__ void k_pack_rows(int n, const int *toff, const int *clen, const int *
   for (int t = lane; t < len; t += 8) { cci[b + t] = tci[a + t]; cv[b + t] = tv[a + t]; }
 }
 
-// C = A B for the rows of A with at most K entries and at most SPG_MERGE_P
+// C = A B for the rows of A with at most K entries and at most merge_p
 // products, one thread per row: a k-way merge of the k rows of B that the
 // row of A selects (each sorted by column, its head kept in registers).  The
 // smallest head column is the next column of C; its products are summed in
@@ -438,11 +438,11 @@ __global__ void k_pack_rows(int n, const int *toff, const int *clen, const int *
 template <int K>
 __global__ void __launch_bounds__(128) k_spgemm_merge(int n, const int *arp, const int *aci, const double *av,
                                                       const int *brp, const int *bci, const double *bv,
-                                                      const int *toff, int *clen, int *cci, double *cv) {
+                                                      const int *toff, int *clen, int *cci, double *cv, int merge_p) {
   int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
   int a0 = arp[row], k = arp[row + 1] - a0;
-  if (k > K || toff[row + 1] - toff[row] > SPG_MERGE_P) return;
+  if (k > K || toff[row + 1] - toff[row] > merge_p) return;
   int pos[K], end[K], col[K];
   double a[K];
 #pragma unroll
@@ -460,11 +460,26 @@ __global__ void __launch_bounds__(128) k_spgemm_merge(int n, const int *arp, con
 #pragma unroll
     for (int q = 0; q < K; q++) c = min(c, col[q]);
     if (c == INT_MAX) break;
+    // the heads on column c, in q order.  Only they issue FP64 work: each is
+    // picked out of the register arrays by a chain of selects (integer
+    // pipes), so the FP64 pipe (a small fraction of the FP32 rate on this
+    // GPU) sees one product and one sum per actual product instead of one
+    // predicated pair per head
+    unsigned hit = 0;
+#pragma unroll
+    for (int q = 0; q < K; q++) hit |= (col[q] == c ? 1u : 0u) << q;
     double s = 0.0;
+    for (unsigned h = hit; h; h &= h - 1) {
+      int qq = __ffs(h) - 1;
+      double aq = a[0];
+      int pq = pos[0];
+#pragma unroll
+      for (int q = 1; q < K; q++) { aq = qq == q ? a[q] : aq; pq = qq == q ? pos[q] : pq; }
+      s = add_rn(s, mul_rn(aq, bv[pq]));
+    }
 #pragma unroll
     for (int q = 0; q < K; q++)
-      if (col[q] == c) {
-        s = add_rn(s, mul_rn(a[q], bv[pos[q]]));
+      if (hit >> q & 1u) {
         pos[q]++;
         col[q] = pos[q] < end[q] ? bci[pos[q]] : INT_MAX;
       }
@@ -475,7 +490,7 @@ __global__ void __launch_bounds__(128) k_spgemm_merge(int n, const int *arp, con
 }
 
 // Rows that the merge kernel leaves (more than SPG_KMAX entries in A, or
-// more than SPG_MERGE_P products), one warp per row of C.  The products are
+// more than merge_p products), one warp per row of C.  The products are
 // taken in sequence order (row of A ascending, then row of B ascending), 32
 // at a time; each lane claims its column's slot in an open-addressing hash
 // table (compare-and-swap on the key, linear probing; the table has at
@@ -495,7 +510,7 @@ __host__ __device__ constexpr size_t spg_warp_doubles(int tcap) {
 __global__ void __launch_bounds__(256) k_spgemm_hash(int n, const int *arp, const int *aci, const double *av,
                                                      const int *brp, const int *bci, const double *bv,
                                                      const int *toff, int *clen, int *cci, double *cv, int tcap,
-                                                     int lo_p, double *gscratch) {
+                                                     int lo_p, double *gscratch, int merge_p) {
   extern __shared__ double sm_hash[];
   const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
@@ -506,7 +521,7 @@ __global__ void __launch_bounds__(256) k_spgemm_hash(int n, const int *arp, cons
   volatile int *vkeys = keys;
   for (int row = blockIdx.x * warps + wid; row < n; row += gridDim.x * warps) {
     int a0 = arp[row], a1 = arp[row + 1], out = toff[row], p = toff[row + 1] - out;
-    if (a1 - a0 <= SPG_KMAX && p <= SPG_MERGE_P) continue;    // the merge kernel's row
+    if (a1 - a0 <= SPG_KMAX && p <= merge_p) continue;        // the merge kernel's row
     if (p > tcap || p <= lo_p) continue;                      // the other launch's row
     int T = 32;
     while (T < p) T <<= 1;
@@ -594,19 +609,26 @@ __global__ void __launch_bounds__(256) k_spgemm_hash(int n, const int *arp, cons
 // SpGEMM C = A B in two phases with one host wait between them.
 // spgemm_count: products per row of C (scratch offsets, toff) and their
 // total in *tot, the long-row marker (1 + the most products of a row that
-// the sorting kernel handles, 0 if none) in *mx (which must be 0 before);
+// the hash kernel handles, 0 if none) in *mx (which must be 0 before);
 // no host wait.  spgemm_fill: given those two values on the host, the
 // numeric product into scratch, the row pointers of C (C.rp[n] and *nnz =
 // nnz(C) on the device) and the packed rows; C's arrays are sized by the
 // product total, an upper bound of nnz(C), so no further wait is needed.
 struct spg_scratch { dbuf<int> toff, clen, tci; dbuf<double> tv, gs; };
 static spg_scratch &spg() { static thread_local spg_scratch z; return z; }
+// Rows for the thread-per-row merge kernel (at most SPG_KMAX entries in A
+// and at most this many products): only when the product has enough rows to
+// fill the GPU with threads; on smaller products a thread's serial merge is
+// the launch's critical path (60-90 µs on the 1M-cell hierarchy's coarse
+// levels) and every row goes to the hash kernel.  Both kernels give the
+// same bits, so the split changes no result.
+static int spg_merge_p(int n) { return n >= 65536 ? SPG_MERGE_P : -1; }
 
 static void spgemm_count(const csr_dev<double> &A, const csr_dev<double> &B, int *tot, int *mx, cudaStream_t s) {
   spg_scratch &z = spg();
   int n = A.n;
   z.toff.ensure(n + 1); z.clen.ensure(n + 1);
-  k_row_products<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, B.rp.p, z.toff.p, mx);
+  k_row_products<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, B.rp.p, z.toff.p, mx, spg_merge_p(n));
   RS_LAUNCHED(1);
   rs_scan_dev(z.toff.p, z.toff.p, n, z.toff.p + n, tot, s);      // row offsets into the scratch arrays
 }
@@ -632,20 +654,22 @@ static void spgemm_fill(const csr_dev<double> &A, const csr_dev<double> &B, csr_
   z.tci.ensure(std::max(total, 1)); z.tv.ensure(std::max(total, 1));
   C.n = n; C.m = B.m; C.nnz = -1;                      // known on the host at the next wait
   C.rp.ensure(n + 1);
-  unsigned gm = grid_for(n, 128);
-  k_spgemm_merge<SPG_KMAX><<<gm, 128, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, z.toff.p, z.clen.p,
-                                              z.tci.p, z.tv.p);
-  RS_LAUNCHED(1);
+  int mp = spg_merge_p(n);
+  if (mp >= 0) {
+    k_spgemm_merge<SPG_KMAX><<<grid_for(n, 128), 128, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p,
+                                                              z.toff.p, z.clen.p, z.tci.p, z.tv.p, mp);
+    RS_LAUNCHED(1);
+  }
   if (mx1 > 0) {                                       // rows for the hash kernel
     unsigned grid = (unsigned)std::min<size_t>((n + warps - 1) / warps, 152 * 32);
     k_spgemm_hash<<<grid, warps * 32, smem, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, z.toff.p,
-                                                 z.clen.p, z.tci.p, z.tv.p, tcap, -1, nullptr);
+                                                 z.clen.p, z.tci.p, z.tv.p, tcap, -1, nullptr, mp);
     RS_LAUNCHED(1);
     if (tall > tcap) {                                 // rows beyond the shared-memory capacity
       const int gw = 4, gblocks = 64;
       z.gs.ensure((size_t)gblocks * gw * spg_warp_doubles(tall));
       k_spgemm_hash<<<gblocks, gw * 32, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, z.toff.p, z.clen.p,
-                                                z.tci.p, z.tv.p, tall, tcap, z.gs.p);
+                                                z.tci.p, z.tv.p, tall, tcap, z.gs.p, mp);
       RS_LAUNCHED(1);
     }
   }
