@@ -581,26 +581,57 @@ __global__ void __launch_bounds__(256) k_spgemm_hash(int n, const int *arp, cons
       u += __popc(mask);
       __syncwarp();
     }
-    int M = 1;
-    while (M < u) M <<= 1;
-    for (int i = u + lane; i < M; i += 32) keys[i] = INT_MAX;
-    __syncwarp();
-    for (int kk = 2; kk <= M; kk <<= 1)
-      for (int j = kk >> 1; j > 0; j >>= 1) {
-        for (int i = lane; i < M; i += 32) {
-          int ixj = i ^ j;
-          if (ixj > i) {
-            int x = keys[i], y = keys[ixj];
-            bool up = (i & kk) == 0;
-            if ((x > y) == up) {
-              keys[i] = y; keys[ixj] = x;
-              double w = vals[i]; vals[i] = vals[ixj]; vals[ixj] = w;
-            }
+    if (u <= 64) {
+      // up to 64 entries: two per lane in registers (indices lane and lane +
+      // 32, padded with INT_MAX), sorted by the same bitonic network over
+      // shuffles instead of shared-memory passes
+      int k0 = lane < u ? keys[lane] : INT_MAX, k1 = lane + 32 < u ? keys[lane + 32] : INT_MAX;
+      double v0 = lane < u ? vals[lane] : 0.0, v1 = lane + 32 < u ? vals[lane + 32] : 0.0;
+      const int M = u <= 32 ? 32 : 64;
+      for (int kk = 2; kk <= M; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+          if (j == 32) {                                // partners in the lane's two registers (kk = 64: ascending)
+            if (k0 > k1) { int x = k0; k0 = k1; k1 = x; double w = v0; v0 = v1; v1 = w; }
+            continue;
+          }
+#pragma unroll
+          for (int r = 0; r < 2; r++) {
+            if (r == 1 && M == 32) break;
+            int x = r ? k1 : k0;
+            double vx = r ? v1 : v0;
+            int y = __shfl_xor_sync(FULL, x, j);
+            double vy = __shfl_xor_sync(FULL, vx, j);
+            int i = lane + 32 * r;
+            bool keep_min = ((i & j) == 0) == ((i & kk) == 0);   // the lower index keeps the minimum when ascending
+            bool take = keep_min ? y < x : y > x;
+            if (take) { x = y; vx = vy; }
+            if (r) { k1 = x; v1 = vx; } else { k0 = x; v0 = vx; }
           }
         }
-        __syncwarp();
-      }
-    for (int i = lane; i < u; i += 32) { cci[out + i] = keys[i]; cv[out + i] = vals[i]; }
+      if (lane < u) { cci[out + lane] = k0; cv[out + lane] = v0; }
+      if (lane + 32 < u) { cci[out + lane + 32] = k1; cv[out + lane + 32] = v1; }
+    } else {
+      int M = 1;
+      while (M < u) M <<= 1;
+      for (int i = u + lane; i < M; i += 32) keys[i] = INT_MAX;
+      __syncwarp();
+      for (int kk = 2; kk <= M; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+          for (int i = lane; i < M; i += 32) {
+            int ixj = i ^ j;
+            if (ixj > i) {
+              int x = keys[i], y = keys[ixj];
+              bool up = (i & kk) == 0;
+              if ((x > y) == up) {
+                keys[i] = y; keys[ixj] = x;
+                double w = vals[i]; vals[i] = vals[ixj]; vals[ixj] = w;
+              }
+            }
+          }
+          __syncwarp();
+        }
+      for (int i = lane; i < u; i += 32) { cci[out + i] = keys[i]; cv[out + i] = vals[i]; }
+    }
     if (lane == 0) clen[row] = u;
     __syncwarp();
   }

@@ -286,24 +286,25 @@ k_assemble(int nx, int ny, int nz, fluid_c f, double top, double dz, double vol_
   reinterpret_cast<double2 *>(b)[c] = make_double2(-R0, -R1);
 }
 
-// well rows, one thread per well, perforations in order: BHP control
-// eq. (11) scaled by the target; a rate control sum_m (cw q_w + co q_o) - 1
-// with the weights of eq. (12) water, (13) oil or (14) liquid rate in
-// surface volumes over the target (production positive for a producer);
-// a shut well keeps p_b (1 * p_b, residual 0)
+// well rows, one warp per well (lanes over its perforations, partial sums
+// combined by shuffles in a fixed order): BHP control eq. (11) scaled by the
+// target; a rate control sum_m (cw q_w + co q_o) - 1 with the weights of
+// eq. (12) water, (13) oil or (14) liquid rate in surface volumes over the
+// target (production positive for a producer); a shut well keeps p_b
+// (1 * p_b, residual 0)
 __global__ void k_wells(int n, int nw, fluid_c f, double top, double dz, int nxy, const double *phi, const double *p,
                         const double *s, const double *pbh, const int *wpptr, const int *pcell, const double *pwi,
                         const int *ppos_wc, const int *wdiag, const int *wkind, const int *wctrl, const double *wtarget,
                         const double *wzref, double *val, double *b) {
-  int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= nw) return;
+  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= nw) return;                               // the whole warp
   int ctrl = wctrl[w];
   double sgn = wkind[w] == SIM_PROD ? -1.0 : 1.0, T = wtarget[w];
   double cw = (ctrl == SIM_WRATE || ctrl == SIM_LRATE) ? sgn / (f.rho_ref[0] * T) : 0.0;
   double co = (ctrl == SIM_ORATE || ctrl == SIM_LRATE) ? sgn / (f.rho_ref[1] * T) : 0.0;
   bool rate = cw != 0.0 || co != 0.0;
   double R = 0.0, Jww = 0.0;
-  for (int q = wpptr[w]; q < wpptr[w + 1]; q++) {
+  for (int q = wpptr[w] + lane; q < wpptr[w + 1]; q += 32) {
     int c = pcell[q];
     double *B = val + 4 * (size_t)ppos_wc[q];
     double b0 = 0, b1 = 0;
@@ -321,6 +322,12 @@ __global__ void k_wells(int n, int nw, fluid_c f, double top, double dz, int nxy
     }
     B[0] = b0; B[1] = b1; B[2] = 0.0; B[3] = 0.0;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    R += __shfl_xor_sync(0xffffffffu, R, o);
+    Jww += __shfl_xor_sync(0xffffffffu, Jww, o);
+  }
+  if (lane != 0) return;
   if (rate) R -= 1.0;
   else if (ctrl == SIM_SHUT) { R = 0.0; Jww = 1.0; }
   else { R = (pbh[w] - wtarget[w]) / wtarget[w]; Jww = 1.0 / wtarget[w]; }
@@ -431,9 +438,9 @@ static void s_props_assemble(sim_s *h) {
                                               ls->b.p);
   RS_LAUNCHED(2);
   if (h->nw) {
-    k_wells<<<grid_for(h->nw, 32), 32, 0, s>>>(n, h->nw, h->fl, h->top, h->dz, nxy, h->phi.p, h->p.p, h->s.p, h->pb.p,
-                                               h->wpptr.p, h->pcell.p, h->pwi.p, h->ppos_wc.p, h->wdiag.p, h->wkind_d.p,
-                                               h->wctrl_d.p, h->wtarget_d.p, h->wzref_d.p, ls->val.p, ls->b.p);
+    k_wells<<<grid_for((size_t)h->nw * 32, 128), 128, 0, s>>>(
+        n, h->nw, h->fl, h->top, h->dz, nxy, h->phi.p, h->p.p, h->s.p, h->pb.p, h->wpptr.p, h->pcell.p, h->pwi.p,
+        h->ppos_wc.p, h->wdiag.p, h->wkind_d.p, h->wctrl_d.p, h->wtarget_d.p, h->wzref_d.p, ls->val.p, ls->b.p);
     RS_LAUNCHED(1);
   }
   k_key<<<grid_for(n, 256), 256, 0, s>>>(n, nxy, h->fl, h->top, h->dz, h->p.p, ls->key.p);
