@@ -71,97 +71,95 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   return z ^ (z >> 31);
 }
 
+// Append i to a list when `on` (one atomic per warp: the warp's entries get
+// consecutive slots in lane order; the list's order is arbitrary and no
+// result depends on it).  Every lane of the warp must call it.
+__device__ __forceinline__ void warp_append(bool on, int i, int *count, int *list) {
+  unsigned m = __ballot_sync(0xffffffffu, on);
+  int lane = threadIdx.x & 31, base = 0;
+  if (lane == 0 && m) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (on) list[base + __popc(m & ((1u << lane) - 1u))] = i;
+}
+
 __global__ void k_pmis_init(int n, const int *rp, const int *ci, const uint8_t *S, const int *tpos,
-                            uint64_t seed, int level, double *w, int8_t *cf, int *undecided) {
+                            uint64_t seed, int level, double *w, int8_t *cf, int8_t *newc, int *undecided,
+                            int *list) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
   int cnt = 0;
-  for (int q = rp[i]; q < rp[i + 1]; q++) if (ci[q] != i && S[tpos[q]]) cnt++;   // |S^T_i|
-  uint64_t z = splitmix64(seed ^ ((uint64_t)level << 40) ^ (uint64_t)(uint32_t)i);
-  double h = (double)(z >> 11) * (1.0 / 9007199254740992.0);
-  w[i] = add_rn((double)cnt, h);
-  cf[i] = cnt == 0 ? (int8_t)-1 : (int8_t)0;
-  if (cnt) atomicAdd(undecided, 1);
-}
-
-// skip: the previous round's undecided count (nullptr in the first round);
-// a round after the last undecided point was decided does nothing
-__global__ void k_pmis_select(int n, const int *rp, const int *ci, const uint8_t *S, const int *tpos,
-                              const double *w, const int8_t *cf, int8_t *newc, const int *skip) {
-  if (skip && *skip == 0) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int8_t best = 0;
-  if (cf[i] == 0) {
-    best = 1;
-    long long wi = __double_as_longlong(w[i]);      // weights are >= +0: their bits order them
-    for (int q = rp[i]; q < rp[i + 1] && best; q++) {
-      int j = ci[q];
-      if (j == i || !(S[q] || S[tpos[q]]) || cf[j] != 0) continue;
-      long long wj = __double_as_longlong(w[j]);
-      if (wj > wi || (wj == wi && j < i)) best = 0;
-    }
+  if (i < n) {
+    for (int q = rp[i]; q < rp[i + 1]; q++) if (ci[q] != i && S[tpos[q]]) cnt++;   // |S^T_i|
+    uint64_t z = splitmix64(seed ^ ((uint64_t)level << 40) ^ (uint64_t)(uint32_t)i);
+    double h = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    w[i] = add_rn((double)cnt, h);
+    cf[i] = cnt == 0 ? (int8_t)-1 : (int8_t)0;
+    newc[i] = 0;                       // no candidate flag left over from another level or setup
   }
-  newc[i] = best;
+  warp_append(i < n && cnt != 0, i, undecided, list);
 }
 
-__global__ void k_pmis_update(int n, const int *rp, const int *ci, const uint8_t *S, int8_t *cf,
-                              const int8_t *newc, int *undecided, const int *skip) {
-  if (skip && *skip == 0) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (cf[i] != 0) return;
-  if (newc[i]) { cf[i] = 1; return; }
-  for (int q = rp[i]; q < rp[i + 1]; q++) {
-    int j = ci[q];
-    if (S[q] && (cf[j] == 1 || newc[j])) { cf[i] = -1; return; }
-  }
-  atomicAdd(undecided, 1);
-}
-
-// The same two PMIS steps with L lanes per row (coarse levels have rows of
-// 20-40 entries, which one thread would walk serially): the lanes split the
-// row's entries and combine their verdicts with ballots, so the outcome is
-// the same boolean as the one-thread version.
+// One PMIS round over the undecided points only: list (cnt[r] entries) ->
+// next (cnt[r + 1] entries).  A round whose list is empty does nothing, so
+// rounds launched past the last one cost a launch each.  L lanes per point
+// (1 for short rows; 4 or 16 split a row's entries, verdicts combined by
+// ballots); the grid strides over the list.
+//   select: an undecided point is a candidate unless an undecided strong
+//           neighbour (in S or S^T) has a larger weight (ties: lower index);
+//   update: candidates become C; an undecided point with a strong (S)
+//           neighbour that is C or a candidate becomes F; the rest stay
+//           undecided and go to the next list.
+// Weights are >= +0, so their bit patterns order them.  newc of a point that
+// left the lists keeps its last value: 1 only for C points, which the update
+// test also finds through cf.
 template <int L>
-__global__ void k_pmis_select_lanes(int n, const int *rp, const int *ci, const uint8_t *S, const int *tpos,
-                                    const double *w, const int8_t *cf, int8_t *newc, const int *skip) {
-  if (skip && *skip == 0) return;
-  int g = (blockIdx.x * blockDim.x + threadIdx.x) / L, k = threadIdx.x % L;
-  int i = g < n ? g : n - 1;
-  bool cand = cf[i] == 0, beaten = false;
-  if (cand) {
-    long long wi = __double_as_longlong(w[i]);      // weights are >= +0: their bits order them
+__global__ void k_pmis_select_w(const int *rp, const int *ci, const uint8_t *S, const int *tpos, const double *w,
+                                const int8_t *cf, int8_t *newc, const int *list, const int *cnt) {
+  int m = *cnt;
+  if (m == 0) return;
+  int groups = gridDim.x * blockDim.x / L, k = threadIdx.x % L;
+  for (int g0 = (blockIdx.x * blockDim.x + threadIdx.x) / L;; g0 += groups) {
+    if (__all_sync(0xffffffffu, g0 >= m)) break;
+    int g = g0 < m ? g0 : m - 1, i = list[g];
+    bool beaten = false;
+    long long wi = __double_as_longlong(w[i]);
     for (int q = rp[i] + k; q < rp[i + 1]; q += L) {
       int j = ci[q];
       if (j == i || !(S[q] || S[tpos[q]]) || cf[j] != 0) continue;
       long long wj = __double_as_longlong(w[j]);
       if (wj > wi || (wj == wi && j < i)) { beaten = true; break; }
     }
+    if (L > 1) {
+      unsigned lanes = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) / L * L));
+      beaten = (__ballot_sync(0xffffffffu, beaten) & lanes) != 0;
+    }
+    if (k == 0 && g0 < m) newc[i] = beaten ? 0 : 1;
   }
-  unsigned lanes = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) / L * L));
-  bool any = __ballot_sync(0xffffffffu, beaten) & lanes;
-  if (k == 0 && g < n) newc[i] = (cand && !any) ? 1 : 0;
 }
 
 template <int L>
-__global__ void k_pmis_update_lanes(int n, const int *rp, const int *ci, const uint8_t *S, int8_t *cf,
-                                    const int8_t *newc, int *undecided, const int *skip) {
-  if (skip && *skip == 0) return;
-  int g = (blockIdx.x * blockDim.x + threadIdx.x) / L, k = threadIdx.x % L;
-  int i = g < n ? g : n - 1;
-  bool open = cf[i] == 0 && !newc[i], hit = false;
-  if (open)
-    for (int q = rp[i] + k; q < rp[i + 1]; q += L) {
-      int j = ci[q];
-      if (S[q] && (cf[j] == 1 || newc[j])) { hit = true; break; }
+__global__ void k_pmis_update_w(const int *rp, const int *ci, const uint8_t *S, int8_t *cf, const int8_t *newc,
+                                const int *list, const int *cnt, int *next, int *cnt_next) {
+  int m = *cnt;
+  if (m == 0) return;
+  int groups = gridDim.x * blockDim.x / L, k = threadIdx.x % L;
+  for (int g0 = (blockIdx.x * blockDim.x + threadIdx.x) / L;; g0 += groups) {
+    if (__all_sync(0xffffffffu, g0 >= m)) break;
+    int g = g0 < m ? g0 : m - 1, i = list[g];
+    bool sel = newc[i] != 0, hit = false;
+    if (!sel)
+      for (int q = rp[i] + k; q < rp[i + 1]; q += L) {
+        int j = ci[q];
+        if (S[q] && (cf[j] == 1 || newc[j])) { hit = true; break; }
+      }
+    if (L > 1) {
+      unsigned lanes = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) / L * L));
+      hit = (__ballot_sync(0xffffffffu, hit) & lanes) != 0;
     }
-  unsigned lanes = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) / L * L));
-  bool any = __ballot_sync(0xffffffffu, hit) & lanes;
-  if (k != 0 || g >= n || cf[i] != 0) return;
-  if (newc[i]) { cf[i] = 1; return; }
-  if (any) { cf[i] = -1; return; }
-  atomicAdd(undecided, 1);
+    bool lead = k == 0 && g0 < m;
+    if (lead && sel) cf[i] = 1;
+    else if (lead && hit) cf[i] = -1;
+    warp_append(lead && !sel && !hit, i, cnt_next, next);
+  }
 }
 
 // lanes per row for the PMIS steps: one thread for short rows, then the
@@ -863,28 +861,27 @@ static const int *amg_read(amg_hier &h, int lo, int count, cudaStream_t s) {
   return h.hflag;
 }
 
-// PMIS rounds [r0, r1): round r runs only while cnt[r] > 0, so the rounds
-// past the last one do nothing
+// PMIS rounds [r0, r1) over the undecided-point lists (round r reads list r
+// % 2 with cnt[r] entries and fills list (r + 1) % 2, counting into cnt[r +
+// 1]); a round after the last undecided point was decided does nothing.
+// Grids stride over the lists: the first two rounds sized for every point,
+// later ones for an eighth (their lists are short; a longer one is strided).
 static void pmis_rounds(amg_level &L, amg_hier &h, int n, int lanes, int r0, int r1, cudaStream_t s) {
   int *cnt = h.flag.p + AF_CNT;
   for (int r = r0; r < r1; r++) {
-    if (lanes == 1) {
-      k_pmis_select<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, h.hashw.p,
-                                                     L.cf.p, h.newc.p, cnt + r);
-      k_pmis_update<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, h.newc.p,
-                                                     cnt + r + 1, cnt + r);
-    } else {
-      unsigned gl = grid_for((size_t)n * lanes, 128);
-#define PMIS_LANES(LL)                                                                                          \
-      if (lanes == LL) {                                                                                        \
-        k_pmis_select_lanes<LL><<<gl, 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, h.hashw.p,      \
-                                                   L.cf.p, h.newc.p, cnt + r);                                  \
-        k_pmis_update_lanes<LL><<<gl, 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, h.newc.p,         \
-                                                   cnt + r + 1, cnt + r);                                       \
-      }
-      PMIS_LANES(4) PMIS_LANES(16)
-#undef PMIS_LANES
+    size_t pts = r < 2 ? (size_t)n : ((size_t)n + 7) / 8;
+    unsigned g = (unsigned)std::min<size_t>(grid_for(pts * lanes, 128), 152 * 16);
+    const int *lst = h.plist.p + (size_t)(r & 1) * n;
+    int *nxt = h.plist.p + (size_t)((r + 1) & 1) * n;
+#define PMIS_ROUND(LL)                                                                                        \
+    if (lanes == LL) {                                                                                        \
+      k_pmis_select_w<LL><<<g, 128, 0, s>>>(L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, h.hashw.p, L.cf.p,      \
+                                            h.newc.p, lst, cnt + r);                                          \
+      k_pmis_update_w<LL><<<g, 128, 0, s>>>(L.A.rp.p, L.A.ci.p, L.strong.p, L.cf.p, h.newc.p, lst, cnt + r,   \
+                                            nxt, cnt + r + 1);                                                \
     }
+    PMIS_ROUND(1) PMIS_ROUND(4) PMIS_ROUND(16)
+#undef PMIS_ROUND
   }
   RS_LAUNCHED(2 * (r1 - r0));
   RS_CHECK_LAUNCH();
@@ -972,9 +969,9 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
     if (nnz_hint > 8LL * n) k_tpos_warp<<<grid_for((size_t)n * 32, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.tpos.p, F + AF_SYM);
     else k_tpos<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.tpos.p, F + AF_SYM);
     k_strength<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, o.theta, L.strong.p);
-    h.hashw.ensure(n); h.newc.ensure(n);
+    h.hashw.ensure(n); h.newc.ensure(n); h.plist.ensure(2 * (size_t)n);
     k_pmis_init<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, o.seed, l,
-                                                 h.hashw.p, L.cf.p, F + AF_CNT);
+                                                 h.hashw.p, L.cf.p, h.newc.p, F + AF_CNT, h.plist.p);
     RS_LAUNCHED(3);
     RS_CHECK_LAUNCH();
     // as many rounds as the previous setup took here, plus two (spare

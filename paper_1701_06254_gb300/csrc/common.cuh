@@ -167,6 +167,7 @@ struct amg_hier {
   dbuf<double> dense_a;         // the coarsest operator as a dense matrix (setup scratch)
   dbuf<double> hashw;           // PMIS weights
   dbuf<int8_t> newc;
+  dbuf<int> plist;              // PMIS undecided-point lists (two of n)
   // the V-cycle of the current hierarchy as a CUDA graph ([0] FP64, [1] FP32),
   // captured on first use after a setup; the capture stream only records
   cudaGraphExec_t vc_exec[2] = {nullptr, nullptr};
