@@ -126,6 +126,61 @@ __global__ void k_qi(int n, int nb, const int *rp, const int *dpos, double *val,
   if (val32) for (int q = rp[i]; q < rp[i + 1]; q++) for (int e = 0; e < 4; e++) val32[4 * (size_t)q + e] = (float)val[4 * (size_t)q + e];
 }
 
+// The same Quasi-IMPES decoupling with the FP32 copy and the double-float
+// lo plane written in the same pass: one warp per 32 block rows reads its
+// contiguous range of blocks coalesced (lane t takes block q0 + t + 32k;
+// its row by a binary search over the warp's row pointers held in lanes),
+// updates the pressure row of each cell block with the row's ratio (the same
+// round-to-nearest operations as k_qi) and writes val, val32 and lo.  Well
+// rows keep their blocks; D and b per row as in k_qi.
+__global__ void __launch_bounds__(256) k_qi_fused(int n, int nb, const int *__restrict__ rp,
+                                                  const int *__restrict__ dpos, double *__restrict__ val,
+                                                  double *__restrict__ b, double *__restrict__ dmat,
+                                                  float *__restrict__ val32, float *__restrict__ lo) {
+  int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int r0 = (blockIdx.x * (blockDim.x >> 5) + wid) * 32;
+  if (r0 >= nb) return;
+  int r = r0 + lane, rend = min(r0 + 32, nb);
+  int myq0 = r < nb ? rp[r] : rp[rend];
+  double ratio = 0.0;
+  if (r < n) {
+    const double *M = val + 4 * (size_t)dpos[r];
+    ratio = div_rn(M[1], M[3]);
+  }
+  if (r < nb) {
+    double *D = dmat + 4 * (size_t)r;
+    D[0] = 1; D[1] = r < n ? ratio : 0.0; D[2] = 0; D[3] = 1;
+    if (r < n) b[2 * (size_t)r] = sub_rn(b[2 * (size_t)r], mul_rn(ratio, b[2 * (size_t)r + 1]));
+  }
+  int nr = rend - r0;
+  int q0 = __shfl_sync(0xffffffffu, myq0, 0), q1 = rp[rend];
+  for (int qb = q0; qb < q1; qb += 32) {
+    int q = qb + lane;
+    // the row of block q: the last row of the warp whose first block is <= q
+    int lo_ = 0, hi_ = nr - 1;
+#pragma unroll
+    for (int it = 0; it < 5; it++) {
+      int mid = (lo_ + hi_ + 1) >> 1;
+      int st = __shfl_sync(0xffffffffu, myq0, mid);
+      if (st <= q) lo_ = mid; else hi_ = mid - 1;
+    }
+    double rt = __shfl_sync(0xffffffffu, ratio, lo_);
+    if (q < q1) {
+      double4 B = reinterpret_cast<double4 *>(val)[q];
+      if (r0 + lo_ < n) {
+        B.x = sub_rn(B.x, mul_rn(rt, B.z));
+        B.y = sub_rn(B.y, mul_rn(rt, B.w));
+        reinterpret_cast<double2 *>(val)[2 * (size_t)q] = make_double2(B.x, B.y);
+      }
+      float4 h = make_float4((float)B.x, (float)B.y, (float)B.z, (float)B.w);
+      reinterpret_cast<float4 *>(val32)[q] = h;
+      reinterpret_cast<float4 *>(lo)[q] =
+          make_float4(__double2float_rn(B.x - (double)h.x), __double2float_rn(B.y - (double)h.y),
+                      __double2float_rn(B.z - (double)h.z), __double2float_rn(B.w - (double)h.w));
+    }
+  }
+}
+
 __global__ void k_identity_d(int nb, double *dmat) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
@@ -427,19 +482,23 @@ void ls_setup(sim_ls_s *ls) {
   rs_timed tm(ls, SIM_T_DECOUPLE);
   if (ls->o.decoupling == SIM_DEC_ABF)
     k_abf<<<g, 128, 0, s>>>(ls->n, ls->nb, ls->rp.p, ls->dpos.p, ls->val.p, ls->b.p, ls->dmat.p, v32);
-  else if (ls->o.decoupling == SIM_DEC_QI)
+  else if (ls->o.decoupling == SIM_DEC_QI && !v32)
     k_qi<<<g, 128, 0, s>>>(ls->n, ls->nb, ls->rp.p, ls->dpos.p, ls->val.p, ls->b.p, ls->dmat.p, v32);
-  else {
+  else if (ls->o.decoupling != SIM_DEC_QI) {
     k_identity_d<<<g, 128, 0, s>>>(ls->nb, ls->dmat.p);
     if (v32) rs_cast_d2f(ls->val.p, v32, 4 * (size_t)ls->nnzb, s);
   }
-  RS_LAUNCHED(1);
   if (v32) {                                 // the double-float SpMV's lo plane
     size_t m4 = 4 * (size_t)ls->nnzb;
     ls->vallo.ensure(m4);
-    k_val_lo<<<grid_for(m4, 256), 256, 0, s>>>(m4, ls->val.p, v32, ls->vallo.p);
+    if (ls->o.decoupling == SIM_DEC_QI)      // decoupling, FP32 copy and lo plane in one pass
+      k_qi_fused<<<grid_for(ls->nb, 256), 256, 0, s>>>(ls->n, ls->nb, ls->rp.p, ls->dpos.p, ls->val.p, ls->b.p,
+                                                       ls->dmat.p, v32, ls->vallo.p);
+    else
+      k_val_lo<<<grid_for(m4, 256), 256, 0, s>>>(m4, ls->val.p, v32, ls->vallo.p);
     RS_LAUNCHED(1);
   }
+  if (!(ls->o.decoupling == SIM_DEC_QI && v32)) RS_LAUNCHED(1);
   csr_dev<double> &A0 = ls->amg.lev[0].A;
   k_extract_app<<<grid_for(A0.nnz, 256), 256, 0, s>>>(A0.nnz, ls->app_src.p, ls->val.p, A0.v.p);
   RS_LAUNCHED(1);
