@@ -23,6 +23,7 @@
 struct fluid_c {
   double rho_ref[2], c_f[2], mu_ref[2], c_mu[2];
   double p_ref, c_r, swc, sor, nw, no, krw_max, kro_max, g;
+  double span, inv_span;               // 1 - swc - sor and its reciprocal (formed once, IEEE)
   int pc_n;                            // 0: no capillary pressure
   double pc_sw[PC_MAX], pc_val[PC_MAX];
 };
@@ -97,8 +98,7 @@ __device__ __forceinline__ void cell_props(const fluid_c &f, double phir, double
   P.phi = phir * (1.0 + f.c_r * dp);
   P.dphi = phir * f.c_r;
   capillary(f, sw, P.pc, P.dpc);
-  double span = sub_rn(sub_rn(1.0, f.swc), f.sor);
-  double sh = div_rn(sub_rn(sw, f.swc), span), dsh = 1.0 / span;
+  double sh = div_rn(sub_rn(sw, f.swc), f.span), dsh = f.inv_span;
   if (sh < 0.0) { sh = 0.0; dsh = 0.0; } else if (sh > 1.0) { sh = 1.0; dsh = 0.0; }
   P.kr[0] = f.krw_max * corey(sh, f.nw);
   P.dkr[0] = f.krw_max * f.nw * corey(sh, f.nw - 1.0) * dsh;
@@ -247,14 +247,21 @@ k_assemble(int nx, int ny, int nz, fluid_c f, double top, double dz, double vol_
       double mc = pr[(size_t)a * n + c], dmpc = pr[(size_t)(2 + a) * n + c], dmsc = pr[(size_t)(4 + a) * n + c];
       double potc = pr[(size_t)(6 + a) * n + c], dpotc = pr[(size_t)(8 + a) * n + c];
       double dpotsc = a == 0 ? pr[(size_t)10 * n + c] : 0.0, dpotsd = a == 0 ? pr[(size_t)10 * n + d] : 0.0;
-      bool upc = (c < d) ? (potc >= potd) : !(potd >= potc);
+      // upstream side by the potentials (compared on integer keys: the same
+      // decision as the IEEE comparison, off the FP64 pipe); the mobility
+      // derivative terms only on the upstream side, so each derivative is one
+      // product plus, upstream, one more (T dpot shared)
+      long long kc = dkey(potc), kd = dkey(potd);
+      bool upc = (c < d) ? (kc >= kd) : !(kd >= kc);
       double dpot = potd - potc;
       double Tm = T * (upc ? mc : md);
       double F = Tm * dpot;
-      double dFdpc = T * ((upc ? dmpc : 0.0) * dpot) - Tm * dpotc;
-      double dFdsc = T * ((upc ? dmsc : 0.0) * dpot) - Tm * dpotsc;
-      double dFdpd = T * ((upc ? 0.0 : dmpd) * dpot) + Tm * dpotd;
-      double dFdsd = T * ((upc ? 0.0 : dmsd) * dpot) + Tm * dpotsd;
+      double X = T * dpot;
+      double up_p = (upc ? dmpc : dmpd) * X, up_s = (upc ? dmsc : dmsd) * X;
+      double dFdpc = (upc ? up_p : 0.0) - Tm * dpotc;
+      double dFdsc = (upc ? up_s : 0.0) - Tm * dpotsc;
+      double dFdpd = (upc ? 0.0 : up_p) + Tm * dpotd;
+      double dFdsd = (upc ? 0.0 : up_s) + Tm * dpotsd;
       if (e == 0) R0 -= F; else R1 -= F;
       D[2 * e] -= dFdpc; D[2 * e + 1] -= dFdsc;
       O[2 * e] = -dFdpd; O[2 * e + 1] = -dFdsd;
@@ -781,6 +788,8 @@ extern "C" sim_status sim_create(sim_t *out, const sim_grid *g, const sim_rock *
     for (int a = 0; a < 2; a++) { F.rho_ref[a] = f->rho_ref[a]; F.c_f[a] = f->c_f[a]; F.mu_ref[a] = f->mu_ref[a]; F.c_mu[a] = f->c_mu[a]; }
     F.p_ref = f->p_ref; F.c_r = f->c_r; F.swc = f->swc; F.sor = f->sor; F.nw = f->nw; F.no = f->no;
     F.krw_max = f->krw_max; F.kro_max = f->kro_max; F.g = f->g;
+    F.span = (1.0 - F.swc) - F.sor;                   // the same IEEE operations as on the device
+    F.inv_span = 1.0 / F.span;
     F.pc_n = f->pc_n;
     for (int k = 0; k < f->pc_n; k++) { F.pc_sw[k] = f->pc_sw[k]; F.pc_val[k] = f->pc_val[k]; }
   }
