@@ -151,7 +151,10 @@ void ras_build_static(sim_ls_s *ls) {
       mmax = std::max(mmax, (int)ms);
     }
     R.m_max = mmax;
-    R.smem_bytes = ((size_t)mmax * yb + 15) / 16 * 16 + ring;    // the ring, then the local vector
+    // the ring, then the local vector, then one product per entry of a group
+    // (a group holds at most a chunk: 16-bit column + block per entry)
+    int chunk = ring / 4, pmax = chunk / (2 + vb) + 1;
+    R.smem_bytes = ((size_t)mmax * yb + 15) / 16 * 16 + ring + (size_t)pmax * yb;
     R.smem_path = fits16 && R.smem_bytes <= RAS_SMEM_BUDGET;
     if (R.smem_path) {
       h2d(R.blob_off, boff, st); R.blob.alloc(boff[nsub]);
@@ -760,6 +763,15 @@ template <int RB> __device__ __forceinline__ void ring_blk4(const unsigned char 
   b0 = u.x; b1 = u.y; b2 = v.x; b3 = v.y;
 }
 
+// explicit round-to-nearest products and sums (no contraction): the
+// entry-parallel sweep forms B_e y_c = fma(b0, y0, b1 y1) and subtracts it
+__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
+
 template <class T> struct v2_t;
 template <> struct v2_t<float> { typedef float2 type; };
 template <> struct v2_t<double> { typedef double2 type; };
@@ -810,7 +822,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity
 template <class T, class Tin, bool ACC, class TB>
 __global__ void __launch_bounds__(32) k_ras_apply_stream(const long long *blob_off, const unsigned char *blobs,
                                                         const int *gidx_all, const int *sub_ptr, const int *order,
-                                                        const Tin *__restrict__ f, T *__restrict__ x, int *err) {
+                                                        const Tin *__restrict__ f, T *__restrict__ x, int *err,
+                                                        int m_max_all) {
   constexpr int RB = ring_cfg<TB>::R, CB = ring_cfg<TB>::C, NSLOT = RB / CB, RU = rrec_u<TB>();
   extern __shared__ uint4 sm4[];
   __shared__ uint64_t bar[NSLOT];
@@ -823,6 +836,7 @@ __global__ void __launch_bounds__(32) k_ras_apply_stream(const long long *blob_o
   unsigned char *ring = reinterpret_cast<unsigned char *>(sm4);
   T2 *y = reinterpret_cast<T2 *>(ring + RB);
   const int m = sub_ptr[s + 1] - sub_ptr[s];
+  T2 *P = reinterpret_cast<T2 *>(reinterpret_cast<unsigned char *>(y) + (((size_t)m_max_all * sizeof(T2) + 15) & ~(size_t)15));
   // header: m, L groups, U groups, stream bytes, first group's start
   const int4 hd = *reinterpret_cast<const int4 *>(st);
   const int ngL = hd.y, ng = hd.y + hd.z, total = hd.w;
@@ -870,20 +884,29 @@ __global__ void __launch_bounds__(32) k_ras_apply_stream(const long long *blob_o
     if (!__all_sync(0xffffffffu, ok)) return;
     const bool up = g >= ngL;
     const int rrec = up ? RU : 8;
+    const uint16_t *cols = reinterpret_cast<const uint16_t *>(G + 16 + al16(rows * rrec));
+    const TB *vals = reinterpret_cast<const TB *>(G + 16 + al16(rows * rrec) + al16(2 * ent));
+    // every entry's product B_e y_c with all lanes (the columns belong to
+    // earlier levels, final already), then each row subtracts its own
+    // products in stored order
+    for (int e = lane; e < ent; e += 32) {
+      T b0, b1, b2, b3;
+      blk4(vals + 4 * e, b0, b1, b2, b3);
+      T2 yc = y[cols[e]], pe;
+      pe.x = r_fma(b0, yc.x, r_mul(b1, yc.y));
+      pe.y = r_fma(b2, yc.x, r_mul(b3, yc.y));
+      P[e] = pe;
+    }
+    __syncwarp();
     if (lane < rows) {
       const unsigned char *rec = G + 16 + lane * rrec;
       const uint2 ri = *reinterpret_cast<const uint2 *>(rec);
       const int i = ri.x & 0xffff, e0 = ri.x >> 16, e1 = ri.y & 0xffff;
-      const uint16_t *cols = reinterpret_cast<const uint16_t *>(G + 16 + al16(rows * rrec));
-      const TB *vals = reinterpret_cast<const TB *>(G + 16 + al16(rows * rrec) + al16(2 * ent));
       T2 a = y[i];
       for (int e = e0; e < e1; e++) {
-        int c = cols[e];
-        T b0, b1, b2, b3;
-        blk4(vals + 4 * e, b0, b1, b2, b3);
-        T2 yc = y[c];
-        a.x -= b0 * yc.x + b1 * yc.y;
-        a.y -= b2 * yc.x + b3 * yc.y;
+        T2 pe = P[e];
+        a.x = r_sub(a.x, pe.x);
+        a.y = r_sub(a.y, pe.y);
       }
       if (up) {
         T d0, d1, d2, d3;
@@ -954,10 +977,12 @@ static void ras_apply_go(sim_ls_s *ls, const Tin *f, T *x, bool acc) {
   ras_data &R = ls->ras;
   if (acc)
     k_ras_apply_stream<T, Tin, true, TB><<<R.nsub, 32, R.smem_bytes, ls->st>>>(R.blob_off.p, R.blob.p, R.gidx.p,
-                                                                              R.sub_ptr.p, R.order.p, f, x, ls->errw_dev);
+                                                                              R.sub_ptr.p, R.order.p, f, x, ls->errw_dev,
+                                                                              R.m_max);
   else
     k_ras_apply_stream<T, Tin, false, TB><<<R.nsub, 32, R.smem_bytes, ls->st>>>(R.blob_off.p, R.blob.p, R.gidx.p,
-                                                                               R.sub_ptr.p, R.order.p, f, x, ls->errw_dev);
+                                                                               R.sub_ptr.p, R.order.p, f, x, ls->errw_dev,
+                                                                               R.m_max);
 }
 template <class T, class Tin> static void ras_apply_launch(sim_ls_s *ls, const Tin *f, T *x, bool acc);
 template <> void ras_apply_launch<double, double>(sim_ls_s *ls, const double *f, double *x, bool acc) {
