@@ -20,7 +20,8 @@
 // a fixed order, flow through a small shared-memory ring filled by bulk
 // copies (cp.async.bulk + mbarrier) a few chunks ahead of the sweep.  The
 // stream of a subdomain (16-byte aligned pieces):
-//   header  {m, L groups, U groups, stream bytes, first group's start} 32 B
+//   header  {m, L groups, U groups, stream bytes, first group's start and
+//           bytes} 32 B
 //   groups  the rows of the L sweep (L levels 1.., level 0 has no entries),
 //           then the rows of the U sweep (U levels 0..), level by level;
 //           a level is split into groups of at most 32 rows (one per lane)
@@ -28,7 +29,7 @@
 //           end of the ring (the stream is padded to the next ring period
 //           instead), so its pieces are contiguous in shared memory
 // A group:
-//   {nrows | nent << 16, bytes, next group's start}   16 B
+//   {nrows | nent << 16, bytes, next group's start, next group's bytes} 16 B
 //   row records: local row, first and end entry   8 B (L) or RREC_U (U, with
 //               (group-relative), U: the inverse  the 2x2 block, 4 values)
 //               diagonal block
@@ -699,8 +700,9 @@ __global__ void k_ras_pack(const int *sub_ptr, const int *lrp_ptr, const int *ex
     ngr[2] = off;
     int *hdr = (int *)b;
     hdr[0] = m; hdr[1] = ngr[0]; hdr[2] = ngr[1]; hdr[3] = off;
-    // each group records the next one's start: the stream header the first
+    // each group records the next one's start and size: the stream header the first's
     hdr[4] = ng ? (gd[0].w >> 1) : 0;
+    hdr[5] = ng ? gby[0] : 0;
   }
   __syncthreads();
   int ng = ngr[0] + ngr[1];
@@ -720,7 +722,8 @@ __global__ void k_ras_pack(const int *sub_ptr, const int *lrp_ptr, const int *ex
     if (lane == 0) {
       int *h = (int *)G;
       h[0] = rows | (ent << 16); h[1] = al16(16 + al16(rows * rrec) + al16(2 * ent) + ent * VB);
-      h[2] = g + 1 < ng ? (gd[g + 1].w >> 1) : 0; h[3] = 0;          // where the next group starts
+      h[2] = g + 1 < ng ? (gd[g + 1].w >> 1) : 0;                    // where the next group starts
+      h[3] = g + 1 < ng ? gby[g + 1] : 0;                              // and its bytes
     }
     if (lane < rows) {
       uint16_t *rec = (uint16_t *)(G + 16 + lane * rrec);
@@ -837,10 +840,11 @@ __global__ void __launch_bounds__(32) k_ras_apply_stream(const long long *blob_o
   T2 *y = reinterpret_cast<T2 *>(ring + RB);
   const int m = sub_ptr[s + 1] - sub_ptr[s];
   T2 *P = reinterpret_cast<T2 *>(reinterpret_cast<unsigned char *>(y) + (((size_t)m_max_all * sizeof(T2) + 15) & ~(size_t)15));
-  // header: m, L groups, U groups, stream bytes, first group's start
+  // header: m, L groups, U groups, stream bytes, first group's start and bytes
   const int4 hd = *reinterpret_cast<const int4 *>(st);
   const int ngL = hd.y, ng = hd.y + hd.z, total = hd.w;
   int cons = reinterpret_cast<const int *>(st)[4];
+  int cur = reinterpret_cast<const int *>(st)[5];   // the group's bytes (each header names the next one's)
   const int nchunk = (total + CB - 1) / CB;
   if (lane == 0) {
     for (int k = 0; k < NSLOT; k++) mbar_init(&bar[k], 1);
@@ -873,15 +877,13 @@ __global__ void __launch_bounds__(32) k_ras_apply_stream(const long long *blob_o
   int landed = 0, freed = 0;                         // chunks waited for; chunks behind the sweep
   bool ok = true;
   for (int g = 0; g < ng; g++) {
-    // the group's header first, then the rest of its bytes
-    int need = (cons + 16 + CB - 1) / CB;
+    // the whole group, its size known from the previous header
+    int need = (cons + cur + CB - 1) / CB;
     for (; landed < need && ok; landed++) ok = mbar_wait_bounded(&bar[landed % NSLOT], (landed / NSLOT) & 1, err, 3);
+    if (!__all_sync(0xffffffffu, ok)) return;
     const unsigned char *G = ring + (cons & (RB - 1));         // the group is contiguous in the ring
     const int4 h4 = *reinterpret_cast<const int4 *>(G);
     const int rows = h4.x & 0xffff, ent = h4.x >> 16;
-    need = (cons + h4.y + CB - 1) / CB;
-    for (; landed < need && ok; landed++) ok = mbar_wait_bounded(&bar[landed % NSLOT], (landed / NSLOT) & 1, err, 3);
-    if (!__all_sync(0xffffffffu, ok)) return;
     const bool up = g >= ngL;
     const int rrec = up ? RU : 8;
     const uint16_t *cols = reinterpret_cast<const uint16_t *>(G + 16 + al16(rows * rrec));
@@ -919,6 +921,7 @@ __global__ void __launch_bounds__(32) k_ras_apply_stream(const long long *blob_o
       }
     }
     cons = h4.z;                                     // the next group's start
+    cur = h4.w;                                      // and bytes
     __syncwarp();
     // chunks wholly behind the sweep are free: refill them
     if (lane == 0 && cons / CB > freed) {
