@@ -395,6 +395,42 @@ __global__ void k_sort_rows_warp(int n, const int *rp, int *ci, double *v) {
   }
 }
 
+// the same with G lanes per row (G = 8 or 16) for levels whose rows are
+// short: a bitonic network over the group's lanes (rows of at most G
+// entries), longer rows by an insertion sort in the group's first lane
+template <int G>
+__global__ void k_sort_rows_g(int n, const int *rp, int *ci, double *v) {
+  if (n <= 0) return;
+  int gi = (blockIdx.x * blockDim.x + threadIdx.x) / G, k = threadIdx.x % G;
+  bool valid = gi < n;
+  int i = valid ? gi : n - 1;                       // whole groups stay in the shuffles
+  int a0 = rp[i], len = rp[i + 1] - a0;
+  bool small = len <= G;
+  int c = (small && k < len) ? ci[a0 + k] : INT_MAX;
+  double x = (small && k < len) ? v[a0 + k] : 0.0;
+#pragma unroll
+  for (int kk = 2; kk <= G; kk <<= 1)
+#pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      int oc = __shfl_xor_sync(0xffffffffu, c, j, G);
+      double ox = __shfl_xor_sync(0xffffffffu, x, j, G);
+      bool up = (k & kk) == 0, lower = (k & j) == 0;
+      bool take = lower == up ? oc < c : oc > c;     // keep the smaller key on the ascending side
+      if (take) { c = oc; x = ox; }
+    }
+  if (!valid) return;
+  if (small) {
+    if (k < len) { ci[a0 + k] = c; v[a0 + k] = x; }
+  } else if (k == 0) {
+    int a1 = a0 + len;
+    for (int a = a0 + 1; a < a1; a++) {
+      int cc = ci[a]; double xx = v[a]; int b = a - 1;
+      while (b >= a0 && ci[b] > cc) { ci[b + 1] = ci[b]; v[b + 1] = v[b]; b--; }
+      ci[b + 1] = cc; v[b + 1] = xx;
+    }
+  }
+}
+
 // -------------------------------------------------------------- SpGEMM ----
 // C = A B, each column of a row of C the sum of its products A_ik B_kj in
 // the order of k (the row of A's column order), starting from 0.  Rows of A
@@ -1015,7 +1051,13 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
     rs_scan_dev(L.R.rp.p, L.R.rp.p, nc, L.R.rp.p + nc, nullptr, s);
     k_transpose_fill<<<grid_for(n, 256), 256, 0, s>>>(n, L.P.rp.p, L.P.ci.p, L.P.v.p, L.R.rp.p, fill.p, L.R.ci.p,
                                                       L.R.v.p);
-    k_sort_rows_warp<<<grid_for((size_t)nc * 32, 128), 128, 0, s>>>(nc, L.R.rp.p, L.R.ci.p, L.R.v.p);
+    {                                                  // rows of R: lanes per row by their mean length
+      double avg = nc ? (double)L.P.nnz / nc : 0.0;
+      if (avg <= 6.0) k_sort_rows_g<8><<<grid_for((size_t)nc * 8, 128), 128, 0, s>>>(nc, L.R.rp.p, L.R.ci.p, L.R.v.p);
+      else if (avg <= 12.0)
+        k_sort_rows_g<16><<<grid_for((size_t)nc * 16, 128), 128, 0, s>>>(nc, L.R.rp.p, L.R.ci.p, L.R.v.p);
+      else k_sort_rows_warp<<<grid_for((size_t)nc * 32, 128), 128, 0, s>>>(nc, L.R.rp.p, L.R.ci.p, L.R.v.p);
+    }
     RS_LAUNCHED(2);
     // A_{l+1} = R (A P)
     spgemm_count(L.R, AP, F + AF_RAPTOT, F + AF_RAPMX, s);

@@ -127,7 +127,9 @@ __device__ __forceinline__ void cell_props(const fluid_c &f, double phir, double
 
 __device__ __forceinline__ double depth(double top, double dz, int k) { return add_rn(top, mul_rn((double)k + 0.5, dz)); }
 
-// per-cell mobility / potential table for the face terms: 11 x n (SoA)
+// per-cell table (SoA, 15 x n): mobilities, potentials and their
+// derivatives for the face terms (rows 0-10), and for the accumulation term
+// phi, rho_w, rho_o and d rho_w / d s_w (rows 11-14)
 __global__ void k_props(int n, int nxy, fluid_c f, double top, double dz, const double *phi, const double *p,
                         const double *s, double *pr) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -140,6 +142,8 @@ __global__ void k_props(int n, int nxy, fluid_c f, double top, double dz, const 
   pr[6 * (size_t)n + c] = P.pot[0]; pr[7 * (size_t)n + c] = P.pot[1];
   pr[8 * (size_t)n + c] = P.dpot[0]; pr[9 * (size_t)n + c] = P.dpot[1];
   pr[10 * (size_t)n + c] = P.dpots[0];                // the oil potential does not depend on s_w
+  pr[11 * (size_t)n + c] = P.phi; pr[12 * (size_t)n + c] = P.rho[0]; pr[13 * (size_t)n + c] = P.rho[1];
+  pr[14 * (size_t)n + c] = P.drhos[0];
 }
 
 // geometric two-point transmissibility of the +x, +y, +z face of each cell
@@ -217,17 +221,20 @@ k_assemble(int nx, int ny, int nz, fluid_c f, double top, double dz, double vol_
   if (c >= n) return;
   int nxy = nx * ny, i = c % nx, j = (c / nx) % ny, k = c / nxy;
   double z = depth(top, dz, k);
-  cprops P;
   double pc = p[c], sc = s[c];
-  cell_props(f, phi[c], z, pc, sc, P);
+  // the accumulation term from the table k_props wrote (the same cell_props
+  // values); the full properties only for a perforated cell
+  double Pphi = pr[11 * (size_t)n + c], Prho0 = pr[12 * (size_t)n + c], Prho1 = pr[13 * (size_t)n + c];
+  double Pdrhos0 = pr[14 * (size_t)n + c], Pdphi = phi[c] * f.c_r;
+  double Pdrho0 = f.rho_ref[0] * f.c_f[0], Pdrho1 = f.rho_ref[1] * f.c_f[1];
   double so = 1.0 - sc;
-  double R0 = vol_dt * (P.phi * P.rho[1] * so - acc0[2 * (size_t)c]);
-  double R1 = vol_dt * (P.phi * P.rho[0] * sc - acc0[2 * (size_t)c + 1]);
+  double R0 = vol_dt * (Pphi * Prho1 * so - acc0[2 * (size_t)c]);
+  double R1 = vol_dt * (Pphi * Prho0 * sc - acc0[2 * (size_t)c + 1]);
   double D[4];
-  D[0] = vol_dt * (P.dphi * P.rho[1] + P.phi * P.drho[1]) * so;
-  D[1] = vol_dt * (-P.phi * P.rho[1]);
-  D[2] = vol_dt * (P.dphi * P.rho[0] + P.phi * P.drho[0]) * sc;
-  D[3] = vol_dt * (P.phi * P.rho[0] + P.phi * P.drhos[0] * sc);
+  D[0] = vol_dt * (Pdphi * Prho1 + Pphi * Pdrho1) * so;
+  D[1] = vol_dt * (-Pphi * Prho1);
+  D[2] = vol_dt * (Pdphi * Prho0 + Pphi * Pdrho0) * sc;
+  D[3] = vol_dt * (Pphi * Prho0 + Pphi * Pdrhos0 * sc);
   // neighbours in ascending column order: -z, -y, -x, (self), +x, +y, +z
   int nb_[6] = {k > 0 ? c - nxy : -1, j > 0 ? c - nx : -1, i > 0 ? c - 1 : -1,
                 i + 1 < nx ? c + 1 : -1, j + 1 < ny ? c + nx : -1, k + 1 < nz ? c + nxy : -1};
@@ -271,6 +278,8 @@ k_assemble(int nx, int ny, int nz, fluid_c f, double top, double dz, double vol_
     reinterpret_cast<double2 *>(Bo)[1] = make_double2(O[2], O[3]);
   }
   // perforations of this cell (eq. 10)
+  cprops P;
+  if (cpp[c + 1] > cpp[c]) cell_props(f, phi[c], z, pc, sc, P);
   for (int a2 = cpp[c]; a2 < cpp[c + 1]; a2++) {
     int q = cpi[a2], w = pwell[q];
     double dz5 = mul_rn(mul_rn(f.g, sub_rn(z, wzref[w])), RS_PA2BAR);
@@ -881,7 +890,7 @@ extern "C" sim_status sim_create(sim_t *out, const sim_grid *g, const sim_rock *
     RS_LAUNCHED(1);
   }
   h->p.alloc(n); h->s.alloc(n); h->pb.alloc(nw ? nw : 1); h->acc0.alloc(2 * (size_t)n);
-  h->props.alloc(11 * (size_t)n); h->p0.alloc(n); h->s0.alloc(n); h->pb0.alloc(nw ? nw : 1);
+  h->props.alloc(15 * (size_t)n); h->p0.alloc(n); h->s0.alloc(n); h->pb0.alloc(nw ? nw : 1);
   rs_fill_d(h->p.p, h->fl.p_ref, n, s); rs_fill_d(h->s.p, h->fl.swc, n, s); rs_fill_d(h->pb.p, 0.0, nw ? nw : 1, s);
   h->ls = new sim_ls_s();
   ls_init(h->ls, nx, ny, nz, nw, rp.data(), ci.data(), wc0.data(), h->o, s);
