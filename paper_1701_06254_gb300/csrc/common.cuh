@@ -265,6 +265,7 @@ struct sim_ls_s {
   dbuf<float> vallo;            // lo plane of the decoupled matrix (hi: val32)
   dbuf<double> bcg;             // BiCGSTAB vectors: rh, p, v, s, t, ph, sh, x (2 nb each)
   dbuf<float> bcg32;            // mixed precision: the FP32 preconditioned vector
+  dbuf<float> cprt32;           // CPR: the first RAS stage's output (FP32)
   // timer brackets recorded inside the graph (event nodes): pairs of events
   // and the family of each pair, read back after every replay
   std::vector<cudaEvent_t> gev;

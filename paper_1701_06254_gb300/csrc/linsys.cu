@@ -237,8 +237,12 @@ template <class T> struct vec2_t;
 template <> struct vec2_t<double> { typedef double2 type; };
 template <> struct vec2_t<float> { typedef float2 type; };
 
-// y = A x  (f == nullptr) or y = f - A x.  One warp owns 32 consecutive
-// block rows: the warp reads its contiguous range of blocks coalesced
+// y = A x  (f == nullptr) or y = f - A x.  Optional, for CPR: with e, x's
+// pressure components of the first np rows read as x_p + e (the pressure
+// correction added on the fly, the same FP32 sum as a separate pass), and
+// the corrected x written to xout for the warp's own rows; with pout, the
+// pressure components of y of the first np rows also written there.  One
+// warp owns 32 consecutive block rows: the warp reads its contiguous range of blocks coalesced
 // (lane t takes block q0 + t + 32k), stages the 2-vectors A_q x_{c(q)} in
 // shared memory, and each lane then sums the products of its own row in
 // ascending block order.
@@ -247,7 +251,8 @@ template <> struct vec2_t<float> { typedef float2 type; };
 template <class Tv, class Tx, class Tf, class Ty>
 __global__ void __launch_bounds__(SPMV_WARPS * 32)
 k_bsr_spmv(int nb, const int *__restrict__ rp, const int *__restrict__ ci, const Tv *__restrict__ val,
-           const Tx *__restrict__ x, const Tf *__restrict__ f, Ty *__restrict__ y) {
+           const Tx *__restrict__ x, const Tf *__restrict__ f, Ty *__restrict__ y, int np = 0,
+           const Tx *__restrict__ e = nullptr, Tx *__restrict__ xout = nullptr, Ty *__restrict__ pout = nullptr) {
   __shared__ Ty prod[SPMV_WARPS][SPMV_CHUNK][2];
   int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int r0 = (blockIdx.x * SPMV_WARPS + wid) * 32;
@@ -272,6 +277,7 @@ k_bsr_spmv(int nb, const int *__restrict__ rp, const int *__restrict__ ci, const
         float4 u = __ldg(reinterpret_cast<const float4 *>(val) + q);
         b0 = (Ty)u.x; b1 = (Ty)u.y; b2 = (Ty)u.z; b3 = (Ty)u.w;
       }
+      if (e && c < np) xv.x = xv.x + e[c];
       Ty x0 = (Ty)xv.x, x1 = (Ty)xv.y;
       prod[wid][q - c0][0] = b0 * x0 + b1 * x1;
       prod[wid][q - c0][1] = b2 * x0 + b3 * x1;
@@ -286,13 +292,21 @@ k_bsr_spmv(int nb, const int *__restrict__ rp, const int *__restrict__ ci, const
     typedef typename vec2_t<Ty>::type Y2;
     Y2 o; o.x = a0; o.y = a1;
     reinterpret_cast<Y2 *>(y)[r] = o;
+    if (pout && r < np) pout[r] = a0;
+    if (xout) {
+      X2 xr = reinterpret_cast<const X2 *>(x)[r];
+      if (e && r < np) xr.x = xr.x + e[r];
+      reinterpret_cast<X2 *>(xout)[r] = xr;
+    }
   }
 }
 
 template <class Tv, class Tx, class Tf, class Ty>
-static void spmv(const sim_ls_s *ls, const Tv *val, const Tx *x, const Tf *f, Ty *y, cudaStream_t s) {
+static void spmv(const sim_ls_s *ls, const Tv *val, const Tx *x, const Tf *f, Ty *y, cudaStream_t s,
+                 const Tx *e = nullptr, Tx *xout = nullptr, Ty *pout = nullptr) {
   unsigned g = grid_for(ls->nb, SPMV_WARPS * 32);
-  k_bsr_spmv<Tv, Tx, Tf, Ty><<<g, SPMV_WARPS * 32, 0, s>>>(ls->nb, ls->rp.p, ls->ci.p, val, x, f, y);
+  k_bsr_spmv<Tv, Tx, Tf, Ty><<<g, SPMV_WARPS * 32, 0, s>>>(ls->nb, ls->rp.p, ls->ci.p, val, x, f, y, ls->n, e, xout,
+                                                           pout);
   RS_LAUNCHED(1);
 }
 
@@ -381,21 +395,27 @@ __global__ void k_add_p(int n, const T *e, T *x) {
 // CPR-FPF (Algorithm 2): z = R^{-1} v; r = v - A z; z += Pi_p M(A_pp)^{-1} Pi_r r;
 // r = v - A z; z += R^{-1} r.  FP64 preconditioner: A is the decoupled FP64
 // matrix; mixed: FP32 matrix, factors, hierarchy and vectors (FP64 coarsest).
+// FP32 scratch vector of the CPR application (the first RAS stage's output)
+static float *cpr_scratch(sim_ls_s *ls) {
+  ls->cprt32.ensure(2 * (size_t)ls->nb);
+  return ls->cprt32.p;
+}
+
 void ls_cpr(sim_ls_s *ls, const double *v, double *z64, float *z32) {
   cudaStream_t s = ls->st;
   int n = ls->n;
   amg_level &L0 = ls->amg.lev[0];
   if (ls->o.precision != SIM_PREC_FP64) {
-    float *z = z32, *r = ls->x32b.p;
-    ls_ras_apply<float, double>(ls, v, z, false);                                      // RAS
-    { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, double, float>(ls, ls->val32.p, z, v, r, s); }  // r = v - A z
-    k_gather_p<float, float><<<grid_for(n, 256), 256, 0, s>>>(n, r, L0.f32.p);
-    RS_LAUNCHED(1);
+    // the first RAS stage into a scratch vector; the second SpMV reads it
+    // with the pressure correction added on the fly and writes the
+    // corrected iterate into z; the first SpMV also writes the pressure
+    // residual the V-cycle starts from
+    float *r = ls->x32b.p, *zt = cpr_scratch(ls);
+    ls_ras_apply<float, double>(ls, v, zt, false);                                     // RAS
+    { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, double, float>(ls, ls->val32.p, zt, v, r, s, nullptr, nullptr, L0.f32.p); }  // r = v - A z
     { rs_timed tm(ls, SIM_T_VCYCLE); if (ls->capturing) amg_vcycle<float>(ls->amg, 0, s); else amg_vcycle_graph<float>(ls->amg, s); }  // pressure V-cycle
-    k_add_p<float><<<grid_for(n, 256), 256, 0, s>>>(n, L0.x32.p, z);
-    RS_LAUNCHED(1);
-    { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, double, float>(ls, ls->val32.p, z, v, r, s); }  // r = v - A z
-    ls_ras_apply<float, float>(ls, r, z, true);                                        // RAS, added
+    { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, double, float>(ls, ls->val32.p, zt, v, r, s, L0.x32.p, z32); }  // z = z + P e, r = v - A z
+    ls_ras_apply<float, float>(ls, r, z32, true);                                      // RAS, added
   } else {
     double *z = z64, *r = ls->x64a.p;
     ls_ras_apply<double, double>(ls, v, z, false);
@@ -417,15 +437,11 @@ void ls_cpr32(sim_ls_s *ls, const float *v, float *z) {
   cudaStream_t s = ls->st;
   int n = ls->n;
   amg_level &L0 = ls->amg.lev[0];
-  float *r = ls->x32b.p;
-  ls_ras_apply<float, float>(ls, v, z, false);                                         // RAS
-  { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, float, float>(ls, ls->val32.p, z, v, r, s); }   // r = v - A z
-  k_gather_p<float, float><<<grid_for(n, 256), 256, 0, s>>>(n, r, L0.f32.p);
-  RS_LAUNCHED(1);
+  float *r = ls->x32b.p, *zt = cpr_scratch(ls);
+  ls_ras_apply<float, float>(ls, v, zt, false);                                        // RAS
+  { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, float, float>(ls, ls->val32.p, zt, v, r, s, nullptr, nullptr, L0.f32.p); }   // r = v - A z
   { rs_timed tm(ls, SIM_T_VCYCLE); if (ls->capturing) amg_vcycle<float>(ls->amg, 0, s); else amg_vcycle_graph<float>(ls->amg, s); }  // pressure V-cycle
-  k_add_p<float><<<grid_for(n, 256), 256, 0, s>>>(n, L0.x32.p, z);
-  RS_LAUNCHED(1);
-  { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, float, float>(ls, ls->val32.p, z, v, r, s); }   // r = v - A z
+  { rs_timed tm(ls, SIM_T_SPMV_PREC); spmv<float, float, float, float>(ls, ls->val32.p, zt, v, r, s, L0.x32.p, z); }   // z = z + P e, r = v - A z
   ls_ras_apply<float, float>(ls, r, z, true);                                          // RAS, added
 }
 
@@ -491,6 +507,7 @@ void ls_setup(sim_ls_s *ls) {
   if (v32) {                                 // the double-float SpMV's lo plane
     size_t m4 = 4 * (size_t)ls->nnzb;
     ls->vallo.ensure(m4);
+    cpr_scratch(ls);                         // allocated before any graph records it
     if (ls->o.decoupling == SIM_DEC_QI)      // decoupling, FP32 copy and lo plane in one pass
       k_qi_fused<<<grid_for(ls->nb, 256), 256, 0, s>>>(ls->n, ls->nb, ls->rp.p, ls->dpos.p, ls->val.p, ls->b.p,
                                                        ls->dmat.p, v32, ls->vallo.p);
