@@ -911,7 +911,9 @@ __global__ void __launch_bounds__(ORTHO_BS, 4) k_ortho_update_df(int nu, int ch,
   }
 }
 // V_{j+1} = w / h_{j+1,j}, the reciprocal split once by k_arnoldi_col (isp)
-__global__ void k_scale_df(int nu, const float *w, const float *isp, float *V, int j1, const int *jd) {
+// v_{j+1} = w / h_{j+1,j} into the basis; with vcur, its hi plane also into
+// the fixed buffer the next graph-replayed step's CPR reads
+__global__ void k_scale_df(int nu, const float *w, const float *isp, float *V, int j1, const int *jd, float *vcur) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (jd) j1 = *jd + 1;
   if (i >= nu) return;
@@ -920,16 +922,17 @@ __global__ void k_scale_df(int nu, const float *w, const float *isp, float *V, i
   df_fast(p, e, h, l);
   V[(size_t)(2 * j1) * nu + i] = h;
   V[(size_t)(2 * j1 + 1) * nu + i] = l;
+  if (vcur) vcur[i] = h;
 }
-__global__ void k_start_df(int nu, const double *r, double beta, float *V, double *G, int m) {
+__global__ void k_start_df(int nu, const double *r, double beta, float *V, double *G, int m, float *vcur) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nu) { float h, l; df_split(r[i] * (1.0 / beta), h, l); V[i] = h; V[(size_t)nu + i] = l; }
+  if (i < nu) {
+    float h, l;
+    df_split(r[i] * (1.0 / beta), h, l);
+    V[i] = h; V[(size_t)nu + i] = l;
+    if (vcur) vcur[i] = h;
+  }
   if (i == 0) { double *g = G + (size_t)m * (m + 1) + 2 * m; for (int k = 0; k <= m; k++) g[k] = 0.0; g[0] = beta; }
-}
-// graph replay: the step's basis vector (hi plane) into a fixed buffer
-__global__ void k_basis_get_df(int nu, const float *V, const int *jd, float *vcur) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nu) vcur[i] = V[(size_t)(2 * *jd) * nu + i];
 }
 
 static void ortho_attr() {
@@ -1284,7 +1287,7 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
       ortho_update_df(nu, chd, nv, V32, w2, h2, part, flag, nblk, c, jdp, tk, nrm_b, nullptr, nullptr);
       k_arnoldi_col<<<1, 32, 0, c>>>(j, m, h1, h2, nrm, nrm_b, flag, G, hn, jdp ? hp_dev : hp_dev + 4 * j, jdp,
                                     ls->isp.p);
-      k_scale_df<<<grid_for(nu, 256), 256, 0, c>>>(nu, w2, ls->isp.p, V32, j + 1, jdp);
+      k_scale_df<<<grid_for(nu, 256), 256, 0, c>>>(nu, w2, ls->isp.p, V32, j + 1, jdp, jdp ? ls->vcur32.p : nullptr);
       RS_LAUNCHED(6);
     } else {
       ortho_dots(nu, nv, ls->V.p, ls->w.p, part, 1, nullptr, nblk, c, jdp);
@@ -1345,8 +1348,7 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
   // one Arnoldi step recorded on stream c (the capture stream)
   auto record_step = [&](cudaStream_t c) {
       const int *jd = ls->jd.p;
-      if (df) {
-        k_basis_get_df<<<grid_for(nu, 256), 256, 0, c>>>(nu, V32, jd, ls->vcur32.p);
+      if (df) {                              // vcur32 holds v_j (k_start_df, k_scale_df)
         ls_cpr32(ls, ls->vcur32.p, ls->zcur32.p);
         {
           rs_timed tm(ls, SIM_T_SPMV64);
@@ -1371,7 +1373,7 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
       ortho_tail(c, 0, jd);
       tm.stop();
       k_step_inc<<<1, 1, 0, c>>>(ls->jd.p);
-      RS_LAUNCHED(3);
+      RS_LAUNCHED(df ? 2 : 3);
       RS_CHECK_LAUNCH();
   };
   if (use_graph && !ls->it_exec) {
@@ -1477,7 +1479,7 @@ int ls_solve(sim_ls_s *ls, double tol, int *its_out, double *relres, bool x0) {
   if (use_loop && !ls->loop_exec) use_loop = false;
   ls->last_mode = use_loop ? 2 : use_graph ? 1 : 0;
   for (;;) {
-    if (df) k_start_df<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->r.p, beta, V32, G, m);
+    if (df) k_start_df<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->r.p, beta, V32, G, m, use_graph ? ls->vcur32.p : nullptr);
     else k_start<<<grid_for(nu, 256), 256, 0, s>>>(nu, ls->r.p, beta, ls->V.p, G, m);
     RS_LAUNCHED(1);
     int jend = 0;
