@@ -1053,8 +1053,10 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
                                                       L.R.v.p);
     {                                                  // rows of R: lanes per row by their mean length
       double avg = nc ? (double)L.P.nnz / nc : 0.0;
-      if (avg <= 6.0) k_sort_rows_g<8><<<grid_for((size_t)nc * 8, 128), 128, 0, s>>>(nc, L.R.rp.p, L.R.ci.p, L.R.v.p);
-      else if (avg <= 12.0)
+      // (a row longer than its group falls to one lane's insertion sort:
+      // groups of 16 only where rows average at most 8 entries)
+      if (avg <= 4.0) k_sort_rows_g<8><<<grid_for((size_t)nc * 8, 128), 128, 0, s>>>(nc, L.R.rp.p, L.R.ci.p, L.R.v.p);
+      else if (avg <= 8.0)
         k_sort_rows_g<16><<<grid_for((size_t)nc * 16, 128), 128, 0, s>>>(nc, L.R.rp.p, L.R.ci.p, L.R.v.p);
       else k_sort_rows_warp<<<grid_for((size_t)nc * 32, 128), 128, 0, s>>>(nc, L.R.rp.p, L.R.ci.p, L.R.v.p);
     }
