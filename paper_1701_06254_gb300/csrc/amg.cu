@@ -974,7 +974,6 @@ static int build_p(amg_level &L, amg_hier &h, const rs_opts &o, int n, size_t ac
 void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
   h.drop_graphs();                                  // buffers below may move
   h.flag.ensure(AF_WORDS);
-  if (!h.vcerr.p) { h.vcerr.ensure(1); RS_CUDA(cudaMemsetAsync(h.vcerr.p, 0, sizeof(int), s)); }
   if (!h.hflag) RS_CUDA(cudaMallocHost((void **)&h.hflag, AF_WORDS * sizeof(int)));
   int *F = h.flag.p;
   bool mixed = o.precision != SIM_PREC_FP64;
@@ -1258,196 +1257,6 @@ template <> struct lvl_ptrs<float> {
   static float *r(amg_level &L) { return L.r32.p; } static float *t(amg_level &L) { return L.t32.p; }
 };
 
-
-// ------------------------------------------------------ coarse-level tail --
-// The V-cycle below level l (the restriction from l, every coarser level's
-// sweeps, the dense coarsest solve, the prolongation back to l) in one CTA
-// when those levels are small: their operators, transfers, D^-1, the dense
-// inverse and the level-l vectors r and x are first copied into shared
-// memory, then the sweeps run one after another from there, separated by
-// block barriers, and only level l's t = x + P e goes back to global memory.
-// The coarse levels' sweeps as separate launches are a few microseconds of
-// launch and load latency each for little work.  Same formulas as the
-// separate kernels, one thread per row (sums in the row's stored order).
-#define VCT_MAXL 4
-template <class T> struct vct_mat { int rows, nnz; const int *rp, *ci; const T *v; int o_rp, o_ci, o_v; };
-template <class T> struct vct_args {
-  int nl;                              // tail levels with sweeps; the dense coarsest follows them
-  int n_in;                            // rows of level l
-  const T *r_in, *x_in;                // level l's r and x (global)
-  T *t_out;                            // level l's t (global)
-  int o_rin, o_xin;
-  vct_mat<T> R0, P0;                   // level l's restriction and prolongation
-  vct_mat<T> A[VCT_MAXL], R[VCT_MAXL], P[VCT_MAXL];
-  const T *dinv[VCT_MAXL];
-  int o_dinv[VCT_MAXL];
-  int n[VCT_MAXL + 1];                 // rows of the tail levels (the last: the coarsest)
-  int o_f[VCT_MAXL + 1], o_x[VCT_MAXL + 1], o_r[VCT_MAXL], o_t[VCT_MAXL];
-  const double *invT;                  // the coarsest inverse, stored transposed
-  int o_inv, nd;
-  unsigned bulk_bytes;                 // the 16-byte parts of every staged array
-  int *err;                            // a bulk-copy wait that gave up (bounded wait)
-};
-
-// copy `bytes` (a multiple of 4; src 16-byte aligned) from global to shared
-// memory: the 16-byte part by one bulk copy (thread 0 issues it, completing
-// on bar), the rest of the words by threads 0-2; returns the bulk bytes
-__device__ __forceinline__ unsigned vct_copy(unsigned char *sm, int off, const void *src, int bytes, uint64_t *bar) {
-  unsigned b16 = (unsigned)bytes & ~15u;
-  if (threadIdx.x == 0 && b16) bulk_g2s(sm + off, src, b16, bar);
-  int w = (int)threadIdx.x, nw = (bytes - (int)b16) / 4;
-  if (w < nw) reinterpret_cast<int *>(sm + off + b16)[w] = reinterpret_cast<const int *>(src)[b16 / 4 + w];
-  return b16;
-}
-template <class T> __device__ __forceinline__ unsigned vct_stage(unsigned char *sm, const vct_mat<T> &m,
-                                                                 uint64_t *bar) {
-  return vct_copy(sm, m.o_rp, m.rp, (m.rows + 1) * 4, bar) + vct_copy(sm, m.o_ci, m.ci, m.nnz * 4, bar) +
-         vct_copy(sm, m.o_v, m.v, m.nnz * (int)sizeof(T), bar);
-}
-// row i of a staged matrix times a shared-memory vector u
-template <class T> __device__ __forceinline__ T vct_row(const unsigned char *sm, const vct_mat<T> &m, int i,
-                                                        const T *u) {
-  const int *rp = reinterpret_cast<const int *>(sm + m.o_rp), *ci = reinterpret_cast<const int *>(sm + m.o_ci);
-  const T *v = reinterpret_cast<const T *>(sm + m.o_v);
-  T s = 0;
-  for (int q = rp[i]; q < rp[i + 1]; q++) s += v[q] * u[ci[q]];
-  return s;
-}
-
-template <class T>
-__global__ void __launch_bounds__(1024, 1) k_vc_tail(const __grid_constant__ vct_args<T> a) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  __shared__ uint64_t bar;
-  pdl_trigger();
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) { mbar_init(&bar, 1); mbar_fence_init(); }
-  __syncthreads();
-  pdl_wait();
-  // every array by bulk copies in flight together on one mbarrier (the
-  // expected byte count is armed first: it is the same sum of sizes)
-  if (tid == 0) mbar_arrive_expect_tx(&bar, a.bulk_bytes);
-  __syncwarp();
-  vct_copy(sm, a.o_rin, a.r_in, a.n_in * (int)sizeof(T), &bar);
-  vct_copy(sm, a.o_xin, a.x_in, a.n_in * (int)sizeof(T), &bar);
-  vct_stage(sm, a.R0, &bar);
-  vct_stage(sm, a.P0, &bar);
-  for (int k = 0; k < a.nl; k++) {
-    vct_stage(sm, a.A[k], &bar); vct_stage(sm, a.R[k], &bar); vct_stage(sm, a.P[k], &bar);
-    vct_copy(sm, a.o_dinv[k], a.dinv[k], a.n[k] * (int)sizeof(T), &bar);
-  }
-  vct_copy(sm, a.o_inv, a.invT, a.nd * a.nd * 8, &bar);
-  mbar_wait_bounded(&bar, 0, a.err, 1);
-  __syncthreads();
-#define VEC(o) reinterpret_cast<T *>(sm + (o))
-  // restriction from level l: f_0 = R r, x_0 = D_0^-1 f_0 (not before the dense level)
-  {
-    const T *r = VEC(a.o_rin);
-    T *f = VEC(a.o_f[0]), *x = VEC(a.o_x[0]);
-    const T *di = a.nl > 0 ? VEC(a.o_dinv[0]) : nullptr;
-    for (int i = tid; i < a.n[0]; i += nt) {
-      T s = vct_row(sm, a.R0, i, r);
-      f[i] = s;
-      if (di) x[i] = s * di[i];
-    }
-  }
-  __syncthreads();
-  for (int k = 0; k < a.nl; k++) {                 // down: pre-smoothing (x = D^-1 f already), restriction
-    T *f = VEC(a.o_f[k]), *x = VEC(a.o_x[k]), *r = VEC(a.o_r[k]);
-    for (int i = tid; i < a.n[k]; i += nt) r[i] = f[i] - vct_row(sm, a.A[k], i, x);
-    __syncthreads();
-    T *fc = VEC(a.o_f[k + 1]), *xc = VEC(a.o_x[k + 1]);
-    const T *dic = k + 1 < a.nl ? VEC(a.o_dinv[k + 1]) : nullptr;
-    for (int i = tid; i < a.n[k + 1]; i += nt) {
-      T s = vct_row(sm, a.R[k], i, r);
-      fc[i] = s;
-      if (dic) xc[i] = s * dic[i];
-    }
-    __syncthreads();
-  }
-  {                                                // the dense coarsest: x = A^{-1} f
-    const double *inv = reinterpret_cast<const double *>(sm + a.o_inv);
-    const T *f = VEC(a.o_f[a.nl]);
-    T *x = VEC(a.o_x[a.nl]);
-    for (int i = tid; i < a.nd; i += nt) {
-      double s = 0.0;
-      for (int c = 0; c < a.nd; c++) s += inv[(size_t)c * a.nd + i] * (double)f[c];
-      x[i] = (T)s;
-    }
-  }
-  __syncthreads();
-  for (int k = a.nl - 1; k >= 0; k--) {            // up: prolongation, post-smoothing
-    T *f = VEC(a.o_f[k]), *x = VEC(a.o_x[k]), *t = VEC(a.o_t[k]);
-    const T *xc = VEC(a.o_x[k + 1]), *di = VEC(a.o_dinv[k]);
-    for (int i = tid; i < a.n[k]; i += nt) t[i] = x[i] + vct_row(sm, a.P[k], i, xc);
-    __syncthreads();
-    for (int i = tid; i < a.n[k]; i += nt) x[i] = t[i] + di[i] * (f[i] - vct_row(sm, a.A[k], i, t));
-    __syncthreads();
-  }
-  // prolongation back to level l: t = x + P x_0
-  {
-    const T *xin = VEC(a.o_xin), *x0 = VEC(a.o_x[0]);
-    for (int i = tid; i < a.n_in; i += nt) a.t_out[i] = xin[i] + vct_row(sm, a.P0, i, x0);
-  }
-#undef VEC
-}
-
-// the tail below level l (its restriction and prolongation included); false
-// when the levels below l do not fit it (then the caller takes the separate
-// kernels)
-template <class T>
-static bool vc_tail_launch(amg_hier &h, int l, cudaStream_t s) {
-  typedef lvl_ptrs<T> LP;
-  int nl = h.nlev - l - 2;
-  if (!h.coarse_dense || nl < 0 || nl > VCT_MAXL) return false;
-  vct_args<T> a = {};
-  size_t off = 0;
-  auto take = [&](size_t bytes) { int o = (int)off; off += (bytes + 15) & ~(size_t)15; return o; };
-  auto mat = [&](vct_mat<T> &m, const csr_dev<T> &c) {
-    m.rows = c.n; m.nnz = c.nnz; m.rp = c.rp.p; m.ci = c.ci.p; m.v = c.v.p;
-    m.o_rp = take((size_t)(c.n + 1) * 4); m.o_ci = take((size_t)c.nnz * 4); m.o_v = take((size_t)c.nnz * sizeof(T));
-  };
-  amg_level &L = h.lev[l];
-  a.nl = nl;
-  a.n_in = LP::A(L).n;
-  a.r_in = LP::r(L); a.x_in = LP::x(L); a.t_out = LP::t(L);
-  a.o_rin = take((size_t)a.n_in * sizeof(T)); a.o_xin = take((size_t)a.n_in * sizeof(T));
-  mat(a.R0, LP::R(L));
-  mat(a.P0, LP::P(L));
-  for (int k = 0; k < nl; k++) {
-    amg_level &M = h.lev[l + 1 + k];
-    mat(a.A[k], LP::A(M)); mat(a.R[k], LP::R(M)); mat(a.P[k], LP::P(M));
-    a.dinv[k] = LP::dinv(M);
-    a.o_dinv[k] = take((size_t)LP::A(M).n * sizeof(T));
-  }
-  for (int k = 0; k <= nl; k++) {
-    a.n[k] = LP::A(h.lev[l + 1 + k]).n;
-    a.o_f[k] = take((size_t)a.n[k] * sizeof(T)); a.o_x[k] = take((size_t)a.n[k] * sizeof(T));
-    if (k < nl) { a.o_r[k] = take((size_t)a.n[k] * sizeof(T)); a.o_t[k] = take((size_t)a.n[k] * sizeof(T)); }
-  }
-  a.nd = a.n[nl];
-  a.invT = h.lu.p;
-  a.o_inv = take((size_t)a.nd * a.nd * 8);
-  if (off > 200 * 1024) return false;
-  // the bulk parts, summed as the kernel issues them
-  auto b16 = [](size_t bytes) { return (unsigned)(bytes & ~(size_t)15); };
-  auto bm = [&](const vct_mat<T> &m) {
-    return b16((size_t)(m.rows + 1) * 4) + b16((size_t)m.nnz * 4) + b16((size_t)m.nnz * sizeof(T));
-  };
-  unsigned bb = 2 * b16((size_t)a.n_in * sizeof(T)) + bm(a.R0) + bm(a.P0) + b16((size_t)a.nd * a.nd * 8);
-  for (int k = 0; k < nl; k++) bb += bm(a.A[k]) + bm(a.R[k]) + bm(a.P[k]) + b16((size_t)a.n[k] * sizeof(T));
-  a.bulk_bytes = bb;
-  a.err = h.vcerr.p;                           // allocated by the setup (no allocation inside a capture)
-  static bool attr = false;
-  if (!attr) {
-    RS_CUDA(cudaFuncSetAttribute(k_vc_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    RS_CUDA(cudaFuncSetAttribute(k_vc_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
-  }
-  launch_pdl(k_vc_tail<T>, 1, 1024, off, s, a);
-  RS_LAUNCHED(1);
-  return true;
-}
-
 template <class T>
 int amg_vcycle(amg_hier &h, int l, cudaStream_t s) {
   typedef lvl_ptrs<T> LP;
@@ -1479,20 +1288,13 @@ int amg_vcycle(amg_hier &h, int l, cudaStream_t s) {
   // then gathers one vector instead of two; same products, same values)
   vc_sweep<T, 0>(la, n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), l > 0 ? LP::x(L) : nullptr, LP::x(L),
                  LP::r(L), s);
-  int k;
-  if (h.tail_rows > 0 && LP::A(Cl).n <= h.tail_rows && vc_tail_launch<T>(h, l, s)) {
-    k = 1;                                       // restriction, coarser levels, prolongation: one CTA
-  } else {
-    // the coarse level's D^-1 f, unless that level is solved directly
-    bool cx = !(l + 1 == h.nlev - 1 && h.coarse_dense);
-    vc_sweep<T, 1>(lr, R.n, R.rp.p, R.ci.p, R.v.p, LP::dinv(Cl), nullptr, LP::r(L), LP::f(Cl), cx ? LP::x(Cl) : nullptr,
-                   s);
-    k = amg_vcycle<T>(h, l + 1, s);
-    vc_sweep<T, 2>(lp, n, P.rp.p, P.ci.p, P.v.p, nullptr, LP::x(L), LP::x(Cl), LP::t(L), nullptr, s);
-    k += 2;
-  }
+  // the coarse level's D^-1 f, unless that level is solved directly
+  bool cx = !(l + 1 == h.nlev - 1 && h.coarse_dense);
+  vc_sweep<T, 1>(lr, R.n, R.rp.p, R.ci.p, R.v.p, LP::dinv(Cl), nullptr, LP::r(L), LP::f(Cl), cx ? LP::x(Cl) : nullptr, s);
+  int k = amg_vcycle<T>(h, l + 1, s);
+  vc_sweep<T, 2>(lp, n, P.rp.p, P.ci.p, P.v.p, nullptr, LP::x(L), LP::x(Cl), LP::t(L), nullptr, s);
   vc_sweep<T, 3>(la, n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), LP::t(L), LP::x(L), nullptr, s);
-  return k + 2;
+  return k + 4;
 }
 template int amg_vcycle<double>(amg_hier &, int, cudaStream_t);
 template int amg_vcycle<float>(amg_hier &, int, cudaStream_t);

@@ -87,43 +87,6 @@ inline void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, si
   RS_CUDA(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
 }
 
-// ------------------------------------------------ bulk copies (TMA) ------
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait: gives up after `limit` polls, records `code` in *err and
-// returns false (the hardware copies themselves cannot stall forever; the
-// bound only turns a fault into an error status instead of a hang)
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, int *err, int code) {
-  for (int it = 0; it < (1 << 22); it++)
-    if (mbar_try_wait(bar, parity)) return true;
-  atomicExch(err, code);
-  return false;
-}
-
 // ------------------------------------------------------- device helpers --
 // Arithmetic used where a floating-point value decides an integer (the
 // decoupled matrix, the reordering key, AMG strength / PMIS / P / RAP):
@@ -197,8 +160,6 @@ struct amg_hier {
   int nlev = 0;
   amg_level lev[32];
   int coarse_dense = 1;
-  int tail_rows = 512;          // V-cycle levels of at most this many rows run in one CTA from shared memory (0: none)
-  dbuf<int> vcerr;              // error word of that kernel's bounded bulk-copy wait
   dbuf<double> lu;              // dense LU of the coarsest level
   dbuf<int> piv;
   dbuf<int> flag;               // device counters / error words
