@@ -111,13 +111,14 @@ __global__ void k_pmis_init(int n, const int *rp, const int *ci, const uint8_t *
 // Weights are >= +0, so their bit patterns order them.  newc of a point that
 // left the lists keeps its last value: 1 only for C points, which the update
 // test also finds through cf.
+// the two steps of one round over list entries g0, g0 + stride, ... (L
+// lanes per point; every lane of a warp runs the loop to its common end)
 template <int L>
-__global__ void k_pmis_select_w(const int *rp, const int *ci, const uint8_t *S, const int *tpos, const double *w,
-                                const int8_t *cf, int8_t *newc, const int *list, const int *cnt) {
-  int m = *cnt;
-  if (m == 0) return;
-  int groups = gridDim.x * blockDim.x / L, k = threadIdx.x % L;
-  for (int g0 = (blockIdx.x * blockDim.x + threadIdx.x) / L;; g0 += groups) {
+__device__ __forceinline__ void pmis_select_pts(const int *rp, const int *ci, const uint8_t *S, const int *tpos,
+                                                const double *w, const int8_t *cf, int8_t *newc, const int *list,
+                                                int m, int g_first, int stride) {
+  const int k = threadIdx.x % L;
+  for (int g0 = g_first;; g0 += stride) {
     if (__all_sync(0xffffffffu, g0 >= m)) break;
     int g = g0 < m ? g0 : m - 1, i = list[g];
     bool beaten = false;
@@ -135,14 +136,12 @@ __global__ void k_pmis_select_w(const int *rp, const int *ci, const uint8_t *S, 
     if (k == 0 && g0 < m) newc[i] = beaten ? 0 : 1;
   }
 }
-
 template <int L>
-__global__ void k_pmis_update_w(const int *rp, const int *ci, const uint8_t *S, int8_t *cf, const int8_t *newc,
-                                const int *list, const int *cnt, int *next, int *cnt_next) {
-  int m = *cnt;
-  if (m == 0) return;
-  int groups = gridDim.x * blockDim.x / L, k = threadIdx.x % L;
-  for (int g0 = (blockIdx.x * blockDim.x + threadIdx.x) / L;; g0 += groups) {
+__device__ __forceinline__ void pmis_update_pts(const int *rp, const int *ci, const uint8_t *S, int8_t *cf,
+                                                const int8_t *newc, const int *list, int m, int g_first, int stride,
+                                                int *next, int *cnt_next) {
+  const int k = threadIdx.x % L;
+  for (int g0 = g_first;; g0 += stride) {
     if (__all_sync(0xffffffffu, g0 >= m)) break;
     int g = g0 < m ? g0 : m - 1, i = list[g];
     bool sel = newc[i] != 0, hit = false;
@@ -160,6 +159,55 @@ __global__ void k_pmis_update_w(const int *rp, const int *ci, const uint8_t *S, 
     else if (lead && hit) cf[i] = -1;
     warp_append(lead && !sel && !hit, i, cnt_next, next);
   }
+}
+
+template <int L>
+__global__ void k_pmis_select_w(const int *rp, const int *ci, const uint8_t *S, const int *tpos, const double *w,
+                                const int8_t *cf, int8_t *newc, const int *list, const int *cnt) {
+  int m = *cnt;
+  if (m == 0) return;
+  pmis_select_pts<L>(rp, ci, S, tpos, w, cf, newc, list, m, (blockIdx.x * blockDim.x + threadIdx.x) / L,
+                     gridDim.x * blockDim.x / L);
+}
+
+template <int L>
+__global__ void k_pmis_update_w(const int *rp, const int *ci, const uint8_t *S, int8_t *cf, const int8_t *newc,
+                                const int *list, const int *cnt, int *next, int *cnt_next) {
+  int m = *cnt;
+  if (m == 0) return;
+  pmis_update_pts<L>(rp, ci, S, cf, newc, list, m, (blockIdx.x * blockDim.x + threadIdx.x) / L,
+                     gridDim.x * blockDim.x / L, next, cnt_next);
+}
+
+// Rounds r0, r0 + 1, ... until a list is empty, in one block: the same two
+// steps per round with block barriers between them, for the short lists of
+// the last rounds (a launch per step costs more than the step there).
+// *z = the first round r whose list cnt[r] is empty (searched from 0), or
+// -1 when rmax rounds were not enough.
+template <int L>
+__global__ void __launch_bounds__(1024) k_pmis_tail(const int *rp, const int *ci, const uint8_t *S, const int *tpos,
+                                                    const double *w, int8_t *cf, int8_t *newc, int *plist, int n,
+                                                    int *cnt, int r0, int rmax, int *z) {
+  const volatile int *vcnt = cnt;
+  __shared__ int zs;
+  if (threadIdx.x == 0) {
+    zs = -1;
+    for (int r = 0; r <= r0; r++) if (vcnt[r] == 0) { zs = r; break; }
+  }
+  __syncthreads();
+  if (zs >= 0) { if (threadIdx.x == 0) *z = zs; return; }
+  const int first = threadIdx.x / L, stride = blockDim.x / L;
+  for (int r = r0; r < rmax; r++) {
+    const int m = vcnt[r];
+    if (m == 0) { if (threadIdx.x == 0) *z = r; return; }
+    const int *lst = plist + (size_t)(r & 1) * n;
+    int *nxt = plist + (size_t)((r + 1) & 1) * n;
+    pmis_select_pts<L>(rp, ci, S, tpos, w, cf, newc, lst, m, first, stride);
+    __syncthreads();
+    pmis_update_pts<L>(rp, ci, S, cf, newc, lst, m, first, stride, nxt, cnt + r + 1);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *z = vcnt[rmax] == 0 ? rmax : -1;
 }
 
 // lanes per row for the PMIS steps: one thread for short rows, then the
@@ -884,12 +932,17 @@ enum {
   AF_PNNZ = 3,       // nnz(P)
   AF_APTOT = 4, AF_APMX = 5, AF_APNNZ = 6,     // products, long-row marker and nnz of A P
   AF_RAPTOT = 7, AF_RAPMX = 8,                 // the same for R (A P)
+  AF_PRND = 9,       // PMIS rounds taken (-1: not finished within the cap)
   AF_SLOTS = 16,
   AF_LNNZ = 16,      // [16 + l]: nnz of level l's operator (l >= 1)
   AF_CNT = 48,       // [48 + r]: undecided points after PMIS round r - 1 (r = 0: after the initialisation)
   AF_ROUNDS_MAX = 1020,
   AF_WORDS = AF_CNT + AF_ROUNDS_MAX + 8
 };
+// PMIS: a list of at most this many points x lanes goes to the one-block
+// tail (two passes of its 1024 threads per step); the counts of the first
+// PMIS_HINT_ROUNDS rounds are read back to choose the next setup's switch
+static const int PMIS_TAIL_PTS = 2048, PMIS_HINT_ROUNDS = 24;
 
 static const int *amg_read(amg_hier &h, int lo, int count, cudaStream_t s) {
   RS_CUDA(cudaMemcpyAsync(h.hflag + lo, h.flag.p + lo, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -920,6 +973,20 @@ static void pmis_rounds(amg_level &L, amg_hier &h, int n, int lanes, int r0, int
 #undef PMIS_ROUND
   }
   RS_LAUNCHED(2 * (r1 - r0));
+  RS_CHECK_LAUNCH();
+}
+
+// the rounds from r0 on in one block of 1024 threads (k_pmis_tail); the
+// number of rounds taken goes to the flag word AF_PRND
+static void pmis_tail(amg_level &L, amg_hier &h, int n, int lanes, int r0, cudaStream_t s) {
+  int *F = h.flag.p;
+#define PMIS_TAIL(LL)                                                                                          \
+  if (lanes == LL)                                                                                             \
+    k_pmis_tail<LL><<<1, 1024, 0, s>>>(L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, h.hashw.p, L.cf.p, h.newc.p,  \
+                                       h.plist.p, n, F + AF_CNT, r0, AF_ROUNDS_MAX, F + AF_PRND);
+  PMIS_TAIL(1) PMIS_TAIL(4) PMIS_TAIL(16)
+#undef PMIS_TAIL
+  RS_LAUNCHED(1);
   RS_CHECK_LAUNCH();
 }
 
@@ -993,7 +1060,6 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
     L.f.ensure(n); L.x.ensure(n); L.r.ensure(n); L.t.ensure(n);
     if (mixed) { L.f32.ensure(n); L.x32.ensure(n); L.r32.ensure(n); L.t32.ensure(n); }
     L.cf.ensure(n); L.strong.ensure(acap); L.tpos.ensure(acap);
-    int rounds_hint = L.rounds;
     L.nc = 0; L.rounds = 0;
     if (n <= o.coarse_max || l == o.max_levels - 1) {      // coarsest: no split (all marks 0)
       RS_CUDA(cudaMemsetAsync(L.cf.p, 0, (size_t)n, s));
@@ -1010,28 +1076,24 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
                                                  h.hashw.p, L.cf.p, h.newc.p, F + AF_CNT, h.plist.p);
     RS_LAUNCHED(3);
     RS_CHECK_LAUNCH();
-    // as many rounds as the previous setup took here, plus two (spare
-    // rounds return at once); more in batches of four when they were not enough
+    // full-grid rounds while the lists are long (the previous setup's
+    // counts say how many), then the rest in one block until a list is empty
     const int lanes = pmis_lanes(nnz_hint, n);
-    int done = std::min(rounds_hint > 0 ? rounds_hint + 2 : 10, (int)AF_ROUNDS_MAX);
-    pmis_rounds(L, h, n, lanes, 0, done, s);
+    const int k = L.tail_r >= 0 ? L.tail_r : ((long long)n * lanes <= PMIS_TAIL_PTS ? 0 : 3);
+    pmis_rounds(L, h, n, lanes, 0, k, s);
+    pmis_tail(L, h, n, lanes, k, s);
     static thread_local dbuf<int> cidx;      // C flags, then coarse index of each C point
     cidx.ensure(n + 1);
-    const int *hf = nullptr;
-    for (;;) {
-      int pnnz = build_p(L, h, o, n, acap, cidx, s);
-      hf = amg_read(h, 0, AF_CNT + done + 1, s);        // wait 1
-      if (hf[AF_SYM]) RS_FAIL(SIM_ERR_ARG, "AMG: level %d pattern is not structurally symmetric", l);
-      if (hf[AF_PCAP]) RS_FAIL(SIM_ERR_ARG, "AMG: level %d interpolation beyond its capacity", l);
-      if (pnnz >= 0) L.P.nnz = pnnz; else L.P.nnz = hf[AF_PNNZ];
-      int z = -1;
-      for (int r = 0; r <= done; r++) if (hf[AF_CNT + r] == 0) { z = r; break; }
-      if (z >= 0) { L.rounds = z; break; }
-      if (done + 4 > AF_ROUNDS_MAX) RS_FAIL(SIM_ERR_TIMEOUT, "AMG: PMIS did not finish in %d rounds", done);
-      pmis_rounds(L, h, n, lanes, done, done + 4, s);
-      done += 4;
-      rs_fill_i(F, 0, AF_SLOTS, s);                       // P and A P again from the finished split
-    }
+    int pnnz = build_p(L, h, o, n, acap, cidx, s);
+    const int *hf = amg_read(h, 0, AF_CNT + PMIS_HINT_ROUNDS, s);   // wait 1
+    if (hf[AF_SYM]) RS_FAIL(SIM_ERR_ARG, "AMG: level %d pattern is not structurally symmetric", l);
+    if (hf[AF_PCAP]) RS_FAIL(SIM_ERR_ARG, "AMG: level %d interpolation beyond its capacity", l);
+    if (hf[AF_PRND] < 0) RS_FAIL(SIM_ERR_TIMEOUT, "AMG: PMIS did not finish in %d rounds", (int)AF_ROUNDS_MAX);
+    L.P.nnz = pnnz >= 0 ? pnnz : hf[AF_PNNZ];
+    L.rounds = hf[AF_PRND];
+    L.tail_r = std::min(L.rounds, PMIS_HINT_ROUNDS - 1);
+    for (int r = 0; r < L.tail_r; r++)
+      if ((long long)hf[AF_CNT + r] * lanes <= PMIS_TAIL_PTS) { L.tail_r = r; break; }
     if (l > 0) L.A.nnz = hf[AF_LNNZ + l];
     int nc = hf[AF_NC], ap_tot = hf[AF_APTOT], ap_mx = hf[AF_APMX];
     L.nc = nc;

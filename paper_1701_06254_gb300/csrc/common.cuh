@@ -151,6 +151,7 @@ struct amg_level {
   dbuf<uint8_t> strong;
   dbuf<int> tpos;               // position of (j,i) in row j for each (i,j)
   int nc = 0, rounds = 0;
+  int tail_r = -1;               // PMIS rounds on the full grid before the one-block tail (-1: not known yet)
   int nnz_prev = 0;             // nnz(A) of this level at the previous setup (a launch-shape hint)
   dbuf<double> f, x, r, t;      // cycle work vectors (FP64)
   dbuf<float> f32, x32, r32, t32;
