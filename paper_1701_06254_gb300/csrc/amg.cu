@@ -7,8 +7,9 @@
 //                 or extended+i (distance two, option interp),
 //              R = P^T, Galerkin A_c = R (A P)
 //   cycle      V(1,1), l1-Jacobi smoothing, zero initial guess
-//   coarsest   dense inverse (FP64): Gauss-Jordan with partial pivoting in
-//              shared memory (n <= 128), else an LU with partial pivoting
+//   coarsest   dense inverse (FP64): LU with partial pivoting in shared
+//              memory, then the columns of the inverse in parallel (n <=
+//              128), else an LU with partial pivoting in one block
 // Setup runs in FP64 with explicit round-to-nearest operations in a fixed
 // order, so the C/F split, P and every coarse operator are bit-identical to
 // a plain sequential evaluation of the same formulas on the same input.
@@ -853,61 +854,106 @@ __global__ void k_dense_lu_inv(int n, double *a, int *piv, double *inv) {
   }
 }
 
-// The inverse of the coarsest operator (n <= 128) by Gauss-Jordan
-// elimination with partial (row) pivoting, in place in shared memory (at
-// most 128 KB).  Step k: warp 0 finds the pivot row (largest |a_ik|, the
-// lowest index on ties), swaps it with row k, saves column k and scales row
-// k by 1/a_kk (a_kk itself becomes 1/a_kk); then every thread eliminates
-// column k from its elements of the other rows (a_ik itself becomes
-// -a_ik/a_kk).  Two block barriers per step.  At the end the row swaps are
-// undone on the columns, in reverse order, while the result is written.
-// Stored transposed: inv[c][i] = (A^{-1})_{ic}.  Equal to the LU solve of
-// the same system up to rounding.
-__global__ void __launch_bounds__(512) k_dense_gj_inv_smem(int n, const double *ag, int *piv, double *inv) {
+// The inverse of the coarsest operator (n <= 128) in two kernels.  FP64
+// is the slow pipe here (a warp's FP64 instruction holds its SM
+// sub-partition for tens of cycles), so both keep FP64 work off the serial
+// chain: one reciprocal per pivot, stored for the second kernel.
+// k_dense_lu_smem: LU with partial pivoting in shared memory (at most 128
+// KB), one block.  Step k: warp 0 finds the pivot row (largest |a_ik|, i >=
+// k, the lowest index on ties; |a_ik| compared on its bit pattern, which
+// orders non-negative doubles), swaps the whole rows, forms r_k = 1/a_kk and
+// the multipliers l_ik = a_ik r_k (i > k); then every warp takes rows i > k
+// and every lane columns j > k: a_ij -= l_ik a_kj.  Two block barriers per
+// step; n^3/3 multiply-adds in all.
+__global__ void __launch_bounds__(512) k_dense_lu_smem(int n, const double *ag, int *piv, double *lu, double *rdiag) {
   extern __shared__ double sa[];
-  __shared__ double fcol[128];
-  __shared__ int sperm[128], scol[128];
-  int t = threadIdx.x, nt = blockDim.x, lane = t & 31;
-  for (int e = t; e < n * n; e += nt) sa[e] = ag[e];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+  for (int e = t; e < n * n; e += blockDim.x) sa[e] = ag[e];
   __syncthreads();
   for (int k = 0; k < n; k++) {
-    if (t < 32) {
-      double best = -1.0; int bi = n;
-      for (int i = k + lane; i < n; i += 32) { double x = fabs(sa[i * n + k]); if (x > best) { best = x; bi = i; } }
+    if (w == 0) {
+      long long best = -1; int bi = n;
+      for (int i = k + lane; i < n; i += 32) {
+        long long x = __double_as_longlong(sa[i * n + k]) & 0x7fffffffffffffffLL;
+        if (x > best) { best = x; bi = i; }
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        double x = __shfl_xor_sync(0xffffffffu, best, o); int xi = __shfl_xor_sync(0xffffffffu, bi, o);
+        long long x = __shfl_xor_sync(0xffffffffu, best, o); int xi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (x > best || (x == best && xi < bi)) { best = x; bi = xi; }
       }
-      int p = bi < n ? bi : k;
+      const int p = bi < n ? bi : k;
       if (p != k)
         for (int j = lane; j < n; j += 32) { double x = sa[k * n + j]; sa[k * n + j] = sa[p * n + j]; sa[p * n + j] = x; }
       __syncwarp();
-      double d = sa[k * n + k];
-      for (int i = lane; i < n; i += 32) fcol[i] = sa[i * n + k];
-      __syncwarp();
-      double r = 1.0 / d;
-      for (int j = lane; j < n; j += 32) sa[k * n + j] = j == k ? r : sa[k * n + j] * r;
-      if (lane == 0) { sperm[k] = p; piv[k] = p; }
+      const double r = 1.0 / sa[k * n + k];
+      for (int i = k + 1 + lane; i < n; i += 32) sa[i * n + k] *= r;
+      if (lane == 0) { piv[k] = p; rdiag[k] = r; }
     }
     __syncthreads();
-    for (int e = t; e < n * n; e += nt) {
-      int i = e / n, j = e - i * n;
-      if (i == k) continue;
-      double f = fcol[i];
-      sa[e] = j == k ? -f * sa[k * n + k] : sa[e] - f * sa[k * n + j];
+    for (int i = k + 1 + w; i < n; i += nw) {
+      const double l = sa[i * n + k];
+      for (int j = k + 1 + lane; j < n; j += 32) sa[i * n + j] = fma(-l, sa[k * n + j], sa[i * n + j]);
     }
     __syncthreads();
   }
-  // undo the row swaps on the columns: the final column c comes from scol[c]
-  if (t == 0) {
-    for (int c = 0; c < n; c++) scol[c] = c;
-    for (int k = n - 1; k >= 0; k--) { int p = sperm[k]; int x = scol[k]; scol[k] = scol[p]; scol[p] = x; }
-  }
+  for (int e = t; e < n * n; e += blockDim.x) lu[e] = sa[e];
+}
+
+// k_dense_inv_cols: column c of A^{-1} = U^{-1} L^{-1} P e_c, one warp per
+// column (two per block), the factors staged in shared memory.  Lane r
+// keeps rows r, r + 32, ... (NR of them) in registers; the forward sweep
+// starts at the row where the swaps put the unit entry (L has a unit
+// diagonal), and both sweeps go column by column (x_j broadcast from its
+// lane, then every row below or above subtracts its term; register rows
+// with no such row are skipped by the whole warp).  Stored transposed:
+// inv[c][i] = (A^{-1})_{ic}.  Equal to the row-by-row LU solve up to
+// rounding.
+template <int NR>
+__global__ void __launch_bounds__(64) k_dense_inv_cols(int n, const double *lu, const int *piv, const double *rdiag,
+                                                      double *inv) {
+  extern __shared__ double sl[];
+  double *sr = sl + (size_t)n * n;
+  int *sp = reinterpret_cast<int *>(sr + n);
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) sl[e] = lu[e];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) { sp[k] = piv[k]; sr[k] = rdiag[k]; }
   __syncthreads();
-  for (int e = t; e < n * n; e += nt) {
-    int c = e / n, i = e - c * n;
-    inv[e] = sa[i * n + scol[c]];
+  const int lane = threadIdx.x & 31, c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (c >= n) return;
+  int pos = c;                                      // the unit entry of P e_c after the swaps in order
+  for (int k = 0; k < n; k++) { int p = sp[k]; pos = pos == k ? p : (pos == p ? k : pos); }
+  double b[NR];
+#pragma unroll
+  for (int u = 0; u < NR; u++) b[u] = (lane + 32 * u) == pos ? 1.0 : 0.0;
+  auto pick = [&](int j) {                           // b of row j, from its lane (no indexed registers)
+    double v = b[0];
+#pragma unroll
+    for (int u = 1; u < NR; u++) if ((j >> 5) == u) v = b[u];
+    return __shfl_sync(0xffffffffu, v, j & 31);
+  };
+  for (int j = pos; j < n - 1; j++) {               // L y = P e_c (rows before pos stay 0)
+    const double yj = pick(j);
+#pragma unroll
+    for (int u = 0; u < NR; u++) {
+      if (32 * u + 31 <= j) continue;               // no row of this register below j
+      const int i = lane + 32 * u;
+      if (i > j && i < n) b[u] = fma(-sl[i * n + j], yj, b[u]);
+    }
+  }
+  for (int j = n - 1; j >= 0; j--) {                // U x = y
+    const double xj = pick(j) * sr[j];
+#pragma unroll
+    for (int u = 0; u < NR; u++) {
+      if (32 * u > j) continue;                     // no row of this register at or above j
+      const int i = lane + 32 * u;
+      if (i == j) b[u] = xj;
+      else if (i < j) b[u] = fma(-sl[i * n + j], xj, b[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < NR; u++) {
+    const int i = lane + 32 * u;
+    if (i < n) inv[(size_t)c * n + i] = b[u];
   }
 }
 
@@ -1151,10 +1197,25 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
     if (n <= 128) {
       static bool attr = false;
       if (!attr) {
-        RS_CUDA(cudaFuncSetAttribute(k_dense_gj_inv_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        RS_CUDA(cudaFuncSetAttribute(k_dense_lu_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        RS_CUDA(cudaFuncSetAttribute(k_dense_inv_cols<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        RS_CUDA(cudaFuncSetAttribute(k_dense_inv_cols<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        RS_CUDA(cudaFuncSetAttribute(k_dense_inv_cols<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        RS_CUDA(cudaFuncSetAttribute(k_dense_inv_cols<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr = true;
       }
-      k_dense_gj_inv_smem<<<1, 512, (size_t)n * n * 8, s>>>(n, a.p, h.piv.p, h.lu.p);
+      h.dense_lu.ensure((size_t)n * n);
+      h.dense_rd.ensure(n);
+      k_dense_lu_smem<<<1, 512, (size_t)n * n * 8, s>>>(n, a.p, h.piv.p, h.dense_lu.p, h.dense_rd.p);
+      const size_t csm = (size_t)n * n * 8 + (size_t)n * 12;
+      const unsigned cg = (unsigned)((n + 1) / 2);
+      switch ((n + 31) / 32) {
+        case 1: k_dense_inv_cols<1><<<cg, 64, csm, s>>>(n, h.dense_lu.p, h.piv.p, h.dense_rd.p, h.lu.p); break;
+        case 2: k_dense_inv_cols<2><<<cg, 64, csm, s>>>(n, h.dense_lu.p, h.piv.p, h.dense_rd.p, h.lu.p); break;
+        case 3: k_dense_inv_cols<3><<<cg, 64, csm, s>>>(n, h.dense_lu.p, h.piv.p, h.dense_rd.p, h.lu.p); break;
+        default: k_dense_inv_cols<4><<<cg, 64, csm, s>>>(n, h.dense_lu.p, h.piv.p, h.dense_rd.p, h.lu.p); break;
+      }
+      RS_LAUNCHED(1);
     } else {
       k_dense_lu_inv<<<1, 512, 0, s>>>(n, a.p, h.piv.p, h.lu.p);
     }

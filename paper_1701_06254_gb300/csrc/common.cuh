@@ -166,6 +166,8 @@ struct amg_hier {
   dbuf<int> flag;               // device counters / error words
   int *hflag = nullptr;         // pinned host copy of flag, read at the setup's few waits
   dbuf<double> dense_a;         // the coarsest operator as a dense matrix (setup scratch)
+  dbuf<double> dense_lu;        // its LU factors (setup scratch)
+  dbuf<double> dense_rd;        // and the reciprocals of U's diagonal
   dbuf<double> hashw;           // PMIS weights
   dbuf<int8_t> newc;
   dbuf<int> plist;              // PMIS undecided-point lists (two of n)
