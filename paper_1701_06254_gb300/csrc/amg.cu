@@ -114,6 +114,7 @@ __global__ void k_pmis_init(int n, const int *rp, const int *ci, const uint8_t *
 // test also finds through cf.
 // the two steps of one round over list entries g0, g0 + stride, ... (L
 // lanes per point; every lane of a warp runs the loop to its common end)
+#define PMIS_B 4
 template <int L>
 __device__ __forceinline__ void pmis_select_pts(const int *rp, const int *ci, const uint8_t *S, const int *tpos,
                                                 const double *w, const int8_t *cf, int8_t *newc, const int *list,
@@ -123,12 +124,26 @@ __device__ __forceinline__ void pmis_select_pts(const int *rp, const int *ci, co
     if (__all_sync(0xffffffffu, g0 >= m)) break;
     int g = g0 < m ? g0 : m - 1, i = list[g];
     bool beaten = false;
-    long long wi = __double_as_longlong(w[i]);
-    for (int q = rp[i] + k; q < rp[i + 1]; q += L) {
-      int j = ci[q];
-      if (j == i || !(S[q] || S[tpos[q]]) || cf[j] != 0) continue;
-      long long wj = __double_as_longlong(w[j]);
-      if (wj > wi || (wj == wi && j < i)) { beaten = true; break; }
+    const long long wi = __double_as_longlong(w[i]);
+    const int q1 = rp[i + 1];
+    // PMIS_B entries of the lane at a time, their loads issued together (two
+    // dependent levels instead of a chain per entry)
+    for (int q0 = rp[i] + k; q0 < q1 && !beaten; q0 += PMIS_B * L) {
+      int jj[PMIS_B], tp[PMIS_B]; bool sq[PMIS_B];
+#pragma unroll
+      for (int u = 0; u < PMIS_B; u++) {
+        const int q = q0 + u * L; const bool in = q < q1;
+        jj[u] = in ? ci[q] : i; sq[u] = in && S[q]; tp[u] = in ? tpos[q] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < PMIS_B; u++) {
+        const int j = jj[u];
+        if (j == i) continue;
+        const bool st = sq[u] || S[tp[u]];
+        const int8_t c = cf[j];
+        const long long wj = __double_as_longlong(w[j]);
+        beaten |= st && c == 0 && (wj > wi || (wj == wi && j < i));
+      }
     }
     if (L > 1) {
       unsigned lanes = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) / L * L));
@@ -146,11 +161,22 @@ __device__ __forceinline__ void pmis_update_pts(const int *rp, const int *ci, co
     if (__all_sync(0xffffffffu, g0 >= m)) break;
     int g = g0 < m ? g0 : m - 1, i = list[g];
     bool sel = newc[i] != 0, hit = false;
-    if (!sel)
-      for (int q = rp[i] + k; q < rp[i + 1]; q += L) {
-        int j = ci[q];
-        if (S[q] && (cf[j] == 1 || newc[j])) { hit = true; break; }
+    if (!sel) {
+      const int q1 = rp[i + 1];
+      for (int q0 = rp[i] + k; q0 < q1 && !hit; q0 += PMIS_B * L) {
+        int jj[PMIS_B]; bool sq[PMIS_B];
+#pragma unroll
+        for (int u = 0; u < PMIS_B; u++) {
+          const int q = q0 + u * L; const bool in = q < q1;
+          jj[u] = in ? ci[q] : i; sq[u] = in && S[q];
+        }
+#pragma unroll
+        for (int u = 0; u < PMIS_B; u++) {
+          const int j = jj[u];
+          hit |= sq[u] && (cf[j] == 1 || newc[j]);
+        }
       }
+    }
     if (L > 1) {
       unsigned lanes = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) / L * L));
       hit = (__ballot_sync(0xffffffffu, hit) & lanes) != 0;
@@ -905,8 +931,8 @@ __global__ void __launch_bounds__(512) k_dense_lu_smem(int n, const double *ag, 
 // keeps rows r, r + 32, ... (NR of them) in registers; the forward sweep
 // starts at the row where the swaps put the unit entry (L has a unit
 // diagonal), and both sweeps go column by column (x_j broadcast from its
-// lane, then every row below or above subtracts its term; register rows
-// with no such row are skipped by the whole warp).  Stored transposed:
+// lane, then every row below or above subtracts its term; registers that
+// hold no such row are not touched).  Stored transposed:
 // inv[c][i] = (A^{-1})_{ic}.  Equal to the row-by-row LU solve up to
 // rounding.
 template <int NR>
@@ -925,29 +951,32 @@ __global__ void __launch_bounds__(64) k_dense_inv_cols(int n, const double *lu, 
   double b[NR];
 #pragma unroll
   for (int u = 0; u < NR; u++) b[u] = (lane + 32 * u) == pos ? 1.0 : 0.0;
-  auto pick = [&](int j) {                           // b of row j, from its lane (no indexed registers)
-    double v = b[0];
+  // column j = 32 jb + jj: its b sits in register jb of lane jj (jb a
+  // compile-time index, so b stays in registers)
 #pragma unroll
-    for (int u = 1; u < NR; u++) if ((j >> 5) == u) v = b[u];
-    return __shfl_sync(0xffffffffu, v, j & 31);
-  };
-  for (int j = pos; j < n - 1; j++) {               // L y = P e_c (rows before pos stay 0)
-    const double yj = pick(j);
+  for (int jb = 0; jb < NR; jb++) {                  // L y = P e_c (rows before pos stay 0)
+    for (int jj = pos > 32 * jb ? pos - 32 * jb : 0; jj < 32 && 32 * jb + jj < n - 1; jj++) {
+      const int j = 32 * jb + jj;
+      const double yj = __shfl_sync(0xffffffffu, b[jb], jj);
 #pragma unroll
-    for (int u = 0; u < NR; u++) {
-      if (32 * u + 31 <= j) continue;               // no row of this register below j
-      const int i = lane + 32 * u;
-      if (i > j && i < n) b[u] = fma(-sl[i * n + j], yj, b[u]);
+      for (int u = jb; u < NR; u++) {               // rows below j live in registers jb and up
+        const int i = lane + 32 * u;
+        if (i > j && i < n) b[u] = fma(-sl[i * n + j], yj, b[u]);
+      }
     }
   }
-  for (int j = n - 1; j >= 0; j--) {                // U x = y
-    const double xj = pick(j) * sr[j];
 #pragma unroll
-    for (int u = 0; u < NR; u++) {
-      if (32 * u > j) continue;                     // no row of this register at or above j
-      const int i = lane + 32 * u;
-      if (i == j) b[u] = xj;
-      else if (i < j) b[u] = fma(-sl[i * n + j], xj, b[u]);
+  for (int jb = NR - 1; jb >= 0; jb--) {             // U x = y
+    for (int jj = 31; jj >= 0; jj--) {
+      const int j = 32 * jb + jj;
+      if (j >= n) continue;
+      const double xj = __shfl_sync(0xffffffffu, b[jb], jj) * sr[j];
+#pragma unroll
+      for (int u = 0; u <= jb; u++) {               // rows at or above j live in registers up to jb
+        const int i = lane + 32 * u;
+        if (i == j) b[u] = xj;
+        else if (i < j) b[u] = fma(-sl[i * n + j], xj, b[u]);
+      }
     }
   }
 #pragma unroll
