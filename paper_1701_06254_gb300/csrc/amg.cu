@@ -50,19 +50,31 @@ __global__ void k_tpos_warp(int n, const int *rp, const int *ci, int *tpos, int 
   }
 }
 
-__global__ void k_strength(int n, const int *rp, const int *ci, const double *v, double theta, uint8_t *S) {
+// Strength of connection (S), and with dinv given the l1-Jacobi diagonal of
+// the same row (d_i = a_ii + sum_{j != i} |a_ij|; 1 / d_i, FP64 and FP32),
+// from one pass over the row.
+__global__ void k_strength(int n, const int *rp, const int *ci, const double *v, double theta, uint8_t *S,
+                           double *dinv, float *dinv32) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   bool have = false; double mx = 0.0; long long mxk = 0;
+  double s = 0.0, aii = 0.0;
   for (int q = rp[i]; q < rp[i + 1]; q++) {
-    if (ci[q] == i) continue;
-    long long tk = -dkey(v[q]);                     // key of t = -a_iq
-    if (!have || tk > mxk) { mx = -v[q]; mxk = tk; have = true; }
+    const double a = v[q];
+    if (ci[q] == i) { aii = a; continue; }
+    s = add_rn(s, fabs(a));
+    long long tk = -dkey(a);                        // key of t = -a_iq
+    if (!have || tk > mxk) { mx = -a; mxk = tk; have = true; }
   }
   long long thrk = dkey(mul_rn(theta, mx));
   bool any = have && mxk > 0;                       // max_k (-a_ik) > 0
   for (int q = rp[i]; q < rp[i + 1]; q++)
     S[q] = (uint8_t)(any && ci[q] != i && -dkey(v[q]) >= thrk);
+  if (dinv) {
+    double d = add_rn(aii, s);
+    dinv[i] = 1.0 / d;
+    if (dinv32) dinv32[i] = (float)(1.0 / d);
+  }
 }
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
@@ -89,7 +101,14 @@ __global__ void k_pmis_init(int n, const int *rp, const int *ci, const uint8_t *
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int cnt = 0;
   if (i < n) {
-    for (int q = rp[i]; q < rp[i + 1]; q++) if (ci[q] != i && S[tpos[q]]) cnt++;   // |S^T_i|
+    const int q1 = rp[i + 1];
+    for (int q0 = rp[i]; q0 < q1; q0 += 4) {       // |S^T_i|, four entries' loads at a time
+      int jj[4], tp[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) { const bool in = q0 + u < q1; jj[u] = in ? ci[q0 + u] : i; tp[u] = in ? tpos[q0 + u] : 0; }
+#pragma unroll
+      for (int u = 0; u < 4; u++) cnt += jj[u] != i && S[tp[u]];
+    }
     uint64_t z = splitmix64(seed ^ ((uint64_t)level << 40) ^ (uint64_t)(uint32_t)i);
     double h = (double)(z >> 11) * (1.0 / 9007199254740992.0);
     w[i] = add_rn((double)cnt, h);
@@ -1130,13 +1149,13 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
     long long nnz_hint = L.A.nnz >= 0 ? L.A.nnz : (L.nnz_prev > 0 ? L.nnz_prev : (long long)acap);
     L.dinv.ensure(n);
     if (mixed) L.dinv32.ensure(n);
-    k_l1<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, L.dinv.p, mixed ? L.dinv32.p : nullptr);
-    RS_LAUNCHED(1);
     L.f.ensure(n); L.x.ensure(n); L.r.ensure(n); L.t.ensure(n);
     if (mixed) { L.f32.ensure(n); L.x32.ensure(n); L.r32.ensure(n); L.t32.ensure(n); }
     L.cf.ensure(n); L.strong.ensure(acap); L.tpos.ensure(acap);
     L.nc = 0; L.rounds = 0;
     if (n <= o.coarse_max || l == o.max_levels - 1) {      // coarsest: no split (all marks 0)
+      k_l1<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, L.dinv.p, mixed ? L.dinv32.p : nullptr);
+      RS_LAUNCHED(1);
       RS_CUDA(cudaMemsetAsync(L.cf.p, 0, (size_t)n, s));
       h.coarse_dense = 1;
       break;
@@ -1145,7 +1164,8 @@ void amg_setup(amg_hier &h, const rs_opts &o, cudaStream_t s) {
     rs_fill_i(F + AF_CNT, 0, AF_WORDS - AF_CNT, s);
     if (nnz_hint > 8LL * n) k_tpos_warp<<<grid_for((size_t)n * 32, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.tpos.p, F + AF_SYM);
     else k_tpos<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.tpos.p, F + AF_SYM);
-    k_strength<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, o.theta, L.strong.p);
+    k_strength<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, o.theta, L.strong.p, L.dinv.p,
+                                              mixed ? L.dinv32.p : nullptr);
     h.hashw.ensure(n); h.newc.ensure(n); h.plist.ensure(2 * (size_t)n);
     k_pmis_init<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.strong.p, L.tpos.p, o.seed, l,
                                                  h.hashw.p, L.cf.p, h.newc.p, F + AF_CNT, h.plist.p);
