@@ -48,31 +48,27 @@ __global__ void k_scan_partials(const int *in, int n, int *part) {
   block_excl_scan(s, sh, &tot);
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
-__global__ void k_scan_single(int *part, int m) {   // exclusive, in place; part[m] = total
-  __shared__ int sh[SCAN_BS / 32]; __shared__ int tot;
-  int carry = 0;
-  for (int c0 = 0; c0 < m; c0 += SCAN_BS) {
-    int i = c0 + threadIdx.x, v = i < m ? part[i] : 0;
-    int e = block_excl_scan(v, sh, &tot);
-    if (i < m) part[i] = carry + e;
-    carry += tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) part[m] = carry;
-}
 // tail: where the total goes besides part[nblk] (out + n for a row-pointer
-// array, a device counter, or nullptr); tot2 a second copy (or nullptr)
-__global__ void k_scan_final(const int *in, int *out, int n, const int *part, int nblk, int *tail, int *tot2) {
-  __shared__ int sh[SCAN_BS / 32]; __shared__ int tot;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (tail) *tail = part[nblk];
-    if (tot2) *tot2 = part[nblk];
-  }
+// array, a device counter, or nullptr); tot2 a second copy (or nullptr).
+// Each block adds up the partial sums of the blocks before it (at most a few
+// thousand integers, read from L2) instead of waiting for a separate scan of
+// the partials; the last block writes the total.
+__global__ void k_scan_final(const int *in, int *out, int n, int *part, int nblk, int *tail, int *tot2) {
+  __shared__ int sh[SCAN_BS / 32]; __shared__ int tot, off;
+  int o = 0;
+  for (int k = threadIdx.x; k < (int)blockIdx.x; k += SCAN_BS) o += part[k];
+  block_excl_scan(o, sh, &off);                     // off = sum of part[0 .. blockIdx.x - 1]
   int base = blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_IT;
   int v[SCAN_IT], s = 0;
   for (int k = 0; k < SCAN_IT; k++) { v[k] = (base + k < n) ? in[base + k] : 0; s += v[k]; }
-  int e = block_excl_scan(s, sh, &tot) + part[blockIdx.x];
+  int e = block_excl_scan(s, sh, &tot) + off;
   for (int k = 0; k < SCAN_IT; k++) if (base + k < n) { out[base + k] = e; e += v[k]; }
+  if (blockIdx.x == nblk - 1 && threadIdx.x == 0) {
+    const int t = off + tot;
+    part[nblk] = t;
+    if (tail) *tail = t;
+    if (tot2) *tot2 = t;
+  }
 }
 
 int rs_scan(const int *in, int *out, int n, cudaStream_t s) {
@@ -81,9 +77,8 @@ int rs_scan(const int *in, int *out, int n, cudaStream_t s) {
   static thread_local dbuf<int> part;
   part.ensure(nblk + 1);
   k_scan_partials<<<nblk, SCAN_BS, 0, s>>>(in, n, part.p);
-  k_scan_single<<<1, SCAN_BS, 0, s>>>(part.p, nblk);
   k_scan_final<<<nblk, SCAN_BS, 0, s>>>(in, out, n, part.p, nblk, nullptr, nullptr);
-  RS_LAUNCHED(3);
+  RS_LAUNCHED(2);
   RS_CHECK_LAUNCH();
   int tot = 0;
   RS_CUDA(cudaMemcpyAsync(&tot, part.p + nblk, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -130,9 +125,8 @@ void rs_scan_dev(const int *in, int *out, int n, int *tail, int *tot2, cudaStrea
   static thread_local dbuf<int> part;
   part.ensure(nblk + 1);
   k_scan_partials<<<nblk, SCAN_BS, 0, s>>>(in, n, part.p);
-  k_scan_single<<<1, SCAN_BS, 0, s>>>(part.p, nblk);
   k_scan_final<<<nblk, SCAN_BS, 0, s>>>(in, out, n, part.p, nblk, tail, tot2);
-  RS_LAUNCHED(3);
+  RS_LAUNCHED(2);
   RS_CHECK_LAUNCH();
 }
 
