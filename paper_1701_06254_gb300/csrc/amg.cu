@@ -1006,11 +1006,10 @@ __global__ void __launch_bounds__(64) k_dense_inv_cols(int n, const double *lu, 
 }
 
 // ----------------------------------------------------------- host setup ---
+// FP32 values of an FP64 operator (the pattern stays the FP64 operator's)
 static void csr_cast(const csr_dev<double> &a, csr_dev<float> &b, cudaStream_t s) {
   b.n = a.n; b.m = a.m; b.nnz = a.nnz;
-  b.rp.ensure(a.n + 1); b.ci.ensure(a.nnz); b.v.ensure(a.nnz);
-  RS_CUDA(cudaMemcpyAsync(b.rp.p, a.rp.p, (a.n + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
-  if (a.nnz) RS_CUDA(cudaMemcpyAsync(b.ci.p, a.ci.p, a.nnz * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  b.v.ensure(a.nnz);
   rs_cast_d2f(a.v.p, b.v.p, a.nnz, s);
 }
 
@@ -1411,19 +1410,22 @@ static void vc_sweep(int L, int n, const int *rp, const int *ci, const T *v, con
   RS_LAUNCHED(1);
 }
 
+// One level operator as the V-cycle reads it: the FP64 operator's pattern
+// with the values of the cycle's precision (the FP32 copies hold values only).
+template <class T> struct csr_ref { int n, nnz; const int *rp, *ci; const T *v; };
 template <class T> struct lvl_ptrs;
 template <> struct lvl_ptrs<double> {
-  static const csr_dev<double> &A(amg_level &L) { return L.A; }
-  static const csr_dev<double> &P(amg_level &L) { return L.P; }
-  static const csr_dev<double> &R(amg_level &L) { return L.R; }
+  static csr_ref<double> A(amg_level &L) { return {L.A.n, L.A.nnz, L.A.rp.p, L.A.ci.p, L.A.v.p}; }
+  static csr_ref<double> P(amg_level &L) { return {L.P.n, L.P.nnz, L.P.rp.p, L.P.ci.p, L.P.v.p}; }
+  static csr_ref<double> R(amg_level &L) { return {L.R.n, L.R.nnz, L.R.rp.p, L.R.ci.p, L.R.v.p}; }
   static double *dinv(amg_level &L) { return L.dinv.p; }
   static double *f(amg_level &L) { return L.f.p; } static double *x(amg_level &L) { return L.x.p; }
   static double *r(amg_level &L) { return L.r.p; } static double *t(amg_level &L) { return L.t.p; }
 };
 template <> struct lvl_ptrs<float> {
-  static const csr_dev<float> &A(amg_level &L) { return L.A32; }
-  static const csr_dev<float> &P(amg_level &L) { return L.P32; }
-  static const csr_dev<float> &R(amg_level &L) { return L.R32; }
+  static csr_ref<float> A(amg_level &L) { return {L.A.n, L.A.nnz, L.A.rp.p, L.A.ci.p, L.A32.v.p}; }
+  static csr_ref<float> P(amg_level &L) { return {L.P.n, L.P.nnz, L.P.rp.p, L.P.ci.p, L.P32.v.p}; }
+  static csr_ref<float> R(amg_level &L) { return {L.R.n, L.R.nnz, L.R.rp.p, L.R.ci.p, L.R32.v.p}; }
   static float *dinv(amg_level &L) { return L.dinv32.p; }
   static float *f(amg_level &L) { return L.f32.p; } static float *x(amg_level &L) { return L.x32.p; }
   static float *r(amg_level &L) { return L.r32.p; } static float *t(amg_level &L) { return L.t32.p; }
@@ -1433,7 +1435,7 @@ template <class T>
 int amg_vcycle(amg_hier &h, int l, cudaStream_t s) {
   typedef lvl_ptrs<T> LP;
   amg_level &L = h.lev[l];
-  const auto &A = LP::A(L);
+  const csr_ref<T> A = LP::A(L);
   int n = A.n;
   if (l == h.nlev - 1) {
     if (h.coarse_dense) {
@@ -1442,10 +1444,10 @@ int amg_vcycle(amg_hier &h, int l, cudaStream_t s) {
       return 1;
     }
     T *x = LP::x(L), *t = LP::t(L);
-    k_vc_pre<T><<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), x, LP::r(L));
+    k_vc_pre<T><<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, A.v, LP::dinv(L), LP::f(L), x, LP::r(L));
     RS_LAUNCHED(1);
     for (int it = 1; it < 10; it++) {
-      k_jacobi<T><<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), x, t);
+      k_jacobi<T><<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, A.v, LP::dinv(L), LP::f(L), x, t);
       std::swap(x, t);
       RS_LAUNCHED(1);
     }
@@ -1453,19 +1455,19 @@ int amg_vcycle(amg_hier &h, int l, cudaStream_t s) {
     return 10;
   }
   amg_level &Cl = h.lev[l + 1];
-  const auto &P = LP::P(L);
-  const auto &R = LP::R(L);
+  const csr_ref<T> P = LP::P(L);
+  const csr_ref<T> R = LP::R(L);
   int la = lanes_for(A.nnz, n), lr = lanes_for(R.nnz, R.n), lp = lanes_for(P.nnz, n);
   // below level 0 the restriction has already formed x = D^-1 f (pre-smoothing
   // then gathers one vector instead of two; same products, same values)
-  vc_sweep<T, 0>(la, n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), l > 0 ? LP::x(L) : nullptr, LP::x(L),
+  vc_sweep<T, 0>(la, n, A.rp, A.ci, A.v, LP::dinv(L), LP::f(L), l > 0 ? LP::x(L) : nullptr, LP::x(L),
                  LP::r(L), s);
   // the coarse level's D^-1 f, unless that level is solved directly
   bool cx = !(l + 1 == h.nlev - 1 && h.coarse_dense);
-  vc_sweep<T, 1>(lr, R.n, R.rp.p, R.ci.p, R.v.p, LP::dinv(Cl), nullptr, LP::r(L), LP::f(Cl), cx ? LP::x(Cl) : nullptr, s);
+  vc_sweep<T, 1>(lr, R.n, R.rp, R.ci, R.v, LP::dinv(Cl), nullptr, LP::r(L), LP::f(Cl), cx ? LP::x(Cl) : nullptr, s);
   int k = amg_vcycle<T>(h, l + 1, s);
-  vc_sweep<T, 2>(lp, n, P.rp.p, P.ci.p, P.v.p, nullptr, LP::x(L), LP::x(Cl), LP::t(L), nullptr, s);
-  vc_sweep<T, 3>(la, n, A.rp.p, A.ci.p, A.v.p, LP::dinv(L), LP::f(L), LP::t(L), LP::x(L), nullptr, s);
+  vc_sweep<T, 2>(lp, n, P.rp, P.ci, P.v, nullptr, LP::x(L), LP::x(Cl), LP::t(L), nullptr, s);
+  vc_sweep<T, 3>(la, n, A.rp, A.ci, A.v, LP::dinv(L), LP::f(L), LP::t(L), LP::x(L), nullptr, s);
   return k + 4;
 }
 template int amg_vcycle<double>(amg_hier &, int, cudaStream_t);

@@ -144,7 +144,7 @@ template <class T> struct csr_dev { int n = 0, m = 0, nnz = 0; dbuf<int> rp, ci;
 struct amg_level {
   csr_dev<double> A;            // FP64 operator (setup)
   csr_dev<double> P, R;         // interpolation / restriction (FP64)
-  csr_dev<float> A32, P32, R32; // mixed-precision copies
+  csr_dev<float> A32, P32, R32; // mixed-precision values (rp, ci unused: the pattern is A's, P's, R's)
   dbuf<double> dinv;            // 1 / l1 diagonal
   dbuf<float> dinv32;
   dbuf<int8_t> cf;
